@@ -1,0 +1,111 @@
+"""Physics pins of the oracle (fixed points named by the method, Sec. II-III).
+
+* Empty box / empty lattice: the exact solution of Eq. final is the pair of
+  incident-field equivalent currents J = n x H_inc, M = -n x E_inc (Eqs.
+  Heq, Eeq) and nothing is scattered; the discrete solution's scattered far
+  field must be small and shrink as the mesh is refined.  A sign error in
+  any block (L, K, coefficients, U_o, excitation) gives O(1) scattering.
+* PEC patch: the Schur complement (Eq. Zmacromodel) equals solving the
+  unreduced system; a lossless cell obeys the optical theorem
+  (scattered power = extinguished power) and reciprocity.
+* GMRES agrees with dense LU.
+"""
+import numpy as np
+import pytest
+
+from oracle import lattice, macromodel, operators, solve
+from oracle.mesh import box_mesh, patch_mesh
+
+LAM = 0.03
+K0 = 2 * np.pi / LAM
+A = B = 0.5 * LAM
+H = 0.25 * LAM
+COEF = (1j * K0, 1.0, -1.0, 1j * K0)
+KHAT = np.array([0.0, 0.0, -1.0])
+EHAT = np.array([1.0, 0.0, 0.0])
+
+
+def _dirs(nth=19, nph=37):
+    th = np.linspace(0, np.pi, nth)
+    ph = np.linspace(0, 2 * np.pi, nph)
+    TH, PH = np.meshgrid(th, ph)
+    return np.stack([np.sin(TH) * np.cos(PH), np.sin(TH) * np.sin(PH), np.cos(TH)], -1).reshape(-1, 3)
+
+
+def _lattice_solution(n, nx, ny, Ztypes, tmap):
+    box = box_mesh(A, B, H, n)
+    idx, sgn, nu = lattice.overlap_map(box, nx, ny, A, B)
+    Ad = lattice.assemble_dense(box, nx, ny, A, B, K0, COEF, Ztypes, tmap, idx, sgn, nu)
+    V = np.concatenate([operators.excitation(box, lattice.cell_shift(m % nx, m // nx, A, B),
+                                             K0, KHAT, EHAT) for m in range(nx * ny)])
+    Vt = lattice.scatter(V, idx, sgn, nu)
+    x = solve.dense_solve(Ad, Vt)
+    return box, Ad, Vt, x, idx, sgn, nu
+
+
+def _scatter_ratio(box, nx, ny, Y):
+    E = box.n_rwg
+    rh = _dirs()
+    F = 0
+    FJ = 0
+    for m in range(nx * ny):
+        rad = operators.radiation_vectors(box, lattice.cell_shift(m % nx, m // nx, A, B), K0, rh)
+        F = F + operators.far_field(rad, rh, K0, Y[m, :E], Y[m, E:])
+        FJ = FJ + operators.far_field(rad, rh, K0, Y[m, :E], 0 * Y[m, E:])
+    return np.abs(F).max() / np.abs(FJ).max()
+
+
+def test_empty_box_scatters_nothing_and_converges():
+    ratios = []
+    for n in (2, 3):
+        box = box_mesh(A, B, H, n)
+        Z = macromodel.empty_box(box, K0)
+        _, _, Vt, x, idx, sgn, nu = _lattice_solution(n, 1, 1, Z[None], np.array([0]))
+        ratios.append(_scatter_ratio(box, 1, 1, x.reshape(1, -1)))
+    assert ratios[0] < 0.03 and ratios[1] < 0.01 and ratios[1] < 0.6 * ratios[0]
+
+
+def test_empty_lattice_with_merged_faces_scatters_nothing():
+    n, nx, ny = 2, 2, 2
+    box = box_mesh(A, B, H, n)
+    Z = macromodel.empty_box(box, K0)
+    box, Ad, Vt, x, idx, sgn, nu = _lattice_solution(n, nx, ny, Z[None], np.zeros(4, int))
+    Y = lattice.gather(x, idx, sgn, nx * ny, 2 * box.n_rwg)
+    assert _scatter_ratio(box, nx, ny, Y) < 0.03
+    # GMRES (plain, restarted) reaches the LU solution
+    xg, it, hist = solve.gmres(lambda v: Ad @ v, Vt, rtol=1e-12, restart=30)
+    assert np.linalg.norm(xg - x) <= 1e-9 * np.linalg.norm(x)
+    assert np.linalg.norm(Ad @ xg - Vt) <= 2e-12 * np.linalg.norm(Vt)
+
+
+@pytest.mark.parametrize("n,npatch", [(2, 3), (3, 4)])
+def test_pec_patch_macromodel(n, npatch):
+    box = box_mesh(A, B, H, n)
+    E = box.n_rwg
+    sheet = patch_mesh(0.3 * LAM, 0.76e-3, npatch)
+    Zt = macromodel.pec_patch(box, sheet, K0)
+    Z0 = macromodel.empty_box(box, K0)        # outer self block B(0) = free-space S_eq operator
+    V = operators.excitation(box, (0, 0, 0), K0, KHAT, EHAT)
+    x = np.linalg.solve(Zt + Z0, V)
+    # Schur step equals the unreduced solve (brute force)
+    Zf, neq = macromodel.pec_sheet_system(box, sheet, K0)
+    Zf[:neq, :neq] += Z0
+    xf = np.linalg.solve(Zf, np.concatenate([V, np.zeros(sheet.n_rwg)]))
+    assert np.linalg.norm(xf[:neq] - x) <= 1e-12 * np.linalg.norm(x)
+    # reciprocity Z~^T = S Z~ S to quadrature accuracy
+    S = np.concatenate([np.ones(E), -np.ones(E)])
+    assert np.linalg.norm(Zt.T - S[:, None] * Zt * S[None, :]) <= 0.03 * np.linalg.norm(Zt)
+    # optical theorem (lossless): sigma_sca = -(4 pi/k) Im[F(khat) . e*]  (e^{jwt})
+    nth, nph = 40, 80
+    th = (np.arange(nth) + 0.5) * np.pi / nth
+    ph = np.arange(nph) * 2 * np.pi / nph
+    TH, PH = np.meshgrid(th, ph, indexing="ij")
+    rh = np.stack([np.sin(TH) * np.cos(PH), np.sin(TH) * np.sin(PH), np.cos(TH)], -1).reshape(-1, 3)
+    dW = (np.pi / nth) * (2 * np.pi / nph) * np.sin(TH).reshape(-1)
+    rad = operators.radiation_vectors(box, (0, 0, 0), K0, rh)
+    F = operators.far_field(rad, rh, K0, x[:E], x[E:])
+    sca = np.sum(np.sum(np.abs(F) ** 2, -1) * dW)
+    Ff = operators.far_field(operators.radiation_vectors(box, (0, 0, 0), K0, KHAT[None]),
+                             KHAT[None], K0, x[:E], x[E:])[0]
+    ext = -(4 * np.pi / K0) * np.imag(Ff @ EHAT)
+    assert ext > 0 and abs(sca - ext) <= 0.01 * ext
