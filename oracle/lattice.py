@@ -60,7 +60,6 @@ def overlap_map(box, nx, ny, a, b):
     E = box.n_rwg
     M = nx * ny
     scale = 1e-9 * max(a, b)
-    tri_key = {}
     edge_members = {}
     for iy in range(ny):
         for ix in range(nx):
@@ -180,6 +179,56 @@ def assemble_dense(box, nx, ny, a, b, k, coef, macromodels, type_map, index, sig
             L, K = galerkin_LK(box, cell_shift(ix, iy, a, b), box, cell_shift(jx, jy, a, b),
                                k, sing)
             Z[m * Kl:(m + 1) * Kl, ms * Kl:(ms + 1) * Kl] = coupling_block(L, K, coef)
+        Z[m * Kl:(m + 1) * Kl, m * Kl:(m + 1) * Kl] += macromodels[type_map[m]]
+    U = np.zeros((M * Kl, n_unique))
+    U[np.arange(M * Kl), index] = sign
+    return U.T @ Z @ U
+
+
+def _block(Lt, Kt, coef, dx, dy, nx, ny):
+    return coupling_block(Lt[dy + ny - 1, dx + nx - 1], Kt[dy + ny - 1, dx + nx - 1], coef)
+
+
+def matvec_direct_rows(x, rows, Lt, Kt, coef, macromodels, type_map, index, sign, nx, ny):
+    """Entries ``rows`` of y = U_o^T [Z_eq + Z_o] U_o x, one at a time:
+    y[u] = sum over local unknowns (m,k) of u of sign * (row k of
+    sum_m' B(c_m - c_m') x1^(m') + Z~^{t(m)} x1^(m))."""
+    E = Lt.shape[-1]
+    Kl = 2 * E
+    M = nx * ny
+    x1 = gather(np.asarray(x), index, sign, M, Kl)
+    out = np.zeros(len(rows), dtype=complex)
+    for q, u in enumerate(rows):
+        for loc in np.nonzero(index == u)[0]:
+            m, k = divmod(int(loc), Kl)
+            ix, iy = m % nx, m // nx
+            acc = macromodels[type_map[m]][k] @ x1[m]
+            for ms in range(M):
+                jx, jy = ms % nx, ms // nx
+                dx, dy = ix - jx, iy - jy
+                half, kk = divmod(k, E)
+                Lr = Lt[dy + ny - 1, dx + nx - 1][kk]
+                Kr = Kt[dy + ny - 1, dx + nx - 1][kk]
+                al, be, ga, de = coef
+                if half == 0:
+                    acc += al * (Lr @ x1[ms, :E]) + be * (Kr @ x1[ms, E:])
+                else:
+                    acc += ga * (Kr @ x1[ms, :E]) + de * (Lr @ x1[ms, E:])
+            out[q] += sign[loc] * acc
+    return out
+
+
+def assemble_from_tables(Lt, Kt, coef, macromodels, type_map, index, sign, n_unique, nx, ny):
+    """Dense U_o^T [Z_eq + Z_o] U_o built block by block from the offset tables."""
+    E = Lt.shape[-1]
+    Kl = 2 * E
+    M = nx * ny
+    Z = np.zeros((M * Kl, M * Kl), dtype=complex)
+    for m in range(M):
+        ix, iy = m % nx, m // nx
+        for ms in range(M):
+            jx, jy = ms % nx, ms // nx
+            Z[m * Kl:(m + 1) * Kl, ms * Kl:(ms + 1) * Kl] = _block(Lt, Kt, coef, ix - jx, iy - jy, nx, ny)
         Z[m * Kl:(m + 1) * Kl, m * Kl:(m + 1) * Kl] += macromodels[type_map[m]]
     U = np.zeros((M * Kl, n_unique))
     U[np.arange(M * Kl), index] = sign

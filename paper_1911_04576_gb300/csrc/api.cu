@@ -1,0 +1,291 @@
+// C ABI entry points: create / matvec / solve / query / destroy.
+#include <algorithm>
+#include <cstdarg>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+namespace emsurf {
+
+namespace {
+thread_local char g_err[512] = "";
+}
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+int dev_alloc(emsurf_handle* h, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (h->budget > 0 && h->device_bytes + (int64_t)bytes > h->budget) {
+        set_error("device memory budget exceeded: %lld + %zu > %lld bytes",
+                  (long long)h->device_bytes, bytes, (long long)h->budget);
+        return EMSURF_ENOMEM;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+        return EMSURF_ENOMEM;
+    }
+    h->allocations.push_back(*p);
+    h->device_bytes += (int64_t)bytes;
+    return EMSURF_OK;
+}
+
+namespace {
+
+class DeviceGuard {
+public:
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev_);
+        ok_ = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() { cudaSetDevice(prev_); }
+    bool ok() const { return ok_; }
+
+private:
+    int prev_ = 0;
+    bool ok_ = false;
+};
+
+int validate(const emsurf_problem* p) {
+    if (!p) { set_error("problem is NULL"); return EMSURF_EINVAL; }
+    if (p->nx < 1 || p->ny < 1 || p->n_edges < 1 || p->n_types < 1 || p->n_unique < 1) {
+        set_error("nx, ny, n_edges, n_types, n_unique must be >= 1");
+        return EMSURF_EINVAL;
+    }
+    if (p->max_rhs < 1 || p->max_rhs > 64) {
+        set_error("max_rhs must be in [1, 64]");
+        return EMSURF_EINVAL;
+    }
+    if (p->precision < EMSURF_FP64 || p->precision > EMSURF_MIXED) {
+        set_error("unknown precision %d", p->precision);
+        return EMSURF_EINVAL;
+    }
+    if (!p->type_map || !p->macromodels || !p->offset_L || !p->offset_K || !p->uo_index ||
+        !p->uo_sign) {
+        set_error("a required input pointer is NULL");
+        return EMSURF_EINVAL;
+    }
+    if ((p->grid_px && p->grid_px < 2 * p->nx - 1) || (p->grid_py && p->grid_py < 2 * p->ny - 1)) {
+        set_error("grid must be at least (2nx-1) x (2ny-1)");
+        return EMSURF_EINVAL;
+    }
+    const int64_t M = (int64_t)p->nx * p->ny, K = 2LL * p->n_edges;
+    if (M * K > INT32_MAX) { set_error("too many local unknowns"); return EMSURF_EINVAL; }
+    for (int64_t m = 0; m < M; ++m)
+        if (p->type_map[m] < 0 || p->type_map[m] >= p->n_types) {
+            set_error("type_map[%lld] = %d out of range", (long long)m, p->type_map[m]);
+            return EMSURF_EINVAL;
+        }
+    for (int64_t e = 0; e < M * K; ++e) {
+        if (p->uo_index[e] < 0 || p->uo_index[e] >= p->n_unique) {
+            set_error("uo_index[%lld] = %d out of range", (long long)e, p->uo_index[e]);
+            return EMSURF_EINVAL;
+        }
+        if (p->uo_sign[e] != 1 && p->uo_sign[e] != -1) {
+            set_error("uo_sign[%lld] = %d is not +-1", (long long)e, (int)p->uo_sign[e]);
+            return EMSURF_EINVAL;
+        }
+    }
+    return EMSURF_OK;
+}
+
+template <typename T>
+int upload(emsurf_handle* h, T** d, const T* src, size_t n) {
+    EMS_TRY(dev_alloc(h, (void**)d, n * sizeof(T)));
+    EMS_CUDA(cudaMemcpy(*d, src, n * sizeof(T), cudaMemcpyHostToDevice));
+    return EMSURF_OK;
+}
+
+int create_impl(const emsurf_problem* p, emsurf_handle* h) {
+    h->device = p->device;
+    h->nx = p->nx;
+    h->ny = p->ny;
+    h->E = p->n_edges;
+    h->K = 2 * p->n_edges;
+    h->M = p->nx * p->ny;
+    h->T = p->n_types;
+    h->n_unique = p->n_unique;
+    h->max_rhs = p->max_rhs;
+    h->precision = p->precision;
+    h->budget = p->device_mem_budget;
+    h->px = p->grid_px ? p->grid_px : smallest_smooth_at_least(2 * p->nx - 1);
+    h->py = p->grid_py ? p->grid_py : smallest_smooth_at_least(2 * p->ny - 1);
+    h->nbins = h->px * h->py;
+    EMS_TRY(fft_plan_create(h->plan_x, h->px));
+    EMS_TRY(fft_plan_create(h->plan_y, h->py));
+    const int M = h->M, K = h->K;
+    const size_t MK = (size_t)M * K;
+    // U_o and its inverse (CSR by unique unknown, local entries in scan order)
+    EMS_TRY(upload(h, &h->d_uo_index, p->uo_index, MK));
+    EMS_TRY(upload(h, &h->d_uo_sign, p->uo_sign, MK));
+    std::vector<int32_t> ptr(h->n_unique + 1, 0), ent(MK);
+    std::vector<int8_t> esg(MK);
+    for (size_t e = 0; e < MK; ++e) ptr[p->uo_index[e] + 1]++;
+    for (int u = 0; u < h->n_unique; ++u) ptr[u + 1] += ptr[u];
+    std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+    for (size_t e = 0; e < MK; ++e) {
+        const int u = p->uo_index[e];
+        ent[fill[u]] = (int32_t)e;
+        esg[fill[u]] = p->uo_sign[e];
+        fill[u]++;
+    }
+    for (int u = 0; u < h->n_unique; ++u)
+        if (ptr[u + 1] == ptr[u]) {
+            set_error("unique unknown %d is referenced by no local unknown", u);
+            return EMSURF_EINVAL;
+        }
+    EMS_TRY(upload(h, &h->d_inv_ptr, ptr.data(), ptr.size()));
+    EMS_TRY(upload(h, &h->d_inv_ent, ent.data(), MK));
+    EMS_TRY(upload(h, &h->d_inv_sgn, esg.data(), MK));
+    // cells grouped by type; macromodel work list in groups of 4 cells
+    std::vector<int32_t> tptr(h->T + 1, 0), cells(M);
+    for (int m = 0; m < M; ++m) tptr[p->type_map[m] + 1]++;
+    for (int t = 0; t < h->T; ++t) tptr[t + 1] += tptr[t];
+    {
+        std::vector<int32_t> f(tptr.begin(), tptr.end() - 1);
+        for (int m = 0; m < M; ++m) cells[f[p->type_map[m]]++] = m;
+    }
+    std::vector<int32_t> blocks;
+    for (int t = 0; t < h->T; ++t)
+        for (int s = tptr[t]; s < tptr[t + 1]; s += 4) {
+            blocks.push_back(t);
+            blocks.push_back(s);
+            blocks.push_back(std::min(4, tptr[t + 1] - s));
+        }
+    h->h_type_ptr = tptr;
+    h->n_mm_blocks = (int)(blocks.size() / 3);
+    EMS_TRY(upload(h, &h->d_type_map, p->type_map, (size_t)M));
+    EMS_TRY(upload(h, &h->d_type_cells, cells.data(), (size_t)M));
+    EMS_TRY(upload(h, &h->d_type_ptr, tptr.data(), tptr.size()));
+    int32_t* dblk = nullptr;
+    EMS_TRY(upload(h, &dblk, blocks.data(), blocks.size()));
+    h->d_mm_blocks = dblk;
+    // operators
+    if (h->precision == EMSURF_FP64 || h->precision == EMSURF_MIXED) {
+        EMS_TRY(build_operator<double2>(h, h->op64, p));
+        h->have64 = true;
+    }
+    if (h->precision == EMSURF_FP32 || h->precision == EMSURF_MIXED) {
+        EMS_TRY(build_operator<float2>(h, h->op32, p));
+        h->have32 = true;
+    }
+    EMS_CUDA(cudaDeviceSynchronize());
+    return EMSURF_OK;
+}
+
+void free_handle(emsurf_handle* h) {
+    for (void* p : h->allocations) cudaFree(p);
+    h->allocations.clear();
+    fft_plan_destroy(h->plan_x);
+    fft_plan_destroy(h->plan_y);
+    delete h;
+}
+
+}  // namespace
+
+void gmres_release(emsurf_handle* h);
+
+}  // namespace emsurf
+
+using namespace emsurf;
+
+extern "C" {
+
+EMSURF_API const char* emsurf_last_error(void) { return g_err; }
+
+EMSURF_API int emsurf_create(const emsurf_problem* problem, emsurf_handle** out) {
+    if (!out) { set_error("out is NULL"); return EMSURF_EINVAL; }
+    *out = nullptr;
+    EMS_TRY(validate(problem));
+    DeviceGuard dg(problem->device);
+    if (!dg.ok()) { set_error("cannot select device %d", problem->device); return EMSURF_EINVAL; }
+    emsurf_handle* h = new (std::nothrow) emsurf_handle();
+    if (!h) { set_error("host allocation failed"); return EMSURF_ENOMEM; }
+    const int s = create_impl(problem, h);
+    if (s != EMSURF_OK) {
+        cudaDeviceSynchronize();
+        gmres_release(h);
+        free_handle(h);
+        return s;
+    }
+    *out = h;
+    return EMSURF_OK;
+}
+
+EMSURF_API int emsurf_matvec(emsurf_handle* h, const emsurf_c128* x, emsurf_c128* y, int32_t nrhs,
+                             int32_t precision, void* stream) {
+    if (!h || !x || !y) { set_error("NULL handle or vector"); return EMSURF_EINVAL; }
+    if (nrhs < 1 || nrhs > h->max_rhs) {
+        set_error("nrhs %d outside [1, %d]", nrhs, h->max_rhs);
+        return EMSURF_EINVAL;
+    }
+    const size_t n = (size_t)nrhs * h->n_unique;
+    const char* xa = reinterpret_cast<const char*>(x);
+    const char* ya = reinterpret_cast<const char*>(y);
+    if (xa < ya + n * sizeof(emsurf_c128) && ya < xa + n * sizeof(emsurf_c128)) {
+        set_error("x and y overlap");
+        return EMSURF_EINVAL;
+    }
+    DeviceGuard dg(h->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (precision == EMSURF_FP64) {
+        if (!h->have64) { set_error("FP64 operator not resident"); return EMSURF_EINVAL; }
+        return apply_operator<double2>(h, h->op64, reinterpret_cast<const double2*>(x),
+                                       reinterpret_cast<double2*>(y), nrhs, st);
+    }
+    if (precision == EMSURF_FP32) {
+        if (!h->have32) { set_error("FP32 operator not resident"); return EMSURF_EINVAL; }
+        return apply_operator<float2>(h, h->op32, reinterpret_cast<const double2*>(x),
+                                      reinterpret_cast<double2*>(y), nrhs, st);
+    }
+    set_error("matvec precision must be EMSURF_FP64 or EMSURF_FP32");
+    return EMSURF_EINVAL;
+}
+
+EMSURF_API int emsurf_solve(emsurf_handle* h, const emsurf_c128* b, emsurf_c128* x, int32_t nrhs,
+                            const emsurf_solve_opts* opts, emsurf_solve_info* info, void* stream) {
+    if (!h || !b || !x || !opts) { set_error("NULL argument"); return EMSURF_EINVAL; }
+    if (nrhs < 1 || nrhs > h->max_rhs) {
+        set_error("nrhs %d outside [1, %d]", nrhs, h->max_rhs);
+        return EMSURF_EINVAL;
+    }
+    if (!(opts->rtol > 0.0) || opts->restart < 1 || opts->restart > 64 || opts->max_iters < 1) {
+        set_error("need rtol > 0, restart in [1, 64], max_iters >= 1");
+        return EMSURF_EINVAL;
+    }
+    if (h->precision == EMSURF_MIXED && opts->max_refine < 1) {
+        set_error("MIXED solve needs max_refine >= 1");
+        return EMSURF_EINVAL;
+    }
+    DeviceGuard dg(h->device);
+    return gmres_solve(h, reinterpret_cast<const double2*>(b), reinterpret_cast<double2*>(x), nrhs,
+                       opts, info, reinterpret_cast<cudaStream_t>(stream));
+}
+
+EMSURF_API int emsurf_query(const emsurf_handle* h, int32_t* grid_px, int32_t* grid_py,
+                            int64_t* device_bytes) {
+    if (!h) { set_error("NULL handle"); return EMSURF_EINVAL; }
+    if (grid_px) *grid_px = h->px;
+    if (grid_py) *grid_py = h->py;
+    if (device_bytes) *device_bytes = h->device_bytes;
+    return EMSURF_OK;
+}
+
+EMSURF_API void emsurf_destroy(emsurf_handle* h) {
+    if (!h) return;
+    DeviceGuard dg(h->device);
+    cudaDeviceSynchronize();
+    gmres_release(h);
+    free_handle(h);
+}
+
+}  // extern "C"

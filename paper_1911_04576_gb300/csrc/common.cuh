@@ -1,0 +1,147 @@
+// Shared device helpers and the handle layout of the emsurf library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "emsurf.h"
+
+namespace emsurf {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+
+#define EMS_CUDA(call)                                                         \
+    do {                                                                       \
+        cudaError_t _e = (call);                                               \
+        if (_e != cudaSuccess) {                                               \
+            ::emsurf::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call,     \
+                                cudaGetErrorString(_e));                       \
+            return EMSURF_ECUDA;                                               \
+        }                                                                      \
+    } while (0)
+
+#define EMS_TRY(expr)                                                          \
+    do {                                                                       \
+        int _s = (expr);                                                       \
+        if (_s != EMSURF_OK) return _s;                                        \
+    } while (0)
+
+// ---------------------------------------------------------------- complex
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// acc += a * b
+__device__ __forceinline__ void cfma(double2& acc, double2 a, double2 b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+__device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+}
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) {
+    return make_double2(a.x + b.x, a.y + b.y);
+}
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+    return make_float2(a.x + b.x, a.y + b.y);
+}
+
+template <typename T2> struct Real;
+template <> struct Real<double2> { using type = double; };
+template <> struct Real<float2> { using type = float; };
+
+template <typename T2> __host__ __device__ __forceinline__ T2 mk(double re, double im);
+template <> __host__ __device__ __forceinline__ double2 mk<double2>(double re, double im) {
+    return make_double2(re, im);
+}
+template <> __host__ __device__ __forceinline__ float2 mk<float2>(double re, double im) {
+    return make_float2((float)re, (float)im);
+}
+
+// ---------------------------------------------------------------- FFT plan
+// One 1-D transform length P = product of radices (each 2, 3, 4 or 5) with
+// a device table tw[k] = exp(-2 pi i k / P), k in [0, P), from host libm.
+struct FftPlan {
+    int P = 0;
+    int nrad = 0;
+    int rad[16] = {0};
+    double2* tw = nullptr;   // device
+};
+
+int fft_plan_create(FftPlan& plan, int P);
+void fft_plan_destroy(FftPlan& plan);
+
+// In-place 1-D transform along p of data[outer][P][inner] (inner contiguous
+// lanes, outer stride outer_stride elements).  sign = -1 forward, +1 inverse
+// (unscaled).
+template <typename T2>
+int fft_pass(T2* data, const FftPlan& plan, long long inner, long long outer,
+             long long outer_stride, int sign, cudaStream_t st);
+
+int smallest_smooth_at_least(int n);   // smallest 2^a 3^b 5^c >= n
+
+// ---------------------------------------------------------------- operator
+// Fourier-domain blocks of one precision: B^[bin][op][j][i] (op 0 = L, 1 = K,
+// stored transposed: source index j outer, test index i contiguous) and the
+// macromodels transposed Zt[type][k'][k].
+template <typename T2>
+struct Operator {
+    T2* Bhat = nullptr;
+    T2* Zt = nullptr;
+    T2* Xg = nullptr;      // work grid [bins][R][2E] (forward)
+    T2* Yg = nullptr;      // work grid [bins][R][2E] (inverse)
+    T2* Ymm = nullptr;     // macromodel output [R][M][2E]
+    T2 coef[4];
+};
+
+}  // namespace emsurf
+
+struct emsurf_handle {
+    int device = 0;
+    int nx = 0, ny = 0, E = 0, K = 0, M = 0, T = 0, n_unique = 0, max_rhs = 1;
+    int px = 0, py = 0, nbins = 0;
+    int precision = EMSURF_FP64;
+    int64_t device_bytes = 0;
+    int64_t budget = 0;
+    emsurf::FftPlan plan_x, plan_y;
+    // U_o: forward map and its inverse (CSR over unique unknowns)
+    int32_t* d_uo_index = nullptr;
+    int8_t* d_uo_sign = nullptr;
+    int32_t* d_inv_ptr = nullptr;     // [n_unique + 1]
+    int32_t* d_inv_ent = nullptr;     // [M*K] local unknown (m*K + k), signed via d_inv_sgn
+    int8_t* d_inv_sgn = nullptr;
+    int32_t* d_type_map = nullptr;    // [M]
+    int32_t* d_type_cells = nullptr;  // cells grouped by type [M]
+    int32_t* d_type_ptr = nullptr;    // [T + 1]
+    std::vector<int32_t> h_type_ptr;
+    void* d_mm_blocks = nullptr;      // macromodel work list (type, first, count)
+    int n_mm_blocks = 0;
+    emsurf::Operator<double2> op64;
+    emsurf::Operator<float2> op32;
+    bool have64 = false, have32 = false;
+    // GMRES workspace (FP64), allocated lazily by emsurf_solve
+    void* gm = nullptr;
+    std::vector<void*> allocations;
+};
+
+namespace emsurf {
+int dev_alloc(emsurf_handle* h, void** p, size_t bytes);
+template <typename T2>
+int build_operator(emsurf_handle* h, Operator<T2>& op, const emsurf_problem* pr);
+template <typename T2>
+int apply_operator(emsurf_handle* h, Operator<T2>& op, const double2* x, double2* y, int nrhs,
+                   cudaStream_t st);
+int gmres_solve(emsurf_handle* h, const double2* b, double2* x, int nrhs,
+                const emsurf_solve_opts* o, emsurf_solve_info* info, cudaStream_t st);
+}  // namespace emsurf

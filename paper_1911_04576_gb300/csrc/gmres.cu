@@ -1,0 +1,504 @@
+// Restarted GMRES on the device for Eq. final (Sec. IV-A).
+//
+// The paper solves Eq. final with GMRES (PETSc); restart length, initial
+// guess and orthogonalisation are not given.  Here: zero initial guess,
+// GMRES(m) with classical Gram-Schmidt applied twice (two reductions per
+// Arnoldi step instead of j+1), Givens rotations and the upper-triangular
+// solve on the device, all in FP64.  Right-hand sides are independent
+// systems that share every operator application.
+//
+// MIXED precision: iterative refinement with FP64 residuals
+//   r = b - A64 x;  solve A32 d = r with FP32-operator GMRES to inner_rtol;
+//   x += d;  until ||r|| / ||b|| <= rtol.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace emsurf {
+
+namespace {
+
+constexpr int kRedBlocks = 304;     // 2 x 152 SMs
+constexpr int kRedThreads = 256;
+
+struct Gm {
+    int m = 0, R = 0;
+    size_t n = 0;
+    double2* V = nullptr;      // [(m+1)][R][n]
+    double2* w = nullptr;      // [R][n]
+    double2* r0 = nullptr;     // [R][n]
+    double2* d = nullptr;      // [R][n] FP64 residual of the refinement (mixed)
+    double2* c = nullptr;      // [R][n] correction of the refinement (mixed)
+    double2* H = nullptr;      // [R][m][m+1]  column j at H[r][j][0..j+1]
+    double2* cs = nullptr;     // [R][m]
+    double2* sn = nullptr;     // [R][m]
+    double2* g = nullptr;      // [R][m+1]
+    double2* hv = nullptr;     // [R][m+1] projections of one CGS pass
+    double2* part = nullptr;   // [R][m+1][kRedBlocks]
+    double* nrm = nullptr;     // [R]
+    double* bnorm = nullptr;   // [R]
+    double* res = nullptr;     // [R] estimated relative residual
+    int* active = nullptr;     // [R]
+    int* jend = nullptr;       // [R]
+    double* h_res = nullptr;   // pinned host mirror [R]
+    int* h_act = nullptr;      // pinned host mirror [R]
+};
+
+__device__ __forceinline__ double2 conj_mul(double2 a, double2 b) {   // conj(a) * b
+    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+
+__device__ __forceinline__ double2 warp_sum(double2 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+
+// part[r][i][blk] = sum over this block's slice of conj(V_i[r]) . w[r]
+__global__ void dot_partial_kernel(const double2* __restrict__ V, int nvec, size_t vstride,
+                                   const double2* __restrict__ w, size_t n, int R,
+                                   double2* __restrict__ part, int ldv) {
+    __shared__ double2 red[kRedThreads / 32];
+    const int i = blockIdx.y, r = blockIdx.z;
+    const double2* a = V + (size_t)i * vstride + (size_t)r * n;
+    const double2* b = w + (size_t)r * n;
+    double2 acc = make_double2(0.0, 0.0);
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const double2 p = conj_mul(a[e], b[e]);
+        acc.x += p.x;
+        acc.y += p.y;
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double2 v = threadIdx.x < blockDim.x / 32 ? red[threadIdx.x] : make_double2(0.0, 0.0);
+        v = warp_sum(v);
+        if (threadIdx.x == 0) part[((size_t)r * ldv + i) * gridDim.x + blockIdx.x] = v;
+    }
+    (void)nvec;
+}
+
+// hv[r][i] = sum_blk part[r][i][blk]; mode 0: H col = hv, 1: H col += hv,
+// 2: nrm[r] = sqrt(Re hv[r][0])
+__global__ void dot_final_kernel(const double2* __restrict__ part, int nblk, int nvec, int ldv,
+                                 double2* __restrict__ hv, double2* __restrict__ H, int m, int j,
+                                 double* __restrict__ nrm, int mode) {
+    const int i = blockIdx.x, r = blockIdx.y;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int b = threadIdx.x; b < nblk; b += 32) {
+        const double2 v = part[((size_t)r * ldv + i) * nblk + b];
+        acc.x += v.x;
+        acc.y += v.y;
+    }
+    acc = warp_sum(acc);
+    if (threadIdx.x == 0) {
+        hv[(size_t)r * ldv + i] = acc;
+        double2* col = H + ((size_t)r * m + j) * (m + 1);
+        if (mode == 0) col[i] = acc;
+        else if (mode == 1) col[i] = make_double2(col[i].x + acc.x, col[i].y + acc.y);
+        else nrm[r] = sqrt(fmax(acc.x, 0.0));
+    }
+    (void)nvec;
+}
+
+// w[r] -= sum_{i<nvec} hv[r][i] V_i[r]
+__global__ void cgs_update_kernel(const double2* __restrict__ V, int nvec, size_t vstride,
+                                  const double2* __restrict__ hv, int ldv, double2* __restrict__ w,
+                                  size_t n, int R) {
+    const size_t total = (size_t)R * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / n);
+        double2 acc = w[e];
+        for (int i = 0; i < nvec; ++i) {
+            const double2 c = hv[(size_t)r * ldv + i];
+            const double2 v = V[(size_t)i * vstride + e];
+            acc.x -= c.x * v.x - c.y * v.y;
+            acc.y -= c.x * v.y + c.y * v.x;
+        }
+        w[e] = acc;
+    }
+}
+
+// dst[r] = src[r] / nrm[r] (0 if nrm == 0); optionally H[j+1][j] = nrm
+__global__ void normalize_kernel(double2* __restrict__ dst, const double2* __restrict__ src,
+                                 const double* __restrict__ nrm, size_t n, int R,
+                                 double2* __restrict__ H, int m, int j) {
+    const size_t total = (size_t)R * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / n);
+        const double s = nrm[r] > 0.0 ? 1.0 / nrm[r] : 0.0;
+        const double2 v = src[e];
+        dst[e] = make_double2(v.x * s, v.y * s);
+    }
+    if (H != nullptr && blockIdx.x == 0 && threadIdx.x < R) {
+        const int r = threadIdx.x;
+        H[((size_t)r * m + j) * (m + 1) + j + 1] = make_double2(nrm[r], 0.0);
+    }
+}
+
+// r0 = b - w
+__global__ void residual_kernel(double2* __restrict__ r0, const double2* __restrict__ b,
+                                const double2* __restrict__ w, size_t total) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x)
+        r0[e] = make_double2(b[e].x - w[e].x, b[e].y - w[e].y);
+}
+
+// start of a cycle: g = [beta, 0...], res = beta/bnorm, active = res > rtol
+__global__ void cycle_start_kernel(const double* __restrict__ nrm, const double* __restrict__ bnorm,
+                                   double2* __restrict__ g, double* __restrict__ res,
+                                   int* __restrict__ active, int* __restrict__ jend, int m, int R,
+                                   double rtol) {
+    const int r = threadIdx.x;
+    if (r >= R) return;
+    const double bn = bnorm[r] > 0.0 ? bnorm[r] : 1.0;
+    res[r] = nrm[r] / bn;
+    active[r] = res[r] > rtol ? 1 : 0;
+    jend[r] = 0;
+    for (int i = 0; i <= m; ++i) g[(size_t)r * (m + 1) + i] = make_double2(0.0, 0.0);
+    g[(size_t)r * (m + 1)] = make_double2(nrm[r], 0.0);
+}
+
+// Givens update of column j for every active right-hand side.
+__global__ void givens_kernel(double2* __restrict__ H, double2* __restrict__ cs,
+                              double2* __restrict__ sn, double2* __restrict__ g,
+                              const double* __restrict__ bnorm, double* __restrict__ res,
+                              int* __restrict__ active, int* __restrict__ jend, int m, int j, int R,
+                              double rtol) {
+    const int r = threadIdx.x;
+    if (r >= R || !active[r]) return;
+    double2* col = H + ((size_t)r * m + j) * (m + 1);
+    double2* c = cs + (size_t)r * m;
+    double2* s = sn + (size_t)r * m;
+    for (int i = 0; i < j; ++i) {
+        const double2 a = col[i], b = col[i + 1];
+        // [conj(c) conj(s); -s c] [a; b]
+        const double2 t = make_double2(c[i].x * a.x + c[i].y * a.y + s[i].x * b.x + s[i].y * b.y,
+                                       c[i].x * a.y - c[i].y * a.x + s[i].x * b.y - s[i].y * b.x);
+        col[i + 1] = make_double2(-(s[i].x * a.x - s[i].y * a.y) + (c[i].x * b.x - c[i].y * b.y),
+                                  -(s[i].x * a.y + s[i].y * a.x) + (c[i].x * b.y + c[i].y * b.x));
+        col[i] = t;
+    }
+    const double2 a = col[j], b = col[j + 1];
+    const double den = sqrt(a.x * a.x + a.y * a.y + b.x * b.x + b.y * b.y);
+    double2 cj, sj;
+    if (den > 0.0) {
+        cj = make_double2(a.x / den, a.y / den);
+        sj = make_double2(b.x / den, b.y / den);
+    } else {
+        cj = make_double2(1.0, 0.0);
+        sj = make_double2(0.0, 0.0);
+    }
+    c[j] = cj;
+    s[j] = sj;
+    col[j] = make_double2(den, 0.0);
+    col[j + 1] = make_double2(0.0, 0.0);
+    double2* gg = g + (size_t)r * (m + 1);
+    const double2 gj = gg[j];
+    gg[j + 1] = make_double2(-(sj.x * gj.x - sj.y * gj.y), -(sj.x * gj.y + sj.y * gj.x));
+    gg[j] = make_double2(cj.x * gj.x + cj.y * gj.y, cj.x * gj.y - cj.y * gj.x);
+    const double bn = bnorm[r] > 0.0 ? bnorm[r] : 1.0;
+    res[r] = sqrt(gg[j + 1].x * gg[j + 1].x + gg[j + 1].y * gg[j + 1].y) / bn;
+    jend[r] = j + 1;
+    if (res[r] <= rtol || den == 0.0) active[r] = 0;
+}
+
+// y = H[0:jend,0:jend]^{-1} g[0:jend] by back substitution (one thread per rhs)
+__global__ void trisolve_kernel(const double2* __restrict__ H, const double2* __restrict__ g,
+                                double2* __restrict__ y, const int* __restrict__ jend, int m, int R) {
+    const int r = threadIdx.x;
+    if (r >= R) return;
+    const int n = jend[r];
+    for (int i = n - 1; i >= 0; --i) {
+        double2 acc = g[(size_t)r * (m + 1) + i];
+        for (int k = i + 1; k < n; ++k) {
+            const double2 hk = H[((size_t)r * m + k) * (m + 1) + i];
+            const double2 yk = y[(size_t)r * (m + 1) + k];
+            acc.x -= hk.x * yk.x - hk.y * yk.y;
+            acc.y -= hk.x * yk.y + hk.y * yk.x;
+        }
+        const double2 d = H[((size_t)r * m + i) * (m + 1) + i];
+        const double dd = d.x * d.x + d.y * d.y;
+        y[(size_t)r * (m + 1) + i] = dd > 0.0 ? make_double2((acc.x * d.x + acc.y * d.y) / dd,
+                                                             (acc.y * d.x - acc.x * d.y) / dd)
+                                              : make_double2(0.0, 0.0);
+    }
+}
+
+// x[r] += sum_{i<jend[r]} y[r][i] V_i[r]
+__global__ void xupdate_kernel(double2* __restrict__ x, const double2* __restrict__ V,
+                               size_t vstride, const double2* __restrict__ y,
+                               const int* __restrict__ jend, int m, size_t n, int R) {
+    const size_t total = (size_t)R * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / n);
+        double2 acc = x[e];
+        for (int i = 0; i < jend[r]; ++i) {
+            const double2 c = y[(size_t)r * (m + 1) + i];
+            const double2 v = V[(size_t)i * vstride + e];
+            acc.x += c.x * v.x - c.y * v.y;
+            acc.y += c.x * v.y + c.y * v.x;
+        }
+        x[e] = acc;
+    }
+}
+
+__global__ void axpy_kernel(double2* __restrict__ x, const double2* __restrict__ d, size_t total) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x)
+        x[e] = make_double2(x[e].x + d[e].x, x[e].y + d[e].y);
+}
+
+int blocks_for(size_t n) {
+    size_t b = (n + 255) / 256;
+    return (int)std::max<size_t>(1, std::min<size_t>(b, 152 * 16));
+}
+
+int gm_alloc(emsurf_handle* h, Gm*& gm, int m, int R) {
+    if (h->gm) {
+        Gm* old = static_cast<Gm*>(h->gm);
+        if (old->m >= m && old->R >= R) {
+            gm = old;
+            return EMSURF_OK;
+        }
+    }
+    // grow: keep the largest shape seen
+    Gm* g = new Gm();
+    const int mm = std::max(m, h->gm ? static_cast<Gm*>(h->gm)->m : 0);
+    const int RR = std::max(R, h->gm ? static_cast<Gm*>(h->gm)->R : 0);
+    g->m = mm;
+    g->R = RR;
+    g->n = (size_t)h->n_unique;
+    const size_t vec = (size_t)RR * g->n * sizeof(double2);
+    EMS_TRY(dev_alloc(h, (void**)&g->V, vec * (mm + 1)));
+    EMS_TRY(dev_alloc(h, (void**)&g->w, vec));
+    EMS_TRY(dev_alloc(h, (void**)&g->r0, vec));
+    EMS_TRY(dev_alloc(h, (void**)&g->d, vec));
+    EMS_TRY(dev_alloc(h, (void**)&g->c, vec));
+    EMS_TRY(dev_alloc(h, (void**)&g->H, sizeof(double2) * RR * mm * (mm + 1)));
+    EMS_TRY(dev_alloc(h, (void**)&g->cs, sizeof(double2) * RR * mm));
+    EMS_TRY(dev_alloc(h, (void**)&g->sn, sizeof(double2) * RR * mm));
+    EMS_TRY(dev_alloc(h, (void**)&g->g, sizeof(double2) * RR * (mm + 1)));
+    EMS_TRY(dev_alloc(h, (void**)&g->hv, sizeof(double2) * RR * (mm + 1)));
+    EMS_TRY(dev_alloc(h, (void**)&g->part, sizeof(double2) * RR * (mm + 1) * kRedBlocks));
+    EMS_TRY(dev_alloc(h, (void**)&g->nrm, sizeof(double) * RR));
+    EMS_TRY(dev_alloc(h, (void**)&g->bnorm, sizeof(double) * RR));
+    EMS_TRY(dev_alloc(h, (void**)&g->res, sizeof(double) * RR));
+    EMS_TRY(dev_alloc(h, (void**)&g->active, sizeof(int) * RR));
+    EMS_TRY(dev_alloc(h, (void**)&g->jend, sizeof(int) * RR));
+    EMS_CUDA(cudaMallocHost(&g->h_res, sizeof(double) * RR));
+    EMS_CUDA(cudaMallocHost(&g->h_act, sizeof(int) * RR));
+    if (h->gm) {
+        Gm* old = static_cast<Gm*>(h->gm);
+        cudaFreeHost(old->h_res);
+        cudaFreeHost(old->h_act);
+        delete old;   // device buffers stay in h->allocations until destroy
+    }
+    h->gm = g;
+    gm = g;
+    return EMSURF_OK;
+}
+
+// nrm[r] = ||v[r]||
+int norms(Gm* g, const double2* v, int R, cudaStream_t st) {
+    dim3 grid(kRedBlocks, 1, R);
+    dot_partial_kernel<<<grid, kRedThreads, 0, st>>>(v, 1, 0, v, g->n, R, g->part, g->m + 1);
+    EMS_CUDA(cudaGetLastError());
+    dot_final_kernel<<<dim3(1, R), 32, 0, st>>>(g->part, kRedBlocks, 1, g->m + 1, g->hv, g->H,
+                                                g->m, 0, g->nrm, 2);
+    EMS_CUDA(cudaGetLastError());
+    return EMSURF_OK;
+}
+
+struct Apply {
+    emsurf_handle* h;
+    int prec;   // operator used inside GMRES
+    int count = 0;
+    int operator()(const double2* x, double2* y, int R, cudaStream_t st) {
+        ++count;
+        if (prec == EMSURF_FP32) return apply_operator<float2>(h, h->op32, x, y, R, st);
+        return apply_operator<double2>(h, h->op64, x, y, R, st);
+    }
+};
+
+// GMRES(m) from x (used as the initial guess), until every rhs reaches rtol
+// or the iteration budget runs out.  Returns the number of Arnoldi steps.
+int gmres_core(emsurf_handle* h, Gm* g, Apply& A, const double2* b, double2* x, int R, int m,
+               double rtol, int max_iters, bool x_is_zero, cudaStream_t st, int* iters_out) {
+    const size_t n = g->n, nv = (size_t)R * n;
+    const size_t vstride = nv;
+    const int nb = blocks_for(nv);
+    int it = 0;
+    // ||b||
+    EMS_TRY(norms(g, b, R, st));
+    EMS_CUDA(cudaMemcpyAsync(g->bnorm, g->nrm, sizeof(double) * R, cudaMemcpyDeviceToDevice, st));
+    bool first = true;
+    while (true) {
+        if (first && x_is_zero) {
+            EMS_CUDA(cudaMemcpyAsync(g->r0, b, nv * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+        } else {
+            EMS_TRY(A(x, g->w, R, st));
+            residual_kernel<<<nb, 256, 0, st>>>(g->r0, b, g->w, nv);
+            EMS_CUDA(cudaGetLastError());
+        }
+        first = false;
+        EMS_TRY(norms(g, g->r0, R, st));
+        cycle_start_kernel<<<1, 64, 0, st>>>(g->nrm, g->bnorm, g->g, g->res, g->active, g->jend,
+                                              m, R, rtol);
+        EMS_CUDA(cudaGetLastError());
+        normalize_kernel<<<nb, 256, 0, st>>>(g->V, g->r0, g->nrm, n, R, nullptr, m, 0);
+        EMS_CUDA(cudaGetLastError());
+        EMS_CUDA(cudaMemcpyAsync(g->h_act, g->active, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+        EMS_CUDA(cudaStreamSynchronize(st));
+        bool any = false;
+        for (int r = 0; r < R; ++r) any = any || g->h_act[r];
+        if (!any || it >= max_iters) break;
+        for (int j = 0; j < m; ++j) {
+            double2* Vj = g->V + (size_t)j * vstride;
+            EMS_TRY(A(Vj, g->w, R, st));
+            // CGS2: two projections onto V_0..V_j
+            for (int pass = 0; pass < 2; ++pass) {
+                dot_partial_kernel<<<dim3(kRedBlocks, j + 1, R), kRedThreads, 0, st>>>(
+                    g->V, j + 1, vstride, g->w, n, R, g->part, m + 1);
+                EMS_CUDA(cudaGetLastError());
+                dot_final_kernel<<<dim3(j + 1, R), 32, 0, st>>>(g->part, kRedBlocks, j + 1, m + 1,
+                                                                g->hv, g->H, m, j, g->nrm, pass);
+                EMS_CUDA(cudaGetLastError());
+                cgs_update_kernel<<<nb, 256, 0, st>>>(g->V, j + 1, vstride, g->hv, m + 1, g->w, n, R);
+                EMS_CUDA(cudaGetLastError());
+            }
+            EMS_TRY(norms(g, g->w, R, st));
+            normalize_kernel<<<nb, 256, 0, st>>>(g->V + (size_t)(j + 1) * vstride, g->w, g->nrm, n,
+                                                 R, g->H, m, j);
+            EMS_CUDA(cudaGetLastError());
+            givens_kernel<<<1, 64, 0, st>>>(g->H, g->cs, g->sn, g->g, g->bnorm, g->res, g->active,
+                                             g->jend, m, j, R, rtol);
+            EMS_CUDA(cudaGetLastError());
+            EMS_CUDA(cudaMemcpyAsync(g->h_act, g->active, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+            EMS_CUDA(cudaStreamSynchronize(st));
+            ++it;
+            bool act = false;
+            for (int r = 0; r < R; ++r) act = act || g->h_act[r];
+            if (!act || it >= max_iters) break;
+        }
+        trisolve_kernel<<<1, 64, 0, st>>>(g->H, g->g, g->hv, g->jend, m, R);
+        EMS_CUDA(cudaGetLastError());
+        xupdate_kernel<<<nb, 256, 0, st>>>(x, g->V, vstride, g->hv, g->jend, m, n, R);
+        EMS_CUDA(cudaGetLastError());
+    }
+    *iters_out = it;
+    return EMSURF_OK;
+}
+
+// true relative residual per rhs with the given operator, into host res[]
+int true_residual(emsurf_handle* h, Gm* g, Apply& A, const double2* b, const double2* x, int R,
+                  cudaStream_t st, double* res) {
+    const size_t nv = (size_t)R * g->n;
+    EMS_TRY(A(x, g->w, R, st));
+    residual_kernel<<<blocks_for(nv), 256, 0, st>>>(g->r0, b, g->w, nv);
+    EMS_CUDA(cudaGetLastError());
+    EMS_TRY(norms(g, g->r0, R, st));
+    std::vector<double> rn(R), bn(R);
+    EMS_CUDA(cudaMemcpyAsync(rn.data(), g->nrm, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+    EMS_TRY(norms(g, b, R, st));
+    EMS_CUDA(cudaMemcpyAsync(bn.data(), g->nrm, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+    EMS_CUDA(cudaStreamSynchronize(st));
+    for (int r = 0; r < R; ++r) res[r] = bn[r] > 0 ? rn[r] / bn[r] : 0.0;
+    return EMSURF_OK;
+}
+
+}  // namespace
+
+int gmres_solve(emsurf_handle* h, const double2* b, double2* x, int R, const emsurf_solve_opts* o,
+                emsurf_solve_info* info, cudaStream_t st) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const int m = o->restart;
+    Gm* g = nullptr;
+    EMS_TRY(gm_alloc(h, g, m, R));
+    const size_t nv = (size_t)R * g->n;
+    EMS_CUDA(cudaMemsetAsync(x, 0, nv * sizeof(double2), st));
+    int iters = 0, refines = 0, nmv = 0;
+    std::vector<double> res(R, 0.0);
+    Apply A64{h, EMSURF_FP64};
+    Apply A32{h, EMSURF_FP32};
+    if (h->precision == EMSURF_MIXED) {
+        const double inner = o->inner_rtol > 0 ? o->inner_rtol : 1e-4;
+        bool zero = true;
+        while (true) {
+            // FP64 residual r = b - A64 x (x = 0 on the first pass)
+            if (zero) {
+                EMS_CUDA(cudaMemcpyAsync(g->d, b, nv * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+                EMS_TRY(norms(g, b, R, st));
+                std::vector<double> bn(R);
+                EMS_CUDA(cudaMemcpyAsync(bn.data(), g->nrm, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+                EMS_CUDA(cudaStreamSynchronize(st));
+                for (int r = 0; r < R; ++r) res[r] = bn[r] > 0 ? 1.0 : 0.0;
+            } else {
+                EMS_TRY(true_residual(h, g, A64, b, x, R, st, res.data()));
+                EMS_CUDA(cudaMemcpyAsync(g->d, g->r0, nv * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+            }
+            double worst = 0.0;
+            for (int r = 0; r < R; ++r) worst = std::max(worst, res[r]);
+            if (worst <= o->rtol || refines >= o->max_refine || iters >= o->max_iters) break;
+            // inner solve A32 c = d with FP32-operator GMRES
+            double2* c = g->c;
+            EMS_CUDA(cudaMemsetAsync(c, 0, nv * sizeof(double2), st));
+            const double tol = std::max(inner, 0.5 * o->rtol / std::max(worst, 1e-300));
+            int it = 0;
+            EMS_TRY(gmres_core(h, g, A32, g->d, c, R, m, std::min(tol, 0.5), o->max_iters - iters,
+                               true, st, &it));
+            iters += it;
+            axpy_kernel<<<blocks_for(nv), 256, 0, st>>>(x, c, nv);
+            EMS_CUDA(cudaGetLastError());
+            ++refines;
+            zero = false;
+        }
+        nmv = A64.count + A32.count;
+    } else {
+        Apply& A = (h->precision == EMSURF_FP32) ? A32 : A64;
+        EMS_TRY(gmres_core(h, g, A, b, x, R, m, o->rtol, o->max_iters, true, st, &iters));
+        EMS_TRY(true_residual(h, g, A, b, x, R, st, res.data()));
+        nmv = A.count;
+    }
+    EMS_CUDA(cudaStreamSynchronize(st));
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    bool all = true;
+    for (int r = 0; r < R; ++r) {
+        const bool ok = res[r] <= o->rtol;
+        all = all && ok;
+        if (info) {
+            info[r].iters = iters;
+            info[r].refinements = refines;
+            info[r].n_matvec = nmv;
+            info[r].converged = ok ? 1 : 0;
+            info[r].rel_residual = res[r];
+            info[r].ms_total = ms;
+        }
+    }
+    return all ? EMSURF_OK : EMSURF_ENOTCONV;
+}
+
+}  // namespace emsurf
+
+namespace emsurf {
+
+void gmres_release(emsurf_handle* h) {
+    if (!h->gm) return;
+    Gm* g = static_cast<Gm*>(h->gm);
+    if (g->h_res) cudaFreeHost(g->h_res);
+    if (g->h_act) cudaFreeHost(g->h_act);
+    delete g;   // device buffers are released with the handle's allocations
+    h->gm = nullptr;
+}
+
+}  // namespace emsurf

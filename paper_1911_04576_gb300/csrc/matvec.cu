@@ -1,0 +1,396 @@
+// The FFT-accelerated product y = U_o^T [Z_eq + Z_o] U_o x (Eq. MVP).
+//
+// Layouts in HBM (P = px*py bins, E RWGs, K = 2E, R right-hand sides):
+//   Bhat [P][2][E][E]  Fourier-domain L^, K^ blocks, source-major (j, i):
+//                      the bin multiply gives each thread one test row i and
+//                      streams a column j across the warp (coalesced);
+//   Zt   [T][K][K]     macromodels transposed (k' outer, k contiguous);
+//   Xg,Yg [P][R][K]    padded grids, lanes (r, k) contiguous;
+//   Ymm  [R][M][K]     macromodel products.
+//
+// Storing only L^ and K^ (not the full K x K block) is the paper's storage
+// count 2^{d+1} N_eq^2 M complex numbers (Sec. IV-C): B(d) repeats L and K
+// in its four quarters (Eq. blockZo with the coefficients of the scaled
+// EFIE/MFIE form).
+#include <algorithm>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace emsurf {
+
+namespace {
+
+// ------------------------------------------------ placement of the tables
+// Bhat[bin(d)][op][j][i] = table_op(d)[i][j] for one chunk of offsets;
+// stage holds [nchunk][2][E][E] complex128 (row-major i, j).
+template <typename T2>
+__global__ void place_blocks_kernel(T2* __restrict__ Bhat, const double2* __restrict__ stage,
+                                    const int* __restrict__ bins, int nchunk, int E) {
+    __shared__ double2 tile[32][33];
+    const int o = blockIdx.z / 2, op = blockIdx.z % 2;
+    const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+    const double2* src = stage + ((size_t)o * 2 + op) * E * E;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int i = i0 + r, j = j0 + threadIdx.x;
+        tile[r][threadIdx.x] = (i < E && j < E) ? src[(size_t)i * E + j] : make_double2(0, 0);
+    }
+    __syncthreads();
+    T2* dst = Bhat + ((size_t)bins[o] * 2 + op) * E * E;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int j = j0 + r, i = i0 + threadIdx.x;
+        if (i < E && j < E) {
+            const double2 v = tile[threadIdx.x][r];
+            dst[(size_t)j * E + i] = mk<T2>(v.x, v.y);
+        }
+    }
+}
+
+// Zt[t][k'][k] = Z[t][k][k']
+template <typename T2>
+__global__ void transpose_mm_kernel(T2* __restrict__ Zt, const double2* __restrict__ Z, int K) {
+    __shared__ double2 tile[32][33];
+    const int t = blockIdx.z;
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    const double2* src = Z + (size_t)t * K * K;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int i = r0 + r, j = c0 + threadIdx.x;
+        tile[r][threadIdx.x] = (i < K && j < K) ? src[(size_t)i * K + j] : make_double2(0, 0);
+    }
+    __syncthreads();
+    T2* dst = Zt + (size_t)t * K * K;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int j = c0 + r, i = r0 + threadIdx.x;
+        if (i < K && j < K) {
+            const double2 v = tile[threadIdx.x][r];
+            dst[(size_t)j * K + i] = mk<T2>(v.x, v.y);
+        }
+    }
+}
+
+__global__ void round_kernel(float2* __restrict__ dst, const double2* __restrict__ src, size_t n) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const double2 v = src[e];
+        dst[e] = make_float2((float)v.x, (float)v.y);
+    }
+}
+
+// ------------------------------------------------ K1: gather + zero-pad
+// Xg[bin][r][k] = sign * x[r][uo_index[m*K+k]] for the bin (ix, iy) of cell
+// m = iy*nx + ix, zero on the padding bins.
+template <typename T2>
+__global__ void gather_pad_kernel(T2* __restrict__ Xg, const double2* __restrict__ x,
+                                  const int32_t* __restrict__ idx, const int8_t* __restrict__ sgn,
+                                  int nx, int ny, int px, int rows, int R, int K, int n_unique) {
+    const size_t total = (size_t)rows * px * R * K;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(e % K);
+        const size_t t = e / K;
+        const int r = (int)(t % R);
+        const size_t bin = t / R;
+        const int ix = (int)(bin % px), iy = (int)(bin / px);
+        T2 v = mk<T2>(0.0, 0.0);
+        if (ix < nx && iy < ny) {
+            const size_t loc = ((size_t)iy * nx + ix) * K + k;
+            const double2 xv = x[(size_t)r * n_unique + idx[loc]];
+            const double s = (double)sgn[loc];
+            v = mk<T2>(s * xv.x, s * xv.y);
+        }
+        Xg[e] = v;
+    }
+}
+
+// ------------------------------------------------ K2: bin multiply
+// Y^(k) = B^(k) X^(k) with B = [[a L, b K], [g K, d L]]:
+//   y_J = a L^ x_J + b K^ x_M,   y_M = g K^ x_J + d L^ x_M.
+// One CTA per bin (grid-stride), one thread per test row i.
+template <typename T2, int RB>
+__global__ void binmul_kernel(const T2* __restrict__ Bhat, const T2* __restrict__ Xh,
+                              T2* __restrict__ Yh, int E, int nbins, int R, int r0,
+                              T2 ca, T2 cb, T2 cg, T2 cd) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2* xs = reinterpret_cast<T2*>(smem_raw);   // [RB][2E]
+    const int K = 2 * E;
+    const T2 zero = mk<T2>(0.0, 0.0);
+    for (int bin = blockIdx.x; bin < nbins; bin += gridDim.x) {
+        __syncthreads();
+        const T2* X = Xh + (size_t)bin * R * K;
+        for (int e = threadIdx.x; e < RB * K; e += blockDim.x) {
+            const int r = e / K, k = e - (e / K) * K;
+            xs[e] = (r0 + r < R) ? X[(size_t)(r0 + r) * K + k] : zero;
+        }
+        __syncthreads();
+        const T2* Lt = Bhat + (size_t)bin * 2 * E * E;
+        const T2* Kt = Lt + (size_t)E * E;
+        for (int i = threadIdx.x; i < E; i += blockDim.x) {
+            T2 lj[RB], lm[RB], kj[RB], km[RB];
+#pragma unroll
+            for (int r = 0; r < RB; ++r) lj[r] = lm[r] = kj[r] = km[r] = zero;
+#pragma unroll 8
+            for (int j = 0; j < E; ++j) {
+                const T2 l = __ldg(Lt + (size_t)j * E + i);
+                const T2 kk = __ldg(Kt + (size_t)j * E + i);
+#pragma unroll
+                for (int r = 0; r < RB; ++r) {
+                    const T2 xj = xs[r * K + j];
+                    const T2 xm = xs[r * K + E + j];
+                    cfma(lj[r], l, xj);
+                    cfma(lm[r], l, xm);
+                    cfma(kj[r], kk, xj);
+                    cfma(km[r], kk, xm);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < RB; ++r) {
+                if (r0 + r < R) {
+                    T2* Y = Yh + ((size_t)bin * R + r0 + r) * K;
+                    Y[i] = cadd(cmul(ca, lj[r]), cmul(cb, km[r]));
+                    Y[E + i] = cadd(cmul(cg, kj[r]), cmul(cd, lm[r]));
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------ K4: macromodel multiply
+// Ymm[r][m][k] = sum_k' Z~^{t(m)}[k][k'] x1[r][m][k'] for a group of up to
+// G cells of one type (x1 = U_o x gathered on the fly).
+struct MmBlock {
+    int type, first, count;
+};
+
+template <typename T2, int G>
+__global__ void macromodel_kernel(const T2* __restrict__ Zt, const double2* __restrict__ x,
+                                  const int32_t* __restrict__ idx, const int8_t* __restrict__ sgn,
+                                  const int32_t* __restrict__ type_cells,
+                                  const MmBlock* __restrict__ blocks, T2* __restrict__ Ymm, int K,
+                                  int M, int R, int n_unique) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2* xs = reinterpret_cast<T2*>(smem_raw);   // [G][K] for one r
+    const MmBlock b = blocks[blockIdx.x];
+    const T2 zero = mk<T2>(0.0, 0.0);
+    const T2* Z = Zt + (size_t)b.type * K * K;
+    for (int r = 0; r < R; ++r) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < G * K; e += blockDim.x) {
+            const int g = e / K, k = e - (e / K) * K;
+            T2 v = zero;
+            if (g < b.count) {
+                const size_t loc = (size_t)type_cells[b.first + g] * K + k;
+                const double2 xv = x[(size_t)r * n_unique + idx[loc]];
+                const double s = (double)sgn[loc];
+                v = mk<T2>(s * xv.x, s * xv.y);
+            }
+            xs[e] = v;
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+            T2 acc[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g) acc[g] = zero;
+#pragma unroll 8
+            for (int kp = 0; kp < K; ++kp) {
+                const T2 z = __ldg(Z + (size_t)kp * K + k);
+#pragma unroll
+                for (int g = 0; g < G; ++g) cfma(acc[g], z, xs[g * K + kp]);
+            }
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+                if (g < b.count)
+                    Ymm[((size_t)r * M + type_cells[b.first + g]) * K + k] = acc[g];
+        }
+    }
+}
+
+// ------------------------------------------------ K3 tail: crop + U_o^T
+// y[r][u] = sum over local unknowns (m,k) of u: sign * (Yg[bin(m)][r][k] / P
+//           + Ymm[r][m][k])
+template <typename T2>
+__global__ void crop_scatter_kernel(double2* __restrict__ y, const T2* __restrict__ Yg,
+                                    const T2* __restrict__ Ymm, const int32_t* __restrict__ ptr,
+                                    const int32_t* __restrict__ ent, const int8_t* __restrict__ esg,
+                                    int nx, int px, int K, int M, int R, int n_unique,
+                                    double scale) {
+    const size_t total = (size_t)R * n_unique;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int u = (int)(e % n_unique);
+        const int r = (int)(e / n_unique);
+        double ax = 0.0, ay = 0.0;
+        for (int q = ptr[u]; q < ptr[u + 1]; ++q) {
+            const int loc = ent[q];
+            const int m = loc / K, k = loc - (loc / K) * K;
+            const int ix = m % nx, iy = m / nx;
+            const T2 g = Yg[(((size_t)iy * px + ix) * R + r) * K + k];
+            const T2 z = Ymm[((size_t)r * M + m) * K + k];
+            const double s = (double)esg[q];
+            ax += s * ((double)g.x * scale + (double)z.x);
+            ay += s * ((double)g.y * scale + (double)z.y);
+        }
+        y[e] = make_double2(ax, ay);
+    }
+}
+
+int grid_for(size_t n, int threads) {
+    size_t b = (n + threads - 1) / threads;
+    if (b > 152 * 32) b = 152 * 32;
+    return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- build
+// Places L(d), K(d) at grid point (dx mod px, dy mod py) -- the circulant's
+// first column (Eq. LJV3 read by columns, d = test - source) -- and
+// transforms the grid with the forward 2-D FFT: B^(k) = F[B](k).
+template <typename T2>
+int build_operator(emsurf_handle* h, Operator<T2>& op, const emsurf_problem* pr) {
+    const int E = h->E, K = h->K;
+    const size_t EE = (size_t)E * E;
+    const int nox = 2 * h->nx - 1, noy = 2 * h->ny - 1;
+    const size_t nbins = (size_t)h->nbins;
+    // FP64 spectrum first (also the source of the FP32 copy)
+    double2* B64 = nullptr;
+    const size_t bbytes64 = nbins * 2 * EE * sizeof(double2);
+    const bool direct64 = sizeof(T2) == sizeof(double2);
+    if (direct64) {
+        EMS_TRY(dev_alloc(h, (void**)&B64, bbytes64));
+    } else {
+        EMS_CUDA(cudaMalloc(&B64, bbytes64));
+    }
+    cudaStream_t st = 0;
+    EMS_CUDA(cudaMemsetAsync(B64, 0, bbytes64, st));
+    // stage offsets in chunks of <= 256 MB
+    const size_t per_off = 2 * EE * sizeof(double2);
+    int chunk = (int)std::max<size_t>(1, (256ull << 20) / per_off);
+    chunk = std::min(chunk, nox * noy);
+    double2* stage = nullptr;
+    int* dbins = nullptr;
+    EMS_CUDA(cudaMalloc(&stage, per_off * chunk));
+    EMS_CUDA(cudaMalloc(&dbins, sizeof(int) * chunk));
+    std::vector<int> hb(chunk);
+    const cudaMemcpyKind kind = pr->tables_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    for (int o0 = 0; o0 < nox * noy; o0 += chunk) {
+        const int nc = std::min(chunk, nox * noy - o0);
+        for (int c = 0; c < nc; ++c) {
+            const int o = o0 + c;
+            const int dyi = o / nox, dxi = o % nox;
+            const int dx = dxi - (h->nx - 1), dy = dyi - (h->ny - 1);
+            const int bx = ((dx % h->px) + h->px) % h->px;
+            const int by = ((dy % h->py) + h->py) % h->py;
+            hb[c] = by * h->px + bx;
+            EMS_CUDA(cudaMemcpyAsync(stage + (size_t)c * 2 * EE, pr->offset_L + (size_t)o * EE,
+                                     EE * sizeof(double2), kind, st));
+            EMS_CUDA(cudaMemcpyAsync(stage + (size_t)c * 2 * EE + EE, pr->offset_K + (size_t)o * EE,
+                                     EE * sizeof(double2), kind, st));
+        }
+        EMS_CUDA(cudaMemcpyAsync(dbins, hb.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, st));
+        dim3 grid((E + 31) / 32, (E + 31) / 32, 2 * nc);
+        place_blocks_kernel<double2><<<grid, dim3(32, 8), 0, st>>>(B64, stage, dbins, nc, E);
+        EMS_CUDA(cudaGetLastError());
+        EMS_CUDA(cudaStreamSynchronize(st));
+    }
+    cudaFree(stage);
+    cudaFree(dbins);
+    // 2-D forward FFT over bins: lanes = 2 E^2 block entries
+    const long long lanes = 2LL * (long long)EE;
+    EMS_TRY(fft_pass<double2>(B64, h->plan_x, lanes, h->py, (long long)h->px * lanes, -1, st));
+    EMS_TRY(fft_pass<double2>(B64, h->plan_y, (long long)h->px * lanes, 1, 0, -1, st));
+    if (direct64) {
+        op.Bhat = reinterpret_cast<T2*>(B64);
+    } else {
+        EMS_TRY(dev_alloc(h, (void**)&op.Bhat, nbins * 2 * EE * sizeof(T2)));
+        round_kernel<<<152 * 8, 256, 0, st>>>(reinterpret_cast<float2*>(op.Bhat), B64,
+                                             nbins * 2 * EE);
+        EMS_CUDA(cudaGetLastError());
+        EMS_CUDA(cudaStreamSynchronize(st));
+        cudaFree(B64);
+    }
+    // macromodels
+    const size_t zbytes = (size_t)h->T * K * K * sizeof(double2);
+    double2* zstage = nullptr;
+    if (pr->tables_on_device) {
+        zstage = const_cast<double2*>(reinterpret_cast<const double2*>(pr->macromodels));
+    } else {
+        EMS_CUDA(cudaMalloc(&zstage, zbytes));
+        EMS_CUDA(cudaMemcpy(zstage, pr->macromodels, zbytes, cudaMemcpyHostToDevice));
+    }
+    EMS_TRY(dev_alloc(h, (void**)&op.Zt, (size_t)h->T * K * K * sizeof(T2)));
+    dim3 zg((K + 31) / 32, (K + 31) / 32, h->T);
+    transpose_mm_kernel<T2><<<zg, dim3(32, 8), 0, st>>>(op.Zt, zstage, K);
+    EMS_CUDA(cudaGetLastError());
+    EMS_CUDA(cudaStreamSynchronize(st));
+    if (!pr->tables_on_device) cudaFree(zstage);
+    // work buffers
+    const size_t grid_elems = nbins * (size_t)h->max_rhs * K;
+    EMS_TRY(dev_alloc(h, (void**)&op.Xg, grid_elems * sizeof(T2)));
+    EMS_TRY(dev_alloc(h, (void**)&op.Yg, grid_elems * sizeof(T2)));
+    EMS_TRY(dev_alloc(h, (void**)&op.Ymm, (size_t)h->max_rhs * h->M * K * sizeof(T2)));
+    for (int c = 0; c < 4; ++c) op.coef[c] = mk<T2>(pr->coef[c].re, pr->coef[c].im);
+    return EMSURF_OK;
+}
+
+// ---------------------------------------------------------------- apply
+template <typename T2>
+int apply_operator(emsurf_handle* h, Operator<T2>& op, const double2* x, double2* y, int R,
+                   cudaStream_t st) {
+    const int E = h->E, K = h->K, px = h->px, py = h->py;
+    const long long lanes = (long long)R * K;
+    // K1: gather rows iy < ny (rows beyond are zero and stay zero under the x-pass)
+    gather_pad_kernel<T2><<<grid_for((size_t)py * px * lanes, 256), 256, 0, st>>>(
+        op.Xg, x, h->d_uo_index, h->d_uo_sign, h->nx, h->ny, px, py, R, K, h->n_unique);
+    EMS_CUDA(cudaGetLastError());
+    EMS_TRY(fft_pass<T2>(op.Xg, h->plan_x, lanes, h->ny, (long long)px * lanes, -1, st));
+    EMS_TRY(fft_pass<T2>(op.Xg, h->plan_y, (long long)px * lanes, 1, 0, -1, st));
+    // K2
+    const int threads = std::min(1024, ((E + 31) / 32) * 32);
+    const int nb = h->nbins;
+    int rb = 1;
+    if (R >= 4) rb = 4;
+    else if (R >= 2) rb = 2;
+    for (int r0 = 0; r0 < R; r0 += rb) {
+        const size_t smem = (size_t)rb * K * sizeof(T2);
+        const int grid = std::min(nb, 152 * 8);
+        if (rb == 4) {
+            binmul_kernel<T2, 4><<<grid, threads, smem, st>>>(op.Bhat, op.Xg, op.Yg, E, nb, R, r0,
+                                                              op.coef[0], op.coef[1], op.coef[2], op.coef[3]);
+        } else if (rb == 2) {
+            binmul_kernel<T2, 2><<<grid, threads, smem, st>>>(op.Bhat, op.Xg, op.Yg, E, nb, R, r0,
+                                                              op.coef[0], op.coef[1], op.coef[2], op.coef[3]);
+        } else {
+            binmul_kernel<T2, 1><<<grid, threads, smem, st>>>(op.Bhat, op.Xg, op.Yg, E, nb, R, r0,
+                                                              op.coef[0], op.coef[1], op.coef[2], op.coef[3]);
+        }
+        EMS_CUDA(cudaGetLastError());
+    }
+    // K3: inverse y-pass on all columns, inverse x-pass on the rows kept
+    EMS_TRY(fft_pass<T2>(op.Yg, h->plan_y, (long long)px * lanes, 1, 0, +1, st));
+    EMS_TRY(fft_pass<T2>(op.Yg, h->plan_x, lanes, h->ny, (long long)px * lanes, +1, st));
+    // K4
+    {
+        constexpr int G = 4;
+        const int nblk = h->n_mm_blocks;
+        const MmBlock* blocks = reinterpret_cast<const MmBlock*>(h->d_mm_blocks);
+        const int mthreads = std::min(1024, ((K + 31) / 32) * 32);
+        macromodel_kernel<T2, G><<<nblk, mthreads, (size_t)G * K * sizeof(T2), st>>>(
+            op.Zt, x, h->d_uo_index, h->d_uo_sign, h->d_type_cells, blocks, op.Ymm, K, h->M, R,
+            h->n_unique);
+        EMS_CUDA(cudaGetLastError());
+    }
+    crop_scatter_kernel<T2><<<grid_for((size_t)R * h->n_unique, 256), 256, 0, st>>>(
+        y, op.Yg, op.Ymm, h->d_inv_ptr, h->d_inv_ent, h->d_inv_sgn, h->nx, px, K, h->M, R,
+        h->n_unique, 1.0 / (double)h->nbins);
+    EMS_CUDA(cudaGetLastError());
+    return EMSURF_OK;
+}
+
+template int build_operator<double2>(emsurf_handle*, Operator<double2>&, const emsurf_problem*);
+template int build_operator<float2>(emsurf_handle*, Operator<float2>&, const emsurf_problem*);
+template int apply_operator<double2>(emsurf_handle*, Operator<double2>&, const double2*, double2*,
+                                     int, cudaStream_t);
+template int apply_operator<float2>(emsurf_handle*, Operator<float2>&, const double2*, double2*,
+                                    int, cudaStream_t);
+
+}  // namespace emsurf

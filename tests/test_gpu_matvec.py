@@ -1,0 +1,126 @@
+"""GPU parity of the FFT matvec (Eq. MVP via Sec. IV-B) against the oracle's
+direct offset sum, through the C ABI.
+
+Tolerances: FP64 path rel-L2 <= 1e-10 per product (the accuracy target of
+the FP64 plain path).  FP32 path: complex64 storage and FP32 arithmetic give
+per-product errors ~ sqrt(number of terms) * 2^-24 * (condition of the
+sums); 3e-5 rel-L2 bounds it on these inputs (derivation in the design doc).
+"""
+import numpy as np
+import pytest
+
+from oracle import lattice
+from oracle.mesh import box_mesh
+from paper_1911_04576_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+A = W.PERIOD
+H = W.BOX_H
+COEF = (1j * W.K0, 1.0, -1.0, 1j * W.K0)
+TOL64 = 1e-10
+TOL32 = 3e-5
+
+
+def relerr(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def random_case(n, nx, ny, T, seed):
+    box = box_mesh(A, A, H, n)
+    idx, sgn, nu = lattice.overlap_map(box, nx, ny, A, A)
+    E = box.n_rwg
+    Lt, Kt = W.random_tables(nx, ny, E, seed)
+    Z = W.random_macromodels(T, 2 * E, seed + 1)
+    tmap = np.random.default_rng(seed + 2).integers(0, T, nx * ny).astype(np.int32)
+    return E, idx, sgn, nu, Lt, Kt, Z, tmap
+
+
+def run_matvec(B, h, x, prec):
+    import torch
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    yd = torch.empty_like(xd)
+    B.emsurf_matvec(h, xd, yd, prec)
+    torch.cuda.synchronize()
+    return yd.cpu().numpy()
+
+
+@pytest.mark.parametrize("n,nx,ny,R", [(1, 1, 1, 1), (2, 2, 2, 1), (2, 3, 5, 2), (2, 4, 4, 3),
+                                       (3, 3, 3, 1), (2, 5, 1, 4), (1, 7, 6, 5)])
+def test_matvec_parity_random_tables(emsurf_lib, n, nx, ny, R):
+    from paper_1911_04576_gb300 import binding as B
+    seed = 100 * n + 10 * nx + ny
+    E, idx, sgn, nu, Lt, Kt, Z, tmap = random_case(n, nx, ny, 3, seed)
+    h = B.emsurf_create(nx, ny, E, nu, tmap, Z, Lt, Kt, COEF, idx, sgn, precision=B.MIXED,
+                        max_rhs=max(R, 2))
+    x = W.random_vectors(R, nu, seed + 3)
+    yref = lattice.matvec_direct(x, Lt, Kt, COEF, Z, tmap, idx, sgn, nu, nx, ny)
+    y64 = run_matvec(B, h, x, B.FP64)
+    y32 = run_matvec(B, h, x, B.FP32)
+    for r in range(R):
+        assert relerr(y64[r], yref[r]) <= TOL64
+        assert relerr(y32[r], yref[r]) <= TOL32
+    h.close()
+
+
+def test_grid_size_does_not_change_result(emsurf_lib):
+    """Any grid >= 2N-1 embeds the Toeplitz blocks exactly: 2N-1 (the paper's
+    5x5 circulant for N = 3), the 2,3,5-smooth default and 2N agree."""
+    from paper_1911_04576_gb300 import binding as B
+    n, nx, ny = 2, 3, 4
+    E, idx, sgn, nu, Lt, Kt, Z, tmap = random_case(n, nx, ny, 2, 77)
+    x = W.random_vectors(1, nu, 78)
+    ys = []
+    for grid in [(0, 0), (2 * nx - 1, 2 * ny - 1), (2 * nx, 2 * ny), (10, 9)]:
+        h = B.emsurf_create(nx, ny, E, nu, tmap, Z, Lt, Kt, COEF, idx, sgn, grid=grid)
+        assert B.emsurf_query(h)[:2] == ((5, 8) if grid == (0, 0) else grid)
+        ys.append(run_matvec(B, h, x, B.FP64))
+        h.close()
+    for y in ys[1:]:
+        assert relerr(y, ys[0]) <= 1e-13
+
+
+def test_matvec_full_size_sampled(emsurf_lib):
+    """16x16 lattice, K = 576, 32 types, one rhs: the bench's launch
+    configuration; 32 sampled outputs recomputed one by one by the oracle."""
+    from paper_1911_04576_gb300 import binding as B
+    w = W.WORKLOADS["lattice16x16_k576"]
+    box = box_mesh(A, A, H, w.n)
+    idx, sgn, nu = lattice.overlap_map(box, w.nx, w.ny, A, A)
+    Lt, Kt = W.random_tables(w.nx, w.ny, w.E, 1600)
+    Z = W.random_macromodels(w.n_types, w.K, 1601)
+    tmap = W.type_map(w)
+    h = B.emsurf_create(w.nx, w.ny, w.E, nu, tmap, Z, Lt, Kt, COEF, idx, sgn, precision=B.MIXED)
+    x = W.random_vectors(1, nu, 1602)
+    rows = np.sort(np.random.default_rng(1603).choice(nu, 32, replace=False))
+    rows[0], rows[-1] = 0, nu - 1
+    yref = lattice.matvec_direct_rows(x[0], rows, Lt, Kt, COEF, Z, tmap, idx, sgn, w.nx, w.ny)
+    y64 = run_matvec(B, h, x, B.FP64)[0]
+    y32 = run_matvec(B, h, x, B.FP32)[0]
+    assert relerr(y64[rows], yref) <= TOL64
+    assert relerr(y32[rows], yref) <= TOL32
+    # repeated calls are bit-identical (no atomics, fixed reduction order)
+    assert np.array_equal(run_matvec(B, h, x, B.FP64)[0], y64)
+    h.close()
+
+
+def test_invalid_calls_rejected(emsurf_lib):
+    import torch
+    from paper_1911_04576_gb300 import binding as B
+    E, idx, sgn, nu, Lt, Kt, Z, tmap = random_case(1, 2, 2, 1, 5)
+    h = B.emsurf_create(2, 2, E, nu, tmap, Z, Lt, Kt, COEF, idx, sgn, precision=B.FP64, max_rhs=2)
+    x = torch.zeros(3, nu, dtype=torch.complex128, device="cuda")
+    y = torch.zeros_like(x)
+    with pytest.raises(B.EmsurfError) as e:
+        B.emsurf_matvec(h, x, y, B.FP64)           # nrhs 3 > max_rhs 2
+    assert e.value.status == B.EMSURF_EINVAL
+    with pytest.raises(B.EmsurfError) as e:
+        B.emsurf_matvec(h, x[:1], y[:1], B.FP32)   # FP32 operator not resident
+    assert e.value.status == B.EMSURF_EINVAL
+    with pytest.raises(B.EmsurfError) as e:
+        B.emsurf_matvec(h, x[:1], x[:1], B.FP64)   # in place
+    assert e.value.status == B.EMSURF_EINVAL
+    with pytest.raises(B.EmsurfError) as e:
+        B.emsurf_create(2, 2, E, nu, tmap, Z, Lt, Kt, COEF, idx, sgn, device_mem_budget=1024)
+    assert e.value.status == B.EMSURF_ENOMEM
+    h.close()

@@ -94,3 +94,22 @@ def test_direct_product_equals_box_pair_assembly():
     x = rng.standard_normal((2, nu)) + 1j * rng.standard_normal((2, nu))
     y = lattice.matvec_direct(x, Lt, Kt, COEF, Zt, tmap, idx, sgn, nu, nx, ny)
     assert np.abs(y - x @ Ad.T).max() <= 1e-13 * np.abs(y).max()
+
+
+def test_sampled_rows_equal_full_direct_product():
+    n, nx, ny = 2, 3, 2
+    box = box_mesh(A, B, H, n)
+    idx, sgn, nu = lattice.overlap_map(box, nx, ny, A, B)
+    rng = np.random.default_rng(5)
+    E = box.n_rwg
+    Lt = rng.standard_normal((2 * ny - 1, 2 * nx - 1, E, E)) + 1j * rng.standard_normal((2 * ny - 1, 2 * nx - 1, E, E))
+    Kt = rng.standard_normal(Lt.shape) + 1j * rng.standard_normal(Lt.shape)
+    Zt = rng.standard_normal((3, 2 * E, 2 * E)) + 0j
+    tmap = np.array([0, 1, 2, 2, 1, 0])
+    x = rng.standard_normal(nu) + 1j * rng.standard_normal(nu)
+    y = lattice.matvec_direct(x, Lt, Kt, COEF, Zt, tmap, idx, sgn, nu, nx, ny)
+    rows = [0, 7, nu // 2, nu - 1]
+    yr = lattice.matvec_direct_rows(x, rows, Lt, Kt, COEF, Zt, tmap, idx, sgn, nx, ny)
+    assert np.abs(yr - y[rows]).max() <= 1e-12 * np.abs(y).max()
+    Ad = lattice.assemble_from_tables(Lt, Kt, COEF, Zt, tmap, idx, sgn, nu, nx, ny)
+    assert np.abs(Ad @ x - y).max() <= 1e-12 * np.abs(y).max()
