@@ -88,7 +88,9 @@ def galerkin_LK(test, test_shift, src, src_shift, k, singular, chunk=8):
     test/src: Mesh; *_shift: translation (3,) of each mesh; k: wavenumber of
     the homogeneous region; singular: if True the 1/R and grad(1/R) parts are
     integrated in closed form over every source triangle (used for touching
-    boxes and inside a cell), else plain 7x7-point quadrature.
+    boxes and inside a cell), else plain 7x7-point quadrature.  In the
+    singular case point pairs closer than 1e-9 of the source triangle size
+    count as coincident (remainder at its R -> 0 limit, no gradient term).
     """
     _, w = radon7()
     tt = test.tri_coords(test_shift)
@@ -108,11 +110,16 @@ def galerkin_LK(test, test_shift, src, src_shift, k, singular, chunk=8):
         v0 = ts[:, 0, :]
         nrm = np.cross(ts[:, 1, :] - v0, ts[:, 2, :] - v0)
         ns = nrm / np.linalg.norm(nrm, axis=-1, keepdims=True)
+        sscale = np.maximum(np.linalg.norm(ts[:, 1] - v0, axis=-1),
+                            np.linalg.norm(ts[:, 2] - v0, axis=-1))
     for t0 in range(0, Tt, chunk):
         sl = slice(t0, min(Tt, t0 + chunk))
         diff = rq[sl, None, :, None, :] - rs[None, :, None, :, :]   # (c,Ts,7,7,3)
         R = np.linalg.norm(diff, axis=-1)
         if singular:
+            # coincident points (up to rounding) take the R -> 0 limit: G_s = -jk/(4 pi)
+            # and no gradient term (its direction is undefined there)
+            R = np.where(R <= 1e-9 * sscale[None, :, None, None], 0.0, R)
             G, gfac = _green_smooth(R, k)
         else:
             G, gfac = _green_far(R, k)
@@ -129,9 +136,7 @@ def galerkin_LK(test, test_shift, src, src_shift, k, singular, chunk=8):
             r = rq[sl][:, :, None, :]                                  # (c,7,1,3)
             I0, I1, Ig = potential_integrals(r, ts[None, None, :, :, :])  # (c,7,Ts)
             d = np.sum(ns[None, None] * (r - v0[None, None]), axis=-1)
-            scale = np.maximum(np.linalg.norm(ts[:, 1] - v0, axis=-1),
-                               np.linalg.norm(ts[:, 2] - v0, axis=-1))
-            d = np.where(np.abs(d) <= 1e-9 * scale[None, None], 0.0, d)
+            d = np.where(np.abs(d) <= 1e-9 * sscale[None, None], 0.0, d)
             rho = r - d[..., None] * ns[None, None]                   # (c,7,Ts,3)
             # int (r'-p_j)/R = I1 + (rho - p_j) I0
             vecL = I1[:, :, :, None, :] + (rho[:, :, :, None, :] - ts[None, None, :, :, :]) \
