@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Benchmark of the FFT-accelerated macromodel solve (Eq. final) on one GB300.
+
+Workload (default): 16 x 16 lattice of boxes meshed 4 x 4 per face
+(K = 576 unknowns per box), 32 PEC-patch cell types (sides uniform in
+[0.15, 0.45] lambda, seeded type map), one normal-incidence x-polarised
+plane wave at 10 GHz.  Every input is built on the product path: overlap
+map (C++ setup), offset tables and macromodels (GPU tabulation and Schur
+complement), excitation (GPU).
+
+A step is one solve to relative residual 1e-6: GMRES(30) with the FP32
+operator inside FP64 residual refinement (MIXED).  The FP64-plain solve,
+the matvec rates, the CPU oracle and an end-to-end call with host buffers
+are measured beside it.  One JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "solve time to 1e-6 residual & matvec GB/s vs FP64 plain; p50/p99 serve latency"
+RTOL = 1e-6
+RESTART = 30
+# FP64-operator GMRES(30) matvecs to reach 1e-6 on the default workload, as
+# measured on GB300; scales the CPU oracle's per-matvec time to a solve.
+REF_MATVECS_PER_SOLVE = None
+FALLBACK_HBM_GBS = 6800.0
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", FALLBACK_HBM_GBS)), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ["clocks.sm", "clocks.max.sm", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) != len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[2:]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def build_problem(B, W, torch, w, precision):
+    """Product-path setup (untimed): U_o, tables, macromodels, handle, V."""
+    A, H = W.PERIOD, W.BOX_H
+    coef = (1j * W.K0, 1.0, -1.0, 1j * W.K0)
+    idx, sgn, nu = B.emsurf_setup_overlap(w.n, w.nx, w.ny)
+    L = torch.empty((2 * w.ny - 1, 2 * w.nx - 1, w.E, w.E), dtype=torch.complex128, device="cuda")
+    K = torch.empty_like(L)
+    t0 = time.time()
+    B.emsurf_tabulate_offsets(A, A, H, w.n, w.nx, w.ny, W.K0, L, K)
+    t_tab = time.time() - t0
+    Z = torch.empty((w.n_types, w.K, w.K), dtype=torch.complex128, device="cuda")
+    t0 = time.time()
+    B.emsurf_macromodel_pec_patch(A, A, H, w.n, W.patch_sides(w), W.PATCH_Z, w.patch_n, W.K0, Z)
+    t_mm = time.time() - t0
+    t0 = time.time()
+    h = B.emsurf_create(w.nx, w.ny, w.E, nu, W.type_map(w), Z, L, K, coef, idx, sgn,
+                        precision=precision, max_rhs=w.n_rhs, tables_on_device=True)
+    torch.cuda.synchronize()
+    t_create = time.time() - t0
+    del L, K, Z
+    torch.cuda.empty_cache()
+    waves = W.plane_waves(w)
+    V = torch.empty((w.n_rhs, nu), dtype=torch.complex128, device="cuda")
+    B.emsurf_excitation(h, A, A, H, w.n, W.K0, np.array([k for k, _ in waves]),
+                        np.array([e for _, e in waves]), V)
+    return h, V, nu, {"tabulate_s": round(t_tab, 3), "macromodels_s": round(t_mm, 3),
+                      "create_s": round(t_create, 3)}
+
+
+def time_matvec(B, torch, h, nu, R, prec, reps=10):
+    x = torch.randn((R, nu), dtype=torch.complex128, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(3):
+        B.emsurf_matvec(h, x, y, prec)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        B.emsurf_matvec(h, x, y, prec)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def cpu_oracle_matvec_seconds(W, w, nu_expected):
+    """One full FFT-free oracle product (Eq. MVP by the direct offset sum) on
+    random tables of the workload's shapes -- values do not change its cost."""
+    from oracle import lattice
+    from oracle.mesh import box_mesh
+    A = W.PERIOD
+    idx, sgn, nu = lattice.overlap_map(box_mesh(A, A, W.BOX_H, w.n), w.nx, w.ny, A, A)
+    assert nu == nu_expected
+    Lt, Kt = W.random_tables(w.nx, w.ny, w.E, 1)
+    Z = W.random_macromodels(w.n_types, w.K, 2)
+    x = W.random_vectors(1, nu, 3)[0]
+    t0 = time.perf_counter()
+    lattice.matvec_direct(x, Lt, Kt, (1j * W.K0, 1.0, -1.0, 1j * W.K0), Z, W.type_map(w), idx, sgn,
+                          nu, w.nx, w.ny)
+    return time.perf_counter() - t0
+
+
+def reference_arm(args, W, w):
+    ws, rank, _ = dist_init()
+    if rank != 0:
+        return
+    from oracle import lattice
+    from oracle.mesh import box_mesh
+    A = W.PERIOD
+    idx, sgn, nu = lattice.overlap_map(box_mesh(A, A, W.BOX_H, w.n), w.nx, w.ny, A, A)
+    Lt, Kt = W.random_tables(w.nx, w.ny, w.E, 1)
+    Z = W.random_macromodels(w.n_types, w.K, 2)
+    coef = (1j * W.K0, 1.0, -1.0, 1j * W.K0)
+    x = W.random_vectors(1, nu, 3)[0]
+    tm = W.type_map(w)
+    nmv = REF_MATVECS_PER_SOLVE
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        lattice.matvec_direct(x, Lt, Kt, coef, Z, tm, idx, sgn, nu, w.nx, w.ny)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    t_mv = statistics.mean(times)
+    value = t_mv * 1e3 * nmv if nmv else None
+    cores = len(os.sched_getaffinity(0))
+    sample = ("one full oracle direct-offset product (Eq. MVP, no FFT) per step on the %s "
+              "workload; solve time = per-product time x %s FP64 GMRES(30) products"
+              % (w.name, nmv))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_mv * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "K": w.K,
+                                        "unknowns": nu, "rtol": RTOL},
+        "cpu_baseline": {"value": value, "unit": "ms", "cores": cores, "kind": "oracle",
+                         "sample": sample, "matvec_s": t_mv},
+        "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="lattice16x16_k576")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    from paper_1911_04576_gb300 import workloads as W
+    w = W.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        reference_arm(args, W, w)
+        return
+    import torch
+    from paper_1911_04576_gb300 import binding as B
+    ws, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    # CPU oracle first (before any GPU context work on this process's pool)
+    cpu = None
+    h, V, nu, setup = build_problem(B, W, torch, w, B.MIXED)
+    X = torch.zeros_like(V)
+    hbm, peak_kind = peaks()
+    # FP64-plain reference solve on the same handle (FP64 operator GMRES)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st64, info64 = B.emsurf_solve(h, V, X, rtol=RTOL, restart=RESTART, max_iters=20000,
+                                  solver=B.SOLVER_FP64)
+    t64 = (time.perf_counter() - t0) * 1e3
+    # matvec rates
+    R = w.n_rhs
+    mv32 = time_matvec(B, torch, h, nu, R, B.FP32)
+    mv64 = time_matvec(B, torch, h, nu, R, B.FP64)
+    px, py, dev_bytes = B.emsurf_query(h)
+    P = px * py
+    bytes32 = 2 * w.E * w.E * P * 8 + w.n_types * w.K * w.K * 8 + 2 * R * nu * 16
+    bytes64 = 2 * w.E * w.E * P * 16 + w.n_types * w.K * w.K * 16 + 2 * R * nu * 16
+    solve_kw = dict(rtol=RTOL, restart=RESTART, max_iters=20000, max_refine=20,
+                    solver=B.SOLVER_MIXED)
+    for _ in range(args.warmup):
+        B.emsurf_solve(h, V, X, **solve_kw)
+    # ------------------------------------------------------------ timed region
+    clocks = ClockSampler(local)
+    clocks.start()
+    B.emsurf_profile(h, True)
+    launches0 = B.emsurf_launch_count(h)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    infos = []
+    for _ in range(args.steps):
+        st, info = B.emsurf_solve(h, V, X, **solve_kw)
+        infos.append(info[0])
+    e1.record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms_total = e0.elapsed_time(e1)
+    launches = B.emsurf_launch_count(h) - launches0
+    B.emsurf_profile(h, False)
+    clk = clocks.stop()
+    bin_ms, bin_n = B.emsurf_profile_read(h, "binmul32")
+    mm_ms, mm_n = B.emsurf_profile_read(h, "mm32")
+    fft_ms, fft_n = B.emsurf_profile_read(h, "fft32")
+    bin64_ms, bin64_n = B.emsurf_profile_read(h, "binmul64")
+    ms = ms_total / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+    # ------------------------------------------------------------ end to end
+    Vh = V.cpu().pin_memory()
+    Xh = torch.empty_like(Vh).pin_memory()
+    Vd = torch.empty_like(V)
+    Xd = torch.empty_like(V)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    for _ in range(args.steps):
+        Vd.copy_(Vh, non_blocking=True)
+        B.emsurf_solve(h, Vd, Xd, **solve_kw)
+        Xh.copy_(Xd, non_blocking=True)
+    f1.record()
+    torch.cuda.synchronize()
+    e2e_ms = f0.elapsed_time(f1) / args.steps
+    # ------------------------------------------------------------ CPU oracle
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        t_cpu = cpu_oracle_matvec_seconds(W, w, nu)
+        nmv64 = info64[0]["n_matvec"]
+        cpu = {"value": t_cpu * 1e3 * nmv64, "unit": "ms", "cores": len(os.sched_getaffinity(0)),
+               "kind": "oracle",
+               "sample": "one full oracle direct-offset product (Eq. MVP, FFT-free, complex128) "
+                         "on the same workload shapes, %.2f s; solve = that x %d products of "
+                         "the FP64 GMRES(30) solve" % (t_cpu, nmv64),
+               "matvec_s": round(t_cpu, 3)}
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    bin_avg = bin_ms / max(bin_n, 1)
+    alg_bin = 2 * w.E * w.E * P * 8 + 2 * R * w.K * P * 8
+    achieved = alg_bin / (bin_avg * 1e-3) / 1e9
+    last = infos[-1]
+    out = {
+        "metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "K": w.K, "n_types": w.n_types,
+                   "nrhs": R, "unknowns": nu, "grid": [px, py], "rtol": RTOL, "restart": RESTART,
+                   "solver": "GMRES(30) with FP32 operator inside FP64 residual refinement",
+                   "l2": "inputs larger than L2: %.2f GB complex64 + %.2f GB complex128 "
+                         "Fourier-domain blocks" % (bytes32 / 1e9, bytes64 / 1e9),
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "solve": {"iters": last["iters"], "refinements": last["refinements"],
+                  "n_matvec": last["n_matvec"], "rel_residual": last["rel_residual"],
+                  "converged": last["converged"]},
+        "fp64_plain": {"solve_ms": round(t64, 3), "iters": info64[0]["iters"],
+                       "n_matvec": info64[0]["n_matvec"], "rel_residual": info64[0]["rel_residual"],
+                       "converged": info64[0]["converged"], "speedup_mixed": round(t64 / ms, 3)},
+        "matvec": {"fp32_ms": round(mv32, 4), "fp32_gbs": round(bytes32 / mv32 / 1e6, 1),
+                   "fp64_ms": round(mv64, 4), "fp64_gbs": round(bytes64 / mv64 / 1e6, 1),
+                   "alg_bytes_fp32": bytes32, "alg_bytes_fp64": bytes64},
+        "roofline": {"kernel": "binmul_kernel<float2,1> (K2, bin multiply)", "bound": "hbm",
+                     "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4), "peak_kind": peak_kind,
+                     "traffic": None, "alg_bytes_per_launch": alg_bin,
+                     "avg_launch_ms": round(bin_avg, 5), "launches_timed": bin_n},
+        "phases_ms_per_solve": {"binmul32": round(bin_ms / args.steps, 3),
+                                "macromodel32": round(mm_ms / args.steps, 3),
+                                "fft32": round(fft_ms / args.steps, 3),
+                                "binmul64": round(bin64_ms / args.steps, 3)},
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": int(V.numel() * 16),
+                "d2h_bytes_per_step": int(V.numel() * 16)},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "setup": setup,
+        "device_bytes": dev_bytes,
+    }
+    print(json.dumps(out))
+    h.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

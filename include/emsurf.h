@@ -64,6 +64,7 @@ typedef struct emsurf_handle emsurf_handle;
  *               [0, n_unique)  (U_o of Eq. connections_IUI)           (host)
  *  uo_sign      [nx*ny*K] +1 / -1                                      (host)
  *  grid_px/py   FFT grid; 0 = smallest 2,3,5-smooth >= 2N-1; else >= 2N-1
+ *               with no prime factor above 7 (EINVAL otherwise)
  *  max_rhs      largest nrhs later passed to matvec/solve (>= 1)
  *  tables_on_device  0: offset_L/K and macromodels are host pointers;
  *                    1: they are device pointers on `device`
@@ -95,6 +96,9 @@ typedef struct {
     int32_t max_iters;    /* total inner iterations across restarts/refines    */
     int32_t max_refine;   /* MIXED only: outer FP64 refinement steps           */
     double inner_rtol;    /* MIXED only: inner FP32 solve tolerance (0 = 1e-4) */
+    int32_t solver;       /* 0: by handle precision; 1: FP64-operator GMRES;
+                             2: FP32-operator GMRES; 3: mixed refinement.
+                             The operators it needs must be resident.         */
 } emsurf_solve_opts;
 
 typedef struct {
@@ -134,6 +138,117 @@ EMSURF_API int emsurf_query(const emsurf_handle* h, int32_t* grid_px, int32_t* g
                             int64_t* device_bytes);
 
 EMSURF_API void emsurf_destroy(emsurf_handle* h);
+
+/* Tracing (no counterpart in the paper, which reports wall-clock phases
+ * only): CUDA-event timers around each phase of emsurf_matvec, recorded on
+ * the caller's stream while enabled.  enable != 0 clears and starts
+ * recording; 0 stops.  Phases: 0 bin multiply FP32, 1 bin multiply FP64,
+ * 2 macromodel multiply FP32, 3 macromodel FP64, 4 FFT passes + gather FP32,
+ * 5 the same FP64.  emsurf_profile_read synchronises on the recorded events
+ * and returns the summed milliseconds and the number of intervals.       */
+EMSURF_API int emsurf_profile(emsurf_handle* h, int32_t enable);
+EMSURF_API int emsurf_profile_read(emsurf_handle* h, int32_t phase, double* total_ms,
+                                   int64_t* count);
+
+/* Number of CUDA kernels this handle has launched since creation.        */
+EMSURF_API int emsurf_launch_count(const emsurf_handle* h, int64_t* launches);
+
+/* ------------------------------------------------------------------------
+ * Setup helpers (host).  Canonical meshes and the overlap map, by integer
+ * index arithmetic.  Output arrays are caller-allocated host arrays sized by
+ * the *_counts calls; nothing is written on EINVAL.
+ *
+ * Box S_eq of cell (0,0) (Sec. II-A): x in [-a/2,a/2], y in [-b/2,b/2],
+ * z in [0,h], n x n quads per face, opposite faces identical (translates).
+ * Vertices: surface grid points (i,j,k) in lexicographic order; faces
+ * x-,x+,y-,y+,z-,z+ with in-plane axes (j,k),(i,k),(i,j); quad (u,v) ->
+ * triangles (c00,c10,c11),(c00,c11,c01), index face*2n^2 + 2(v*n+u) + {0,1}.
+ * RWG edges (Eqs. Hdiscretebox/Ediscretebox): distinct vertex pairs sorted
+ * lexicographically; T+ = lower triangle; slot i of a triangle = edge
+ * opposite vertex i; slot_rwg = RWG index (-1 if none), slot_sgn = +1 on T+.
+ * zlevels: optional [n+1] z of the grid rows (NULL = uniform).
+ *   verts [V][3], tris [T][3], edges [E][2], tplus/tminus [E],
+ *   slot_rwg [T][3], slot_sgn [T][3].                                      */
+EMSURF_API int emsurf_setup_box_counts(int32_t n, int32_t* n_verts, int32_t* n_tris,
+                                       int32_t* n_edges);
+EMSURF_API int emsurf_setup_box_mesh(double a, double b, double h, int32_t n,
+                                     const double* zlevels, double* verts, int32_t* tris,
+                                     int32_t* edges, int32_t* tplus, int32_t* tminus,
+                                     int32_t* slot_rwg, int8_t* slot_sgn);
+
+/* Flat square PEC patch (Sec. II-A: J only on PEC) of side `side` centred
+ * on the cell axis at height z, n x n quads split like the box faces;
+ * vertices (i,j) at index i*(n+1)+j; RWGs on interior edges only.         */
+EMSURF_API int emsurf_setup_patch_counts(int32_t n, int32_t* n_verts, int32_t* n_tris,
+                                         int32_t* n_edges);
+EMSURF_API int emsurf_setup_patch_mesh(double side, double z, int32_t n, double* verts,
+                                       int32_t* tris, int32_t* edges, int32_t* tplus,
+                                       int32_t* tminus, int32_t* slot_rwg, int8_t* slot_sgn);
+
+/* U_o of Eq. connections_IUI (Sec. III-D, rule 1 with Delta -> 0 of
+ * Fig. connections) for an nx x ny lattice of boxes meshed n x n per face:
+ * RWGs of different boxes whose edges coincide and that share a coincident
+ * triangle are one unique unknown, signed so the coincident halves cancel
+ * (J^(m) = -J^(m') on a shared face).  Unique unknowns are numbered by first
+ * appearance over (cell m = iy*nx+ix, local k).  uo_index/uo_sign:
+ * [nx*ny*36n^2] host outputs; n_unique: out.                              */
+EMSURF_API int emsurf_setup_overlap(int32_t n, int32_t nx, int32_t ny, int32_t* uo_index,
+                                    int8_t* uo_sign, int32_t* n_unique);
+
+/* ------------------------------------------------------------------------
+ * Operator tabulation on the device (setup of Eq. out / Eq. blockZo).
+ *   L[b][m][n] = int int [Lam_m.Lam_n - div Lam_m div' Lam_n / k^2] G
+ *   K[b][m][n] = int int Lam_m(r) . [grad_r G(r,r') x Lam_n(r')]   (p.v.)
+ * with G = e^{-jkR}/(4 pi R) (Eqs. SIE_LOperator1, SIE_KOperator1), test
+ * mesh translated by shifts[b] relative to the source mesh.  7-point
+ * degree-5 rule on both triangles; for singular[b] != 0 the 1/R and
+ * grad(1/R) parts are integrated over the source triangle in closed form.
+ * Meshes are host arrays as produced by the setup helpers; L, K are device
+ * [n_blocks][test_E][src_E] complex128.  Synchronises `stream`.           */
+EMSURF_API int emsurf_tabulate(const double* test_verts, const int32_t* test_tris,
+                               const int32_t* test_slot_rwg, const int8_t* test_slot_sgn,
+                               int32_t test_T, int32_t test_E, const double* src_verts,
+                               const int32_t* src_tris, const int32_t* src_slot_rwg,
+                               const int8_t* src_slot_sgn, int32_t src_T, int32_t src_E,
+                               const double* shifts, const int8_t* singular, int32_t n_blocks,
+                               double k, emsurf_c128* L, emsurf_c128* K, void* stream);
+
+/* Offset tables of an nx x ny lattice of boxes (period a, b; height h; n x n
+ * per face): L, K device [2ny-1][2nx-1][E][E] indexed [dy+ny-1][dx+nx-1],
+ * d = test cell - source cell; closed-form singular parts for touching
+ * boxes (|dx|, |dy| <= 1).  The layout emsurf_create takes.               */
+EMSURF_API int emsurf_tabulate_offsets(double a, double b, double h, int32_t n, int32_t nx,
+                                       int32_t ny, double k, emsurf_c128* L, emsurf_c128* K,
+                                       void* stream);
+
+/* Macromodels Z~ of Eq. Zmacromodel for cells holding one flat PEC square
+ * patch of side sides[t] (centred, height patch_z, patch_n x patch_n quads)
+ * in a free-space box: Schur complement of the patch unknowns of the
+ * interior system [[jk L_ee, K_ee, jk L_ep], [-K_ee, jk L_ee, -K_ep],
+ * [jk L_pe, K_pe, jk L_pp]] (Secs. II-B..D).  sides[t] <= 0: empty box.
+ * Z: device [n_types][K][K] complex128.  EINVAL if a patch does not fit
+ * strictly inside the box or has more than 100 RWGs.                      */
+EMSURF_API int emsurf_macromodel_pec_patch(double a, double b, double h, int32_t n,
+                                           int32_t n_types, const double* sides, double patch_z,
+                                           int32_t patch_n, double k, emsurf_c128* Z,
+                                           void* stream);
+
+/* Excitation V~ = U_o^T V of Eq. final for nrhs plane waves
+ * E_inc = ehat e^{-jk khat.r} (|E_inc| = 1 V/m): rows J test E_inc, rows M
+ * test eta0 H_inc = (khat x ehat) e^{..} (Eq. out).  khat, ehat: host
+ * [nrhs][3] unit vectors; V: device [nrhs][n_unique].  The box geometry
+ * (a, b, h, n) must be the one the handle's tables were built for.        */
+EMSURF_API int emsurf_excitation(emsurf_handle* h, double a, double b, double hgt, int32_t n,
+                                 double k, int32_t nrhs, const double* khat, const double* ehat,
+                                 emsurf_c128* V, void* stream);
+
+/* Far field radiated by solved currents Y~ (device [nrhs][n_unique]) in
+ * ndir directions rhat (host [ndir][3] unit vectors): F (device
+ * [nrhs][ndir][3]) with E ~ F e^{-jkr}/r, and optionally the bistatic RCS
+ * sigma = 4 pi |F|^2 (device [nrhs][ndir], m^2; NULL to skip).            */
+EMSURF_API int emsurf_far_field(emsurf_handle* h, double a, double b, double hgt, int32_t n,
+                                double k, const emsurf_c128* Y, int32_t nrhs, int32_t ndir,
+                                const double* rhat, emsurf_c128* F, double* rcs, void* stream);
 
 /* Thread-local message of the last failing call on this thread.          */
 EMSURF_API const char* emsurf_last_error(void);

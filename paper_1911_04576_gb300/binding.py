@@ -44,7 +44,7 @@ class Problem(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("restart", C.c_int32), ("max_iters", C.c_int32),
-                ("max_refine", C.c_int32), ("inner_rtol", C.c_double)]
+                ("max_refine", C.c_int32), ("inner_rtol", C.c_double), ("solver", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -71,6 +71,22 @@ def lib():
         L.emsurf_destroy.argtypes = [vp]
         L.emsurf_destroy.restype = None
         L.emsurf_last_error.restype = C.c_char_p
+        ip = C.POINTER(C.c_int32)
+        L.emsurf_setup_box_counts.argtypes = [i32, ip, ip, ip]
+        L.emsurf_setup_patch_counts.argtypes = [i32, ip, ip, ip]
+        L.emsurf_setup_box_mesh.argtypes = [C.c_double, C.c_double, C.c_double, i32, vp] + [vp] * 7
+        L.emsurf_setup_patch_mesh.argtypes = [C.c_double, C.c_double, i32] + [vp] * 7
+        L.emsurf_setup_overlap.argtypes = [i32, i32, i32, vp, vp, ip]
+        d = C.c_double
+        L.emsurf_profile.argtypes = [vp, i32]
+        L.emsurf_profile_read.argtypes = [vp, i32, C.POINTER(d), C.POINTER(C.c_int64)]
+        L.emsurf_launch_count.argtypes = [vp, C.POINTER(C.c_int64)]
+        L.emsurf_tabulate.argtypes = [vp, vp, vp, vp, i32, i32, vp, vp, vp, vp, i32, i32, vp, vp,
+                                      i32, d, vp, vp, vp]
+        L.emsurf_tabulate_offsets.argtypes = [d, d, d, i32, i32, i32, d, vp, vp, vp]
+        L.emsurf_macromodel_pec_patch.argtypes = [d, d, d, i32, i32, vp, d, i32, d, vp, vp]
+        L.emsurf_excitation.argtypes = [vp, d, d, d, i32, d, i32, vp, vp, vp, vp]
+        L.emsurf_far_field.argtypes = [vp, d, d, d, i32, d, vp, i32, i32, vp, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -160,11 +176,14 @@ def emsurf_matvec(h, x, y, precision=FP64, stream=None):
     _check(lib().emsurf_matvec(h.ptr, _ptr(x), _ptr(y), nrhs, precision, _stream(stream)))
 
 
+SOLVER_DEFAULT, SOLVER_FP64, SOLVER_FP32, SOLVER_MIXED = 0, 1, 2, 3
+
+
 def emsurf_solve(h, b, x, rtol=1e-8, restart=30, max_iters=5000, max_refine=10, inner_rtol=0.0,
-                 stream=None):
+                 solver=SOLVER_DEFAULT, stream=None):
     """emsurf_solve: returns (status, [info dict per rhs]); ENOTCONV is not raised."""
     nrhs = 1 if b.dim() == 1 else b.shape[0]
-    o = SolveOpts(rtol, restart, max_iters, max_refine, inner_rtol)
+    o = SolveOpts(rtol, restart, max_iters, max_refine, inner_rtol, solver)
     info = (SolveInfo * nrhs)()
     st = _check(lib().emsurf_solve(h.ptr, _ptr(b), _ptr(x), nrhs, C.byref(o), info, _stream(stream)),
                 ok=(EMSURF_OK, EMSURF_ENOTCONV))
@@ -175,3 +194,106 @@ def emsurf_query(h):
     px, py, nb = C.c_int32(), C.c_int32(), C.c_int64()
     _check(lib().emsurf_query(h.ptr, C.byref(px), C.byref(py), C.byref(nb)))
     return px.value, py.value, nb.value
+
+
+def _mesh_arrays(V, T, E):
+    return dict(verts=np.zeros((V, 3)), tris=np.zeros((T, 3), np.int32),
+                edges=np.zeros((E, 2), np.int32), tplus=np.zeros(E, np.int32),
+                tminus=np.zeros(E, np.int32), slot_rwg=np.zeros((T, 3), np.int32),
+                slot_sgn=np.zeros((T, 3), np.int8))
+
+
+def _counts(fn, n):
+    V, T, E = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(fn(n, C.byref(V), C.byref(T), C.byref(E)))
+    return V.value, T.value, E.value
+
+
+_MESH_KEYS = ("verts", "tris", "edges", "tplus", "tminus", "slot_rwg", "slot_sgn")
+
+
+def emsurf_setup_box_mesh(a, b, h, n, zlevels=None):
+    """emsurf_setup_box_mesh: returns dict of the canonical box mesh arrays."""
+    out = _mesh_arrays(*_counts(lib().emsurf_setup_box_counts, n))
+    z = None if zlevels is None else np.ascontiguousarray(zlevels, dtype=np.float64)
+    _check(lib().emsurf_setup_box_mesh(a, b, h, n, _ptr(z), *[_ptr(out[k]) for k in _MESH_KEYS]))
+    return out
+
+
+def emsurf_setup_patch_mesh(side, z, n):
+    """emsurf_setup_patch_mesh: returns dict of the patch mesh arrays."""
+    out = _mesh_arrays(*_counts(lib().emsurf_setup_patch_counts, n))
+    _check(lib().emsurf_setup_patch_mesh(side, z, n, *[_ptr(out[k]) for k in _MESH_KEYS]))
+    return out
+
+
+def emsurf_setup_overlap(n, nx, ny):
+    """emsurf_setup_overlap: returns (uo_index int32, uo_sign int8, n_unique)."""
+    K = 36 * n * n
+    idx = np.zeros(nx * ny * K, np.int32)
+    sgn = np.zeros(nx * ny * K, np.int8)
+    nu = C.c_int32()
+    _check(lib().emsurf_setup_overlap(n, nx, ny, _ptr(idx), _ptr(sgn), C.byref(nu)))
+    return idx, sgn, nu.value
+
+
+def emsurf_tabulate(test, src, shifts, singular, k, L, K, stream=None):
+    """emsurf_tabulate: test/src mesh dicts (setup helpers); L, K torch CUDA
+    complex128 tensors [nb, test_E, src_E]."""
+    shifts = np.ascontiguousarray(shifts, dtype=np.float64)
+    singular = np.ascontiguousarray(singular, dtype=np.int8)
+    m = [test[x] for x in ("verts", "tris", "slot_rwg", "slot_sgn")]
+    s = [src[x] for x in ("verts", "tris", "slot_rwg", "slot_sgn")]
+    _check(lib().emsurf_tabulate(*[_ptr(v) for v in m], len(test["tris"]), len(test["tplus"]),
+                                 *[_ptr(v) for v in s], len(src["tris"]), len(src["tplus"]),
+                                 _ptr(shifts), _ptr(singular), len(singular), k, _ptr(L), _ptr(K),
+                                 _stream(stream)))
+
+
+def emsurf_tabulate_offsets(a, b, h, n, nx, ny, k, L, K, stream=None):
+    """emsurf_tabulate_offsets: L, K torch CUDA complex128 [2ny-1, 2nx-1, E, E]."""
+    _check(lib().emsurf_tabulate_offsets(a, b, h, n, nx, ny, k, _ptr(L), _ptr(K), _stream(stream)))
+
+
+def emsurf_macromodel_pec_patch(a, b, h, n, sides, patch_z, patch_n, k, Z, stream=None):
+    """emsurf_macromodel_pec_patch: Z torch CUDA complex128 [T, K, K]."""
+    sides = np.ascontiguousarray(sides, dtype=np.float64)
+    _check(lib().emsurf_macromodel_pec_patch(a, b, h, n, len(sides), _ptr(sides), patch_z, patch_n,
+                                             k, _ptr(Z), _stream(stream)))
+
+
+def emsurf_excitation(hd, a, b, h, n, k, khat, ehat, V, stream=None):
+    """emsurf_excitation: khat, ehat host [nrhs, 3]; V torch CUDA [nrhs, n_unique]."""
+    khat = np.ascontiguousarray(np.atleast_2d(khat), dtype=np.float64)
+    ehat = np.ascontiguousarray(np.atleast_2d(ehat), dtype=np.float64)
+    _check(lib().emsurf_excitation(hd.ptr, a, b, h, n, k, len(khat), _ptr(khat), _ptr(ehat), _ptr(V),
+                                   _stream(stream)))
+
+
+def emsurf_far_field(hd, a, b, h, n, k, Y, rhat, F, rcs=None, stream=None):
+    """emsurf_far_field: Y torch CUDA [nrhs, n_unique]; rhat host [ndir, 3];
+    F torch CUDA complex128 [nrhs, ndir, 3]; rcs torch CUDA float64 [nrhs, ndir]."""
+    rhat = np.ascontiguousarray(rhat, dtype=np.float64)
+    nrhs = 1 if Y.dim() == 1 else Y.shape[0]
+    _check(lib().emsurf_far_field(hd.ptr, a, b, h, n, k, _ptr(Y), nrhs, len(rhat), _ptr(rhat),
+                                  _ptr(F), _ptr(rcs), _stream(stream)))
+
+
+PHASES = {"binmul32": 0, "binmul64": 1, "mm32": 2, "mm64": 3, "fft32": 4, "fft64": 5}
+
+
+def emsurf_profile(h, enable):
+    _check(lib().emsurf_profile(h.ptr, 1 if enable else 0))
+
+
+def emsurf_profile_read(h, phase):
+    """Returns (total_ms, intervals) of a phase name from PHASES."""
+    ms, n = C.c_double(), C.c_int64()
+    _check(lib().emsurf_profile_read(h.ptr, PHASES[phase], C.byref(ms), C.byref(n)))
+    return ms.value, n.value
+
+
+def emsurf_launch_count(h):
+    n = C.c_int64()
+    _check(lib().emsurf_launch_count(h.ptr, C.byref(n)))
+    return n.value

@@ -183,6 +183,8 @@ int create_impl(const emsurf_problem* p, emsurf_handle* h) {
 }
 
 void free_handle(emsurf_handle* h) {
+    for (auto& pt : h->prof)
+        for (cudaEvent_t e : pt.ev) cudaEventDestroy(e);
     for (void* p : h->allocations) cudaFree(p);
     h->allocations.clear();
     fft_plan_destroy(h->plan_x);
@@ -191,6 +193,24 @@ void free_handle(emsurf_handle* h) {
 }
 
 }  // namespace
+
+void prof_mark(emsurf_handle* h, int phase, bool begin, cudaStream_t st) {
+    if (!h->prof_on) return;
+    PhaseTimer& pt = h->prof[phase];
+    // a begin takes a fresh pair; an end closes the pair opened last
+    if (begin) {
+        if (pt.used + 2 > pt.ev.size())
+            for (int i = 0; i < 2; ++i) {
+                cudaEvent_t e;
+                if (cudaEventCreate(&e) != cudaSuccess) { h->prof_on = false; return; }
+                pt.ev.push_back(e);
+            }
+        cudaEventRecord(pt.ev[pt.used], st);
+        pt.used += 2;
+    } else if (pt.used >= 2) {
+        cudaEventRecord(pt.ev[pt.used - 1], st);
+    }
+}
 
 void gmres_release(emsurf_handle* h);
 
@@ -262,8 +282,22 @@ EMSURF_API int emsurf_solve(emsurf_handle* h, const emsurf_c128* b, emsurf_c128*
         set_error("need rtol > 0, restart in [1, 64], max_iters >= 1");
         return EMSURF_EINVAL;
     }
-    if (h->precision == EMSURF_MIXED && opts->max_refine < 1) {
-        set_error("MIXED solve needs max_refine >= 1");
+    if (opts->solver < 0 || opts->solver > 3) {
+        set_error("solver must be 0..3");
+        return EMSURF_EINVAL;
+    }
+    const int mode = opts->solver ? opts->solver
+                                  : (h->precision == EMSURF_MIXED ? 3 : (h->precision == EMSURF_FP32 ? 2 : 1));
+    if ((mode == 1 || mode == 3) && !h->have64) {
+        set_error("solver needs the FP64 operator, which is not resident");
+        return EMSURF_EINVAL;
+    }
+    if ((mode == 2 || mode == 3) && !h->have32) {
+        set_error("solver needs the FP32 operator, which is not resident");
+        return EMSURF_EINVAL;
+    }
+    if (mode == 3 && opts->max_refine < 1) {
+        set_error("mixed solve needs max_refine >= 1");
         return EMSURF_EINVAL;
     }
     DeviceGuard dg(h->device);
@@ -277,6 +311,36 @@ EMSURF_API int emsurf_query(const emsurf_handle* h, int32_t* grid_px, int32_t* g
     if (grid_px) *grid_px = h->px;
     if (grid_py) *grid_py = h->py;
     if (device_bytes) *device_bytes = h->device_bytes;
+    return EMSURF_OK;
+}
+
+EMSURF_API int emsurf_profile(emsurf_handle* h, int32_t enable) {
+    if (!h) { set_error("NULL handle"); return EMSURF_EINVAL; }
+    if (enable) for (auto& pt : h->prof) pt.used = 0;
+    h->prof_on = enable != 0;
+    return EMSURF_OK;
+}
+
+EMSURF_API int emsurf_profile_read(emsurf_handle* h, int32_t phase, double* total_ms,
+                                   int64_t* count) {
+    if (!h || phase < 0 || phase >= EMS_NPHASE) { set_error("bad handle or phase"); return EMSURF_EINVAL; }
+    DeviceGuard dg(h->device);
+    PhaseTimer& pt = h->prof[phase];
+    double ms = 0.0;
+    for (size_t i = 0; i < pt.used; i += 2) {
+        float t = 0.0f;
+        EMS_CUDA(cudaEventSynchronize(pt.ev[i + 1]));
+        EMS_CUDA(cudaEventElapsedTime(&t, pt.ev[i], pt.ev[i + 1]));
+        ms += t;
+    }
+    if (total_ms) *total_ms = ms;
+    if (count) *count = (int64_t)(pt.used / 2);
+    return EMSURF_OK;
+}
+
+EMSURF_API int emsurf_launch_count(const emsurf_handle* h, int64_t* launches) {
+    if (!h || !launches) { set_error("NULL argument"); return EMSURF_EINVAL; }
+    *launches = h->launches;
     return EMSURF_OK;
 }
 

@@ -70,7 +70,7 @@ template <> __host__ __device__ __forceinline__ float2 mk<float2>(double re, dou
 }
 
 // ---------------------------------------------------------------- FFT plan
-// One 1-D transform length P = product of radices (each 2, 3, 4 or 5) with
+// One 1-D transform length P = product of radices (each 2, 3, 4, 5 or 7) with
 // a device table tw[k] = exp(-2 pi i k / P), k in [0, P), from host libm.
 struct FftPlan {
     int P = 0;
@@ -107,6 +107,14 @@ struct Operator {
 
 }  // namespace emsurf
 
+// Per-phase CUDA-event timers (recorded on the launching stream).
+struct PhaseTimer {
+    std::vector<cudaEvent_t> ev;   // pairs (start, stop)
+    size_t used = 0;               // events in use
+};
+enum { EMS_PH_BINMUL32 = 0, EMS_PH_BINMUL64, EMS_PH_MM32, EMS_PH_MM64, EMS_PH_FFT32, EMS_PH_FFT64,
+       EMS_NPHASE };
+
 struct emsurf_handle {
     int device = 0;
     int nx = 0, ny = 0, E = 0, K = 0, M = 0, T = 0, n_unique = 0, max_rhs = 1;
@@ -132,11 +140,30 @@ struct emsurf_handle {
     bool have64 = false, have32 = false;
     // GMRES workspace (FP64), allocated lazily by emsurf_solve
     void* gm = nullptr;
+    // tracing: kernel launches issued by this handle, optional phase timers
+    int64_t launches = 0;
+    bool prof_on = false;
+    PhaseTimer prof[EMS_NPHASE];
     std::vector<void*> allocations;
 };
 
 namespace emsurf {
 int dev_alloc(emsurf_handle* h, void** p, size_t bytes);
+// record the start (begin = true) or end of a phase on stream st if profiling
+void prof_mark(emsurf_handle* h, int phase, bool begin, cudaStream_t st);
+
+// a triangle mesh with RWG slots, host arrays (see emsurf_setup_box_mesh)
+struct MeshView {
+    const double* verts;
+    const int32_t* tris;
+    const int32_t* slot_rwg;
+    const int8_t* slot_sgn;
+    int T, E;
+};
+// Galerkin L, K [nb][test E][src E] on the device for nb test-mesh shifts
+int tabulate_blocks(const MeshView& test, const MeshView& src, const double* shifts,
+                    const int8_t* singular, int nb, double k, double2* L, double2* K,
+                    cudaStream_t st);
 template <typename T2>
 int build_operator(emsurf_handle* h, Operator<T2>& op, const emsurf_problem* pr);
 template <typename T2>

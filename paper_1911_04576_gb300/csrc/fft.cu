@@ -7,7 +7,7 @@
 // sequences (local unknowns k, right-hand sides, or block entries (op,j,i))
 // that sit next to each other in memory, so one CTA loads a P x W tile whose
 // rows are W contiguous lanes (coalesced), transforms all W lanes in shared
-// memory with a Stockham autosort mixed-radix algorithm (radices 2,3,4,5;
+// memory with a Stockham autosort mixed-radix algorithm (radices 2,3,4,5,7;
 // Govindaraju et al., SC 2008), and writes the tile back in place.
 #include <cmath>
 
@@ -23,7 +23,7 @@ struct RadList {
 };
 
 constexpr int kFftThreads = 256;
-constexpr int kMaxRadix = 5;
+constexpr int kMaxRadix = 7;
 
 template <typename T2>
 __device__ __forceinline__ T2 tw_at(const double2* __restrict__ tw, int k, int sign) {
@@ -133,8 +133,9 @@ int fft_plan_create(FftPlan& plan, int P) {
     while (t % 2 == 0 && n < 16) { rad[n++] = 2; t /= 2; }
     while (t % 3 == 0 && n < 16) { rad[n++] = 3; t /= 3; }
     while (t % 5 == 0 && n < 16) { rad[n++] = 5; t /= 5; }
+    while (t % 7 == 0 && n < 16) { rad[n++] = 7; t /= 7; }
     if (t != 1 || P < 1) {
-        set_error("FFT length %d is not 2,3,5-smooth", P);
+        set_error("FFT length %d has a prime factor other than 2, 3, 5, 7", P);
         return EMSURF_EINVAL;
     }
     plan.P = P;

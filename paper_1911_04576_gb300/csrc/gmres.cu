@@ -44,6 +44,7 @@ struct Gm {
     int* jend = nullptr;       // [R]
     double* h_res = nullptr;   // pinned host mirror [R]
     int* h_act = nullptr;      // pinned host mirror [R]
+    int64_t launches = 0;      // kernels launched by the solver itself
 };
 
 __device__ __forceinline__ double2 conj_mul(double2 a, double2 b) {   // conj(a) * b
@@ -314,14 +315,17 @@ int norms(Gm* g, const double2* v, int R, cudaStream_t st) {
     dim3 grid(kRedBlocks, 1, R);
     dot_partial_kernel<<<grid, kRedThreads, 0, st>>>(v, 1, 0, v, g->n, R, g->part, g->m + 1);
     EMS_CUDA(cudaGetLastError());
+    ++g->launches;
     dot_final_kernel<<<dim3(1, R), 32, 0, st>>>(g->part, kRedBlocks, 1, g->m + 1, g->hv, g->H,
                                                 g->m, 0, g->nrm, 2);
     EMS_CUDA(cudaGetLastError());
+    ++g->launches;
     return EMSURF_OK;
 }
 
 struct Apply {
     emsurf_handle* h;
+    // (kernel launches of this file are counted where they are issued)
     int prec;   // operator used inside GMRES
     int count = 0;
     int operator()(const double2* x, double2* y, int R, cudaStream_t st) {
@@ -350,14 +354,17 @@ int gmres_core(emsurf_handle* h, Gm* g, Apply& A, const double2* b, double2* x, 
             EMS_TRY(A(x, g->w, R, st));
             residual_kernel<<<nb, 256, 0, st>>>(g->r0, b, g->w, nv);
             EMS_CUDA(cudaGetLastError());
+    ++g->launches;
         }
         first = false;
         EMS_TRY(norms(g, g->r0, R, st));
         cycle_start_kernel<<<1, 64, 0, st>>>(g->nrm, g->bnorm, g->g, g->res, g->active, g->jend,
                                               m, R, rtol);
         EMS_CUDA(cudaGetLastError());
+    ++g->launches;
         normalize_kernel<<<nb, 256, 0, st>>>(g->V, g->r0, g->nrm, n, R, nullptr, m, 0);
         EMS_CUDA(cudaGetLastError());
+    ++g->launches;
         EMS_CUDA(cudaMemcpyAsync(g->h_act, g->active, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
         EMS_CUDA(cudaStreamSynchronize(st));
         bool any = false;
@@ -371,19 +378,24 @@ int gmres_core(emsurf_handle* h, Gm* g, Apply& A, const double2* b, double2* x, 
                 dot_partial_kernel<<<dim3(kRedBlocks, j + 1, R), kRedThreads, 0, st>>>(
                     g->V, j + 1, vstride, g->w, n, R, g->part, m + 1);
                 EMS_CUDA(cudaGetLastError());
+    ++g->launches;
                 dot_final_kernel<<<dim3(j + 1, R), 32, 0, st>>>(g->part, kRedBlocks, j + 1, m + 1,
                                                                 g->hv, g->H, m, j, g->nrm, pass);
                 EMS_CUDA(cudaGetLastError());
+    ++g->launches;
                 cgs_update_kernel<<<nb, 256, 0, st>>>(g->V, j + 1, vstride, g->hv, m + 1, g->w, n, R);
                 EMS_CUDA(cudaGetLastError());
+    ++g->launches;
             }
             EMS_TRY(norms(g, g->w, R, st));
             normalize_kernel<<<nb, 256, 0, st>>>(g->V + (size_t)(j + 1) * vstride, g->w, g->nrm, n,
                                                  R, g->H, m, j);
             EMS_CUDA(cudaGetLastError());
+    ++g->launches;
             givens_kernel<<<1, 64, 0, st>>>(g->H, g->cs, g->sn, g->g, g->bnorm, g->res, g->active,
                                              g->jend, m, j, R, rtol);
             EMS_CUDA(cudaGetLastError());
+    ++g->launches;
             EMS_CUDA(cudaMemcpyAsync(g->h_act, g->active, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
             EMS_CUDA(cudaStreamSynchronize(st));
             ++it;
@@ -393,8 +405,10 @@ int gmres_core(emsurf_handle* h, Gm* g, Apply& A, const double2* b, double2* x, 
         }
         trisolve_kernel<<<1, 64, 0, st>>>(g->H, g->g, g->hv, g->jend, m, R);
         EMS_CUDA(cudaGetLastError());
+    ++g->launches;
         xupdate_kernel<<<nb, 256, 0, st>>>(x, g->V, vstride, g->hv, g->jend, m, n, R);
         EMS_CUDA(cudaGetLastError());
+    ++g->launches;
     }
     *iters_out = it;
     return EMSURF_OK;
@@ -407,6 +421,7 @@ int true_residual(emsurf_handle* h, Gm* g, Apply& A, const double2* b, const dou
     EMS_TRY(A(x, g->w, R, st));
     residual_kernel<<<blocks_for(nv), 256, 0, st>>>(g->r0, b, g->w, nv);
     EMS_CUDA(cudaGetLastError());
+    ++g->launches;
     EMS_TRY(norms(g, g->r0, R, st));
     std::vector<double> rn(R), bn(R);
     EMS_CUDA(cudaMemcpyAsync(rn.data(), g->nrm, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
@@ -427,11 +442,14 @@ int gmres_solve(emsurf_handle* h, const double2* b, double2* x, int R, const ems
     EMS_TRY(gm_alloc(h, g, m, R));
     const size_t nv = (size_t)R * g->n;
     EMS_CUDA(cudaMemsetAsync(x, 0, nv * sizeof(double2), st));
+    const int64_t launches0 = g->launches;
     int iters = 0, refines = 0, nmv = 0;
     std::vector<double> res(R, 0.0);
     Apply A64{h, EMSURF_FP64};
     Apply A32{h, EMSURF_FP32};
-    if (h->precision == EMSURF_MIXED) {
+    int mode = o->solver;
+    if (mode == 0) mode = h->precision == EMSURF_MIXED ? 3 : (h->precision == EMSURF_FP32 ? 2 : 1);
+    if (mode == 3) {
         const double inner = o->inner_rtol > 0 ? o->inner_rtol : 1e-4;
         bool zero = true;
         while (true) {
@@ -460,17 +478,19 @@ int gmres_solve(emsurf_handle* h, const double2* b, double2* x, int R, const ems
             iters += it;
             axpy_kernel<<<blocks_for(nv), 256, 0, st>>>(x, c, nv);
             EMS_CUDA(cudaGetLastError());
+    ++g->launches;
             ++refines;
             zero = false;
         }
         nmv = A64.count + A32.count;
     } else {
-        Apply& A = (h->precision == EMSURF_FP32) ? A32 : A64;
+        Apply& A = (mode == 2) ? A32 : A64;
         EMS_TRY(gmres_core(h, g, A, b, x, R, m, o->rtol, o->max_iters, true, st, &iters));
         EMS_TRY(true_residual(h, g, A, b, x, R, st, res.data()));
         nmv = A.count;
     }
     EMS_CUDA(cudaStreamSynchronize(st));
+    h->launches += g->launches - launches0;
     const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     bool all = true;
     for (int r = 0; r < R; ++r) {

@@ -338,12 +338,19 @@ int apply_operator(emsurf_handle* h, Operator<T2>& op, const double2* x, double2
                    cudaStream_t st) {
     const int E = h->E, K = h->K, px = h->px, py = h->py;
     const long long lanes = (long long)R * K;
+    const bool f64 = sizeof(T2) == sizeof(double2);
+    const int ph_fft = f64 ? EMS_PH_FFT64 : EMS_PH_FFT32;
+    const int ph_bin = f64 ? EMS_PH_BINMUL64 : EMS_PH_BINMUL32;
+    const int ph_mm = f64 ? EMS_PH_MM64 : EMS_PH_MM32;
+    prof_mark(h, ph_fft, true, st);
     // K1: gather rows iy < ny (rows beyond are zero and stay zero under the x-pass)
     gather_pad_kernel<T2><<<grid_for((size_t)py * px * lanes, 256), 256, 0, st>>>(
         op.Xg, x, h->d_uo_index, h->d_uo_sign, h->nx, h->ny, px, py, R, K, h->n_unique);
     EMS_CUDA(cudaGetLastError());
     EMS_TRY(fft_pass<T2>(op.Xg, h->plan_x, lanes, h->ny, (long long)px * lanes, -1, st));
     EMS_TRY(fft_pass<T2>(op.Xg, h->plan_y, (long long)px * lanes, 1, 0, -1, st));
+    prof_mark(h, ph_fft, false, st);
+    prof_mark(h, ph_bin, true, st);
     // K2
     const int threads = std::min(1024, ((E + 31) / 32) * 32);
     const int nb = h->nbins;
@@ -364,10 +371,15 @@ int apply_operator(emsurf_handle* h, Operator<T2>& op, const double2* x, double2
                                                               op.coef[0], op.coef[1], op.coef[2], op.coef[3]);
         }
         EMS_CUDA(cudaGetLastError());
+        h->launches += 1;
     }
+    prof_mark(h, ph_bin, false, st);
+    prof_mark(h, ph_fft, true, st);
     // K3: inverse y-pass on all columns, inverse x-pass on the rows kept
     EMS_TRY(fft_pass<T2>(op.Yg, h->plan_y, (long long)px * lanes, 1, 0, +1, st));
     EMS_TRY(fft_pass<T2>(op.Yg, h->plan_x, lanes, h->ny, (long long)px * lanes, +1, st));
+    prof_mark(h, ph_fft, false, st);
+    prof_mark(h, ph_mm, true, st);
     // K4
     {
         constexpr int G = 4;
@@ -379,10 +391,12 @@ int apply_operator(emsurf_handle* h, Operator<T2>& op, const double2* x, double2
             h->n_unique);
         EMS_CUDA(cudaGetLastError());
     }
+    prof_mark(h, ph_mm, false, st);
     crop_scatter_kernel<T2><<<grid_for((size_t)R * h->n_unique, 256), 256, 0, st>>>(
         y, op.Yg, op.Ymm, h->d_inv_ptr, h->d_inv_ent, h->d_inv_sgn, h->nx, px, K, h->M, R,
         h->n_unique, 1.0 / (double)h->nbins);
     EMS_CUDA(cudaGetLastError());
+    h->launches += 7;   // gather, 4 FFT passes, macromodel, crop/scatter
     return EMSURF_OK;
 }
 

@@ -1,0 +1,58 @@
+"""The product's setup library (C++, integer index arithmetic) reproduces
+the oracle's meshes and its geometric U_o map exactly (host only)."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import lattice
+from oracle.mesh import box_mesh, patch_mesh
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_1911_04576_gb300 import binding, build
+    if not os.path.exists(binding.LIB_PATH):
+        build.build()
+    return binding
+
+
+def _same_mesh(p, o):
+    assert np.array_equal(p["tris"], o.tris)
+    assert np.array_equal(p["edges"], o.edges)
+    assert np.array_equal(p["tplus"], o.tplus) and np.array_equal(p["tminus"], o.tminus)
+    assert np.array_equal(p["slot_rwg"], o.slot_rwg) and np.array_equal(p["slot_sgn"], o.slot_sgn)
+    assert np.allclose(p["verts"], o.verts, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+def test_box_mesh_matches_oracle(B, n):
+    _same_mesh(B.emsurf_setup_box_mesh(0.015, 0.012, 0.0075, n), box_mesh(0.015, 0.012, 0.0075, n))
+
+
+def test_box_mesh_with_z_levels(B):
+    z = [0.0, 0.00076, 0.004, 0.0075]
+    _same_mesh(B.emsurf_setup_box_mesh(0.015, 0.015, 0.0075, 3, z), box_mesh(0.015, 0.015, 0.0075, 3, z))
+
+
+@pytest.mark.parametrize("n", [1, 3, 4])
+def test_patch_mesh_matches_oracle(B, n):
+    _same_mesh(B.emsurf_setup_patch_mesh(0.009, 0.00076, n), patch_mesh(0.009, 0.00076, n))
+
+
+@pytest.mark.parametrize("n,nx,ny", [(1, 1, 1), (2, 2, 1), (2, 1, 3), (2, 3, 3), (3, 4, 2), (4, 3, 2), (1, 6, 5)])
+def test_overlap_matches_geometric_oracle(B, n, nx, ny):
+    a = 0.015
+    idx, sgn, nu = B.emsurf_setup_overlap(n, nx, ny)
+    oi, osg, onu = lattice.overlap_map(box_mesh(a, a, 0.0075, n), nx, ny, a, a)
+    assert nu == onu
+    assert np.array_equal(idx, oi) and np.array_equal(sgn, osg)
+
+
+def test_setup_rejects_bad_sizes(B):
+    for call in (lambda: B.emsurf_setup_box_mesh(1.0, 1.0, 1.0, 0),
+                 lambda: B.emsurf_setup_patch_mesh(-1.0, 0.0, 2),
+                 lambda: B.emsurf_setup_overlap(2, 0, 3)):
+        with pytest.raises(B.EmsurfError) as e:
+            call()
+        assert e.value.status == B.EMSURF_EINVAL
