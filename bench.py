@@ -35,7 +35,7 @@ RTOL = 1e-6
 RESTART = 30
 # FP64-operator GMRES(30) matvecs to reach 1e-6 on the default workload, as
 # measured on GB300; scales the CPU oracle's per-matvec time to a solve.
-REF_MATVECS_PER_SOLVE = None
+REF_MATVECS_PER_SOLVE = 1905
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -216,6 +216,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="lattice16x16_k576")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--matvecs-only", type=int, default=0,
+                    help="profiler driver: build the workload, run this many products, exit")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32", "fp64"],
+                    help="operators kept resident (--matvecs-only)")
     args = ap.parse_args()
     from paper_1911_04576_gb300 import workloads as W
     w = W.WORKLOADS[args.workload]
@@ -230,8 +234,18 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    # CPU oracle first (before any GPU context work on this process's pool)
     cpu = None
+    if args.matvecs_only:
+        prec = {"mixed": B.MIXED, "fp32": B.FP32, "fp64": B.FP64}[args.precision]
+        h, V, nu, _ = build_problem(B, W, torch, w, prec)
+        for p in ((B.FP32,) if prec == B.FP32 else (B.FP64,) if prec == B.FP64 else (B.FP32, B.FP64)):
+            x = torch.randn((w.n_rhs, nu), dtype=torch.complex128, device="cuda")
+            y = torch.empty_like(x)
+            for _ in range(args.matvecs_only):
+                B.emsurf_matvec(h, x, y, p)
+        torch.cuda.synchronize()
+        h.close()
+        return
     h, V, nu, setup = build_problem(B, W, torch, w, B.MIXED)
     X = torch.zeros_like(V)
     hbm, peak_kind = peaks()

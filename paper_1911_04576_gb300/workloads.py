@@ -60,6 +60,10 @@ WORKLOADS = {
     # 16x16 lattice, K = 576, 32 patch types, one normal-incidence rhs
     "lattice16x16_k576": Workload("lattice16x16_k576", 16, 16, 4, 32, 0.15, 0.45, 1, 4, 16,
                                   angles=normal_incidence()),
+    # 12x12 lattice, K = 576: the bin multiply of the 16x16 case on a smaller
+    # grid (576 bins, 0.76 GB of complex64 blocks > L2) for profiler captures
+    "lattice12x12_k576": Workload("lattice12x12_k576", 12, 12, 4, 32, 0.15, 0.45, 1, 4, 12,
+                                  angles=normal_incidence()),
     # 48x48 lattice, K = 576, 32 types, 32 plane waves
     "lattice48x48_k576_r32": Workload(
         "lattice48x48_k576_r32", 48, 48, 4, 32, 0.15, 0.45, 32, 4, 48,
