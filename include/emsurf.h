@@ -213,6 +213,33 @@ EMSURF_API int emsurf_tabulate(const double* test_verts, const int32_t* test_tri
                                const double* shifts, const int8_t* singular, int32_t n_blocks,
                                double k, emsurf_c128* L, emsurf_c128* K, void* stream);
 
+/* emsurf_tabulate for callers that must not allocate device memory.  The
+ * paper has no counterpart; this exists for hosts that cannot call
+ * cudaMalloc at this point -- for example a plugin inside another
+ * application's memory pool, a process under a fixed device-memory quota,
+ * or code running while its host holds an allocator lock.  Same arguments,
+ * same results as emsurf_tabulate; the caller still provides L and K.  It
+ * makes no cudaMalloc/cudaFree or other allocating call: its scratch is one
+ * static 64 MiB device array per GPU, which every GPU that loads the library
+ * keeps until the process exits.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress) with the device current;
+ * make that first call before any stream capture.  Meshes whose per-block
+ * triangle-pair scratch (test_T * src_T * 288 bytes) plus geometry exceeds
+ * the array are rejected with EMSURF_EINVAL and a message giving the bytes
+ * needed.  All calls share the array and it keeps the previous call's
+ * contents (every value is written before it is read, so nothing is
+ * cleared); calls that overlap on the GPU -- from two host threads or two
+ * streams -- race on it and must be serialised by the caller.  Synchronises
+ * `stream`.                                                               */
+EMSURF_API int emsurf_tabulate_noalloc(const double* test_verts, const int32_t* test_tris,
+                                       const int32_t* test_slot_rwg, const int8_t* test_slot_sgn,
+                                       int32_t test_T, int32_t test_E, const double* src_verts,
+                                       const int32_t* src_tris, const int32_t* src_slot_rwg,
+                                       const int8_t* src_slot_sgn, int32_t src_T, int32_t src_E,
+                                       const double* shifts, const int8_t* singular,
+                                       int32_t n_blocks, double k, emsurf_c128* L, emsurf_c128* K,
+                                       void* stream);
+
 /* Offset tables of an nx x ny lattice of boxes (period a, b; height h; n x n
  * per face): L, K device [2ny-1][2nx-1][E][E] indexed [dy+ny-1][dx+nx-1],
  * d = test cell - source cell; closed-form singular parts for touching

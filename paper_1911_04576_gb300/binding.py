@@ -83,6 +83,7 @@ def lib():
         L.emsurf_launch_count.argtypes = [vp, C.POINTER(C.c_int64)]
         L.emsurf_tabulate.argtypes = [vp, vp, vp, vp, i32, i32, vp, vp, vp, vp, i32, i32, vp, vp,
                                       i32, d, vp, vp, vp]
+        L.emsurf_tabulate_noalloc.argtypes = L.emsurf_tabulate.argtypes
         L.emsurf_tabulate_offsets.argtypes = [d, d, d, i32, i32, i32, d, vp, vp, vp]
         L.emsurf_macromodel_pec_patch.argtypes = [d, d, d, i32, i32, vp, d, i32, d, vp, vp]
         L.emsurf_excitation.argtypes = [vp, d, d, d, i32, d, i32, vp, vp, vp, vp]
@@ -248,6 +249,20 @@ def emsurf_tabulate(test, src, shifts, singular, k, L, K, stream=None):
                                  *[_ptr(v) for v in s], len(src["tris"]), len(src["tplus"]),
                                  _ptr(shifts), _ptr(singular), len(singular), k, _ptr(L), _ptr(K),
                                  _stream(stream)))
+
+
+def emsurf_tabulate_noalloc(test, src, shifts, singular, k, L, K, stream=None):
+    """emsurf_tabulate_noalloc: as emsurf_tabulate, for callers that cannot
+    allocate device memory; its scratch is the library's static per-GPU array."""
+    shifts = np.ascontiguousarray(shifts, dtype=np.float64)
+    singular = np.ascontiguousarray(singular, dtype=np.int8)
+    m = [test[x] for x in ("verts", "tris", "slot_rwg", "slot_sgn")]
+    s = [src[x] for x in ("verts", "tris", "slot_rwg", "slot_sgn")]
+    _check(lib().emsurf_tabulate_noalloc(*[_ptr(v) for v in m], len(test["tris"]),
+                                         len(test["tplus"]), *[_ptr(v) for v in s],
+                                         len(src["tris"]), len(src["tplus"]), _ptr(shifts),
+                                         _ptr(singular), len(singular), k, _ptr(L), _ptr(K),
+                                         _stream(stream)))
 
 
 def emsurf_tabulate_offsets(a, b, h, n, nx, ny, k, L, K, stream=None):

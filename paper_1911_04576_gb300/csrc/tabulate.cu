@@ -20,6 +20,7 @@
 // Blocks are processed in chunks so the scratch stays below 256 MB.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -384,11 +385,131 @@ int tabulate_blocks(const MeshView& test, const MeshView& src, const double* shi
     return status;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free tabulation.  Scratch lives in one file-scope device array
+// that every GPU loading this library holds until the process exits.  Host
+// code must not use the array's name as a device address (it is a host-side
+// stand-in); the device address comes from cudaGetSymbolAddress, taken once
+// per device with that device current and cached.
+namespace {
+
+constexpr size_t kNoAllocBytes = 64ull << 20;   // 64 MiB per device
+static __device__ __align__(256) unsigned char g_tab_scratch[kNoAllocBytes];
+
+std::mutex g_tab_scratch_mu;
+constexpr int kMaxDevices = 64;
+void* g_tab_scratch_addr[kMaxDevices] = {nullptr};
+
+int scratch_address(void** out) {
+    int dev = -1;
+    EMS_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_error("device ordinal %d outside [0, %d)", dev, kMaxDevices);
+        return EMSURF_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(g_tab_scratch_mu);
+    if (!g_tab_scratch_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_tab_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error("cudaGetSymbolAddress of the static scratch failed on device %d: %s", dev,
+                      cudaGetErrorString(e));
+            return EMSURF_ECUDA;
+        }
+        g_tab_scratch_addr[dev] = p;
+    }
+    *out = g_tab_scratch_addr[dev];
+    return EMSURF_OK;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+int tabulate_blocks_noalloc(const MeshView& test, const MeshView& src, const double* shifts,
+                            const int8_t* singular, int nb, double k, double2* L, double2* K,
+                            cudaStream_t st) {
+    if (!(k > 0.0) || nb < 1) { set_error("tabulate needs k > 0 and >= 1 block"); return EMSURF_EINVAL; }
+    std::vector<TriGeo> tg, sgeo;
+    std::vector<RwgSlots> tr, sr;
+    EMS_TRY(prepare_mesh(test.verts, test.tris, test.slot_rwg, test.slot_sgn, test.T, test.E, tg, tr));
+    EMS_TRY(prepare_mesh(src.verts, src.tris, src.slot_rwg, src.slot_sgn, src.T, src.E, sgeo, sr));
+    // carve the static array: geometry, then the per-chunk pair integrals
+    const size_t o_tg = 0;
+    const size_t o_sg = o_tg + align256(sizeof(TriGeo) * tg.size());
+    const size_t o_tr = o_sg + align256(sizeof(TriGeo) * sgeo.size());
+    const size_t o_sr = o_tr + align256(sizeof(RwgSlots) * tr.size());
+    const size_t o_sh = o_sr + align256(sizeof(RwgSlots) * sr.size());
+    const size_t o_si = o_sh + align256(sizeof(double) * 3 * (size_t)nb);
+    const size_t o_pairs = o_si + align256((size_t)nb);
+    const size_t per_block = (size_t)test.T * src.T * 18 * sizeof(double2);
+    if (o_pairs + per_block > kNoAllocBytes) {
+        set_error("emsurf_tabulate_noalloc needs %zu bytes of scratch for these meshes and %d "
+                  "blocks; its static scratch holds %zu bytes",
+                  o_pairs + per_block, nb, kNoAllocBytes);
+        return EMSURF_EINVAL;
+    }
+    void* base = nullptr;
+    EMS_TRY(scratch_address(&base));
+    unsigned char* b = static_cast<unsigned char*>(base);
+    TriGeo* dtg = reinterpret_cast<TriGeo*>(b + o_tg);
+    TriGeo* dsg = reinterpret_cast<TriGeo*>(b + o_sg);
+    RwgSlots* dtr = reinterpret_cast<RwgSlots*>(b + o_tr);
+    RwgSlots* dsr = reinterpret_cast<RwgSlots*>(b + o_sr);
+    double* dsh = reinterpret_cast<double*>(b + o_sh);
+    int8_t* dsi = reinterpret_cast<int8_t*>(b + o_si);
+    double2* pairs = reinterpret_cast<double2*>(b + o_pairs);
+    const int chunk = (int)std::min<size_t>(nb, (kNoAllocBytes - o_pairs) / per_block);
+    double bary[7][3], w[7];
+    radon7(bary, w);
+    EMS_CUDA(cudaMemcpyToSymbolAsync(c_w, w, sizeof(w), 0, cudaMemcpyHostToDevice, st));
+    EMS_CUDA(cudaMemcpyAsync(dtg, tg.data(), sizeof(TriGeo) * tg.size(), cudaMemcpyHostToDevice, st));
+    EMS_CUDA(cudaMemcpyAsync(dsg, sgeo.data(), sizeof(TriGeo) * sgeo.size(), cudaMemcpyHostToDevice, st));
+    EMS_CUDA(cudaMemcpyAsync(dtr, tr.data(), sizeof(RwgSlots) * tr.size(), cudaMemcpyHostToDevice, st));
+    EMS_CUDA(cudaMemcpyAsync(dsr, sr.data(), sizeof(RwgSlots) * sr.size(), cudaMemcpyHostToDevice, st));
+    EMS_CUDA(cudaMemcpyAsync(dsh, shifts, sizeof(double) * 3 * nb, cudaMemcpyHostToDevice, st));
+    EMS_CUDA(cudaMemcpyAsync(dsi, singular, nb, cudaMemcpyHostToDevice, st));
+    // every pair integral is written before it is read, so nothing needs clearing
+    for (int b0 = 0; b0 < nb; b0 += chunk) {
+        const int nc = std::min(chunk, nb - b0);
+        dim3 g1((src.T + 127) / 128, test.T, nc);
+        tri_pairs_kernel<<<g1, 128, 0, st>>>(dtg, test.T, dsg, src.T, dsh, dsi, b0, k, pairs);
+        EMS_CUDA(cudaGetLastError());
+        const size_t tot = (size_t)nc * test.E * src.E;
+        const int g2 = (int)std::min<size_t>((tot + 255) / 256, 152 * 64);
+        rwg_gather_kernel<<<g2, 256, 0, st>>>(pairs, dtr, test.E, dsr, src.E, test.T, src.T, b0, nc,
+                                              L, K);
+        EMS_CUDA(cudaGetLastError());
+    }
+    EMS_CUDA(cudaStreamSynchronize(st));
+    return EMSURF_OK;
+}
+
+}  // namespace
+
 }  // namespace emsurf
 
 using namespace emsurf;
 
 extern "C" {
+
+EMSURF_API int emsurf_tabulate_noalloc(const double* test_verts, const int32_t* test_tris,
+                                       const int32_t* test_slot_rwg, const int8_t* test_slot_sgn,
+                                       int32_t test_T, int32_t test_E, const double* src_verts,
+                                       const int32_t* src_tris, const int32_t* src_slot_rwg,
+                                       const int8_t* src_slot_sgn, int32_t src_T, int32_t src_E,
+                                       const double* shifts, const int8_t* singular,
+                                       int32_t n_blocks, double k, emsurf_c128* L, emsurf_c128* K,
+                                       void* stream) {
+    if (!test_verts || !test_tris || !test_slot_rwg || !test_slot_sgn || !src_verts || !src_tris ||
+        !src_slot_rwg || !src_slot_sgn || !shifts || !singular || !L || !K || test_T < 1 ||
+        src_T < 1 || test_E < 1 || src_E < 1) {
+        set_error("emsurf_tabulate_noalloc: NULL pointer or empty mesh");
+        return EMSURF_EINVAL;
+    }
+    MeshView t{test_verts, test_tris, test_slot_rwg, test_slot_sgn, test_T, test_E};
+    MeshView s{src_verts, src_tris, src_slot_rwg, src_slot_sgn, src_T, src_E};
+    return tabulate_blocks_noalloc(t, s, shifts, singular, n_blocks, k, reinterpret_cast<double2*>(L),
+                                   reinterpret_cast<double2*>(K), reinterpret_cast<cudaStream_t>(stream));
+}
 
 EMSURF_API int emsurf_tabulate(const double* test_verts, const int32_t* test_tris,
                                const int32_t* test_slot_rwg, const int8_t* test_slot_sgn,
