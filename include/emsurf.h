@@ -150,6 +150,13 @@ EMSURF_API int emsurf_profile(emsurf_handle* h, int32_t enable);
 EMSURF_API int emsurf_profile_read(emsurf_handle* h, int32_t phase, double* total_ms,
                                    int64_t* count);
 
+/* Synchronise the handle's device and report whether any bounded device
+ * wait of this handle's kernels expired since the last check
+ * (EMSURF_ETIMEDOUT, flag cleared) -- the kernels give up instead of
+ * hanging, so the context stays usable.  emsurf_solve does the same check
+ * before it returns.                                                      */
+EMSURF_API int emsurf_check(emsurf_handle* h);
+
 /* Number of CUDA kernels this handle has launched since creation.        */
 EMSURF_API int emsurf_launch_count(const emsurf_handle* h, int64_t* launches);
 

@@ -81,6 +81,7 @@ def lib():
         L.emsurf_profile.argtypes = [vp, i32]
         L.emsurf_profile_read.argtypes = [vp, i32, C.POINTER(d), C.POINTER(C.c_int64)]
         L.emsurf_launch_count.argtypes = [vp, C.POINTER(C.c_int64)]
+        L.emsurf_check.argtypes = [vp]
         L.emsurf_tabulate.argtypes = [vp, vp, vp, vp, i32, i32, vp, vp, vp, vp, i32, i32, vp, vp,
                                       i32, d, vp, vp, vp]
         L.emsurf_tabulate_noalloc.argtypes = L.emsurf_tabulate.argtypes
@@ -312,3 +313,8 @@ def emsurf_launch_count(h):
     n = C.c_int64()
     _check(lib().emsurf_launch_count(h.ptr, C.byref(n)))
     return n.value
+
+
+def emsurf_check(h):
+    """emsurf_check: raises EmsurfError(ETIMEDOUT) if a bounded device wait expired."""
+    _check(lib().emsurf_check(h.ptr))

@@ -120,6 +120,9 @@ int create_impl(const emsurf_problem* p, emsurf_handle* h) {
     h->px = p->grid_px ? p->grid_px : smallest_smooth_at_least(2 * p->nx - 1);
     h->py = p->grid_py ? p->grid_py : smallest_smooth_at_least(2 * p->ny - 1);
     h->nbins = h->px * h->py;
+    EMS_CUDA(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+    EMS_TRY(dev_alloc(h, (void**)&h->d_err, sizeof(int)));
+    EMS_CUDA(cudaMemset(h->d_err, 0, sizeof(int)));
     EMS_TRY(fft_plan_create(h->plan_x, h->px));
     EMS_TRY(fft_plan_create(h->plan_y, h->py));
     const int M = h->M, K = h->K;
@@ -146,7 +149,7 @@ int create_impl(const emsurf_problem* p, emsurf_handle* h) {
     EMS_TRY(upload(h, &h->d_inv_ptr, ptr.data(), ptr.size()));
     EMS_TRY(upload(h, &h->d_inv_ent, ent.data(), MK));
     EMS_TRY(upload(h, &h->d_inv_sgn, esg.data(), MK));
-    // cells grouped by type; macromodel work list in groups of 4 cells
+    // cells grouped by type; macromodel work list in groups of 8 cells
     std::vector<int32_t> tptr(h->T + 1, 0), cells(M);
     for (int m = 0; m < M; ++m) tptr[p->type_map[m] + 1]++;
     for (int t = 0; t < h->T; ++t) tptr[t + 1] += tptr[t];
@@ -156,10 +159,10 @@ int create_impl(const emsurf_problem* p, emsurf_handle* h) {
     }
     std::vector<int32_t> blocks;
     for (int t = 0; t < h->T; ++t)
-        for (int s = tptr[t]; s < tptr[t + 1]; s += 4) {
+        for (int s = tptr[t]; s < tptr[t + 1]; s += kMmGroup) {
             blocks.push_back(t);
             blocks.push_back(s);
-            blocks.push_back(std::min(4, tptr[t + 1] - s));
+            blocks.push_back(std::min(kMmGroup, tptr[t + 1] - s));
         }
     h->h_type_ptr = tptr;
     h->n_mm_blocks = (int)(blocks.size() / 3);
@@ -335,6 +338,20 @@ EMSURF_API int emsurf_profile_read(emsurf_handle* h, int32_t phase, double* tota
     }
     if (total_ms) *total_ms = ms;
     if (count) *count = (int64_t)(pt.used / 2);
+    return EMSURF_OK;
+}
+
+EMSURF_API int emsurf_check(emsurf_handle* h) {
+    if (!h) { set_error("NULL handle"); return EMSURF_EINVAL; }
+    DeviceGuard dg(h->device);
+    EMS_CUDA(cudaDeviceSynchronize());
+    int flag = 0;
+    EMS_CUDA(cudaMemcpy(&flag, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        EMS_CUDA(cudaMemset(h->d_err, 0, sizeof(int)));
+        set_error("a bounded device wait expired (flag %d); results of the affected calls are invalid", flag);
+        return EMSURF_ETIMEDOUT;
+    }
     return EMSURF_OK;
 }
 

@@ -11,6 +11,8 @@
 
 namespace emsurf {
 
+constexpr int kMmGroup = 8;   // cells of one type per macromodel CTA
+
 // ---------------------------------------------------------------- errors
 void set_error(const char* fmt, ...);
 
@@ -84,10 +86,19 @@ void fft_plan_destroy(FftPlan& plan);
 
 // In-place 1-D transform along p of data[outer][P][inner] (inner contiguous
 // lanes, outer stride outer_stride elements).  sign = -1 forward, +1 inverse
-// (unscaled).
+// (unscaled).  Only points p < p_in are read (the rest are zero) and only
+// p < p_out are written; -1 means P.
 template <typename T2>
 int fft_pass(T2* data, const FftPlan& plan, long long inner, long long outer,
-             long long outer_stride, int sign, cudaStream_t st);
+             long long outer_stride, int sign, cudaStream_t st, int p_in = -1, int p_out = -1);
+
+// Forward pass over the cell rows whose input is read through U_o from the
+// unique-unknown vector x ([R][n_unique]); lane L = r*K + k, row iy = outer
+// index, point ix < p_in = nx.
+template <typename T2>
+int fft_pass_gather(T2* data, const FftPlan& plan, long long inner, long long outer,
+                    long long outer_stride, int p_in, const double2* x, const int32_t* idx,
+                    const int8_t* sgn, int nx, int K, int n_unique, cudaStream_t st);
 
 int smallest_smooth_at_least(int n);   // smallest 2^a 3^b 5^c >= n
 
@@ -138,6 +149,8 @@ struct emsurf_handle {
     emsurf::Operator<double2> op64;
     emsurf::Operator<float2> op32;
     bool have64 = false, have32 = false;
+    int num_sms = 0;
+    int* d_err = nullptr;             // device error flag of bounded waits (0 = ok)
     // GMRES workspace (FP64), allocated lazily by emsurf_solve
     void* gm = nullptr;
     // tracing: kernel launches issued by this handle, optional phase timers

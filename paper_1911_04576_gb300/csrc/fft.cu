@@ -8,7 +8,17 @@
 // that sit next to each other in memory, so one CTA loads a P x W tile whose
 // rows are W contiguous lanes (coalesced), transforms all W lanes in shared
 // memory with a Stockham autosort mixed-radix algorithm (radices 2,3,4,5,7;
-// Govindaraju et al., SC 2008), and writes the tile back in place.
+// Govindaraju et al., SC 2008), and writes the tile back.
+//
+// Pruning: only the first p_in points along P are read (the rest are the
+// zero padding of the circulant embedding) and only the first p_out are
+// written (the crop of the inverse transform).  The forward pass over the
+// cell rows can read its input straight from the unique-unknown vector
+// through U_o (x1 = U_o x, Eq. MVP), so no padded grid is ever written.
+//
+// Grid sizes used by the lattices here have compile-time kernels (radices,
+// strides and twiddle indices are constants, twiddles sit in shared memory);
+// any other 2,3,5,7-smooth size runs a generic kernel.
 #include <cmath>
 
 #include "common.cuh"
@@ -17,13 +27,157 @@ namespace emsurf {
 
 namespace {
 
+constexpr int kFftThreads = 256;
+constexpr int kMaxRadix = 7;
+
+// ---------------------------------------------------------------- radices
+constexpr int rad_count(int P) {
+    int n = 0;
+    const int qs[5] = {4, 2, 3, 5, 7};
+    for (int i = 0; i < 5; ++i)
+        while (P % qs[i] == 0 && P > 1) {
+            P /= qs[i];
+            ++n;
+        }
+    return n;
+}
+constexpr int rad_at(int P, int s) {
+    int n = 0;
+    const int qs[5] = {4, 2, 3, 5, 7};
+    for (int i = 0; i < 5; ++i)
+        while (P % qs[i] == 0 && P > 1) {
+            if (n == s) return qs[i];
+            P /= qs[i];
+            ++n;
+        }
+    return 1;
+}
+
+template <typename T2>
+__device__ __forceinline__ T2 mul_i(T2 a, int s) {   // a * (s i), s = +-1
+    T2 r;
+    r.x = -s * a.y;
+    r.y = s * a.x;
+    return r;
+}
+template <typename T2>
+__device__ __forceinline__ T2 csub2(T2 a, T2 b) {
+    T2 r;
+    r.x = a.x - b.x;
+    r.y = a.y - b.y;
+    return r;
+}
+
+// One Stockham stage of radix R (compile time) over all W lanes.
+template <typename T2, int W, int P, int R, int NS, int SIGN>
+__device__ __forceinline__ void stage(const T2* __restrict__ in, T2* __restrict__ out,
+                                      const T2* __restrict__ tw) {
+    constexpr int NR = P / R;
+    constexpr int tstep = P / (NS * R);
+    constexpr int qstep = P / R;
+    for (int e = threadIdx.x; e < NR * W; e += blockDim.x) {
+        const int j = e / W, l = e % W;
+        const int jm = j % NS;
+        T2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const T2 a = in[(j + r * NR) * W + l];
+            v[r] = (r == 0 || NS == 1) ? a : cmul(a, tw[jm * r * tstep]);
+        }
+        const int idxD = (j / NS) * NS * R + jm;
+        if constexpr (R == 2) {
+            out[idxD * W + l] = cadd(v[0], v[1]);
+            out[(idxD + NS) * W + l] = csub2(v[0], v[1]);
+        } else if constexpr (R == 4) {
+            // w_4 = e^{SIGN 2 pi i / 4} = SIGN i
+            const T2 s02 = cadd(v[0], v[2]), d02 = csub2(v[0], v[2]);
+            const T2 s13 = cadd(v[1], v[3]), d13 = csub2(v[1], v[3]);
+            out[idxD * W + l] = cadd(s02, s13);
+            out[(idxD + NS) * W + l] = cadd(d02, mul_i(d13, SIGN));
+            out[(idxD + 2 * NS) * W + l] = csub2(s02, s13);
+            out[(idxD + 3 * NS) * W + l] = csub2(d02, mul_i(d13, SIGN));
+        } else {
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                T2 acc = v[0];
+#pragma unroll
+                for (int r = 1; r < R; ++r) acc = cadd(acc, cmul(v[r], tw[((q * r) % R) * qstep]));
+                out[(idxD + q * NS) * W + l] = acc;
+            }
+        }
+    }
+}
+
+template <typename T2, int W, int P, int S, int NS, int SIGN>
+struct Stages {
+    // returns the buffer holding the result
+    static __device__ __forceinline__ T2* run(T2* in, T2* out, const T2* tw) {
+        if constexpr (S < rad_count(P)) {
+            constexpr int R = rad_at(P, S);
+            stage<T2, W, P, R, NS, SIGN>(in, out, tw);
+            __syncthreads();
+            return Stages<T2, W, P, S + 1, NS * R, SIGN>::run(out, in, tw);
+        } else {
+            return in;
+        }
+    }
+};
+
+// Gather source of the forward pass over cell rows: element (row iy, point
+// ix, lane L = r*K + k) = sign * x[r][uo_index[(iy*nx + ix)*K + k]].
+struct GatherSrc {
+    const double2* x;
+    const int32_t* idx;
+    const int8_t* sgn;
+    int nx, K, n_unique;
+};
+
+template <typename T2, int W, int P, int SIGN, bool GATHER>
+__global__ void __launch_bounds__(kFftThreads)
+fft_fixed_kernel(T2* __restrict__ data, long long inner, long long outer_stride, int p_in, int p_out,
+                 const double2* __restrict__ twg, GatherSrc gs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2* buf0 = reinterpret_cast<T2*>(smem_raw);
+    T2* buf1 = buf0 + P * W;
+    T2* tw = buf1 + P * W;
+    for (int e = threadIdx.x; e < P; e += blockDim.x) {
+        const double2 w = twg[e];
+        tw[e] = mk<T2>(w.x, SIGN < 0 ? w.y : -w.y);
+    }
+    const long long lane0 = (long long)blockIdx.x * W;
+    const int wl = (int)min((long long)W, inner - lane0);
+    T2* base = data + (long long)blockIdx.y * outer_stride + lane0;
+    const T2 zero = mk<T2>(0.0, 0.0);
+    for (int e = threadIdx.x; e < P * W; e += blockDim.x) {
+        const int p = e / W, l = e % W;
+        T2 v = zero;
+        if (l < wl && p < p_in) {
+            if constexpr (GATHER) {
+                const long long L = lane0 + l;
+                const int r = (int)(L / gs.K), k = (int)(L % gs.K);
+                const size_t loc = ((size_t)blockIdx.y * gs.nx + p) * gs.K + k;
+                const double2 xv = gs.x[(size_t)r * gs.n_unique + gs.idx[loc]];
+                const double s = (double)gs.sgn[loc];
+                v = mk<T2>(s * xv.x, s * xv.y);
+            } else {
+                v = base[(long long)p * inner + l];
+            }
+        }
+        buf0[e] = v;
+    }
+    __syncthreads();
+    const T2* res = Stages<T2, W, P, 0, 1, SIGN>::run(buf0, buf1, tw);
+    for (int e = threadIdx.x; e < p_out * W; e += blockDim.x) {
+        const int p = e / W, l = e % W;
+        if (l < wl) base[(long long)p * inner + l] = res[e];
+    }
+}
+
+// ---------------------------------------------------------------- generic
 struct RadList {
     int n;
     int r[16];
 };
-
-constexpr int kFftThreads = 256;
-constexpr int kMaxRadix = 7;
 
 template <typename T2>
 __device__ __forceinline__ T2 tw_at(const double2* __restrict__ tw, int k, int sign) {
@@ -33,8 +187,9 @@ __device__ __forceinline__ T2 tw_at(const double2* __restrict__ tw, int k, int s
 
 template <typename T2, int W>
 __global__ void __launch_bounds__(kFftThreads)
-fft_pass_kernel(T2* __restrict__ data, int P, long long inner, long long outer_stride,
-                const double2* __restrict__ tw, RadList rad, int sign) {
+fft_pass_kernel(T2* __restrict__ data, int P, long long inner, long long outer_stride, int p_in,
+                int p_out, const double2* __restrict__ tw, RadList rad, int sign, GatherSrc gs,
+                int gather) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T2* buf0 = reinterpret_cast<T2*>(smem_raw);
     T2* buf1 = buf0 + (size_t)P * W;
@@ -45,7 +200,20 @@ fft_pass_kernel(T2* __restrict__ data, int P, long long inner, long long outer_s
 
     for (int e = threadIdx.x; e < P * W; e += blockDim.x) {
         const int p = e / W, l = e - (e / W) * W;
-        buf0[e] = (l < wl) ? base[(long long)p * inner + l] : zero;
+        T2 v = zero;
+        if (l < wl && p < p_in) {
+            if (gather) {
+                const long long L = lane0 + l;
+                const int r = (int)(L / gs.K), k = (int)(L % gs.K);
+                const size_t loc = ((size_t)blockIdx.y * gs.nx + p) * gs.K + k;
+                const double2 xv = gs.x[(size_t)r * gs.n_unique + gs.idx[loc]];
+                const double s = (double)gs.sgn[loc];
+                v = mk<T2>(s * xv.x, s * xv.y);
+            } else {
+                v = base[(long long)p * inner + l];
+            }
+        }
+        buf0[e] = v;
     }
     __syncthreads();
 
@@ -65,7 +233,7 @@ fft_pass_kernel(T2* __restrict__ data, int P, long long inner, long long outer_s
             for (int r = 0; r < kMaxRadix; ++r) {
                 if (r < R) {
                     T2 a = in[(j + r * NR) * W + l];
-                    v[r] = (r == 0 || jm == 0) ? a : cmul(a, tw_at<T2>(tw, (jm * r * tstep) % P, sign));
+                    v[r] = (r == 0 || jm == 0) ? a : cmul(a, tw_at<T2>(tw, jm * r * tstep, sign));
                 }
             }
             const int idxD = (j / Ns) * Ns * R + jm;
@@ -88,15 +256,37 @@ fft_pass_kernel(T2* __restrict__ data, int P, long long inner, long long outer_s
         __syncthreads();
     }
 
-    for (int e = threadIdx.x; e < P * W; e += blockDim.x) {
+    for (int e = threadIdx.x; e < p_out * W; e += blockDim.x) {
         const int p = e / W, l = e - (e / W) * W;
         if (l < wl) base[(long long)p * inner + l] = in[e];
     }
 }
 
+// lanes per CTA: the largest of 32, 16, 8 whose two buffers fit in 96 KB
+template <typename T2>
+constexpr int lanes_for(int P) {
+    return (2 * P * 32 * (int)sizeof(T2) <= 96 * 1024) ? 32
+         : (2 * P * 16 * (int)sizeof(T2) <= 96 * 1024) ? 16 : 8;
+}
+
+template <typename T2, int P, int SIGN, bool GATHER>
+int launch_fixed(T2* data, const FftPlan& plan, long long inner, long long outer,
+                 long long outer_stride, int p_in, int p_out, const GatherSrc& gs, cudaStream_t st) {
+    constexpr int W = lanes_for<T2>(P);
+    const size_t smem = (2ull * P * W + P) * sizeof(T2);
+    auto kern = fft_fixed_kernel<T2, W, P, SIGN, GATHER>;
+    EMS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const long long gx = (inner + W - 1) / W;
+    dim3 grid((unsigned)gx, (unsigned)outer);
+    kern<<<grid, kFftThreads, smem, st>>>(data, inner, outer_stride, p_in, p_out, plan.tw, gs);
+    EMS_CUDA(cudaGetLastError());
+    return EMSURF_OK;
+}
+
 template <typename T2, int W>
-int launch_pass(T2* data, const FftPlan& plan, long long inner, long long outer,
-                long long outer_stride, int sign, cudaStream_t st) {
+int launch_generic(T2* data, const FftPlan& plan, long long inner, long long outer,
+                   long long outer_stride, int p_in, int p_out, int sign, const GatherSrc& gs,
+                   bool gather, cudaStream_t st) {
     RadList rl;
     rl.n = plan.nrad;
     for (int i = 0; i < 16; ++i) rl.r[i] = plan.rad[i];
@@ -104,15 +294,61 @@ int launch_pass(T2* data, const FftPlan& plan, long long inner, long long outer,
     EMS_CUDA(cudaFuncSetAttribute(fft_pass_kernel<T2, W>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const long long gx = (inner + W - 1) / W;
-    if (outer > 65535 || gx > 2147483647LL) {
+    dim3 grid((unsigned)gx, (unsigned)outer);
+    fft_pass_kernel<T2, W><<<grid, kFftThreads, smem, st>>>(data, plan.P, inner, outer_stride, p_in,
+                                                            p_out, plan.tw, rl, sign, gs, gather ? 1 : 0);
+    EMS_CUDA(cudaGetLastError());
+    return EMSURF_OK;
+}
+
+template <typename T2, int SIGN, bool GATHER>
+int dispatch_fixed(int P, T2* data, const FftPlan& plan, long long inner, long long outer,
+                   long long os, int p_in, int p_out, const GatherSrc& gs, cudaStream_t st,
+                   bool* done) {
+    *done = true;
+    switch (P) {
+        case 5: return launch_fixed<T2, 5, SIGN, GATHER>(data, plan, inner, outer, os, p_in, p_out, gs, st);
+        case 8: return launch_fixed<T2, 8, SIGN, GATHER>(data, plan, inner, outer, os, p_in, p_out, gs, st);
+        case 15: return launch_fixed<T2, 15, SIGN, GATHER>(data, plan, inner, outer, os, p_in, p_out, gs, st);
+        case 16: return launch_fixed<T2, 16, SIGN, GATHER>(data, plan, inner, outer, os, p_in, p_out, gs, st);
+        case 32: return launch_fixed<T2, 32, SIGN, GATHER>(data, plan, inner, outer, os, p_in, p_out, gs, st);
+        case 48: return launch_fixed<T2, 48, SIGN, GATHER>(data, plan, inner, outer, os, p_in, p_out, gs, st);
+        case 64: return launch_fixed<T2, 64, SIGN, GATHER>(data, plan, inner, outer, os, p_in, p_out, gs, st);
+        case 96: return launch_fixed<T2, 96, SIGN, GATHER>(data, plan, inner, outer, os, p_in, p_out, gs, st);
+        case 128: return launch_fixed<T2, 128, SIGN, GATHER>(data, plan, inner, outer, os, p_in, p_out, gs, st);
+        case 200: return launch_fixed<T2, 200, SIGN, GATHER>(data, plan, inner, outer, os, p_in, p_out, gs, st);
+        default: *done = false; return EMSURF_OK;
+    }
+}
+
+template <typename T2>
+int pass_impl(T2* data, const FftPlan& plan, long long inner, long long outer, long long outer_stride,
+              int sign, int p_in, int p_out, const GatherSrc& gs, bool gather, cudaStream_t st) {
+    if (outer <= 0 || inner <= 0) return EMSURF_OK;
+    if (outer > 65535 || (inner + 7) / 8 > 2147483647LL) {
         set_error("fft_pass: grid too large (outer %lld, lanes %lld)", outer, inner);
         return EMSURF_EINVAL;
     }
-    dim3 grid((unsigned)gx, (unsigned)outer);
-    fft_pass_kernel<T2, W><<<grid, kFftThreads, smem, st>>>(data, plan.P, inner, outer_stride,
-                                                            plan.tw, rl, sign);
-    EMS_CUDA(cudaGetLastError());
-    return EMSURF_OK;
+    p_in = p_in < 0 ? plan.P : std::min(p_in, plan.P);
+    p_out = p_out < 0 ? plan.P : std::min(p_out, plan.P);
+    bool done = false;
+    int s = EMSURF_OK;
+    if (sign < 0 && gather)
+        s = dispatch_fixed<T2, -1, true>(plan.P, data, plan, inner, outer, outer_stride, p_in, p_out, gs, st, &done);
+    else if (sign < 0)
+        s = dispatch_fixed<T2, -1, false>(plan.P, data, plan, inner, outer, outer_stride, p_in, p_out, gs, st, &done);
+    else if (!gather)
+        s = dispatch_fixed<T2, +1, false>(plan.P, data, plan, inner, outer, outer_stride, p_in, p_out, gs, st, &done);
+    if (s != EMSURF_OK || done) return s;
+    const size_t per_lane = 2ull * plan.P * sizeof(T2);
+    if (per_lane * 32 <= 200 * 1024)
+        return launch_generic<T2, 32>(data, plan, inner, outer, outer_stride, p_in, p_out, sign, gs, gather, st);
+    if (per_lane * 16 <= 200 * 1024)
+        return launch_generic<T2, 16>(data, plan, inner, outer, outer_stride, p_in, p_out, sign, gs, gather, st);
+    if (per_lane * 8 <= 200 * 1024)
+        return launch_generic<T2, 8>(data, plan, inner, outer, outer_stride, p_in, p_out, sign, gs, gather, st);
+    set_error("FFT length %d too large for one shared-memory pass", plan.P);
+    return EMSURF_EINVAL;
 }
 
 }  // namespace
@@ -164,22 +400,28 @@ void fft_plan_destroy(FftPlan& plan) {
 
 template <typename T2>
 int fft_pass(T2* data, const FftPlan& plan, long long inner, long long outer,
-             long long outer_stride, int sign, cudaStream_t st) {
-    if (outer <= 0 || inner <= 0) return EMSURF_OK;
-    const size_t per_lane = 2ull * plan.P * sizeof(T2);
-    if (per_lane * 32 <= 200 * 1024)
-        return launch_pass<T2, 32>(data, plan, inner, outer, outer_stride, sign, st);
-    if (per_lane * 16 <= 200 * 1024)
-        return launch_pass<T2, 16>(data, plan, inner, outer, outer_stride, sign, st);
-    if (per_lane * 8 <= 200 * 1024)
-        return launch_pass<T2, 8>(data, plan, inner, outer, outer_stride, sign, st);
-    set_error("FFT length %d too large for one shared-memory pass", plan.P);
-    return EMSURF_EINVAL;
+             long long outer_stride, int sign, cudaStream_t st, int p_in, int p_out) {
+    GatherSrc gs{nullptr, nullptr, nullptr, 0, 1, 0};
+    return pass_impl<T2>(data, plan, inner, outer, outer_stride, sign, p_in, p_out, gs, false, st);
+}
+
+template <typename T2>
+int fft_pass_gather(T2* data, const FftPlan& plan, long long inner, long long outer,
+                    long long outer_stride, int p_in, const double2* x, const int32_t* idx,
+                    const int8_t* sgn, int nx, int K, int n_unique, cudaStream_t st) {
+    GatherSrc gs{x, idx, sgn, nx, K, n_unique};
+    return pass_impl<T2>(data, plan, inner, outer, outer_stride, -1, p_in, plan.P, gs, true, st);
 }
 
 template int fft_pass<double2>(double2*, const FftPlan&, long long, long long, long long, int,
-                               cudaStream_t);
+                               cudaStream_t, int, int);
 template int fft_pass<float2>(float2*, const FftPlan&, long long, long long, long long, int,
-                              cudaStream_t);
+                              cudaStream_t, int, int);
+template int fft_pass_gather<double2>(double2*, const FftPlan&, long long, long long, long long, int,
+                                      const double2*, const int32_t*, const int8_t*, int, int, int,
+                                      cudaStream_t);
+template int fft_pass_gather<float2>(float2*, const FftPlan&, long long, long long, long long, int,
+                                     const double2*, const int32_t*, const int8_t*, int, int, int,
+                                     cudaStream_t);
 
 }  // namespace emsurf

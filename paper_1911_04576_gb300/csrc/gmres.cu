@@ -491,6 +491,15 @@ int gmres_solve(emsurf_handle* h, const double2* b, double2* x, int R, const ems
     }
     EMS_CUDA(cudaStreamSynchronize(st));
     h->launches += g->launches - launches0;
+    {
+        int flag = 0;
+        EMS_CUDA(cudaMemcpy(&flag, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (flag) {
+            EMS_CUDA(cudaMemset(h->d_err, 0, sizeof(int)));
+            set_error("a bounded device wait expired during the solve");
+            return EMSURF_ETIMEDOUT;
+        }
+    }
     const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     bool all = true;
     for (int r = 0; r < R; ++r) {

@@ -14,12 +14,15 @@
 // EFIE/MFIE form).
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "common.cuh"
 
 namespace emsurf {
 
 namespace {
+
+constexpr int kMmSplit = 8;   // k' chunks of the macromodel product
 
 // ------------------------------------------------ placement of the tables
 // Bhat[bin(d)][op][j][i] = table_op(d)[i][j] for one chunk of offsets;
@@ -76,32 +79,6 @@ __global__ void round_kernel(float2* __restrict__ dst, const double2* __restrict
     }
 }
 
-// ------------------------------------------------ K1: gather + zero-pad
-// Xg[bin][r][k] = sign * x[r][uo_index[m*K+k]] for the bin (ix, iy) of cell
-// m = iy*nx + ix, zero on the padding bins.
-template <typename T2>
-__global__ void gather_pad_kernel(T2* __restrict__ Xg, const double2* __restrict__ x,
-                                  const int32_t* __restrict__ idx, const int8_t* __restrict__ sgn,
-                                  int nx, int ny, int px, int rows, int R, int K, int n_unique) {
-    const size_t total = (size_t)rows * px * R * K;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-         e += (size_t)gridDim.x * blockDim.x) {
-        const int k = (int)(e % K);
-        const size_t t = e / K;
-        const int r = (int)(t % R);
-        const size_t bin = t / R;
-        const int ix = (int)(bin % px), iy = (int)(bin / px);
-        T2 v = mk<T2>(0.0, 0.0);
-        if (ix < nx && iy < ny) {
-            const size_t loc = ((size_t)iy * nx + ix) * K + k;
-            const double2 xv = x[(size_t)r * n_unique + idx[loc]];
-            const double s = (double)sgn[loc];
-            v = mk<T2>(s * xv.x, s * xv.y);
-        }
-        Xg[e] = v;
-    }
-}
-
 // ------------------------------------------------ K2: bin multiply
 // Y^(k) = B^(k) X^(k) with B = [[a L, b K], [g K, d L]]:
 //   y_J = a L^ x_J + b K^ x_M,   y_M = g K^ x_J + d L^ x_M.
@@ -154,9 +131,162 @@ __global__ void binmul_kernel(const T2* __restrict__ Bhat, const T2* __restrict_
     }
 }
 
+// ------------------------------------------------ K2, FP32, one rhs: TMA-fed
+// Persistent CTAs walk their bins as a sequence of stages; a stage is a block
+// of JB source columns j of L^T and K^T (two contiguous JB x E slabs, since j
+// is the outer index), brought into a ring of kBmStages shared-memory slots
+// by 1-D bulk asynchronous copies (cp.async.bulk) signalled on mbarriers.
+// The first stage of a bin also brings X^(bin).  Warp 0 lane 0 issues the
+// copies; the other warps own one test row i each and release a slot with an
+// mbarrier arrive.  Every wait is bounded: on expiry the kernel sets *err,
+// the producer waits (bounded) for its copies in flight, and all return.
+constexpr int kBmJB = 8;
+constexpr int kBmStages = 4;
+constexpr long long kWaitLimit = 1LL << 22;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait; false on expiry
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (long long it = 0; it < kWaitLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__global__ void binmul_tma_kernel(const float2* __restrict__ Bhat, const float2* __restrict__ Xh,
+                                  float2* __restrict__ Yh, int E, int nbins, float2 ca, float2 cb,
+                                  float2 cg, float2 cd, int* __restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int stage_elems = 2 * kBmJB * E;
+    float2* sbuf = reinterpret_cast<float2*>(smem_raw);
+    float2* xbuf = sbuf + (size_t)kBmStages * stage_elems;      // [2][2E]
+    uint64_t* full = reinterpret_cast<uint64_t*>(xbuf + 4 * E);
+    uint64_t* empty = full + kBmStages;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ncw = (E + 31) / 32;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kBmStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], ncw);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    const int nloc = (nbins - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int nj = (E + kBmJB - 1) / kBmJB;
+    const long long total = (long long)nloc * nj;
+    if (warp == 0) {
+        if (lane != 0) return;
+        long long issued = 0;
+        bool ok = true;
+        for (long long q = 0; q < total; ++q) {
+            const int s = (int)(q % kBmStages);
+            if (q >= kBmStages && !mbar_wait(&empty[s], (uint32_t)((q / kBmStages - 1) & 1))) {
+                ok = false;
+                break;
+            }
+            const int t = (int)(q / nj), jb = (int)(q % nj);
+            const int bin = (int)blockIdx.x + t * (int)gridDim.x;
+            const int j0 = jb * kBmJB, jn = min(kBmJB, E - j0);
+            const uint32_t bytes_op = (uint32_t)(jn * E * sizeof(float2));
+            const uint32_t bytes_x = (uint32_t)(2 * E * sizeof(float2));
+            mbar_expect_tx(&full[s], 2 * bytes_op + (jb == 0 ? bytes_x : 0u));
+            const float2* src = Bhat + (size_t)bin * 2 * E * E + (size_t)j0 * E;
+            float2* dst = sbuf + (size_t)s * stage_elems;
+            bulk_g2s(dst, src, bytes_op, &full[s]);
+            bulk_g2s(dst + kBmJB * E, src + (size_t)E * E, bytes_op, &full[s]);
+            if (jb == 0) bulk_g2s(xbuf + (t & 1) * 2 * E, Xh + (size_t)bin * 2 * E, bytes_x, &full[s]);
+            issued = q + 1;
+        }
+        if (!ok) {
+            atomicExch(err, 1);
+            // wait (bounded) for the copies still in flight before leaving
+            for (long long q = (issued > kBmStages ? issued - kBmStages : 0); q < issued; ++q)
+                mbar_wait(&full[q % kBmStages], (uint32_t)((q / kBmStages) & 1));
+        }
+        return;
+    }
+    const int i = (warp - 1) * 32 + lane;
+    float2 lj = make_float2(0.f, 0.f), lm = lj, kj = lj, km = lj;
+    for (long long q = 0; q < total; ++q) {
+        const int s = (int)(q % kBmStages);
+        const int t = (int)(q / nj), jb = (int)(q % nj);
+        if (!mbar_wait(&full[s], (uint32_t)((q / kBmStages) & 1))) {
+            atomicExch(err, 1);
+            return;
+        }
+        if (jb == 0) lj = lm = kj = km = make_float2(0.f, 0.f);
+        const float2* Ls = sbuf + (size_t)s * stage_elems;
+        const float2* Ks = Ls + kBmJB * E;
+        const float2* xs = xbuf + (t & 1) * 2 * E;
+        const int j0 = jb * kBmJB, jn = min(kBmJB, E - j0);
+        if (i < E) {
+#pragma unroll
+            for (int jj = 0; jj < kBmJB; ++jj) {
+                if (jj < jn) {
+                    const float2 l = Ls[jj * E + i];
+                    const float2 k = Ks[jj * E + i];
+                    const float2 xj = xs[j0 + jj];
+                    const float2 xm = xs[E + j0 + jj];
+                    cfma(lj, l, xj);
+                    cfma(lm, l, xm);
+                    cfma(kj, k, xj);
+                    cfma(km, k, xm);
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+        if (jb == nj - 1 && i < E) {
+            const int bin = (int)blockIdx.x + t * (int)gridDim.x;
+            float2* Y = Yh + (size_t)bin * 2 * E;
+            Y[i] = cadd(cmul(ca, lj), cmul(cb, km));
+            Y[E + i] = cadd(cmul(cg, kj), cmul(cd, lm));
+        }
+    }
+}
+
+size_t binmul_tma_smem(int E) {
+    return (size_t)kBmStages * 2 * kBmJB * E * sizeof(float2) + 4ull * E * sizeof(float2) +
+           2ull * kBmStages * sizeof(uint64_t);
+}
+
 // ------------------------------------------------ K4: macromodel multiply
-// Ymm[r][m][k] = sum_k' Z~^{t(m)}[k][k'] x1[r][m][k'] for a group of up to
-// G cells of one type (x1 = U_o x gathered on the fly).
+// Ymm[s][r][m][k] = sum_{k' in chunk s} Z~^{t(m)}[k][k'] x1[r][m][k'] for a
+// group of up to G cells of one type (x1 = U_o x gathered on the fly).  The
+// k' range is split over gridDim.y chunks so the product of a few dozen
+// types fills the GPU; the crop/scatter kernel adds the chunk partials in a
+// fixed order (deterministic).
 struct MmBlock {
     int type, first, count;
 };
@@ -166,22 +296,24 @@ __global__ void macromodel_kernel(const T2* __restrict__ Zt, const double2* __re
                                   const int32_t* __restrict__ idx, const int8_t* __restrict__ sgn,
                                   const int32_t* __restrict__ type_cells,
                                   const MmBlock* __restrict__ blocks, T2* __restrict__ Ymm, int K,
-                                  int M, int R, int n_unique) {
+                                  int M, int R, int n_unique, int chunk) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T2* xs = reinterpret_cast<T2*>(smem_raw);   // [G][K] for one r
+    T2* xs = reinterpret_cast<T2*>(smem_raw);   // [G][chunk] for one r
     const MmBlock b = blocks[blockIdx.x];
+    const int s = blockIdx.y;
+    const int k0 = s * chunk, k1 = min(K, k0 + chunk), nk = k1 - k0;
     const T2 zero = mk<T2>(0.0, 0.0);
     const T2* Z = Zt + (size_t)b.type * K * K;
     for (int r = 0; r < R; ++r) {
         __syncthreads();
-        for (int e = threadIdx.x; e < G * K; e += blockDim.x) {
-            const int g = e / K, k = e - (e / K) * K;
+        for (int e = threadIdx.x; e < G * chunk; e += blockDim.x) {
+            const int g = e / chunk, kk = e - (e / chunk) * chunk;
             T2 v = zero;
-            if (g < b.count) {
-                const size_t loc = (size_t)type_cells[b.first + g] * K + k;
+            if (g < b.count && kk < nk) {
+                const size_t loc = (size_t)type_cells[b.first + g] * K + k0 + kk;
                 const double2 xv = x[(size_t)r * n_unique + idx[loc]];
-                const double s = (double)sgn[loc];
-                v = mk<T2>(s * xv.x, s * xv.y);
+                const double sg = (double)sgn[loc];
+                v = mk<T2>(sg * xv.x, sg * xv.y);
             }
             xs[e] = v;
         }
@@ -190,16 +322,16 @@ __global__ void macromodel_kernel(const T2* __restrict__ Zt, const double2* __re
             T2 acc[G];
 #pragma unroll
             for (int g = 0; g < G; ++g) acc[g] = zero;
-#pragma unroll 8
-            for (int kp = 0; kp < K; ++kp) {
-                const T2 z = __ldg(Z + (size_t)kp * K + k);
+#pragma unroll 4
+            for (int kk = 0; kk < nk; ++kk) {
+                const T2 z = __ldg(Z + (size_t)(k0 + kk) * K + k);
 #pragma unroll
-                for (int g = 0; g < G; ++g) cfma(acc[g], z, xs[g * K + kp]);
+                for (int g = 0; g < G; ++g) cfma(acc[g], z, xs[g * chunk + kk]);
             }
 #pragma unroll
             for (int g = 0; g < G; ++g)
                 if (g < b.count)
-                    Ymm[((size_t)r * M + type_cells[b.first + g]) * K + k] = acc[g];
+                    Ymm[(((size_t)s * R + r) * M + type_cells[b.first + g]) * K + k] = acc[g];
         }
     }
 }
@@ -212,7 +344,7 @@ __global__ void crop_scatter_kernel(double2* __restrict__ y, const T2* __restric
                                     const T2* __restrict__ Ymm, const int32_t* __restrict__ ptr,
                                     const int32_t* __restrict__ ent, const int8_t* __restrict__ esg,
                                     int nx, int px, int K, int M, int R, int n_unique,
-                                    double scale) {
+                                    double scale, int nsplit) {
     const size_t total = (size_t)R * n_unique;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
          e += (size_t)gridDim.x * blockDim.x) {
@@ -224,10 +356,15 @@ __global__ void crop_scatter_kernel(double2* __restrict__ y, const T2* __restric
             const int m = loc / K, k = loc - (loc / K) * K;
             const int ix = m % nx, iy = m / nx;
             const T2 g = Yg[(((size_t)iy * px + ix) * R + r) * K + k];
-            const T2 z = Ymm[((size_t)r * M + m) * K + k];
+            double zx = 0.0, zy = 0.0;
+            for (int sp = 0; sp < nsplit; ++sp) {
+                const T2 z = Ymm[(((size_t)sp * R + r) * M + m) * K + k];
+                zx += (double)z.x;
+                zy += (double)z.y;
+            }
             const double s = (double)esg[q];
-            ax += s * ((double)g.x * scale + (double)z.x);
-            ay += s * ((double)g.y * scale + (double)z.y);
+            ax += s * ((double)g.x * scale + zx);
+            ay += s * ((double)g.y * scale + zy);
         }
         y[e] = make_double2(ax, ay);
     }
@@ -327,7 +464,7 @@ int build_operator(emsurf_handle* h, Operator<T2>& op, const emsurf_problem* pr)
     const size_t grid_elems = nbins * (size_t)h->max_rhs * K;
     EMS_TRY(dev_alloc(h, (void**)&op.Xg, grid_elems * sizeof(T2)));
     EMS_TRY(dev_alloc(h, (void**)&op.Yg, grid_elems * sizeof(T2)));
-    EMS_TRY(dev_alloc(h, (void**)&op.Ymm, (size_t)h->max_rhs * h->M * K * sizeof(T2)));
+    EMS_TRY(dev_alloc(h, (void**)&op.Ymm, (size_t)kMmSplit * h->max_rhs * h->M * K * sizeof(T2)));
     for (int c = 0; c < 4; ++c) op.coef[c] = mk<T2>(pr->coef[c].re, pr->coef[c].im);
     return EMSURF_OK;
 }
@@ -343,17 +480,34 @@ int apply_operator(emsurf_handle* h, Operator<T2>& op, const double2* x, double2
     const int ph_bin = f64 ? EMS_PH_BINMUL64 : EMS_PH_BINMUL32;
     const int ph_mm = f64 ? EMS_PH_MM64 : EMS_PH_MM32;
     prof_mark(h, ph_fft, true, st);
-    // K1: gather rows iy < ny (rows beyond are zero and stay zero under the x-pass)
-    gather_pad_kernel<T2><<<grid_for((size_t)py * px * lanes, 256), 256, 0, st>>>(
-        op.Xg, x, h->d_uo_index, h->d_uo_sign, h->nx, h->ny, px, py, R, K, h->n_unique);
-    EMS_CUDA(cudaGetLastError());
-    EMS_TRY(fft_pass<T2>(op.Xg, h->plan_x, lanes, h->ny, (long long)px * lanes, -1, st));
-    EMS_TRY(fft_pass<T2>(op.Xg, h->plan_y, (long long)px * lanes, 1, 0, -1, st));
+    // K1: x-pass over the cell rows iy < ny reading x1 = U_o x directly
+    // (points ix >= nx are the zero padding), then the y-pass with rows
+    // iy >= ny taken as zero
+    EMS_TRY(fft_pass_gather<T2>(op.Xg, h->plan_x, lanes, h->ny, (long long)px * lanes, h->nx, x,
+                                h->d_uo_index, h->d_uo_sign, h->nx, K, h->n_unique, st));
+    EMS_TRY(fft_pass<T2>(op.Xg, h->plan_y, (long long)px * lanes, 1, 0, -1, st, h->ny, py));
     prof_mark(h, ph_fft, false, st);
     prof_mark(h, ph_bin, true, st);
     // K2
     const int threads = std::min(1024, ((E + 31) / 32) * 32);
     const int nb = h->nbins;
+    if constexpr (std::is_same<T2, float2>::value) {
+        const size_t smem = binmul_tma_smem(E);
+        // the x double buffer needs at least kBmStages stages per bin
+        if (R == 1 && smem <= 227 * 1024 && E + 32 <= 1024 && (E + kBmJB - 1) / kBmJB >= kBmStages) {
+            EMS_CUDA(cudaFuncSetAttribute(binmul_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+            const int grid = std::min(nb, std::max(1, h->num_sms));
+            binmul_tma_kernel<<<grid, 32 * (1 + (E + 31) / 32), smem, st>>>(
+                op.Bhat, op.Xg, op.Yg, E, nb, op.coef[0], op.coef[1], op.coef[2], op.coef[3], h->d_err);
+            EMS_CUDA(cudaGetLastError());
+            h->launches += 1;
+            prof_mark(h, ph_bin, false, st);
+            prof_mark(h, ph_fft, true, st);
+            goto inverse;
+        }
+    }
+    {
     int rb = 1;
     if (R >= 4) rb = 4;
     else if (R >= 2) rb = 2;
@@ -375,28 +529,32 @@ int apply_operator(emsurf_handle* h, Operator<T2>& op, const double2* x, double2
     }
     prof_mark(h, ph_bin, false, st);
     prof_mark(h, ph_fft, true, st);
+    }
+inverse:
     // K3: inverse y-pass on all columns, inverse x-pass on the rows kept
-    EMS_TRY(fft_pass<T2>(op.Yg, h->plan_y, (long long)px * lanes, 1, 0, +1, st));
-    EMS_TRY(fft_pass<T2>(op.Yg, h->plan_x, lanes, h->ny, (long long)px * lanes, +1, st));
+    EMS_TRY(fft_pass<T2>(op.Yg, h->plan_y, (long long)px * lanes, 1, 0, +1, st, py, h->ny));
+    EMS_TRY(fft_pass<T2>(op.Yg, h->plan_x, lanes, h->ny, (long long)px * lanes, +1, st, px, h->nx));
     prof_mark(h, ph_fft, false, st);
     prof_mark(h, ph_mm, true, st);
     // K4
+    const int nsplit = std::max(1, std::min(kMmSplit, K / 64));
     {
-        constexpr int G = 4;
         const int nblk = h->n_mm_blocks;
+        const int chunk = (K + nsplit - 1) / nsplit;
         const MmBlock* blocks = reinterpret_cast<const MmBlock*>(h->d_mm_blocks);
         const int mthreads = std::min(1024, ((K + 31) / 32) * 32);
-        macromodel_kernel<T2, G><<<nblk, mthreads, (size_t)G * K * sizeof(T2), st>>>(
+        macromodel_kernel<T2, kMmGroup><<<dim3(nblk, nsplit), mthreads,
+                                           (size_t)kMmGroup * chunk * sizeof(T2), st>>>(
             op.Zt, x, h->d_uo_index, h->d_uo_sign, h->d_type_cells, blocks, op.Ymm, K, h->M, R,
-            h->n_unique);
+            h->n_unique, chunk);
         EMS_CUDA(cudaGetLastError());
     }
     prof_mark(h, ph_mm, false, st);
     crop_scatter_kernel<T2><<<grid_for((size_t)R * h->n_unique, 256), 256, 0, st>>>(
         y, op.Yg, op.Ymm, h->d_inv_ptr, h->d_inv_ent, h->d_inv_sgn, h->nx, px, K, h->M, R,
-        h->n_unique, 1.0 / (double)h->nbins);
+        h->n_unique, 1.0 / (double)h->nbins, nsplit);
     EMS_CUDA(cudaGetLastError());
-    h->launches += 7;   // gather, 4 FFT passes, macromodel, crop/scatter
+    h->launches += 6;   // 4 FFT passes, macromodel, crop/scatter
     return EMSURF_OK;
 }
 

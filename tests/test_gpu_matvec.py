@@ -60,6 +60,7 @@ def test_matvec_parity_random_tables(emsurf_lib, n, nx, ny, R):
     for r in range(R):
         assert relerr(y64[r], yref[r]) <= TOL64
         assert relerr(y32[r], yref[r]) <= TOL32
+    B.emsurf_check(h)
     h.close()
 
 
@@ -101,6 +102,8 @@ def test_matvec_full_size_sampled(emsurf_lib):
     assert relerr(y32[rows], yref) <= TOL32
     # repeated calls are bit-identical (no atomics, fixed reduction order)
     assert np.array_equal(run_matvec(B, h, x, B.FP64)[0], y64)
+    assert np.array_equal(run_matvec(B, h, x, B.FP32)[0], y32)
+    B.emsurf_check(h)          # no bounded device wait expired
     h.close()
 
 
