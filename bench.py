@@ -220,6 +220,9 @@ def main():
                     help="profiler driver: build the workload, run this many products, exit")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32", "fp64"],
                     help="operators kept resident (--matvecs-only)")
+    ap.add_argument("--solve-iters", type=int, default=0,
+                    help="profiler driver: with --matvecs-only, also run one mixed solve capped "
+                         "at this many GMRES iterations")
     args = ap.parse_args()
     from paper_1911_04576_gb300 import workloads as W
     w = W.WORKLOADS[args.workload]
@@ -243,6 +246,10 @@ def main():
             y = torch.empty_like(x)
             for _ in range(args.matvecs_only):
                 B.emsurf_matvec(h, x, y, p)
+        if args.solve_iters and prec == B.MIXED:
+            X = torch.zeros_like(V)
+            B.emsurf_solve(h, V, X, rtol=RTOL, restart=RESTART, max_iters=args.solve_iters,
+                           max_refine=20, solver=B.SOLVER_MIXED)
         torch.cuda.synchronize()
         h.close()
         return
@@ -293,6 +300,10 @@ def main():
     mm_ms, mm_n = B.emsurf_profile_read(h, "mm32")
     fft_ms, fft_n = B.emsurf_profile_read(h, "fft32")
     bin64_ms, bin64_n = B.emsurf_profile_read(h, "binmul64")
+    arn_ms, _ = B.emsurf_profile_read(h, "arnoldi")
+    sct_ms, _ = B.emsurf_profile_read(h, "scatter")
+    fft64_ms, _ = B.emsurf_profile_read(h, "fft64")
+    mm64_ms, _ = B.emsurf_profile_read(h, "mm64")
     ms = ms_total / args.steps
     if dist:
         t = torch.tensor([ms], device="cuda")
@@ -358,7 +369,10 @@ def main():
         "phases_ms_per_solve": {"binmul32": round(bin_ms / args.steps, 3),
                                 "macromodel32": round(mm_ms / args.steps, 3),
                                 "fft32": round(fft_ms / args.steps, 3),
-                                "binmul64": round(bin64_ms / args.steps, 3)},
+                                "binmul64": round(bin64_ms / args.steps, 3),
+                                "fft64+mm64": round((fft64_ms + mm64_ms) / args.steps, 3),
+                                "arnoldi": round(arn_ms / args.steps, 3),
+                                "scatter": round(sct_ms / args.steps, 3)},
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": int(V.numel() * 16),
                 "d2h_bytes_per_step": int(V.numel() * 16)},

@@ -144,7 +144,8 @@ EMSURF_API void emsurf_destroy(emsurf_handle* h);
  * the caller's stream while enabled.  enable != 0 clears and starts
  * recording; 0 stops.  Phases: 0 bin multiply FP32, 1 bin multiply FP64,
  * 2 macromodel multiply FP32, 3 macromodel FP64, 4 FFT passes + gather FP32,
- * 5 the same FP64.  emsurf_profile_read synchronises on the recorded events
+ * 5 the same FP64, 6 Arnoldi orthogonalisation/norm/Givens kernels of
+ * emsurf_solve, 7 crop + U_o^T scatter of emsurf_matvec.  emsurf_profile_read synchronises on the recorded events
  * and returns the summed milliseconds and the number of intervals.       */
 EMSURF_API int emsurf_profile(emsurf_handle* h, int32_t enable);
 EMSURF_API int emsurf_profile_read(emsurf_handle* h, int32_t phase, double* total_ms,

@@ -295,7 +295,8 @@ def emsurf_far_field(hd, a, b, h, n, k, Y, rhat, F, rcs=None, stream=None):
                                   _ptr(F), _ptr(rcs), _stream(stream)))
 
 
-PHASES = {"binmul32": 0, "binmul64": 1, "mm32": 2, "mm64": 3, "fft32": 4, "fft64": 5}
+PHASES = {"binmul32": 0, "binmul64": 1, "mm32": 2, "mm64": 3, "fft32": 4, "fft64": 5,
+          "arnoldi": 6, "scatter": 7}
 
 
 def emsurf_profile(h, enable):

@@ -2,7 +2,10 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <utility>
 
 #include "common.cuh"
 
@@ -17,6 +20,20 @@ void set_error(const char* fmt, ...) {
     va_start(ap, fmt);
     vsnprintf(g_err, sizeof(g_err), fmt, ap);
     va_end(ap);
+}
+
+int set_smem_attr(const void* kernel, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> have;
+    int dev = 0;
+    EMS_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    auto key = std::make_pair(dev, kernel);
+    auto it = have.find(key);
+    if (it != have.end() && it->second >= bytes) return EMSURF_OK;
+    EMS_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    have[key] = bytes;
+    return EMSURF_OK;
 }
 
 int dev_alloc(emsurf_handle* h, void** p, size_t bytes) {

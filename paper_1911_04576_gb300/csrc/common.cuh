@@ -32,6 +32,14 @@ void set_error(const char* fmt, ...);
         if (_s != EMSURF_OK) return _s;                                        \
     } while (0)
 
+// Set a kernel's dynamic shared-memory limit once per (kernel, device): the
+// call is costly on the host and the attribute persists for the process.
+int set_smem_attr(const void* kernel, size_t bytes);
+template <typename F>
+int set_smem_once(F* kernel, size_t bytes) {
+    return set_smem_attr(reinterpret_cast<const void*>(kernel), bytes);
+}
+
 // ---------------------------------------------------------------- complex
 __host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -100,6 +108,13 @@ int fft_pass_gather(T2* data, const FftPlan& plan, long long inner, long long ou
                     long long outer_stride, int p_in, const double2* x, const int32_t* idx,
                     const int8_t* sgn, int nx, int K, int n_unique, cudaStream_t st);
 
+// Inverse pass over the kept rows (outer = ny) whose store writes only points
+// ix < nx, as y1[r][iy*nx+ix][k] = scale * value + sum_s mm[s][r][m][k].
+template <typename T2>
+int fft_pass_crop(T2* data, const FftPlan& plan, long long inner, long long outer,
+                  long long outer_stride, int nx, const T2* mm, int nsplit, int R, int M, int K,
+                  double scale, T2* y1, cudaStream_t st);
+
 int smallest_smooth_at_least(int n);   // smallest 2^a 3^b 5^c >= n
 
 // ---------------------------------------------------------------- operator
@@ -112,7 +127,8 @@ struct Operator {
     T2* Zt = nullptr;
     T2* Xg = nullptr;      // work grid [bins][R][2E] (forward)
     T2* Yg = nullptr;      // work grid [bins][R][2E] (inverse)
-    T2* Ymm = nullptr;     // macromodel output [R][M][2E]
+    T2* Ymm = nullptr;     // macromodel partial outputs [split][R][M][2E]
+    T2* Y1 = nullptr;      // local-space product [R][M][2E]
     T2 coef[4];
 };
 
@@ -124,7 +140,7 @@ struct PhaseTimer {
     size_t used = 0;               // events in use
 };
 enum { EMS_PH_BINMUL32 = 0, EMS_PH_BINMUL64, EMS_PH_MM32, EMS_PH_MM64, EMS_PH_FFT32, EMS_PH_FFT64,
-       EMS_NPHASE };
+       EMS_PH_ARNOLDI, EMS_PH_SCATTER, EMS_NPHASE };
 
 struct emsurf_handle {
     int device = 0;

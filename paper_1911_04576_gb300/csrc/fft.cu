@@ -132,10 +132,34 @@ struct GatherSrc {
     int nx, K, n_unique;
 };
 
-template <typename T2, int W, int P, int SIGN, bool GATHER>
+// Store epilogue of the inverse pass over the kept rows: point ix < nx of row
+// iy, lane L = r*K + k, goes to y1[r][iy*nx + ix][k] = scale * value +
+// sum_s mm[s][r][m][k] (the macromodel partials).
+template <typename T2>
+struct CropEpi {
+    const T2* mm;
+    T2* y1;
+    int nsplit, R, M, nx, K;
+    double scale;
+};
+
+template <typename T2>
+__device__ __forceinline__ void crop_store(const CropEpi<T2>& ep, int iy, int p, long long L, T2 v) {
+    const int r = (int)(L / ep.K), k = (int)(L % ep.K);
+    const size_t m = (size_t)iy * ep.nx + p;
+    double ax = (double)v.x * ep.scale, ay = (double)v.y * ep.scale;
+    for (int s = 0; s < ep.nsplit; ++s) {
+        const T2 z = ep.mm[(((size_t)s * ep.R + r) * ep.M + m) * ep.K + k];
+        ax += (double)z.x;
+        ay += (double)z.y;
+    }
+    ep.y1[((size_t)r * ep.M + m) * ep.K + k] = mk<T2>(ax, ay);
+}
+
+template <typename T2, int W, int P, int SIGN, bool GATHER, bool EPI>
 __global__ void __launch_bounds__(kFftThreads)
 fft_fixed_kernel(T2* __restrict__ data, long long inner, long long outer_stride, int p_in, int p_out,
-                 const double2* __restrict__ twg, GatherSrc gs) {
+                 const double2* __restrict__ twg, GatherSrc gs, CropEpi<T2> ep) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T2* buf0 = reinterpret_cast<T2*>(smem_raw);
     T2* buf1 = buf0 + P * W;
@@ -169,7 +193,10 @@ fft_fixed_kernel(T2* __restrict__ data, long long inner, long long outer_stride,
     const T2* res = Stages<T2, W, P, 0, 1, SIGN>::run(buf0, buf1, tw);
     for (int e = threadIdx.x; e < p_out * W; e += blockDim.x) {
         const int p = e / W, l = e % W;
-        if (l < wl) base[(long long)p * inner + l] = res[e];
+        if (l < wl) {
+            if constexpr (EPI) crop_store(ep, blockIdx.y, p, lane0 + l, res[e]);
+            else base[(long long)p * inner + l] = res[e];
+        }
     }
 }
 
@@ -189,7 +216,7 @@ template <typename T2, int W>
 __global__ void __launch_bounds__(kFftThreads)
 fft_pass_kernel(T2* __restrict__ data, int P, long long inner, long long outer_stride, int p_in,
                 int p_out, const double2* __restrict__ tw, RadList rad, int sign, GatherSrc gs,
-                int gather) {
+                int gather, CropEpi<T2> ep, int epi) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T2* buf0 = reinterpret_cast<T2*>(smem_raw);
     T2* buf1 = buf0 + (size_t)P * W;
@@ -258,7 +285,10 @@ fft_pass_kernel(T2* __restrict__ data, int P, long long inner, long long outer_s
 
     for (int e = threadIdx.x; e < p_out * W; e += blockDim.x) {
         const int p = e / W, l = e - (e / W) * W;
-        if (l < wl) base[(long long)p * inner + l] = in[e];
+        if (l < wl) {
+            if (epi) crop_store(ep, blockIdx.y, p, lane0 + l, in[e]);
+            else base[(long long)p * inner + l] = in[e];
+        }
     }
 }
 
@@ -269,16 +299,17 @@ constexpr int lanes_for(int P) {
          : (2 * P * 16 * (int)sizeof(T2) <= 96 * 1024) ? 16 : 8;
 }
 
-template <typename T2, int P, int SIGN, bool GATHER>
+template <typename T2, int P, int SIGN, bool GATHER, bool EPI>
 int launch_fixed(T2* data, const FftPlan& plan, long long inner, long long outer,
-                 long long outer_stride, int p_in, int p_out, const GatherSrc& gs, cudaStream_t st) {
+                 long long outer_stride, int p_in, int p_out, const GatherSrc& gs,
+                 const CropEpi<T2>& ep, cudaStream_t st) {
     constexpr int W = lanes_for<T2>(P);
     const size_t smem = (2ull * P * W + P) * sizeof(T2);
-    auto kern = fft_fixed_kernel<T2, W, P, SIGN, GATHER>;
-    EMS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    auto kern = fft_fixed_kernel<T2, W, P, SIGN, GATHER, EPI>;
+    EMS_TRY(set_smem_once(kern, smem));
     const long long gx = (inner + W - 1) / W;
     dim3 grid((unsigned)gx, (unsigned)outer);
-    kern<<<grid, kFftThreads, smem, st>>>(data, inner, outer_stride, p_in, p_out, plan.tw, gs);
+    kern<<<grid, kFftThreads, smem, st>>>(data, inner, outer_stride, p_in, p_out, plan.tw, gs, ep);
     EMS_CUDA(cudaGetLastError());
     return EMSURF_OK;
 }
@@ -286,44 +317,49 @@ int launch_fixed(T2* data, const FftPlan& plan, long long inner, long long outer
 template <typename T2, int W>
 int launch_generic(T2* data, const FftPlan& plan, long long inner, long long outer,
                    long long outer_stride, int p_in, int p_out, int sign, const GatherSrc& gs,
-                   bool gather, cudaStream_t st) {
+                   bool gather, const CropEpi<T2>& ep, bool epi, cudaStream_t st) {
     RadList rl;
     rl.n = plan.nrad;
     for (int i = 0; i < 16; ++i) rl.r[i] = plan.rad[i];
     const size_t smem = 2ull * plan.P * W * sizeof(T2);
-    EMS_CUDA(cudaFuncSetAttribute(fft_pass_kernel<T2, W>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    EMS_TRY(set_smem_once(fft_pass_kernel<T2, W>, smem));
     const long long gx = (inner + W - 1) / W;
     dim3 grid((unsigned)gx, (unsigned)outer);
     fft_pass_kernel<T2, W><<<grid, kFftThreads, smem, st>>>(data, plan.P, inner, outer_stride, p_in,
-                                                            p_out, plan.tw, rl, sign, gs, gather ? 1 : 0);
+                                                            p_out, plan.tw, rl, sign, gs, gather ? 1 : 0,
+                                                            ep, epi ? 1 : 0);
     EMS_CUDA(cudaGetLastError());
     return EMSURF_OK;
 }
 
-template <typename T2, int SIGN, bool GATHER>
+template <typename T2, int SIGN, bool GATHER, bool EPI>
 int dispatch_fixed(int P, T2* data, const FftPlan& plan, long long inner, long long outer,
-                   long long os, int p_in, int p_out, const GatherSrc& gs, cudaStream_t st,
-                   bool* done) {
+                   long long os, int p_in, int p_out, const GatherSrc& gs, const CropEpi<T2>& ep,
+                   cudaStream_t st, bool* done) {
     *done = true;
+#define EMS_FFT_CASE(N) \
+    case N: return launch_fixed<T2, N, SIGN, GATHER, EPI>(data, plan, inner, outer, os, p_in, p_out, gs, ep, st);
     switch (P) {
-        case 5: return launch_fixed<T2, 5, SIGN, GATHER>(data, plan, inner, outer, os, p_in, p_out, gs, st);
-        case 8: return launch_fixed<T2, 8, SIGN, GATHER>(data, plan, inner, outer, os, p_in, p_out, gs, st);
-        case 15: return launch_fixed<T2, 15, SIGN, GATHER>(data, plan, inner, outer, os, p_in, p_out, gs, st);
-        case 16: return launch_fixed<T2, 16, SIGN, GATHER>(data, plan, inner, outer, os, p_in, p_out, gs, st);
-        case 32: return launch_fixed<T2, 32, SIGN, GATHER>(data, plan, inner, outer, os, p_in, p_out, gs, st);
-        case 48: return launch_fixed<T2, 48, SIGN, GATHER>(data, plan, inner, outer, os, p_in, p_out, gs, st);
-        case 64: return launch_fixed<T2, 64, SIGN, GATHER>(data, plan, inner, outer, os, p_in, p_out, gs, st);
-        case 96: return launch_fixed<T2, 96, SIGN, GATHER>(data, plan, inner, outer, os, p_in, p_out, gs, st);
-        case 128: return launch_fixed<T2, 128, SIGN, GATHER>(data, plan, inner, outer, os, p_in, p_out, gs, st);
-        case 200: return launch_fixed<T2, 200, SIGN, GATHER>(data, plan, inner, outer, os, p_in, p_out, gs, st);
+        EMS_FFT_CASE(5)
+        EMS_FFT_CASE(8)
+        EMS_FFT_CASE(15)
+        EMS_FFT_CASE(16)
+        EMS_FFT_CASE(24)
+        EMS_FFT_CASE(32)
+        EMS_FFT_CASE(48)
+        EMS_FFT_CASE(64)
+        EMS_FFT_CASE(96)
+        EMS_FFT_CASE(128)
+        EMS_FFT_CASE(200)
         default: *done = false; return EMSURF_OK;
     }
+#undef EMS_FFT_CASE
 }
 
 template <typename T2>
 int pass_impl(T2* data, const FftPlan& plan, long long inner, long long outer, long long outer_stride,
-              int sign, int p_in, int p_out, const GatherSrc& gs, bool gather, cudaStream_t st) {
+              int sign, int p_in, int p_out, const GatherSrc& gs, bool gather, const CropEpi<T2>& ep,
+              bool epi, cudaStream_t st) {
     if (outer <= 0 || inner <= 0) return EMSURF_OK;
     if (outer > 65535 || (inner + 7) / 8 > 2147483647LL) {
         set_error("fft_pass: grid too large (outer %lld, lanes %lld)", outer, inner);
@@ -334,19 +370,21 @@ int pass_impl(T2* data, const FftPlan& plan, long long inner, long long outer, l
     bool done = false;
     int s = EMSURF_OK;
     if (sign < 0 && gather)
-        s = dispatch_fixed<T2, -1, true>(plan.P, data, plan, inner, outer, outer_stride, p_in, p_out, gs, st, &done);
+        s = dispatch_fixed<T2, -1, true, false>(plan.P, data, plan, inner, outer, outer_stride, p_in, p_out, gs, ep, st, &done);
     else if (sign < 0)
-        s = dispatch_fixed<T2, -1, false>(plan.P, data, plan, inner, outer, outer_stride, p_in, p_out, gs, st, &done);
-    else if (!gather)
-        s = dispatch_fixed<T2, +1, false>(plan.P, data, plan, inner, outer, outer_stride, p_in, p_out, gs, st, &done);
+        s = dispatch_fixed<T2, -1, false, false>(plan.P, data, plan, inner, outer, outer_stride, p_in, p_out, gs, ep, st, &done);
+    else if (epi)
+        s = dispatch_fixed<T2, +1, false, true>(plan.P, data, plan, inner, outer, outer_stride, p_in, p_out, gs, ep, st, &done);
+    else
+        s = dispatch_fixed<T2, +1, false, false>(plan.P, data, plan, inner, outer, outer_stride, p_in, p_out, gs, ep, st, &done);
     if (s != EMSURF_OK || done) return s;
     const size_t per_lane = 2ull * plan.P * sizeof(T2);
     if (per_lane * 32 <= 200 * 1024)
-        return launch_generic<T2, 32>(data, plan, inner, outer, outer_stride, p_in, p_out, sign, gs, gather, st);
+        return launch_generic<T2, 32>(data, plan, inner, outer, outer_stride, p_in, p_out, sign, gs, gather, ep, epi, st);
     if (per_lane * 16 <= 200 * 1024)
-        return launch_generic<T2, 16>(data, plan, inner, outer, outer_stride, p_in, p_out, sign, gs, gather, st);
+        return launch_generic<T2, 16>(data, plan, inner, outer, outer_stride, p_in, p_out, sign, gs, gather, ep, epi, st);
     if (per_lane * 8 <= 200 * 1024)
-        return launch_generic<T2, 8>(data, plan, inner, outer, outer_stride, p_in, p_out, sign, gs, gather, st);
+        return launch_generic<T2, 8>(data, plan, inner, outer, outer_stride, p_in, p_out, sign, gs, gather, ep, epi, st);
     set_error("FFT length %d too large for one shared-memory pass", plan.P);
     return EMSURF_EINVAL;
 }
@@ -402,7 +440,9 @@ template <typename T2>
 int fft_pass(T2* data, const FftPlan& plan, long long inner, long long outer,
              long long outer_stride, int sign, cudaStream_t st, int p_in, int p_out) {
     GatherSrc gs{nullptr, nullptr, nullptr, 0, 1, 0};
-    return pass_impl<T2>(data, plan, inner, outer, outer_stride, sign, p_in, p_out, gs, false, st);
+    CropEpi<T2> ep{nullptr, nullptr, 0, 1, 1, 1, 1, 1.0};
+    return pass_impl<T2>(data, plan, inner, outer, outer_stride, sign, p_in, p_out, gs, false, ep,
+                         false, st);
 }
 
 template <typename T2>
@@ -410,7 +450,19 @@ int fft_pass_gather(T2* data, const FftPlan& plan, long long inner, long long ou
                     long long outer_stride, int p_in, const double2* x, const int32_t* idx,
                     const int8_t* sgn, int nx, int K, int n_unique, cudaStream_t st) {
     GatherSrc gs{x, idx, sgn, nx, K, n_unique};
-    return pass_impl<T2>(data, plan, inner, outer, outer_stride, -1, p_in, plan.P, gs, true, st);
+    CropEpi<T2> ep{nullptr, nullptr, 0, 1, 1, 1, 1, 1.0};
+    return pass_impl<T2>(data, plan, inner, outer, outer_stride, -1, p_in, plan.P, gs, true, ep, false,
+                         st);
+}
+
+template <typename T2>
+int fft_pass_crop(T2* data, const FftPlan& plan, long long inner, long long outer,
+                  long long outer_stride, int nx, const T2* mm, int nsplit, int R, int M, int K,
+                  double scale, T2* y1, cudaStream_t st) {
+    GatherSrc gs{nullptr, nullptr, nullptr, 0, 1, 0};
+    CropEpi<T2> ep{mm, y1, nsplit, R, M, nx, K, scale};
+    return pass_impl<T2>(data, plan, inner, outer, outer_stride, +1, plan.P, nx, gs, false, ep, true,
+                         st);
 }
 
 template int fft_pass<double2>(double2*, const FftPlan&, long long, long long, long long, int,
@@ -423,5 +475,9 @@ template int fft_pass_gather<double2>(double2*, const FftPlan&, long long, long 
 template int fft_pass_gather<float2>(float2*, const FftPlan&, long long, long long, long long, int,
                                      const double2*, const int32_t*, const int8_t*, int, int, int,
                                      cudaStream_t);
+template int fft_pass_crop<double2>(double2*, const FftPlan&, long long, long long, long long, int,
+                                    const double2*, int, int, int, int, double, double2*, cudaStream_t);
+template int fft_pass_crop<float2>(float2*, const FftPlan&, long long, long long, long long, int,
+                                   const float2*, int, int, int, int, double, float2*, cudaStream_t);
 
 }  // namespace emsurf

@@ -2,9 +2,9 @@
 //
 // The paper solves Eq. final with GMRES (PETSc); restart length, initial
 // guess and orthogonalisation are not given.  Here: zero initial guess,
-// GMRES(m) with classical Gram-Schmidt applied twice (two reductions per
-// Arnoldi step instead of j+1), Givens rotations and the upper-triangular
-// solve on the device, all in FP64.  Right-hand sides are independent
+// GMRES(m) with classical Gram-Schmidt and a second pass when the DGKS test
+// asks for it (||w'|| < ||w||/sqrt 2; Daniel, Gragg, Kaufman, Stewart 1976),
+// Givens rotations and the upper-triangular solve on the device, all FP64.  Right-hand sides are independent
 // systems that share every operator application.
 //
 // MIXED precision: iterative refinement with FP64 residuals
@@ -20,8 +20,11 @@ namespace emsurf {
 
 namespace {
 
-constexpr int kRedBlocks = 304;     // 2 x 152 SMs
+constexpr int kRedBlocks = 152;     // one per SM of GB300
 constexpr int kRedThreads = 256;
+constexpr int kCheckEvery = 6;      // Arnoldi steps between host convergence checks
+constexpr int kArnThreads = 512;    // 16 warps: one per Krylov vector in the dot phase
+constexpr int kArnChunkMax = 4096;  // vector elements per block (64 KB of shared w)
 
 struct Gm {
     int m = 0, R = 0;
@@ -36,6 +39,10 @@ struct Gm {
     double2* sn = nullptr;     // [R][m]
     double2* g = nullptr;      // [R][m+1]
     double2* hv = nullptr;     // [R][m+1] projections of one CGS pass
+    double2* hv2 = nullptr;    // [R][m+1] projections of the second CGS pass
+    unsigned* counter = nullptr;   // [R] last-block counters of the fused reductions
+    int nblk = 0, chunk = 0;       // Arnoldi blocks and elements per block
+    int* reorth = nullptr;         // [R] second Gram-Schmidt pass needed (DGKS test)
     double2* part = nullptr;   // [R][m+1][kRedBlocks]
     double* nrm = nullptr;     // [R]
     double* bnorm = nullptr;   // [R]
@@ -109,25 +116,6 @@ __global__ void dot_final_kernel(const double2* __restrict__ part, int nblk, int
     (void)nvec;
 }
 
-// w[r] -= sum_{i<nvec} hv[r][i] V_i[r]
-__global__ void cgs_update_kernel(const double2* __restrict__ V, int nvec, size_t vstride,
-                                  const double2* __restrict__ hv, int ldv, double2* __restrict__ w,
-                                  size_t n, int R) {
-    const size_t total = (size_t)R * n;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-         e += (size_t)gridDim.x * blockDim.x) {
-        const int r = (int)(e / n);
-        double2 acc = w[e];
-        for (int i = 0; i < nvec; ++i) {
-            const double2 c = hv[(size_t)r * ldv + i];
-            const double2 v = V[(size_t)i * vstride + e];
-            acc.x -= c.x * v.x - c.y * v.y;
-            acc.y -= c.x * v.y + c.y * v.x;
-        }
-        w[e] = acc;
-    }
-}
-
 // dst[r] = src[r] / nrm[r] (0 if nrm == 0); optionally H[j+1][j] = nrm
 __global__ void normalize_kernel(double2* __restrict__ dst, const double2* __restrict__ src,
                                  const double* __restrict__ nrm, size_t n, int R,
@@ -154,6 +142,222 @@ __global__ void residual_kernel(double2* __restrict__ r0, const double2* __restr
         r0[e] = make_double2(b[e].x - w[e].x, b[e].y - w[e].y);
 }
 
+// ---------------------------------------------------------------- fused step
+// Block reduction of one complex value; result valid in thread 0.
+__device__ __forceinline__ double2 block_sum(double2 v, double2* red /* [blockDim/32] */) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double2 t = make_double2(0.0, 0.0);
+    if (wid == 0) {
+        t = lane < (int)(blockDim.x >> 5) ? red[lane] : make_double2(0.0, 0.0);
+        t = warp_sum(t);
+    }
+    return t;
+}
+
+// After every block wrote its partials: returns true in the last block to
+// arrive (classic threadfence reduction); that block resets the counter.
+__device__ __forceinline__ bool last_block(unsigned* counter, bool* flag) {
+    __threadfence();
+    if (threadIdx.x == 0) *flag = atomicAdd(counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (*flag) {
+        __threadfence();
+        if (threadIdx.x == 0) *counter = 0;
+    }
+    return *flag;
+}
+
+// sum of part[r][i][0..nb) in block order -> out (one warp per i)
+__device__ __forceinline__ void finalize_sums(const double2* part, int nb, int nvec, int ldv, int r,
+                                              double2* out_hv, double2* Hcol, bool add) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = wid; i < nvec; i += nw) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int b = lane; b < nb; b += 32) {
+            const double2 v = part[((size_t)r * ldv + i) * nb + b];
+            acc.x += v.x;
+            acc.y += v.y;
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            out_hv[(size_t)r * ldv + i] = acc;
+            if (Hcol) Hcol[i] = add ? make_double2(Hcol[i].x + acc.x, Hcol[i].y + acc.y) : acc;
+        }
+    }
+}
+
+// w -= sum_i c_i V_i on one element (c from shared memory), 8 loads in flight
+__device__ __forceinline__ double2 update_one(const double2* __restrict__ V, int nvec,
+                                              size_t vstride, size_t off, double2 acc,
+                                              const double2* __restrict__ cs) {
+    for (int i0 = 0; i0 < nvec; i0 += 8) {
+        double2 v[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            v[c] = (i0 + c < nvec) ? V[(size_t)(i0 + c) * vstride + off] : make_double2(0.0, 0.0);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            if (i0 + c < nvec) {
+                const double2 q = cs[i0 + c];
+                acc.x -= q.x * v[c].x - q.y * v[c].y;
+                acc.y -= q.x * v[c].y + q.y * v[c].x;
+            }
+        }
+    }
+    return acc;
+}
+
+// Projections h_i = V_i^H w (i < nvec) for every rhs.  Each block owns a
+// contiguous chunk of the vector: it stages that chunk of w in shared memory
+// (after applying w -= sum_i upd_i V_i when upd != nullptr, the previous
+// Gram-Schmidt pass), then one warp per Krylov vector forms the chunk's dot
+// product with a single warp reduction.  The last block sums the block
+// partials in block order into hv and sets (add = 0) or adds to column j of H.
+__global__ void __launch_bounds__(kArnThreads)
+cgs_pass_kernel(const double2* __restrict__ V, int nvec, size_t vstride, double2* __restrict__ w,
+                size_t n, int chunk, const double2* __restrict__ upd, double2* __restrict__ part,
+                int ldv, unsigned* __restrict__ counter, double2* __restrict__ hv,
+                double2* __restrict__ H, int m, int j, int add, int* __restrict__ reorth) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2* ws = reinterpret_cast<double2*>(smem_raw);   // [chunk]
+    __shared__ double2 cs[65];
+    __shared__ bool is_last;
+    const int r = blockIdx.y;
+    double2* wr = w + (size_t)r * n;
+    const size_t e0 = (size_t)blockIdx.x * chunk;
+    const int ne = (int)(e0 < n ? min((size_t)chunk, n - e0) : 0);
+    if (upd && !reorth[r]) {
+        // second pass not needed: apply the first pass's update only
+        for (int i = threadIdx.x; i < nvec; i += blockDim.x) cs[i] = upd[(size_t)r * ldv + i];
+        __syncthreads();
+        for (int q = threadIdx.x; q < ne; q += blockDim.x)
+            wr[e0 + q] = update_one(V, nvec, vstride, (size_t)r * n + e0 + q, wr[e0 + q], cs);
+        if (blockIdx.x == 0)
+            for (int i = threadIdx.x; i < nvec; i += blockDim.x) hv[(size_t)r * ldv + i] = make_double2(0.0, 0.0);
+        return;
+    }
+    if (upd) {
+        for (int i = threadIdx.x; i < nvec; i += blockDim.x) cs[i] = upd[(size_t)r * ldv + i];
+        __syncthreads();
+        for (int q = threadIdx.x; q < ne; q += blockDim.x) {
+            const double2 v = update_one(V, nvec, vstride, (size_t)r * n + e0 + q, wr[e0 + q], cs);
+            wr[e0 + q] = v;
+            ws[q] = v;
+        }
+    } else {
+        for (int q = threadIdx.x; q < ne; q += blockDim.x) ws[q] = wr[e0 + q];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // the first pass also forms ||w||^2 (as "vector" nvec) for the
+    // reorthogonalisation test
+    const int ndots = upd ? nvec : nvec + 1;
+    for (int i = wid; i < ndots; i += nw) {
+        const double2* a = (i < nvec ? V + (size_t)i * vstride + (size_t)r * n : wr) + e0;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int q = lane; q < ne; q += 32) {
+            const double2 p = conj_mul(a[q], ws[q]);
+            acc.x += p.x;
+            acc.y += p.y;
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) part[((size_t)r * ldv + i) * gridDim.x + blockIdx.x] = acc;
+    }
+    if (last_block(counter + r, &is_last)) {
+        finalize_sums(part, gridDim.x, ndots, ldv, r, hv, nullptr, false);
+        __syncthreads();
+        double2* col = H + ((size_t)r * m + j) * (m + 1);
+        for (int i = threadIdx.x; i < nvec; i += blockDim.x)
+            col[i] = add ? make_double2(col[i].x + hv[(size_t)r * ldv + i].x, col[i].y + hv[(size_t)r * ldv + i].y)
+                         : hv[(size_t)r * ldv + i];
+        if (!upd && threadIdx.x == 0) {
+            // DGKS: after w' = w - V h, ||w'||^2 = ||w||^2 - ||h||^2; a second
+            // pass is needed when ||w'|| < ||w|| / sqrt(2)
+            double hh = 0.0;
+            for (int i = 0; i < nvec; ++i) {
+                const double2 v = hv[(size_t)r * ldv + i];
+                hh += v.x * v.x + v.y * v.y;
+            }
+            const double ww = hv[(size_t)r * ldv + nvec].x;
+            reorth[r] = (ww - hh < 0.5 * ww) ? 1 : 0;
+        }
+    }
+}
+
+__device__ void givens_update(int r, double2* __restrict__ col, double2* __restrict__ c,
+                              double2* __restrict__ s, double2* __restrict__ gg,
+                              const double* __restrict__ bnorm, double* __restrict__ res,
+                              int* __restrict__ active, int* __restrict__ jend, int m, int j,
+                              double rtol);
+
+// w -= sum_i upd_i V_i, ||w||, H[j+1][j] = ||w||, then (last block, one
+// thread per rhs) the Givens update of column j.
+__global__ void __launch_bounds__(kArnThreads)
+cgs_norm_givens_kernel(const double2* __restrict__ V, int nvec, size_t vstride,
+                       double2* __restrict__ w, size_t n, int chunk, const double2* __restrict__ upd,
+                       double2* __restrict__ part, int ldv, unsigned* __restrict__ counter,
+                       double* __restrict__ nrm, double2* __restrict__ H, double2* __restrict__ cs,
+                       double2* __restrict__ sn, double2* __restrict__ g,
+                       const double* __restrict__ bnorm, double* __restrict__ res,
+                       int* __restrict__ active, int* __restrict__ jend, int m, int j, double rtol,
+                       const int* __restrict__ reorth) {
+    __shared__ double2 red[kArnThreads / 32];
+    __shared__ double2 cs_[65];
+    __shared__ bool is_last;
+    const int r = blockIdx.y;
+    double2* wr = w + (size_t)r * n;
+    const size_t e0 = (size_t)blockIdx.x * chunk;
+    const int ne = (int)(e0 < n ? min((size_t)chunk, n - e0) : 0);
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) cs_[i] = upd[(size_t)r * ldv + i];
+    __syncthreads();
+    double ss = 0.0;
+    const bool second = reorth[r] != 0;
+    for (int q = threadIdx.x; q < ne; q += blockDim.x) {
+        const double2 acc = second ? update_one(V, nvec, vstride, (size_t)r * n + e0 + q, wr[e0 + q], cs_)
+                                   : wr[e0 + q];
+        if (second) wr[e0 + q] = acc;
+        ss += acc.x * acc.x + acc.y * acc.y;
+    }
+    const double2 t = block_sum(make_double2(ss, 0.0), red);
+    if (threadIdx.x == 0) part[((size_t)r * ldv) * gridDim.x + blockIdx.x] = t;
+    if (last_block(counter + r, &is_last)) {
+        // stage column j, the rotations and g in shared memory (parallel loads)
+        __shared__ double2 scol[66], sc[65], ssn[65], sg[66];
+        double2* col = H + ((size_t)r * m + j) * (m + 1);
+        for (int i = threadIdx.x; i <= j; i += blockDim.x) scol[i] = col[i];
+        for (int i = threadIdx.x; i < j; i += blockDim.x) {
+            sc[i] = cs[(size_t)r * m + i];
+            ssn[i] = sn[(size_t)r * m + i];
+        }
+        for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) sg[i] = g[(size_t)r * (m + 1) + i];
+        double acc = 0.0;
+        if (threadIdx.x < 32) {
+            for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) acc += part[((size_t)r * ldv) * gridDim.x + b].x;
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const double v = sqrt(fmax(acc, 0.0));
+            nrm[r] = v;
+            scol[j + 1] = make_double2(v, 0.0);
+            givens_update(r, scol, sc, ssn, sg, bnorm, res, active, jend, m, j, rtol);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) {
+            col[i] = scol[i];
+            g[(size_t)r * (m + 1) + i] = sg[i];
+        }
+        if (threadIdx.x == 0) {
+            cs[(size_t)r * m + j] = sc[j];
+            sn[(size_t)r * m + j] = ssn[j];
+        }
+    }
+}
+
 // start of a cycle: g = [beta, 0...], res = beta/bnorm, active = res > rtol
 __global__ void cycle_start_kernel(const double* __restrict__ nrm, const double* __restrict__ bnorm,
                                    double2* __restrict__ g, double* __restrict__ res,
@@ -169,17 +373,14 @@ __global__ void cycle_start_kernel(const double* __restrict__ nrm, const double*
     g[(size_t)r * (m + 1)] = make_double2(nrm[r], 0.0);
 }
 
-// Givens update of column j for every active right-hand side.
-__global__ void givens_kernel(double2* __restrict__ H, double2* __restrict__ cs,
-                              double2* __restrict__ sn, double2* __restrict__ g,
+// Givens update of column j of right-hand side r (if still active): col =
+// column j of its Hessenberg matrix, c/s its rotations, gg its g vector.
+__device__ void givens_update(int r, double2* __restrict__ col, double2* __restrict__ c,
+                              double2* __restrict__ s, double2* __restrict__ gg,
                               const double* __restrict__ bnorm, double* __restrict__ res,
-                              int* __restrict__ active, int* __restrict__ jend, int m, int j, int R,
+                              int* __restrict__ active, int* __restrict__ jend, int m, int j,
                               double rtol) {
-    const int r = threadIdx.x;
-    if (r >= R || !active[r]) return;
-    double2* col = H + ((size_t)r * m + j) * (m + 1);
-    double2* c = cs + (size_t)r * m;
-    double2* s = sn + (size_t)r * m;
+    if (!active[r]) return;
     for (int i = 0; i < j; ++i) {
         const double2 a = col[i], b = col[i + 1];
         // [conj(c) conj(s); -s c] [a; b]
@@ -203,7 +404,6 @@ __global__ void givens_kernel(double2* __restrict__ H, double2* __restrict__ cs,
     s[j] = sj;
     col[j] = make_double2(den, 0.0);
     col[j + 1] = make_double2(0.0, 0.0);
-    double2* gg = g + (size_t)r * (m + 1);
     const double2 gj = gg[j];
     gg[j + 1] = make_double2(-(sj.x * gj.x - sj.y * gj.y), -(sj.x * gj.y + sj.y * gj.x));
     gg[j] = make_double2(cj.x * gj.x + cj.y * gj.y, cj.x * gj.y - cj.y * gj.x);
@@ -291,7 +491,14 @@ int gm_alloc(emsurf_handle* h, Gm*& gm, int m, int R) {
     EMS_TRY(dev_alloc(h, (void**)&g->sn, sizeof(double2) * RR * mm));
     EMS_TRY(dev_alloc(h, (void**)&g->g, sizeof(double2) * RR * (mm + 1)));
     EMS_TRY(dev_alloc(h, (void**)&g->hv, sizeof(double2) * RR * (mm + 1)));
-    EMS_TRY(dev_alloc(h, (void**)&g->part, sizeof(double2) * RR * (mm + 1) * kRedBlocks));
+    EMS_TRY(dev_alloc(h, (void**)&g->hv2, sizeof(double2) * RR * (mm + 1)));
+    EMS_TRY(dev_alloc(h, (void**)&g->counter, sizeof(unsigned) * RR));
+    EMS_TRY(dev_alloc(h, (void**)&g->reorth, sizeof(int) * RR));
+    EMS_CUDA(cudaMemset(g->counter, 0, sizeof(unsigned) * RR));
+    g->nblk = (int)std::max<size_t>(2 * 152, (g->n + kArnChunkMax - 1) / kArnChunkMax);
+    g->chunk = (int)((g->n + g->nblk - 1) / g->nblk);
+    EMS_TRY(dev_alloc(h, (void**)&g->part,
+                      sizeof(double2) * RR * (mm + 1) * std::max<size_t>(g->nblk, kRedBlocks)));
     EMS_TRY(dev_alloc(h, (void**)&g->nrm, sizeof(double) * RR));
     EMS_TRY(dev_alloc(h, (void**)&g->bnorm, sizeof(double) * RR));
     EMS_TRY(dev_alloc(h, (void**)&g->res, sizeof(double) * RR));
@@ -373,35 +580,39 @@ int gmres_core(emsurf_handle* h, Gm* g, Apply& A, const double2* b, double2* x, 
         for (int j = 0; j < m; ++j) {
             double2* Vj = g->V + (size_t)j * vstride;
             EMS_TRY(A(Vj, g->w, R, st));
-            // CGS2: two projections onto V_0..V_j
-            for (int pass = 0; pass < 2; ++pass) {
-                dot_partial_kernel<<<dim3(kRedBlocks, j + 1, R), kRedThreads, 0, st>>>(
-                    g->V, j + 1, vstride, g->w, n, R, g->part, m + 1);
-                EMS_CUDA(cudaGetLastError());
-    ++g->launches;
-                dot_final_kernel<<<dim3(j + 1, R), 32, 0, st>>>(g->part, kRedBlocks, j + 1, m + 1,
-                                                                g->hv, g->H, m, j, g->nrm, pass);
-                EMS_CUDA(cudaGetLastError());
-    ++g->launches;
-                cgs_update_kernel<<<nb, 256, 0, st>>>(g->V, j + 1, vstride, g->hv, m + 1, g->w, n, R);
-                EMS_CUDA(cudaGetLastError());
-    ++g->launches;
-            }
-            EMS_TRY(norms(g, g->w, R, st));
+            // CGS2 (two projections onto V_0..V_j), norm and Givens: 3 fused kernels
+            const dim3 rg(g->nblk, R);
+            const size_t wsm = (size_t)g->chunk * sizeof(double2);
+            EMS_TRY(set_smem_once(cgs_pass_kernel, wsm));
+            prof_mark(h, EMS_PH_ARNOLDI, true, st);
+            cgs_pass_kernel<<<rg, kArnThreads, wsm, st>>>(g->V, j + 1, vstride, g->w, n, g->chunk, nullptr,
+                                                          g->part, m + 1, g->counter, g->hv, g->H, m, j, 0,
+                                                          g->reorth);
+            EMS_CUDA(cudaGetLastError());
+            cgs_pass_kernel<<<rg, kArnThreads, wsm, st>>>(g->V, j + 1, vstride, g->w, n, g->chunk, g->hv,
+                                                          g->part, m + 1, g->counter, g->hv2, g->H, m, j, 1,
+                                                          g->reorth);
+            EMS_CUDA(cudaGetLastError());
+            cgs_norm_givens_kernel<<<rg, kArnThreads, 0, st>>>(
+                g->V, j + 1, vstride, g->w, n, g->chunk, g->hv2, g->part, m + 1, g->counter, g->nrm, g->H,
+                g->cs, g->sn, g->g, g->bnorm, g->res, g->active, g->jend, m, j, rtol, g->reorth);
+            EMS_CUDA(cudaGetLastError());
             normalize_kernel<<<nb, 256, 0, st>>>(g->V + (size_t)(j + 1) * vstride, g->w, g->nrm, n,
-                                                 R, g->H, m, j);
+                                                 R, nullptr, m, j);
             EMS_CUDA(cudaGetLastError());
-    ++g->launches;
-            givens_kernel<<<1, 64, 0, st>>>(g->H, g->cs, g->sn, g->g, g->bnorm, g->res, g->active,
-                                             g->jend, m, j, R, rtol);
-            EMS_CUDA(cudaGetLastError());
-    ++g->launches;
-            EMS_CUDA(cudaMemcpyAsync(g->h_act, g->active, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
-            EMS_CUDA(cudaStreamSynchronize(st));
+            prof_mark(h, EMS_PH_ARNOLDI, false, st);
+            g->launches += 4;
             ++it;
-            bool act = false;
-            for (int r = 0; r < R; ++r) act = act || g->h_act[r];
-            if (!act || it >= max_iters) break;
+            // convergence is read back every kCheckEvery steps (the steps after
+            // a right-hand side converged leave its solution untouched)
+            if (it >= max_iters) break;
+            if ((j + 1) % kCheckEvery == 0 && j + 1 < m) {
+                EMS_CUDA(cudaMemcpyAsync(g->h_act, g->active, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+                EMS_CUDA(cudaStreamSynchronize(st));
+                bool act = false;
+                for (int r = 0; r < R; ++r) act = act || g->h_act[r];
+                if (!act) break;
+            }
         }
         trisolve_kernel<<<1, 64, 0, st>>>(g->H, g->g, g->hv, g->jend, m, R);
         EMS_CUDA(cudaGetLastError());

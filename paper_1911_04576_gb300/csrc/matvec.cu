@@ -185,7 +185,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 __global__ void binmul_tma_kernel(const float2* __restrict__ Bhat, const float2* __restrict__ Xh,
                                   float2* __restrict__ Yh, int E, int nbins, float2 ca, float2 cb,
                                   float2 cg, float2 cd, int* __restrict__ err) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int stage_elems = 2 * kBmJB * E;
     float2* sbuf = reinterpret_cast<float2*>(smem_raw);
     float2* xbuf = sbuf + (size_t)kBmStages * stage_elems;      // [2][2E]
@@ -336,15 +336,12 @@ __global__ void macromodel_kernel(const T2* __restrict__ Zt, const double2* __re
     }
 }
 
-// ------------------------------------------------ K3 tail: crop + U_o^T
-// y[r][u] = sum over local unknowns (m,k) of u: sign * (Yg[bin(m)][r][k] / P
-//           + Ymm[r][m][k])
+// ------------------------------------------------ K3 tail: U_o^T
+// y[r][u] = sum over local unknowns (m,k) of u: sign * y1[r][m][k]
 template <typename T2>
-__global__ void crop_scatter_kernel(double2* __restrict__ y, const T2* __restrict__ Yg,
-                                    const T2* __restrict__ Ymm, const int32_t* __restrict__ ptr,
-                                    const int32_t* __restrict__ ent, const int8_t* __restrict__ esg,
-                                    int nx, int px, int K, int M, int R, int n_unique,
-                                    double scale, int nsplit) {
+__global__ void scatter_kernel(double2* __restrict__ y, const T2* __restrict__ y1,
+                               const int32_t* __restrict__ ptr, const int32_t* __restrict__ ent,
+                               const int8_t* __restrict__ esg, int MK, int R, int n_unique) {
     const size_t total = (size_t)R * n_unique;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
          e += (size_t)gridDim.x * blockDim.x) {
@@ -352,19 +349,10 @@ __global__ void crop_scatter_kernel(double2* __restrict__ y, const T2* __restric
         const int r = (int)(e / n_unique);
         double ax = 0.0, ay = 0.0;
         for (int q = ptr[u]; q < ptr[u + 1]; ++q) {
-            const int loc = ent[q];
-            const int m = loc / K, k = loc - (loc / K) * K;
-            const int ix = m % nx, iy = m / nx;
-            const T2 g = Yg[(((size_t)iy * px + ix) * R + r) * K + k];
-            double zx = 0.0, zy = 0.0;
-            for (int sp = 0; sp < nsplit; ++sp) {
-                const T2 z = Ymm[(((size_t)sp * R + r) * M + m) * K + k];
-                zx += (double)z.x;
-                zy += (double)z.y;
-            }
+            const T2 v = y1[(size_t)r * MK + ent[q]];
             const double s = (double)esg[q];
-            ax += s * ((double)g.x * scale + zx);
-            ay += s * ((double)g.y * scale + zy);
+            ax += s * (double)v.x;
+            ay += s * (double)v.y;
         }
         y[e] = make_double2(ax, ay);
     }
@@ -465,6 +453,7 @@ int build_operator(emsurf_handle* h, Operator<T2>& op, const emsurf_problem* pr)
     EMS_TRY(dev_alloc(h, (void**)&op.Xg, grid_elems * sizeof(T2)));
     EMS_TRY(dev_alloc(h, (void**)&op.Yg, grid_elems * sizeof(T2)));
     EMS_TRY(dev_alloc(h, (void**)&op.Ymm, (size_t)kMmSplit * h->max_rhs * h->M * K * sizeof(T2)));
+    EMS_TRY(dev_alloc(h, (void**)&op.Y1, (size_t)h->max_rhs * h->M * K * sizeof(T2)));
     for (int c = 0; c < 4; ++c) op.coef[c] = mk<T2>(pr->coef[c].re, pr->coef[c].im);
     return EMSURF_OK;
 }
@@ -487,54 +476,6 @@ int apply_operator(emsurf_handle* h, Operator<T2>& op, const double2* x, double2
                                 h->d_uo_index, h->d_uo_sign, h->nx, K, h->n_unique, st));
     EMS_TRY(fft_pass<T2>(op.Xg, h->plan_y, (long long)px * lanes, 1, 0, -1, st, h->ny, py));
     prof_mark(h, ph_fft, false, st);
-    prof_mark(h, ph_bin, true, st);
-    // K2
-    const int threads = std::min(1024, ((E + 31) / 32) * 32);
-    const int nb = h->nbins;
-    if constexpr (std::is_same<T2, float2>::value) {
-        const size_t smem = binmul_tma_smem(E);
-        // the x double buffer needs at least kBmStages stages per bin
-        if (R == 1 && smem <= 227 * 1024 && E + 32 <= 1024 && (E + kBmJB - 1) / kBmJB >= kBmStages) {
-            EMS_CUDA(cudaFuncSetAttribute(binmul_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
-            const int grid = std::min(nb, std::max(1, h->num_sms));
-            binmul_tma_kernel<<<grid, 32 * (1 + (E + 31) / 32), smem, st>>>(
-                op.Bhat, op.Xg, op.Yg, E, nb, op.coef[0], op.coef[1], op.coef[2], op.coef[3], h->d_err);
-            EMS_CUDA(cudaGetLastError());
-            h->launches += 1;
-            prof_mark(h, ph_bin, false, st);
-            prof_mark(h, ph_fft, true, st);
-            goto inverse;
-        }
-    }
-    {
-    int rb = 1;
-    if (R >= 4) rb = 4;
-    else if (R >= 2) rb = 2;
-    for (int r0 = 0; r0 < R; r0 += rb) {
-        const size_t smem = (size_t)rb * K * sizeof(T2);
-        const int grid = std::min(nb, 152 * 8);
-        if (rb == 4) {
-            binmul_kernel<T2, 4><<<grid, threads, smem, st>>>(op.Bhat, op.Xg, op.Yg, E, nb, R, r0,
-                                                              op.coef[0], op.coef[1], op.coef[2], op.coef[3]);
-        } else if (rb == 2) {
-            binmul_kernel<T2, 2><<<grid, threads, smem, st>>>(op.Bhat, op.Xg, op.Yg, E, nb, R, r0,
-                                                              op.coef[0], op.coef[1], op.coef[2], op.coef[3]);
-        } else {
-            binmul_kernel<T2, 1><<<grid, threads, smem, st>>>(op.Bhat, op.Xg, op.Yg, E, nb, R, r0,
-                                                              op.coef[0], op.coef[1], op.coef[2], op.coef[3]);
-        }
-        EMS_CUDA(cudaGetLastError());
-        h->launches += 1;
-    }
-    prof_mark(h, ph_bin, false, st);
-    prof_mark(h, ph_fft, true, st);
-    }
-inverse:
-    // K3: inverse y-pass on all columns, inverse x-pass on the rows kept
-    EMS_TRY(fft_pass<T2>(op.Yg, h->plan_y, (long long)px * lanes, 1, 0, +1, st, py, h->ny));
-    EMS_TRY(fft_pass<T2>(op.Yg, h->plan_x, lanes, h->ny, (long long)px * lanes, +1, st, px, h->nx));
-    prof_mark(h, ph_fft, false, st);
     prof_mark(h, ph_mm, true, st);
     // K4
     const int nsplit = std::max(1, std::min(kMmSplit, K / 64));
@@ -550,10 +491,57 @@ inverse:
         EMS_CUDA(cudaGetLastError());
     }
     prof_mark(h, ph_mm, false, st);
-    crop_scatter_kernel<T2><<<grid_for((size_t)R * h->n_unique, 256), 256, 0, st>>>(
-        y, op.Yg, op.Ymm, h->d_inv_ptr, h->d_inv_ent, h->d_inv_sgn, h->nx, px, K, h->M, R,
-        h->n_unique, 1.0 / (double)h->nbins, nsplit);
+    prof_mark(h, ph_bin, true, st);
+    // K2
+    const int threads = std::min(1024, ((E + 31) / 32) * 32);
+    const int nb = h->nbins;
+    bool bin_done = false;
+    if constexpr (std::is_same<T2, float2>::value) {
+        const size_t smem = binmul_tma_smem(E);
+        // the x double buffer needs at least kBmStages stages per bin
+        if (R == 1 && smem <= 227 * 1024 && E + 32 <= 1024 && (E + kBmJB - 1) / kBmJB >= kBmStages) {
+            EMS_TRY(set_smem_once(binmul_tma_kernel, smem));
+            const int grid = std::min(nb, std::max(1, h->num_sms));
+            binmul_tma_kernel<<<grid, 32 * (1 + (E + 31) / 32), smem, st>>>(
+                op.Bhat, op.Xg, op.Yg, E, nb, op.coef[0], op.coef[1], op.coef[2], op.coef[3], h->d_err);
+            EMS_CUDA(cudaGetLastError());
+            h->launches += 1;
+            bin_done = true;
+        }
+    }
+    if (!bin_done) {
+        int rb = 1;
+        if (R >= 4) rb = 4;
+        else if (R >= 2) rb = 2;
+        for (int r0 = 0; r0 < R; r0 += rb) {
+            const size_t smem = (size_t)rb * K * sizeof(T2);
+            const int grid = std::min(nb, 152 * 8);
+            if (rb == 4) {
+                binmul_kernel<T2, 4><<<grid, threads, smem, st>>>(op.Bhat, op.Xg, op.Yg, E, nb, R, r0,
+                                                                  op.coef[0], op.coef[1], op.coef[2], op.coef[3]);
+            } else if (rb == 2) {
+                binmul_kernel<T2, 2><<<grid, threads, smem, st>>>(op.Bhat, op.Xg, op.Yg, E, nb, R, r0,
+                                                                  op.coef[0], op.coef[1], op.coef[2], op.coef[3]);
+            } else {
+                binmul_kernel<T2, 1><<<grid, threads, smem, st>>>(op.Bhat, op.Xg, op.Yg, E, nb, R, r0,
+                                                                  op.coef[0], op.coef[1], op.coef[2], op.coef[3]);
+            }
+            EMS_CUDA(cudaGetLastError());
+            h->launches += 1;
+        }
+    }
+    prof_mark(h, ph_bin, false, st);
+    prof_mark(h, ph_fft, true, st);
+    // K3: inverse y-pass on all columns, inverse x-pass on the rows kept
+    EMS_TRY(fft_pass<T2>(op.Yg, h->plan_y, (long long)px * lanes, 1, 0, +1, st, py, h->ny));
+    EMS_TRY(fft_pass_crop<T2>(op.Yg, h->plan_x, lanes, h->ny, (long long)px * lanes, h->nx, op.Ymm,
+                              nsplit, R, h->M, K, 1.0 / (double)h->nbins, op.Y1, st));
+    prof_mark(h, ph_fft, false, st);
+    prof_mark(h, EMS_PH_SCATTER, true, st);
+    scatter_kernel<T2><<<grid_for((size_t)R * h->n_unique, 256), 256, 0, st>>>(
+        y, op.Y1, h->d_inv_ptr, h->d_inv_ent, h->d_inv_sgn, h->M * K, R, h->n_unique);
     EMS_CUDA(cudaGetLastError());
+    prof_mark(h, EMS_PH_SCATTER, false, st);
     h->launches += 6;   // 4 FFT passes, macromodel, crop/scatter
     return EMSURF_OK;
 }
