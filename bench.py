@@ -169,6 +169,56 @@ def cpu_oracle_matvec_seconds(W, w, nu_expected):
     return time.perf_counter() - t0
 
 
+SERVE_SIZES = (8, 12, 16)      # lattice N x N of the serving stream
+SERVE_MESH = (3, 4)            # boxes meshed n x n: K = 324 or 576
+SERVE_RHS = (1, 2)
+SERVE_RATE = 20.0              # Poisson arrivals per second
+SERVE_BUDGET = 80 << 30        # device-memory budget of the server
+
+
+def serve_stream(B, W, nreq, seed, precision, max_active):
+    """Submit a seeded Poisson stream of solve requests at their arrival
+    times, wait for all, return latency percentiles and throughput."""
+    rng = np.random.default_rng(seed)
+    lib_sides = rng.uniform(0.15, 0.45, 32) * W.LAMBDA
+    arrivals = np.cumsum(rng.exponential(1.0 / SERVE_RATE, nreq))
+    reqs = []
+    for _ in range(nreq):
+        N = int(rng.choice(SERVE_SIZES))
+        n = int(rng.choice(SERVE_MESH))
+        R = int(rng.choice(SERVE_RHS))
+        th = rng.uniform(0.0, 60.0, R)
+        ph = rng.choice([0.0, 90.0], R)
+        waves = [W.plane_waves(W.Workload("s", 1, 1, 1, 1, 0, 0, angles=[(t, p, "theta")]))[0]
+                 for t, p in zip(th, ph)]
+        reqs.append(dict(a=W.PERIOD, b=W.PERIOD, h=W.BOX_H, n=n, nx=N, ny=N, k0=W.K0,
+                         patch_sides=lib_sides, patch_z=W.PATCH_Z, patch_n=4,
+                         type_map=rng.integers(0, 32, N * N), khat=np.array([w_[0] for w_ in waves]),
+                         ehat=np.array([w_[1] for w_ in waves]), precision=precision, rtol=RTOL,
+                         restart=RESTART, max_iters=20000, max_refine=20))
+    sv = B.emsurf_server_create(0, SERVE_BUDGET, max_active)
+    tickets = []
+    t0 = time.perf_counter()
+    for at, r in zip(arrivals, reqs):
+        dt = t0 + at - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        q, keep = B.make_request(**r)
+        tickets.append(B.emsurf_submit(sv, q, keep))
+    res = [B.emsurf_wait(sv, t, 3600 * 1000) for t in tickets]
+    makespan = time.perf_counter() - t0
+    sv.close()
+    lat = np.array([r["latency_ms"] for r in res])
+    ok = all(r["status"] == B.EMSURF_OK for r in res)
+    return {"requests": nreq, "p50_ms": round(float(np.percentile(lat, 50)), 1),
+            "p99_ms": round(float(np.percentile(lat, 99)), 1),
+            "mean_ms": round(float(lat.mean()), 1),
+            "throughput_rps": round(nreq / makespan, 3), "makespan_s": round(makespan, 2),
+            "solve_ms_mean": round(float(np.mean([r["solve_ms"] for r in res])), 1),
+            "queue_ms_mean": round(float(np.mean([r["queue_ms"] for r in res])), 1),
+            "all_converged": ok, "max_active": max_active}
+
+
 def reference_arm(args, W, w):
     ws, rank, _ = dist_init()
     if rank != 0:
@@ -216,6 +266,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="lattice16x16_k576")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=10,
+                    help="requests of the serving stream (0 = skip the serving measurement)")
     ap.add_argument("--matvecs-only", type=int, default=0,
                     help="profiler driver: build the workload, run this many products, exit")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32", "fp64"],
@@ -324,6 +376,15 @@ def main():
     f1.record()
     torch.cuda.synchronize()
     e2e_ms = f0.elapsed_time(f1) / args.steps
+    # ------------------------------------------------------------ serving
+    serve = None
+    if args.serve_requests > 0:
+        h.close()          # free the bench handle's device memory for the server
+        serve = {"stream": "Poisson %.0f/s; lattices %s, K %s, rhs %s, 32-type library; rtol %g"
+                           % (SERVE_RATE, list(SERVE_SIZES), [36 * m * m for m in SERVE_MESH],
+                              list(SERVE_RHS), RTOL),
+                 "mixed_batched": serve_stream(B, W, args.serve_requests, 7, B.MIXED, 4),
+                 "fp64_one_at_a_time": serve_stream(B, W, args.serve_requests, 7, B.FP64, 1)}
     # ------------------------------------------------------------ CPU oracle
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         t_cpu = cpu_oracle_matvec_seconds(W, w, nu)
@@ -378,6 +439,7 @@ def main():
                 "d2h_bytes_per_step": int(V.numel() * 16)},
         "gpu_launches": int(launches),
         "clocks": clk,
+        "serve": serve,
         "setup": setup,
         "device_bytes": dev_bytes,
     }

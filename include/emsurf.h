@@ -88,6 +88,9 @@ typedef struct {
     int32_t tables_on_device;
     int64_t device_mem_budget;   /* bytes; 0 = no limit; ENOMEM if exceeded */
     int32_t device;
+    void* stream;                /* CUDA stream for the setup work of
+                                    emsurf_create (NULL = legacy default);
+                                    create synchronises it before returning */
 } emsurf_problem;
 
 typedef struct {
@@ -284,6 +287,69 @@ EMSURF_API int emsurf_excitation(emsurf_handle* h, double a, double b, double hg
 EMSURF_API int emsurf_far_field(emsurf_handle* h, double a, double b, double hgt, int32_t n,
                                 double k, const emsurf_c128* Y, int32_t nrhs, int32_t ndir,
                                 const double* rhat, emsurf_c128* F, double* rcs, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Serving (no counterpart in the paper, which solves one array at a time):
+ * continuous batching of whole lattice solves.  A request describes one
+ * lattice; a server worker builds it on the device (U_o, offset tables,
+ * macromodels, FFT-domain operator, excitation), solves Eq. final and copies
+ * the currents to x_out.  Up to max_active requests run at once, each on its
+ * own non-blocking stream; a queued request is admitted (first fit) when a
+ * slot is free and its device-memory estimate (emsurf_request_bytes) fits
+ * in what the budget has left.                                            */
+typedef struct emsurf_server emsurf_server;
+
+typedef struct {
+    int32_t device;
+    int64_t device_mem_budget;   /* bytes admitted at once; 0 = free memory   */
+    int32_t max_active;          /* concurrent solves, 1..64                  */
+} emsurf_server_opts;
+
+typedef struct {
+    double a, b, h;              /* cell period x, y and box height (m)       */
+    int32_t n;                   /* box faces meshed n x n (K = 36 n^2)       */
+    int32_t nx, ny;              /* lattice                                   */
+    double k0;                   /* free-space wavenumber (1/m)               */
+    int32_t n_types;
+    const double* patch_sides;   /* [n_types] PEC patch side (m), <= 0 empty  */
+    double patch_z;              /* patch height (m)                          */
+    int32_t patch_n;             /* patch mesh patch_n x patch_n              */
+    const int32_t* type_map;     /* [ny*nx] cell -> type                      */
+    int32_t nrhs;                /* plane waves, 1..64                        */
+    const double* khat;          /* [nrhs][3] propagation directions          */
+    const double* ehat;          /* [nrhs][3] polarisations                   */
+    int32_t precision;           /* EMSURF_FP64 / FP32 / MIXED                */
+    emsurf_solve_opts opts;
+    emsurf_c128* x_out;          /* host [nrhs][n_unique] or NULL; must stay
+                                    valid until the result is collected       */
+} emsurf_request;
+
+typedef struct {
+    int32_t status;              /* status of the solve (OK, ENOTCONV, ...)   */
+    int32_t n_unique, nrhs;
+    emsurf_solve_info info;      /* worst residual / all-converged over rhs   */
+    double queue_ms;             /* submit -> admitted                        */
+    double setup_ms;             /* tables, macromodels, operator, excitation */
+    double solve_ms;             /* GMRES and the copy of x                   */
+    double latency_ms;           /* submit -> done                            */
+    int64_t est_bytes;           /* admission estimate                        */
+    int64_t handle_bytes;        /* device bytes the solve handle held        */
+} emsurf_result;
+
+EMSURF_API int emsurf_server_create(const emsurf_server_opts* opts, emsurf_server** out);
+/* Admission estimate of a request in bytes of device memory.              */
+EMSURF_API int emsurf_request_bytes(const emsurf_request* req, int64_t* bytes);
+/* Queue a request (its small arrays are copied; x_out is not).  EBUSY if
+ * its estimate exceeds the whole budget or the server is stopping.        */
+EMSURF_API int emsurf_submit(emsurf_server* s, const emsurf_request* req, uint64_t* ticket);
+/* EAGAIN while queued or running; OK with the result once done (the ticket
+ * is then forgotten); EINVAL for an unknown ticket.                       */
+EMSURF_API int emsurf_poll(emsurf_server* s, uint64_t ticket, emsurf_result* out);
+/* As poll, but blocks up to timeout_ms; ETIMEDOUT if not done by then.    */
+EMSURF_API int emsurf_wait(emsurf_server* s, uint64_t ticket, int64_t timeout_ms,
+                           emsurf_result* out);
+/* Stops accepting requests, finishes the queued and running ones, frees. */
+EMSURF_API void emsurf_server_destroy(emsurf_server* s);
 
 /* Thread-local message of the last failing call on this thread.          */
 EMSURF_API const char* emsurf_last_error(void);

@@ -38,7 +38,7 @@ class Problem(C.Structure):
         ("uo_index", C.c_void_p), ("uo_sign", C.c_void_p),
         ("grid_px", C.c_int32), ("grid_py", C.c_int32),
         ("precision", C.c_int32), ("tables_on_device", C.c_int32),
-        ("device_mem_budget", C.c_int64), ("device", C.c_int32),
+        ("device_mem_budget", C.c_int64), ("device", C.c_int32), ("stream", C.c_void_p),
     ]
 
 
@@ -167,6 +167,7 @@ def emsurf_create(nx, ny, n_edges, n_unique, type_map, macromodels, offset_L, of
     p.tables_on_device = 1 if tables_on_device else 0
     p.device_mem_budget = device_mem_budget
     p.device = device
+    p.stream = None
     out = C.c_void_p()
     _check(lib().emsurf_create(C.byref(p), C.byref(out)))
     return Handle(out.value, (type_map, uo_index, uo_sign))
@@ -319,3 +320,117 @@ def emsurf_launch_count(h):
 def emsurf_check(h):
     """emsurf_check: raises EmsurfError(ETIMEDOUT) if a bounded device wait expired."""
     _check(lib().emsurf_check(h.ptr))
+
+
+# ------------------------------------------------------------------ serving
+class ServerOpts(C.Structure):
+    _fields_ = [("device", C.c_int32), ("device_mem_budget", C.c_int64), ("max_active", C.c_int32)]
+
+
+class Request(C.Structure):
+    _fields_ = [("a", C.c_double), ("b", C.c_double), ("h", C.c_double), ("n", C.c_int32),
+                ("nx", C.c_int32), ("ny", C.c_int32), ("k0", C.c_double), ("n_types", C.c_int32),
+                ("patch_sides", C.c_void_p), ("patch_z", C.c_double), ("patch_n", C.c_int32),
+                ("type_map", C.c_void_p), ("nrhs", C.c_int32), ("khat", C.c_void_p),
+                ("ehat", C.c_void_p), ("precision", C.c_int32), ("opts", SolveOpts),
+                ("x_out", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("n_unique", C.c_int32), ("nrhs", C.c_int32),
+                ("info", SolveInfo), ("queue_ms", C.c_double), ("setup_ms", C.c_double),
+                ("solve_ms", C.c_double), ("latency_ms", C.c_double), ("est_bytes", C.c_int64),
+                ("handle_bytes", C.c_int64)]
+
+
+def _serve_lib():
+    L = lib()
+    if not getattr(L, "_serve_ready", False):
+        vp = C.c_void_p
+        L.emsurf_server_create.argtypes = [C.POINTER(ServerOpts), C.POINTER(vp)]
+        L.emsurf_request_bytes.argtypes = [C.POINTER(Request), C.POINTER(C.c_int64)]
+        L.emsurf_submit.argtypes = [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]
+        L.emsurf_poll.argtypes = [vp, C.c_uint64, C.POINTER(Result)]
+        L.emsurf_wait.argtypes = [vp, C.c_uint64, C.c_int64, C.POINTER(Result)]
+        L.emsurf_server_destroy.argtypes = [vp]
+        L.emsurf_server_destroy.restype = None
+        L._serve_ready = True
+    return L
+
+
+class Server:
+    """Owns an emsurf_server; keeps each request's arrays alive until collected."""
+
+    def __init__(self, ptr):
+        self.ptr = ptr
+        self.keep = {}
+
+    def close(self):
+        if self.ptr:
+            _serve_lib().emsurf_server_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def emsurf_server_create(device=0, device_mem_budget=0, max_active=2):
+    o = ServerOpts(device, device_mem_budget, max_active)
+    out = C.c_void_p()
+    _check(_serve_lib().emsurf_server_create(C.byref(o), C.byref(out)))
+    return Server(out.value)
+
+
+def make_request(a, b, h, n, nx, ny, k0, patch_sides, patch_z, patch_n, type_map, khat, ehat,
+                 precision=MIXED, rtol=1e-6, restart=30, max_iters=20000, max_refine=20,
+                 inner_rtol=0.0, solver=0, x_out=None):
+    """Build an emsurf_request; returns (Request, arrays that must stay alive)."""
+    sides = np.ascontiguousarray(patch_sides, dtype=np.float64)
+    tmap = np.ascontiguousarray(type_map, dtype=np.int32)
+    kh = np.ascontiguousarray(np.atleast_2d(khat), dtype=np.float64)
+    eh = np.ascontiguousarray(np.atleast_2d(ehat), dtype=np.float64)
+    q = Request(a, b, h, n, nx, ny, k0, len(sides), _ptr(sides), patch_z, patch_n, _ptr(tmap),
+                len(kh), _ptr(kh), _ptr(eh), precision,
+                SolveOpts(rtol, restart, max_iters, max_refine, inner_rtol, solver), _ptr(x_out))
+    return q, (sides, tmap, kh, eh, x_out)
+
+
+def emsurf_request_bytes(req):
+    nb = C.c_int64()
+    _check(_serve_lib().emsurf_request_bytes(C.byref(req), C.byref(nb)))
+    return nb.value
+
+
+def emsurf_submit(server, req, keep=()):
+    """emsurf_submit: returns the ticket; EmsurfError(EBUSY) if never admissible."""
+    t = C.c_uint64()
+    _check(_serve_lib().emsurf_submit(server.ptr, C.byref(req), C.byref(t)))
+    server.keep[t.value] = keep
+    return t.value
+
+
+def _result(r):
+    d = {f: getattr(r, f) for f, _ in Result._fields_ if f != "info"}
+    d["info"] = {f: getattr(r.info, f) for f, _ in SolveInfo._fields_}
+    return d
+
+
+def emsurf_poll(server, ticket):
+    """emsurf_poll: None while pending, else the result dict."""
+    r = Result()
+    st = _check(_serve_lib().emsurf_poll(server.ptr, ticket, C.byref(r)), ok=(EMSURF_OK, EMSURF_EAGAIN))
+    if st == EMSURF_EAGAIN:
+        return None
+    server.keep.pop(ticket, None)
+    return _result(r)
+
+
+def emsurf_wait(server, ticket, timeout_ms=600000):
+    """emsurf_wait: the result dict; EmsurfError(ETIMEDOUT) if not done in time."""
+    r = Result()
+    _check(_serve_lib().emsurf_wait(server.ptr, ticket, int(timeout_ms), C.byref(r)))
+    server.keep.pop(ticket, None)
+    return _result(r)

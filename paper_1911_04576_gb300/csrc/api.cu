@@ -118,12 +118,13 @@ int validate(const emsurf_problem* p) {
 template <typename T>
 int upload(emsurf_handle* h, T** d, const T* src, size_t n) {
     EMS_TRY(dev_alloc(h, (void**)d, n * sizeof(T)));
-    EMS_CUDA(cudaMemcpy(*d, src, n * sizeof(T), cudaMemcpyHostToDevice));
+    EMS_CUDA(cudaMemcpyAsync(*d, src, n * sizeof(T), cudaMemcpyHostToDevice, h->setup_stream));
     return EMSURF_OK;
 }
 
 int create_impl(const emsurf_problem* p, emsurf_handle* h) {
     h->device = p->device;
+    h->setup_stream = reinterpret_cast<cudaStream_t>(p->stream);
     h->nx = p->nx;
     h->ny = p->ny;
     h->E = p->n_edges;
@@ -139,7 +140,7 @@ int create_impl(const emsurf_problem* p, emsurf_handle* h) {
     h->nbins = h->px * h->py;
     EMS_CUDA(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
     EMS_TRY(dev_alloc(h, (void**)&h->d_err, sizeof(int)));
-    EMS_CUDA(cudaMemset(h->d_err, 0, sizeof(int)));
+    EMS_CUDA(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->setup_stream));
     EMS_TRY(fft_plan_create(h->plan_x, h->px));
     EMS_TRY(fft_plan_create(h->plan_y, h->py));
     const int M = h->M, K = h->K;
@@ -194,11 +195,14 @@ int create_impl(const emsurf_problem* p, emsurf_handle* h) {
         EMS_TRY(build_operator<double2>(h, h->op64, p));
         h->have64 = true;
     }
-    if (h->precision == EMSURF_FP32 || h->precision == EMSURF_MIXED) {
+    if (h->precision == EMSURF_FP32) {
         EMS_TRY(build_operator<float2>(h, h->op32, p));
         h->have32 = true;
+    } else if (h->precision == EMSURF_MIXED) {
+        EMS_TRY(derive_fp32_operator(h, p));
+        h->have32 = true;
     }
-    EMS_CUDA(cudaDeviceSynchronize());
+    EMS_CUDA(cudaStreamSynchronize(h->setup_stream));
     return EMSURF_OK;
 }
 
@@ -252,7 +256,7 @@ EMSURF_API int emsurf_create(const emsurf_problem* problem, emsurf_handle** out)
     if (!h) { set_error("host allocation failed"); return EMSURF_ENOMEM; }
     const int s = create_impl(problem, h);
     if (s != EMSURF_OK) {
-        cudaDeviceSynchronize();
+        cudaStreamSynchronize(h->setup_stream);
         gmres_release(h);
         free_handle(h);
         return s;

@@ -166,6 +166,7 @@ struct emsurf_handle {
     emsurf::Operator<float2> op32;
     bool have64 = false, have32 = false;
     int num_sms = 0;
+    cudaStream_t setup_stream = nullptr;   // stream of the create-time work
     int* d_err = nullptr;             // device error flag of bounded waits (0 = ok)
     // GMRES workspace (FP64), allocated lazily by emsurf_solve
     void* gm = nullptr;
@@ -195,6 +196,7 @@ int tabulate_blocks(const MeshView& test, const MeshView& src, const double* shi
                     cudaStream_t st);
 template <typename T2>
 int build_operator(emsurf_handle* h, Operator<T2>& op, const emsurf_problem* pr);
+int derive_fp32_operator(emsurf_handle* h, const emsurf_problem* pr);
 template <typename T2>
 int apply_operator(emsurf_handle* h, Operator<T2>& op, const double2* x, double2* y, int nrhs,
                    cudaStream_t st);

@@ -161,7 +161,10 @@ __device__ __forceinline__ double2 block_sum(double2 v, double2* red /* [blockDi
 // After every block wrote its partials: returns true in the last block to
 // arrive (classic threadfence reduction); that block resets the counter.
 __device__ __forceinline__ bool last_block(unsigned* counter, bool* flag) {
+    // every thread that wrote a partial makes it visible, then the whole
+    // block has finished writing before thread 0 announces it
     __threadfence();
+    __syncthreads();
     if (threadIdx.x == 0) *flag = atomicAdd(counter, 1u) == gridDim.x - 1;
     __syncthreads();
     if (*flag) {
@@ -495,6 +498,7 @@ int gm_alloc(emsurf_handle* h, Gm*& gm, int m, int R) {
     EMS_TRY(dev_alloc(h, (void**)&g->counter, sizeof(unsigned) * RR));
     EMS_TRY(dev_alloc(h, (void**)&g->reorth, sizeof(int) * RR));
     EMS_CUDA(cudaMemset(g->counter, 0, sizeof(unsigned) * RR));
+    EMS_CUDA(cudaDeviceSynchronize());   // the counters must be zero before any solve stream uses them
     g->nblk = (int)std::max<size_t>(2 * 152, (g->n + kArnChunkMax - 1) / kArnChunkMax);
     g->chunk = (int)((g->n + g->nblk - 1) / g->nblk);
     EMS_TRY(dev_alloc(h, (void**)&g->part,

@@ -385,7 +385,7 @@ int build_operator(emsurf_handle* h, Operator<T2>& op, const emsurf_problem* pr)
     } else {
         EMS_CUDA(cudaMalloc(&B64, bbytes64));
     }
-    cudaStream_t st = 0;
+    cudaStream_t st = h->setup_stream;
     EMS_CUDA(cudaMemsetAsync(B64, 0, bbytes64, st));
     // stage offsets in chunks of <= 256 MB
     const size_t per_off = 2 * EE * sizeof(double2);
@@ -440,7 +440,7 @@ int build_operator(emsurf_handle* h, Operator<T2>& op, const emsurf_problem* pr)
         zstage = const_cast<double2*>(reinterpret_cast<const double2*>(pr->macromodels));
     } else {
         EMS_CUDA(cudaMalloc(&zstage, zbytes));
-        EMS_CUDA(cudaMemcpy(zstage, pr->macromodels, zbytes, cudaMemcpyHostToDevice));
+        EMS_CUDA(cudaMemcpyAsync(zstage, pr->macromodels, zbytes, cudaMemcpyHostToDevice, st));
     }
     EMS_TRY(dev_alloc(h, (void**)&op.Zt, (size_t)h->T * K * K * sizeof(T2)));
     dim3 zg((K + 31) / 32, (K + 31) / 32, h->T);
@@ -455,6 +455,29 @@ int build_operator(emsurf_handle* h, Operator<T2>& op, const emsurf_problem* pr)
     EMS_TRY(dev_alloc(h, (void**)&op.Ymm, (size_t)kMmSplit * h->max_rhs * h->M * K * sizeof(T2)));
     EMS_TRY(dev_alloc(h, (void**)&op.Y1, (size_t)h->max_rhs * h->M * K * sizeof(T2)));
     for (int c = 0; c < 4; ++c) op.coef[c] = mk<T2>(pr->coef[c].re, pr->coef[c].im);
+    return EMSURF_OK;
+}
+
+// FP32 operator of a MIXED handle: round the resident FP64 spectrum and
+// macromodels instead of transforming the tables a second time.
+int derive_fp32_operator(emsurf_handle* h, const emsurf_problem* pr) {
+    const int K = h->K;
+    const size_t EE = (size_t)h->E * h->E;
+    const size_t nb = (size_t)h->nbins;
+    cudaStream_t st = h->setup_stream;
+    Operator<float2>& op = h->op32;
+    EMS_TRY(dev_alloc(h, (void**)&op.Bhat, nb * 2 * EE * sizeof(float2)));
+    round_kernel<<<152 * 8, 256, 0, st>>>(op.Bhat, h->op64.Bhat, nb * 2 * EE);
+    EMS_CUDA(cudaGetLastError());
+    EMS_TRY(dev_alloc(h, (void**)&op.Zt, (size_t)h->T * K * K * sizeof(float2)));
+    round_kernel<<<152 * 8, 256, 0, st>>>(op.Zt, h->op64.Zt, (size_t)h->T * K * K);
+    EMS_CUDA(cudaGetLastError());
+    const size_t grid_elems = nb * (size_t)h->max_rhs * K;
+    EMS_TRY(dev_alloc(h, (void**)&op.Xg, grid_elems * sizeof(float2)));
+    EMS_TRY(dev_alloc(h, (void**)&op.Yg, grid_elems * sizeof(float2)));
+    EMS_TRY(dev_alloc(h, (void**)&op.Ymm, (size_t)kMmSplit * h->max_rhs * h->M * K * sizeof(float2)));
+    EMS_TRY(dev_alloc(h, (void**)&op.Y1, (size_t)h->max_rhs * h->M * K * sizeof(float2)));
+    for (int c = 0; c < 4; ++c) op.coef[c] = mk<float2>(pr->coef[c].re, pr->coef[c].im);
     return EMSURF_OK;
 }
 

@@ -1,0 +1,84 @@
+"""Serving (emsurf_submit / emsurf_poll): requests of uneven lattice size and
+right-hand-side count run concurrently on one GPU; each result equals the
+result of the same request solved alone; admission refuses requests that can
+never fit; polling reports pending and unknown tickets."""
+import numpy as np
+import pytest
+
+from paper_1911_04576_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+A, H = W.PERIOD, W.BOX_H
+
+
+def _requests(B):
+    rng = np.random.default_rng(42)
+    specs = [(2, 2, 2, 1), (3, 3, 2, 2), (4, 3, 3, 1), (2, 5, 2, 3), (3, 2, 3, 2)]
+    out = []
+    for nx, ny, n, R in specs:
+        T = 3
+        sides = rng.uniform(0.15, 0.45, T) * W.LAMBDA
+        sides[0] = 0.0                                        # one empty type
+        tmap = rng.integers(0, T, nx * ny)
+        waves = [W.plane_waves(W.Workload("w", 1, 1, 1, 1, 0, 0, angles=[(th, ph, "theta")]))[0]
+                 for th, ph in zip(rng.uniform(0, 50, R), rng.uniform(0, 360, R))]
+        kh = np.array([w_[0] for w_ in waves])
+        eh = np.array([w_[1] for w_ in waves])
+        _, _, nu = B.emsurf_setup_overlap(n, nx, ny)
+        out.append(dict(a=A, b=A, h=H, n=n, nx=nx, ny=ny, k0=W.K0, patch_sides=sides,
+                        patch_z=W.PATCH_Z, patch_n=3, type_map=tmap, khat=kh, ehat=eh,
+                        precision=B.MIXED, rtol=1e-9, restart=30, max_iters=6000, nu=nu, R=R))
+    return out
+
+
+def _run(B, reqs, max_active):
+    sv = B.emsurf_server_create(0, 0, max_active)
+    xs, tickets = [], []
+    for r in reqs:
+        x = np.zeros((r["R"], r["nu"]), np.complex128)
+        kw = {k: v for k, v in r.items() if k not in ("nu", "R")}
+        q, keep = B.make_request(x_out=x, **kw)
+        tickets.append(B.emsurf_submit(sv, q, keep))
+        xs.append(x)
+    res = [B.emsurf_wait(sv, t, 600000) for t in tickets]
+    sv.close()
+    return xs, res
+
+
+def test_each_result_same_alone_and_in_the_mix(emsurf_lib):
+    from paper_1911_04576_gb300 import binding as B
+    reqs = _requests(B)
+    xs_mix, res_mix = _run(B, reqs, 3)
+    for r in res_mix:
+        assert r["status"] == B.EMSURF_OK and r["info"]["converged"] == 1
+        assert r["info"]["rel_residual"] <= 1e-9
+    for i, r in enumerate(reqs):
+        xa, ra = _run(B, [r], 1)
+        assert np.linalg.norm(xa[0] - xs_mix[i]) <= 1e-12 * np.linalg.norm(xa[0])
+
+
+def test_admission_and_polling(emsurf_lib):
+    from paper_1911_04576_gb300 import binding as B
+    r = _requests(B)[0]
+    kw = {k: v for k, v in r.items() if k not in ("nu", "R")}
+    q, keep = B.make_request(**kw)
+    need = B.emsurf_request_bytes(q)
+    # a budget below one request's estimate: refused at submit
+    sv = B.emsurf_server_create(0, need // 2, 2)
+    with pytest.raises(B.EmsurfError) as e:
+        B.emsurf_submit(sv, q, keep)
+    assert e.value.status == B.EMSURF_EBUSY
+    sv.close()
+    # a budget that fits one request at a time: both still complete
+    sv = B.emsurf_server_create(0, int(need * 1.5), 2)
+    t1 = B.emsurf_submit(sv, q, keep)
+    t2 = B.emsurf_submit(sv, q, keep)
+    first = B.emsurf_poll(sv, t1)                   # normally still pending
+    r1 = first if first is not None else B.emsurf_wait(sv, t1, 600000)
+    r2 = B.emsurf_wait(sv, t2, 600000)
+    assert r1["status"] == B.EMSURF_OK and r2["status"] == B.EMSURF_OK
+    with pytest.raises(B.EmsurfError) as e:
+        B.emsurf_poll(sv, t1)                       # collected already
+    assert e.value.status == B.EMSURF_EINVAL
+    sv.close()
