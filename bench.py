@@ -8,10 +8,12 @@ plane wave at 10 GHz.  Every input is built on the product path: overlap
 map (C++ setup), offset tables and macromodels (GPU tabulation and Schur
 complement), excitation (GPU).
 
-A step is one solve to relative residual 1e-6: GMRES(30) with the FP32
-operator inside FP64 residual refinement (MIXED).  The FP64-plain solve,
-the matvec rates, the CPU oracle and an end-to-end call with host buffers
-are measured beside it.  One JSON line on rank 0.
+A step is one solve to relative residual 1e-6: flexible GMRES(30),
+right-preconditioned by the near-field preconditioner (restricted additive
+Schwarz by cells, one mesh layer of overlap), with the FP32 operator inside
+FP64 residual refinement (MIXED).  The unpreconditioned MIXED and FP64
+solves, the matvec rates, the CPU oracle and an end-to-end call with host
+buffers are measured beside it.  One JSON line on rank 0.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -37,6 +39,7 @@ RESTART = 30
 # measured on GB300; scales the CPU oracle's per-matvec time to a solve.
 REF_MATVECS_PER_SOLVE = 1905
 FALLBACK_HBM_GBS = 6800.0
+PC_OVERLAP = 0.6               # preconditioner margin, in mesh cells (a / n)
 
 
 def peaks():
@@ -108,11 +111,13 @@ def dist_init():
     return ws, rank, local
 
 
-def build_problem(B, W, torch, w, precision):
-    """Product-path setup (untimed): U_o, tables, macromodels, handle, V."""
+def build_problem(B, W, torch, w, precision, precond=True):
+    """Product-path setup (untimed): U_o, tables, macromodels, handle with
+    the near-field preconditioner, V."""
     A, H = W.PERIOD, W.BOX_H
     coef = (1j * W.K0, 1.0, -1.0, 1j * W.K0)
     idx, sgn, nu = B.emsurf_setup_overlap(w.n, w.nx, w.ny)
+    xy = B.emsurf_setup_unknown_xy(A, A, H, w.n, w.nx, w.ny, idx, nu) if precond else None
     L = torch.empty((2 * w.ny - 1, 2 * w.nx - 1, w.E, w.E), dtype=torch.complex128, device="cuda")
     K = torch.empty_like(L)
     t0 = time.time()
@@ -124,7 +129,9 @@ def build_problem(B, W, torch, w, precision):
     t_mm = time.time() - t0
     t0 = time.time()
     h = B.emsurf_create(w.nx, w.ny, w.E, nu, W.type_map(w), Z, L, K, coef, idx, sgn,
-                        precision=precision, max_rhs=w.n_rhs, tables_on_device=True)
+                        precision=precision, max_rhs=w.n_rhs, tables_on_device=True,
+                        unknown_xy=xy, cell=(A, A),
+                        precond_overlap=PC_OVERLAP * A / w.n if precond else 0.0)
     torch.cuda.synchronize()
     t_create = time.time() - t0
     del L, K, Z
@@ -176,7 +183,7 @@ SERVE_RATE = 20.0              # Poisson arrivals per second
 SERVE_BUDGET = 80 << 30        # device-memory budget of the server
 
 
-def serve_stream(B, W, nreq, seed, precision, max_active):
+def serve_stream(B, W, nreq, seed, precision, max_active, precond):
     """Submit a seeded Poisson stream of solve requests at their arrival
     times, wait for all, return latency percentiles and throughput."""
     rng = np.random.default_rng(seed)
@@ -195,7 +202,8 @@ def serve_stream(B, W, nreq, seed, precision, max_active):
                          patch_sides=lib_sides, patch_z=W.PATCH_Z, patch_n=4,
                          type_map=rng.integers(0, 32, N * N), khat=np.array([w_[0] for w_ in waves]),
                          ehat=np.array([w_[1] for w_ in waves]), precision=precision, rtol=RTOL,
-                         restart=RESTART, max_iters=20000, max_refine=20))
+                         restart=RESTART, max_iters=20000, max_refine=20,
+                         precond_overlap=PC_OVERLAP * W.PERIOD / n if precond else 0.0))
     sv = B.emsurf_server_create(0, SERVE_BUDGET, max_active)
     tickets = []
     t0 = time.perf_counter()
@@ -216,7 +224,7 @@ def serve_stream(B, W, nreq, seed, precision, max_active):
             "throughput_rps": round(nreq / makespan, 3), "makespan_s": round(makespan, 2),
             "solve_ms_mean": round(float(np.mean([r["solve_ms"] for r in res])), 1),
             "queue_ms_mean": round(float(np.mean([r["queue_ms"] for r in res])), 1),
-            "all_converged": ok, "max_active": max_active}
+            "all_converged": ok, "max_active": max_active, "precond": precond}
 
 
 def reference_arm(args, W, w):
@@ -308,12 +316,22 @@ def main():
     h, V, nu, setup = build_problem(B, W, torch, w, B.MIXED)
     X = torch.zeros_like(V)
     hbm, peak_kind = peaks()
-    # FP64-plain reference solve on the same handle (FP64 operator GMRES)
+    # FP64-plain reference solve on the same handle (FP64 operator GMRES,
+    # no preconditioner), and the unpreconditioned MIXED solve
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     st64, info64 = B.emsurf_solve(h, V, X, rtol=RTOL, restart=RESTART, max_iters=20000,
-                                  solver=B.SOLVER_FP64)
+                                  solver=B.SOLVER_FP64, precond=-1)
     t64 = (time.perf_counter() - t0) * 1e3
+    t0 = time.perf_counter()
+    stnp, infonp = B.emsurf_solve(h, V, X, rtol=RTOL, restart=RESTART, max_iters=20000,
+                                  max_refine=20, solver=B.SOLVER_MIXED, precond=-1)
+    tnp = (time.perf_counter() - t0) * 1e3
+    t0 = time.perf_counter()
+    st64p, info64p = B.emsurf_solve(h, V, X, rtol=RTOL, restart=RESTART, max_iters=20000,
+                                    solver=B.SOLVER_FP64)
+    t64p = (time.perf_counter() - t0) * 1e3
+    pc_elems, pc_subtot, pc_nmax = B.emsurf_precond_info(h)
     # matvec rates
     R = w.n_rhs
     mv32 = time_matvec(B, torch, h, nu, R, B.FP32)
@@ -354,6 +372,7 @@ def main():
     bin64_ms, bin64_n = B.emsurf_profile_read(h, "binmul64")
     arn_ms, _ = B.emsurf_profile_read(h, "arnoldi")
     sct_ms, _ = B.emsurf_profile_read(h, "scatter")
+    pc_ms, pc_n = B.emsurf_profile_read(h, "precond")
     fft64_ms, _ = B.emsurf_profile_read(h, "fft64")
     mm64_ms, _ = B.emsurf_profile_read(h, "mm64")
     ms = ms_total / args.steps
@@ -383,8 +402,8 @@ def main():
         serve = {"stream": "Poisson %.0f/s; lattices %s, K %s, rhs %s, 32-type library; rtol %g"
                            % (SERVE_RATE, list(SERVE_SIZES), [36 * m * m for m in SERVE_MESH],
                               list(SERVE_RHS), RTOL),
-                 "mixed_batched": serve_stream(B, W, args.serve_requests, 7, B.MIXED, 4),
-                 "fp64_one_at_a_time": serve_stream(B, W, args.serve_requests, 7, B.FP64, 1)}
+                 "mixed_batched": serve_stream(B, W, args.serve_requests, 7, B.MIXED, 4, True),
+                 "fp64_one_at_a_time": serve_stream(B, W, args.serve_requests, 7, B.FP64, 1, False)}
     # ------------------------------------------------------------ CPU oracle
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         t_cpu = cpu_oracle_matvec_seconds(W, w, nu)
@@ -402,6 +421,10 @@ def main():
     bin_avg = bin_ms / max(bin_n, 1)
     alg_bin = 2 * w.E * w.E * P * 8 + 2 * R * w.K * P * 8
     achieved = alg_bin / (bin_avg * 1e-3) / 1e9
+    # preconditioner apply: FP32 LU factors once, r gathered, owned rows written
+    pc_avg = pc_ms / max(pc_n, 1)
+    alg_pc = pc_elems * 8 + R * (pc_subtot * 16 + pc_subtot * 8 + nu * 16)
+    pc_achieved = alg_pc / (pc_avg * 1e-3) / 1e9 if pc_n else None
     last = infos[-1]
     out = {
         "metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": ws, "steps": args.steps,
@@ -409,7 +432,9 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "K": w.K, "n_types": w.n_types,
                    "nrhs": R, "unknowns": nu, "grid": [px, py], "rtol": RTOL, "restart": RESTART,
-                   "solver": "GMRES(30) with FP32 operator inside FP64 residual refinement",
+                   "solver": "flexible GMRES(30), near-field RAS preconditioner (overlap %.1f "
+                             "mesh cells), FP32 operator inside FP64 residual refinement"
+                             % PC_OVERLAP,
                    "l2": "inputs larger than L2: %.2f GB complex64 + %.2f GB complex128 "
                          "Fourier-domain blocks" % (bytes32 / 1e9, bytes64 / 1e9),
                    "parallelism": "replicas" if ws > 1 else "single"},
@@ -418,7 +443,19 @@ def main():
                   "converged": last["converged"]},
         "fp64_plain": {"solve_ms": round(t64, 3), "iters": info64[0]["iters"],
                        "n_matvec": info64[0]["n_matvec"], "rel_residual": info64[0]["rel_residual"],
-                       "converged": info64[0]["converged"], "speedup_mixed": round(t64 / ms, 3)},
+                       "converged": info64[0]["converged"], "speedup": round(t64 / ms, 3)},
+        "mixed_unpreconditioned": {"solve_ms": round(tnp, 3), "iters": infonp[0]["iters"],
+                                   "n_matvec": infonp[0]["n_matvec"],
+                                   "converged": infonp[0]["converged"]},
+        "fp64_preconditioned": {"solve_ms": round(t64p, 3), "iters": info64p[0]["iters"],
+                                "n_matvec": info64p[0]["n_matvec"],
+                                "converged": info64p[0]["converged"]},
+        "precond": {"overlap_mesh_cells": PC_OVERLAP, "factor_entries": pc_elems,
+                    "subdomain_total": pc_subtot, "max_subdomain": pc_nmax,
+                    "apply_ms": round(pc_avg, 5) if pc_n else None,
+                    "apply_gbs": round(pc_achieved, 1) if pc_n else None,
+                    "apply_frac": round(pc_achieved / hbm, 4) if pc_n else None,
+                    "alg_bytes_per_apply": alg_pc},
         "matvec": {"fp32_ms": round(mv32, 4), "fp32_gbs": round(bytes32 / mv32 / 1e6, 1),
                    "fp64_ms": round(mv64, 4), "fp64_gbs": round(bytes64 / mv64 / 1e6, 1),
                    "alg_bytes_fp32": bytes32, "alg_bytes_fp64": bytes64},
@@ -433,7 +470,8 @@ def main():
                                 "binmul64": round(bin64_ms / args.steps, 3),
                                 "fft64+mm64": round((fft64_ms + mm64_ms) / args.steps, 3),
                                 "arnoldi": round(arn_ms / args.steps, 3),
-                                "scatter": round(sct_ms / args.steps, 3)},
+                                "scatter": round(sct_ms / args.steps, 3),
+                                "precond": round(pc_ms / args.steps, 3)},
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": int(V.numel() * 16),
                 "d2h_bytes_per_step": int(V.numel() * 16)},

@@ -91,6 +91,16 @@ typedef struct {
     void* stream;                /* CUDA stream for the setup work of
                                     emsurf_create (NULL = legacy default);
                                     create synchronises it before returning */
+    /* Near-field preconditioner (Eq. final_precond), built when
+     * precond_overlap > 0 and unknown_xy != NULL: restricted additive
+     * Schwarz over cell subdomains, subdomain m = unknowns whose RWG edge
+     * midpoint lies in cell m's footprint (cell_a x cell_b, centred at
+     * (ix*cell_a, iy*cell_b)) grown by precond_overlap metres.  unknown_xy:
+     * host [n_unique][2] edge-midpoint x, y of each unique unknown
+     * (emsurf_setup_unknown_xy).  At most 1100 unknowns per subdomain.      */
+    const double* unknown_xy;
+    double cell_a, cell_b;
+    double precond_overlap;
 } emsurf_problem;
 
 typedef struct {
@@ -102,6 +112,8 @@ typedef struct {
     int32_t solver;       /* 0: by handle precision; 1: FP64-operator GMRES;
                              2: FP32-operator GMRES; 3: mixed refinement.
                              The operators it needs must be resident.         */
+    int32_t precond;      /* 0: right-precondition with the handle's near-field
+                             preconditioner if it was built; -1: do not      */
 } emsurf_solve_opts;
 
 typedef struct {
@@ -135,6 +147,20 @@ EMSURF_API int emsurf_solve(emsurf_handle* h, const emsurf_c128* b, emsurf_c128*
                             int32_t nrhs, const emsurf_solve_opts* opts,
                             emsurf_solve_info* info, void* stream);
 
+/* y = M^{-1} r with the handle's near-field preconditioner (restricted
+ * additive Schwarz over cells, the grouping of Eq. final_precond's near
+ * field used here): y = sum_m Rt_m^T A_m^{-1} R_m r, A_m the exact block of
+ * Eq. final on subdomain m, factored in complex FP32.  r, y: device
+ * [nrhs][n_unique] complex128, must not overlap; nrhs <= max_rhs.
+ * Errors: EINVAL (no preconditioner built, bad nrhs or pointers).        */
+EMSURF_API int emsurf_precond_apply(emsurf_handle* h, const emsurf_c128* r, emsurf_c128* y,
+                                    int32_t nrhs, void* stream);
+
+/* Sizes of the near-field preconditioner: sum over cells of n_m^2 (complex
+ * FP32 factor entries), sum of n_m, and the largest n_m; all 0 if none.   */
+EMSURF_API int emsurf_precond_info(const emsurf_handle* h, int64_t* factor_entries,
+                                   int64_t* subdomain_total, int32_t* max_subdomain);
+
 /* Grid chosen by emsurf_create, unknown count and bytes of device memory
  * held by the handle.                                                     */
 EMSURF_API int emsurf_query(const emsurf_handle* h, int32_t* grid_px, int32_t* grid_py,
@@ -148,7 +174,8 @@ EMSURF_API void emsurf_destroy(emsurf_handle* h);
  * recording; 0 stops.  Phases: 0 bin multiply FP32, 1 bin multiply FP64,
  * 2 macromodel multiply FP32, 3 macromodel FP64, 4 FFT passes + gather FP32,
  * 5 the same FP64, 6 Arnoldi orthogonalisation/norm/Givens kernels of
- * emsurf_solve, 7 crop + U_o^T scatter of emsurf_matvec.  emsurf_profile_read synchronises on the recorded events
+ * emsurf_solve, 7 crop + U_o^T scatter of emsurf_matvec, 8 near-field
+ * preconditioner applications of emsurf_solve.  emsurf_profile_read synchronises on the recorded events
  * and returns the summed milliseconds and the number of intervals.       */
 EMSURF_API int emsurf_profile(emsurf_handle* h, int32_t enable);
 EMSURF_API int emsurf_profile_read(emsurf_handle* h, int32_t phase, double* total_ms,
@@ -195,6 +222,13 @@ EMSURF_API int emsurf_setup_patch_counts(int32_t n, int32_t* n_verts, int32_t* n
 EMSURF_API int emsurf_setup_patch_mesh(double side, double z, int32_t n, double* verts,
                                        int32_t* tris, int32_t* edges, int32_t* tplus,
                                        int32_t* tminus, int32_t* slot_rwg, int8_t* slot_sgn);
+
+/* Edge-midpoint (x, y) of every unique unknown of an nx x ny lattice
+ * (box of cell (ix,iy) centred at (ix*a, iy*b)), from the canonical box
+ * mesh and the overlap map: xy host [n_unique][2].                        */
+EMSURF_API int emsurf_setup_unknown_xy(double a, double b, double h, int32_t n, int32_t nx,
+                                       int32_t ny, const int32_t* uo_index, int32_t n_unique,
+                                       double* xy);
 
 /* U_o of Eq. connections_IUI (Sec. III-D, rule 1 with Delta -> 0 of
  * Fig. connections) for an nx x ny lattice of boxes meshed n x n per face:
@@ -322,6 +356,8 @@ typedef struct {
     emsurf_solve_opts opts;
     emsurf_c128* x_out;          /* host [nrhs][n_unique] or NULL; must stay
                                     valid until the result is collected       */
+    double precond_overlap;      /* near-field preconditioner margin (m),
+                                    <= 0: none                                */
 } emsurf_request;
 
 typedef struct {

@@ -21,6 +21,9 @@ step by step, in plain NumPy/SciPy, without blocking, fusion or FFTs:
                      (Eq. MVP) and dense assembly of Eq. final.
 * ``macromodel``  -- per-cell macromodels by Schur complement (Eq. Zmacromodel).
 * ``solve``       -- dense LU and plain restarted GMRES for Eq. final.
+* ``precond``     -- the cell-grouped near-field preconditioner (Sec. IV-A,
+                     Eq. final_precond) as restricted additive Schwarz with
+                     dense complex128 subdomain solves.
 
 Parity status of each function is stated in its module header.
 """

@@ -1,0 +1,64 @@
+"""Near-field preconditioner by cell subdomains (oracle; test infrastructure only).
+
+Sec. IV-A preconditions Eq. final on the right with the near-field part of
+the system (Eq. final_precond: entries between basis functions closer than a
+threshold).  The preconditioner checked here groups that near field by cell
+and applies it as restricted additive Schwarz (Cai & Sarkis 1999):
+
+* position of a unique unknown: the midpoint of its RWG edge in the first
+  cell that references it (all copies merged by U_o share that edge, so any
+  copy gives the same point);
+* owner of a unique unknown: the first cell that references it (cells
+  scanned m = iy*Nx + ix, local unknowns in order);
+* subdomain S_m: every unique unknown whose position lies in cell m's
+  footprint [-a/2, a/2] x [-b/2, b/2] (centred on the cell's shift) grown by
+  the margin delta on each side;
+* M^{-1} r = sum_m Rt_m^T A[S_m, S_m]^{-1} r[S_m], where Rt_m keeps only the
+  entries of S_m owned by m.
+
+A is the dense matrix of Eq. final (assemble_from_tables).  Everything is
+complex128 with dense solves, so this is the exact-arithmetic definition that
+the device's FP32 factorisation is compared with.
+"""
+import numpy as np
+
+from .lattice import cell_shift
+
+
+def unknown_positions(box, index, nx, ny, a, b):
+    """(xy [n_unique, 2], owner [n_unique]) from the first referencing copy."""
+    E = box.n_rwg
+    Kl = 2 * E
+    n_unique = int(index.max()) + 1
+    mid = 0.5 * (box.verts[box.edges[:, 0]] + box.verts[box.edges[:, 1]])
+    xy = np.zeros((n_unique, 2))
+    owner = -np.ones(n_unique, dtype=np.int64)
+    for m in range(nx * ny):
+        shift = cell_shift(m % nx, m // nx, a, b)
+        for k in range(Kl):
+            u = index[m * Kl + k]
+            if owner[u] < 0:
+                owner[u] = m
+                xy[u] = (mid[k % E] + shift)[:2]
+    return xy, owner
+
+
+def subdomains(xy, owner, nx, ny, a, b, delta, eps=1e-12):
+    """[(S_m sorted unique ids, owned mask)] for every cell m."""
+    out = []
+    for m in range(nx * ny):
+        c = cell_shift(m % nx, m // nx, a, b)
+        inside = (np.abs(xy[:, 0] - c[0]) <= 0.5 * a + delta + eps) & \
+                 (np.abs(xy[:, 1] - c[1]) <= 0.5 * b + delta + eps)
+        S = np.nonzero(inside)[0]
+        out.append((S, owner[S] == m))
+    return out
+
+
+def ras_apply(A, subs, r):
+    """M^{-1} r for one vector r (complex128)."""
+    y = np.zeros(A.shape[0], dtype=np.complex128)
+    for S, own in subs:
+        z = np.linalg.solve(A[np.ix_(S, S)], r[S])
+        y[S[own]] += z[own]
+    return y

@@ -39,12 +39,15 @@ class Problem(C.Structure):
         ("grid_px", C.c_int32), ("grid_py", C.c_int32),
         ("precision", C.c_int32), ("tables_on_device", C.c_int32),
         ("device_mem_budget", C.c_int64), ("device", C.c_int32), ("stream", C.c_void_p),
+        ("unknown_xy", C.c_void_p), ("cell_a", C.c_double), ("cell_b", C.c_double),
+        ("precond_overlap", C.c_double),
     ]
 
 
 class SolveOpts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("restart", C.c_int32), ("max_iters", C.c_int32),
-                ("max_refine", C.c_int32), ("inner_rtol", C.c_double), ("solver", C.c_int32)]
+                ("max_refine", C.c_int32), ("inner_rtol", C.c_double), ("solver", C.c_int32),
+                ("precond", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -77,6 +80,11 @@ def lib():
         L.emsurf_setup_box_mesh.argtypes = [C.c_double, C.c_double, C.c_double, i32, vp] + [vp] * 7
         L.emsurf_setup_patch_mesh.argtypes = [C.c_double, C.c_double, i32] + [vp] * 7
         L.emsurf_setup_overlap.argtypes = [i32, i32, i32, vp, vp, ip]
+        L.emsurf_precond_apply.argtypes = [vp, vp, vp, i32, vp]
+        L.emsurf_precond_info.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                          C.POINTER(i32)]
+        L.emsurf_setup_unknown_xy.argtypes = [C.c_double, C.c_double, C.c_double, i32, i32, i32,
+                                              vp, i32, vp]
         d = C.c_double
         L.emsurf_profile.argtypes = [vp, i32]
         L.emsurf_profile_read.argtypes = [vp, i32, C.POINTER(d), C.POINTER(C.c_int64)]
@@ -144,9 +152,12 @@ class Handle:
 
 def emsurf_create(nx, ny, n_edges, n_unique, type_map, macromodels, offset_L, offset_K, coef,
                   uo_index, uo_sign, precision=FP64, max_rhs=1, grid=(0, 0),
-                  tables_on_device=False, device_mem_budget=0, device=0):
+                  tables_on_device=False, device_mem_budget=0, device=0, unknown_xy=None,
+                  cell=(0.0, 0.0), precond_overlap=0.0):
     """emsurf_create: host NumPy inputs (or torch CUDA tensors for the tables
-    and macromodels when tables_on_device=True); returns a Handle."""
+    and macromodels when tables_on_device=True); returns a Handle.  With
+    unknown_xy ([n_unique, 2] from emsurf_setup_unknown_xy), cell = (a, b) and
+    precond_overlap > 0 the near-field preconditioner is built."""
     type_map = np.ascontiguousarray(type_map, dtype=np.int32)
     uo_index = np.ascontiguousarray(uo_index, dtype=np.int32)
     uo_sign = np.ascontiguousarray(uo_sign, dtype=np.int8)
@@ -168,6 +179,11 @@ def emsurf_create(nx, ny, n_edges, n_unique, type_map, macromodels, offset_L, of
     p.device_mem_budget = device_mem_budget
     p.device = device
     p.stream = None
+    if unknown_xy is not None:
+        unknown_xy = np.ascontiguousarray(unknown_xy, dtype=np.float64)
+        p.unknown_xy = _ptr(unknown_xy)
+    p.cell_a, p.cell_b = cell
+    p.precond_overlap = precond_overlap
     out = C.c_void_p()
     _check(lib().emsurf_create(C.byref(p), C.byref(out)))
     return Handle(out.value, (type_map, uo_index, uo_sign))
@@ -179,14 +195,28 @@ def emsurf_matvec(h, x, y, precision=FP64, stream=None):
     _check(lib().emsurf_matvec(h.ptr, _ptr(x), _ptr(y), nrhs, precision, _stream(stream)))
 
 
+def emsurf_precond_apply(h, r, y, stream=None):
+    """emsurf_precond_apply: r, y torch complex128 CUDA tensors [nrhs, n_unique]."""
+    nrhs = 1 if r.dim() == 1 else r.shape[0]
+    _check(lib().emsurf_precond_apply(h.ptr, _ptr(r), _ptr(y), nrhs, _stream(stream)))
+
+
+def emsurf_precond_info(h):
+    """(factor entries sum n_m^2, sum n_m, max n_m) of the handle's preconditioner."""
+    fe, st, mx = C.c_int64(), C.c_int64(), C.c_int32()
+    _check(lib().emsurf_precond_info(h.ptr, C.byref(fe), C.byref(st), C.byref(mx)))
+    return fe.value, st.value, mx.value
+
+
 SOLVER_DEFAULT, SOLVER_FP64, SOLVER_FP32, SOLVER_MIXED = 0, 1, 2, 3
 
 
 def emsurf_solve(h, b, x, rtol=1e-8, restart=30, max_iters=5000, max_refine=10, inner_rtol=0.0,
-                 solver=SOLVER_DEFAULT, stream=None):
-    """emsurf_solve: returns (status, [info dict per rhs]); ENOTCONV is not raised."""
+                 solver=SOLVER_DEFAULT, stream=None, precond=0):
+    """emsurf_solve: returns (status, [info dict per rhs]); ENOTCONV is not raised.
+    precond = -1 ignores the handle's near-field preconditioner."""
     nrhs = 1 if b.dim() == 1 else b.shape[0]
-    o = SolveOpts(rtol, restart, max_iters, max_refine, inner_rtol, solver)
+    o = SolveOpts(rtol, restart, max_iters, max_refine, inner_rtol, solver, precond)
     info = (SolveInfo * nrhs)()
     st = _check(lib().emsurf_solve(h.ptr, _ptr(b), _ptr(x), nrhs, C.byref(o), info, _stream(stream)),
                 ok=(EMSURF_OK, EMSURF_ENOTCONV))
@@ -228,6 +258,14 @@ def emsurf_setup_patch_mesh(side, z, n):
     out = _mesh_arrays(*_counts(lib().emsurf_setup_patch_counts, n))
     _check(lib().emsurf_setup_patch_mesh(side, z, n, *[_ptr(out[k]) for k in _MESH_KEYS]))
     return out
+
+
+def emsurf_setup_unknown_xy(a, b, h, n, nx, ny, uo_index, n_unique):
+    """emsurf_setup_unknown_xy: [n_unique, 2] edge-midpoint (x, y) per unknown."""
+    idx = np.ascontiguousarray(uo_index, dtype=np.int32)
+    xy = np.zeros((n_unique, 2), np.float64)
+    _check(lib().emsurf_setup_unknown_xy(a, b, h, n, nx, ny, _ptr(idx), n_unique, _ptr(xy)))
+    return xy
 
 
 def emsurf_setup_overlap(n, nx, ny):
@@ -297,7 +335,7 @@ def emsurf_far_field(hd, a, b, h, n, k, Y, rhat, F, rcs=None, stream=None):
 
 
 PHASES = {"binmul32": 0, "binmul64": 1, "mm32": 2, "mm64": 3, "fft32": 4, "fft64": 5,
-          "arnoldi": 6, "scatter": 7}
+          "arnoldi": 6, "scatter": 7, "precond": 8}
 
 
 def emsurf_profile(h, enable):
@@ -333,7 +371,7 @@ class Request(C.Structure):
                 ("patch_sides", C.c_void_p), ("patch_z", C.c_double), ("patch_n", C.c_int32),
                 ("type_map", C.c_void_p), ("nrhs", C.c_int32), ("khat", C.c_void_p),
                 ("ehat", C.c_void_p), ("precision", C.c_int32), ("opts", SolveOpts),
-                ("x_out", C.c_void_p)]
+                ("x_out", C.c_void_p), ("precond_overlap", C.c_double)]
 
 
 class Result(C.Structure):
@@ -386,7 +424,7 @@ def emsurf_server_create(device=0, device_mem_budget=0, max_active=2):
 
 def make_request(a, b, h, n, nx, ny, k0, patch_sides, patch_z, patch_n, type_map, khat, ehat,
                  precision=MIXED, rtol=1e-6, restart=30, max_iters=20000, max_refine=20,
-                 inner_rtol=0.0, solver=0, x_out=None):
+                 inner_rtol=0.0, solver=0, x_out=None, precond_overlap=0.0):
     """Build an emsurf_request; returns (Request, arrays that must stay alive)."""
     sides = np.ascontiguousarray(patch_sides, dtype=np.float64)
     tmap = np.ascontiguousarray(type_map, dtype=np.int32)
@@ -394,7 +432,8 @@ def make_request(a, b, h, n, nx, ny, k0, patch_sides, patch_z, patch_n, type_map
     eh = np.ascontiguousarray(np.atleast_2d(ehat), dtype=np.float64)
     q = Request(a, b, h, n, nx, ny, k0, len(sides), _ptr(sides), patch_z, patch_n, _ptr(tmap),
                 len(kh), _ptr(kh), _ptr(eh), precision,
-                SolveOpts(rtol, restart, max_iters, max_refine, inner_rtol, solver), _ptr(x_out))
+                SolveOpts(rtol, restart, max_iters, max_refine, inner_rtol, solver, 0), _ptr(x_out),
+                precond_overlap)
     return q, (sides, tmap, kh, eh, x_out)
 
 

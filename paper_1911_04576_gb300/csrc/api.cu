@@ -202,6 +202,13 @@ int create_impl(const emsurf_problem* p, emsurf_handle* h) {
         EMS_TRY(derive_fp32_operator(h, p));
         h->have32 = true;
     }
+    if (p->precond_overlap > 0.0 && p->unknown_xy) {
+        if (!(p->cell_a > 0.0) || !(p->cell_b > 0.0)) {
+            set_error("the preconditioner needs cell_a, cell_b > 0");
+            return EMSURF_EINVAL;
+        }
+        EMS_TRY(pc_build(h, p));
+    }
     EMS_CUDA(cudaStreamSynchronize(h->setup_stream));
     return EMSURF_OK;
 }
@@ -293,6 +300,32 @@ EMSURF_API int emsurf_matvec(emsurf_handle* h, const emsurf_c128* x, emsurf_c128
     }
     set_error("matvec precision must be EMSURF_FP64 or EMSURF_FP32");
     return EMSURF_EINVAL;
+}
+
+EMSURF_API int emsurf_precond_info(const emsurf_handle* h, int64_t* factor_entries,
+                                   int64_t* subdomain_total, int32_t* max_subdomain) {
+    if (!h) { set_error("NULL handle"); return EMSURF_EINVAL; }
+    if (factor_entries) *factor_entries = h->have_pc ? h->pc_elems : 0;
+    if (subdomain_total) *subdomain_total = h->have_pc ? h->pc_sub_total : 0;
+    if (max_subdomain) *max_subdomain = h->have_pc ? h->pc_nmax : 0;
+    return EMSURF_OK;
+}
+
+EMSURF_API int emsurf_precond_apply(emsurf_handle* h, const emsurf_c128* r, emsurf_c128* y,
+                                    int32_t nrhs, void* stream) {
+    if (!h || !r || !y) { set_error("NULL handle or vector"); return EMSURF_EINVAL; }
+    if (!h->have_pc) { set_error("no preconditioner was built for this handle"); return EMSURF_EINVAL; }
+    if (nrhs < 1 || nrhs > h->max_rhs) {
+        set_error("nrhs %d outside [1, %d]", nrhs, h->max_rhs);
+        return EMSURF_EINVAL;
+    }
+    const size_t n = (size_t)nrhs * h->n_unique * sizeof(emsurf_c128);
+    const char* ra = reinterpret_cast<const char*>(r);
+    const char* ya = reinterpret_cast<const char*>(y);
+    if (ra < ya + n && ya < ra + n) { set_error("r and y overlap"); return EMSURF_EINVAL; }
+    DeviceGuard dg(h->device);
+    return pc_apply(h, reinterpret_cast<const double2*>(r), reinterpret_cast<double2*>(y), nrhs,
+                    reinterpret_cast<cudaStream_t>(stream));
 }
 
 EMSURF_API int emsurf_solve(emsurf_handle* h, const emsurf_c128* b, emsurf_c128* x, int32_t nrhs,

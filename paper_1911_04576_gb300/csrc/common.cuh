@@ -140,7 +140,7 @@ struct PhaseTimer {
     size_t used = 0;               // events in use
 };
 enum { EMS_PH_BINMUL32 = 0, EMS_PH_BINMUL64, EMS_PH_MM32, EMS_PH_MM64, EMS_PH_FFT32, EMS_PH_FFT64,
-       EMS_PH_ARNOLDI, EMS_PH_SCATTER, EMS_NPHASE };
+       EMS_PH_ARNOLDI, EMS_PH_SCATTER, EMS_PH_PRECOND, EMS_NPHASE };
 
 struct emsurf_handle {
     int device = 0;
@@ -167,6 +167,18 @@ struct emsurf_handle {
     bool have64 = false, have32 = false;
     int num_sms = 0;
     cudaStream_t setup_stream = nullptr;   // stream of the create-time work
+    // near-field preconditioner (restricted additive Schwarz, FP32 LU blocks)
+    bool have_pc = false;
+    int pc_nmax = 0;
+    int64_t pc_elems = 0;           // sum over cells of n_m^2 (factor entries)
+    int64_t pc_sub_total = 0;       // sum over cells of n_m
+    float2* pc_mat = nullptr;       // LU factors, per cell n_m x n_m row-major
+    int64_t* pc_off = nullptr;      // [M] element offset of each cell's block
+    int32_t* pc_n = nullptr;        // [M] subdomain sizes
+    int32_t* pc_own = nullptr;      // [M] owned unknowns (first in each subdomain)
+    int32_t* pc_sub_ptr = nullptr;  // [M+1]
+    int32_t* pc_sub_ids = nullptr;  // unique ids of each subdomain
+    int32_t* pc_perm = nullptr;     // pivot permutation per subdomain
     int* d_err = nullptr;             // device error flag of bounded waits (0 = ok)
     // GMRES workspace (FP64), allocated lazily by emsurf_solve
     void* gm = nullptr;
@@ -200,6 +212,8 @@ int derive_fp32_operator(emsurf_handle* h, const emsurf_problem* pr);
 template <typename T2>
 int apply_operator(emsurf_handle* h, Operator<T2>& op, const double2* x, double2* y, int nrhs,
                    cudaStream_t st);
+int pc_build(emsurf_handle* h, const emsurf_problem* p);
+int pc_apply(emsurf_handle* h, const double2* r, double2* y, int R, cudaStream_t st);
 int gmres_solve(emsurf_handle* h, const double2* b, double2* x, int nrhs,
                 const emsurf_solve_opts* o, emsurf_solve_info* info, cudaStream_t st);
 }  // namespace emsurf

@@ -7,6 +7,11 @@
 // Givens rotations and the upper-triangular solve on the device, all FP64.  Right-hand sides are independent
 // systems that share every operator application.
 //
+// With the near-field preconditioner M (Sec. IV-A applies it on the right)
+// the Arnoldi process runs on A M^{-1} in its flexible form (Saad 1993):
+// Z_j = M^{-1} V_j is kept and the update is x += Z y, so the FP32
+// factorisation inside M^{-1} does not limit the accuracy of x.
+//
 // MIXED precision: iterative refinement with FP64 residuals
 //   r = b - A64 x;  solve A32 d = r with FP32-operator GMRES to inner_rtol;
 //   x += d;  until ||r|| / ||b|| <= rtol.
@@ -30,6 +35,7 @@ struct Gm {
     int m = 0, R = 0;
     size_t n = 0;
     double2* V = nullptr;      // [(m+1)][R][n]
+    double2* Z = nullptr;      // [m][R][n] preconditioned directions (with M)
     double2* w = nullptr;      // [R][n]
     double2* r0 = nullptr;     // [R][n]
     double2* d = nullptr;      // [R][n] FP64 residual of the refinement (mixed)
@@ -485,6 +491,7 @@ int gm_alloc(emsurf_handle* h, Gm*& gm, int m, int R) {
     g->n = (size_t)h->n_unique;
     const size_t vec = (size_t)RR * g->n * sizeof(double2);
     EMS_TRY(dev_alloc(h, (void**)&g->V, vec * (mm + 1)));
+    if (h->have_pc) EMS_TRY(dev_alloc(h, (void**)&g->Z, vec * mm));
     EMS_TRY(dev_alloc(h, (void**)&g->w, vec));
     EMS_TRY(dev_alloc(h, (void**)&g->r0, vec));
     EMS_TRY(dev_alloc(h, (void**)&g->d, vec));
@@ -549,7 +556,7 @@ struct Apply {
 // GMRES(m) from x (used as the initial guess), until every rhs reaches rtol
 // or the iteration budget runs out.  Returns the number of Arnoldi steps.
 int gmres_core(emsurf_handle* h, Gm* g, Apply& A, const double2* b, double2* x, int R, int m,
-               double rtol, int max_iters, bool x_is_zero, cudaStream_t st, int* iters_out) {
+               double rtol, int max_iters, bool x_is_zero, bool pc, cudaStream_t st, int* iters_out) {
     const size_t n = g->n, nv = (size_t)R * n;
     const size_t vstride = nv;
     const int nb = blocks_for(nv);
@@ -583,7 +590,15 @@ int gmres_core(emsurf_handle* h, Gm* g, Apply& A, const double2* b, double2* x, 
         if (!any || it >= max_iters) break;
         for (int j = 0; j < m; ++j) {
             double2* Vj = g->V + (size_t)j * vstride;
-            EMS_TRY(A(Vj, g->w, R, st));
+            if (pc) {
+                double2* Zj = g->Z + (size_t)j * vstride;
+                prof_mark(h, EMS_PH_PRECOND, true, st);
+                EMS_TRY(pc_apply(h, Vj, Zj, R, st));
+                prof_mark(h, EMS_PH_PRECOND, false, st);
+                EMS_TRY(A(Zj, g->w, R, st));
+            } else {
+                EMS_TRY(A(Vj, g->w, R, st));
+            }
             // CGS2 (two projections onto V_0..V_j), norm and Givens: 3 fused kernels
             const dim3 rg(g->nblk, R);
             const size_t wsm = (size_t)g->chunk * sizeof(double2);
@@ -621,7 +636,7 @@ int gmres_core(emsurf_handle* h, Gm* g, Apply& A, const double2* b, double2* x, 
         trisolve_kernel<<<1, 64, 0, st>>>(g->H, g->g, g->hv, g->jend, m, R);
         EMS_CUDA(cudaGetLastError());
     ++g->launches;
-        xupdate_kernel<<<nb, 256, 0, st>>>(x, g->V, vstride, g->hv, g->jend, m, n, R);
+        xupdate_kernel<<<nb, 256, 0, st>>>(x, pc ? g->Z : g->V, vstride, g->hv, g->jend, m, n, R);
         EMS_CUDA(cudaGetLastError());
     ++g->launches;
     }
@@ -662,6 +677,7 @@ int gmres_solve(emsurf_handle* h, const double2* b, double2* x, int R, const ems
     std::vector<double> res(R, 0.0);
     Apply A64{h, EMSURF_FP64};
     Apply A32{h, EMSURF_FP32};
+    const bool pc = h->have_pc && o->precond >= 0;
     int mode = o->solver;
     if (mode == 0) mode = h->precision == EMSURF_MIXED ? 3 : (h->precision == EMSURF_FP32 ? 2 : 1);
     if (mode == 3) {
@@ -689,7 +705,7 @@ int gmres_solve(emsurf_handle* h, const double2* b, double2* x, int R, const ems
             const double tol = std::max(inner, 0.5 * o->rtol / std::max(worst, 1e-300));
             int it = 0;
             EMS_TRY(gmres_core(h, g, A32, g->d, c, R, m, std::min(tol, 0.5), o->max_iters - iters,
-                               true, st, &it));
+                               true, pc, st, &it));
             iters += it;
             axpy_kernel<<<blocks_for(nv), 256, 0, st>>>(x, c, nv);
             EMS_CUDA(cudaGetLastError());
@@ -700,7 +716,7 @@ int gmres_solve(emsurf_handle* h, const double2* b, double2* x, int R, const ems
         nmv = A64.count + A32.count;
     } else {
         Apply& A = (mode == 2) ? A32 : A64;
-        EMS_TRY(gmres_core(h, g, A, b, x, R, m, o->rtol, o->max_iters, true, st, &iters));
+        EMS_TRY(gmres_core(h, g, A, b, x, R, m, o->rtol, o->max_iters, true, pc, st, &iters));
         EMS_TRY(true_residual(h, g, A, b, x, R, st, res.data()));
         nmv = A.count;
     }

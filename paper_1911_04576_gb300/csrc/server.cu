@@ -60,8 +60,14 @@ int64_t request_bytes(const emsurf_request& q) {
     else if (q.precision == EMSURF_FP32) op = b32 + b64 + mm;          // FP64 spectrum is a temporary
     else op = b64 + b32 + mm + mm / 2;
     const int64_t work = 2LL * P * R * K * 16 + 10LL * R * M * K * 16;
-    const int64_t krylov = (int64_t)(std::max(q.opts.restart, 1) + 8) * R * M * K * 16;
-    return tables + mm + op + work + krylov + (768LL << 20);            // + tabulation scratch, slack
+    int64_t krylov = (int64_t)(std::max(q.opts.restart, 1) + 8) * R * M * K * 16;
+    int64_t pc = 0;
+    if (q.precond_overlap > 0.0) {
+        const int64_t nm = std::min<int64_t>(1100, 3 * K / 2);          // largest subdomain
+        pc = M * nm * nm * 8 + 2 * M * nm * 4 + 50LL * E * E * 16;
+        krylov += (int64_t)std::max(q.opts.restart, 1) * R * M * K * 16;   // Z_j of flexible GMRES
+    }
+    return tables + mm + op + work + krylov + pc + (768LL << 20);       // + tabulation scratch, slack
 }
 
 }  // namespace
@@ -134,7 +140,16 @@ int run_job(emsurf_server* sv, Job& jb, cudaStream_t st) {
         p.tables_on_device = 1;
         p.device = sv->device;
         p.stream = st;
-        s = emsurf_create(&p, &hd);
+        std::vector<double> xy;
+        if (q.precond_overlap > 0.0) {
+            xy.resize((size_t)2 * nu);
+            s = emsurf_setup_unknown_xy(q.a, q.b, q.h, q.n, q.nx, q.ny, idx.data(), nu, xy.data());
+            p.unknown_xy = xy.data();
+            p.cell_a = q.a;
+            p.cell_b = q.b;
+            p.precond_overlap = q.precond_overlap;
+        }
+        if (!s) s = emsurf_create(&p, &hd);
     }
     cudaFree(L);
     cudaFree(Kt);

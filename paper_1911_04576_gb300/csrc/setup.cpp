@@ -242,6 +242,33 @@ EMSURF_API int emsurf_setup_patch_mesh(double side, double z, int32_t n, double*
     return EMSURF_OK;
 }
 
+EMSURF_API int emsurf_setup_unknown_xy(double a, double b, double h, int32_t n, int32_t nx,
+                                       int32_t ny, const int32_t* uo_index, int32_t n_unique,
+                                       double* xy) {
+    if (n < 1 || nx < 1 || ny < 1 || !uo_index || !xy || n_unique < 1) {
+        set_error("emsurf_setup_unknown_xy: bad arguments");
+        return EMSURF_EINVAL;
+    }
+    MeshOut m;
+    EMS_TRY(build_box(a, b, h, n, nullptr, m, nullptr));
+    const int E = (int)m.tplus.size(), K = 2 * E;
+    std::vector<char> set(n_unique, 0);
+    for (int c = 0; c < nx * ny; ++c)
+        for (int k = 0; k < K; ++k) {
+            const int u = uo_index[(size_t)c * K + k];
+            if (u < 0 || u >= n_unique) {
+                set_error("emsurf_setup_unknown_xy: uo_index out of range");
+                return EMSURF_EINVAL;
+            }
+            if (set[u]) continue;
+            set[u] = 1;
+            const int e = k % E, p = m.edges[2 * e], q = m.edges[2 * e + 1];
+            xy[2 * u] = 0.5 * (m.verts[3 * p] + m.verts[3 * q]) + (c % nx) * a;
+            xy[2 * u + 1] = 0.5 * (m.verts[3 * p + 1] + m.verts[3 * q + 1]) + (c / nx) * b;
+        }
+    return EMSURF_OK;
+}
+
 EMSURF_API int emsurf_setup_overlap(int32_t n, int32_t nx, int32_t ny, int32_t* uo_index,
                                     int8_t* uo_sign, int32_t* n_unique) {
     if (n < 1 || nx < 1 || ny < 1 || !uo_index || !uo_sign || !n_unique) {

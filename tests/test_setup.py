@@ -56,3 +56,24 @@ def test_setup_rejects_bad_sizes(B):
         with pytest.raises(B.EmsurfError) as e:
             call()
         assert e.value.status == B.EMSURF_EINVAL
+
+
+@pytest.mark.parametrize("n,nx,ny", [(1, 2, 3), (2, 3, 2), (3, 1, 1)])
+def test_unknown_positions_match_oracle(B, n, nx, ny):
+    """Edge-midpoint positions of the unique unknowns (host, for the
+    near-field preconditioner) equal the oracle's first-copy positions."""
+    from oracle import precond
+    a, b, h = 0.015, 0.012, 0.0075
+    box = box_mesh(a, b, h, n)
+    idx, sgn, nu = lattice.overlap_map(box, nx, ny, a, b)
+    xy = B.emsurf_setup_unknown_xy(a, b, h, n, nx, ny, idx, nu)
+    ref, _ = precond.unknown_positions(box, idx, nx, ny, a, b)
+    assert np.allclose(xy, ref, rtol=0, atol=1e-15)
+
+
+def test_unknown_positions_reject_bad_index(B):
+    idx, sgn, nu = B.emsurf_setup_overlap(1, 2, 2)
+    bad = idx.copy()
+    bad[5] = nu
+    with pytest.raises(B.EmsurfError):
+        B.emsurf_setup_unknown_xy(0.015, 0.015, 0.0075, 1, 2, 2, bad, nu)
