@@ -108,7 +108,9 @@ typedef struct {
     int32_t restart;      /* GMRES restart length m (1..64)                    */
     int32_t max_iters;    /* total inner iterations across restarts/refines    */
     int32_t max_refine;   /* MIXED only: outer FP64 refinement steps           */
-    double inner_rtol;    /* MIXED only: inner FP32 solve tolerance (0 = 1e-4) */
+    double inner_rtol;    /* MIXED only: floor of the inner FP32 solve tolerance,
+                             which is max(floor, 0.5 rtol / current residual)
+                             (0 = 1e-6)                                        */
     int32_t solver;       /* 0: by handle precision; 1: FP64-operator GMRES;
                              2: FP32-operator GMRES; 3: mixed refinement.
                              The operators it needs must be resident.         */

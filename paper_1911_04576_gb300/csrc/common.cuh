@@ -170,15 +170,21 @@ struct emsurf_handle {
     // near-field preconditioner (restricted additive Schwarz, FP32 LU blocks)
     bool have_pc = false;
     int pc_nmax = 0;
-    int64_t pc_elems = 0;           // sum over cells of n_m^2 (factor entries)
+    int64_t pc_elems = 0;           // sum over cells of own_m * ld_m (stored entries)
     int64_t pc_sub_total = 0;       // sum over cells of n_m
-    float2* pc_mat = nullptr;       // LU factors, per cell n_m x n_m row-major
-    int64_t* pc_off = nullptr;      // [M] element offset of each cell's block
+    int pc_own_max = 0;
+    float2* pc_mat = nullptr;       // owned rows of A_m^{-1}: per cell own_m x ld_m, row-major
+    int64_t* pc_off = nullptr;      // [M] element offset of each cell's rows
+    int32_t* pc_ld = nullptr;       // [M] row length (n_m rounded up to even)
+    int32_t* pc_own_ptr = nullptr;  // [M+1] first owned row of each cell in the row list
+    int32_t* pc_sub_cell = nullptr; // cell of each subdomain entry
+    int64_t* pc_rs_off = nullptr;   // [M] start of each cell's segment in pc_rs
+    float2* pc_rs = nullptr;        // [max_rhs][pc_rs_stride] gathered r (FP32)
+    int64_t pc_rs_stride = 0;
     int32_t* pc_n = nullptr;        // [M] subdomain sizes
     int32_t* pc_own = nullptr;      // [M] owned unknowns (first in each subdomain)
     int32_t* pc_sub_ptr = nullptr;  // [M+1]
     int32_t* pc_sub_ids = nullptr;  // unique ids of each subdomain
-    int32_t* pc_perm = nullptr;     // pivot permutation per subdomain
     int* d_err = nullptr;             // device error flag of bounded waits (0 = ok)
     // GMRES workspace (FP64), allocated lazily by emsurf_solve
     void* gm = nullptr;

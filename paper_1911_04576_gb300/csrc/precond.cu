@@ -7,14 +7,17 @@
 // grouped by cell: subdomain m holds every unique unknown whose RWG edge
 // midpoint lies inside cell m's footprint grown by an overlap margin delta
 // (one mesh layer of the neighbours).  Its exact block A_m = R_m A R_m^T of
-// Eq. final is assembled from the offset tables and macromodels, factored
-// once (complex FP32 LU with partial pivoting, one CTA per cell), and each
+// Eq. final is assembled from the offset tables and macromodels and factored
+// once (complex FP32 LU with partial pivoting, one CTA per cell).  Each
 // application computes
 //     M^{-1} r = sum_m R~_m^T A_m^{-1} R_m r,
 // where R~_m keeps only the unknowns the cell owns (restricted additive
 // Schwarz; each unknown is owned by the first cell that references it), so
 // every output is written once and the result does not depend on the order
-// of the cells.
+// of the cells.  Only the owned rows of A_m^{-1} are ever used, so they are
+// formed from the factors at create time and the application is a batched
+// matrix-vector product over own_m x n_m entries (about half of n_m^2, and
+// without the serial steps of a triangular solve); the factors are freed.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -27,6 +30,10 @@ namespace {
 constexpr int kLuNB = 16;           // panel width of the blocked LU
 constexpr int kLuThreads = 512;
 constexpr int kPcMaxN = 1100;       // largest subdomain (panel must fit in shared memory)
+constexpr int kInvNR = 16;          // inverse rows per CTA
+constexpr int kInvThreads = 512;
+constexpr int kApThreads = 256;
+constexpr int kApUnroll = 8;        // 16-byte loads in flight per lane
 
 __device__ __forceinline__ float2 csubf(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 cdivf(float2 a, float2 b) {
@@ -205,95 +212,181 @@ pc_lu_kernel(float2* __restrict__ mats, const int64_t* __restrict__ off, const i
     }
 }
 
-// y[sub[a]] = (A_m^{-1} R_m r)[a] for the owned a of every cell m: gather
-// with the pivot permutation, blocked forward (unit L) and backward (U)
-// substitution in shared memory, owned rows written out.  One CTA per cell.
-__global__ void __launch_bounds__(256)
-pc_apply_kernel(const float2* __restrict__ mats, const int64_t* __restrict__ off,
-                const int32_t* __restrict__ nsz, const int32_t* __restrict__ own,
-                const int32_t* __restrict__ sub_ptr, const int32_t* __restrict__ sub_ids,
-                const int32_t* __restrict__ perm_all, const double2* __restrict__ r, double2* __restrict__ y,
-                int n_unique) {
+__device__ __forceinline__ float2 crecipf(float2 b) {
+    const float d = b.x * b.x + b.y * b.y;
+    return make_float2(b.x / d, -b.y / d);
+}
+
+// Owned rows of A_m^{-1} from the factors P A = L U:  A^{-1} = U^{-1} L^{-1} P,
+// so row i is v^T P with U^T w = e_i (forward) and L^T v = w (backward), and
+// row[perm[a]] = v[a].  U^T w = e_i is solved in the scaled form s = D w
+// (D = diag U): s[b] -= (U[a][b] / U[a][a]) s[a], then w = D^{-1} s.  Both
+// sweeps read one row of the factors per step (coalesced); the kInvNR right-
+// hand sides of the CTA live in shared memory as W[q][a].
+__global__ void __launch_bounds__(kInvThreads)
+pc_invrows_kernel(const float2* __restrict__ lu, const int64_t* __restrict__ luoff,
+                  const int32_t* __restrict__ nsz, const int32_t* __restrict__ own,
+                  const int32_t* __restrict__ sub_ptr, const int32_t* __restrict__ perm_all,
+                  float2* __restrict__ X, const int64_t* __restrict__ xoff, const int32_t* __restrict__ ldx) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* b = reinterpret_cast<float2*>(smem_raw);   // [n]
-    const int m = blockIdx.x;
-    const int rr = blockIdx.y;
-    const int n = nsz[m];
-    const float2* A = mats + off[m];
-    const int32_t* sub = sub_ids + sub_ptr[m];
-    const int32_t* perm = perm_all + sub_ptr[m];
-    const double2* rv = r + (size_t)rr * n_unique;
-    for (int a = threadIdx.x; a < n; a += blockDim.x) {
-        const double2 v = rv[sub[perm[a]]];
-        b[a] = make_float2((float)v.x, (float)v.y);
+    float2* W = reinterpret_cast<float2*>(smem_raw);     // [kInvNR][n]
+    const int m = blockIdx.y;
+    const int n = nsz[m], i0 = blockIdx.x * kInvNR;
+    if (i0 >= own[m]) return;
+    const int nr = min(kInvNR, own[m] - i0);
+    const float2* A = lu + luoff[m];
+    const int tid = threadIdx.x;
+    for (int e = tid; e < kInvNR * n; e += blockDim.x) {
+        const int q = e / n, a = e % n;
+        W[e] = make_float2(q < nr && a == i0 + q ? 1.f : 0.f, 0.f);
+    }
+    // forward: e_i has no entry before i0
+    for (int a = i0; a < n - 1; ++a) {
+        __syncthreads();
+        const float2 rd = crecipf(A[(size_t)a * n + a]);
+        for (int b = a + 1 + tid; b < n; b += blockDim.x) {
+            const float2 u = cmul(A[(size_t)a * n + b], rd);
+            for (int q = 0; q < nr; ++q) W[q * n + b] = csubf(W[q * n + b], cmul(u, W[q * n + a]));
+        }
     }
     __syncthreads();
-    __shared__ float2 tile[32][33];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    // forward: L z = b, blocks of 32 rows (diagonal block staged in shared memory)
-    for (int s = 0; s < n; s += 32) {
-        const int bs = min(32, n - s);
-        for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) {
-            const int i = e / bs, j = e % bs;
-            tile[i][j] = A[(size_t)(s + i) * n + s + j];
-        }
-        __syncthreads();
-        if (wid == 0) {
-            float2 v = lane < bs ? b[s + lane] : make_float2(0.f, 0.f);
-            for (int j = 0; j < bs; ++j) {
-                const float2 zj = make_float2(__shfl_sync(0xffffffffu, v.x, j), __shfl_sync(0xffffffffu, v.y, j));
-                if (lane > j && lane < bs) v = csubf(v, cmul(tile[lane][j], zj));
-            }
-            if (lane < bs) b[s + lane] = v;
-        }
-        __syncthreads();
-        for (int i = s + bs + threadIdx.x; i < n; i += blockDim.x) {
-            float2 acc = b[i];
-            const float2* row = A + (size_t)i * n + s;
-            for (int j = 0; j < bs; ++j) acc = csubf(acc, cmul(row[j], b[s + j]));
-            b[i] = acc;
-        }
-        __syncthreads();
+    for (int e = tid; e < nr * n; e += blockDim.x) {
+        const int a = e % n;
+        W[e] = cmul(W[e], crecipf(A[(size_t)a * n + a]));
     }
-    // backward: U x = z, blocks of 32 rows from the bottom
-    for (int e = n; e > 0; e -= 32) {
-        const int s = max(0, e - 32), bs = e - s;
-        for (int q = threadIdx.x; q < bs * bs; q += blockDim.x) {
-            const int i = q / bs, j = q % bs;
-            tile[i][j] = A[(size_t)(s + i) * n + s + j];
-        }
+    // backward with the unit upper L^T
+    for (int a = n - 1; a > 0; --a) {
         __syncthreads();
-        if (wid == 0) {
-            float2 v = lane < bs ? b[s + lane] : make_float2(0.f, 0.f);
-            for (int j = bs - 1; j >= 0; --j) {
-                if (lane == j) v = cdivf(v, tile[j][j]);
-                const float2 xj = make_float2(__shfl_sync(0xffffffffu, v.x, j), __shfl_sync(0xffffffffu, v.y, j));
-                if (lane < j) v = csubf(v, cmul(tile[lane][j], xj));
-            }
-            if (lane < bs) b[s + lane] = v;
+        for (int b = tid; b < a; b += blockDim.x) {
+            const float2 l = A[(size_t)a * n + b];
+            for (int q = 0; q < nr; ++q) W[q * n + b] = csubf(W[q * n + b], cmul(l, W[q * n + a]));
         }
-        __syncthreads();
-        for (int i = threadIdx.x; i < s; i += blockDim.x) {
-            float2 acc = b[i];
-            const float2* row = A + (size_t)i * n + s;
-            for (int j = 0; j < bs; ++j) acc = csubf(acc, cmul(row[j], b[s + j]));
-            b[i] = acc;
-        }
-        __syncthreads();
     }
-    double2* yv = y + (size_t)rr * n_unique;
-    for (int a = threadIdx.x; a < own[m]; a += blockDim.x) yv[sub[a]] = make_double2((double)b[a].x, (double)b[a].y);
+    __syncthreads();
+    const int32_t* perm = perm_all + sub_ptr[m];
+    const int ld = ldx[m];
+    float2* Xm = X + xoff[m];
+    for (int e = tid; e < nr * n; e += blockDim.x) {
+        const int q = e / n, a = e % n;
+        Xm[(size_t)(i0 + q) * ld + perm[a]] = W[e];
+    }
+}
+
+// rs[q][j] = r[q][sub_ids[j]] in FP32 for every subdomain entry j (all cells
+// back to back, each cell's segment starting at an even index).
+__global__ void pc_gather_kernel(const double2* __restrict__ r, const int32_t* __restrict__ sub_ids,
+                                 const int32_t* __restrict__ sub_cell, const int32_t* __restrict__ sub_ptr,
+                                 const int64_t* __restrict__ rs_off, float2* __restrict__ rs,
+                                 int total, int n_unique, int64_t rs_stride, int R) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < total; j += gridDim.x * blockDim.x) {
+        const int m = sub_cell[j];
+        const int64_t o = rs_off[m] + (j - sub_ptr[m]);
+        const int u = sub_ids[j];
+        for (int q = 0; q < R; ++q) {
+            const double2 d = r[(size_t)q * n_unique + u];
+            rs[q * rs_stride + o] = make_float2((float)d.x, (float)d.y);
+        }
+    }
+}
+
+// y[sub[i]] = sum_c X_m[i][c] rs_m[c] for the owned rows i of every cell
+// (the restricted additive Schwarz sum: each unknown is owned once).  The
+// owned rows of all cells form one list; each warp takes whole rows (16-byte
+// loads of X, eight in flight per lane; the cell's rs segment is reused by
+// all its rows from L1/L2) and reduces once per row and right-hand side.
+// The grid is exactly the resident capacity, so the row list is shared out
+// in one wave.
+template <int RQ>
+__global__ void __launch_bounds__(kApThreads, 4)
+pc_apply_kernel(const float2* __restrict__ X, const int64_t* __restrict__ xoff,
+                const int32_t* __restrict__ ldx, const int32_t* __restrict__ own_ptr,
+                const int32_t* __restrict__ sub_ptr, const int32_t* __restrict__ sub_ids,
+                const int64_t* __restrict__ rs_off, const float2* __restrict__ rs, int64_t rs_stride,
+                double2* __restrict__ y, int n_rows, int M, int n_unique, int r0) {
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < n_rows; g += warps) {
+        // cell of owned row g: own_ptr[m] <= g < own_ptr[m+1]
+        int lo = 0, hi = M;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (own_ptr[mid] <= g) lo = mid; else hi = mid;
+        }
+        const int m = lo, i = g - own_ptr[m], ld = ldx[m], half = ld >> 1;
+        const float4* row = reinterpret_cast<const float4*>(X + xoff[m] + (size_t)i * ld);
+        const float4* rv4 = reinterpret_cast<const float4*>(rs + rs_off[m]);
+        float2 acc[RQ];
+#pragma unroll
+        for (int q = 0; q < RQ; ++q) acc[q] = make_float2(0.f, 0.f);
+        for (int c0 = lane; c0 < half; c0 += 32 * kApUnroll) {
+            float4 xv[kApUnroll];
+#pragma unroll
+            for (int u = 0; u < kApUnroll; ++u)
+                xv[u] = c0 + 32 * u < half ? __ldg(row + c0 + 32 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < kApUnroll; ++u) {
+                const int c2 = min(c0 + 32 * u, half - 1);
+#pragma unroll
+                for (int q = 0; q < RQ; ++q) {
+                    const float4 rv = __ldg(rv4 + q * (rs_stride >> 1) + c2);
+                    acc[q].x += xv[u].x * rv.x - xv[u].y * rv.y + xv[u].z * rv.z - xv[u].w * rv.w;
+                    acc[q].y += xv[u].x * rv.y + xv[u].y * rv.x + xv[u].z * rv.w + xv[u].w * rv.z;
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < RQ; ++q)
+            for (int o = 16; o > 0; o >>= 1) {
+                acc[q].x += __shfl_xor_sync(0xffffffffu, acc[q].x, o);
+                acc[q].y += __shfl_xor_sync(0xffffffffu, acc[q].y, o);
+            }
+        if (lane == 0) {
+            const int u = sub_ids[sub_ptr[m] + i];
+#pragma unroll
+            for (int q = 0; q < RQ; ++q)
+                y[(size_t)(r0 + q) * n_unique + u] = make_double2((double)acc[q].x, (double)acc[q].y);
+        }
+    }
+}
+
+template <int RQ>
+int launch_apply(emsurf_handle* h, double2* y, int r0, cudaStream_t st) {
+    static int occ[8] = {0};   // resident blocks per SM (same for every device of this build)
+    if (!occ[RQ]) {
+        int b = 0;
+        EMS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pc_apply_kernel<RQ>, kApThreads, 0));
+        occ[RQ] = std::max(b, 1);
+    }
+    const int blocks = h->num_sms * occ[RQ];
+    pc_apply_kernel<RQ><<<blocks, kApThreads, 0, st>>>(h->pc_mat, h->pc_off, h->pc_ld, h->pc_own_ptr,
+                                                        h->pc_sub_ptr, h->pc_sub_ids, h->pc_rs_off,
+                                                        h->pc_rs + (size_t)r0 * h->pc_rs_stride,
+                                                        h->pc_rs_stride, y, h->n_unique, h->M, h->n_unique, r0);
+    EMS_CUDA(cudaGetLastError());
+    h->launches += 1;
+    return EMSURF_OK;
 }
 
 }  // namespace
 
 int pc_apply(emsurf_handle* h, const double2* r, double2* y, int R, cudaStream_t st) {
-    const size_t smem = (size_t)h->pc_nmax * sizeof(float2);
-    EMS_TRY(set_smem_once(pc_apply_kernel, smem));
-    pc_apply_kernel<<<dim3(h->M, R), 256, smem, st>>>(h->pc_mat, h->pc_off, h->pc_n, h->pc_own, h->pc_sub_ptr,
-                                                       h->pc_sub_ids, h->pc_perm, r, y, h->n_unique);
+    if (R > h->max_rhs) {
+        set_error("preconditioner: %d right-hand sides, handle holds %d", R, h->max_rhs);
+        return EMSURF_EINVAL;
+    }
+    const int total = (int)h->pc_sub_total;
+    pc_gather_kernel<<<std::min((total + 255) / 256, h->num_sms * 8), 256, 0, st>>>(
+        r, h->pc_sub_ids, h->pc_sub_cell, h->pc_sub_ptr, h->pc_rs_off, h->pc_rs, total, h->n_unique,
+        h->pc_rs_stride, R);
     EMS_CUDA(cudaGetLastError());
     h->launches += 1;
+    for (int r0 = 0; r0 < R; r0 += 4) {
+        const int nr = std::min(4, R - r0);
+        if (nr == 1) EMS_TRY(launch_apply<1>(h, y, r0, st));
+        else if (nr == 2) EMS_TRY(launch_apply<2>(h, y, r0, st));
+        else if (nr == 3) EMS_TRY(launch_apply<3>(h, y, r0, st));
+        else EMS_TRY(launch_apply<4>(h, y, r0, st));
+    }
     return EMSURF_OK;
 }
 
@@ -359,8 +452,15 @@ int pc_build(emsurf_handle* h, const emsurf_problem* p) {
             return EMSURF_EINVAL;
         }
     }
-    std::vector<int64_t> moff(M + 1, 0);
-    for (int m = 0; m < M; ++m) moff[m + 1] = moff[m] + (int64_t)nsz[m] * nsz[m];
+    // LU factors n_m x n_m (temporary); owned inverse rows own_m x ld_m (kept)
+    std::vector<int64_t> moff(M + 1, 0), xoff(M + 1, 0);
+    std::vector<int32_t> ldv(M);
+    for (int m = 0; m < M; ++m) {
+        moff[m + 1] = moff[m] + (int64_t)nsz[m] * nsz[m];
+        ldv[m] = (nsz[m] + 1) & ~1;
+        xoff[m + 1] = xoff[m] + (int64_t)own[m] * ldv[m];
+        h->pc_own_max = std::max(h->pc_own_max, own[m]);
+    }
     cudaStream_t st = h->setup_stream;
     auto up = [&](auto** d, const auto* src, size_t cnt) -> int {
         EMS_TRY(dev_alloc(h, (void**)d, cnt * sizeof(**d)));
@@ -371,9 +471,37 @@ int pc_build(emsurf_handle* h, const emsurf_problem* p) {
     EMS_TRY(up(&h->pc_sub_ids, sids.data(), sids.size()));
     EMS_TRY(up(&h->pc_own, own.data(), own.size()));
     EMS_TRY(up(&h->pc_n, nsz.data(), nsz.size()));
-    EMS_TRY(up(&h->pc_off, moff.data(), (size_t)M));
-    EMS_TRY(dev_alloc(h, (void**)&h->pc_perm, sids.size() * sizeof(int32_t)));
-    EMS_TRY(dev_alloc(h, (void**)&h->pc_mat, (size_t)moff[M] * sizeof(float2)));
+    EMS_TRY(up(&h->pc_off, xoff.data(), (size_t)M));
+    EMS_TRY(up(&h->pc_ld, ldv.data(), (size_t)M));
+    {
+        // owned-row list, subdomain entry -> cell, FP32 gather buffer
+        std::vector<int32_t> optr(M + 1, 0), scell(sids.size());
+        std::vector<int64_t> rsoff(M + 1, 0);
+        for (int m = 0; m < M; ++m) {
+            optr[m + 1] = optr[m] + own[m];
+            rsoff[m + 1] = rsoff[m] + ldv[m];
+            for (int q = sptr[m]; q < sptr[m + 1]; ++q) scell[q] = m;
+        }
+        if (optr[M] != h->n_unique) {
+            set_error("preconditioner: %d owned rows for %d unknowns", optr[M], h->n_unique);
+            return EMSURF_EINVAL;
+        }
+        EMS_TRY(up(&h->pc_own_ptr, optr.data(), optr.size()));
+        EMS_TRY(up(&h->pc_sub_cell, scell.data(), scell.size()));
+        EMS_TRY(up(&h->pc_rs_off, rsoff.data(), (size_t)M));
+        h->pc_rs_stride = rsoff[M];
+        EMS_TRY(dev_alloc(h, (void**)&h->pc_rs, (size_t)h->max_rhs * rsoff[M] * sizeof(float2)));
+        EMS_CUDA(cudaMemsetAsync(h->pc_rs, 0, (size_t)h->max_rhs * rsoff[M] * sizeof(float2), st));
+    }
+    EMS_TRY(dev_alloc(h, (void**)&h->pc_mat, (size_t)xoff[M] * sizeof(float2)));
+    EMS_CUDA(cudaMemsetAsync(h->pc_mat, 0, (size_t)xoff[M] * sizeof(float2), st));   // row padding
+    int64_t* d_luoff = nullptr;
+    int32_t* d_perm = nullptr;
+    float2* d_lu = nullptr;
+    EMS_CUDA(cudaMalloc(&d_luoff, sizeof(int64_t) * M));
+    EMS_CUDA(cudaMemcpyAsync(d_luoff, moff.data(), sizeof(int64_t) * M, cudaMemcpyHostToDevice, st));
+    EMS_CUDA(cudaMalloc(&d_perm, sids.size() * sizeof(int32_t)));
+    EMS_CUDA(cudaMalloc(&d_lu, (size_t)moff[M] * sizeof(float2)));
     // near offset tables |dx|, |dy| <= 2 -> [5][5][E][E] (zero outside the lattice)
     const size_t EE = (size_t)E * E;
     double2 *nL = nullptr, *nK = nullptr;
@@ -412,7 +540,7 @@ int pc_build(emsurf_handle* h, const emsurf_problem* p) {
     }
     double2 co[4];
     for (int c = 0; c < 4; ++c) co[c] = make_double2(p->coef[c].re, p->coef[c].im);
-    pc_assemble_kernel<<<dim3(M, 64), 256, 0, st>>>(h->pc_mat, h->pc_off, h->pc_n, h->pc_sub_ptr, h->pc_sub_ids,
+    pc_assemble_kernel<<<dim3(M, 64), 256, 0, st>>>(d_lu, d_luoff, h->pc_n, h->pc_sub_ptr, h->pc_sub_ids,
                                                     h->d_inv_ptr, h->d_inv_ent, h->d_inv_sgn, nL, nK, Zt,
                                                     h->d_type_map, nx, E, co[0], co[1], co[2], co[3]);
     EMS_CUDA(cudaGetLastError());
@@ -421,12 +549,20 @@ int pc_build(emsurf_handle* h, const emsurf_problem* p) {
     EMS_CUDA(cudaMemsetAsync(dstat, 0, sizeof(int) * M, st));
     const size_t lsm = (size_t)h->pc_nmax * kLuNB * sizeof(float2);
     EMS_TRY(set_smem_once(pc_lu_kernel, lsm));
-    pc_lu_kernel<<<M, kLuThreads, lsm, st>>>(h->pc_mat, h->pc_off, h->pc_n, h->pc_sub_ptr, h->pc_perm, dstat);
+    pc_lu_kernel<<<M, kLuThreads, lsm, st>>>(d_lu, d_luoff, h->pc_n, h->pc_sub_ptr, d_perm, dstat);
+    EMS_CUDA(cudaGetLastError());
+    const size_t ism = (size_t)kInvNR * h->pc_nmax * sizeof(float2);
+    EMS_TRY(set_smem_once(pc_invrows_kernel, ism));
+    pc_invrows_kernel<<<dim3((h->pc_own_max + kInvNR - 1) / kInvNR, M), kInvThreads, ism, st>>>(
+        d_lu, d_luoff, h->pc_n, h->pc_own, h->pc_sub_ptr, d_perm, h->pc_mat, h->pc_off, h->pc_ld);
     EMS_CUDA(cudaGetLastError());
     std::vector<int> hs(M);
     EMS_CUDA(cudaMemcpyAsync(hs.data(), dstat, sizeof(int) * M, cudaMemcpyDeviceToHost, st));
     EMS_CUDA(cudaStreamSynchronize(st));
     cudaFree(dstat);
+    cudaFree(d_lu);
+    cudaFree(d_perm);
+    cudaFree(d_luoff);
     cudaFree(nL);
     cudaFree(nK);
     if (own_zt) cudaFree(Zt);
@@ -435,7 +571,7 @@ int pc_build(emsurf_handle* h, const emsurf_problem* p) {
             set_error("preconditioner block of cell %d is singular", m);
             return EMSURF_EINVAL;
         }
-    h->pc_elems = moff[M];
+    h->pc_elems = xoff[M];
     h->pc_sub_total = (int64_t)sids.size();
     h->have_pc = true;
     return EMSURF_OK;
