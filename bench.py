@@ -40,6 +40,11 @@ RESTART = 30
 REF_MATVECS_PER_SOLVE = 1905
 FALLBACK_HBM_GBS = 6800.0
 PC_OVERLAP = 0.6               # preconditioner margin, in mesh cells (a / n)
+# DRAM bytes (read + write) per bin of one binmul_tma_kernel launch, from the
+# ncu capture in profiles/binmul_tma_lattice12x12_k576.md (12x12 lattice,
+# 576 bins); the kernel streams each bin's blocks once, so traffic scales
+# with the bin count.
+BINMUL_DRAM_BYTES_PER_BIN = (767108096 + 5353216) / 576
 
 
 def peaks():
@@ -459,10 +464,12 @@ def main():
         "matvec": {"fp32_ms": round(mv32, 4), "fp32_gbs": round(bytes32 / mv32 / 1e6, 1),
                    "fp64_ms": round(mv64, 4), "fp64_gbs": round(bytes64 / mv64 / 1e6, 1),
                    "alg_bytes_fp32": bytes32, "alg_bytes_fp64": bytes64},
-        "roofline": {"kernel": "binmul_kernel<float2,1> (K2, bin multiply)", "bound": "hbm",
+        "roofline": {"kernel": "binmul_tma_kernel (bin multiply, FP32)", "bound": "hbm",
                      "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "peak_kind": peak_kind,
-                     "traffic": None, "alg_bytes_per_launch": alg_bin,
+                     "traffic": (round(BINMUL_DRAM_BYTES_PER_BIN * P) if BINMUL_DRAM_BYTES_PER_BIN
+                                 else None),
+                     "alg_bytes_per_launch": alg_bin,
                      "avg_launch_ms": round(bin_avg, 5), "launches_timed": bin_n},
         "phases_ms_per_solve": {"binmul32": round(bin_ms / args.steps, 3),
                                 "macromodel32": round(mm_ms / args.steps, 3),

@@ -190,6 +190,13 @@ EMSURF_API int emsurf_profile_read(emsurf_handle* h, int32_t phase, double* tota
  * before it returns.                                                      */
 EMSURF_API int emsurf_check(emsurf_handle* h);
 
+/* Self-test of the bounded-wait path (no counterpart in the paper): one
+ * kernel waits on an mbarrier that nothing arrives on, at most `limit`
+ * polls (1..2^22), then sets the handle's error flag exactly as the bin
+ * multiply's waits do on expiry.  The next emsurf_check returns ETIMEDOUT
+ * and clears the flag.  Nothing faults or hangs.                          */
+EMSURF_API int emsurf_selftest_wait(emsurf_handle* h, int64_t limit, void* stream);
+
 /* Number of CUDA kernels this handle has launched since creation.        */
 EMSURF_API int emsurf_launch_count(const emsurf_handle* h, int64_t* launches);
 

@@ -81,6 +81,7 @@ def lib():
         L.emsurf_setup_patch_mesh.argtypes = [C.c_double, C.c_double, i32] + [vp] * 7
         L.emsurf_setup_overlap.argtypes = [i32, i32, i32, vp, vp, ip]
         L.emsurf_precond_apply.argtypes = [vp, vp, vp, i32, vp]
+        L.emsurf_selftest_wait.argtypes = [vp, C.c_int64, vp]
         L.emsurf_precond_info.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                           C.POINTER(i32)]
         L.emsurf_setup_unknown_xy.argtypes = [C.c_double, C.c_double, C.c_double, i32, i32, i32,
@@ -199,6 +200,11 @@ def emsurf_precond_apply(h, r, y, stream=None):
     """emsurf_precond_apply: r, y torch complex128 CUDA tensors [nrhs, n_unique]."""
     nrhs = 1 if r.dim() == 1 else r.shape[0]
     _check(lib().emsurf_precond_apply(h.ptr, _ptr(r), _ptr(y), nrhs, _stream(stream)))
+
+
+def emsurf_selftest_wait(h, limit=1000, stream=None):
+    """emsurf_selftest_wait: a bounded device wait that always expires."""
+    _check(lib().emsurf_selftest_wait(h.ptr, limit, _stream(stream)))
 
 
 def emsurf_precond_info(h):

@@ -409,6 +409,15 @@ EMSURF_API int emsurf_check(emsurf_handle* h) {
     return EMSURF_OK;
 }
 
+EMSURF_API int emsurf_selftest_wait(emsurf_handle* h, int64_t limit, void* stream) {
+    if (!h || limit < 1 || limit > (1LL << 22)) {
+        set_error("emsurf_selftest_wait: NULL handle or limit outside [1, 2^22]");
+        return EMSURF_EINVAL;
+    }
+    DeviceGuard dg(h->device);
+    return wait_selftest(h, (long long)limit, reinterpret_cast<cudaStream_t>(stream));
+}
+
 EMSURF_API int emsurf_launch_count(const emsurf_handle* h, int64_t* launches) {
     if (!h || !launches) { set_error("NULL argument"); return EMSURF_EINVAL; }
     *launches = h->launches;

@@ -219,6 +219,7 @@ template <typename T2>
 int apply_operator(emsurf_handle* h, Operator<T2>& op, const double2* x, double2* y, int nrhs,
                    cudaStream_t st);
 int pc_build(emsurf_handle* h, const emsurf_problem* p);
+int wait_selftest(emsurf_handle* h, long long limit, cudaStream_t st);
 int pc_apply(emsurf_handle* h, const double2* r, double2* y, int R, cudaStream_t st);
 int gmres_solve(emsurf_handle* h, const double2* b, double2* x, int nrhs,
                 const emsurf_solve_opts* o, emsurf_solve_info* info, cudaStream_t st);

@@ -169,10 +169,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 // bounded wait; false on expiry
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (long long it = 0; it < kWaitLimit; ++it)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = kWaitLimit) {
+    for (long long it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
+}
+
+// Exercises the expiry path of mbar_wait: waits on an mbarrier that nothing
+// arrives on, with a short limit, and reports like the production kernels.
+__global__ void wait_selftest_kernel(long long limit, int* __restrict__ err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait(&bar, 0, limit)) atomicExch(err, 3);
 }
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
     asm volatile(
@@ -576,4 +586,13 @@ template int apply_operator<double2>(emsurf_handle*, Operator<double2>&, const d
 template int apply_operator<float2>(emsurf_handle*, Operator<float2>&, const double2*, double2*,
                                     int, cudaStream_t);
 
+}  // namespace emsurf
+
+namespace emsurf {
+int wait_selftest(emsurf_handle* h, long long limit, cudaStream_t st) {
+    wait_selftest_kernel<<<1, 32, 0, st>>>(limit, h->d_err);
+    EMS_CUDA(cudaGetLastError());
+    h->launches += 1;
+    return EMSURF_OK;
+}
 }  // namespace emsurf

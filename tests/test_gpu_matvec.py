@@ -127,3 +127,25 @@ def test_invalid_calls_rejected(emsurf_lib):
         B.emsurf_create(2, 2, E, nu, tmap, Z, Lt, Kt, COEF, idx, sgn, device_mem_budget=1024)
     assert e.value.status == B.EMSURF_ENOMEM
     h.close()
+
+
+def test_bounded_wait_expiry_is_reported(emsurf_lib):
+    """A device wait that nothing satisfies gives up after its limit, the
+    host reads ETIMEDOUT once, and the context stays usable (the product
+    afterwards is still exact)."""
+    from paper_1911_04576_gb300 import binding as B
+    E, idx, sgn, nu, Lt, Kt, Z, tmap = random_case(2, 3, 2, 2, 77)
+    h = B.emsurf_create(3, 2, E, nu, tmap, Z, Lt, Kt, COEF, idx, sgn, precision=B.MIXED)
+    B.emsurf_check(h)
+    B.emsurf_selftest_wait(h, 2000)
+    with pytest.raises(B.EmsurfError) as ei:
+        B.emsurf_check(h)
+    assert ei.value.status == B.EMSURF_ETIMEDOUT
+    B.emsurf_check(h)                       # the flag was cleared
+    x = W.random_vectors(1, nu, 78)
+    yref = lattice.matvec_direct(x, Lt, Kt, COEF, Z, tmap, idx, sgn, nu, 3, 2)
+    assert relerr(run_matvec(B, h, x, B.FP32)[0], yref[0]) <= TOL32
+    B.emsurf_check(h)
+    with pytest.raises(B.EmsurfError):
+        B.emsurf_selftest_wait(h, 0)        # limit outside [1, 2^22]
+    h.close()
