@@ -106,7 +106,8 @@ int fft_pass(T2* data, const FftPlan& plan, long long inner, long long outer,
 template <typename T2>
 int fft_pass_gather(T2* data, const FftPlan& plan, long long inner, long long outer,
                     long long outer_stride, int p_in, const double2* x, const int32_t* idx,
-                    const int8_t* sgn, int nx, int K, int n_unique, cudaStream_t st);
+                    const int8_t* sgn, int nx, int K, int n_unique, cudaStream_t st,
+                    const float2* xf = nullptr);
 
 // Inverse pass over the kept rows (outer = ny) whose store writes only points
 // ix < nx, as y1[r][iy*nx+ix][k] = scale * value + sum_s mm[s][r][m][k].
@@ -166,6 +167,7 @@ struct emsurf_handle {
     emsurf::Operator<float2> op32;
     bool have64 = false, have32 = false;
     int num_sms = 0;
+    int mm_occ[2] = {0, 0};                // resident macromodel CTAs per SM (FP32, FP64)
     cudaStream_t setup_stream = nullptr;   // stream of the create-time work
     // near-field preconditioner (restricted additive Schwarz, FP32 LU blocks)
     bool have_pc = false;
@@ -218,9 +220,12 @@ int derive_fp32_operator(emsurf_handle* h, const emsurf_problem* pr);
 template <typename T2>
 int apply_operator(emsurf_handle* h, Operator<T2>& op, const double2* x, double2* y, int nrhs,
                    cudaStream_t st);
+// FP32 operator on FP32 vectors [R][n_unique] (the inner solve of MIXED)
+int apply_operator_f32(emsurf_handle* h, const float2* x, float2* y, int R, cudaStream_t st);
 int pc_build(emsurf_handle* h, const emsurf_problem* p);
 int wait_selftest(emsurf_handle* h, long long limit, cudaStream_t st);
 int pc_apply(emsurf_handle* h, const double2* r, double2* y, int R, cudaStream_t st);
+int pc_apply_f32(emsurf_handle* h, const float2* r, float2* y, int R, cudaStream_t st);
 int gmres_solve(emsurf_handle* h, const double2* b, double2* x, int nrhs,
                 const emsurf_solve_opts* o, emsurf_solve_info* info, cudaStream_t st);
 }  // namespace emsurf

@@ -130,7 +130,24 @@ struct GatherSrc {
     const int32_t* idx;
     const int8_t* sgn;
     int nx, K, n_unique;
+    const float2* xf;   // FP32 source instead of x when not null
 };
+
+// sign * x[r][u] of the gather, from the FP64 or the FP32 source; an FP32
+// source into an FP32 grid needs no FP64 arithmetic
+template <typename T2>
+__device__ __forceinline__ T2 gather_value(const GatherSrc& gs, int r, size_t loc) {
+    const size_t at = (size_t)r * gs.n_unique + gs.idx[loc];
+    if (gs.xf) {
+        const float2 xv = gs.xf[at];
+        const float s = (float)gs.sgn[loc];
+        if constexpr (sizeof(T2) == sizeof(float2)) return make_float2(s * xv.x, s * xv.y);
+        else return mk<T2>((double)(s * xv.x), (double)(s * xv.y));
+    }
+    const double2 xv = gs.x[at];
+    const double s = (double)gs.sgn[loc];
+    return mk<T2>(s * xv.x, s * xv.y);
+}
 
 // Store epilogue of the inverse pass over the kept rows: point ix < nx of row
 // iy, lane L = r*K + k, goes to y1[r][iy*nx + ix][k] = scale * value +
@@ -147,13 +164,19 @@ template <typename T2>
 __device__ __forceinline__ void crop_store(const CropEpi<T2>& ep, int iy, int p, long long L, T2 v) {
     const int r = (int)(L / ep.K), k = (int)(L % ep.K);
     const size_t m = (size_t)iy * ep.nx + p;
-    double ax = (double)v.x * ep.scale, ay = (double)v.y * ep.scale;
+    // in the precision of the grid (no FP64 arithmetic on the FP32 path)
+    using S = decltype(v.x);
+    const S sc = (S)ep.scale;
+    S ax = v.x * sc, ay = v.y * sc;
     for (int s = 0; s < ep.nsplit; ++s) {
         const T2 z = ep.mm[(((size_t)s * ep.R + r) * ep.M + m) * ep.K + k];
-        ax += (double)z.x;
-        ay += (double)z.y;
+        ax += z.x;
+        ay += z.y;
     }
-    ep.y1[((size_t)r * ep.M + m) * ep.K + k] = mk<T2>(ax, ay);
+    T2 o;
+    o.x = ax;
+    o.y = ay;
+    ep.y1[((size_t)r * ep.M + m) * ep.K + k] = o;
 }
 
 template <typename T2, int W, int P, int SIGN, bool GATHER, bool EPI>
@@ -180,9 +203,7 @@ fft_fixed_kernel(T2* __restrict__ data, long long inner, long long outer_stride,
                 const long long L = lane0 + l;
                 const int r = (int)(L / gs.K), k = (int)(L % gs.K);
                 const size_t loc = ((size_t)blockIdx.y * gs.nx + p) * gs.K + k;
-                const double2 xv = gs.x[(size_t)r * gs.n_unique + gs.idx[loc]];
-                const double s = (double)gs.sgn[loc];
-                v = mk<T2>(s * xv.x, s * xv.y);
+                v = gather_value<T2>(gs, r, loc);
             } else {
                 v = base[(long long)p * inner + l];
             }
@@ -233,9 +254,7 @@ fft_pass_kernel(T2* __restrict__ data, int P, long long inner, long long outer_s
                 const long long L = lane0 + l;
                 const int r = (int)(L / gs.K), k = (int)(L % gs.K);
                 const size_t loc = ((size_t)blockIdx.y * gs.nx + p) * gs.K + k;
-                const double2 xv = gs.x[(size_t)r * gs.n_unique + gs.idx[loc]];
-                const double s = (double)gs.sgn[loc];
-                v = mk<T2>(s * xv.x, s * xv.y);
+                v = gather_value<T2>(gs, r, loc);
             } else {
                 v = base[(long long)p * inner + l];
             }
@@ -439,7 +458,7 @@ void fft_plan_destroy(FftPlan& plan) {
 template <typename T2>
 int fft_pass(T2* data, const FftPlan& plan, long long inner, long long outer,
              long long outer_stride, int sign, cudaStream_t st, int p_in, int p_out) {
-    GatherSrc gs{nullptr, nullptr, nullptr, 0, 1, 0};
+    GatherSrc gs{nullptr, nullptr, nullptr, 0, 1, 0, nullptr};
     CropEpi<T2> ep{nullptr, nullptr, 0, 1, 1, 1, 1, 1.0};
     return pass_impl<T2>(data, plan, inner, outer, outer_stride, sign, p_in, p_out, gs, false, ep,
                          false, st);
@@ -448,8 +467,8 @@ int fft_pass(T2* data, const FftPlan& plan, long long inner, long long outer,
 template <typename T2>
 int fft_pass_gather(T2* data, const FftPlan& plan, long long inner, long long outer,
                     long long outer_stride, int p_in, const double2* x, const int32_t* idx,
-                    const int8_t* sgn, int nx, int K, int n_unique, cudaStream_t st) {
-    GatherSrc gs{x, idx, sgn, nx, K, n_unique};
+                    const int8_t* sgn, int nx, int K, int n_unique, cudaStream_t st, const float2* xf) {
+    GatherSrc gs{x, idx, sgn, nx, K, n_unique, xf};
     CropEpi<T2> ep{nullptr, nullptr, 0, 1, 1, 1, 1, 1.0};
     return pass_impl<T2>(data, plan, inner, outer, outer_stride, -1, p_in, plan.P, gs, true, ep, false,
                          st);
@@ -459,7 +478,7 @@ template <typename T2>
 int fft_pass_crop(T2* data, const FftPlan& plan, long long inner, long long outer,
                   long long outer_stride, int nx, const T2* mm, int nsplit, int R, int M, int K,
                   double scale, T2* y1, cudaStream_t st) {
-    GatherSrc gs{nullptr, nullptr, nullptr, 0, 1, 0};
+    GatherSrc gs{nullptr, nullptr, nullptr, 0, 1, 0, nullptr};
     CropEpi<T2> ep{mm, y1, nsplit, R, M, nx, K, scale};
     return pass_impl<T2>(data, plan, inner, outer, outer_stride, +1, plan.P, nx, gs, false, ep, true,
                          st);
@@ -471,10 +490,10 @@ template int fft_pass<float2>(float2*, const FftPlan&, long long, long long, lon
                               cudaStream_t, int, int);
 template int fft_pass_gather<double2>(double2*, const FftPlan&, long long, long long, long long, int,
                                       const double2*, const int32_t*, const int8_t*, int, int, int,
-                                      cudaStream_t);
+                                      cudaStream_t, const float2*);
 template int fft_pass_gather<float2>(float2*, const FftPlan&, long long, long long, long long, int,
                                      const double2*, const int32_t*, const int8_t*, int, int, int,
-                                     cudaStream_t);
+                                     cudaStream_t, const float2*);
 template int fft_pass_crop<double2>(double2*, const FftPlan&, long long, long long, long long, int,
                                     const double2*, int, int, int, int, double, double2*, cudaStream_t);
 template int fft_pass_crop<float2>(float2*, const FftPlan&, long long, long long, long long, int,

@@ -15,9 +15,16 @@
 // MIXED precision: iterative refinement with FP64 residuals
 //   r = b - A64 x;  solve A32 d = r with FP32-operator GMRES to inner_rtol;
 //   x += d;  until ||r|| / ||b|| <= rtol.
+// The inner GMRES keeps its Krylov vectors in FP32 and forms products and
+// updates in FP32 (FP64 arithmetic is ~60x slower on this part); sums across
+// lanes and blocks, the Hessenberg matrix, the rotations and the least
+// squares stay FP64.  The vector kernels are templates over the vector type
+// VT (double2 for the FP64 solver, float2 for the inner solve).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <type_traits>
+#include <vector>
 
 #include "common.cuh"
 
@@ -36,6 +43,13 @@ struct Gm {
     size_t n = 0;
     double2* V = nullptr;      // [(m+1)][R][n]
     double2* Z = nullptr;      // [m][R][n] preconditioned directions (with M)
+    // FP32 Krylov state of the inner solve of MIXED
+    float2* V32 = nullptr;     // [(m+1)][R][n]
+    float2* Z32 = nullptr;     // [m][R][n] (with M)
+    float2* w32 = nullptr;     // [R][n]
+    float2* r032 = nullptr;    // [R][n]
+    float2* d32 = nullptr;     // [R][n] right-hand side of the inner solve
+    float2* c32 = nullptr;     // [R][n] its solution
     double2* w = nullptr;      // [R][n]
     double2* r0 = nullptr;     // [R][n]
     double2* d = nullptr;      // [R][n] FP64 residual of the refinement (mixed)
@@ -60,8 +74,24 @@ struct Gm {
     int64_t launches = 0;      // kernels launched by the solver itself
 };
 
-__device__ __forceinline__ double2 conj_mul(double2 a, double2 b) {   // conj(a) * b
-    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+template <typename VT> struct VScalar;
+template <> struct VScalar<double2> { using T = double; };
+template <> struct VScalar<float2> { using T = float; };
+
+__device__ __forceinline__ double2 to_d2(double2 v) { return v; }
+__device__ __forceinline__ double2 to_d2(float2 v) { return make_double2((double)v.x, (double)v.y); }
+template <typename VT> __device__ __forceinline__ VT from_d2(double2 v);
+template <> __device__ __forceinline__ double2 from_d2<double2>(double2 v) { return v; }
+template <> __device__ __forceinline__ float2 from_d2<float2>(double2 v) {
+    return make_float2((float)v.x, (float)v.y);
+}
+
+template <typename VT>
+__device__ __forceinline__ VT conj_mul(VT a, VT b) {   // conj(a) * b
+    VT r;
+    r.x = a.x * b.x + a.y * b.y;
+    r.y = a.x * b.y - a.y * b.x;
+    return r;
 }
 
 __device__ __forceinline__ double2 warp_sum(double2 v) {
@@ -74,21 +104,24 @@ __device__ __forceinline__ double2 warp_sum(double2 v) {
 }
 
 // part[r][i][blk] = sum over this block's slice of conj(V_i[r]) . w[r]
-__global__ void dot_partial_kernel(const double2* __restrict__ V, int nvec, size_t vstride,
-                                   const double2* __restrict__ w, size_t n, int R,
+template <typename VT>
+__global__ void dot_partial_kernel(const VT* __restrict__ V, int nvec, size_t vstride,
+                                   const VT* __restrict__ w, size_t n, int R,
                                    double2* __restrict__ part, int ldv) {
     __shared__ double2 red[kRedThreads / 32];
     const int i = blockIdx.y, r = blockIdx.z;
-    const double2* a = V + (size_t)i * vstride + (size_t)r * n;
-    const double2* b = w + (size_t)r * n;
-    double2 acc = make_double2(0.0, 0.0);
+    const VT* a = V + (size_t)i * vstride + (size_t)r * n;
+    const VT* b = w + (size_t)r * n;
+    VT accv;
+    accv.x = 0;
+    accv.y = 0;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
          e += (size_t)gridDim.x * blockDim.x) {
-        const double2 p = conj_mul(a[e], b[e]);
-        acc.x += p.x;
-        acc.y += p.y;
+        const VT p = conj_mul(a[e], b[e]);
+        accv.x += p.x;
+        accv.y += p.y;
     }
-    acc = warp_sum(acc);
+    double2 acc = warp_sum(to_d2(accv));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x < 32) {
@@ -123,16 +156,23 @@ __global__ void dot_final_kernel(const double2* __restrict__ part, int nblk, int
 }
 
 // dst[r] = src[r] / nrm[r] (0 if nrm == 0); optionally H[j+1][j] = nrm
-__global__ void normalize_kernel(double2* __restrict__ dst, const double2* __restrict__ src,
+template <typename VT>
+__global__ void normalize_kernel(VT* __restrict__ dst, const VT* __restrict__ src,
                                  const double* __restrict__ nrm, size_t n, int R,
                                  double2* __restrict__ H, int m, int j) {
+    using S = typename VScalar<VT>::T;
+    __shared__ S sinv[64];
+    for (int r = threadIdx.x; r < R; r += blockDim.x) sinv[r] = (S)(nrm[r] > 0.0 ? 1.0 / nrm[r] : 0.0);
+    __syncthreads();
     const size_t total = (size_t)R * n;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
          e += (size_t)gridDim.x * blockDim.x) {
-        const int r = (int)(e / n);
-        const double s = nrm[r] > 0.0 ? 1.0 / nrm[r] : 0.0;
-        const double2 v = src[e];
-        dst[e] = make_double2(v.x * s, v.y * s);
+        const S s = sinv[(int)(e / n)];
+        const VT v = src[e];
+        VT o;
+        o.x = v.x * s;
+        o.y = v.y * s;
+        dst[e] = o;
     }
     if (H != nullptr && blockIdx.x == 0 && threadIdx.x < R) {
         const int r = threadIdx.x;
@@ -141,11 +181,23 @@ __global__ void normalize_kernel(double2* __restrict__ dst, const double2* __res
 }
 
 // r0 = b - w
-__global__ void residual_kernel(double2* __restrict__ r0, const double2* __restrict__ b,
-                                const double2* __restrict__ w, size_t total) {
+template <typename VT>
+__global__ void residual_kernel(VT* __restrict__ r0, const VT* __restrict__ b,
+                                const VT* __restrict__ w, size_t total) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        VT o;
+        o.x = b[e].x - w[e].x;
+        o.y = b[e].y - w[e].y;
+        r0[e] = o;
+    }
+}
+
+// o = (float) i
+__global__ void to_f32_kernel(float2* __restrict__ o, const double2* __restrict__ i, size_t total) {
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
          e += (size_t)gridDim.x * blockDim.x)
-        r0[e] = make_double2(b[e].x - w[e].x, b[e].y - w[e].y);
+        o[e] = make_float2((float)i[e].x, (float)i[e].y);
 }
 
 // ---------------------------------------------------------------- fused step
@@ -200,18 +252,24 @@ __device__ __forceinline__ void finalize_sums(const double2* part, int nb, int n
 }
 
 // w -= sum_i c_i V_i on one element (c from shared memory), 8 loads in flight
-__device__ __forceinline__ double2 update_one(const double2* __restrict__ V, int nvec,
-                                              size_t vstride, size_t off, double2 acc,
-                                              const double2* __restrict__ cs) {
+template <typename VT>
+__device__ __forceinline__ VT update_one(const VT* __restrict__ V, int nvec, size_t vstride,
+                                         size_t off, VT acc, const VT* __restrict__ cs) {
     for (int i0 = 0; i0 < nvec; i0 += 8) {
-        double2 v[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c)
-            v[c] = (i0 + c < nvec) ? V[(size_t)(i0 + c) * vstride + off] : make_double2(0.0, 0.0);
+        VT v[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             if (i0 + c < nvec) {
-                const double2 q = cs[i0 + c];
+                v[c] = V[(size_t)(i0 + c) * vstride + off];
+            } else {
+                v[c].x = 0;
+                v[c].y = 0;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            if (i0 + c < nvec) {
+                const VT q = cs[i0 + c];
                 acc.x -= q.x * v[c].x - q.y * v[c].y;
                 acc.y -= q.x * v[c].y + q.y * v[c].x;
             }
@@ -226,22 +284,23 @@ __device__ __forceinline__ double2 update_one(const double2* __restrict__ V, int
 // Gram-Schmidt pass), then one warp per Krylov vector forms the chunk's dot
 // product with a single warp reduction.  The last block sums the block
 // partials in block order into hv and sets (add = 0) or adds to column j of H.
+template <typename VT>
 __global__ void __launch_bounds__(kArnThreads)
-cgs_pass_kernel(const double2* __restrict__ V, int nvec, size_t vstride, double2* __restrict__ w,
+cgs_pass_kernel(const VT* __restrict__ V, int nvec, size_t vstride, VT* __restrict__ w,
                 size_t n, int chunk, const double2* __restrict__ upd, double2* __restrict__ part,
                 int ldv, unsigned* __restrict__ counter, double2* __restrict__ hv,
                 double2* __restrict__ H, int m, int j, int add, int* __restrict__ reorth) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double2* ws = reinterpret_cast<double2*>(smem_raw);   // [chunk]
-    __shared__ double2 cs[65];
+    VT* ws = reinterpret_cast<VT*>(smem_raw);   // [chunk]
+    __shared__ VT cs[65];
     __shared__ bool is_last;
     const int r = blockIdx.y;
-    double2* wr = w + (size_t)r * n;
+    VT* wr = w + (size_t)r * n;
     const size_t e0 = (size_t)blockIdx.x * chunk;
     const int ne = (int)(e0 < n ? min((size_t)chunk, n - e0) : 0);
     if (upd && !reorth[r]) {
         // second pass not needed: apply the first pass's update only
-        for (int i = threadIdx.x; i < nvec; i += blockDim.x) cs[i] = upd[(size_t)r * ldv + i];
+        for (int i = threadIdx.x; i < nvec; i += blockDim.x) cs[i] = from_d2<VT>(upd[(size_t)r * ldv + i]);
         __syncthreads();
         for (int q = threadIdx.x; q < ne; q += blockDim.x)
             wr[e0 + q] = update_one(V, nvec, vstride, (size_t)r * n + e0 + q, wr[e0 + q], cs);
@@ -250,10 +309,10 @@ cgs_pass_kernel(const double2* __restrict__ V, int nvec, size_t vstride, double2
         return;
     }
     if (upd) {
-        for (int i = threadIdx.x; i < nvec; i += blockDim.x) cs[i] = upd[(size_t)r * ldv + i];
+        for (int i = threadIdx.x; i < nvec; i += blockDim.x) cs[i] = from_d2<VT>(upd[(size_t)r * ldv + i]);
         __syncthreads();
         for (int q = threadIdx.x; q < ne; q += blockDim.x) {
-            const double2 v = update_one(V, nvec, vstride, (size_t)r * n + e0 + q, wr[e0 + q], cs);
+            const VT v = update_one(V, nvec, vstride, (size_t)r * n + e0 + q, wr[e0 + q], cs);
             wr[e0 + q] = v;
             ws[q] = v;
         }
@@ -263,17 +322,19 @@ cgs_pass_kernel(const double2* __restrict__ V, int nvec, size_t vstride, double2
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     // the first pass also forms ||w||^2 (as "vector" nvec) for the
-    // reorthogonalisation test
+    // reorthogonalisation test; lane sums in VT's precision, the warp sum in FP64
     const int ndots = upd ? nvec : nvec + 1;
     for (int i = wid; i < ndots; i += nw) {
-        const double2* a = (i < nvec ? V + (size_t)i * vstride + (size_t)r * n : wr) + e0;
-        double2 acc = make_double2(0.0, 0.0);
+        const VT* a = (i < nvec ? V + (size_t)i * vstride + (size_t)r * n : wr) + e0;
+        VT accv;
+        accv.x = 0;
+        accv.y = 0;
         for (int q = lane; q < ne; q += 32) {
-            const double2 p = conj_mul(a[q], ws[q]);
-            acc.x += p.x;
-            acc.y += p.y;
+            const VT p = conj_mul(a[q], ws[q]);
+            accv.x += p.x;
+            accv.y += p.y;
         }
-        acc = warp_sum(acc);
+        const double2 acc = warp_sum(to_d2(accv));
         if (lane == 0) part[((size_t)r * ldv + i) * gridDim.x + blockIdx.x] = acc;
     }
     if (last_block(counter + r, &is_last)) {
@@ -305,33 +366,35 @@ __device__ void givens_update(int r, double2* __restrict__ col, double2* __restr
 
 // w -= sum_i upd_i V_i, ||w||, H[j+1][j] = ||w||, then (last block, one
 // thread per rhs) the Givens update of column j.
+template <typename VT>
 __global__ void __launch_bounds__(kArnThreads)
-cgs_norm_givens_kernel(const double2* __restrict__ V, int nvec, size_t vstride,
-                       double2* __restrict__ w, size_t n, int chunk, const double2* __restrict__ upd,
+cgs_norm_givens_kernel(const VT* __restrict__ V, int nvec, size_t vstride,
+                       VT* __restrict__ w, size_t n, int chunk, const double2* __restrict__ upd,
                        double2* __restrict__ part, int ldv, unsigned* __restrict__ counter,
                        double* __restrict__ nrm, double2* __restrict__ H, double2* __restrict__ cs,
                        double2* __restrict__ sn, double2* __restrict__ g,
                        const double* __restrict__ bnorm, double* __restrict__ res,
                        int* __restrict__ active, int* __restrict__ jend, int m, int j, double rtol,
                        const int* __restrict__ reorth) {
+    using S = typename VScalar<VT>::T;
     __shared__ double2 red[kArnThreads / 32];
-    __shared__ double2 cs_[65];
+    __shared__ VT cs_[65];
     __shared__ bool is_last;
     const int r = blockIdx.y;
-    double2* wr = w + (size_t)r * n;
+    VT* wr = w + (size_t)r * n;
     const size_t e0 = (size_t)blockIdx.x * chunk;
     const int ne = (int)(e0 < n ? min((size_t)chunk, n - e0) : 0);
-    for (int i = threadIdx.x; i < nvec; i += blockDim.x) cs_[i] = upd[(size_t)r * ldv + i];
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) cs_[i] = from_d2<VT>(upd[(size_t)r * ldv + i]);
     __syncthreads();
-    double ss = 0.0;
+    S ss = 0;
     const bool second = reorth[r] != 0;
     for (int q = threadIdx.x; q < ne; q += blockDim.x) {
-        const double2 acc = second ? update_one(V, nvec, vstride, (size_t)r * n + e0 + q, wr[e0 + q], cs_)
-                                   : wr[e0 + q];
+        const VT acc = second ? update_one(V, nvec, vstride, (size_t)r * n + e0 + q, wr[e0 + q], cs_)
+                              : wr[e0 + q];
         if (second) wr[e0 + q] = acc;
         ss += acc.x * acc.x + acc.y * acc.y;
     }
-    const double2 t = block_sum(make_double2(ss, 0.0), red);
+    const double2 t = block_sum(make_double2((double)ss, 0.0), red);
     if (threadIdx.x == 0) part[((size_t)r * ldv) * gridDim.x + blockIdx.x] = t;
     if (last_block(counter + r, &is_last)) {
         // stage column j, the rotations and g in shared memory (parallel loads)
@@ -444,18 +507,23 @@ __global__ void trisolve_kernel(const double2* __restrict__ H, const double2* __
     }
 }
 
-// x[r] += sum_{i<jend[r]} y[r][i] V_i[r]
-__global__ void xupdate_kernel(double2* __restrict__ x, const double2* __restrict__ V,
+// x[r] += sum_{i<jend[r]} y[r][i] V_i[r]  (y staged in VT precision)
+template <typename VT>
+__global__ void xupdate_kernel(VT* __restrict__ x, const VT* __restrict__ V,
                                size_t vstride, const double2* __restrict__ y,
                                const int* __restrict__ jend, int m, size_t n, int R) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    VT* ys = reinterpret_cast<VT*>(smem_raw);   // [R][m+1]
+    for (int q = threadIdx.x; q < R * (m + 1); q += blockDim.x) ys[q] = from_d2<VT>(y[q]);
+    __syncthreads();
     const size_t total = (size_t)R * n;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
          e += (size_t)gridDim.x * blockDim.x) {
         const int r = (int)(e / n);
-        double2 acc = x[e];
+        VT acc = x[e];
         for (int i = 0; i < jend[r]; ++i) {
-            const double2 c = y[(size_t)r * (m + 1) + i];
-            const double2 v = V[(size_t)i * vstride + e];
+            const VT c = ys[(size_t)r * (m + 1) + i];
+            const VT v = V[(size_t)i * vstride + e];
             acc.x += c.x * v.x - c.y * v.y;
             acc.y += c.x * v.y + c.y * v.x;
         }
@@ -463,10 +531,14 @@ __global__ void xupdate_kernel(double2* __restrict__ x, const double2* __restric
     }
 }
 
-__global__ void axpy_kernel(double2* __restrict__ x, const double2* __restrict__ d, size_t total) {
+// x += d (x FP64, d of either precision)
+template <typename VT>
+__global__ void axpy_kernel(double2* __restrict__ x, const VT* __restrict__ d, size_t total) {
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-         e += (size_t)gridDim.x * blockDim.x)
-        x[e] = make_double2(x[e].x + d[e].x, x[e].y + d[e].y);
+         e += (size_t)gridDim.x * blockDim.x) {
+        const double2 v = to_d2(d[e]);
+        x[e] = make_double2(x[e].x + v.x, x[e].y + v.y);
+    }
 }
 
 int blocks_for(size_t n) {
@@ -496,6 +568,15 @@ int gm_alloc(emsurf_handle* h, Gm*& gm, int m, int R) {
     EMS_TRY(dev_alloc(h, (void**)&g->r0, vec));
     EMS_TRY(dev_alloc(h, (void**)&g->d, vec));
     EMS_TRY(dev_alloc(h, (void**)&g->c, vec));
+    if (h->have32) {
+        const size_t vec32 = (size_t)RR * g->n * sizeof(float2);
+        EMS_TRY(dev_alloc(h, (void**)&g->V32, vec32 * (mm + 1)));
+        if (h->have_pc) EMS_TRY(dev_alloc(h, (void**)&g->Z32, vec32 * mm));
+        EMS_TRY(dev_alloc(h, (void**)&g->w32, vec32));
+        EMS_TRY(dev_alloc(h, (void**)&g->r032, vec32));
+        EMS_TRY(dev_alloc(h, (void**)&g->d32, vec32));
+        EMS_TRY(dev_alloc(h, (void**)&g->c32, vec32));
+    }
     EMS_TRY(dev_alloc(h, (void**)&g->H, sizeof(double2) * RR * mm * (mm + 1)));
     EMS_TRY(dev_alloc(h, (void**)&g->cs, sizeof(double2) * RR * mm));
     EMS_TRY(dev_alloc(h, (void**)&g->sn, sizeof(double2) * RR * mm));
@@ -529,9 +610,10 @@ int gm_alloc(emsurf_handle* h, Gm*& gm, int m, int R) {
 }
 
 // nrm[r] = ||v[r]||
-int norms(Gm* g, const double2* v, int R, cudaStream_t st) {
+template <typename VT>
+int norms(Gm* g, const VT* v, int R, cudaStream_t st) {
     dim3 grid(kRedBlocks, 1, R);
-    dot_partial_kernel<<<grid, kRedThreads, 0, st>>>(v, 1, 0, v, g->n, R, g->part, g->m + 1);
+    dot_partial_kernel<VT><<<grid, kRedThreads, 0, st>>>(v, 1, 0, v, g->n, R, g->part, g->m + 1);
     EMS_CUDA(cudaGetLastError());
     ++g->launches;
     dot_final_kernel<<<dim3(1, R), 32, 0, st>>>(g->part, kRedBlocks, 1, g->m + 1, g->hv, g->H,
@@ -541,83 +623,104 @@ int norms(Gm* g, const double2* v, int R, cudaStream_t st) {
     return EMSURF_OK;
 }
 
+// The operator and the preconditioner on vectors of type VT: FP64 vectors
+// take the FP64 or the FP32 operator, FP32 vectors the FP32 one.
+template <typename VT>
 struct Apply {
     emsurf_handle* h;
-    // (kernel launches of this file are counted where they are issued)
-    int prec;   // operator used inside GMRES
+    int prec;   // operator used inside GMRES (EMSURF_FP64 / EMSURF_FP32)
     int count = 0;
-    int operator()(const double2* x, double2* y, int R, cudaStream_t st) {
+    int operator()(const VT* x, VT* y, int R, cudaStream_t st) {
         ++count;
-        if (prec == EMSURF_FP32) return apply_operator<float2>(h, h->op32, x, y, R, st);
-        return apply_operator<double2>(h, h->op64, x, y, R, st);
+        if constexpr (std::is_same<VT, float2>::value) {
+            return apply_operator_f32(h, x, y, R, st);
+        } else {
+            if (prec == EMSURF_FP32) return apply_operator<float2>(h, h->op32, x, y, R, st);
+            return apply_operator<double2>(h, h->op64, x, y, R, st);
+        }
+    }
+    int precond(const VT* r, VT* y, int R, cudaStream_t st) {
+        if constexpr (std::is_same<VT, float2>::value) return pc_apply_f32(h, r, y, R, st);
+        else return pc_apply(h, r, y, R, st);
     }
 };
 
+// The Krylov buffers of one vector type.
+template <typename VT>
+struct Kv {
+    VT *V, *Z, *w, *r0;
+};
+template <typename VT> Kv<VT> kv(Gm* g);
+template <> Kv<double2> kv<double2>(Gm* g) { return {g->V, g->Z, g->w, g->r0}; }
+template <> Kv<float2> kv<float2>(Gm* g) { return {g->V32, g->Z32, g->w32, g->r032}; }
+
 // GMRES(m) from x (used as the initial guess), until every rhs reaches rtol
 // or the iteration budget runs out.  Returns the number of Arnoldi steps.
-int gmres_core(emsurf_handle* h, Gm* g, Apply& A, const double2* b, double2* x, int R, int m,
+template <typename VT>
+int gmres_core(emsurf_handle* h, Gm* g, Apply<VT>& A, const VT* b, VT* x, int R, int m,
                double rtol, int max_iters, bool x_is_zero, bool pc, cudaStream_t st, int* iters_out) {
     const size_t n = g->n, nv = (size_t)R * n;
     const size_t vstride = nv;
     const int nb = blocks_for(nv);
+    const Kv<VT> K = kv<VT>(g);
     int it = 0;
     // ||b||
-    EMS_TRY(norms(g, b, R, st));
+    EMS_TRY(norms<VT>(g, b, R, st));
     EMS_CUDA(cudaMemcpyAsync(g->bnorm, g->nrm, sizeof(double) * R, cudaMemcpyDeviceToDevice, st));
     bool first = true;
     while (true) {
         if (first && x_is_zero) {
-            EMS_CUDA(cudaMemcpyAsync(g->r0, b, nv * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+            EMS_CUDA(cudaMemcpyAsync(K.r0, b, nv * sizeof(VT), cudaMemcpyDeviceToDevice, st));
         } else {
-            EMS_TRY(A(x, g->w, R, st));
-            residual_kernel<<<nb, 256, 0, st>>>(g->r0, b, g->w, nv);
+            EMS_TRY(A(x, K.w, R, st));
+            residual_kernel<VT><<<nb, 256, 0, st>>>(K.r0, b, K.w, nv);
             EMS_CUDA(cudaGetLastError());
-    ++g->launches;
+            ++g->launches;
         }
         first = false;
-        EMS_TRY(norms(g, g->r0, R, st));
+        EMS_TRY(norms<VT>(g, K.r0, R, st));
         cycle_start_kernel<<<1, 64, 0, st>>>(g->nrm, g->bnorm, g->g, g->res, g->active, g->jend,
                                               m, R, rtol);
         EMS_CUDA(cudaGetLastError());
-    ++g->launches;
-        normalize_kernel<<<nb, 256, 0, st>>>(g->V, g->r0, g->nrm, n, R, nullptr, m, 0);
+        ++g->launches;
+        normalize_kernel<VT><<<nb, 256, 0, st>>>(K.V, K.r0, g->nrm, n, R, nullptr, m, 0);
         EMS_CUDA(cudaGetLastError());
-    ++g->launches;
+        ++g->launches;
         EMS_CUDA(cudaMemcpyAsync(g->h_act, g->active, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
         EMS_CUDA(cudaStreamSynchronize(st));
         bool any = false;
         for (int r = 0; r < R; ++r) any = any || g->h_act[r];
         if (!any || it >= max_iters) break;
         for (int j = 0; j < m; ++j) {
-            double2* Vj = g->V + (size_t)j * vstride;
+            VT* Vj = K.V + (size_t)j * vstride;
             if (pc) {
-                double2* Zj = g->Z + (size_t)j * vstride;
+                VT* Zj = K.Z + (size_t)j * vstride;
                 prof_mark(h, EMS_PH_PRECOND, true, st);
-                EMS_TRY(pc_apply(h, Vj, Zj, R, st));
+                EMS_TRY(A.precond(Vj, Zj, R, st));
                 prof_mark(h, EMS_PH_PRECOND, false, st);
-                EMS_TRY(A(Zj, g->w, R, st));
+                EMS_TRY(A(Zj, K.w, R, st));
             } else {
-                EMS_TRY(A(Vj, g->w, R, st));
+                EMS_TRY(A(Vj, K.w, R, st));
             }
-            // CGS2 (two projections onto V_0..V_j), norm and Givens: 3 fused kernels
+            // CGS with the DGKS second pass, norm and Givens: 3 fused kernels
             const dim3 rg(g->nblk, R);
-            const size_t wsm = (size_t)g->chunk * sizeof(double2);
-            EMS_TRY(set_smem_once(cgs_pass_kernel, wsm));
+            const size_t wsm = (size_t)g->chunk * sizeof(VT);
+            EMS_TRY(set_smem_once(cgs_pass_kernel<VT>, wsm));
             prof_mark(h, EMS_PH_ARNOLDI, true, st);
-            cgs_pass_kernel<<<rg, kArnThreads, wsm, st>>>(g->V, j + 1, vstride, g->w, n, g->chunk, nullptr,
-                                                          g->part, m + 1, g->counter, g->hv, g->H, m, j, 0,
-                                                          g->reorth);
+            cgs_pass_kernel<VT><<<rg, kArnThreads, wsm, st>>>(K.V, j + 1, vstride, K.w, n, g->chunk, nullptr,
+                                                              g->part, m + 1, g->counter, g->hv, g->H, m, j, 0,
+                                                              g->reorth);
             EMS_CUDA(cudaGetLastError());
-            cgs_pass_kernel<<<rg, kArnThreads, wsm, st>>>(g->V, j + 1, vstride, g->w, n, g->chunk, g->hv,
-                                                          g->part, m + 1, g->counter, g->hv2, g->H, m, j, 1,
-                                                          g->reorth);
+            cgs_pass_kernel<VT><<<rg, kArnThreads, wsm, st>>>(K.V, j + 1, vstride, K.w, n, g->chunk, g->hv,
+                                                              g->part, m + 1, g->counter, g->hv2, g->H, m, j, 1,
+                                                              g->reorth);
             EMS_CUDA(cudaGetLastError());
-            cgs_norm_givens_kernel<<<rg, kArnThreads, 0, st>>>(
-                g->V, j + 1, vstride, g->w, n, g->chunk, g->hv2, g->part, m + 1, g->counter, g->nrm, g->H,
+            cgs_norm_givens_kernel<VT><<<rg, kArnThreads, 0, st>>>(
+                K.V, j + 1, vstride, K.w, n, g->chunk, g->hv2, g->part, m + 1, g->counter, g->nrm, g->H,
                 g->cs, g->sn, g->g, g->bnorm, g->res, g->active, g->jend, m, j, rtol, g->reorth);
             EMS_CUDA(cudaGetLastError());
-            normalize_kernel<<<nb, 256, 0, st>>>(g->V + (size_t)(j + 1) * vstride, g->w, g->nrm, n,
-                                                 R, nullptr, m, j);
+            normalize_kernel<VT><<<nb, 256, 0, st>>>(K.V + (size_t)(j + 1) * vstride, K.w, g->nrm, n,
+                                                     R, nullptr, m, j);
             EMS_CUDA(cudaGetLastError());
             prof_mark(h, EMS_PH_ARNOLDI, false, st);
             g->launches += 4;
@@ -635,27 +738,28 @@ int gmres_core(emsurf_handle* h, Gm* g, Apply& A, const double2* b, double2* x, 
         }
         trisolve_kernel<<<1, 64, 0, st>>>(g->H, g->g, g->hv, g->jend, m, R);
         EMS_CUDA(cudaGetLastError());
-    ++g->launches;
-        xupdate_kernel<<<nb, 256, 0, st>>>(x, pc ? g->Z : g->V, vstride, g->hv, g->jend, m, n, R);
+        ++g->launches;
+        xupdate_kernel<VT><<<nb, 256, (size_t)R * (m + 1) * sizeof(VT), st>>>(
+            x, pc ? K.Z : K.V, vstride, g->hv, g->jend, m, n, R);
         EMS_CUDA(cudaGetLastError());
-    ++g->launches;
+        ++g->launches;
     }
     *iters_out = it;
     return EMSURF_OK;
 }
 
-// true relative residual per rhs with the given operator, into host res[]
-int true_residual(emsurf_handle* h, Gm* g, Apply& A, const double2* b, const double2* x, int R,
+// true relative residual per rhs with the given FP64-vector operator, into host res[]
+int true_residual(emsurf_handle* h, Gm* g, Apply<double2>& A, const double2* b, const double2* x, int R,
                   cudaStream_t st, double* res) {
     const size_t nv = (size_t)R * g->n;
     EMS_TRY(A(x, g->w, R, st));
-    residual_kernel<<<blocks_for(nv), 256, 0, st>>>(g->r0, b, g->w, nv);
+    residual_kernel<double2><<<blocks_for(nv), 256, 0, st>>>(g->r0, b, g->w, nv);
     EMS_CUDA(cudaGetLastError());
     ++g->launches;
-    EMS_TRY(norms(g, g->r0, R, st));
+    EMS_TRY(norms<double2>(g, g->r0, R, st));
     std::vector<double> rn(R), bn(R);
     EMS_CUDA(cudaMemcpyAsync(rn.data(), g->nrm, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
-    EMS_TRY(norms(g, b, R, st));
+    EMS_TRY(norms<double2>(g, b, R, st));
     EMS_CUDA(cudaMemcpyAsync(bn.data(), g->nrm, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
     EMS_CUDA(cudaStreamSynchronize(st));
     for (int r = 0; r < R; ++r) res[r] = bn[r] > 0 ? rn[r] / bn[r] : 0.0;
@@ -675,8 +779,9 @@ int gmres_solve(emsurf_handle* h, const double2* b, double2* x, int R, const ems
     const int64_t launches0 = g->launches;
     int iters = 0, refines = 0, nmv = 0;
     std::vector<double> res(R, 0.0);
-    Apply A64{h, EMSURF_FP64};
-    Apply A32{h, EMSURF_FP32};
+    Apply<double2> A64{h, EMSURF_FP64};
+    Apply<double2> A32{h, EMSURF_FP32};
+    Apply<float2> A32f{h, EMSURF_FP32};
     const bool pc = h->have_pc && o->precond >= 0;
     int mode = o->solver;
     if (mode == 0) mode = h->precision == EMSURF_MIXED ? 3 : (h->precision == EMSURF_FP32 ? 2 : 1);
@@ -691,7 +796,7 @@ int gmres_solve(emsurf_handle* h, const double2* b, double2* x, int R, const ems
             // FP64 residual r = b - A64 x (x = 0 on the first pass)
             if (zero) {
                 EMS_CUDA(cudaMemcpyAsync(g->d, b, nv * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-                EMS_TRY(norms(g, b, R, st));
+                EMS_TRY(norms<double2>(g, b, R, st));
                 std::vector<double> bn(R);
                 EMS_CUDA(cudaMemcpyAsync(bn.data(), g->nrm, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
                 EMS_CUDA(cudaStreamSynchronize(st));
@@ -703,24 +808,26 @@ int gmres_solve(emsurf_handle* h, const double2* b, double2* x, int R, const ems
             double worst = 0.0;
             for (int r = 0; r < R; ++r) worst = std::max(worst, res[r]);
             if (worst <= o->rtol || refines >= o->max_refine || iters >= o->max_iters) break;
-            // inner solve A32 c = d with FP32-operator GMRES
-            double2* c = g->c;
-            EMS_CUDA(cudaMemsetAsync(c, 0, nv * sizeof(double2), st));
+            // inner solve A32 c = d with FP32-operator GMRES on FP32 vectors
+            to_f32_kernel<<<blocks_for(nv), 256, 0, st>>>(g->d32, g->d, nv);
+            EMS_CUDA(cudaGetLastError());
+            ++g->launches;
+            EMS_CUDA(cudaMemsetAsync(g->c32, 0, nv * sizeof(float2), st));
             const double tol = std::max(inner, 0.5 * o->rtol / std::max(worst, 1e-300));
             int it = 0;
-            EMS_TRY(gmres_core(h, g, A32, g->d, c, R, m, std::min(tol, 0.5), o->max_iters - iters,
-                               true, pc, st, &it));
+            EMS_TRY(gmres_core<float2>(h, g, A32f, g->d32, g->c32, R, m, std::min(tol, 0.5),
+                                       o->max_iters - iters, true, pc, st, &it));
             iters += it;
-            axpy_kernel<<<blocks_for(nv), 256, 0, st>>>(x, c, nv);
+            axpy_kernel<float2><<<blocks_for(nv), 256, 0, st>>>(x, g->c32, nv);
             EMS_CUDA(cudaGetLastError());
     ++g->launches;
             ++refines;
             zero = false;
         }
-        nmv = A64.count + A32.count;
+        nmv = A64.count + A32f.count;
     } else {
-        Apply& A = (mode == 2) ? A32 : A64;
-        EMS_TRY(gmres_core(h, g, A, b, x, R, m, o->rtol, o->max_iters, true, pc, st, &iters));
+        Apply<double2>& A = (mode == 2) ? A32 : A64;
+        EMS_TRY(gmres_core<double2>(h, g, A, b, x, R, m, o->rtol, o->max_iters, true, pc, st, &iters));
         EMS_TRY(true_residual(h, g, A, b, x, R, st, res.data()));
         nmv = A.count;
     }

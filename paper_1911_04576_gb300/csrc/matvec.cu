@@ -306,7 +306,7 @@ __global__ void macromodel_kernel(const T2* __restrict__ Zt, const double2* __re
                                   const int32_t* __restrict__ idx, const int8_t* __restrict__ sgn,
                                   const int32_t* __restrict__ type_cells,
                                   const MmBlock* __restrict__ blocks, T2* __restrict__ Ymm, int K,
-                                  int M, int R, int n_unique, int chunk) {
+                                  int M, int R, int n_unique, int chunk, const float2* __restrict__ xf) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T2* xs = reinterpret_cast<T2*>(smem_raw);   // [G][chunk] for one r
     const MmBlock b = blocks[blockIdx.x];
@@ -321,9 +321,17 @@ __global__ void macromodel_kernel(const T2* __restrict__ Zt, const double2* __re
             T2 v = zero;
             if (g < b.count && kk < nk) {
                 const size_t loc = (size_t)type_cells[b.first + g] * K + k0 + kk;
-                const double2 xv = x[(size_t)r * n_unique + idx[loc]];
-                const double sg = (double)sgn[loc];
-                v = mk<T2>(sg * xv.x, sg * xv.y);
+                const size_t at = (size_t)r * n_unique + idx[loc];
+                if (xf) {
+                    const float2 xv = xf[at];
+                    const float sg = (float)sgn[loc];
+                    if constexpr (sizeof(T2) == sizeof(float2)) v = make_float2(sg * xv.x, sg * xv.y);
+                    else v = mk<T2>((double)(sg * xv.x), (double)(sg * xv.y));
+                } else {
+                    const double2 xv = x[at];
+                    const double sg = (double)sgn[loc];
+                    v = mk<T2>(sg * xv.x, sg * xv.y);
+                }
             }
             xs[e] = v;
         }
@@ -348,23 +356,28 @@ __global__ void macromodel_kernel(const T2* __restrict__ Zt, const double2* __re
 
 // ------------------------------------------------ K3 tail: U_o^T
 // y[r][u] = sum over local unknowns (m,k) of u: sign * y1[r][m][k]
-template <typename T2>
-__global__ void scatter_kernel(double2* __restrict__ y, const T2* __restrict__ y1,
+// (sums in the grid's precision; V2 is the output vector type)
+template <typename T2, typename V2>
+__global__ void scatter_kernel(V2* __restrict__ y, const T2* __restrict__ y1,
                                const int32_t* __restrict__ ptr, const int32_t* __restrict__ ent,
                                const int8_t* __restrict__ esg, int MK, int R, int n_unique) {
+    using S = decltype(y1[0].x);
     const size_t total = (size_t)R * n_unique;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
          e += (size_t)gridDim.x * blockDim.x) {
         const int u = (int)(e % n_unique);
         const int r = (int)(e / n_unique);
-        double ax = 0.0, ay = 0.0;
+        S ax = 0, ay = 0;
         for (int q = ptr[u]; q < ptr[u + 1]; ++q) {
             const T2 v = y1[(size_t)r * MK + ent[q]];
-            const double s = (double)esg[q];
-            ax += s * (double)v.x;
-            ay += s * (double)v.y;
+            const S s = (S)esg[q];
+            ax += s * v.x;
+            ay += s * v.y;
         }
-        y[e] = make_double2(ax, ay);
+        V2 o;
+        o.x = ax;
+        o.y = ay;
+        y[e] = o;
     }
 }
 
@@ -493,8 +506,8 @@ int derive_fp32_operator(emsurf_handle* h, const emsurf_problem* pr) {
 
 // ---------------------------------------------------------------- apply
 template <typename T2>
-int apply_operator(emsurf_handle* h, Operator<T2>& op, const double2* x, double2* y, int R,
-                   cudaStream_t st) {
+int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, const float2* xf,
+                      double2* y, float2* yf, int R, cudaStream_t st) {
     const int E = h->E, K = h->K, px = h->px, py = h->py;
     const long long lanes = (long long)R * K;
     const bool f64 = sizeof(T2) == sizeof(double2);
@@ -506,21 +519,35 @@ int apply_operator(emsurf_handle* h, Operator<T2>& op, const double2* x, double2
     // (points ix >= nx are the zero padding), then the y-pass with rows
     // iy >= ny taken as zero
     EMS_TRY(fft_pass_gather<T2>(op.Xg, h->plan_x, lanes, h->ny, (long long)px * lanes, h->nx, x,
-                                h->d_uo_index, h->d_uo_sign, h->nx, K, h->n_unique, st));
+                                h->d_uo_index, h->d_uo_sign, h->nx, K, h->n_unique, st, xf));
     EMS_TRY(fft_pass<T2>(op.Xg, h->plan_y, (long long)px * lanes, 1, 0, -1, st, h->ny, py));
     prof_mark(h, ph_fft, false, st);
     prof_mark(h, ph_mm, true, st);
     // K4
-    const int nsplit = std::max(1, std::min(kMmSplit, K / 64));
+    // K splits of the macromodel product: as many as fill one wave of
+    // resident CTAs (a partial second wave would double its time), at most
+    // kMmSplit and at least 32 columns each
+    const int mthreads = std::min(1024, ((K + 31) / 32) * 32);
+    int nsplit = std::max(1, std::min(kMmSplit, K / 32));
+    {
+        int& occ = h->mm_occ[std::is_same<T2, float2>::value ? 0 : 1];
+        if (!occ) {
+            int b = 0;
+            EMS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &b, macromodel_kernel<T2, kMmGroup>, mthreads, (size_t)kMmGroup * ((K + 1) / 2) * sizeof(T2)));
+            occ = std::max(b, 1);
+        }
+        const int slots = h->num_sms * occ;
+        nsplit = std::max(1, std::min(nsplit, slots / std::max(1, h->n_mm_blocks)));
+    }
     {
         const int nblk = h->n_mm_blocks;
         const int chunk = (K + nsplit - 1) / nsplit;
         const MmBlock* blocks = reinterpret_cast<const MmBlock*>(h->d_mm_blocks);
-        const int mthreads = std::min(1024, ((K + 31) / 32) * 32);
         macromodel_kernel<T2, kMmGroup><<<dim3(nblk, nsplit), mthreads,
                                            (size_t)kMmGroup * chunk * sizeof(T2), st>>>(
             op.Zt, x, h->d_uo_index, h->d_uo_sign, h->d_type_cells, blocks, op.Ymm, K, h->M, R,
-            h->n_unique, chunk);
+            h->n_unique, chunk, xf);
         EMS_CUDA(cudaGetLastError());
     }
     prof_mark(h, ph_mm, false, st);
@@ -571,8 +598,12 @@ int apply_operator(emsurf_handle* h, Operator<T2>& op, const double2* x, double2
                               nsplit, R, h->M, K, 1.0 / (double)h->nbins, op.Y1, st));
     prof_mark(h, ph_fft, false, st);
     prof_mark(h, EMS_PH_SCATTER, true, st);
-    scatter_kernel<T2><<<grid_for((size_t)R * h->n_unique, 256), 256, 0, st>>>(
-        y, op.Y1, h->d_inv_ptr, h->d_inv_ent, h->d_inv_sgn, h->M * K, R, h->n_unique);
+    if (yf)
+        scatter_kernel<T2, float2><<<grid_for((size_t)R * h->n_unique, 256), 256, 0, st>>>(
+            yf, op.Y1, h->d_inv_ptr, h->d_inv_ent, h->d_inv_sgn, h->M * K, R, h->n_unique);
+    else
+        scatter_kernel<T2, double2><<<grid_for((size_t)R * h->n_unique, 256), 256, 0, st>>>(
+            y, op.Y1, h->d_inv_ptr, h->d_inv_ent, h->d_inv_sgn, h->M * K, R, h->n_unique);
     EMS_CUDA(cudaGetLastError());
     prof_mark(h, EMS_PH_SCATTER, false, st);
     h->launches += 6;   // 4 FFT passes, macromodel, crop/scatter
@@ -581,6 +612,16 @@ int apply_operator(emsurf_handle* h, Operator<T2>& op, const double2* x, double2
 
 template int build_operator<double2>(emsurf_handle*, Operator<double2>&, const emsurf_problem*);
 template int build_operator<float2>(emsurf_handle*, Operator<float2>&, const emsurf_problem*);
+template <typename T2>
+int apply_operator(emsurf_handle* h, Operator<T2>& op, const double2* x, double2* y, int R,
+                   cudaStream_t st) {
+    return apply_operator_io<T2>(h, op, x, nullptr, y, nullptr, R, st);
+}
+
+int apply_operator_f32(emsurf_handle* h, const float2* x, float2* y, int R, cudaStream_t st) {
+    return apply_operator_io<float2>(h, h->op32, nullptr, x, nullptr, y, R, st);
+}
+
 template int apply_operator<double2>(emsurf_handle*, Operator<double2>&, const double2*, double2*,
                                      int, cudaStream_t);
 template int apply_operator<float2>(emsurf_handle*, Operator<float2>&, const double2*, double2*,

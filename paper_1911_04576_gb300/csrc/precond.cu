@@ -274,7 +274,8 @@ pc_invrows_kernel(const float2* __restrict__ lu, const int64_t* __restrict__ luo
 
 // rs[q][j] = r[q][sub_ids[j]] in FP32 for every subdomain entry j (all cells
 // back to back, each cell's segment starting at an even index).
-__global__ void pc_gather_kernel(const double2* __restrict__ r, const int32_t* __restrict__ sub_ids,
+template <typename VT>
+__global__ void pc_gather_kernel(const VT* __restrict__ r, const int32_t* __restrict__ sub_ids,
                                  const int32_t* __restrict__ sub_cell, const int32_t* __restrict__ sub_ptr,
                                  const int64_t* __restrict__ rs_off, float2* __restrict__ rs,
                                  int total, int n_unique, int64_t rs_stride, int R) {
@@ -283,7 +284,7 @@ __global__ void pc_gather_kernel(const double2* __restrict__ r, const int32_t* _
         const int64_t o = rs_off[m] + (j - sub_ptr[m]);
         const int u = sub_ids[j];
         for (int q = 0; q < R; ++q) {
-            const double2 d = r[(size_t)q * n_unique + u];
+            const VT d = r[(size_t)q * n_unique + u];
             rs[q * rs_stride + o] = make_float2((float)d.x, (float)d.y);
         }
     }
@@ -296,13 +297,13 @@ __global__ void pc_gather_kernel(const double2* __restrict__ r, const int32_t* _
 // all its rows from L1/L2) and reduces once per row and right-hand side.
 // The grid is exactly the resident capacity, so the row list is shared out
 // in one wave.
-template <int RQ>
+template <int RQ, typename VO>
 __global__ void __launch_bounds__(kApThreads, 4)
 pc_apply_kernel(const float2* __restrict__ X, const int64_t* __restrict__ xoff,
                 const int32_t* __restrict__ ldx, const int32_t* __restrict__ own_ptr,
                 const int32_t* __restrict__ sub_ptr, const int32_t* __restrict__ sub_ids,
                 const int64_t* __restrict__ rs_off, const float2* __restrict__ rs, int64_t rs_stride,
-                double2* __restrict__ y, int n_rows, int M, int n_unique, int r0) {
+                VO* __restrict__ y, int n_rows, int M, int n_unique, int r0) {
     const int lane = threadIdx.x & 31;
     const int warps = gridDim.x * (blockDim.x >> 5);
     for (int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < n_rows; g += warps) {
@@ -343,22 +344,28 @@ pc_apply_kernel(const float2* __restrict__ X, const int64_t* __restrict__ xoff,
         if (lane == 0) {
             const int u = sub_ids[sub_ptr[m] + i];
 #pragma unroll
-            for (int q = 0; q < RQ; ++q)
-                y[(size_t)(r0 + q) * n_unique + u] = make_double2((double)acc[q].x, (double)acc[q].y);
+            for (int q = 0; q < RQ; ++q) {
+                VO o;
+                o.x = acc[q].x;
+                o.y = acc[q].y;
+                y[(size_t)(r0 + q) * n_unique + u] = o;
+            }
         }
     }
 }
 
-template <int RQ>
-int launch_apply(emsurf_handle* h, double2* y, int r0, cudaStream_t st) {
-    static int occ[8] = {0};   // resident blocks per SM (same for every device of this build)
-    if (!occ[RQ]) {
+template <int RQ, typename VO>
+int launch_apply(emsurf_handle* h, VO* y, int r0, cudaStream_t st) {
+    // resident blocks per SM (the same for every device of this build)
+    static int occ[8][2] = {};
+    int& o = occ[RQ][sizeof(VO) == sizeof(float2) ? 1 : 0];
+    if (!o) {
         int b = 0;
-        EMS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pc_apply_kernel<RQ>, kApThreads, 0));
-        occ[RQ] = std::max(b, 1);
+        EMS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pc_apply_kernel<RQ, VO>, kApThreads, 0));
+        o = std::max(b, 1);
     }
-    const int blocks = h->num_sms * occ[RQ];
-    pc_apply_kernel<RQ><<<blocks, kApThreads, 0, st>>>(h->pc_mat, h->pc_off, h->pc_ld, h->pc_own_ptr,
+    const int blocks = h->num_sms * o;
+    pc_apply_kernel<RQ, VO><<<blocks, kApThreads, 0, st>>>(h->pc_mat, h->pc_off, h->pc_ld, h->pc_own_ptr,
                                                         h->pc_sub_ptr, h->pc_sub_ids, h->pc_rs_off,
                                                         h->pc_rs + (size_t)r0 * h->pc_rs_stride,
                                                         h->pc_rs_stride, y, h->n_unique, h->M, h->n_unique, r0);
@@ -369,25 +376,34 @@ int launch_apply(emsurf_handle* h, double2* y, int r0, cudaStream_t st) {
 
 }  // namespace
 
-int pc_apply(emsurf_handle* h, const double2* r, double2* y, int R, cudaStream_t st) {
+template <typename VT>
+int pc_apply_t(emsurf_handle* h, const VT* r, VT* y, int R, cudaStream_t st) {
     if (R > h->max_rhs) {
         set_error("preconditioner: %d right-hand sides, handle holds %d", R, h->max_rhs);
         return EMSURF_EINVAL;
     }
     const int total = (int)h->pc_sub_total;
-    pc_gather_kernel<<<std::min((total + 255) / 256, h->num_sms * 8), 256, 0, st>>>(
+    pc_gather_kernel<VT><<<std::min((total + 255) / 256, h->num_sms * 8), 256, 0, st>>>(
         r, h->pc_sub_ids, h->pc_sub_cell, h->pc_sub_ptr, h->pc_rs_off, h->pc_rs, total, h->n_unique,
         h->pc_rs_stride, R);
     EMS_CUDA(cudaGetLastError());
     h->launches += 1;
     for (int r0 = 0; r0 < R; r0 += 4) {
         const int nr = std::min(4, R - r0);
-        if (nr == 1) EMS_TRY(launch_apply<1>(h, y, r0, st));
-        else if (nr == 2) EMS_TRY(launch_apply<2>(h, y, r0, st));
-        else if (nr == 3) EMS_TRY(launch_apply<3>(h, y, r0, st));
-        else EMS_TRY(launch_apply<4>(h, y, r0, st));
+        if (nr == 1) EMS_TRY((launch_apply<1, VT>(h, y, r0, st)));
+        else if (nr == 2) EMS_TRY((launch_apply<2, VT>(h, y, r0, st)));
+        else if (nr == 3) EMS_TRY((launch_apply<3, VT>(h, y, r0, st)));
+        else EMS_TRY((launch_apply<4, VT>(h, y, r0, st)));
     }
     return EMSURF_OK;
+}
+
+int pc_apply(emsurf_handle* h, const double2* r, double2* y, int R, cudaStream_t st) {
+    return pc_apply_t<double2>(h, r, y, R, st);
+}
+
+int pc_apply_f32(emsurf_handle* h, const float2* r, float2* y, int R, cudaStream_t st) {
+    return pc_apply_t<float2>(h, r, y, R, st);
 }
 
 // Subdomains, near tables, assembly and factorisation (create time).
