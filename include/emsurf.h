@@ -101,6 +101,12 @@ typedef struct {
     const double* unknown_xy;
     double cell_a, cell_b;
     double precond_overlap;
+    /* 1: also keep BF16x3 split planes of the FP32 operator (same bytes as
+     * its complex64 spectrum) and run FP32 products with nrhs >= 8 as
+     * tensor-core GEMMs per bin (tcgen05, FP32 accumulation; relative error
+     * per product term <= 3 * 2^-18 instead of 2^-24).  Needs an FP32
+     * operator (EMSURF_FP32 or EMSURF_MIXED) and E >= 64; ignored otherwise. */
+    int32_t tensor_cores;
 } emsurf_problem;
 
 typedef struct {

@@ -40,7 +40,7 @@ class Problem(C.Structure):
         ("precision", C.c_int32), ("tables_on_device", C.c_int32),
         ("device_mem_budget", C.c_int64), ("device", C.c_int32), ("stream", C.c_void_p),
         ("unknown_xy", C.c_void_p), ("cell_a", C.c_double), ("cell_b", C.c_double),
-        ("precond_overlap", C.c_double),
+        ("precond_overlap", C.c_double), ("tensor_cores", C.c_int32),
     ]
 
 
@@ -154,7 +154,7 @@ class Handle:
 def emsurf_create(nx, ny, n_edges, n_unique, type_map, macromodels, offset_L, offset_K, coef,
                   uo_index, uo_sign, precision=FP64, max_rhs=1, grid=(0, 0),
                   tables_on_device=False, device_mem_budget=0, device=0, unknown_xy=None,
-                  cell=(0.0, 0.0), precond_overlap=0.0):
+                  cell=(0.0, 0.0), precond_overlap=0.0, tensor_cores=False):
     """emsurf_create: host NumPy inputs (or torch CUDA tensors for the tables
     and macromodels when tables_on_device=True); returns a Handle.  With
     unknown_xy ([n_unique, 2] from emsurf_setup_unknown_xy), cell = (a, b) and
@@ -185,6 +185,7 @@ def emsurf_create(nx, ny, n_edges, n_unique, type_map, macromodels, offset_L, of
         p.unknown_xy = _ptr(unknown_xy)
     p.cell_a, p.cell_b = cell
     p.precond_overlap = precond_overlap
+    p.tensor_cores = 1 if tensor_cores else 0
     out = C.c_void_p()
     _check(lib().emsurf_create(C.byref(p), C.byref(out)))
     return Handle(out.value, (type_map, uo_index, uo_sign))

@@ -202,6 +202,7 @@ int create_impl(const emsurf_problem* p, emsurf_handle* h) {
         EMS_TRY(derive_fp32_operator(h, p));
         h->have32 = true;
     }
+    if (p->tensor_cores && h->have32 && h->E >= 64) EMS_TRY(tc_build(h));
     if (p->precond_overlap > 0.0 && p->unknown_xy) {
         if (!(p->cell_a > 0.0) || !(p->cell_b > 0.0)) {
             set_error("the preconditioner needs cell_a, cell_b > 0");

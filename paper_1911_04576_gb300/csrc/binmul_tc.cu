@@ -1,0 +1,457 @@
+// Bin multiply on the tensor cores for many right-hand sides (Sec. IV-B,
+// Eqs. LJV3-LJV5 per bin): with R rhs the product B^(k) X^(k) of every bin
+// is a complex GEMM (E x E by E x R, twice: L^ and K^), which at R >= 8 is
+// compute-bound on the FP32 pipes.  Here it runs as BF16x3 split precision
+// on tcgen05 with FP32 accumulation in TMEM:
+//   v = hi + lo (both bf16, hi = rn(v), lo = rn(v - hi)),
+//   A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi,
+// which keeps ~16 significant bits per factor (relative error per product
+// term <= 3 * 2^-18).  The split planes take the same bytes as the FP32
+// complex spectrum, so the kernel stays bound by streaming the spectrum.
+//
+// Complex arithmetic as real GEMMs.  For one bin, operator op in {L, K},
+// test row i, source j:  the "B" operand holds the spectrum as real rows
+// m = 2 i + c (c = 0 real part, 1 imaginary part) over j; the "A" operand
+// holds the X^ planes as real rows rho = 4 r + q (q = 0 Re x_J, 1 Im x_J,
+// 2 Re x_M, 3 Im x_M) over j, 32 rhs per pass (M = 128).  D_op[rho][m] =
+// sum_j A[rho][j] B_op[m][j]; then, e.g., (L x_J)_i = (D_L[4r][2i] -
+// D_L[4r+1][2i+1]) + i (D_L[4r+1][2i] + D_L[4r][2i+1]), combined into
+// y_J = a L x_J + b K x_M and y_M = g K x_J + d L x_M in the epilogue.
+//
+// Kernel: persistent, one CTA per SM, items = (rhs group, bin, chunk of 48
+// test rows).  Warp 0 issues TMA tensor loads (128B swizzle) of 64-source
+// stages into a 2-deep ring; warp 1 issues the MMAs (M = 128, N = 96,
+// K = 16) into one of two TMEM accumulator sets; warps 2-5 drain the other
+// set (tcgen05.ld), combine and store Y^.  Every wait is bounded: on expiry
+// the kernel sets the error flag, waits (bounded) for its copies and MMAs in
+// flight, frees TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace emsurf {
+namespace {
+
+constexpr int kTcM = 128;          // A rows: 32 rhs x 4 planes
+constexpr int kTcRhs = 32;
+constexpr int kTcN = 96;           // B rows per item: 48 test rows x (re, im)
+constexpr int kTcKc = 64;          // sources per stage (128 bytes of bf16)
+constexpr int kTcStages = 2;
+constexpr int kTcThreads = 192;    // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int kTcABytes = kTcM * 128;      // 16 KB
+constexpr int kTcBBytes = kTcN * 128;      // 12 KB
+constexpr int kTcStageBytes = 2 * kTcABytes + 4 * kTcBBytes;   // A hi/lo, B hi/lo x (L, K)
+constexpr int kTcSmem = 1024 + kTcStages * kTcStageBytes;
+constexpr uint32_t kTcTmemCols = 512;     // two accumulator sets of 2 x 96 columns
+constexpr long long kTcWait = 1LL << 22;
+// instruction descriptor: kind::f16, bf16 x bf16 -> f32, K-major A and B, N = 96, M = 128
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
+                              ((uint32_t)(kTcM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
+    for (long long it = 0; it < kTcWait; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(saddr(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void bar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
+}
+__device__ __forceinline__ void bar_expect(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void tma3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(
+            saddr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(saddr(bar)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+// shared-memory matrix descriptor: K-major, 128B swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | (1ull << 16) | (64ull << 32) | (1ull << 46) | (2ull << 61);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(kTcIdesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
+struct TcArgs {
+    float2* Y;            // [bins][R][2E]
+    int E, nbins, R, groups, chunks, nk, items;
+    float2 ca, cb, cg, cd;
+    int* err;
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+binmul_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
+                 const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, TcArgs g) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full[kTcStages], empty[kTcStages], accf[2], acce[2], mma_done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_slot)),
+                     "r"(kTcTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kTcStages; ++s) {
+            bar_init(&full[s], 1);
+            bar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            bar_init(&accf[a], 1);
+            bar_init(&acce[a], 4);
+        }
+        bar_init(&mma_done, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_slot;
+    const int E = g.E, K2 = 2 * g.E;
+
+    if (warp == 0) {
+        // ---------------------------------------------------------- TMA
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int issued[kTcStages] = {0, 0};
+            for (int item = blockIdx.x; item < g.items && !*(volatile int*)&abort_flag; item += gridDim.x) {
+                const int grp = item / (g.nbins * g.chunks), rem = item % (g.nbins * g.chunks);
+                const int bin = rem / g.chunks, ch = rem % g.chunks;
+                for (int ks = 0; ks < g.nk; ++ks) {
+                    if (!bar_wait(&empty[stage], phase ^ 1)) {
+                        atomicExch(g.err, 4);
+                        *(volatile int*)&abort_flag = 1;
+                        break;
+                    }
+                    unsigned char* st = smem + stage * kTcStageBytes;
+                    bar_expect(&full[stage], kTcStageBytes);
+                    const int j0 = ks * kTcKc;
+                    tma3d(st, &mAh, j0, kTcM * grp, bin, &full[stage]);
+                    tma3d(st + kTcABytes, &mAl, j0, kTcM * grp, bin, &full[stage]);
+                    for (int op = 0; op < 2; ++op) {
+                        unsigned char* b = st + 2 * kTcABytes + op * 2 * kTcBBytes;
+                        tma3d(b, &mBh, j0, kTcN * ch, 2 * bin + op, &full[stage]);
+                        tma3d(b + kTcBBytes, &mBl, j0, kTcN * ch, 2 * bin + op, &full[stage]);
+                    }
+                    ++issued[stage];
+                    if (++stage == kTcStages) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
+                }
+            }
+            // every copy this thread issued has landed before the CTA can exit
+            for (int s = 0; s < kTcStages; ++s)
+                if (issued[s] && !bar_wait(&full[s], (uint32_t)((issued[s] - 1) & 1))) atomicExch(g.err, 4);
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------- MMA
+        if (lane == 0) {
+            int stage = 0, acc = 0;
+            uint32_t phase = 0, aphase = 0;
+            bool any = false;
+            for (int item = blockIdx.x; item < g.items && !*(volatile int*)&abort_flag; item += gridDim.x) {
+                if (!bar_wait(&acce[acc], aphase ^ 1)) {
+                    atomicExch(g.err, 5);
+                    *(volatile int*)&abort_flag = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t dL = tmem + (uint32_t)(acc * 256), dK = dL + kTcN;
+                bool ok = true;
+                for (int ks = 0; ks < g.nk; ++ks) {
+                    if (!bar_wait(&full[stage], phase)) {
+                        atomicExch(g.err, 6);
+                        *(volatile int*)&abort_flag = 1;
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const uint32_t st = saddr(smem + stage * kTcStageBytes);
+                    const uint32_t ah = st, al = st + kTcABytes;
+                    for (int kk = 0; kk < kTcKc / 16; ++kk) {
+                        const uint32_t off = 32u * kk;
+                        const uint64_t dah = sdesc(ah + off), dal = sdesc(al + off);
+                        for (int op = 0; op < 2; ++op) {
+                            const uint32_t b = st + 2 * kTcABytes + op * 2 * kTcBBytes;
+                            const uint64_t dbh = sdesc(b + off), dbl = sdesc(b + kTcBBytes + off);
+                            const uint32_t d = op ? dK : dL;
+                            mma_bf16(d, dah, dbh, (ks > 0 || kk > 0) ? 1u : 0u);
+                            mma_bf16(d, dah, dbl, 1u);
+                            mma_bf16(d, dal, dbh, 1u);
+                        }
+                    }
+                    mma_commit(&empty[stage]);   // the stage is free once these MMAs have read it
+                    any = true;
+                    if (++stage == kTcStages) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
+                }
+                if (!ok) break;
+                mma_commit(&accf[acc]);
+                if (++acc == 2) {
+                    acc = 0;
+                    aphase ^= 1;
+                }
+            }
+            // all issued MMAs complete before teardown
+            if (any) {
+                mma_commit(&mma_done);
+                if (!bar_wait(&mma_done, 0)) atomicExch(g.err, 7);
+            }
+        }
+    } else {
+        // ---------------------------------------------------------- epilogue
+        const int qd = warp & 3;                 // TMEM lane quadrant of this warp
+        const int rho = 32 * qd + lane, rl = rho >> 2, q = rho & 3;
+        const int base = lane & ~3;
+        int acc = 0;
+        uint32_t aphase = 0;
+        for (int item = blockIdx.x; item < g.items && !*(volatile int*)&abort_flag; item += gridDim.x) {
+            const int grp = item / (g.nbins * g.chunks), rem = item % (g.nbins * g.chunks);
+            const int bin = rem / g.chunks, ch = rem % g.chunks;
+            if (!bar_wait(&accf[acc], aphase)) {
+                if (lane == 0) atomicExch(g.err, 8);
+                *(volatile int*)&abort_flag = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const int r = kTcRhs * grp + rl;
+            const uint32_t t0 = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(acc * 256);
+            float2* Yb = g.Y + ((size_t)bin * g.R + (r < g.R ? r : 0)) * K2;
+            for (int c0 = 0; c0 < kTcN; c0 += 32) {
+                uint32_t a[32], b[32];
+                tmem_ld32(t0 + c0, a);
+                tmem_ld32(t0 + kTcN + c0, b);
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+                for (int t = 0; t < 16; ++t) {
+                    float LR[4], LI[4], KR[4], KI[4];
+#pragma unroll
+                    for (int s = 0; s < 4; ++s) {
+                        LR[s] = __shfl_sync(0xffffffffu, __uint_as_float(a[2 * t]), base + s);
+                        LI[s] = __shfl_sync(0xffffffffu, __uint_as_float(a[2 * t + 1]), base + s);
+                        KR[s] = __shfl_sync(0xffffffffu, __uint_as_float(b[2 * t]), base + s);
+                        KI[s] = __shfl_sync(0xffffffffu, __uint_as_float(b[2 * t + 1]), base + s);
+                    }
+                    const int i = ch * (kTcN / 2) + c0 / 2 + t;
+                    if (r < g.R && i < E && q < 2) {
+                        float2 y;
+                        if (q == 0) {
+                            // y_J = a L x_J + b K x_M
+                            const float uR = LR[0] - LI[1], uI = LR[1] + LI[0];
+                            const float wR = KR[2] - KI[3], wI = KR[3] + KI[2];
+                            y.x = g.ca.x * uR - g.ca.y * uI + g.cb.x * wR - g.cb.y * wI;
+                            y.y = g.ca.x * uI + g.ca.y * uR + g.cb.x * wI + g.cb.y * wR;
+                            Yb[i] = y;
+                        } else {
+                            // y_M = g K x_J + d L x_M
+                            const float wR = KR[0] - KI[1], wI = KR[1] + KI[0];
+                            const float uR = LR[2] - LI[3], uI = LR[3] + LI[2];
+                            y.x = g.cg.x * wR - g.cg.y * wI + g.cd.x * uR - g.cd.y * uI;
+                            y.y = g.cg.x * wI + g.cg.y * wR + g.cd.x * uI + g.cd.y * uR;
+                            Yb[E + i] = y;
+                        }
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) bar_arrive(&acce[acc]);
+            if (++acc == 2) {
+                acc = 0;
+                aphase ^= 1;
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols));
+}
+
+// Split planes of the spectrum, test-major: out[bin][op][2i+c][j] = hi/lo of
+// (c ? Im : Re) Bhat[bin][op][j][i] (source-major FP32), rows padded to ej.
+__global__ void tc_split_spectrum_kernel(const float2* __restrict__ Bhat, __nv_bfloat16* __restrict__ hi,
+                                         __nv_bfloat16* __restrict__ lo, int E, int ej) {
+    __shared__ float2 tile[32][33];
+    const int bo = blockIdx.z;                  // bin * 2 + op
+    const int j0 = blockIdx.x * 32, i0 = blockIdx.y * 32;
+    const float2* src = Bhat + (size_t)bo * E * E;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int j = j0 + r, i = i0 + threadIdx.x;
+        tile[r][threadIdx.x] = (j < E && i < E) ? src[(size_t)j * E + i] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    // write rows m = 2i + c, columns j (j < ej; padding columns are zero)
+    for (int r = threadIdx.y; r < 64; r += blockDim.y) {
+        const int il = r >> 1, c = r & 1, i = i0 + il, j = j0 + threadIdx.x;
+        if (i >= E || j >= ej) continue;
+        const float v = c ? tile[threadIdx.x][il].y : tile[threadIdx.x][il].x;
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+        const size_t at = ((size_t)bo * 2 * E + (size_t)(2 * i + c)) * ej + j;
+        hi[at] = h;
+        lo[at] = l;
+    }
+}
+
+// Split planes of X^: out[bin][4r+q][j], q = (Re x_J, Im x_J, Re x_M, Im x_M),
+// zero for r >= R and j >= E.
+__global__ void tc_split_x_kernel(const float2* __restrict__ X, __nv_bfloat16* __restrict__ hi,
+                                  __nv_bfloat16* __restrict__ lo, int E, int ej, int R, int rows, size_t total) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e % ej);
+        const size_t br = e / ej;
+        const int rho = (int)(br % rows);
+        const size_t bin = br / rows;
+        const int r = rho >> 2, q = rho & 3;
+        float v = 0.f;
+        if (r < R && j < E) {
+            const float2 x = X[(bin * R + r) * (size_t)(2 * E) + (q >> 1) * E + j];
+            v = (q & 1) ? x.y : x.x;
+        }
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        hi[e] = h;
+        lo[e] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+int encode3d(CUtensorMap* map, void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b0, uint32_t b1) {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            !p) {
+            set_error("tensor-core path: cuTensorMapEncodeTiled is not available");
+            return EMSURF_ECUDA;
+        }
+        fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    const cuuint64_t dims[3] = {d0, d1, d2};
+    const cuuint64_t strides[2] = {d0 * 2, d0 * 2 * d1};
+    const cuuint32_t box[3] = {b0, b1, 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("tensor-core path: tensor map encoding failed (%d)", (int)r);
+        return EMSURF_ECUDA;
+    }
+    return EMSURF_OK;
+}
+
+}  // namespace
+
+// Create-time: split planes of the FP32 spectrum and the tensor maps.
+int tc_build(emsurf_handle* h) {
+    const int E = h->E;
+    const int ej = (E + 7) & ~7;     // rows of 16-byte multiples
+    const int rows = 4 * kTcRhs * ((h->max_rhs + kTcRhs - 1) / kTcRhs);
+    const size_t nb = (size_t)h->nbins;
+    const size_t spec = nb * 2 * 2 * E * ej;
+    EMS_TRY(dev_alloc(h, (void**)&h->tc_Bh, spec * sizeof(__nv_bfloat16)));
+    EMS_TRY(dev_alloc(h, (void**)&h->tc_Bl, spec * sizeof(__nv_bfloat16)));
+    EMS_CUDA(cudaMemsetAsync(h->tc_Bh, 0, spec * sizeof(__nv_bfloat16), h->setup_stream));
+    EMS_CUDA(cudaMemsetAsync(h->tc_Bl, 0, spec * sizeof(__nv_bfloat16), h->setup_stream));
+    const size_t xs = nb * rows * ej;
+    EMS_TRY(dev_alloc(h, (void**)&h->tc_Xh, xs * sizeof(__nv_bfloat16)));
+    EMS_TRY(dev_alloc(h, (void**)&h->tc_Xl, xs * sizeof(__nv_bfloat16)));
+    const dim3 grid((E + 31) / 32, (E + 31) / 32, (unsigned)(nb * 2));
+    tc_split_spectrum_kernel<<<grid, dim3(32, 8), 0, h->setup_stream>>>(
+        h->op32.Bhat, reinterpret_cast<__nv_bfloat16*>(h->tc_Bh), reinterpret_cast<__nv_bfloat16*>(h->tc_Bl), E, ej);
+    EMS_CUDA(cudaGetLastError());
+    h->launches += 1;
+    static_assert(sizeof(CUtensorMap) <= sizeof(h->tc_maps[0]), "tensor map storage");
+    CUtensorMap* m = reinterpret_cast<CUtensorMap*>(h->tc_maps);
+    EMS_TRY(encode3d(&m[0], h->tc_Xh, ej, rows, nb, kTcKc, kTcM));
+    EMS_TRY(encode3d(&m[1], h->tc_Xl, ej, rows, nb, kTcKc, kTcM));
+    EMS_TRY(encode3d(&m[2], h->tc_Bh, ej, 2 * E, 2 * nb, kTcKc, kTcN));
+    EMS_TRY(encode3d(&m[3], h->tc_Bl, ej, 2 * E, 2 * nb, kTcKc, kTcN));
+    h->tc_ej = ej;
+    h->tc_rows = rows;
+    h->have_tc = true;
+    return EMSURF_OK;
+}
+
+// Y^ = B^ X^ for every bin on the tensor cores (R rhs, FP32 grids [bins][R][2E]).
+int tc_binmul(emsurf_handle* h, const float2* X, float2* Y, int R, const float2* coef, cudaStream_t st) {
+    const int E = h->E, ej = h->tc_ej, rows = h->tc_rows;
+    const size_t nb = (size_t)h->nbins;
+    const size_t xs = nb * rows * ej;
+    tc_split_x_kernel<<<(int)std::min<size_t>((xs + 255) / 256, (size_t)h->num_sms * 16), 256, 0, st>>>(
+        X, reinterpret_cast<__nv_bfloat16*>(h->tc_Xh), reinterpret_cast<__nv_bfloat16*>(h->tc_Xl), E, ej, R, rows, xs);
+    EMS_CUDA(cudaGetLastError());
+    TcArgs a;
+    a.Y = Y;
+    a.E = E;
+    a.nbins = (int)nb;
+    a.R = R;
+    a.groups = (R + kTcRhs - 1) / kTcRhs;
+    a.chunks = (2 * E + kTcN - 1) / kTcN;
+    a.nk = (ej + kTcKc - 1) / kTcKc;
+    a.items = a.groups * a.nbins * a.chunks;
+    a.ca = coef[0];
+    a.cb = coef[1];
+    a.cg = coef[2];
+    a.cd = coef[3];
+    a.err = h->d_err;
+    EMS_TRY(set_smem_once(binmul_tc_kernel, (size_t)kTcSmem));
+    const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(h->tc_maps);
+    const int grid = std::min(a.items, h->num_sms);
+    binmul_tc_kernel<<<grid, kTcThreads, kTcSmem, st>>>(m[0], m[1], m[2], m[3], a);
+    EMS_CUDA(cudaGetLastError());
+    h->launches += 2;
+    return EMSURF_OK;
+}
+
+}  // namespace emsurf

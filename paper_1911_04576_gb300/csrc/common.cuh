@@ -167,6 +167,14 @@ struct emsurf_handle {
     emsurf::Operator<float2> op32;
     bool have64 = false, have32 = false;
     int num_sms = 0;
+    // BF16x3 split planes of the FP32 operator for the tensor-core bin multiply
+    bool have_tc = false;
+    void* tc_Bh = nullptr;          // spectrum hi/lo [bin][op][2i+c][ej] bf16
+    void* tc_Bl = nullptr;
+    void* tc_Xh = nullptr;          // X^ planes hi/lo [bin][rows][ej] bf16
+    void* tc_Xl = nullptr;
+    int tc_ej = 0, tc_rows = 0;
+    alignas(64) unsigned char tc_maps[4][128];   // tensor maps (X hi, X lo, B hi, B lo)
     int mm_occ[2] = {0, 0};                // resident macromodel CTAs per SM (FP32, FP64)
     cudaStream_t setup_stream = nullptr;   // stream of the create-time work
     // near-field preconditioner (restricted additive Schwarz, FP32 LU blocks)
@@ -224,6 +232,10 @@ int apply_operator(emsurf_handle* h, Operator<T2>& op, const double2* x, double2
 int apply_operator_f32(emsurf_handle* h, const float2* x, float2* y, int R, cudaStream_t st);
 int pc_build(emsurf_handle* h, const emsurf_problem* p);
 int wait_selftest(emsurf_handle* h, long long limit, cudaStream_t st);
+// tensor-core bin multiply (BF16x3) for nrhs >= kTcMinRhs
+constexpr int kTcMinRhs = 8;
+int tc_build(emsurf_handle* h);
+int tc_binmul(emsurf_handle* h, const float2* X, float2* Y, int R, const float2* coef, cudaStream_t st);
 int pc_apply(emsurf_handle* h, const double2* r, double2* y, int R, cudaStream_t st);
 int pc_apply_f32(emsurf_handle* h, const float2* r, float2* y, int R, cudaStream_t st);
 int gmres_solve(emsurf_handle* h, const double2* b, double2* x, int nrhs,

@@ -557,9 +557,15 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
     const int nb = h->nbins;
     bool bin_done = false;
     if constexpr (std::is_same<T2, float2>::value) {
+        if (h->have_tc && R >= kTcMinRhs) {
+            EMS_TRY(tc_binmul(h, op.Xg, op.Yg, R, op.coef, st));
+            bin_done = true;
+        }
+    }
+    if constexpr (std::is_same<T2, float2>::value) {
         const size_t smem = binmul_tma_smem(E);
         // the x double buffer needs at least kBmStages stages per bin
-        if (R == 1 && smem <= 227 * 1024 && E + 32 <= 1024 && (E + kBmJB - 1) / kBmJB >= kBmStages) {
+        if (!bin_done && R == 1 && smem <= 227 * 1024 && E + 32 <= 1024 && (E + kBmJB - 1) / kBmJB >= kBmStages) {
             EMS_TRY(set_smem_once(binmul_tma_kernel, smem));
             const int grid = std::min(nb, std::max(1, h->num_sms));
             binmul_tma_kernel<<<grid, 32 * (1 + (E + 31) / 32), smem, st>>>(
