@@ -47,6 +47,9 @@ PC_OVERLAP = 0.6               # preconditioner margin, in mesh cells (a / n)
 BINMUL_DRAM_BYTES_PER_BIN = (767108096 + 5353216) / 576
 
 
+FALLBACK_BF16_TFLOPS = 1900.0
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -54,6 +57,67 @@ def peaks():
             d = json.load(f)
         return float(d.get("hbm_gbs", FALLBACK_HBM_GBS)), "measured"
     return FALLBACK_HBM_GBS, "fallback"
+
+
+def bf16_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        if "bf16_tflops" in d:
+            return float(d["bf16_tflops"]), "measured"
+    return FALLBACK_BF16_TFLOPS, "fallback"
+
+
+MULTI_RHS = 32
+
+
+def multi_rhs_section(B, W, torch, w, hbm):
+    """FP32 products with MULTI_RHS right-hand sides: the tensor-core bin
+    multiply (BF16x3) against the FP32 register-blocked kernel."""
+    out = {"R": MULTI_RHS}
+    tflops_peak, tkind = bf16_peak()
+    for tc in (True, False):
+        h, _, nu, _ = build_problem(B, W, torch, w, B.FP32, precond=False, max_rhs=MULTI_RHS,
+                                    tensor_cores=tc)
+        px, py, _ = B.emsurf_query(h)
+        P = px * py
+        x = torch.randn((MULTI_RHS, nu), dtype=torch.complex128, device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(3):
+            B.emsurf_matvec(h, x, y, B.FP32)
+        torch.cuda.synchronize()
+        B.emsurf_profile(h, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 10
+        e0.record()
+        for _ in range(reps):
+            B.emsurf_matvec(h, x, y, B.FP32)
+        e1.record()
+        torch.cuda.synchronize()
+        B.emsurf_profile(h, False)
+        bm, n = B.emsurf_profile_read(h, "binmul32")
+        bm /= max(n, 1)
+        ph = {k: round(B.emsurf_profile_read(h, k)[0] / reps, 4) for k in ("fft32", "mm32", "scatter")}
+        useful = 32.0 * w.E * w.E * MULTI_RHS * P        # complex MACs x 8 flops
+        spec = 2 * w.E * w.E * P * 8                     # complex64 spectrum (= bf16 hi + lo)
+        key = "tensor_bf16x3" if tc else "fp32_simt"
+        out[key] = {"matvec_ms": round(e0.elapsed_time(e1) / reps, 3), "binmul_ms": round(bm, 4),
+                    "useful_tflops": round(useful / bm / 1e9, 1),
+                    "spectrum_gbs": round(spec / bm / 1e6, 1), "other_phases_ms": ph}
+        if tc:
+            # MMA work issued: 3 split passes x 2 operators x 2 M N K per bin, with
+            # M = 128 per 32 rhs, N = 2E in chunks of 96, K = E in stages of 64
+            groups, chunks, nk = -(-MULTI_RHS // 32), -(-2 * w.E // 96), -(-w.E // 64)
+            executed = 3 * 2 * 2.0 * (128 * groups) * (96 * chunks) * (64 * nk) * P
+            out[key]["tensor_tflops_executed"] = round(executed / bm / 1e9, 1)
+            out[key]["tensor_frac"] = round(executed / bm / 1e9 / tflops_peak, 4)
+            out[key]["hbm_frac"] = round(spec / bm / 1e6 / hbm, 4)
+            out[key]["peak_kind"] = tkind
+        h.close()
+        torch.cuda.empty_cache()
+    out["speedup"] = round(out["fp32_simt"]["binmul_ms"] / out["tensor_bf16x3"]["binmul_ms"], 2)
+    return out
 
 
 class ClockSampler:
@@ -116,7 +180,7 @@ def dist_init():
     return ws, rank, local
 
 
-def build_problem(B, W, torch, w, precision, precond=True):
+def build_problem(B, W, torch, w, precision, precond=True, max_rhs=None, tensor_cores=False):
     """Product-path setup (untimed): U_o, tables, macromodels, handle with
     the near-field preconditioner, V."""
     A, H = W.PERIOD, W.BOX_H
@@ -134,9 +198,10 @@ def build_problem(B, W, torch, w, precision, precond=True):
     t_mm = time.time() - t0
     t0 = time.time()
     h = B.emsurf_create(w.nx, w.ny, w.E, nu, W.type_map(w), Z, L, K, coef, idx, sgn,
-                        precision=precision, max_rhs=w.n_rhs, tables_on_device=True,
+                        precision=precision, max_rhs=max_rhs or w.n_rhs, tables_on_device=True,
                         unknown_xy=xy, cell=(A, A),
-                        precond_overlap=PC_OVERLAP * A / w.n if precond else 0.0)
+                        precond_overlap=PC_OVERLAP * A / w.n if precond else 0.0,
+                        tensor_cores=tensor_cores)
     torch.cuda.synchronize()
     t_create = time.time() - t0
     del L, K, Z
@@ -183,7 +248,7 @@ def cpu_oracle_matvec_seconds(W, w, nu_expected):
 
 SERVE_SIZES = (8, 12, 16)      # lattice N x N of the serving stream
 SERVE_MESH = (3, 4)            # boxes meshed n x n: K = 324 or 576
-SERVE_RHS = (1, 2)
+SERVE_RHS = tuple(range(1, 17))   # rhs per request, uniform in 1..16
 SERVE_RATE = 20.0              # Poisson arrivals per second
 SERVE_BUDGET = 80 << 30        # device-memory budget of the server
 
@@ -279,12 +344,18 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="lattice16x16_k576")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--multi-rhs", type=int, default=1,
+                    help="also time %d-rhs FP32 products, tensor cores vs FP32 kernels (0 = skip)" % 32)
     ap.add_argument("--serve-requests", type=int, default=10,
                     help="requests of the serving stream (0 = skip the serving measurement)")
     ap.add_argument("--matvecs-only", type=int, default=0,
                     help="profiler driver: build the workload, run this many products, exit")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32", "fp64"],
                     help="operators kept resident (--matvecs-only)")
+    ap.add_argument("--rhs", type=int, default=0,
+                    help="profiler driver: right-hand sides of the --matvecs-only products")
+    ap.add_argument("--tensor-cores", action="store_true",
+                    help="profiler driver: build the tensor-core planes (--matvecs-only)")
     ap.add_argument("--solve-iters", type=int, default=0,
                     help="profiler driver: with --matvecs-only, also run one mixed solve capped "
                          "at this many GMRES iterations")
@@ -305,9 +376,11 @@ def main():
     cpu = None
     if args.matvecs_only:
         prec = {"mixed": B.MIXED, "fp32": B.FP32, "fp64": B.FP64}[args.precision]
-        h, V, nu, _ = build_problem(B, W, torch, w, prec)
+        R = args.rhs or w.n_rhs
+        h, V, nu, _ = build_problem(B, W, torch, w, prec, max_rhs=max(R, w.n_rhs),
+                                    tensor_cores=args.tensor_cores)
         for p in ((B.FP32,) if prec == B.FP32 else (B.FP64,) if prec == B.FP64 else (B.FP32, B.FP64)):
-            x = torch.randn((w.n_rhs, nu), dtype=torch.complex128, device="cuda")
+            x = torch.randn((R, nu), dtype=torch.complex128, device="cuda")
             y = torch.empty_like(x)
             for _ in range(args.matvecs_only):
                 B.emsurf_matvec(h, x, y, p)
@@ -400,15 +473,19 @@ def main():
     f1.record()
     torch.cuda.synchronize()
     e2e_ms = f0.elapsed_time(f1) / args.steps
+    # ------------------------------------------------------------ many rhs
+    multi = multi_rhs_section(B, W, torch, w, hbm) if args.multi_rhs else None
     # ------------------------------------------------------------ serving
     serve = None
     if args.serve_requests > 0:
         h.close()          # free the bench handle's device memory for the server
-        serve = {"stream": "Poisson %.0f/s; lattices %s, K %s, rhs %s, 32-type library; rtol %g"
+        serve = {"stream": "Poisson %.0f/s; lattices %s, K %s, rhs %d..%d, 32-type library; rtol %g; "
+                           "near-field preconditioner in both arms; MIXED requests with >= 8 rhs "
+                           "use the tensor-core bin multiply"
                            % (SERVE_RATE, list(SERVE_SIZES), [36 * m * m for m in SERVE_MESH],
-                              list(SERVE_RHS), RTOL),
+                              SERVE_RHS[0], SERVE_RHS[-1], RTOL),
                  "mixed_batched": serve_stream(B, W, args.serve_requests, 7, B.MIXED, 4, True),
-                 "fp64_one_at_a_time": serve_stream(B, W, args.serve_requests, 7, B.FP64, 1, False)}
+                 "fp64_one_at_a_time": serve_stream(B, W, args.serve_requests, 7, B.FP64, 1, True)}
     # ------------------------------------------------------------ CPU oracle
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         t_cpu = cpu_oracle_matvec_seconds(W, w, nu)
@@ -484,6 +561,7 @@ def main():
                 "d2h_bytes_per_step": int(V.numel() * 16)},
         "gpu_launches": int(launches),
         "clocks": clk,
+        "multi_rhs": multi,
         "serve": serve,
         "setup": setup,
         "device_bytes": dev_bytes,

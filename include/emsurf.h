@@ -342,7 +342,9 @@ EMSURF_API int emsurf_far_field(emsurf_handle* h, double a, double b, double hgt
  * continuous batching of whole lattice solves.  A request describes one
  * lattice; a server worker builds it on the device (U_o, offset tables,
  * macromodels, FFT-domain operator, excitation), solves Eq. final and copies
- * the currents to x_out.  Up to max_active requests run at once, each on its
+ * the currents to x_out.  Requests with nrhs >= 8 and an FP32 operator use
+ * the tensor-core bin multiply (see tensor_cores in emsurf_problem).  Up to
+ * max_active requests run at once, each on its
  * own non-blocking stream; a queued request is admitted (first fit) when a
  * slot is free and its device-memory estimate (emsurf_request_bytes) fits
  * in what the budget has left.                                            */

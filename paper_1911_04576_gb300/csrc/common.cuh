@@ -175,7 +175,8 @@ struct emsurf_handle {
     void* tc_Xl = nullptr;
     int tc_ej = 0, tc_rows = 0;
     alignas(64) unsigned char tc_maps[4][128];   // tensor maps (X hi, X lo, B hi, B lo)
-    int mm_occ[2] = {0, 0};                // resident macromodel CTAs per SM (FP32, FP64)
+    int mm_occ[4] = {0, 0, 0, 0};          // resident macromodel CTAs per SM (FP32, FP64; x 1 / 4 rhs)
+    int mm_threads[4] = {0, 0, 0, 0};      // macromodel block size per variant
     cudaStream_t setup_stream = nullptr;   // stream of the create-time work
     // near-field preconditioner (restricted additive Schwarz, FP32 LU blocks)
     bool have_pc = false;

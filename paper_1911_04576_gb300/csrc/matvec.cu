@@ -301,27 +301,28 @@ struct MmBlock {
     int type, first, count;
 };
 
-template <typename T2, int G>
+// RB rhs per pass share every load of Z (register block G cells x RB rhs).
+template <typename T2, int G, int RB>
 __global__ void macromodel_kernel(const T2* __restrict__ Zt, const double2* __restrict__ x,
                                   const int32_t* __restrict__ idx, const int8_t* __restrict__ sgn,
                                   const int32_t* __restrict__ type_cells,
                                   const MmBlock* __restrict__ blocks, T2* __restrict__ Ymm, int K,
                                   int M, int R, int n_unique, int chunk, const float2* __restrict__ xf) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T2* xs = reinterpret_cast<T2*>(smem_raw);   // [G][chunk] for one r
+    T2* xs = reinterpret_cast<T2*>(smem_raw);   // [RB][G][chunk]
     const MmBlock b = blocks[blockIdx.x];
     const int s = blockIdx.y;
     const int k0 = s * chunk, k1 = min(K, k0 + chunk), nk = k1 - k0;
     const T2 zero = mk<T2>(0.0, 0.0);
     const T2* Z = Zt + (size_t)b.type * K * K;
-    for (int r = 0; r < R; ++r) {
+    for (int r0 = 0; r0 < R; r0 += RB) {
         __syncthreads();
-        for (int e = threadIdx.x; e < G * chunk; e += blockDim.x) {
-            const int g = e / chunk, kk = e - (e / chunk) * chunk;
+        for (int e = threadIdx.x; e < RB * G * chunk; e += blockDim.x) {
+            const int rr = e / (G * chunk), g = (e / chunk) % G, kk = e % chunk;
             T2 v = zero;
-            if (g < b.count && kk < nk) {
+            if (r0 + rr < R && g < b.count && kk < nk) {
                 const size_t loc = (size_t)type_cells[b.first + g] * K + k0 + kk;
-                const size_t at = (size_t)r * n_unique + idx[loc];
+                const size_t at = (size_t)(r0 + rr) * n_unique + idx[loc];
                 if (xf) {
                     const float2 xv = xf[at];
                     const float sg = (float)sgn[loc];
@@ -337,19 +338,25 @@ __global__ void macromodel_kernel(const T2* __restrict__ Zt, const double2* __re
         }
         __syncthreads();
         for (int k = threadIdx.x; k < K; k += blockDim.x) {
-            T2 acc[G];
+            T2 acc[RB][G];
 #pragma unroll
-            for (int g = 0; g < G; ++g) acc[g] = zero;
+            for (int rr = 0; rr < RB; ++rr)
+#pragma unroll
+                for (int g = 0; g < G; ++g) acc[rr][g] = zero;
 #pragma unroll 4
             for (int kk = 0; kk < nk; ++kk) {
                 const T2 z = __ldg(Z + (size_t)(k0 + kk) * K + k);
 #pragma unroll
-                for (int g = 0; g < G; ++g) cfma(acc[g], z, xs[g * chunk + kk]);
+                for (int rr = 0; rr < RB; ++rr)
+#pragma unroll
+                    for (int g = 0; g < G; ++g) cfma(acc[rr][g], z, xs[(rr * G + g) * chunk + kk]);
             }
 #pragma unroll
-            for (int g = 0; g < G; ++g)
-                if (g < b.count)
-                    Ymm[(((size_t)s * R + r) * M + type_cells[b.first + g]) * K + k] = acc[g];
+            for (int rr = 0; rr < RB; ++rr)
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+                    if (g < b.count && r0 + rr < R)
+                        Ymm[(((size_t)s * R + r0 + rr) * M + type_cells[b.first + g]) * K + k] = acc[rr][g];
         }
     }
 }
@@ -527,14 +534,28 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
     // K splits of the macromodel product: as many as fill one wave of
     // resident CTAs (a partial second wave would double its time), at most
     // kMmSplit and at least 32 columns each
-    const int mthreads = std::min(1024, ((K + 31) / 32) * 32);
+    const bool blk4 = R >= 4;      // 4 rhs share each load of Z
+    const int variant = (std::is_same<T2, float2>::value ? 0 : 1) + (blk4 ? 2 : 0);
+    int& mthreads = h->mm_threads[variant];
+    if (!mthreads) {
+        // one thread per output row, capped by what the kernel's registers allow
+        cudaFuncAttributes fa;
+        if (blk4) EMS_CUDA(cudaFuncGetAttributes(&fa, macromodel_kernel<T2, kMmGroup, 4>));
+        else EMS_CUDA(cudaFuncGetAttributes(&fa, macromodel_kernel<T2, kMmGroup, 1>));
+        mthreads = std::max(32, (std::min(fa.maxThreadsPerBlock, ((K + 31) / 32) * 32) / 32) * 32);
+    }
     int nsplit = std::max(1, std::min(kMmSplit, K / 32));
     {
-        int& occ = h->mm_occ[std::is_same<T2, float2>::value ? 0 : 1];
+        int& occ = h->mm_occ[variant];
         if (!occ) {
             int b = 0;
-            EMS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &b, macromodel_kernel<T2, kMmGroup>, mthreads, (size_t)kMmGroup * ((K + 1) / 2) * sizeof(T2)));
+            const size_t sm = (size_t)(blk4 ? 4 : 1) * kMmGroup * ((K + 1) / 2) * sizeof(T2);
+            if (blk4)
+                EMS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, macromodel_kernel<T2, kMmGroup, 4>,
+                                                                       mthreads, sm));
+            else
+                EMS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, macromodel_kernel<T2, kMmGroup, 1>,
+                                                                       mthreads, sm));
             occ = std::max(b, 1);
         }
         const int slots = h->num_sms * occ;
@@ -544,10 +565,18 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
         const int nblk = h->n_mm_blocks;
         const int chunk = (K + nsplit - 1) / nsplit;
         const MmBlock* blocks = reinterpret_cast<const MmBlock*>(h->d_mm_blocks);
-        macromodel_kernel<T2, kMmGroup><<<dim3(nblk, nsplit), mthreads,
-                                           (size_t)kMmGroup * chunk * sizeof(T2), st>>>(
-            op.Zt, x, h->d_uo_index, h->d_uo_sign, h->d_type_cells, blocks, op.Ymm, K, h->M, R,
-            h->n_unique, chunk, xf);
+        if (blk4) {
+            const size_t sm = (size_t)4 * kMmGroup * chunk * sizeof(T2);
+            EMS_TRY(set_smem_once(macromodel_kernel<T2, kMmGroup, 4>, sm));
+            macromodel_kernel<T2, kMmGroup, 4><<<dim3(nblk, nsplit), mthreads, sm, st>>>(
+                op.Zt, x, h->d_uo_index, h->d_uo_sign, h->d_type_cells, blocks, op.Ymm, K, h->M, R,
+                h->n_unique, chunk, xf);
+        } else {
+            macromodel_kernel<T2, kMmGroup, 1><<<dim3(nblk, nsplit), mthreads,
+                                                 (size_t)kMmGroup * chunk * sizeof(T2), st>>>(
+                op.Zt, x, h->d_uo_index, h->d_uo_sign, h->d_type_cells, blocks, op.Ymm, K, h->M, R,
+                h->n_unique, chunk, xf);
+        }
         EMS_CUDA(cudaGetLastError());
     }
     prof_mark(h, ph_mm, false, st);

@@ -59,6 +59,9 @@ int64_t request_bytes(const emsurf_request& q) {
     if (q.precision == EMSURF_FP64) op = b64 + mm;
     else if (q.precision == EMSURF_FP32) op = b32 + b64 + mm;          // FP64 spectrum is a temporary
     else op = b64 + b32 + mm + mm / 2;
+    // BF16x3 planes of the tensor-core path: spectrum (= b32) + X^ planes
+    if (q.precision != EMSURF_FP64 && q.nrhs >= kTcMinRhs && E >= 64)
+        op += b32 + P * 4LL * 32 * ((R + 31) / 32) * E * 4;
     const int64_t work = 2LL * P * R * K * 16 + 10LL * R * M * K * 16;
     int64_t krylov = (int64_t)(std::max(q.opts.restart, 1) + 8) * R * M * K * 16;
     int64_t pc = 0;
@@ -140,6 +143,8 @@ int run_job(emsurf_server* sv, Job& jb, cudaStream_t st) {
         p.tables_on_device = 1;
         p.device = sv->device;
         p.stream = st;
+        // many right-hand sides: FP32 products as tensor-core GEMMs
+        p.tensor_cores = (q.precision != EMSURF_FP64 && q.nrhs >= kTcMinRhs) ? 1 : 0;
         std::vector<double> xy;
         if (q.precond_overlap > 0.0) {
             xy.resize((size_t)2 * nu);
