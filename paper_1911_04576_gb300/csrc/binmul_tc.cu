@@ -359,6 +359,235 @@ __global__ void tc_split_x_kernel(const float2* __restrict__ X, __nv_bfloat16* _
     }
 }
 
+// ---------------------------------------------------------------- macromodels
+// The per-type macromodel product (Eq. Zmacromodel_Array) with many rhs is a
+// complex GEMM per type t: Y1[r][m] = Z~^t x1[r][m] for the cells m of type
+// t, i.e. K x K times K x (cells_t R).  Same BF16x3 scheme: "A" = the x1
+// planes of a tile of 64 complex columns (cell, rhs) of one type, rows
+// rho = 2c + q (q = Re, Im of column c); "B" = the Z~^t planes, rows
+// m = 2k + c over k'.  Re y_k = D[2c][2k] - D[2c+1][2k+1],
+// Im y_k = D[2c+1][2k] + D[2c][2k+1].  Items = (tile, chunk of 48 rows k),
+// 3 stages of 56 KB, one TMEM accumulator set of 96 columns per item
+// (two sets alternate).
+constexpr int kMmStageBytes = 2 * kTcABytes + 2 * kTcBBytes;   // 56 KB
+constexpr int kMmStages = 3;
+constexpr int kMmSmem = 1024 + kMmStages * kMmStageBytes;
+constexpr uint32_t kMmTmemCols = 256;
+
+struct MmArgs {
+    float2* Y;                    // Ymm[0] = [R][M][K]
+    const int2* tiles;            // (type, first column)
+    const int32_t* type_ptr;      // [T+1] cells of each type in type_cells
+    const int32_t* type_cells;
+    int K, M, R, ntiles, chunks, nk, items;
+    int* err;
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+mm_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
+             const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, MmArgs g) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full[kMmStages], empty[kMmStages], accf[2], acce[2], mma_done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_slot)),
+                     "r"(kMmTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kMmStages; ++s) {
+            bar_init(&full[s], 1);
+            bar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            bar_init(&accf[a], 1);
+            bar_init(&acce[a], 4);
+        }
+        bar_init(&mma_done, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_slot;
+    volatile int* abort_v = &abort_flag;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int issued[kMmStages] = {0, 0, 0};
+            for (int item = blockIdx.x; item < g.items && !*abort_v; item += gridDim.x) {
+                const int tile = item / g.chunks, ch = item % g.chunks;
+                const int type = g.tiles[tile].x;
+                for (int ks = 0; ks < g.nk; ++ks) {
+                    if (!bar_wait(&empty[stage], phase ^ 1)) {
+                        atomicExch(g.err, 9);
+                        *abort_v = 1;
+                        break;
+                    }
+                    unsigned char* st = smem + stage * kMmStageBytes;
+                    bar_expect(&full[stage], kMmStageBytes);
+                    const int j0 = ks * kTcKc;
+                    tma3d(st, &mAh, j0, 0, tile, &full[stage]);
+                    tma3d(st + kTcABytes, &mAl, j0, 0, tile, &full[stage]);
+                    tma3d(st + 2 * kTcABytes, &mBh, j0, kTcN * ch, type, &full[stage]);
+                    tma3d(st + 2 * kTcABytes + kTcBBytes, &mBl, j0, kTcN * ch, type, &full[stage]);
+                    ++issued[stage];
+                    if (++stage == kMmStages) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
+                }
+            }
+            for (int s = 0; s < kMmStages; ++s) {
+                // the n-th use of a stage completes phase n-1 of its full barrier
+                if (issued[s] && !bar_wait(&full[s], (uint32_t)((issued[s] - 1) & 1))) atomicExch(g.err, 9);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int stage = 0, acc = 0;
+            uint32_t phase = 0, aphase = 0;
+            bool any = false;
+            for (int item = blockIdx.x; item < g.items && !*abort_v; item += gridDim.x) {
+                if (!bar_wait(&acce[acc], aphase ^ 1)) {
+                    atomicExch(g.err, 10);
+                    *abort_v = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t d = tmem + (uint32_t)(acc * 128);
+                bool ok = true;
+                for (int ks = 0; ks < g.nk; ++ks) {
+                    if (!bar_wait(&full[stage], phase)) {
+                        atomicExch(g.err, 11);
+                        *abort_v = 1;
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const uint32_t st = saddr(smem + stage * kMmStageBytes);
+                    const uint32_t ah = st, al = st + kTcABytes, bh = st + 2 * kTcABytes, bl = bh + kTcBBytes;
+                    for (int kk = 0; kk < kTcKc / 16; ++kk) {
+                        const uint32_t off = 32u * kk;
+                        mma_bf16(d, sdesc(ah + off), sdesc(bh + off), (ks > 0 || kk > 0) ? 1u : 0u);
+                        mma_bf16(d, sdesc(ah + off), sdesc(bl + off), 1u);
+                        mma_bf16(d, sdesc(al + off), sdesc(bh + off), 1u);
+                    }
+                    mma_commit(&empty[stage]);
+                    any = true;
+                    if (++stage == kMmStages) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
+                }
+                if (!ok) break;
+                mma_commit(&accf[acc]);
+                if (++acc == 2) {
+                    acc = 0;
+                    aphase ^= 1;
+                }
+            }
+            if (any) {
+                mma_commit(&mma_done);
+                if (!bar_wait(&mma_done, 0)) atomicExch(g.err, 12);
+            }
+        }
+    } else {
+        const int qd = warp & 3;
+        const int rho = 32 * qd + lane, c = rho >> 1, q = rho & 1;
+        int acc = 0;
+        uint32_t aphase = 0;
+        for (int item = blockIdx.x; item < g.items && !*abort_v; item += gridDim.x) {
+            const int tile = item / g.chunks, ch = item % g.chunks;
+            const int2 tl = g.tiles[tile];
+            if (!bar_wait(&accf[acc], aphase)) {
+                if (lane == 0) atomicExch(g.err, 13);
+                *abort_v = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const int col = tl.y + c;
+            const int n_t = g.type_ptr[tl.x + 1] - g.type_ptr[tl.x];
+            const bool valid = col < n_t * g.R;
+            float2* Yc = g.Y;
+            if (valid) {
+                const int slot = col / g.R, r = col % g.R;
+                const int cell = g.type_cells[g.type_ptr[tl.x] + slot];
+                Yc = g.Y + ((size_t)r * g.M + cell) * g.K;
+            }
+            const uint32_t t0 = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(acc * 128);
+            for (int c0 = 0; c0 < kTcN; c0 += 32) {
+                uint32_t a[32];
+                tmem_ld32(t0 + c0, a);
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+                for (int t = 0; t < 16; ++t) {
+                    const float pR = __shfl_xor_sync(0xffffffffu, __uint_as_float(a[2 * t]), 1);
+                    const float pI = __shfl_xor_sync(0xffffffffu, __uint_as_float(a[2 * t + 1]), 1);
+                    const int k = ch * (kTcN / 2) + c0 / 2 + t;
+                    if (valid && q == 0 && k < g.K) {
+                        // own row = Re x (2c), partner = Im x (2c+1)
+                        float2 y;
+                        y.x = __uint_as_float(a[2 * t]) - pI;
+                        y.y = pR + __uint_as_float(a[2 * t + 1]);
+                        Yc[k] = y;
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) bar_arrive(&acce[acc]);
+            if (++acc == 2) {
+                acc = 0;
+                aphase ^= 1;
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kMmTmemCols));
+}
+
+// x1 planes of the macromodel tiles: out[tile][2c+q][k'] = hi/lo of
+// (q ? Im : Re)(sign * x[r][U_o index]) for column c = (cell slot, rhs) of
+// the tile's type; zero past the type's columns and for k' >= K.
+__global__ void tc_mm_gather_kernel(const double2* __restrict__ x, const float2* __restrict__ xf,
+                                    const int32_t* __restrict__ idx, const int8_t* __restrict__ sgn,
+                                    const int2* __restrict__ tiles, const int32_t* __restrict__ type_ptr,
+                                    const int32_t* __restrict__ type_cells, __nv_bfloat16* __restrict__ hi,
+                                    __nv_bfloat16* __restrict__ lo, int K, int kp, int R, int n_unique,
+                                    size_t total) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int kk = (int)(e % kp);
+        const size_t tr = e / kp;
+        const int rho = (int)(tr % kTcM);
+        const int tile = (int)(tr / kTcM);
+        const int2 tl = tiles[tile];
+        const int col = tl.y + (rho >> 1), q = rho & 1;
+        const int n_t = type_ptr[tl.x + 1] - type_ptr[tl.x];
+        float v = 0.f;
+        if (col < n_t * R && kk < K) {
+            const int slot = col / R, r = col % R;
+            const int cell = type_cells[type_ptr[tl.x] + slot];
+            const size_t loc = (size_t)cell * K + kk;
+            const size_t at = (size_t)r * n_unique + idx[loc];
+            const float s = (float)sgn[loc];
+            if (xf) v = s * (q ? xf[at].y : xf[at].x);
+            else v = s * (float)(q ? x[at].y : x[at].x);
+        }
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        hi[e] = h;
+        lo[e] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -419,7 +648,79 @@ int tc_build(emsurf_handle* h) {
     EMS_TRY(encode3d(&m[3], h->tc_Bl, ej, 2 * E, 2 * nb, kTcKc, kTcN));
     h->tc_ej = ej;
     h->tc_rows = rows;
+    // macromodel planes: Z~ [t][2k+c][kp] and x1 tiles [tile][128][kp]
+    const int K = h->K, kp = (K + 7) & ~7;
+    const size_t zs = (size_t)h->T * 2 * K * kp;
+    EMS_TRY(dev_alloc(h, (void**)&h->tc_Zh, zs * sizeof(__nv_bfloat16)));
+    EMS_TRY(dev_alloc(h, (void**)&h->tc_Zl, zs * sizeof(__nv_bfloat16)));
+    EMS_CUDA(cudaMemsetAsync(h->tc_Zh, 0, zs * sizeof(__nv_bfloat16), h->setup_stream));
+    EMS_CUDA(cudaMemsetAsync(h->tc_Zl, 0, zs * sizeof(__nv_bfloat16), h->setup_stream));
+    const dim3 zgrid((K + 31) / 32, (K + 31) / 32, (unsigned)h->T);
+    tc_split_spectrum_kernel<<<zgrid, dim3(32, 8), 0, h->setup_stream>>>(
+        h->op32.Zt, reinterpret_cast<__nv_bfloat16*>(h->tc_Zh), reinterpret_cast<__nv_bfloat16*>(h->tc_Zl), K, kp);
+    EMS_CUDA(cudaGetLastError());
+    h->launches += 1;
+    int maxtiles = 0;
+    for (int t = 0; t < h->T; ++t)
+        maxtiles += ((h->h_type_ptr[t + 1] - h->h_type_ptr[t]) * h->max_rhs + 63) / 64;
+    maxtiles = std::max(maxtiles, 1);
+    const size_t ms = (size_t)maxtiles * kTcM * kp;
+    EMS_TRY(dev_alloc(h, (void**)&h->tc_Mh, ms * sizeof(__nv_bfloat16)));
+    EMS_TRY(dev_alloc(h, (void**)&h->tc_Ml, ms * sizeof(__nv_bfloat16)));
+    EMS_TRY(encode3d(&m[4], h->tc_Mh, kp, kTcM, maxtiles, kTcKc, kTcM));
+    EMS_TRY(encode3d(&m[5], h->tc_Ml, kp, kTcM, maxtiles, kTcKc, kTcM));
+    EMS_TRY(encode3d(&m[6], h->tc_Zh, kp, 2 * K, h->T, kTcKc, kTcN));
+    EMS_TRY(encode3d(&m[7], h->tc_Zl, kp, 2 * K, h->T, kTcKc, kTcN));
+    h->tc_kp = kp;
+    h->tc_mm_tiles.assign(h->max_rhs + 1, nullptr);
+    h->tc_mm_ntiles.assign(h->max_rhs + 1, 0);
     h->have_tc = true;
+    return EMSURF_OK;
+}
+
+// Macromodel products of R rhs on the tensor cores into Ymm[0] ([R][M][K]).
+int tc_macromodel(emsurf_handle* h, const double2* x, const float2* xf, float2* Ymm, int R, cudaStream_t st) {
+    const int K = h->K, kp = h->tc_kp;
+    if (!h->tc_mm_tiles[R]) {
+        // tiles of 64 columns (cell slot, rhs) per type, for this rhs count
+        std::vector<int2> tl;
+        for (int t = 0; t < h->T; ++t) {
+            const int ncol = (h->h_type_ptr[t + 1] - h->h_type_ptr[t]) * R;
+            for (int c0 = 0; c0 < ncol; c0 += 64) tl.push_back(make_int2(t, c0));
+        }
+        if (tl.empty()) tl.push_back(make_int2(0, 1 << 30));
+        int2* d = nullptr;
+        EMS_TRY(dev_alloc(h, (void**)&d, tl.size() * sizeof(int2)));
+        EMS_CUDA(cudaMemcpy(d, tl.data(), tl.size() * sizeof(int2), cudaMemcpyHostToDevice));
+        h->tc_mm_tiles[R] = d;
+        h->tc_mm_ntiles[R] = (int)tl.size();
+    }
+    const int ntiles = h->tc_mm_ntiles[R];
+    const int2* tiles = static_cast<const int2*>(h->tc_mm_tiles[R]);
+    const size_t total = (size_t)ntiles * kTcM * kp;
+    tc_mm_gather_kernel<<<(int)std::min<size_t>((total + 255) / 256, (size_t)h->num_sms * 16), 256, 0, st>>>(
+        x, xf, h->d_uo_index, h->d_uo_sign, tiles, h->d_type_ptr, h->d_type_cells,
+        reinterpret_cast<__nv_bfloat16*>(h->tc_Mh), reinterpret_cast<__nv_bfloat16*>(h->tc_Ml), K, kp, R,
+        h->n_unique, total);
+    EMS_CUDA(cudaGetLastError());
+    MmArgs a;
+    a.Y = Ymm;
+    a.tiles = tiles;
+    a.type_ptr = h->d_type_ptr;
+    a.type_cells = h->d_type_cells;
+    a.K = K;
+    a.M = h->M;
+    a.R = R;
+    a.ntiles = ntiles;
+    a.chunks = (2 * K + kTcN - 1) / kTcN;
+    a.nk = (kp + kTcKc - 1) / kTcKc;
+    a.items = ntiles * a.chunks;
+    a.err = h->d_err;
+    EMS_TRY(set_smem_once(mm_tc_kernel, (size_t)kMmSmem));
+    const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(h->tc_maps);
+    mm_tc_kernel<<<std::min(a.items, h->num_sms), kTcThreads, kMmSmem, st>>>(m[4], m[5], m[6], m[7], a);
+    EMS_CUDA(cudaGetLastError());
+    h->launches += 2;
     return EMSURF_OK;
 }
 

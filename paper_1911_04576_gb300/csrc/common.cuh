@@ -173,8 +173,15 @@ struct emsurf_handle {
     void* tc_Bl = nullptr;
     void* tc_Xh = nullptr;          // X^ planes hi/lo [bin][rows][ej] bf16
     void* tc_Xl = nullptr;
-    int tc_ej = 0, tc_rows = 0;
-    alignas(64) unsigned char tc_maps[4][128];   // tensor maps (X hi, X lo, B hi, B lo)
+    int tc_ej = 0, tc_rows = 0, tc_kp = 0;
+    void* tc_Zh = nullptr;          // macromodel planes hi/lo [t][2k+c][kp] bf16
+    void* tc_Zl = nullptr;
+    void* tc_Mh = nullptr;          // x1 tiles of the macromodel product hi/lo [tile][128][kp]
+    void* tc_Ml = nullptr;
+    std::vector<void*> tc_mm_tiles;   // per rhs count: device (type, first column) tile list
+    std::vector<int> tc_mm_ntiles;
+    // tensor maps: X hi, X lo, B hi, B lo (bin multiply); x1 hi, x1 lo, Z hi, Z lo (macromodels)
+    alignas(64) unsigned char tc_maps[8][128];
     int mm_occ[4] = {0, 0, 0, 0};          // resident macromodel CTAs per SM (FP32, FP64; x 1 / 4 rhs)
     int mm_threads[4] = {0, 0, 0, 0};      // macromodel block size per variant
     cudaStream_t setup_stream = nullptr;   // stream of the create-time work
@@ -237,6 +244,7 @@ int wait_selftest(emsurf_handle* h, long long limit, cudaStream_t st);
 constexpr int kTcMinRhs = 8;
 int tc_build(emsurf_handle* h);
 int tc_binmul(emsurf_handle* h, const float2* X, float2* Y, int R, const float2* coef, cudaStream_t st);
+int tc_macromodel(emsurf_handle* h, const double2* x, const float2* xf, float2* Ymm, int R, cudaStream_t st);
 int pc_apply(emsurf_handle* h, const double2* r, double2* y, int R, cudaStream_t st);
 int pc_apply_f32(emsurf_handle* h, const float2* r, float2* y, int R, cudaStream_t st);
 int gmres_solve(emsurf_handle* h, const double2* b, double2* x, int nrhs,

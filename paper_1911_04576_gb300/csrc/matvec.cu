@@ -534,6 +534,13 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
     // K splits of the macromodel product: as many as fill one wave of
     // resident CTAs (a partial second wave would double its time), at most
     // kMmSplit and at least 32 columns each
+    bool mm_done = false;
+    if constexpr (std::is_same<T2, float2>::value) {
+        if (h->have_tc && R >= kTcMinRhs) {
+            EMS_TRY(tc_macromodel(h, x, xf, op.Ymm, R, st));
+            mm_done = true;
+        }
+    }
     const bool blk4 = R >= 4;      // 4 rhs share each load of Z
     const int variant = (std::is_same<T2, float2>::value ? 0 : 1) + (blk4 ? 2 : 0);
     int& mthreads = h->mm_threads[variant];
@@ -561,7 +568,8 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
         const int slots = h->num_sms * occ;
         nsplit = std::max(1, std::min(nsplit, slots / std::max(1, h->n_mm_blocks)));
     }
-    {
+    if (mm_done) nsplit = 1;   // the tensor-core product wrote Ymm[0] whole
+    if (!mm_done) {
         const int nblk = h->n_mm_blocks;
         const int chunk = (K + nsplit - 1) / nsplit;
         const MmBlock* blocks = reinterpret_cast<const MmBlock*>(h->d_mm_blocks);
