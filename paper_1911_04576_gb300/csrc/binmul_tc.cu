@@ -30,6 +30,8 @@
 
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
+#include <vector>
 
 #include "common.cuh"
 
@@ -588,6 +590,242 @@ __global__ void tc_mm_gather_kernel(const double2* __restrict__ x, const float2*
     }
 }
 
+// ---------------------------------------------------------------- preconditioner
+// The restricted additive Schwarz apply with many rhs is a complex GEMM per
+// cell: y[own rows] = X_m (own_m x n_m) r[S_m] (n_m x R).  Same BF16x3
+// scheme as the macromodels: "A" = the gathered r planes of cell m (rows
+// 2c + q for rhs c < 64, over the subdomain index j), "B" = the planes of
+// the owned inverse rows (one flat list over all cells, rows 2g + c for
+// owned row g).  Items = (cell, 48 owned rows); the K loop covers n_m.
+struct PcArgs {
+    void* y;                       // [R][n_unique], float2 or double2
+    int y_f32;
+    const int2* items;             // (cell, first owned row)
+    const int32_t* own_ptr;        // [M+1]
+    const int32_t* nsz;            // [M]
+    const int32_t* sub_ptr;
+    const int32_t* sub_ids;
+    int R, n_unique, nitems;
+    int* err;
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+pc_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
+             const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, PcArgs g) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full[kMmStages], empty[kMmStages], accf[2], acce[2], mma_done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_slot)),
+                     "r"(kMmTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kMmStages; ++s) {
+            bar_init(&full[s], 1);
+            bar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            bar_init(&accf[a], 1);
+            bar_init(&acce[a], 4);
+        }
+        bar_init(&mma_done, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_slot;
+    volatile int* abort_v = &abort_flag;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int issued[kMmStages] = {0, 0, 0};
+            for (int item = blockIdx.x; item < g.nitems && !*abort_v; item += gridDim.x) {
+                const int2 it = g.items[item];
+                const int nk = (g.nsz[it.x] + kTcKc - 1) / kTcKc;
+                const int brow = 2 * (g.own_ptr[it.x] + it.y);
+                for (int ks = 0; ks < nk; ++ks) {
+                    if (!bar_wait(&empty[stage], phase ^ 1)) {
+                        atomicExch(g.err, 14);
+                        *abort_v = 1;
+                        break;
+                    }
+                    unsigned char* st = smem + stage * kMmStageBytes;
+                    bar_expect(&full[stage], kMmStageBytes);
+                    const int j0 = ks * kTcKc;
+                    tma3d(st, &mAh, j0, 0, it.x, &full[stage]);
+                    tma3d(st + kTcABytes, &mAl, j0, 0, it.x, &full[stage]);
+                    tma3d(st + 2 * kTcABytes, &mBh, j0, brow, 0, &full[stage]);
+                    tma3d(st + 2 * kTcABytes + kTcBBytes, &mBl, j0, brow, 0, &full[stage]);
+                    ++issued[stage];
+                    if (++stage == kMmStages) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
+                }
+            }
+            for (int s = 0; s < kMmStages; ++s)
+                if (issued[s] && !bar_wait(&full[s], (uint32_t)((issued[s] - 1) & 1))) atomicExch(g.err, 14);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int stage = 0, acc = 0;
+            uint32_t phase = 0, aphase = 0;
+            bool any = false;
+            for (int item = blockIdx.x; item < g.nitems && !*abort_v; item += gridDim.x) {
+                const int nk = (g.nsz[g.items[item].x] + kTcKc - 1) / kTcKc;
+                if (!bar_wait(&acce[acc], aphase ^ 1)) {
+                    atomicExch(g.err, 15);
+                    *abort_v = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t d = tmem + (uint32_t)(acc * 128);
+                bool ok = true;
+                for (int ks = 0; ks < nk; ++ks) {
+                    if (!bar_wait(&full[stage], phase)) {
+                        atomicExch(g.err, 16);
+                        *abort_v = 1;
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const uint32_t st = saddr(smem + stage * kMmStageBytes);
+                    const uint32_t ah = st, al = st + kTcABytes, bh = st + 2 * kTcABytes, bl = bh + kTcBBytes;
+                    for (int kk = 0; kk < kTcKc / 16; ++kk) {
+                        const uint32_t off = 32u * kk;
+                        mma_bf16(d, sdesc(ah + off), sdesc(bh + off), (ks > 0 || kk > 0) ? 1u : 0u);
+                        mma_bf16(d, sdesc(ah + off), sdesc(bl + off), 1u);
+                        mma_bf16(d, sdesc(al + off), sdesc(bh + off), 1u);
+                    }
+                    mma_commit(&empty[stage]);
+                    any = true;
+                    if (++stage == kMmStages) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
+                }
+                if (!ok) break;
+                mma_commit(&accf[acc]);
+                if (++acc == 2) {
+                    acc = 0;
+                    aphase ^= 1;
+                }
+            }
+            if (any) {
+                mma_commit(&mma_done);
+                if (!bar_wait(&mma_done, 0)) atomicExch(g.err, 17);
+            }
+        }
+    } else {
+        const int qd = warp & 3;
+        const int rho = 32 * qd + lane, c = rho >> 1, q = rho & 1;
+        int acc = 0;
+        uint32_t aphase = 0;
+        for (int item = blockIdx.x; item < g.nitems && !*abort_v; item += gridDim.x) {
+            const int2 it = g.items[item];
+            if (!bar_wait(&accf[acc], aphase)) {
+                if (lane == 0) atomicExch(g.err, 18);
+                *abort_v = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const int own = g.own_ptr[it.x + 1] - g.own_ptr[it.x];
+            const int32_t* sub = g.sub_ids + g.sub_ptr[it.x];
+            const uint32_t t0 = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(acc * 128);
+            for (int c0 = 0; c0 < kTcN; c0 += 32) {
+                uint32_t a[32];
+                tmem_ld32(t0 + c0, a);
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+                for (int t = 0; t < 16; ++t) {
+                    const float pR = __shfl_xor_sync(0xffffffffu, __uint_as_float(a[2 * t]), 1);
+                    const float pI = __shfl_xor_sync(0xffffffffu, __uint_as_float(a[2 * t + 1]), 1);
+                    const int i = it.y + c0 / 2 + t;
+                    if (q == 0 && c < g.R && i < own) {
+                        const float yr = __uint_as_float(a[2 * t]) - pI;
+                        const float yi = pR + __uint_as_float(a[2 * t + 1]);
+                        const size_t at = (size_t)c * g.n_unique + sub[i];
+                        if (g.y_f32) static_cast<float2*>(g.y)[at] = make_float2(yr, yi);
+                        else static_cast<double2*>(g.y)[at] = make_double2((double)yr, (double)yi);
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) bar_arrive(&acce[acc]);
+            if (++acc == 2) {
+                acc = 0;
+                aphase ^= 1;
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kMmTmemCols));
+}
+
+// planes of the owned inverse rows: out[2g + c][j] = hi/lo of (c ? Im : Re)
+// X_m[i][j] for owned row g = own_ptr[m] + i, zero for j >= n_m
+__global__ void pc_tc_split_rows_kernel(const float2* __restrict__ X, const int64_t* __restrict__ xoff,
+                                        const int32_t* __restrict__ ldx, const int32_t* __restrict__ nsz,
+                                        const int32_t* __restrict__ own_ptr, int M, int np,
+                                        __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
+                                        size_t total) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e % np);
+        const size_t rc = e / np;
+        const int c = (int)(rc & 1);
+        const int gr = (int)(rc >> 1);
+        int lo_ = 0, hi_ = M;
+        while (hi_ - lo_ > 1) {
+            const int mid = (lo_ + hi_) >> 1;
+            if (own_ptr[mid] <= gr) lo_ = mid; else hi_ = mid;
+        }
+        const int m = lo_, i = gr - own_ptr[m];
+        float v = 0.f;
+        if (j < nsz[m]) {
+            const float2 x = X[xoff[m] + (size_t)i * ldx[m] + j];
+            v = c ? x.y : x.x;
+        }
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        hi[e] = h;
+        lo[e] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+}
+
+// gathered r planes per cell: out[m][2c+q][j] = hi/lo of (q ? Im : Re)
+// r[c][sub_m[j]] for rhs c < R and j < n_m, zero otherwise
+template <typename VT>
+__global__ void pc_tc_gather_kernel(const VT* __restrict__ r, const int32_t* __restrict__ sub_ptr,
+                                    const int32_t* __restrict__ sub_ids, const int32_t* __restrict__ nsz,
+                                    int R, int n_unique, int np, __nv_bfloat16* __restrict__ hi,
+                                    __nv_bfloat16* __restrict__ lo, size_t total) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e % np);
+        const size_t mr = e / np;
+        const int rho = (int)(mr % kTcM);
+        const int m = (int)(mr / kTcM);
+        const int cc = rho >> 1, q = rho & 1;
+        float v = 0.f;
+        if (cc < R && j < nsz[m]) {
+            const VT x = r[(size_t)cc * n_unique + sub_ids[sub_ptr[m] + j]];
+            v = (float)(q ? x.y : x.x);
+        }
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        hi[e] = h;
+        lo[e] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -754,5 +992,75 @@ int tc_binmul(emsurf_handle* h, const float2* X, float2* Y, int R, const float2*
     h->launches += 2;
     return EMSURF_OK;
 }
+
+}  // namespace emsurf
+
+namespace emsurf {
+
+// Create-time: planes of the owned inverse rows, gather buffer, items, maps.
+int pc_tc_build(emsurf_handle* h, const std::vector<int32_t>& optr) {
+    const int np = (h->pc_nmax + 7) & ~7;
+    const size_t rows = (size_t)2 * h->n_unique;
+    EMS_TRY(dev_alloc(h, (void**)&h->pc_tc_Xh, rows * np * sizeof(__nv_bfloat16)));
+    EMS_TRY(dev_alloc(h, (void**)&h->pc_tc_Xl, rows * np * sizeof(__nv_bfloat16)));
+    const size_t total = rows * np;
+    pc_tc_split_rows_kernel<<<(int)std::min<size_t>((total + 255) / 256, (size_t)h->num_sms * 16), 256, 0,
+                              h->setup_stream>>>(h->pc_mat, h->pc_off, h->pc_ld, h->pc_n, h->pc_own_ptr, h->M, np,
+                                                 reinterpret_cast<__nv_bfloat16*>(h->pc_tc_Xh),
+                                                 reinterpret_cast<__nv_bfloat16*>(h->pc_tc_Xl), total);
+    EMS_CUDA(cudaGetLastError());
+    h->launches += 1;
+    const size_t gs = (size_t)h->M * kTcM * np;
+    EMS_TRY(dev_alloc(h, (void**)&h->pc_tc_Rh, gs * sizeof(__nv_bfloat16)));
+    EMS_TRY(dev_alloc(h, (void**)&h->pc_tc_Rl, gs * sizeof(__nv_bfloat16)));
+    std::vector<int2> items;
+    for (int m = 0; m < h->M; ++m)
+        for (int i0 = 0; i0 < optr[m + 1] - optr[m]; i0 += kTcN / 2) items.push_back(make_int2(m, i0));
+    if (items.empty()) items.push_back(make_int2(0, 1 << 30));
+    int2* d = nullptr;
+    EMS_TRY(dev_alloc(h, (void**)&d, items.size() * sizeof(int2)));
+    EMS_CUDA(cudaMemcpy(d, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    h->pc_tc_items = d;
+    h->pc_tc_nitems = (int)items.size();
+    h->pc_tc_np = np;
+    CUtensorMap* m = reinterpret_cast<CUtensorMap*>(h->pc_tc_maps);
+    EMS_TRY(encode3d(&m[0], h->pc_tc_Rh, np, kTcM, h->M, kTcKc, kTcM));
+    EMS_TRY(encode3d(&m[1], h->pc_tc_Rl, np, kTcM, h->M, kTcKc, kTcM));
+    EMS_TRY(encode3d(&m[2], h->pc_tc_Xh, np, rows, 1, kTcKc, kTcN));
+    EMS_TRY(encode3d(&m[3], h->pc_tc_Xl, np, rows, 1, kTcKc, kTcN));
+    h->have_pc_tc = true;
+    return EMSURF_OK;
+}
+
+template <typename VT>
+int pc_tc_apply(emsurf_handle* h, const VT* r, VT* y, int R, cudaStream_t st) {
+    const int np = h->pc_tc_np;
+    const size_t gs = (size_t)h->M * kTcM * np;
+    pc_tc_gather_kernel<VT><<<(int)std::min<size_t>((gs + 255) / 256, (size_t)h->num_sms * 16), 256, 0, st>>>(
+        r, h->pc_sub_ptr, h->pc_sub_ids, h->pc_n, R, h->n_unique, np,
+        reinterpret_cast<__nv_bfloat16*>(h->pc_tc_Rh), reinterpret_cast<__nv_bfloat16*>(h->pc_tc_Rl), gs);
+    EMS_CUDA(cudaGetLastError());
+    PcArgs a;
+    a.y = y;
+    a.y_f32 = std::is_same<VT, float2>::value ? 1 : 0;
+    a.items = static_cast<const int2*>(h->pc_tc_items);
+    a.own_ptr = h->pc_own_ptr;
+    a.nsz = h->pc_n;
+    a.sub_ptr = h->pc_sub_ptr;
+    a.sub_ids = h->pc_sub_ids;
+    a.R = R;
+    a.n_unique = h->n_unique;
+    a.nitems = h->pc_tc_nitems;
+    a.err = h->d_err;
+    EMS_TRY(set_smem_once(pc_tc_kernel, (size_t)kMmSmem));
+    const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(h->pc_tc_maps);
+    pc_tc_kernel<<<std::min(a.nitems, h->num_sms), kTcThreads, kMmSmem, st>>>(m[0], m[1], m[2], m[3], a);
+    EMS_CUDA(cudaGetLastError());
+    h->launches += 2;
+    return EMSURF_OK;
+}
+
+template int pc_tc_apply<double2>(emsurf_handle*, const double2*, double2*, int, cudaStream_t);
+template int pc_tc_apply<float2>(emsurf_handle*, const float2*, float2*, int, cudaStream_t);
 
 }  // namespace emsurf

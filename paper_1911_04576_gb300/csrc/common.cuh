@@ -199,6 +199,15 @@ struct emsurf_handle {
     int64_t* pc_rs_off = nullptr;   // [M] start of each cell's segment in pc_rs
     float2* pc_rs = nullptr;        // [max_rhs][pc_rs_stride] gathered r (FP32)
     int64_t pc_rs_stride = 0;
+    // tensor-core apply (>= kTcMinRhs rhs): bf16 planes of the owned rows and of r per cell
+    bool have_pc_tc = false;
+    void* pc_tc_Xh = nullptr;       // [2 n_unique][np]
+    void* pc_tc_Xl = nullptr;
+    void* pc_tc_Rh = nullptr;       // [M][128][np]
+    void* pc_tc_Rl = nullptr;
+    void* pc_tc_items = nullptr;    // (cell, first owned row) per item
+    int pc_tc_nitems = 0, pc_tc_np = 0;
+    alignas(64) unsigned char pc_tc_maps[4][128];
     int32_t* pc_n = nullptr;        // [M] subdomain sizes
     int32_t* pc_own = nullptr;      // [M] owned unknowns (first in each subdomain)
     int32_t* pc_sub_ptr = nullptr;  // [M+1]
@@ -245,6 +254,9 @@ constexpr int kTcMinRhs = 8;
 int tc_build(emsurf_handle* h);
 int tc_binmul(emsurf_handle* h, const float2* X, float2* Y, int R, const float2* coef, cudaStream_t st);
 int tc_macromodel(emsurf_handle* h, const double2* x, const float2* xf, float2* Ymm, int R, cudaStream_t st);
+int pc_tc_build(emsurf_handle* h, const std::vector<int32_t>& own_ptr);
+template <typename VT>
+int pc_tc_apply(emsurf_handle* h, const VT* r, VT* y, int R, cudaStream_t st);
 int pc_apply(emsurf_handle* h, const double2* r, double2* y, int R, cudaStream_t st);
 int pc_apply_f32(emsurf_handle* h, const float2* r, float2* y, int R, cudaStream_t st);
 int gmres_solve(emsurf_handle* h, const double2* b, double2* x, int nrhs,

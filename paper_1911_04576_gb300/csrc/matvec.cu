@@ -568,6 +568,13 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
         const int slots = h->num_sms * occ;
         nsplit = std::max(1, std::min(nsplit, slots / std::max(1, h->n_mm_blocks)));
     }
+    {
+        // the staged x1 block (rhs block x kMmGroup cells x chunk) must fit in shared memory
+        const size_t per_col = (size_t)(blk4 ? 4 : 1) * kMmGroup * sizeof(T2);
+        const int max_chunk = (int)((200u * 1024u) / per_col);
+        nsplit = std::max(nsplit, (K + max_chunk - 1) / max_chunk);
+        nsplit = std::min(nsplit, kMmSplit);
+    }
     if (mm_done) nsplit = 1;   // the tensor-core product wrote Ymm[0] whole
     if (!mm_done) {
         const int nblk = h->n_mm_blocks;

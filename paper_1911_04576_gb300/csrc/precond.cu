@@ -292,19 +292,23 @@ __global__ void pc_gather_kernel(const VT* __restrict__ r, const int32_t* __rest
 
 // y[sub[i]] = sum_c X_m[i][c] rs_m[c] for the owned rows i of every cell
 // (the restricted additive Schwarz sum: each unknown is owned once).  The
-// owned rows of all cells form one list; each warp takes whole rows (16-byte
-// loads of X, eight in flight per lane; the cell's rs segment is reused by
-// all its rows from L1/L2) and reduces once per row and right-hand side.
+// owned rows of all cells form one list; each warp takes whole rows
+// (16-byte loads of X, eight in flight per lane; the cell's rs segment is
+// reused from L1/L2) and reduces once per row and right-hand side.  Used for
+// fewer rhs than the tensor-core path takes.
 // The grid is exactly the resident capacity, so the row list is shared out
 // in one wave.
 template <int RQ, typename VO>
-__global__ void __launch_bounds__(kApThreads, 4)
+__global__ void __launch_bounds__(kApThreads, RQ >= 2 ? 2 : 4)
 pc_apply_kernel(const float2* __restrict__ X, const int64_t* __restrict__ xoff,
                 const int32_t* __restrict__ ldx, const int32_t* __restrict__ own_ptr,
                 const int32_t* __restrict__ sub_ptr, const int32_t* __restrict__ sub_ids,
                 const int64_t* __restrict__ rs_off, const float2* __restrict__ rs, int64_t rs_stride,
-                VO* __restrict__ y, int n_rows, int M, int n_unique, int r0) {
+                VO* __restrict__ y, int n_rows, int M, int n_unique, int r0, int nr) {
     const int lane = threadIdx.x & 31;
+    // warps take rows in a grid stride: at any time the warps of the whole
+    // grid work on one window of consecutive rows (a few cells), whose
+    // gathered r segments stay in L1/L2
     const int warps = gridDim.x * (blockDim.x >> 5);
     for (int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < n_rows; g += warps) {
         // cell of owned row g: own_ptr[m] <= g < own_ptr[m+1]
@@ -313,7 +317,8 @@ pc_apply_kernel(const float2* __restrict__ X, const int64_t* __restrict__ xoff,
             const int mid = (lo + hi) >> 1;
             if (own_ptr[mid] <= g) lo = mid; else hi = mid;
         }
-        const int m = lo, i = g - own_ptr[m], ld = ldx[m], half = ld >> 1;
+        const int m = lo;
+        const int i = g - own_ptr[m], ld = ldx[m], half = ld >> 1;
         const float4* row = reinterpret_cast<const float4*>(X + xoff[m] + (size_t)i * ld);
         const float4* rv4 = reinterpret_cast<const float4*>(rs + rs_off[m]);
         float2 acc[RQ];
@@ -329,6 +334,7 @@ pc_apply_kernel(const float2* __restrict__ X, const int64_t* __restrict__ xoff,
                 const int c2 = min(c0 + 32 * u, half - 1);
 #pragma unroll
                 for (int q = 0; q < RQ; ++q) {
+                    if (q >= nr) break;   // rhs past the live count: no reads (uniform branch)
                     const float4 rv = __ldg(rv4 + q * (rs_stride >> 1) + c2);
                     acc[q].x += xv[u].x * rv.x - xv[u].y * rv.y + xv[u].z * rv.z - xv[u].w * rv.w;
                     acc[q].y += xv[u].x * rv.y + xv[u].y * rv.x + xv[u].z * rv.w + xv[u].w * rv.z;
@@ -345,6 +351,7 @@ pc_apply_kernel(const float2* __restrict__ X, const int64_t* __restrict__ xoff,
             const int u = sub_ids[sub_ptr[m] + i];
 #pragma unroll
             for (int q = 0; q < RQ; ++q) {
+                if (q >= nr) break;
                 VO o;
                 o.x = acc[q].x;
                 o.y = acc[q].y;
@@ -355,9 +362,9 @@ pc_apply_kernel(const float2* __restrict__ X, const int64_t* __restrict__ xoff,
 }
 
 template <int RQ, typename VO>
-int launch_apply(emsurf_handle* h, VO* y, int r0, cudaStream_t st) {
+int launch_apply(emsurf_handle* h, VO* y, int r0, int nr, cudaStream_t st) {
     // resident blocks per SM (the same for every device of this build)
-    static int occ[8][2] = {};
+    static int occ[9][2] = {};
     int& o = occ[RQ][sizeof(VO) == sizeof(float2) ? 1 : 0];
     if (!o) {
         int b = 0;
@@ -368,7 +375,7 @@ int launch_apply(emsurf_handle* h, VO* y, int r0, cudaStream_t st) {
     pc_apply_kernel<RQ, VO><<<blocks, kApThreads, 0, st>>>(h->pc_mat, h->pc_off, h->pc_ld, h->pc_own_ptr,
                                                         h->pc_sub_ptr, h->pc_sub_ids, h->pc_rs_off,
                                                         h->pc_rs + (size_t)r0 * h->pc_rs_stride,
-                                                        h->pc_rs_stride, y, h->n_unique, h->M, h->n_unique, r0);
+                                                        h->pc_rs_stride, y, h->n_unique, h->M, h->n_unique, r0, nr);
     EMS_CUDA(cudaGetLastError());
     h->launches += 1;
     return EMSURF_OK;
@@ -382,18 +389,19 @@ int pc_apply_t(emsurf_handle* h, const VT* r, VT* y, int R, cudaStream_t st) {
         set_error("preconditioner: %d right-hand sides, handle holds %d", R, h->max_rhs);
         return EMSURF_EINVAL;
     }
+    if (h->have_pc_tc && R >= kTcMinRhs) return pc_tc_apply<VT>(h, r, y, R, st);
     const int total = (int)h->pc_sub_total;
     pc_gather_kernel<VT><<<std::min((total + 255) / 256, h->num_sms * 8), 256, 0, st>>>(
         r, h->pc_sub_ids, h->pc_sub_cell, h->pc_sub_ptr, h->pc_rs_off, h->pc_rs, total, h->n_unique,
         h->pc_rs_stride, R);
     EMS_CUDA(cudaGetLastError());
     h->launches += 1;
-    for (int r0 = 0; r0 < R; r0 += 4) {
-        const int nr = std::min(4, R - r0);
-        if (nr == 1) EMS_TRY((launch_apply<1, VT>(h, y, r0, st)));
-        else if (nr == 2) EMS_TRY((launch_apply<2, VT>(h, y, r0, st)));
-        else if (nr == 3) EMS_TRY((launch_apply<3, VT>(h, y, r0, st)));
-        else EMS_TRY((launch_apply<4, VT>(h, y, r0, st)));
+    for (int r0 = 0; r0 < R; r0 += 8) {
+        const int nr = std::min(8, R - r0);
+        if (nr == 1) EMS_TRY((launch_apply<1, VT>(h, y, r0, nr, st)));
+        else if (nr == 2) EMS_TRY((launch_apply<2, VT>(h, y, r0, nr, st)));
+        else if (nr <= 4) EMS_TRY((launch_apply<4, VT>(h, y, r0, nr, st)));
+        else EMS_TRY((launch_apply<8, VT>(h, y, r0, nr, st)));
     }
     return EMSURF_OK;
 }
@@ -487,6 +495,7 @@ int pc_build(emsurf_handle* h, const emsurf_problem* p) {
     EMS_TRY(up(&h->pc_sub_ids, sids.data(), sids.size()));
     EMS_TRY(up(&h->pc_own, own.data(), own.size()));
     EMS_TRY(up(&h->pc_n, nsz.data(), nsz.size()));
+    std::vector<int32_t> own_ptr_host;
     EMS_TRY(up(&h->pc_off, xoff.data(), (size_t)M));
     EMS_TRY(up(&h->pc_ld, ldv.data(), (size_t)M));
     {
@@ -503,6 +512,7 @@ int pc_build(emsurf_handle* h, const emsurf_problem* p) {
             return EMSURF_EINVAL;
         }
         EMS_TRY(up(&h->pc_own_ptr, optr.data(), optr.size()));
+        own_ptr_host = optr;
         EMS_TRY(up(&h->pc_sub_cell, scell.data(), scell.size()));
         EMS_TRY(up(&h->pc_rs_off, rsoff.data(), (size_t)M));
         h->pc_rs_stride = rsoff[M];
@@ -590,6 +600,8 @@ int pc_build(emsurf_handle* h, const emsurf_problem* p) {
     h->pc_elems = xoff[M];
     h->pc_sub_total = (int64_t)sids.size();
     h->have_pc = true;
+    // many rhs: the apply as tensor-core GEMMs (with the handle's tensor-core option)
+    if (h->have_tc && h->max_rhs >= kTcMinRhs) EMS_TRY(pc_tc_build(h, own_ptr_host));
     return EMSURF_OK;
 }
 

@@ -156,7 +156,8 @@ def test_precond_invalid(emsurf_lib, phys):
     h.close()
 
 
-def test_precond_random_ragged_lattice(emsurf_lib):
+@pytest.mark.parametrize("R", [3, 11])
+def test_precond_random_ragged_lattice(emsurf_lib, R):
     """A 4 x 3 lattice of n = 2 boxes with synthetic tables and strongly
     diagonal macromodels: cells at the edge and corners have smaller
     subdomains than interior ones (ragged sizes)."""
@@ -175,15 +176,40 @@ def test_precond_random_ragged_lattice(emsurf_lib):
     delta = 0.6 * A / n
     subs = precond.subdomains(xy, owner, nx, ny, A, A, delta)
     assert len({len(S) for S, _ in subs}) >= 3
-    h = B.emsurf_create(nx, ny, E, nu, tmap, Z, Lt, Kt, coef, idx, sgn, precision=B.FP64, max_rhs=3,
+    h = B.emsurf_create(nx, ny, E, nu, tmap, Z, Lt, Kt, coef, idx, sgn, precision=B.FP64, max_rhs=R,
                         unknown_xy=xy, cell=(A, A), precond_overlap=delta)
-    r = W.random_vectors(3, nu, 19)
+    r = W.random_vectors(R, nu, 19)
     rd = torch.from_numpy(r).cuda()
     yd = torch.empty_like(rd)
     B.emsurf_precond_apply(h, rd, yd)
     y = yd.cpu().numpy()
     tol = _bound(Ad, subs)
-    for q in range(3):
+    for q in range(R):
         ref = precond.ras_apply(Ad, subs, r[q])
         assert np.linalg.norm(y[q] - ref) <= tol * np.linalg.norm(ref)
+    h.close()
+
+
+@pytest.mark.parametrize("R", [8, 13])
+def test_precond_apply_tensor_cores(emsurf_lib, phys, R):
+    """With >= 8 rhs and the tensor-core option the apply runs as BF16x3
+    GEMMs per cell: the FP32-LU bound plus the split's 3 * 2^-18 per term
+    times sqrt(n_max) (random-phase sums), against the oracle."""
+    import torch
+    from paper_1911_04576_gb300 import binding as B
+    w = phys["w"]
+    h = B.emsurf_create(w.nx, w.ny, w.E, phys["nu"], phys["tmap"], phys["Z"], phys["Lt"], phys["Kt"], COEF,
+                        phys["idx"], phys["sgn"], precision=B.MIXED, max_rhs=R, unknown_xy=phys["xy"],
+                        cell=(A, A), precond_overlap=phys["delta"], tensor_cores=True)
+    r = W.random_vectors(R, phys["nu"], 61)
+    rd = torch.from_numpy(r).cuda()
+    yd = torch.full_like(rd, float("nan"))
+    B.emsurf_precond_apply(h, rd, yd)
+    y = yd.cpu().numpy()
+    nmax = max(len(S) for S, _ in phys["subs"])
+    tol = _bound(phys["Ad"], phys["subs"]) + 3 * 2.0 ** -18 * np.sqrt(nmax)
+    for q in range(R):
+        ref = precond.ras_apply(phys["Ad"], phys["subs"], r[q])
+        assert np.all(np.isfinite(y[q]))
+        assert np.linalg.norm(y[q] - ref) <= tol * np.linalg.norm(ref), (q, tol)
     h.close()
