@@ -303,7 +303,11 @@ EMSURF_API int emsurf_tabulate_noalloc(const double* test_verts, const int32_t* 
 /* Offset tables of an nx x ny lattice of boxes (period a, b; height h; n x n
  * per face): L, K device [2ny-1][2nx-1][E][E] indexed [dy+ny-1][dx+nx-1],
  * d = test cell - source cell; closed-form singular parts for touching
- * boxes (|dx|, |dy| <= 1).  The layout emsurf_create takes.               */
+ * boxes (|dx|, |dy| <= 1).  The tables are the reciprocal part of the
+ * one-sided blocks of emsurf_tabulate, T(d) = (T1(d) + T1(-d)^T) / 2, so
+ * L(-d) = L(d)^T and K(-d) = K(d)^T hold exactly (the one-sided closed-form
+ * integration breaks them at touching offsets).  The layout emsurf_create
+ * takes; with reciprocal tables it stores half of the FP32 spectrum.      */
 EMSURF_API int emsurf_tabulate_offsets(double a, double b, double h, int32_t n, int32_t nx,
                                        int32_t ny, double k, emsurf_c128* L, emsurf_c128* K,
                                        void* stream);

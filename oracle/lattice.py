@@ -2,7 +2,14 @@
 
 * offset_tables: L(d), K(d) for every lattice offset d = test cell - source
   cell (Eqs. out, blockZo); blocks depend only on d because all boxes are
-  translates of one mesh and G is translation invariant (Sec. IV-A).
+  translates of one mesh and G is translation invariant (Sec. IV-A).  The
+  continuous operators are reciprocal (L(-d) = L(d)^T, K(-d) = K(d)^T by
+  the symmetry of G and of the Galerkin pairing); the closed-form singular
+  parts integrate the source triangle exactly and the test triangle by
+  quadrature, which breaks that symmetry at touching offsets.  The tables
+  are therefore the reciprocal part of the one-sided blocks,
+  L(d) = (L1(d) + L1(-d)^T) / 2 (same for K): the average of the two
+  one-sided quadratures, exactly reciprocal.
 * overlap_map: the sparse +-1 matrix U_o of Eq. connections_IUI, built
   geometrically: two RWG functions of different boxes are merged when their
   edges coincide and one of their triangles coincides (rule 1, "surface
@@ -40,14 +47,22 @@ def offset_tables(box, nx, ny, a, b, k, offsets=None):
     def one(dx, dy):
         sing = abs(dx) <= 1 and abs(dy) <= 1
         return galerkin_LK(box, cell_shift(dx, dy, a, b), box, (0.0, 0.0, 0.0), k, sing)
+
+    def sym(dx, dy):
+        Lp, Kp = one(dx, dy)
+        Lm, Km = one(-dx, -dy)
+        return 0.5 * (Lp + Lm.T), 0.5 * (Kp + Km.T)
     if offsets is not None:
-        return {d: one(*d) for d in offsets}
+        return {d: sym(*d) for d in offsets}
     E = box.n_rwg
-    Lt = np.zeros((2 * ny - 1, 2 * nx - 1, E, E), dtype=complex)
-    Kt = np.zeros_like(Lt)
+    L1 = np.zeros((2 * ny - 1, 2 * nx - 1, E, E), dtype=complex)
+    K1 = np.zeros_like(L1)
     for dy in range(-(ny - 1), ny):
         for dx in range(-(nx - 1), nx):
-            Lt[dy + ny - 1, dx + nx - 1], Kt[dy + ny - 1, dx + nx - 1] = one(dx, dy)
+            L1[dy + ny - 1, dx + nx - 1], K1[dy + ny - 1, dx + nx - 1] = one(dx, dy)
+    # entry -d of the flipped table, transposed
+    Lt = 0.5 * (L1 + np.swapaxes(L1[::-1, ::-1], 2, 3))
+    Kt = 0.5 * (K1 + np.swapaxes(K1[::-1, ::-1], 2, 3))
     return Lt, Kt
 
 
@@ -166,7 +181,8 @@ def matvec_direct(x, Lt, Kt, coef, macromodels, type_map, index, sign, n_unique,
 
 def assemble_dense(box, nx, ny, a, b, k, coef, macromodels, type_map, index, sign, n_unique):
     """Dense A = U_o^T [Z_eq + Z_o] U_o (Eq. final) with every box pair
-    (m, m') tabulated directly by quadrature."""
+    (m, m') tabulated directly by quadrature (reciprocal part of the
+    one-sided blocks, as in offset_tables)."""
     E = box.n_rwg
     Kl = 2 * E
     M = nx * ny
@@ -176,8 +192,11 @@ def assemble_dense(box, nx, ny, a, b, k, coef, macromodels, type_map, index, sig
         for ms in range(M):
             jx, jy = ms % nx, ms // nx
             sing = abs(ix - jx) <= 1 and abs(iy - jy) <= 1
-            L, K = galerkin_LK(box, cell_shift(ix, iy, a, b), box, cell_shift(jx, jy, a, b),
-                               k, sing)
+            Lp, Kp = galerkin_LK(box, cell_shift(ix, iy, a, b), box, cell_shift(jx, jy, a, b),
+                                 k, sing)
+            Lm, Km = galerkin_LK(box, cell_shift(jx, jy, a, b), box, cell_shift(ix, iy, a, b),
+                                 k, sing)
+            L, K = 0.5 * (Lp + Lm.T), 0.5 * (Kp + Km.T)
             Z[m * Kl:(m + 1) * Kl, ms * Kl:(ms + 1) * Kl] = coupling_block(L, K, coef)
         Z[m * Kl:(m + 1) * Kl, m * Kl:(m + 1) * Kl] += macromodels[type_map[m]]
     U = np.zeros((M * Kl, n_unique))

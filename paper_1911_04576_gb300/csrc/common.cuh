@@ -167,6 +167,11 @@ struct emsurf_handle {
     emsurf::Operator<float2> op32;
     bool have64 = false, have32 = false;
     int num_sms = 0;
+    // half FP32 spectrum (reciprocal tables, single rhs): stored bins and partners
+    bool half32 = false;
+    int nst = 0;
+    int32_t* d_st_bin = nullptr;
+    int32_t* d_st_part = nullptr;
     // BF16x3 split planes of the FP32 operator for the tensor-core bin multiply
     bool have_tc = false;
     void* tc_Bh = nullptr;          // spectrum hi/lo [bin][op][2i+c][ej] bf16

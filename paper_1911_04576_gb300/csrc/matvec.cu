@@ -79,6 +79,42 @@ __global__ void round_kernel(float2* __restrict__ dst, const double2* __restrict
     }
 }
 
+// Reciprocity of the spectrum: with L(-d) = L(d)^T and K(-d) = K(d)^T the
+// blocks of bins k and -k are transposes, B^(-k) = B^(k)^T.  out[0] = max
+// |B^(-k)[i][j] - B^(k)[j][i]|, out[1] = max |B^| (as ordered bit patterns
+// of non-negative doubles).
+__global__ void reciprocity_kernel(const double2* __restrict__ B, const int32_t* __restrict__ partner,
+                                   int E, size_t nbins, unsigned long long* __restrict__ out) {
+    const size_t EE = (size_t)E * E, total = nbins * 2 * EE;
+    double dmax = 0.0, vmax = 0.0;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t bin = e / (2 * EE), rem = e % (2 * EE);
+        const int op = (int)(rem / EE), j = (int)((rem % EE) / E), i = (int)(rem % E);
+        const double2 a = B[e];
+        const double2 b = B[((size_t)partner[bin] * 2 + op) * EE + (size_t)i * E + j];
+        dmax = fmax(dmax, fmax(fabs(a.x - b.x), fabs(a.y - b.y)));
+        vmax = fmax(vmax, fmax(fabs(a.x), fabs(a.y)));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&out[0], (unsigned long long)__double_as_longlong(dmax));
+        atomicMax(&out[1], (unsigned long long)__double_as_longlong(vmax));
+    }
+}
+
+// half spectrum: dst[s] = (float) B^(st_bin[s]) for the stored bins
+__global__ void half_round_kernel(float2* __restrict__ dst, const double2* __restrict__ src,
+                                  const int32_t* __restrict__ st_bin, size_t per_bin, size_t n) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t s = e / per_bin, r = e % per_bin;
+        const double2 v = src[(size_t)st_bin[s] * per_bin + r];
+        dst[e] = make_float2((float)v.x, (float)v.y);
+    }
+}
+
 // ------------------------------------------------ K2: bin multiply
 // Y^(k) = B^(k) X^(k) with B = [[a L, b K], [g K, d L]]:
 //   y_J = a L^ x_J + b K^ x_M,   y_M = g K^ x_J + d L^ x_M.
@@ -291,6 +327,170 @@ size_t binmul_tma_smem(int E) {
            2ull * kBmStages * sizeof(uint64_t);
 }
 
+// ------------------------------------------------ K2, FP32, one rhs, half spectrum
+// With reciprocal tables only one bin k of each pair (k, -k) is stored and
+// its blocks serve both: y(k) = B^(k) x(k) (one thread per test row, as in
+// binmul_tma_kernel) and y(-k) = B^(k)^T x(-k), i.e. for each source column
+// j of a slab, y_J(-k)[j] = a sum_i L[i][j] x_J(-k)[i] + b sum_i K[i][j]
+// x_M(-k)[i] (and y_M likewise).  The second product has its own kBmJB
+// warps (one column of the slab each, a warp reduction per output), so both
+// run concurrently on every stage.  Each stored slab is read from HBM once
+// for both bins.  Self-paired bins (k = -k) take only the first product.
+__global__ void binmul_tma_pair_kernel(const float2* __restrict__ Bhat, const float2* __restrict__ Xh,
+                                       float2* __restrict__ Yh, const int32_t* __restrict__ st_bin,
+                                       const int32_t* __restrict__ st_part, int E, int nst, float2 ca,
+                                       float2 cb, float2 cg, float2 cd, int* __restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int stage_elems = 2 * kBmJB * E;
+    float2* sbuf = reinterpret_cast<float2*>(smem_raw);
+    float2* xbuf = sbuf + (size_t)kBmStages * stage_elems;      // [2 buffers][x(k), x(-k)][2E]
+    uint64_t* full = reinterpret_cast<uint64_t*>(xbuf + 8 * E);
+    uint64_t* empty = full + kBmStages;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ncw = (E + 31) / 32;        // warps 1..ncw: y(k); the next kBmJB warps: y(-k)
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kBmStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], ncw + kBmJB);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    const int nloc = (nst - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int nj = (E + kBmJB - 1) / kBmJB;
+    const long long total = (long long)nloc * nj;
+    if (warp == 0) {
+        if (lane != 0) return;
+        long long issued = 0;
+        bool ok = true;
+        for (long long q = 0; q < total; ++q) {
+            const int s = (int)(q % kBmStages);
+            if (q >= kBmStages && !mbar_wait(&empty[s], (uint32_t)((q / kBmStages - 1) & 1))) {
+                ok = false;
+                break;
+            }
+            const int t = (int)(q / nj), jb = (int)(q % nj);
+            const int sb = (int)blockIdx.x + t * (int)gridDim.x;
+            const int bin = st_bin[sb], part = st_part[sb];
+            const int j0 = jb * kBmJB, jn = min(kBmJB, E - j0);
+            const uint32_t bytes_op = (uint32_t)(jn * E * sizeof(float2));
+            const uint32_t bytes_x = (uint32_t)(2 * E * sizeof(float2));
+            const uint32_t xb = jb == 0 ? (part != bin ? 2 * bytes_x : bytes_x) : 0u;
+            mbar_expect_tx(&full[s], 2 * bytes_op + xb);
+            const float2* src = Bhat + (size_t)sb * 2 * E * E + (size_t)j0 * E;
+            float2* dst = sbuf + (size_t)s * stage_elems;
+            bulk_g2s(dst, src, bytes_op, &full[s]);
+            bulk_g2s(dst + kBmJB * E, src + (size_t)E * E, bytes_op, &full[s]);
+            if (jb == 0) {
+                float2* xd = xbuf + (t & 1) * 4 * E;
+                bulk_g2s(xd, Xh + (size_t)bin * 2 * E, bytes_x, &full[s]);
+                if (part != bin) bulk_g2s(xd + 2 * E, Xh + (size_t)part * 2 * E, bytes_x, &full[s]);
+            }
+            issued = q + 1;
+        }
+        if (!ok) {
+            atomicExch(err, 1);
+            for (long long q = (issued > kBmStages ? issued - kBmStages : 0); q < issued; ++q)
+                mbar_wait(&full[q % kBmStages], (uint32_t)((q / kBmStages) & 1));
+        }
+        return;
+    }
+    if (warp > ncw) {
+        // ---- y(-k) = B^(k)^T x(-k): this warp's column of every slab
+        const int jj = warp - ncw - 1;
+        for (long long q = 0; q < total; ++q) {
+            const int s = (int)(q % kBmStages);
+            const int t = (int)(q / nj), jb = (int)(q % nj);
+            if (!mbar_wait(&full[s], (uint32_t)((q / kBmStages) & 1))) {
+                atomicExch(err, 1);
+                return;
+            }
+            const int sb = (int)blockIdx.x + t * (int)gridDim.x;
+            const int bin = st_bin[sb], part = st_part[sb];
+            const int j0 = jb * kBmJB, jn = min(kBmJB, E - j0);
+            if (part != bin && jj < jn) {
+                const float2* Ls = sbuf + (size_t)s * stage_elems;
+                const float2* xp = xbuf + (t & 1) * 4 * E + 2 * E;
+                const float2* Lc = Ls + jj * E;
+                const float2* Kc = Lc + kBmJB * E;
+                float2 pj = make_float2(0.f, 0.f), pm = pj, qj = pj, qm = pj;
+                for (int ii = lane; ii < E; ii += 32) {
+                    const float2 l = Lc[ii], k = Kc[ii], xj = xp[ii], xm = xp[E + ii];
+                    cfma(pj, l, xj);
+                    cfma(pm, l, xm);
+                    cfma(qj, k, xj);
+                    cfma(qm, k, xm);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    pj.x += __shfl_xor_sync(0xffffffffu, pj.x, o);
+                    pj.y += __shfl_xor_sync(0xffffffffu, pj.y, o);
+                    pm.x += __shfl_xor_sync(0xffffffffu, pm.x, o);
+                    pm.y += __shfl_xor_sync(0xffffffffu, pm.y, o);
+                    qj.x += __shfl_xor_sync(0xffffffffu, qj.x, o);
+                    qj.y += __shfl_xor_sync(0xffffffffu, qj.y, o);
+                    qm.x += __shfl_xor_sync(0xffffffffu, qm.x, o);
+                    qm.y += __shfl_xor_sync(0xffffffffu, qm.y, o);
+                }
+                if (lane == 0) {
+                    float2* Y = Yh + (size_t)part * 2 * E;
+                    Y[j0 + jj] = cadd(cmul(ca, pj), cmul(cb, qm));
+                    Y[E + j0 + jj] = cadd(cmul(cg, qj), cmul(cd, pm));
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+        }
+        return;
+    }
+    // ---- y(k) = B^(k) x(k): one thread per test row
+    const int i = (warp - 1) * 32 + lane;
+    float2 lj = make_float2(0.f, 0.f), lm = lj, kj = lj, km = lj;
+    for (long long q = 0; q < total; ++q) {
+        const int s = (int)(q % kBmStages);
+        const int t = (int)(q / nj), jb = (int)(q % nj);
+        if (!mbar_wait(&full[s], (uint32_t)((q / kBmStages) & 1))) {
+            atomicExch(err, 1);
+            return;
+        }
+        const int sb = (int)blockIdx.x + t * (int)gridDim.x;
+        const int bin = st_bin[sb];
+        if (jb == 0) lj = lm = kj = km = make_float2(0.f, 0.f);
+        const float2* Ls = sbuf + (size_t)s * stage_elems;
+        const float2* Ks = Ls + kBmJB * E;
+        const float2* xs = xbuf + (t & 1) * 4 * E;
+        const int j0 = jb * kBmJB, jn = min(kBmJB, E - j0);
+        if (i < E) {
+#pragma unroll
+            for (int jj = 0; jj < kBmJB; ++jj) {
+                if (jj < jn) {
+                    const float2 l = Ls[jj * E + i];
+                    const float2 k = Ks[jj * E + i];
+                    const float2 xj = xs[j0 + jj];
+                    const float2 xm = xs[E + j0 + jj];
+                    cfma(lj, l, xj);
+                    cfma(lm, l, xm);
+                    cfma(kj, k, xj);
+                    cfma(km, k, xm);
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+        if (jb == nj - 1 && i < E) {
+            float2* Y = Yh + (size_t)bin * 2 * E;
+            Y[i] = cadd(cmul(ca, lj), cmul(cb, km));
+            Y[E + i] = cadd(cmul(cg, kj), cmul(cd, lm));
+        }
+    }
+}
+
+size_t binmul_tma_pair_smem(int E) {
+    return (size_t)kBmStages * 2 * kBmJB * E * sizeof(float2) + 8ull * E * sizeof(float2) +
+           2ull * kBmStages * sizeof(uint64_t);
+}
+
 // ------------------------------------------------ K4: macromodel multiply
 // Ymm[s][r][m][k] = sum_{k' in chunk s} Z~^{t(m)}[k][k'] x1[r][m][k'] for a
 // group of up to G cells of one type (x1 = U_o x gathered on the fly).  The
@@ -496,9 +696,59 @@ int derive_fp32_operator(emsurf_handle* h, const emsurf_problem* pr) {
     const size_t nb = (size_t)h->nbins;
     cudaStream_t st = h->setup_stream;
     Operator<float2>& op = h->op32;
-    EMS_TRY(dev_alloc(h, (void**)&op.Bhat, nb * 2 * EE * sizeof(float2)));
-    round_kernel<<<152 * 8, 256, 0, st>>>(op.Bhat, h->op64.Bhat, nb * 2 * EE);
-    EMS_CUDA(cudaGetLastError());
+    // With reciprocal tables B^(-k) = B^(k)^T: single-rhs handles without the
+    // tensor-core planes keep one bin of each pair (k, -k) (checked here on
+    // the FP64 spectrum, to 1e-12 of its largest entry).
+    bool half = false;
+    std::vector<int32_t> partner(nb), sbin, spart;
+    for (int ky = 0; ky < h->py; ++ky)
+        for (int kx = 0; kx < h->px; ++kx)
+            partner[(size_t)ky * h->px + kx] = ((h->py - ky) % h->py) * h->px + (h->px - kx) % h->px;
+    const int ncw = (h->E + 31) / 32;
+    if (h->max_rhs == 1 && !pr->tensor_cores && binmul_tma_pair_smem(h->E) <= 227 * 1024 &&
+        32 * (1 + ncw + kBmJB) <= 1024 && (h->E + kBmJB - 1) / kBmJB >= kBmStages) {
+        int32_t* dpart = nullptr;
+        unsigned long long* dout = nullptr;
+        EMS_CUDA(cudaMalloc(&dpart, nb * sizeof(int32_t)));
+        EMS_CUDA(cudaMalloc(&dout, 2 * sizeof(unsigned long long)));
+        EMS_CUDA(cudaMemcpyAsync(dpart, partner.data(), nb * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        EMS_CUDA(cudaMemsetAsync(dout, 0, 2 * sizeof(unsigned long long), st));
+        reciprocity_kernel<<<152 * 8, 256, 0, st>>>(h->op64.Bhat, dpart, h->E, nb, dout);
+        EMS_CUDA(cudaGetLastError());
+        unsigned long long hout[2] = {0, 0};
+        EMS_CUDA(cudaMemcpyAsync(hout, dout, sizeof(hout), cudaMemcpyDeviceToHost, st));
+        EMS_CUDA(cudaStreamSynchronize(st));
+        cudaFree(dpart);
+        cudaFree(dout);
+        double dmax, vmax;
+        std::memcpy(&dmax, &hout[0], sizeof(double));
+        std::memcpy(&vmax, &hout[1], sizeof(double));
+        half = vmax > 0.0 && dmax <= 1e-12 * vmax;
+    }
+    if (half) {
+        for (size_t b = 0; b < nb; ++b)
+            if ((int32_t)b <= partner[b]) {
+                sbin.push_back((int32_t)b);
+                spart.push_back(partner[b]);
+            }
+        h->nst = (int)sbin.size();
+        int32_t *dsb = nullptr, *dsp = nullptr;
+        EMS_TRY(dev_alloc(h, (void**)&dsb, sbin.size() * sizeof(int32_t)));
+        EMS_TRY(dev_alloc(h, (void**)&dsp, spart.size() * sizeof(int32_t)));
+        EMS_CUDA(cudaMemcpyAsync(dsb, sbin.data(), sbin.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        EMS_CUDA(cudaMemcpyAsync(dsp, spart.data(), spart.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        h->d_st_bin = dsb;
+        h->d_st_part = dsp;
+        EMS_TRY(dev_alloc(h, (void**)&op.Bhat, (size_t)h->nst * 2 * EE * sizeof(float2)));
+        half_round_kernel<<<152 * 8, 256, 0, st>>>(op.Bhat, h->op64.Bhat, dsb, 2 * EE, (size_t)h->nst * 2 * EE);
+        EMS_CUDA(cudaGetLastError());
+        EMS_CUDA(cudaStreamSynchronize(st));   // the host vectors above go out of scope
+        h->half32 = true;
+    } else {
+        EMS_TRY(dev_alloc(h, (void**)&op.Bhat, nb * 2 * EE * sizeof(float2)));
+        round_kernel<<<152 * 8, 256, 0, st>>>(op.Bhat, h->op64.Bhat, nb * 2 * EE);
+        EMS_CUDA(cudaGetLastError());
+    }
     EMS_TRY(dev_alloc(h, (void**)&op.Zt, (size_t)h->T * K * K * sizeof(float2)));
     round_kernel<<<152 * 8, 256, 0, st>>>(op.Zt, h->op64.Zt, (size_t)h->T * K * K);
     EMS_CUDA(cudaGetLastError());
@@ -607,6 +857,18 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
         }
     }
     if constexpr (std::is_same<T2, float2>::value) {
+        if (!bin_done && h->half32) {
+            // half spectrum (single rhs): one read of each stored bin serves k and -k
+            const size_t smem = binmul_tma_pair_smem(E);
+            EMS_TRY(set_smem_once(binmul_tma_pair_kernel, smem));
+            const int grid = std::min(h->nst, std::max(1, h->num_sms));
+            binmul_tma_pair_kernel<<<grid, 32 * (1 + (E + 31) / 32 + kBmJB), smem, st>>>(
+                op.Bhat, op.Xg, op.Yg, h->d_st_bin, h->d_st_part, E, h->nst, op.coef[0], op.coef[1], op.coef[2],
+                op.coef[3], h->d_err);
+            EMS_CUDA(cudaGetLastError());
+            h->launches += 1;
+            bin_done = true;
+        }
         const size_t smem = binmul_tma_smem(E);
         // the x double buffer needs at least kBmStages stages per bin
         if (!bin_done && R == 1 && smem <= 227 * 1024 && E + 32 <= 1024 && (E + kBmJB - 1) / kBmJB >= kBmStages) {

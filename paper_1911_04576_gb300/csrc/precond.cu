@@ -334,7 +334,7 @@ pc_apply_kernel(const float2* __restrict__ X, const int64_t* __restrict__ xoff,
                 const int c2 = min(c0 + 32 * u, half - 1);
 #pragma unroll
                 for (int q = 0; q < RQ; ++q) {
-                    if (q >= nr) break;   // rhs past the live count: no reads (uniform branch)
+                    if (RQ > 2 && q >= nr) break;   // rhs past the live count (wide kernels only)
                     const float4 rv = __ldg(rv4 + q * (rs_stride >> 1) + c2);
                     acc[q].x += xv[u].x * rv.x - xv[u].y * rv.y + xv[u].z * rv.z - xv[u].w * rv.w;
                     acc[q].y += xv[u].x * rv.y + xv[u].y * rv.x + xv[u].z * rv.w + xv[u].w * rv.z;
@@ -351,7 +351,7 @@ pc_apply_kernel(const float2* __restrict__ X, const int64_t* __restrict__ xoff,
             const int u = sub_ids[sub_ptr[m] + i];
 #pragma unroll
             for (int q = 0; q < RQ; ++q) {
-                if (q >= nr) break;
+                if (RQ > 2 && q >= nr) break;
                 VO o;
                 o.x = acc[q].x;
                 o.y = acc[q].y;

@@ -530,6 +530,34 @@ EMSURF_API int emsurf_tabulate(const double* test_verts, const int32_t* test_tri
                            reinterpret_cast<double2*>(K), reinterpret_cast<cudaStream_t>(stream));
 }
 
+}  // extern "C"
+
+namespace emsurf {
+namespace {
+// T(d) <- (T(d) + T(-d)^T) / 2 for both tables in place: offset o and its
+// mirror nof - 1 - o form one pair, handled by one thread per entry pair.
+__global__ void reciprocal_part_kernel(double2* __restrict__ L, double2* __restrict__ K, int nof, int E) {
+    const size_t EE = (size_t)E * E, total = (size_t)nof * EE;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int o = (int)(e / EE), om = nof - 1 - o;
+        const int i = (int)((e % EE) / E), j = (int)(e % E);
+        if (o > om || (o == om && i >= j)) continue;
+        const size_t p = e, q = (size_t)om * EE + (size_t)j * E + i;
+        double2 t[2] = {L[p], K[p]};
+        double2 u[2] = {L[q], K[q]};
+        const double2 sl = make_double2((t[0].x + u[0].x) * 0.5, (t[0].y + u[0].y) * 0.5);
+        const double2 sk = make_double2((t[1].x + u[1].x) * 0.5, (t[1].y + u[1].y) * 0.5);
+        L[p] = sl;
+        L[q] = sl;
+        K[p] = sk;
+        K[q] = sk;
+    }
+}
+}  // namespace
+}  // namespace emsurf
+
+extern "C" {
+
 EMSURF_API int emsurf_tabulate_offsets(double a, double b, double h, int32_t n, int32_t nx,
                                        int32_t ny, double k, emsurf_c128* L, emsurf_c128* K,
                                        void* stream) {
@@ -557,9 +585,16 @@ EMSURF_API int emsurf_tabulate_offsets(double a, double b, double h, int32_t n, 
             sing[o] = (std::abs(dx) <= 1 && std::abs(dy) <= 1) ? 1 : 0;
         }
     MeshView mv{verts.data(), tris.data(), srw.data(), ssg.data(), T, E};
-    return tabulate_blocks(mv, mv, shifts.data(), sing.data(), nox * noy, k,
-                           reinterpret_cast<double2*>(L), reinterpret_cast<double2*>(K),
-                           reinterpret_cast<cudaStream_t>(stream));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    EMS_TRY(tabulate_blocks(mv, mv, shifts.data(), sing.data(), nox * noy, k, reinterpret_cast<double2*>(L),
+                            reinterpret_cast<double2*>(K), st));
+    // reciprocal part of the one-sided blocks (exactly reciprocal tables)
+    const size_t total = (size_t)nox * noy * E * E;
+    reciprocal_part_kernel<<<(int)std::min<size_t>((total + 255) / 256, 152 * 64), 256, 0, st>>>(
+        reinterpret_cast<double2*>(L), reinterpret_cast<double2*>(K), nox * noy, E);
+    EMS_CUDA(cudaGetLastError());
+    EMS_CUDA(cudaStreamSynchronize(st));
+    return EMSURF_OK;
 }
 
 }  // extern "C"

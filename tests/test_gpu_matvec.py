@@ -149,3 +149,39 @@ def test_bounded_wait_expiry_is_reported(emsurf_lib):
     with pytest.raises(B.EmsurfError):
         B.emsurf_selftest_wait(h, 0)        # limit outside [1, 2^22]
     h.close()
+
+
+def reciprocal(T):
+    """Reciprocal part of a table: T(d) <- (T(d) + T(-d)^T) / 2."""
+    return 0.5 * (T + np.swapaxes(T[::-1, ::-1], 2, 3))
+
+
+@pytest.mark.parametrize("n,nx,ny,grid", [(2, 3, 2, (0, 0)), (2, 4, 4, (8, 8)), (3, 2, 3, (0, 0)),
+                                          (2, 5, 3, (10, 6))])
+def test_half_spectrum_parity(emsurf_lib, n, nx, ny, grid):
+    """Reciprocal tables (L(-d) = L(d)^T, K(-d) = K(d)^T) on a single-rhs MIXED
+    handle: the FP32 operator stores one bin of each pair (k, -k) and the
+    paired kernel applies B^(k) to x(k) and B^(k)^T to x(-k).  Same FP32 bar
+    against the oracle; odd and even grids (1, 2 or 4 self-paired bins)."""
+    from paper_1911_04576_gb300 import binding as B
+    seed = 700 + 10 * nx + ny
+    E, idx, sgn, nu, Lt, Kt, Z, tmap = random_case(n, nx, ny, 3, seed)
+    Lt, Kt = reciprocal(Lt), reciprocal(Kt)
+    h = B.emsurf_create(nx, ny, E, nu, tmap, Z, Lt, Kt, COEF, idx, sgn, precision=B.MIXED, grid=grid)
+    x = W.random_vectors(1, nu, seed + 3)
+    yref = lattice.matvec_direct(x, Lt, Kt, COEF, Z, tmap, idx, sgn, nu, nx, ny)
+    assert relerr(run_matvec(B, h, x, B.FP32)[0], yref[0]) <= TOL32
+    assert relerr(run_matvec(B, h, x, B.FP64)[0], yref[0]) <= TOL64
+    # the FP32 spectrum is (about) half of a non-reciprocal handle's
+    Lr, Kr = W.random_tables(nx, ny, E, seed)
+    h2 = B.emsurf_create(nx, ny, E, nu, tmap, Z, Lr, Kr, COEF, idx, sgn, precision=B.MIXED, grid=grid)
+    px, py, bytes_half = B.emsurf_query(h)
+    bytes_full = B.emsurf_query(h2)[2]
+    P = px * py
+    stored = (P + sum(1 for kx in range(px) for ky in range(py)
+                      if (2 * kx) % px == 0 and (2 * ky) % py == 0)) // 2
+    # (minus the stored-bin index arrays)
+    assert abs((bytes_full - bytes_half) - (P - stored) * 2 * E * E * 8) <= 8 * stored + 4096
+    B.emsurf_check(h)
+    h.close()
+    h2.close()

@@ -113,3 +113,27 @@ def test_sampled_rows_equal_full_direct_product():
     assert np.abs(yr - y[rows]).max() <= 1e-12 * np.abs(y).max()
     Ad = lattice.assemble_from_tables(Lt, Kt, COEF, Zt, tmap, idx, sgn, nu, nx, ny)
     assert np.abs(Ad @ x - y).max() <= 1e-12 * np.abs(y).max()
+
+
+def test_offset_tables_reciprocal_exactly():
+    """The tables are the reciprocal part of the one-sided blocks: L(-d) =
+    L(d)^T and K(-d) = K(d)^T to rounding at every offset, touching ones
+    included, and at far offsets (where the one-sided blocks are already
+    reciprocal) they equal the one-sided blocks."""
+    from oracle.operators import galerkin_LK
+    box = box_mesh(A, B, H, 2)
+    nx, ny = 3, 3
+    Lt, Kt = lattice.offset_tables(box, nx, ny, A, B, K0)
+    for dy in range(-(ny - 1), ny):
+        for dx in range(-(nx - 1), nx):
+            Lp, Kp = Lt[dy + ny - 1, dx + nx - 1], Kt[dy + ny - 1, dx + nx - 1]
+            Lm, Km = Lt[-dy + ny - 1, -dx + nx - 1], Kt[-dy + ny - 1, -dx + nx - 1]
+            assert np.abs(Lm - Lp.T).max() <= 1e-15 * np.abs(Lp).max()
+            assert np.abs(Km - Kp.T).max() <= 1e-15 * np.abs(Kp).max() + 1e-300
+    L1, K1 = galerkin_LK(box, lattice.cell_shift(2, 1, A, B), box, (0.0, 0.0, 0.0), K0, False)
+    assert np.abs(Lt[1 + ny - 1, 2 + nx - 1] - L1).max() <= 1e-13 * np.abs(L1).max()
+    assert np.abs(Kt[1 + ny - 1, 2 + nx - 1] - K1).max() <= 1e-13 * np.abs(K1).max()
+    # the explicit-offset form gives the same blocks
+    d = lattice.offset_tables(box, nx, ny, A, B, K0, offsets=[(1, 0), (0, 0)])
+    assert np.array_equal(d[(1, 0)][0], Lt[ny - 1, 1 + nx - 1])
+    assert np.array_equal(d[(0, 0)][1], Kt[ny - 1, nx - 1])
