@@ -178,6 +178,7 @@ __global__ void binmul_kernel(const T2* __restrict__ Bhat, const T2* __restrict_
 // the producer waits (bounded) for its copies in flight, and all return.
 constexpr int kBmJB = 8;
 constexpr int kBmStages = 4;
+constexpr int kPairStages = 5;    // the half-spectrum kernel's ring (its x buffers are larger)
 constexpr long long kWaitLimit = 1LL << 22;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -343,13 +344,13 @@ __global__ void binmul_tma_pair_kernel(const float2* __restrict__ Bhat, const fl
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int stage_elems = 2 * kBmJB * E;
     float2* sbuf = reinterpret_cast<float2*>(smem_raw);
-    float2* xbuf = sbuf + (size_t)kBmStages * stage_elems;      // [2 buffers][x(k), x(-k)][2E]
+    float2* xbuf = sbuf + (size_t)kPairStages * stage_elems;      // [2 buffers][x(k), x(-k)][2E]
     uint64_t* full = reinterpret_cast<uint64_t*>(xbuf + 8 * E);
-    uint64_t* empty = full + kBmStages;
+    uint64_t* empty = full + kPairStages;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ncw = (E + 31) / 32;        // warps 1..ncw: y(k); the next kBmJB warps: y(-k)
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kBmStages; ++s) {
+        for (int s = 0; s < kPairStages; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], ncw + kBmJB);
         }
@@ -365,8 +366,8 @@ __global__ void binmul_tma_pair_kernel(const float2* __restrict__ Bhat, const fl
         long long issued = 0;
         bool ok = true;
         for (long long q = 0; q < total; ++q) {
-            const int s = (int)(q % kBmStages);
-            if (q >= kBmStages && !mbar_wait(&empty[s], (uint32_t)((q / kBmStages - 1) & 1))) {
+            const int s = (int)(q % kPairStages);
+            if (q >= kPairStages && !mbar_wait(&empty[s], (uint32_t)((q / kPairStages - 1) & 1))) {
                 ok = false;
                 break;
             }
@@ -391,8 +392,8 @@ __global__ void binmul_tma_pair_kernel(const float2* __restrict__ Bhat, const fl
         }
         if (!ok) {
             atomicExch(err, 1);
-            for (long long q = (issued > kBmStages ? issued - kBmStages : 0); q < issued; ++q)
-                mbar_wait(&full[q % kBmStages], (uint32_t)((q / kBmStages) & 1));
+            for (long long q = (issued > kPairStages ? issued - kPairStages : 0); q < issued; ++q)
+                mbar_wait(&full[q % kPairStages], (uint32_t)((q / kPairStages) & 1));
         }
         return;
     }
@@ -400,9 +401,9 @@ __global__ void binmul_tma_pair_kernel(const float2* __restrict__ Bhat, const fl
         // ---- y(-k) = B^(k)^T x(-k): this warp's column of every slab
         const int jj = warp - ncw - 1;
         for (long long q = 0; q < total; ++q) {
-            const int s = (int)(q % kBmStages);
+            const int s = (int)(q % kPairStages);
             const int t = (int)(q / nj), jb = (int)(q % nj);
-            if (!mbar_wait(&full[s], (uint32_t)((q / kBmStages) & 1))) {
+            if (!mbar_wait(&full[s], (uint32_t)((q / kPairStages) & 1))) {
                 atomicExch(err, 1);
                 return;
             }
@@ -414,26 +415,67 @@ __global__ void binmul_tma_pair_kernel(const float2* __restrict__ Bhat, const fl
                 const float2* xp = xbuf + (t & 1) * 4 * E + 2 * E;
                 const float2* Lc = Ls + jj * E;
                 const float2* Kc = Lc + kBmJB * E;
-                float2 pj = make_float2(0.f, 0.f), pm = pj, qj = pj, qm = pj;
-                for (int ii = lane; ii < E; ii += 32) {
-                    const float2 l = Lc[ii], k = Kc[ii], xj = xp[ii], xm = xp[E + ii];
-                    cfma(pj, l, xj);
-                    cfma(pm, l, xm);
-                    cfma(qj, k, xj);
-                    cfma(qm, k, xm);
+                // rows in pairs (16-byte loads): two independent FMA chains per lane
+                float2 a[2][4];
+#pragma unroll
+                for (int h2 = 0; h2 < 2; ++h2)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) a[h2][c] = make_float2(0.f, 0.f);
+                for (int r = 2 * lane; r < E; r += 64) {
+                    const float4 l = *reinterpret_cast<const float4*>(Lc + r);
+                    const float4 k = *reinterpret_cast<const float4*>(Kc + r);
+                    const float4 xj = *reinterpret_cast<const float4*>(xp + r);
+                    const float4 xm = *reinterpret_cast<const float4*>(xp + E + r);
+                    const float2 l0 = make_float2(l.x, l.y), l1 = make_float2(l.z, l.w);
+                    const float2 k0 = make_float2(k.x, k.y), k1 = make_float2(k.z, k.w);
+                    const float2 xj0 = make_float2(xj.x, xj.y), xj1 = make_float2(xj.z, xj.w);
+                    const float2 xm0 = make_float2(xm.x, xm.y), xm1 = make_float2(xm.z, xm.w);
+                    cfma(a[0][0], l0, xj0);
+                    cfma(a[0][1], l0, xm0);
+                    cfma(a[0][2], k0, xj0);
+                    cfma(a[0][3], k0, xm0);
+                    cfma(a[1][0], l1, xj1);
+                    cfma(a[1][1], l1, xm1);
+                    cfma(a[1][2], k1, xj1);
+                    cfma(a[1][3], k1, xm1);
+                }
+                // v = (pj, pm, qj, qm) as 8 floats; reduce-scatter butterfly over
+                // the warp (4 + 2 + 1 + 1 + 1 shuffles), after which lane 4c
+                // holds the warp sum of value c
+                float v[8];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    v[2 * c] = a[0][c].x + a[1][c].x;
+                    v[2 * c + 1] = a[0][c].y + a[1][c].y;
+                }
+                const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+                float w4[4], w2[2];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float send = b4 ? v[c] : v[c + 4];
+                    const float keep = b4 ? v[c + 4] : v[c];
+                    w4[c] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
                 }
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    pj.x += __shfl_xor_sync(0xffffffffu, pj.x, o);
-                    pj.y += __shfl_xor_sync(0xffffffffu, pj.y, o);
-                    pm.x += __shfl_xor_sync(0xffffffffu, pm.x, o);
-                    pm.y += __shfl_xor_sync(0xffffffffu, pm.y, o);
-                    qj.x += __shfl_xor_sync(0xffffffffu, qj.x, o);
-                    qj.y += __shfl_xor_sync(0xffffffffu, qj.y, o);
-                    qm.x += __shfl_xor_sync(0xffffffffu, qm.x, o);
-                    qm.y += __shfl_xor_sync(0xffffffffu, qm.y, o);
+                for (int c = 0; c < 2; ++c) {
+                    const float send = b3 ? w4[c] : w4[c + 2];
+                    const float keep = b3 ? w4[c + 2] : w4[c];
+                    w2[c] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
                 }
+                float w1;
+                {
+                    const float send = b2 ? w2[0] : w2[1];
+                    const float keep = b2 ? w2[1] : w2[0];
+                    w1 = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+                }
+                w1 += __shfl_xor_sync(0xffffffffu, w1, 2);
+                w1 += __shfl_xor_sync(0xffffffffu, w1, 1);
+                float f[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) f[c] = __shfl_sync(0xffffffffu, w1, 4 * c);
                 if (lane == 0) {
+                    const float2 pj = make_float2(f[0], f[1]), pm = make_float2(f[2], f[3]);
+                    const float2 qj = make_float2(f[4], f[5]), qm = make_float2(f[6], f[7]);
                     float2* Y = Yh + (size_t)part * 2 * E;
                     Y[j0 + jj] = cadd(cmul(ca, pj), cmul(cb, qm));
                     Y[E + j0 + jj] = cadd(cmul(cg, qj), cmul(cd, pm));
@@ -448,38 +490,55 @@ __global__ void binmul_tma_pair_kernel(const float2* __restrict__ Bhat, const fl
     const int i = (warp - 1) * 32 + lane;
     float2 lj = make_float2(0.f, 0.f), lm = lj, kj = lj, km = lj;
     for (long long q = 0; q < total; ++q) {
-        const int s = (int)(q % kBmStages);
+        const int s = (int)(q % kPairStages);
         const int t = (int)(q / nj), jb = (int)(q % nj);
-        if (!mbar_wait(&full[s], (uint32_t)((q / kBmStages) & 1))) {
+        if (!mbar_wait(&full[s], (uint32_t)((q / kPairStages) & 1))) {
             atomicExch(err, 1);
             return;
         }
-        const int sb = (int)blockIdx.x + t * (int)gridDim.x;
-        const int bin = st_bin[sb];
         if (jb == 0) lj = lm = kj = km = make_float2(0.f, 0.f);
         const float2* Ls = sbuf + (size_t)s * stage_elems;
         const float2* Ks = Ls + kBmJB * E;
         const float2* xs = xbuf + (t & 1) * 4 * E;
         const int j0 = jb * kBmJB, jn = min(kBmJB, E - j0);
         if (i < E) {
+            // x(k) of the slab's columns (broadcast reads, two complex per 16 bytes)
+            float2 xjv[kBmJB], xmv[kBmJB];
+            if (jn == kBmJB) {
+                const float4* xj4 = reinterpret_cast<const float4*>(xs + j0);
+                const float4* xm4 = reinterpret_cast<const float4*>(xs + E + j0);
+#pragma unroll
+                for (int p = 0; p < kBmJB / 2; ++p) {
+                    const float4 a = xj4[p], b = xm4[p];
+                    xjv[2 * p] = make_float2(a.x, a.y);
+                    xjv[2 * p + 1] = make_float2(a.z, a.w);
+                    xmv[2 * p] = make_float2(b.x, b.y);
+                    xmv[2 * p + 1] = make_float2(b.z, b.w);
+                }
+            } else {
+#pragma unroll
+                for (int jj = 0; jj < kBmJB; ++jj) {
+                    xjv[jj] = jj < jn ? xs[j0 + jj] : make_float2(0.f, 0.f);
+                    xmv[jj] = jj < jn ? xs[E + j0 + jj] : make_float2(0.f, 0.f);
+                }
+            }
 #pragma unroll
             for (int jj = 0; jj < kBmJB; ++jj) {
                 if (jj < jn) {
                     const float2 l = Ls[jj * E + i];
                     const float2 k = Ks[jj * E + i];
-                    const float2 xj = xs[j0 + jj];
-                    const float2 xm = xs[E + j0 + jj];
-                    cfma(lj, l, xj);
-                    cfma(lm, l, xm);
-                    cfma(kj, k, xj);
-                    cfma(km, k, xm);
+                    cfma(lj, l, xjv[jj]);
+                    cfma(lm, l, xmv[jj]);
+                    cfma(kj, k, xjv[jj]);
+                    cfma(km, k, xmv[jj]);
                 }
             }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
         if (jb == nj - 1 && i < E) {
-            float2* Y = Yh + (size_t)bin * 2 * E;
+            const int sb = (int)blockIdx.x + t * (int)gridDim.x;
+            float2* Y = Yh + (size_t)st_bin[sb] * 2 * E;
             Y[i] = cadd(cmul(ca, lj), cmul(cb, km));
             Y[E + i] = cadd(cmul(cg, kj), cmul(cd, lm));
         }
@@ -487,8 +546,8 @@ __global__ void binmul_tma_pair_kernel(const float2* __restrict__ Bhat, const fl
 }
 
 size_t binmul_tma_pair_smem(int E) {
-    return (size_t)kBmStages * 2 * kBmJB * E * sizeof(float2) + 8ull * E * sizeof(float2) +
-           2ull * kBmStages * sizeof(uint64_t);
+    return (size_t)kPairStages * 2 * kBmJB * E * sizeof(float2) + 8ull * E * sizeof(float2) +
+           2ull * kPairStages * sizeof(uint64_t);
 }
 
 // ------------------------------------------------ K4: macromodel multiply
@@ -705,8 +764,8 @@ int derive_fp32_operator(emsurf_handle* h, const emsurf_problem* pr) {
         for (int kx = 0; kx < h->px; ++kx)
             partner[(size_t)ky * h->px + kx] = ((h->py - ky) % h->py) * h->px + (h->px - kx) % h->px;
     const int ncw = (h->E + 31) / 32;
-    if (h->max_rhs == 1 && !pr->tensor_cores && binmul_tma_pair_smem(h->E) <= 227 * 1024 &&
-        32 * (1 + ncw + kBmJB) <= 1024 && (h->E + kBmJB - 1) / kBmJB >= kBmStages) {
+    if (h->max_rhs == 1 && !pr->tensor_cores && (h->E & 1) == 0 && binmul_tma_pair_smem(h->E) <= 227 * 1024 &&
+        32 * (1 + ncw + kBmJB) <= 1024 && (h->E + kBmJB - 1) / kBmJB >= kPairStages) {
         int32_t* dpart = nullptr;
         unsigned long long* dout = nullptr;
         EMS_CUDA(cudaMalloc(&dpart, nb * sizeof(int32_t)));
