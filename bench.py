@@ -45,6 +45,9 @@ PC_OVERLAP = 0.6               # preconditioner margin, in mesh cells (a / n)
 # 576 bins); the kernel streams each bin's blocks once, so traffic scales
 # with the bin count.
 BINMUL_DRAM_BYTES_PER_BIN = (767108096 + 5353216) / 576
+# the same for binmul_tma_pair_kernel (half spectrum) per stored bin, from
+# profiles/binmul_tma_pair_lattice12x12_k576.md (290 stored bins)
+PAIR_DRAM_BYTES_PER_STORED_BIN = (387570432 + 4896000) / 290
 
 
 FALLBACK_BF16_TFLOPS = 1900.0
@@ -416,7 +419,7 @@ def main():
     mv64 = time_matvec(B, torch, h, nu, R, B.FP64)
     px, py, dev_bytes = B.emsurf_query(h)
     P = px * py
-    bytes32 = 2 * w.E * w.E * P * 8 + w.n_types * w.K * w.K * 8 + 2 * R * nu * 16
+    bytes32 = 2 * w.E * w.E * B.emsurf_operator_info(h)[0] * 8 + w.n_types * w.K * w.K * 8 + 2 * R * nu * 16
     bytes64 = 2 * w.E * w.E * P * 16 + w.n_types * w.K * w.K * 16 + 2 * R * nu * 16
     solve_kw = dict(rtol=RTOL, restart=RESTART, max_iters=20000, max_refine=20,
                     solver=B.SOLVER_MIXED)
@@ -501,8 +504,14 @@ def main():
             dist.destroy_process_group()
         return
     bin_avg = bin_ms / max(bin_n, 1)
-    alg_bin = 2 * w.E * w.E * P * 8 + 2 * R * w.K * P * 8
+    stored, _ = B.emsurf_operator_info(h)
+    half = stored < P
+    # algorithmic bytes of the kernel that ran: the stored spectrum bins once,
+    # X^ read and Y^ written for every bin
+    alg_bin = 2 * w.E * w.E * stored * 8 + 2 * R * w.K * P * 8
     achieved = alg_bin / (bin_avg * 1e-3) / 1e9
+    traffic = (PAIR_DRAM_BYTES_PER_STORED_BIN * stored if half
+               else BINMUL_DRAM_BYTES_PER_BIN * P if BINMUL_DRAM_BYTES_PER_BIN else None)
     # preconditioner apply: FP32 LU factors once, r gathered, owned rows written
     pc_avg = pc_ms / max(pc_n, 1)
     alg_pc = pc_elems * 8 + R * (pc_subtot * 16 + pc_subtot * 8 + nu * 16)
@@ -541,11 +550,12 @@ def main():
         "matvec": {"fp32_ms": round(mv32, 4), "fp32_gbs": round(bytes32 / mv32 / 1e6, 1),
                    "fp64_ms": round(mv64, 4), "fp64_gbs": round(bytes64 / mv64 / 1e6, 1),
                    "alg_bytes_fp32": bytes32, "alg_bytes_fp64": bytes64},
-        "roofline": {"kernel": "binmul_tma_kernel (bin multiply, FP32)", "bound": "hbm",
+        "roofline": {"kernel": ("binmul_tma_pair_kernel (bin multiply, FP32, half spectrum: %d of %d bins)"
+                                % (stored, P) if half else "binmul_tma_kernel (bin multiply, FP32)"),
+                     "bound": "hbm",
                      "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "peak_kind": peak_kind,
-                     "traffic": (round(BINMUL_DRAM_BYTES_PER_BIN * P) if BINMUL_DRAM_BYTES_PER_BIN
-                                 else None),
+                     "traffic": round(traffic) if traffic else None,
                      "alg_bytes_per_launch": alg_bin,
                      "avg_launch_ms": round(bin_avg, 5), "launches_timed": bin_n},
         "phases_ms_per_solve": {"binmul32": round(bin_ms / args.steps, 3),

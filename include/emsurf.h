@@ -169,6 +169,12 @@ EMSURF_API int emsurf_precond_apply(emsurf_handle* h, const emsurf_c128* r, emsu
 EMSURF_API int emsurf_precond_info(const emsurf_handle* h, int64_t* factor_entries,
                                    int64_t* subdomain_total, int32_t* max_subdomain);
 
+/* FP32 operator layout: spectrum bins it stores (grid_px * grid_py, or
+ * about half of that when the tables are reciprocal and the handle holds a
+ * single rhs: one bin of each pair (k, -k), Sec. IV-B with L(-d) = L(d)^T)
+ * and whether the tensor-core planes were built (1) or not (0).          */
+EMSURF_API int emsurf_operator_info(const emsurf_handle* h, int32_t* stored_bins, int32_t* tensor_cores);
+
 /* Grid chosen by emsurf_create, unknown count and bytes of device memory
  * held by the handle.                                                     */
 EMSURF_API int emsurf_query(const emsurf_handle* h, int32_t* grid_px, int32_t* grid_py,

@@ -82,6 +82,7 @@ def lib():
         L.emsurf_setup_overlap.argtypes = [i32, i32, i32, vp, vp, ip]
         L.emsurf_precond_apply.argtypes = [vp, vp, vp, i32, vp]
         L.emsurf_selftest_wait.argtypes = [vp, C.c_int64, vp]
+        L.emsurf_operator_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
         L.emsurf_precond_info.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                           C.POINTER(i32)]
         L.emsurf_setup_unknown_xy.argtypes = [C.c_double, C.c_double, C.c_double, i32, i32, i32,
@@ -206,6 +207,13 @@ def emsurf_precond_apply(h, r, y, stream=None):
 def emsurf_selftest_wait(h, limit=1000, stream=None):
     """emsurf_selftest_wait: a bounded device wait that always expires."""
     _check(lib().emsurf_selftest_wait(h.ptr, limit, _stream(stream)))
+
+
+def emsurf_operator_info(h):
+    """(stored spectrum bins of the FP32 operator, tensor-core planes built)."""
+    nb, tc = C.c_int32(), C.c_int32()
+    _check(lib().emsurf_operator_info(h.ptr, C.byref(nb), C.byref(tc)))
+    return nb.value, bool(tc.value)
 
 
 def emsurf_precond_info(h):

@@ -303,6 +303,13 @@ EMSURF_API int emsurf_matvec(emsurf_handle* h, const emsurf_c128* x, emsurf_c128
     return EMSURF_EINVAL;
 }
 
+EMSURF_API int emsurf_operator_info(const emsurf_handle* h, int32_t* stored_bins, int32_t* tensor_cores) {
+    if (!h) { set_error("NULL handle"); return EMSURF_EINVAL; }
+    if (stored_bins) *stored_bins = h->half32 ? h->nst : h->nbins;
+    if (tensor_cores) *tensor_cores = h->have_tc ? 1 : 0;
+    return EMSURF_OK;
+}
+
 EMSURF_API int emsurf_precond_info(const emsurf_handle* h, int64_t* factor_entries,
                                    int64_t* subdomain_total, int32_t* max_subdomain) {
     if (!h) { set_error("NULL handle"); return EMSURF_EINVAL; }

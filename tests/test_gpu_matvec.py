@@ -180,6 +180,8 @@ def test_half_spectrum_parity(emsurf_lib, n, nx, ny, grid):
     P = px * py
     stored = (P + sum(1 for kx in range(px) for ky in range(py)
                       if (2 * kx) % px == 0 and (2 * ky) % py == 0)) // 2
+    assert B.emsurf_operator_info(h) == (stored, False)
+    assert B.emsurf_operator_info(h2) == (P, False)
     # (minus the stored-bin index arrays)
     assert abs((bytes_full - bytes_half) - (P - stored) * 2 * E * E * 8) <= 8 * stored + 4096
     B.emsurf_check(h)
