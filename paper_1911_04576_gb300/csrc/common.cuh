@@ -189,6 +189,7 @@ struct emsurf_handle {
     alignas(64) unsigned char tc_maps[8][128];
     int mm_occ[4] = {0, 0, 0, 0};          // resident macromodel CTAs per SM (FP32, FP64; x 1 / 4 rhs)
     int mm_threads[4] = {0, 0, 0, 0};      // macromodel block size per variant
+    int mm2_occ = 0;                       // resident single-rhs FP32 macromodel CTAs per SM
     cudaStream_t setup_stream = nullptr;   // stream of the create-time work
     // near-field preconditioner (restricted additive Schwarz, FP32 LU blocks)
     bool have_pc = false;

@@ -620,6 +620,88 @@ __global__ void macromodel_kernel(const T2* __restrict__ Zt, const double2* __re
     }
 }
 
+// Single-rhs FP32 variant: each thread owns two adjacent output rows and
+// keeps eight 16-byte loads of Z in flight (the one-row kernel is bound by
+// load latency at one rhs); the staged x1 is read two columns at a time.
+constexpr int kMm2Unroll = 8;
+template <int G>
+__global__ void __launch_bounds__(320)
+macromodel2_kernel(const float2* __restrict__ Zt, const double2* __restrict__ x,
+                   const int32_t* __restrict__ idx, const int8_t* __restrict__ sgn,
+                   const int32_t* __restrict__ type_cells, const MmBlock* __restrict__ blocks,
+                   float2* __restrict__ Ymm, int K, int M, int n_unique, int chunk, const float2* __restrict__ xf) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* xs = reinterpret_cast<float2*>(smem_raw);   // [G][chunk], chunk a multiple of kMm2Unroll
+    const MmBlock b = blocks[blockIdx.x];
+    const int s = blockIdx.y;
+    const int k0 = s * chunk, k1 = min(K, k0 + chunk), nk = k1 - k0;
+    // gather x1 (independent iterations: unrolled so their loads overlap)
+#pragma unroll 4
+    for (int e = threadIdx.x; e < G * chunk; e += blockDim.x) {
+        const int g = e / chunk, kk = e % chunk;
+        float2 v = make_float2(0.f, 0.f);
+        if (g < b.count && kk < nk) {
+            const size_t loc = (size_t)type_cells[b.first + g] * K + k0 + kk;
+            const size_t at = idx[loc];
+            const float sg = (float)sgn[loc];
+            if (xf) {
+                const float2 xv = xf[at];
+                v = make_float2(sg * xv.x, sg * xv.y);
+            } else {
+                const double2 xv = x[at];
+                v = make_float2((float)(sg * xv.x), (float)(sg * xv.y));
+            }
+        }
+        xs[e] = v;
+    }
+    __syncthreads();
+    const int K2 = K >> 1;
+    const float4* Z4 = reinterpret_cast<const float4*>(Zt + (size_t)b.type * K * K + (size_t)k0 * K);
+    for (int k2 = threadIdx.x; k2 < K2; k2 += blockDim.x) {
+        float2 a0[G], a1[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) a0[g] = a1[g] = make_float2(0.f, 0.f);
+        // register double buffer: the next block's loads are in flight while
+        // the current one is multiplied
+        float4 zb[2][kMm2Unroll];
+        auto load = [&](float4 (&z)[kMm2Unroll], int kb) {
+#pragma unroll
+            for (int u = 0; u < kMm2Unroll; ++u)
+                z[u] = kb + u < nk ? __ldg(Z4 + (size_t)(kb + u) * K2 + k2) : make_float4(0.f, 0.f, 0.f, 0.f);
+        };
+        auto mul = [&](const float4 (&z)[kMm2Unroll], int kb) {
+#pragma unroll
+            for (int u = 0; u < kMm2Unroll; u += 2) {
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    // x1 of columns kb+u, kb+u+1 (zero past nk, so no guard on the FMAs)
+                    const float4 xv = *reinterpret_cast<const float4*>(xs + g * chunk + kb + u);
+                    const float2 x0 = make_float2(xv.x, xv.y), x1 = make_float2(xv.z, xv.w);
+                    cfma(a0[g], make_float2(z[u].x, z[u].y), x0);
+                    cfma(a1[g], make_float2(z[u].z, z[u].w), x0);
+                    cfma(a0[g], make_float2(z[u + 1].x, z[u + 1].y), x1);
+                    cfma(a1[g], make_float2(z[u + 1].z, z[u + 1].w), x1);
+                }
+            }
+        };
+        load(zb[0], 0);
+        for (int kb = 0; kb < nk; kb += 2 * kMm2Unroll) {
+            if (kb + kMm2Unroll < nk) load(zb[1], kb + kMm2Unroll);
+            mul(zb[0], kb);
+            if (kb + kMm2Unroll >= nk) break;
+            if (kb + 2 * kMm2Unroll < nk) load(zb[0], kb + 2 * kMm2Unroll);
+            mul(zb[1], kb + kMm2Unroll);
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            if (g < b.count) {
+                float2* y = Ymm + ((size_t)s * M + type_cells[b.first + g]) * K + 2 * k2;
+                y[0] = a0[g];
+                y[1] = a1[g];
+            }
+    }
+}
+
 // ------------------------------------------------ K3 tail: U_o^T
 // y[r][u] = sum over local unknowns (m,k) of u: sign * y1[r][m][k]
 // (sums in the grid's precision; V2 is the output vector type)
@@ -885,6 +967,34 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
         nsplit = std::min(nsplit, kMmSplit);
     }
     if (mm_done) nsplit = 1;   // the tensor-core product wrote Ymm[0] whole
+    if constexpr (std::is_same<T2, float2>::value) {
+        if (!mm_done && R == 1 && (K & 1) == 0) {
+            // one rhs: the two-rows-per-thread kernel (K split to fill one wave)
+            int& occ2 = h->mm2_occ;
+            const int threads2 = std::min(320, ((K / 2 + 31) / 32) * 32);
+            const int nblk = h->n_mm_blocks;
+            if (!occ2) {
+                int b2 = 0;
+                EMS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, macromodel2_kernel<kMmGroup>, threads2,
+                                                                       (size_t)kMmGroup * ((K + 1) / 2) * sizeof(float2)));
+                occ2 = std::max(b2, 1);
+            }
+            int ns2 = std::max(1, std::min(kMmSplit, K / 64));
+            ns2 = std::max(1, std::min(ns2, h->num_sms * occ2 / std::max(1, nblk)));
+            int chunk2 = (K + ns2 - 1) / ns2;
+            // a multiple of the unroll: the paired x1 reads of a row stay inside it
+            chunk2 = (chunk2 + kMm2Unroll - 1) / kMm2Unroll * kMm2Unroll;
+            ns2 = (K + chunk2 - 1) / chunk2;
+            const size_t sm = (size_t)kMmGroup * chunk2 * sizeof(float2);
+            EMS_TRY(set_smem_once(macromodel2_kernel<kMmGroup>, sm));
+            macromodel2_kernel<kMmGroup><<<dim3(nblk, ns2), threads2, sm, st>>>(
+                op.Zt, x, h->d_uo_index, h->d_uo_sign, h->d_type_cells,
+                reinterpret_cast<const MmBlock*>(h->d_mm_blocks), op.Ymm, K, h->M, h->n_unique, chunk2, xf);
+            EMS_CUDA(cudaGetLastError());
+            nsplit = ns2;
+            mm_done = true;
+        }
+    }
     if (!mm_done) {
         const int nblk = h->n_mm_blocks;
         const int chunk = (K + nsplit - 1) / nsplit;
