@@ -512,9 +512,10 @@ def main():
     achieved = alg_bin / (bin_avg * 1e-3) / 1e9
     traffic = (PAIR_DRAM_BYTES_PER_STORED_BIN * stored if half
                else BINMUL_DRAM_BYTES_PER_BIN * P if BINMUL_DRAM_BYTES_PER_BIN else None)
-    # preconditioner apply: FP32 LU factors once, r gathered, owned rows written
+    # preconditioner apply: FP16 owned inverse rows (4 bytes per entry, one FP32
+    # scale per row) once, r gathered, owned rows written
     pc_avg = pc_ms / max(pc_n, 1)
-    alg_pc = pc_elems * 8 + R * (pc_subtot * 16 + pc_subtot * 8 + nu * 16)
+    alg_pc = pc_elems * 4 + nu * 4 + R * (pc_subtot * 16 + pc_subtot * 8 + nu * 16)
     pc_achieved = alg_pc / (pc_avg * 1e-3) / 1e9 if pc_n else None
     last = infos[-1]
     out = {

@@ -158,14 +158,17 @@ EMSURF_API int emsurf_solve(emsurf_handle* h, const emsurf_c128* b, emsurf_c128*
 /* y = M^{-1} r with the handle's near-field preconditioner (restricted
  * additive Schwarz over cells, the grouping of Eq. final_precond's near
  * field used here): y = sum_m Rt_m^T A_m^{-1} R_m r, A_m the exact block of
- * Eq. final on subdomain m, factored in complex FP32.  r, y: device
+ * Eq. final on subdomain m, factored in complex FP32; its owned rows of
+ * A_m^{-1} are applied from FP16 copies scaled per row (relative error per
+ * entry <= 2^-11), or as BF16x3 tensor-core GEMMs for >= 8 rhs.  r, y: device
  * [nrhs][n_unique] complex128, must not overlap; nrhs <= max_rhs.
  * Errors: EINVAL (no preconditioner built, bad nrhs or pointers).        */
 EMSURF_API int emsurf_precond_apply(emsurf_handle* h, const emsurf_c128* r, emsurf_c128* y,
                                     int32_t nrhs, void* stream);
 
-/* Sizes of the near-field preconditioner: sum over cells of n_m^2 (complex
- * FP32 factor entries), sum of n_m, and the largest n_m; all 0 if none.   */
+/* Sizes of the near-field preconditioner: stored entries of the owned rows
+ * of the subdomain inverses (complex FP16 pairs, 4 bytes each, plus one FP32
+ * scale per row), sum of n_m, and the largest n_m; all 0 if none.        */
 EMSURF_API int emsurf_precond_info(const emsurf_handle* h, int64_t* factor_entries,
                                    int64_t* subdomain_total, int32_t* max_subdomain);
 

@@ -197,7 +197,9 @@ struct emsurf_handle {
     int64_t pc_elems = 0;           // sum over cells of own_m * ld_m (stored entries)
     int64_t pc_sub_total = 0;       // sum over cells of n_m
     int pc_own_max = 0;
-    float2* pc_mat = nullptr;       // owned rows of A_m^{-1}: per cell own_m x ld_m, row-major
+    float2* pc_mat = nullptr;       // owned rows of A_m^{-1} in FP32 (create time only): own_m x ld_m per cell
+    void* pc_mat16 = nullptr;       // the same rows as FP16 (re, im) pairs, scaled per row
+    float* pc_rscale = nullptr;     // [n_unique] scale of each owned row
     int64_t* pc_off = nullptr;      // [M] element offset of each cell's rows
     int32_t* pc_ld = nullptr;       // [M] row length (n_m rounded up to even)
     int32_t* pc_own_ptr = nullptr;  // [M+1] first owned row of each cell in the row list

@@ -18,6 +18,11 @@
 // formed from the factors at create time and the application is a batched
 // matrix-vector product over own_m x n_m entries (about half of n_m^2, and
 // without the serial steps of a triangular solve); the factors are freed.
+// The rows are kept in FP16 with one FP32 scale per row (the preconditioner
+// only steers the flexible GMRES, whose accuracy comes from the operator):
+// half the bytes of complex64 per application.
+#include <cuda_fp16.h>
+
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -272,6 +277,34 @@ pc_invrows_kernel(const float2* __restrict__ lu, const int64_t* __restrict__ luo
     }
 }
 
+// FP16 copy of the owned inverse rows for the apply: one warp per owned row
+// g, scale = (largest |component| of the row) / 2^14, so every entry keeps
+// FP16's 11-bit significand unless it is below ~6e-5 of the row maximum
+// (then its absolute error is below 2^-24 of that maximum).
+__global__ void pc_to_half_kernel(const float2* __restrict__ X, const int64_t* __restrict__ xoff,
+                                  const int32_t* __restrict__ ldx, const int32_t* __restrict__ own_ptr, int M,
+                                  int n_rows, __half2* __restrict__ H, float* __restrict__ rscale) {
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < n_rows; g += warps) {
+        int lo = 0, hi = M;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (own_ptr[mid] <= g) lo = mid; else hi = mid;
+        }
+        const int m = lo, i = g - own_ptr[m], ld = ldx[m];
+        const float2* row = X + xoff[m] + (size_t)i * ld;
+        float mx = 0.f;
+        for (int c = lane; c < ld; c += 32) mx = fmaxf(mx, fmaxf(fabsf(row[c].x), fabsf(row[c].y)));
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const float sc = mx > 0.f ? mx / 16384.f : 1.f;
+        const float inv = 1.f / sc;
+        __half2* out = H + xoff[m] + (size_t)i * ld;
+        for (int c = lane; c < ld; c += 32) out[c] = __floats2half2_rn(row[c].x * inv, row[c].y * inv);
+        if (lane == 0) rscale[g] = sc;
+    }
+}
+
 // rs[q][j] = r[q][sub_ids[j]] in FP32 for every subdomain entry j (all cells
 // back to back, each cell's segment starting at an even index).
 template <typename VT>
@@ -300,7 +333,7 @@ __global__ void pc_gather_kernel(const VT* __restrict__ r, const int32_t* __rest
 // in one wave.
 template <int RQ, typename VO>
 __global__ void __launch_bounds__(kApThreads, RQ >= 2 ? 2 : 4)
-pc_apply_kernel(const float2* __restrict__ X, const int64_t* __restrict__ xoff,
+pc_apply_kernel(const __half2* __restrict__ X, const float* __restrict__ rscale, const int64_t* __restrict__ xoff,
                 const int32_t* __restrict__ ldx, const int32_t* __restrict__ own_ptr,
                 const int32_t* __restrict__ sub_ptr, const int32_t* __restrict__ sub_ids,
                 const int64_t* __restrict__ rs_off, const float2* __restrict__ rs, int64_t rs_stride,
@@ -318,27 +351,42 @@ pc_apply_kernel(const float2* __restrict__ X, const int64_t* __restrict__ xoff,
             if (own_ptr[mid] <= g) lo = mid; else hi = mid;
         }
         const int m = lo;
-        const int i = g - own_ptr[m], ld = ldx[m], half = ld >> 1;
-        const float4* row = reinterpret_cast<const float4*>(X + xoff[m] + (size_t)i * ld);
+        const int i = g - own_ptr[m], ld = ldx[m], quarter = ld >> 2;
+        const uint4* row = reinterpret_cast<const uint4*>(X + xoff[m] + (size_t)i * ld);   // 4 complex each
         const float4* rv4 = reinterpret_cast<const float4*>(rs + rs_off[m]);
         float2 acc[RQ];
 #pragma unroll
         for (int q = 0; q < RQ; ++q) acc[q] = make_float2(0.f, 0.f);
-        for (int c0 = lane; c0 < half; c0 += 32 * kApUnroll) {
-            float4 xv[kApUnroll];
+        for (int c0 = lane; c0 < quarter; c0 += 32 * kApUnroll) {
+            uint4 xv[kApUnroll];
 #pragma unroll
             for (int u = 0; u < kApUnroll; ++u)
-                xv[u] = c0 + 32 * u < half ? __ldg(row + c0 + 32 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
+                xv[u] = c0 + 32 * u < quarter ? __ldg(row + c0 + 32 * u) : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
             for (int u = 0; u < kApUnroll; ++u) {
-                const int c2 = min(c0 + 32 * u, half - 1);
+                const int c4 = min(c0 + 32 * u, quarter - 1);
+                const float2 f0 = __half22float2(*reinterpret_cast<const __half2*>(&xv[u].x));
+                const float2 f1 = __half22float2(*reinterpret_cast<const __half2*>(&xv[u].y));
+                const float2 f2 = __half22float2(*reinterpret_cast<const __half2*>(&xv[u].z));
+                const float2 f3 = __half22float2(*reinterpret_cast<const __half2*>(&xv[u].w));
 #pragma unroll
                 for (int q = 0; q < RQ; ++q) {
                     if (RQ > 2 && q >= nr) break;   // rhs past the live count (wide kernels only)
-                    const float4 rv = __ldg(rv4 + q * (rs_stride >> 1) + c2);
-                    acc[q].x += xv[u].x * rv.x - xv[u].y * rv.y + xv[u].z * rv.z - xv[u].w * rv.w;
-                    acc[q].y += xv[u].x * rv.y + xv[u].y * rv.x + xv[u].z * rv.w + xv[u].w * rv.z;
+                    const float4 ra = __ldg(rv4 + q * (rs_stride >> 1) + 2 * c4);
+                    const float4 rb = __ldg(rv4 + q * (rs_stride >> 1) + 2 * c4 + 1);
+                    acc[q].x += f0.x * ra.x - f0.y * ra.y + f1.x * ra.z - f1.y * ra.w +
+                                f2.x * rb.x - f2.y * rb.y + f3.x * rb.z - f3.y * rb.w;
+                    acc[q].y += f0.x * ra.y + f0.y * ra.x + f1.x * ra.w + f1.y * ra.z +
+                                f2.x * rb.y + f2.y * rb.x + f3.x * rb.w + f3.y * rb.z;
                 }
+            }
+        }
+        {
+            const float sc = rscale[g];
+#pragma unroll
+            for (int q = 0; q < RQ; ++q) {
+                acc[q].x *= sc;
+                acc[q].y *= sc;
             }
         }
 #pragma unroll
@@ -372,7 +420,8 @@ int launch_apply(emsurf_handle* h, VO* y, int r0, int nr, cudaStream_t st) {
         o = std::max(b, 1);
     }
     const int blocks = h->num_sms * o;
-    pc_apply_kernel<RQ, VO><<<blocks, kApThreads, 0, st>>>(h->pc_mat, h->pc_off, h->pc_ld, h->pc_own_ptr,
+    pc_apply_kernel<RQ, VO><<<blocks, kApThreads, 0, st>>>(reinterpret_cast<const __half2*>(h->pc_mat16), h->pc_rscale,
+                                                        h->pc_off, h->pc_ld, h->pc_own_ptr,
                                                         h->pc_sub_ptr, h->pc_sub_ids, h->pc_rs_off,
                                                         h->pc_rs + (size_t)r0 * h->pc_rs_stride,
                                                         h->pc_rs_stride, y, h->n_unique, h->M, h->n_unique, r0, nr);
@@ -481,7 +530,7 @@ int pc_build(emsurf_handle* h, const emsurf_problem* p) {
     std::vector<int32_t> ldv(M);
     for (int m = 0; m < M; ++m) {
         moff[m + 1] = moff[m] + (int64_t)nsz[m] * nsz[m];
-        ldv[m] = (nsz[m] + 1) & ~1;
+        ldv[m] = (nsz[m] + 3) & ~3;     // 4 complex per 16-byte load of the FP16 rows
         xoff[m + 1] = xoff[m] + (int64_t)own[m] * ldv[m];
         h->pc_own_max = std::max(h->pc_own_max, own[m]);
     }
@@ -519,7 +568,8 @@ int pc_build(emsurf_handle* h, const emsurf_problem* p) {
         EMS_TRY(dev_alloc(h, (void**)&h->pc_rs, (size_t)h->max_rhs * rsoff[M] * sizeof(float2)));
         EMS_CUDA(cudaMemsetAsync(h->pc_rs, 0, (size_t)h->max_rhs * rsoff[M] * sizeof(float2), st));
     }
-    EMS_TRY(dev_alloc(h, (void**)&h->pc_mat, (size_t)xoff[M] * sizeof(float2)));
+    // FP32 inverse rows: a create-time temporary (the apply keeps FP16 rows)
+    EMS_CUDA(cudaMalloc(&h->pc_mat, (size_t)xoff[M] * sizeof(float2)));
     EMS_CUDA(cudaMemsetAsync(h->pc_mat, 0, (size_t)xoff[M] * sizeof(float2), st));   // row padding
     int64_t* d_luoff = nullptr;
     int32_t* d_perm = nullptr;
@@ -594,15 +644,29 @@ int pc_build(emsurf_handle* h, const emsurf_problem* p) {
     if (own_zt) cudaFree(Zt);
     for (int m = 0; m < M; ++m)
         if (hs[m]) {
+            cudaFree(h->pc_mat);
+            h->pc_mat = nullptr;
             set_error("preconditioner block of cell %d is singular", m);
             return EMSURF_EINVAL;
         }
     h->pc_elems = xoff[M];
     h->pc_sub_total = (int64_t)sids.size();
+    // FP16 rows with a per-row scale for the apply
+    EMS_TRY(dev_alloc(h, &h->pc_mat16, (size_t)xoff[M] * 4));
+    EMS_TRY(dev_alloc(h, (void**)&h->pc_rscale, (size_t)h->n_unique * sizeof(float)));
+    pc_to_half_kernel<<<h->num_sms * 16, 256, 0, st>>>(h->pc_mat, h->pc_off, h->pc_ld, h->pc_own_ptr, M,
+                                                       h->n_unique, reinterpret_cast<__half2*>(h->pc_mat16),
+                                                       h->pc_rscale);
+    EMS_CUDA(cudaGetLastError());
+    h->launches += 1;
     h->have_pc = true;
     // many rhs: the apply as tensor-core GEMMs (with the handle's tensor-core option)
-    if (h->have_tc && h->max_rhs >= kTcMinRhs) EMS_TRY(pc_tc_build(h, own_ptr_host));
-    return EMSURF_OK;
+    int st_tc = EMSURF_OK;
+    if (h->have_tc && h->max_rhs >= kTcMinRhs) st_tc = pc_tc_build(h, own_ptr_host);
+    EMS_CUDA(cudaStreamSynchronize(st));
+    cudaFree(h->pc_mat);
+    h->pc_mat = nullptr;
+    return st_tc;
 }
 
 }  // namespace emsurf
