@@ -419,7 +419,8 @@ def main():
     mv64 = time_matvec(B, torch, h, nu, R, B.FP64)
     px, py, dev_bytes = B.emsurf_query(h)
     P = px * py
-    bytes32 = 2 * w.E * w.E * B.emsurf_operator_info(h)[0] * 8 + w.n_types * w.K * w.K * 8 + 2 * R * nu * 16
+    stored, _ = B.emsurf_operator_info(h)        # FP32 spectrum bins held (half with reciprocal tables)
+    bytes32 = 2 * w.E * w.E * stored * 8 + w.n_types * w.K * w.K * 8 + 2 * R * nu * 16
     bytes64 = 2 * w.E * w.E * P * 16 + w.n_types * w.K * w.K * 16 + 2 * R * nu * 16
     solve_kw = dict(rtol=RTOL, restart=RESTART, max_iters=20000, max_refine=20,
                     solver=B.SOLVER_MIXED)
@@ -504,7 +505,6 @@ def main():
             dist.destroy_process_group()
         return
     bin_avg = bin_ms / max(bin_n, 1)
-    stored, _ = B.emsurf_operator_info(h)
     half = stored < P
     # algorithmic bytes of the kernel that ran: the stored spectrum bins once,
     # X^ read and Y^ written for every bin
