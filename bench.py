@@ -429,7 +429,9 @@ def main():
     # ------------------------------------------------------------ timed region
     clocks = ClockSampler(local)
     clocks.start()
-    B.emsurf_profile(h, True)
+    # only the dominant kernel is timed live (two events per product): the
+    # full phase breakdown comes from a separate profiled solve below
+    B.emsurf_profile_phases(h, ["binmul32"])
     launches0 = B.emsurf_launch_count(h)
     if dist:
         dist.barrier()
@@ -448,6 +450,14 @@ def main():
     launches = B.emsurf_launch_count(h) - launches0
     B.emsurf_profile(h, False)
     clk = clocks.stop()
+    bin_ms, bin_n = B.emsurf_profile_read(h, "binmul32")
+    bin_ms_timed, bin_n_timed = bin_ms, bin_n
+    # phase breakdown: one more solve (outside the timed region) with every
+    # phase recorded; per-solve figures below are from this run
+    B.emsurf_profile(h, True)
+    B.emsurf_solve(h, V, X, **solve_kw)
+    torch.cuda.synchronize()
+    B.emsurf_profile(h, False)
     bin_ms, bin_n = B.emsurf_profile_read(h, "binmul32")
     mm_ms, mm_n = B.emsurf_profile_read(h, "mm32")
     fft_ms, fft_n = B.emsurf_profile_read(h, "fft32")
@@ -504,7 +514,7 @@ def main():
         if dist:
             dist.destroy_process_group()
         return
-    bin_avg = bin_ms / max(bin_n, 1)
+    bin_avg = bin_ms_timed / max(bin_n_timed, 1)     # live over the timed region
     half = stored < P
     # algorithmic bytes of the kernel that ran: the stored spectrum bins once,
     # X^ read and Y^ written for every bin
@@ -558,15 +568,16 @@ def main():
                      "frac": round(achieved / hbm, 4), "peak_kind": peak_kind,
                      "traffic": round(traffic) if traffic else None,
                      "alg_bytes_per_launch": alg_bin,
-                     "avg_launch_ms": round(bin_avg, 5), "launches_timed": bin_n},
-        "phases_ms_per_solve": {"binmul32": round(bin_ms / args.steps, 3),
-                                "macromodel32": round(mm_ms / args.steps, 3),
-                                "fft32": round(fft_ms / args.steps, 3),
-                                "binmul64": round(bin64_ms / args.steps, 3),
-                                "fft64+mm64": round((fft64_ms + mm64_ms) / args.steps, 3),
-                                "arnoldi": round(arn_ms / args.steps, 3),
-                                "scatter": round(sct_ms / args.steps, 3),
-                                "precond": round(pc_ms / args.steps, 3)},
+                     "avg_launch_ms": round(bin_avg, 5), "launches_timed": bin_n_timed},
+        "phases_ms_per_solve": {"binmul32": round(bin_ms, 3),
+                                "macromodel32": round(mm_ms, 3),
+                                "fft32": round(fft_ms, 3),
+                                "binmul64": round(bin64_ms, 3),
+                                "fft64+mm64": round(fft64_ms + mm64_ms, 3),
+                                "arnoldi": round(arn_ms, 3),
+                                "scatter": round(sct_ms, 3),
+                                "precond": round(pc_ms, 3),
+                                "note": "one extra profiled solve outside the timed region (events add host work)"},
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": int(V.numel() * 16),
                 "d2h_bytes_per_step": int(V.numel() * 16)},

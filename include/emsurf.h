@@ -195,6 +195,10 @@ EMSURF_API void emsurf_destroy(emsurf_handle* h);
  * preconditioner applications of emsurf_solve.  emsurf_profile_read synchronises on the recorded events
  * and returns the summed milliseconds and the number of intervals.       */
 EMSURF_API int emsurf_profile(emsurf_handle* h, int32_t enable);
+/* As emsurf_profile(h, 1) but recording only the phases whose bit is set in
+ * phase_mask (bit i = phase i; 0 stops): fewer events on the stream when
+ * one kernel is timed inside a longer run.                                */
+EMSURF_API int emsurf_profile_phases(emsurf_handle* h, uint32_t phase_mask);
 EMSURF_API int emsurf_profile_read(emsurf_handle* h, int32_t phase, double* total_ms,
                                    int64_t* count);
 

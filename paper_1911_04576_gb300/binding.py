@@ -89,6 +89,7 @@ def lib():
                                               vp, i32, vp]
         d = C.c_double
         L.emsurf_profile.argtypes = [vp, i32]
+        L.emsurf_profile_phases.argtypes = [vp, C.c_uint32]
         L.emsurf_profile_read.argtypes = [vp, i32, C.POINTER(d), C.POINTER(C.c_int64)]
         L.emsurf_launch_count.argtypes = [vp, C.POINTER(C.c_int64)]
         L.emsurf_check.argtypes = [vp]
@@ -355,6 +356,14 @@ PHASES = {"binmul32": 0, "binmul64": 1, "mm32": 2, "mm64": 3, "fft32": 4, "fft64
 
 def emsurf_profile(h, enable):
     _check(lib().emsurf_profile(h.ptr, 1 if enable else 0))
+
+
+def emsurf_profile_phases(h, phases):
+    """emsurf_profile_phases: record only the named phases (empty: stop)."""
+    mask = 0
+    for p in phases:
+        mask |= 1 << PHASES[p]
+    _check(lib().emsurf_profile_phases(h.ptr, mask))
 
 
 def emsurf_profile_read(h, phase):

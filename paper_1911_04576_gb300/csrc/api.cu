@@ -227,7 +227,7 @@ void free_handle(emsurf_handle* h) {
 }  // namespace
 
 void prof_mark(emsurf_handle* h, int phase, bool begin, cudaStream_t st) {
-    if (!h->prof_on) return;
+    if (!h->prof_on || !((h->prof_mask >> phase) & 1u)) return;
     PhaseTimer& pt = h->prof[phase];
     // a begin takes a fresh pair; an end closes the pair opened last
     if (begin) {
@@ -383,6 +383,15 @@ EMSURF_API int emsurf_profile(emsurf_handle* h, int32_t enable) {
     if (!h) { set_error("NULL handle"); return EMSURF_EINVAL; }
     if (enable) for (auto& pt : h->prof) pt.used = 0;
     h->prof_on = enable != 0;
+    h->prof_mask = 0xffffffffu;
+    return EMSURF_OK;
+}
+
+EMSURF_API int emsurf_profile_phases(emsurf_handle* h, uint32_t phase_mask) {
+    if (!h) { set_error("NULL handle"); return EMSURF_EINVAL; }
+    for (auto& pt : h->prof) pt.used = 0;
+    h->prof_on = phase_mask != 0;
+    h->prof_mask = phase_mask;
     return EMSURF_OK;
 }
 

@@ -226,6 +226,7 @@ struct emsurf_handle {
     // tracing: kernel launches issued by this handle, optional phase timers
     int64_t launches = 0;
     bool prof_on = false;
+    uint32_t prof_mask = 0xffffffffu;      // phases recorded while prof_on
     PhaseTimer prof[EMS_NPHASE];
     std::vector<void*> allocations;
 };
