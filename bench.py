@@ -47,7 +47,7 @@ PC_OVERLAP = 0.6               # preconditioner margin, in mesh cells (a / n)
 BINMUL_DRAM_BYTES_PER_BIN = (767108096 + 5353216) / 576
 # the same for binmul_tma_pair_kernel (half spectrum) per stored bin, from
 # profiles/binmul_tma_pair_lattice12x12_k576.md (290 stored bins)
-PAIR_DRAM_BYTES_PER_STORED_BIN = (387570432 + 4896000) / 290
+PAIR_DRAM_BYTES_PER_STORED_BIN = (389593600 + 5169408) / 290
 
 
 FALLBACK_BF16_TFLOPS = 1900.0
@@ -520,8 +520,8 @@ def main():
     # X^ read and Y^ written for every bin
     alg_bin = 2 * w.E * w.E * stored * 8 + 2 * R * w.K * P * 8
     achieved = alg_bin / (bin_avg * 1e-3) / 1e9
-    traffic = (PAIR_DRAM_BYTES_PER_STORED_BIN * stored if half
-               else BINMUL_DRAM_BYTES_PER_BIN * P if BINMUL_DRAM_BYTES_PER_BIN else None)
+    per_unit = PAIR_DRAM_BYTES_PER_STORED_BIN if half else BINMUL_DRAM_BYTES_PER_BIN
+    traffic = per_unit * (stored if half else P) if per_unit else None
     # preconditioner apply: FP16 owned inverse rows (4 bytes per entry, one FP32
     # scale per row) once, r gathered, owned rows written
     pc_avg = pc_ms / max(pc_n, 1)

@@ -246,6 +246,15 @@ void prof_mark(emsurf_handle* h, int phase, bool begin, cudaStream_t st) {
 
 void gmres_release(emsurf_handle* h);
 
+// Clears the bounded-wait error flag and the state an aborted launch may
+// have left behind (the pair kernel's arrival counters).
+int clear_wait_error(emsurf_handle* h) {
+    EMS_CUDA(cudaDeviceSynchronize());
+    EMS_CUDA(cudaMemset(h->d_err, 0, sizeof(int)));
+    if (h->d_pair_cnt) EMS_CUDA(cudaMemset(h->d_pair_cnt, 0, h->pair_cnt_bytes));
+    return EMSURF_OK;
+}
+
 }  // namespace emsurf
 
 using namespace emsurf;
@@ -419,7 +428,7 @@ EMSURF_API int emsurf_check(emsurf_handle* h) {
     int flag = 0;
     EMS_CUDA(cudaMemcpy(&flag, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (flag) {
-        EMS_CUDA(cudaMemset(h->d_err, 0, sizeof(int)));
+        EMS_TRY(clear_wait_error(h));
         set_error("a bounded device wait expired (flag %d); results of the affected calls are invalid", flag);
         return EMSURF_ETIMEDOUT;
     }

@@ -172,6 +172,10 @@ struct emsurf_handle {
     int nst = 0;
     int32_t* d_st_bin = nullptr;
     int32_t* d_st_part = nullptr;
+    int pair_grid = 0;                // CTAs of the pair kernel (equal slab ranges)
+    float2* d_pair_part = nullptr;    // partial row sums of straddling bins [cta][2][2E]
+    int* d_pair_cnt = nullptr;        // arrival counters [stored bin][row warp]
+    size_t pair_cnt_bytes = 0;
     // BF16x3 split planes of the FP32 operator for the tensor-core bin multiply
     bool have_tc = false;
     void* tc_Bh = nullptr;          // spectrum hi/lo [bin][op][2i+c][ej] bf16
@@ -251,6 +255,7 @@ int tabulate_blocks(const MeshView& test, const MeshView& src, const double* shi
 template <typename T2>
 int build_operator(emsurf_handle* h, Operator<T2>& op, const emsurf_problem* pr);
 int derive_fp32_operator(emsurf_handle* h, const emsurf_problem* pr);
+int clear_wait_error(emsurf_handle* h);
 template <typename T2>
 int apply_operator(emsurf_handle* h, Operator<T2>& op, const double2* x, double2* y, int nrhs,
                    cudaStream_t st);

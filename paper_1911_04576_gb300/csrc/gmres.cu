@@ -838,7 +838,7 @@ int gmres_solve(emsurf_handle* h, const double2* b, double2* x, int R, const ems
         int flag = 0;
         EMS_CUDA(cudaMemcpy(&flag, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
         if (flag) {
-            EMS_CUDA(cudaMemset(h->d_err, 0, sizeof(int)));
+            EMS_TRY(clear_wait_error(h));
             set_error("a bounded device wait expired during the solve");
             return EMSURF_ETIMEDOUT;
         }

@@ -80,8 +80,9 @@ __global__ void round_kernel(float2* __restrict__ dst, const double2* __restrict
 }
 
 // Reciprocity of the spectrum: with L(-d) = L(d)^T and K(-d) = K(d)^T the
-// blocks of bins k and -k are transposes, B^(-k) = B^(k)^T.  out[0] = max
-// |B^(-k)[i][j] - B^(k)[j][i]|, out[1] = max |B^| (as ordered bit patterns
+// blocks of bins k and -k are transposes, L^(-k) = L^(k)^T and
+// K^(-k) = K^(k)^T.  out[0] = max over both operators of
+// |O^(-k)[i][j] - O^(k)[j][i]|, out[1] = max |O^| (as ordered bit patterns
 // of non-negative doubles).
 __global__ void reciprocity_kernel(const double2* __restrict__ B, const int32_t* __restrict__ partner,
                                    int E, size_t nbins, unsigned long long* __restrict__ out) {
@@ -178,7 +179,6 @@ __global__ void binmul_kernel(const T2* __restrict__ Bhat, const T2* __restrict_
 // the producer waits (bounded) for its copies in flight, and all return.
 constexpr int kBmJB = 8;
 constexpr int kBmStages = 4;
-constexpr int kPairStages = 5;    // the half-spectrum kernel's ring (its x buffers are larger)
 constexpr long long kWaitLimit = 1LL << 22;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -329,186 +329,245 @@ size_t binmul_tma_smem(int E) {
 }
 
 // ------------------------------------------------ K2, FP32, one rhs, half spectrum
-// With reciprocal tables only one bin k of each pair (k, -k) is stored and
-// its blocks serve both: y(k) = B^(k) x(k) (one thread per test row, as in
-// binmul_tma_kernel) and y(-k) = B^(k)^T x(-k), i.e. for each source column
-// j of a slab, y_J(-k)[j] = a sum_i L[i][j] x_J(-k)[i] + b sum_i K[i][j]
-// x_M(-k)[i] (and y_M likewise).  The second product has its own kBmJB
-// warps (one column of the slab each, a warp reduction per output), so both
-// run concurrently on every stage.  Each stored slab is read from HBM once
-// for both bins.  Self-paired bins (k = -k) take only the first product.
-__global__ void binmul_tma_pair_kernel(const float2* __restrict__ Bhat, const float2* __restrict__ Xh,
+// With reciprocal tables L^(-k) = L^(k)^T and K^(-k) = K^(k)^T, so only one
+// bin k of each pair (k, -k) is stored and its blocks serve both:
+// y(k) = B^(k) x(k) (one thread per test row, as in binmul_tma_kernel) and
+// y_J(-k)[j] = a sum_i L[j][i] x_J(-k)[i] + b sum_i K[j][i] x_M(-k)[i]
+// (y_M(-k) likewise with g, d), dot products along the contiguous test index
+// of the slab's columns, computed by kPairColWarps further warps (two
+// columns per warp, a warp reduction per slab).  Each stored slab is read
+// from HBM once for both bins.  Self-paired bins (k = -k) take only the
+// first product.
+//
+// Work split: the Q = nst * nj slabs (stored bins in order, nj slabs each)
+// are cut into gridDim.x contiguous ranges whose lengths differ by at most
+// one, so every CTA streams the same number of bytes and a bin may straddle
+// CTAs.  A y(-k) output is complete within its slab.  The y(k) row sums of a
+// bin that is not whole in one CTA are written per row warp as partials,
+// part[cta][slot][2E] (slot 0: the range's first bin, 1: its last), and the
+// warp whose arrival completes that (bin, warp) counter adds the partials
+// of all contributing CTAs in CTA order (a deterministic sum), writes Y^ and
+// resets the counter for the next launch.  No wait depends on another CTA.
+constexpr int kPairStages = 3;     // ring depth
+constexpr int kPairJB = 12;         // slab width (source columns per stage)
+constexpr int kPairColWarps = 6;    // y(-k) warps
+constexpr int kPairCpw = kPairJB / kPairColWarps;   // slab columns per y(-k) warp
+constexpr int kPairNv = 8 * kPairCpw;               // floats reduced per lane and slab
+constexpr int kPairUnroll = 5;      // row pairs per lane in flight in a y(-k) warp
+constexpr int kPairMaxThreads = 576;
+static_assert(kPairCpw * kPairColWarps == kPairJB && (kPairCpw == 1 || kPairCpw == 2),
+              "one or two slab columns per y(-k) warp");
+
+// the CTA whose slab range holds slab q (ranges [b Q / G, (b + 1) Q / G))
+__device__ __forceinline__ int pair_cta_of(long long q, long long Q, int G) {
+    return (int)(((q + 1) * G - 1) / Q);
+}
+
+__global__ void __launch_bounds__(kPairMaxThreads, 1) binmul_tma_pair_kernel(const float2* __restrict__ Bhat, const float2* __restrict__ Xh,
                                        float2* __restrict__ Yh, const int32_t* __restrict__ st_bin,
                                        const int32_t* __restrict__ st_part, int E, int nst, float2 ca,
-                                       float2 cb, float2 cg, float2 cd, int* __restrict__ err) {
+                                       float2 cb, float2 cg, float2 cd, float2* __restrict__ part,
+                                       int* __restrict__ cnt, int* __restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int stage_elems = 2 * kBmJB * E;
+    const int stage_elems = 2 * kPairJB * E;
     float2* sbuf = reinterpret_cast<float2*>(smem_raw);
     float2* xbuf = sbuf + (size_t)kPairStages * stage_elems;      // [2 buffers][x(k), x(-k)][2E]
     uint64_t* full = reinterpret_cast<uint64_t*>(xbuf + 8 * E);
     uint64_t* empty = full + kPairStages;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ncw = (E + 31) / 32;        // warps 1..ncw: y(k); the next kBmJB warps: y(-k)
+    const int ncw = (E + 31) / 32;        // warps 1..ncw: y(k); the next kPairColWarps warps: y(-k)
     if (threadIdx.x == 0) {
         for (int s = 0; s < kPairStages; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], ncw + kBmJB);
+            mbar_init(&empty[s], ncw + kPairColWarps);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
-    const int nloc = (nst - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
-    const int nj = (E + kBmJB - 1) / kBmJB;
-    const long long total = (long long)nloc * nj;
+    const int nj = (E + kPairJB - 1) / kPairJB;
+    const int G = (int)gridDim.x;
+    const long long Q = (long long)nst * nj;
+    const long long q0 = (long long)blockIdx.x * Q / G, q1 = (long long)(blockIdx.x + 1) * Q / G;
+    if (q0 >= q1) return;
+    // position of the range's first slab; every role advances (s, ph, sb, jb,
+    // t) by one slab per step (t counts the bins met, for the x double buffer)
+    const int sb0 = (int)(q0 / nj), jb0 = (int)(q0 % nj);
     if (warp == 0) {
         if (lane != 0) return;
+        const uint32_t bytes_x = (uint32_t)(2 * E * sizeof(float2));
+        int s = 0, sb = sb0, jb = jb0, t = 0;
+        uint32_t ph = 0;
         long long issued = 0;
         bool ok = true;
-        for (long long q = 0; q < total; ++q) {
-            const int s = (int)(q % kPairStages);
-            if (q >= kPairStages && !mbar_wait(&empty[s], (uint32_t)((q / kPairStages - 1) & 1))) {
+        for (long long q = q0; q < q1; ++q) {
+            if (q - q0 >= kPairStages && !mbar_wait(&empty[s], ph ^ 1u)) {
                 ok = false;
                 break;
             }
-            const int t = (int)(q / nj), jb = (int)(q % nj);
-            const int sb = (int)blockIdx.x + t * (int)gridDim.x;
-            const int bin = st_bin[sb], part = st_part[sb];
-            const int j0 = jb * kBmJB, jn = min(kBmJB, E - j0);
+            const int j0 = jb * kPairJB, jn = min(kPairJB, E - j0);
             const uint32_t bytes_op = (uint32_t)(jn * E * sizeof(float2));
-            const uint32_t bytes_x = (uint32_t)(2 * E * sizeof(float2));
-            const uint32_t xb = jb == 0 ? (part != bin ? 2 * bytes_x : bytes_x) : 0u;
+            const bool newbin = jb == 0 || q == q0;
+            int bin = 0, prt = 0;
+            if (newbin) {
+                bin = st_bin[sb];
+                prt = st_part[sb];
+            }
+            const uint32_t xb = newbin ? (prt != bin ? 2 * bytes_x : bytes_x) : 0u;
             mbar_expect_tx(&full[s], 2 * bytes_op + xb);
             const float2* src = Bhat + (size_t)sb * 2 * E * E + (size_t)j0 * E;
             float2* dst = sbuf + (size_t)s * stage_elems;
             bulk_g2s(dst, src, bytes_op, &full[s]);
-            bulk_g2s(dst + kBmJB * E, src + (size_t)E * E, bytes_op, &full[s]);
-            if (jb == 0) {
+            bulk_g2s(dst + kPairJB * E, src + (size_t)E * E, bytes_op, &full[s]);
+            if (newbin) {
                 float2* xd = xbuf + (t & 1) * 4 * E;
                 bulk_g2s(xd, Xh + (size_t)bin * 2 * E, bytes_x, &full[s]);
-                if (part != bin) bulk_g2s(xd + 2 * E, Xh + (size_t)part * 2 * E, bytes_x, &full[s]);
+                if (prt != bin) bulk_g2s(xd + 2 * E, Xh + (size_t)prt * 2 * E, bytes_x, &full[s]);
             }
-            issued = q + 1;
+            issued = q - q0 + 1;
+            if (++s == kPairStages) { s = 0; ph ^= 1u; }
+            if (++jb == nj) { jb = 0; ++sb; ++t; }
         }
         if (!ok) {
             atomicExch(err, 1);
-            for (long long q = (issued > kPairStages ? issued - kPairStages : 0); q < issued; ++q)
-                mbar_wait(&full[q % kPairStages], (uint32_t)((q / kPairStages) & 1));
+            for (long long u = (issued > kPairStages ? issued - kPairStages : 0); u < issued; ++u)
+                mbar_wait(&full[u % kPairStages], (uint32_t)((u / kPairStages) & 1));
         }
         return;
     }
     if (warp > ncw) {
-        // ---- y(-k) = B^(k)^T x(-k): this warp's column of every slab
-        const int jj = warp - ncw - 1;
-        for (long long q = 0; q < total; ++q) {
-            const int s = (int)(q % kPairStages);
-            const int t = (int)(q / nj), jb = (int)(q % nj);
-            if (!mbar_wait(&full[s], (uint32_t)((q / kPairStages) & 1))) {
+        // ---- y(-k): columns cw + u kPairColWarps (u < kPairCpw) of every
+        // slab, rows in pairs over the lanes
+        const int cw = warp - ncw - 1;
+        int s = 0, sb = sb0, jb = jb0, t = 0;
+        uint32_t ph = 0;
+        int bin = st_bin[sb], prt = st_part[sb];
+        // after the reduce-scatter lane l holds value l >> (5 - log2 kPairNv);
+        // lanes 0 .. 2 kPairCpw - 1 then gather the two complex sums of their
+        // output (column u = l >> 1, J for even l, M for odd l)
+        const int lo = lane & (2 * kPairCpw - 1), uo = lo >> 1;
+        const int ip = 8 * uo + ((lo & 1) ? 4 : 0), iq = 8 * uo + ((lo & 1) ? 2 : 6);
+        constexpr int kSpan = 32 / kPairNv;          // lanes per reduced value
+        const float2 cP = (lo & 1) ? cg : ca, cQ = (lo & 1) ? cd : cb;
+        const int cme = cw + uo * kPairColWarps;
+        for (long long q = q0; q < q1; ++q) {
+            if (!mbar_wait(&full[s], ph)) {
                 atomicExch(err, 1);
                 return;
             }
-            const int sb = (int)blockIdx.x + t * (int)gridDim.x;
-            const int bin = st_bin[sb], part = st_part[sb];
-            const int j0 = jb * kBmJB, jn = min(kBmJB, E - j0);
-            if (part != bin && jj < jn) {
+            if (prt != bin) {
+                const int j0 = jb * kPairJB, jn = min(kPairJB, E - j0);
                 const float2* Ls = sbuf + (size_t)s * stage_elems;
                 const float2* xp = xbuf + (t & 1) * 4 * E + 2 * E;
-                const float2* Lc = Ls + jj * E;
-                const float2* Kc = Lc + kBmJB * E;
-                // rows in pairs (16-byte loads): two independent FMA chains per lane
-                float2 a[2][4];
+                // a[u][pj, pm, qj, qm]: L x_J, L x_M, K x_J, K x_M of column u
+                float2 a[kPairCpw][4];
 #pragma unroll
-                for (int h2 = 0; h2 < 2; ++h2)
+                for (int u = 0; u < kPairCpw; ++u)
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) a[h2][c] = make_float2(0.f, 0.f);
-                for (int r = 2 * lane; r < E; r += 64) {
-                    const float4 l = *reinterpret_cast<const float4*>(Lc + r);
-                    const float4 k = *reinterpret_cast<const float4*>(Kc + r);
-                    const float4 xj = *reinterpret_cast<const float4*>(xp + r);
-                    const float4 xm = *reinterpret_cast<const float4*>(xp + E + r);
-                    const float2 l0 = make_float2(l.x, l.y), l1 = make_float2(l.z, l.w);
-                    const float2 k0 = make_float2(k.x, k.y), k1 = make_float2(k.z, k.w);
-                    const float2 xj0 = make_float2(xj.x, xj.y), xj1 = make_float2(xj.z, xj.w);
-                    const float2 xm0 = make_float2(xm.x, xm.y), xm1 = make_float2(xm.z, xm.w);
-                    cfma(a[0][0], l0, xj0);
-                    cfma(a[0][1], l0, xm0);
-                    cfma(a[0][2], k0, xj0);
-                    cfma(a[0][3], k0, xm0);
-                    cfma(a[1][0], l1, xj1);
-                    cfma(a[1][1], l1, xm1);
-                    cfma(a[1][2], k1, xj1);
-                    cfma(a[1][3], k1, xm1);
+                    for (int v = 0; v < 4; ++v) a[u][v] = make_float2(0.f, 0.f);
+                // rows in pairs (16-byte loads), kPairUnroll pairs per lane in
+                // flight; columns past jn hold stale data that is read but never
+                // written out
+                for (int rb = 0; rb < E; rb += 64 * kPairUnroll) {
+#pragma unroll
+                    for (int it = 0; it < kPairUnroll; ++it) {
+                        const int r = rb + 64 * it + 2 * lane;
+                        if (r < E) {
+                            const float4 xj = *reinterpret_cast<const float4*>(xp + r);
+                            const float4 xm = *reinterpret_cast<const float4*>(xp + E + r);
+                            const float2 xj0 = make_float2(xj.x, xj.y), xj1 = make_float2(xj.z, xj.w);
+                            const float2 xm0 = make_float2(xm.x, xm.y), xm1 = make_float2(xm.z, xm.w);
+#pragma unroll
+                            for (int u = 0; u < kPairCpw; ++u) {
+                                const float2* Lc = Ls + (cw + u * kPairColWarps) * E;
+                                const float4 l = *reinterpret_cast<const float4*>(Lc + r);
+                                const float4 k = *reinterpret_cast<const float4*>(Lc + kPairJB * E + r);
+                                const float2 l0 = make_float2(l.x, l.y), l1 = make_float2(l.z, l.w);
+                                const float2 k0 = make_float2(k.x, k.y), k1 = make_float2(k.z, k.w);
+                                cfma(a[u][0], l0, xj0);
+                                cfma(a[u][1], l0, xm0);
+                                cfma(a[u][2], k0, xj0);
+                                cfma(a[u][3], k0, xm0);
+                                cfma(a[u][0], l1, xj1);
+                                cfma(a[u][1], l1, xm1);
+                                cfma(a[u][2], k1, xj1);
+                                cfma(a[u][3], k1, xm1);
+                            }
+                        }
+                    }
                 }
-                // v = (pj, pm, qj, qm) as 8 floats; reduce-scatter butterfly over
-                // the warp (4 + 2 + 1 + 1 + 1 shuffles), after which lane 4c
-                // holds the warp sum of value c
-                float v[8];
+                // kPairNv floats per lane -> reduce-scatter butterfly (half of
+                // the values cross at each distance 16, 8, ...), then all-reduce
+                // over the remaining distances
+                float v[kPairNv];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    v[2 * c] = a[0][c].x + a[1][c].x;
-                    v[2 * c + 1] = a[0][c].y + a[1][c].y;
-                }
-                const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
-                float w4[4], w2[2];
+                for (int u = 0; u < kPairCpw; ++u)
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const float send = b4 ? v[c] : v[c + 4];
-                    const float keep = b4 ? v[c + 4] : v[c];
-                    w4[c] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-                }
+                    for (int c = 0; c < 4; ++c) {
+                        v[8 * u + 2 * c] = a[u][c].x;
+                        v[8 * u + 2 * c + 1] = a[u][c].y;
+                    }
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const float send = b3 ? w4[c] : w4[c + 2];
-                    const float keep = b3 ? w4[c + 2] : w4[c];
-                    w2[c] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-                }
-                float w1;
-                {
-                    const float send = b2 ? w2[0] : w2[1];
-                    const float keep = b2 ? w2[1] : w2[0];
-                    w1 = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-                }
-                w1 += __shfl_xor_sync(0xffffffffu, w1, 2);
-                w1 += __shfl_xor_sync(0xffffffffu, w1, 1);
-                float f[8];
+                for (int n = kPairNv, D = 16; n > 1; n >>= 1, D >>= 1) {
+                    const bool up = lane & D;
 #pragma unroll
-                for (int c = 0; c < 8; ++c) f[c] = __shfl_sync(0xffffffffu, w1, 4 * c);
-                if (lane == 0) {
-                    const float2 pj = make_float2(f[0], f[1]), pm = make_float2(f[2], f[3]);
-                    const float2 qj = make_float2(f[4], f[5]), qm = make_float2(f[6], f[7]);
-                    float2* Y = Yh + (size_t)part * 2 * E;
-                    Y[j0 + jj] = cadd(cmul(ca, pj), cmul(cb, qm));
-                    Y[E + j0 + jj] = cadd(cmul(cg, qj), cmul(cd, pm));
+                    for (int c = 0; c < n / 2; ++c) {
+                        const float send = up ? v[c] : v[c + n / 2];
+                        const float keep = up ? v[c + n / 2] : v[c];
+                        v[c] = keep + __shfl_xor_sync(0xffffffffu, send, D);
+                    }
+                }
+                float w1 = v[0];
+#pragma unroll
+                for (int D = 16 / kPairNv; D >= 1; D >>= 1) w1 += __shfl_xor_sync(0xffffffffu, w1, D);
+                const float px = __shfl_sync(0xffffffffu, w1, kSpan * ip);
+                const float py = __shfl_sync(0xffffffffu, w1, kSpan * (ip + 1));
+                const float qx = __shfl_sync(0xffffffffu, w1, kSpan * iq);
+                const float qy = __shfl_sync(0xffffffffu, w1, kSpan * (iq + 1));
+                if (lane < 2 * kPairCpw && cme < jn) {
+                    float2* Y = Yh + (size_t)prt * 2 * E + (lo & 1) * E;
+                    Y[j0 + cme] = cadd(cmul(cP, make_float2(px, py)), cmul(cQ, make_float2(qx, qy)));
                 }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
+            if (++s == kPairStages) { s = 0; ph ^= 1u; }
+            if (++jb == nj) {
+                jb = 0;
+                ++sb;
+                ++t;
+                if (q + 1 < q1) {
+                    bin = st_bin[sb];
+                    prt = st_part[sb];
+                }
+            }
         }
         return;
     }
     // ---- y(k) = B^(k) x(k): one thread per test row
-    const int i = (warp - 1) * 32 + lane;
+    const int w = warp - 1;
+    const int i = w * 32 + lane;
+    int s = 0, sb = sb0, jb = jb0, t = 0;
+    uint32_t ph = 0;
+    long long qb = (long long)sb0 * nj;     // first slab of bin sb
     float2 lj = make_float2(0.f, 0.f), lm = lj, kj = lj, km = lj;
-    for (long long q = 0; q < total; ++q) {
-        const int s = (int)(q % kPairStages);
-        const int t = (int)(q / nj), jb = (int)(q % nj);
-        if (!mbar_wait(&full[s], (uint32_t)((q / kPairStages) & 1))) {
+    for (long long q = q0; q < q1; ++q) {
+        if (!mbar_wait(&full[s], ph)) {
             atomicExch(err, 1);
             return;
         }
-        if (jb == 0) lj = lm = kj = km = make_float2(0.f, 0.f);
         const float2* Ls = sbuf + (size_t)s * stage_elems;
-        const float2* Ks = Ls + kBmJB * E;
+        const float2* Ks = Ls + kPairJB * E;
         const float2* xs = xbuf + (t & 1) * 4 * E;
-        const int j0 = jb * kBmJB, jn = min(kBmJB, E - j0);
+        const int j0 = jb * kPairJB, jn = min(kPairJB, E - j0);
         if (i < E) {
             // x(k) of the slab's columns (broadcast reads, two complex per 16 bytes)
-            float2 xjv[kBmJB], xmv[kBmJB];
-            if (jn == kBmJB) {
+            float2 xjv[kPairJB], xmv[kPairJB];
+            if (jn == kPairJB) {
                 const float4* xj4 = reinterpret_cast<const float4*>(xs + j0);
                 const float4* xm4 = reinterpret_cast<const float4*>(xs + E + j0);
 #pragma unroll
-                for (int p = 0; p < kBmJB / 2; ++p) {
+                for (int p = 0; p < kPairJB / 2; ++p) {
                     const float4 a = xj4[p], b = xm4[p];
                     xjv[2 * p] = make_float2(a.x, a.y);
                     xjv[2 * p + 1] = make_float2(a.z, a.w);
@@ -517,13 +576,13 @@ __global__ void binmul_tma_pair_kernel(const float2* __restrict__ Bhat, const fl
                 }
             } else {
 #pragma unroll
-                for (int jj = 0; jj < kBmJB; ++jj) {
+                for (int jj = 0; jj < kPairJB; ++jj) {
                     xjv[jj] = jj < jn ? xs[j0 + jj] : make_float2(0.f, 0.f);
                     xmv[jj] = jj < jn ? xs[E + j0 + jj] : make_float2(0.f, 0.f);
                 }
             }
 #pragma unroll
-            for (int jj = 0; jj < kBmJB; ++jj) {
+            for (int jj = 0; jj < kPairJB; ++jj) {
                 if (jj < jn) {
                     const float2 l = Ls[jj * E + i];
                     const float2 k = Ks[jj * E + i];
@@ -536,17 +595,60 @@ __global__ void binmul_tma_pair_kernel(const float2* __restrict__ Bhat, const fl
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
-        if (jb == nj - 1 && i < E) {
-            const int sb = (int)blockIdx.x + t * (int)gridDim.x;
+        if (jb == nj - 1 || q == q1 - 1) {
+            // this CTA's part of bin sb ends here
+            const float2 y0 = cadd(cmul(ca, lj), cmul(cb, km));
+            const float2 y1 = cadd(cmul(cg, kj), cmul(cd, lm));
             float2* Y = Yh + (size_t)st_bin[sb] * 2 * E;
-            Y[i] = cadd(cmul(ca, lj), cmul(cb, km));
-            Y[E + i] = cadd(cmul(cg, kj), cmul(cd, lm));
+            if (qb >= q0 && jb == nj - 1) {
+                if (i < E) {
+                    Y[i] = y0;
+                    Y[E + i] = y1;
+                }
+            } else {
+                float2* P = part + ((size_t)blockIdx.x * 2 + (t == 0 ? 0 : 1)) * 2 * E;
+                if (i < E) {
+                    P[i] = y0;
+                    P[E + i] = y1;
+                }
+                __threadfence();
+                __syncwarp();
+                const int bf = pair_cta_of(qb, Q, G), bl = pair_cta_of(qb + nj - 1, Q, G);
+                int* c = cnt + (size_t)sb * ncw + w;
+                int old = 0;
+                if (lane == 0) old = atomicAdd(c, 1);
+                old = __shfl_sync(0xffffffffu, old, 0);
+                if (old == bl - bf) {
+                    // every contributor has written its partial
+                    if (lane == 0) *c = 0;
+                    __threadfence();
+                    if (i < E) {
+                        float2 a0 = make_float2(0.f, 0.f), a1 = a0;
+                        for (int b = bf; b <= bl; ++b) {
+                            const int sl = ((long long)b * Q / G) / nj == sb ? 0 : 1;
+                            const float2* Pb = part + ((size_t)b * 2 + sl) * 2 * E;
+                            a0 = cadd(a0, __ldcg(Pb + i));
+                            a1 = cadd(a1, __ldcg(Pb + E + i));
+                        }
+                        Y[i] = a0;
+                        Y[E + i] = a1;
+                    }
+                }
+            }
+            lj = lm = kj = km = make_float2(0.f, 0.f);
+        }
+        if (++s == kPairStages) { s = 0; ph ^= 1u; }
+        if (++jb == nj) {
+            jb = 0;
+            ++sb;
+            ++t;
+            qb += nj;
         }
     }
 }
 
 size_t binmul_tma_pair_smem(int E) {
-    return (size_t)kPairStages * 2 * kBmJB * E * sizeof(float2) + 8ull * E * sizeof(float2) +
+    return (size_t)kPairStages * 2 * kPairJB * E * sizeof(float2) + 8ull * E * sizeof(float2) +
            2ull * kPairStages * sizeof(uint64_t);
 }
 
@@ -837,9 +939,10 @@ int derive_fp32_operator(emsurf_handle* h, const emsurf_problem* pr) {
     const size_t nb = (size_t)h->nbins;
     cudaStream_t st = h->setup_stream;
     Operator<float2>& op = h->op32;
-    // With reciprocal tables B^(-k) = B^(k)^T: single-rhs handles without the
-    // tensor-core planes keep one bin of each pair (k, -k) (checked here on
-    // the FP64 spectrum, to 1e-12 of its largest entry).
+    // With reciprocal tables L^(-k) = L^(k)^T and K^(-k) = K^(k)^T: single-rhs
+    // handles without the tensor-core planes keep one bin of each pair
+    // (k, -k) (checked here on the FP64 spectrum, to 1e-12 of its largest
+    // entry).
     bool half = false;
     std::vector<int32_t> partner(nb), sbin, spart;
     for (int ky = 0; ky < h->py; ++ky)
@@ -847,7 +950,7 @@ int derive_fp32_operator(emsurf_handle* h, const emsurf_problem* pr) {
             partner[(size_t)ky * h->px + kx] = ((h->py - ky) % h->py) * h->px + (h->px - kx) % h->px;
     const int ncw = (h->E + 31) / 32;
     if (h->max_rhs == 1 && !pr->tensor_cores && (h->E & 1) == 0 && binmul_tma_pair_smem(h->E) <= 227 * 1024 &&
-        32 * (1 + ncw + kBmJB) <= 1024 && (h->E + kBmJB - 1) / kBmJB >= kPairStages) {
+        32 * (1 + ncw + kPairColWarps) <= kPairMaxThreads && (h->E + kPairJB - 1) / kPairJB >= kPairStages) {
         int32_t* dpart = nullptr;
         unsigned long long* dout = nullptr;
         EMS_CUDA(cudaMalloc(&dpart, nb * sizeof(int32_t)));
@@ -880,6 +983,15 @@ int derive_fp32_operator(emsurf_handle* h, const emsurf_problem* pr) {
         EMS_CUDA(cudaMemcpyAsync(dsp, spart.data(), spart.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         h->d_st_bin = dsb;
         h->d_st_part = dsp;
+        // slab ranges of the pair kernel: one per SM, none empty; partial row
+        // sums of straddling bins and their arrival counters (kept at zero
+        // between launches)
+        const long long nslab = (long long)h->nst * ((h->E + kPairJB - 1) / kPairJB);
+        h->pair_grid = (int)std::min<long long>(std::max(1, h->num_sms), nslab);
+        EMS_TRY(dev_alloc(h, (void**)&h->d_pair_part, (size_t)h->pair_grid * 2 * 2 * h->E * sizeof(float2)));
+        h->pair_cnt_bytes = (size_t)h->nst * ncw * sizeof(int);
+        EMS_TRY(dev_alloc(h, (void**)&h->d_pair_cnt, h->pair_cnt_bytes));
+        EMS_CUDA(cudaMemsetAsync(h->d_pair_cnt, 0, h->pair_cnt_bytes, st));
         EMS_TRY(dev_alloc(h, (void**)&op.Bhat, (size_t)h->nst * 2 * EE * sizeof(float2)));
         half_round_kernel<<<152 * 8, 256, 0, st>>>(op.Bhat, h->op64.Bhat, dsb, 2 * EE, (size_t)h->nst * 2 * EE);
         EMS_CUDA(cudaGetLastError());
@@ -1030,10 +1142,9 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
             // half spectrum (single rhs): one read of each stored bin serves k and -k
             const size_t smem = binmul_tma_pair_smem(E);
             EMS_TRY(set_smem_once(binmul_tma_pair_kernel, smem));
-            const int grid = std::min(h->nst, std::max(1, h->num_sms));
-            binmul_tma_pair_kernel<<<grid, 32 * (1 + (E + 31) / 32 + kBmJB), smem, st>>>(
+            binmul_tma_pair_kernel<<<h->pair_grid, 32 * (1 + (E + 31) / 32 + kPairColWarps), smem, st>>>(
                 op.Bhat, op.Xg, op.Yg, h->d_st_bin, h->d_st_part, E, h->nst, op.coef[0], op.coef[1], op.coef[2],
-                op.coef[3], h->d_err);
+                op.coef[3], h->d_pair_part, h->d_pair_cnt, h->d_err);
             EMS_CUDA(cudaGetLastError());
             h->launches += 1;
             bin_done = true;
