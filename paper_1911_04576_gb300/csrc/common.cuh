@@ -67,6 +67,37 @@ __host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) {
     return make_float2(a.x + b.x, a.y + b.y);
 }
 
+// ---------------------------------------------------------------- L2 priority
+// Data streamed once per product (the Fourier-domain blocks, the
+// preconditioner rows) is loaded with an evict-first L2 policy and data
+// reused by every product (the macromodels) with evict-last, so the 129 MB L2
+// keeps the reused arrays between products.  Both are hints (createpolicy,
+// L2::cache_hint); results do not depend on them.
+__device__ __forceinline__ uint64_t l2_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint4 ldg_l2hint(const uint4* a, uint64_t pol) {
+    uint4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float4 ldg_l2hint(const float4* a, uint64_t pol) {
+    float4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(a), "l"(pol));
+    return v;
+}
+
 template <typename T2> struct Real;
 template <> struct Real<double2> { using type = double; };
 template <> struct Real<float2> { using type = float; };

@@ -221,6 +221,15 @@ __global__ void wait_selftest_kernel(long long limit, int* __restrict__ err) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     if (!mbar_wait(&bar, 0, limit)) atomicExch(err, 3);
 }
+// the same with an L2 policy (l2_evict_first for data read once per product)
+__device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                              uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], "
+        "%4;" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
+        : "memory");
+}
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -254,6 +263,7 @@ __global__ void binmul_tma_kernel(const float2* __restrict__ Bhat, const float2*
     const long long total = (long long)nloc * nj;
     if (warp == 0) {
         if (lane != 0) return;
+        const uint64_t pol = l2_evict_first();
         long long issued = 0;
         bool ok = true;
         for (long long q = 0; q < total; ++q) {
@@ -270,8 +280,8 @@ __global__ void binmul_tma_kernel(const float2* __restrict__ Bhat, const float2*
             mbar_expect_tx(&full[s], 2 * bytes_op + (jb == 0 ? bytes_x : 0u));
             const float2* src = Bhat + (size_t)bin * 2 * E * E + (size_t)j0 * E;
             float2* dst = sbuf + (size_t)s * stage_elems;
-            bulk_g2s(dst, src, bytes_op, &full[s]);
-            bulk_g2s(dst + kBmJB * E, src + (size_t)E * E, bytes_op, &full[s]);
+            bulk_g2s_hint(dst, src, bytes_op, &full[s], pol);
+            bulk_g2s_hint(dst + kBmJB * E, src + (size_t)E * E, bytes_op, &full[s], pol);
             if (jb == 0) bulk_g2s(xbuf + (t & 1) * 2 * E, Xh + (size_t)bin * 2 * E, bytes_x, &full[s]);
             issued = q + 1;
         }
@@ -395,6 +405,7 @@ __global__ void __launch_bounds__(kPairMaxThreads, 1) binmul_tma_pair_kernel(con
     const int sb0 = (int)(q0 / nj), jb0 = (int)(q0 % nj);
     if (warp == 0) {
         if (lane != 0) return;
+        const uint64_t pol = l2_evict_first();
         const uint32_t bytes_x = (uint32_t)(2 * E * sizeof(float2));
         int s = 0, sb = sb0, jb = jb0, t = 0;
         uint32_t ph = 0;
@@ -417,8 +428,8 @@ __global__ void __launch_bounds__(kPairMaxThreads, 1) binmul_tma_pair_kernel(con
             mbar_expect_tx(&full[s], 2 * bytes_op + xb);
             const float2* src = Bhat + (size_t)sb * 2 * E * E + (size_t)j0 * E;
             float2* dst = sbuf + (size_t)s * stage_elems;
-            bulk_g2s(dst, src, bytes_op, &full[s]);
-            bulk_g2s(dst + kPairJB * E, src + (size_t)E * E, bytes_op, &full[s]);
+            bulk_g2s_hint(dst, src, bytes_op, &full[s], pol);
+            bulk_g2s_hint(dst + kPairJB * E, src + (size_t)E * E, bytes_op, &full[s], pol);
             if (newbin) {
                 float2* xd = xbuf + (t & 1) * 4 * E;
                 bulk_g2s(xd, Xh + (size_t)bin * 2 * E, bytes_x, &full[s]);
@@ -725,9 +736,9 @@ __global__ void macromodel_kernel(const T2* __restrict__ Zt, const double2* __re
 // Single-rhs FP32 variant: each thread owns two adjacent output rows and
 // keeps eight 16-byte loads of Z in flight (the one-row kernel is bound by
 // load latency at one rhs); the staged x1 is read two columns at a time.
-constexpr int kMm2Unroll = 8;
+constexpr int kMm2Unroll = 4;   // 16-byte loads per buffer (two blocks of 320 threads per SM)
 template <int G>
-__global__ void __launch_bounds__(320)
+__global__ void __launch_bounds__(320, 2)
 macromodel2_kernel(const float2* __restrict__ Zt, const double2* __restrict__ x,
                    const int32_t* __restrict__ idx, const int8_t* __restrict__ sgn,
                    const int32_t* __restrict__ type_cells, const MmBlock* __restrict__ blocks,
@@ -759,6 +770,7 @@ macromodel2_kernel(const float2* __restrict__ Zt, const double2* __restrict__ x,
     __syncthreads();
     const int K2 = K >> 1;
     const float4* Z4 = reinterpret_cast<const float4*>(Zt + (size_t)b.type * K * K + (size_t)k0 * K);
+    const uint64_t pol = l2_evict_last();      // the macromodels are read by every product
     for (int k2 = threadIdx.x; k2 < K2; k2 += blockDim.x) {
         float2 a0[G], a1[G];
 #pragma unroll
@@ -769,7 +781,7 @@ macromodel2_kernel(const float2* __restrict__ Zt, const double2* __restrict__ x,
         auto load = [&](float4 (&z)[kMm2Unroll], int kb) {
 #pragma unroll
             for (int u = 0; u < kMm2Unroll; ++u)
-                z[u] = kb + u < nk ? __ldg(Z4 + (size_t)(kb + u) * K2 + k2) : make_float4(0.f, 0.f, 0.f, 0.f);
+                z[u] = kb + u < nk ? ldg_l2hint(Z4 + (size_t)(kb + u) * K2 + k2, pol) : make_float4(0.f, 0.f, 0.f, 0.f);
         };
         auto mul = [&](const float4 (&z)[kMm2Unroll], int kb) {
 #pragma unroll

@@ -409,6 +409,154 @@ pc_apply_kernel(const __half2* __restrict__ X, const float* __restrict__ rscale,
     }
 }
 
+// Single- and two-rhs apply without the gather pass.  The owned rows are cut
+// into gridDim.x contiguous ranges of equal length; a block walks its range
+// cell by cell: it gathers the cell's r segment straight from r into shared
+// memory (FP32, zero past n_m up to ld_m), then each warp takes two rows at a
+// time (16-byte loads of the FP16 rows, kApSegLoads per row and lane in
+// flight) and reduces both rows' sums with one reduce-scatter.
+constexpr int kApSegThreads = 256;
+constexpr int kApSegMaxLd = 1024;   // longest row (complex entries) of this kernel
+constexpr int kApSegLoads = 4;
+
+template <typename VT>
+__device__ __forceinline__ float2 to_f2(VT v) { return make_float2((float)v.x, (float)v.y); }
+
+template <int RQ, typename VT>
+__global__ void __launch_bounds__(kApSegThreads, RQ == 1 ? 4 : 3)
+pc_apply_seg_kernel(const __half2* __restrict__ X, const float* __restrict__ rscale,
+                    const int64_t* __restrict__ xoff, const int32_t* __restrict__ ldx,
+                    const int32_t* __restrict__ own_ptr, const int32_t* __restrict__ sub_ptr,
+                    const int32_t* __restrict__ sub_ids, const VT* __restrict__ r, VT* __restrict__ y,
+                    int n_rows, int M, int n_unique) {
+    __shared__ __align__(16) float2 rsm[RQ][kApSegMaxLd];
+    constexpr int NV = 4 * RQ;            // floats per lane and row pair: [row][q][re, im]
+    constexpr int kSpan = 32 / NV;        // lanes per reduced value
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint64_t pol = l2_evict_first();     // the rows are read once per apply
+    const int g0 = (int)((long long)blockIdx.x * n_rows / gridDim.x);
+    const int g1 = (int)((long long)(blockIdx.x + 1) * n_rows / gridDim.x);
+    if (g0 >= g1) return;
+    // cell of row g0: the last m with own_ptr[m] <= g0
+    int lo = 0, hi = M;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (own_ptr[mid] <= g0) lo = mid; else hi = mid;
+    }
+    int m = lo;
+    for (int g = g0; g < g1;) {
+        while (own_ptr[m + 1] <= g) ++m;           // cells that own no row
+        const int e = min(g1, own_ptr[m + 1]);
+        const int ld = ldx[m], n = sub_ptr[m + 1] - sub_ptr[m];
+        const int32_t* ids = sub_ids + sub_ptr[m];
+        __syncthreads();                           // readers of the previous segment are done
+        for (int c = threadIdx.x; c < ld; c += blockDim.x) {
+            const int u = c < n ? ids[c] : 0;
+#pragma unroll
+            for (int q = 0; q < RQ; ++q)
+                rsm[q][c] = c < n ? to_f2(r[(size_t)q * n_unique + u]) : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        const int quarter = ld >> 2;
+        const uint4* Xm = reinterpret_cast<const uint4*>(X + xoff[m]);
+        const int i0 = g - own_ptr[m], cnt = e - g;
+        for (int p = 2 * warp; p < cnt; p += 2 * nw) {
+            const int ia = i0 + p, ib = p + 1 < cnt ? ia + 1 : ia;
+            const uint4* ra = Xm + (size_t)ia * quarter;
+            const uint4* rb = Xm + (size_t)ib * quarter;
+            float2 acc[2][RQ];
+#pragma unroll
+            for (int w = 0; w < 2; ++w)
+#pragma unroll
+                for (int q = 0; q < RQ; ++q) acc[w][q] = make_float2(0.f, 0.f);
+            for (int c0 = lane; c0 < quarter; c0 += 32 * kApSegLoads) {
+                uint4 xv[2][kApSegLoads];
+#pragma unroll
+                for (int u = 0; u < kApSegLoads; ++u) {
+                    const bool in = c0 + 32 * u < quarter;
+                    xv[0][u] = in ? ldg_l2hint(ra + c0 + 32 * u, pol) : make_uint4(0u, 0u, 0u, 0u);
+                    xv[1][u] = in ? ldg_l2hint(rb + c0 + 32 * u, pol) : make_uint4(0u, 0u, 0u, 0u);
+                }
+#pragma unroll
+                for (int u = 0; u < kApSegLoads; ++u) {
+                    const int c4 = min(c0 + 32 * u, quarter - 1);
+#pragma unroll
+                    for (int q = 0; q < RQ; ++q) {
+                        const float4 r0 = reinterpret_cast<const float4*>(rsm[q])[2 * c4];
+                        const float4 r1 = reinterpret_cast<const float4*>(rsm[q])[2 * c4 + 1];
+#pragma unroll
+                        for (int w = 0; w < 2; ++w) {
+                            const float2 f0 = __half22float2(*reinterpret_cast<const __half2*>(&xv[w][u].x));
+                            const float2 f1 = __half22float2(*reinterpret_cast<const __half2*>(&xv[w][u].y));
+                            const float2 f2 = __half22float2(*reinterpret_cast<const __half2*>(&xv[w][u].z));
+                            const float2 f3 = __half22float2(*reinterpret_cast<const __half2*>(&xv[w][u].w));
+                            acc[w][q].x += f0.x * r0.x - f0.y * r0.y + f1.x * r0.z - f1.y * r0.w +
+                                           f2.x * r1.x - f2.y * r1.y + f3.x * r1.z - f3.y * r1.w;
+                            acc[w][q].y += f0.x * r0.y + f0.y * r0.x + f1.x * r0.w + f1.y * r0.z +
+                                           f2.x * r1.y + f2.y * r1.x + f3.x * r1.w + f3.y * r1.z;
+                        }
+                    }
+                }
+            }
+            // reduce-scatter: lane l ends with the warp sum of value l / kSpan
+            float v[NV];
+#pragma unroll
+            for (int w = 0; w < 2; ++w)
+#pragma unroll
+                for (int q = 0; q < RQ; ++q) {
+                    v[(w * RQ + q) * 2] = acc[w][q].x;
+                    v[(w * RQ + q) * 2 + 1] = acc[w][q].y;
+                }
+#pragma unroll
+            for (int nn = NV, D = 16; nn > 1; nn >>= 1, D >>= 1) {
+                const bool up = lane & D;
+#pragma unroll
+                for (int c = 0; c < nn / 2; ++c) {
+                    const float send = up ? v[c] : v[c + nn / 2];
+                    const float keep = up ? v[c + nn / 2] : v[c];
+                    v[c] = keep + __shfl_xor_sync(0xffffffffu, send, D);
+                }
+            }
+            float s1 = v[0];
+#pragma unroll
+            for (int D = 16 / NV; D >= 1; D >>= 1) s1 += __shfl_xor_sync(0xffffffffu, s1, D);
+            const float s2 = __shfl_down_sync(0xffffffffu, s1, kSpan);   // the next value (imaginary part)
+            const int vi = lane / kSpan;
+            if (lane % kSpan == 0 && (vi & 1) == 0) {
+                const int w = vi / (2 * RQ), q = (vi >> 1) % RQ;
+                if (w == 0 || p + 1 < cnt) {
+                    const int i = w ? ib : ia;
+                    const float sc = rscale[own_ptr[m] + i];
+                    VT o;
+                    o.x = s1 * sc;
+                    o.y = s2 * sc;
+                    y[(size_t)q * n_unique + ids[i]] = o;
+                }
+            }
+        }
+        g = e;
+        ++m;
+    }
+}
+
+template <int RQ, typename VT>
+int launch_apply_seg(emsurf_handle* h, const VT* r, VT* y, cudaStream_t st) {
+    static int occ[3][2] = {};
+    int& o = occ[RQ][sizeof(VT) == sizeof(float2) ? 1 : 0];
+    if (!o) {
+        int b = 0;
+        EMS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pc_apply_seg_kernel<RQ, VT>, kApSegThreads, 0));
+        o = std::max(b, 1);
+    }
+    const int blocks = std::max(1, std::min(h->num_sms * o, h->n_unique));
+    pc_apply_seg_kernel<RQ, VT><<<blocks, kApSegThreads, 0, st>>>(
+        reinterpret_cast<const __half2*>(h->pc_mat16), h->pc_rscale, h->pc_off, h->pc_ld, h->pc_own_ptr,
+        h->pc_sub_ptr, h->pc_sub_ids, r, y, h->n_unique, h->M, h->n_unique);
+    EMS_CUDA(cudaGetLastError());
+    h->launches += 1;
+    return EMSURF_OK;
+}
+
 template <int RQ, typename VO>
 int launch_apply(emsurf_handle* h, VO* y, int r0, int nr, cudaStream_t st) {
     // resident blocks per SM (the same for every device of this build)
@@ -439,6 +587,8 @@ int pc_apply_t(emsurf_handle* h, const VT* r, VT* y, int R, cudaStream_t st) {
         return EMSURF_EINVAL;
     }
     if (h->have_pc_tc && R >= kTcMinRhs) return pc_tc_apply<VT>(h, r, y, R, st);
+    if (R <= 2 && ((h->pc_nmax + 3) & ~3) <= kApSegMaxLd)
+        return R == 1 ? launch_apply_seg<1, VT>(h, r, y, st) : launch_apply_seg<2, VT>(h, r, y, st);
     const int total = (int)h->pc_sub_total;
     pc_gather_kernel<VT><<<std::min((total + 255) / 256, h->num_sms * 8), 256, 0, st>>>(
         r, h->pc_sub_ids, h->pc_sub_cell, h->pc_sub_ptr, h->pc_rs_off, h->pc_rs, total, h->n_unique,

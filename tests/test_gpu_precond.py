@@ -160,7 +160,7 @@ def test_precond_invalid(emsurf_lib, phys):
     h.close()
 
 
-@pytest.mark.parametrize("R", [3, 11])
+@pytest.mark.parametrize("R", [1, 2, 3, 11])
 def test_precond_random_ragged_lattice(emsurf_lib, R):
     """A 4 x 3 lattice of n = 2 boxes with synthetic tables and strongly
     diagonal macromodels: cells at the edge and corners have smaller
