@@ -18,11 +18,13 @@ and applies it as restricted additive Schwarz (Cai & Sarkis 1999):
 
 A is the dense matrix of Eq. final (assemble_from_tables).  Everything is
 complex128 with dense solves, so this is the exact-arithmetic definition that
-the device's FP32 factorisation is compared with.
+the device's FP32 factorisation is compared with.  For lattices too large for
+a dense A, subdomain_matrix forms one block A[S, S] from the same definition
+restricted to the cells that hold a copy of an unknown in S.
 """
 import numpy as np
 
-from .lattice import cell_shift
+from .lattice import _block, cell_shift
 
 
 def unknown_positions(box, index, nx, ny, a, b):
@@ -62,3 +64,31 @@ def ras_apply(A, subs, r):
         z = np.linalg.solve(A[np.ix_(S, S)], r[S])
         y[S[own]] += z[own]
     return y
+
+
+def subdomain_matrix(S, Lt, Kt, coef, macromodels, type_map, index, sign, nx, ny):
+    """A[S, S] of A = U_o^T [Z_eq + Z_o] U_o (Eq. final) for unique unknowns S.
+    Column u of U_o is zero outside the local slots that copy u, so only the
+    cells holding such a copy enter: Z_eq + Z_o is formed over those cells
+    (offset blocks plus the macromodel on the diagonal, Eqs. out, blockZo,
+    Zmacromodel_Array) and reduced with the matching rows of U_o."""
+    E = Lt.shape[-1]
+    Kl = 2 * E
+    S = np.asarray(S)
+    col = -np.ones(int(index.max()) + 1, dtype=np.int64)
+    col[S] = np.arange(len(S))
+    locs = np.nonzero(col[index] >= 0)[0]
+    cells = np.unique(locs // Kl)
+    pos = {int(m): a for a, m in enumerate(cells)}
+    nc = len(cells)
+    Z = np.zeros((nc * Kl, nc * Kl), dtype=complex)
+    for a, m in enumerate(cells):
+        ix, iy = m % nx, m // nx
+        for b, ms in enumerate(cells):
+            jx, jy = ms % nx, ms // nx
+            Z[a * Kl:(a + 1) * Kl, b * Kl:(b + 1) * Kl] = _block(Lt, Kt, coef, ix - jx, iy - jy, nx, ny)
+        Z[a * Kl:(a + 1) * Kl, a * Kl:(a + 1) * Kl] += macromodels[type_map[m]]
+    U = np.zeros((nc * Kl, len(S)))
+    rows = np.array([pos[int(l // Kl)] * Kl + int(l % Kl) for l in locs], dtype=np.int64)
+    U[rows, col[index[locs]]] = sign[locs]
+    return U.T @ Z @ U

@@ -34,8 +34,7 @@ namespace {
 
 constexpr int kRedBlocks = 152;     // one per SM of GB300
 constexpr int kRedThreads = 256;
-constexpr int kCheckEvery = 6;      // Arnoldi steps between host convergence checks
-constexpr int kArnThreads = 512;    // 16 warps: one per Krylov vector in the dot phase
+constexpr int kArnThreads = 1024;   // 32 warps: one per Krylov vector in the dot phase
 constexpr int kArnChunkMax = 4096;  // vector elements per block (64 KB of shared w)
 
 struct Gm {
@@ -60,10 +59,10 @@ struct Gm {
     double2* g = nullptr;      // [R][m+1]
     double2* hv = nullptr;     // [R][m+1] projections of one CGS pass
     double2* hv2 = nullptr;    // [R][m+1] projections of the second CGS pass
-    unsigned* counter = nullptr;   // [R] last-block counters of the fused reductions
     int nblk = 0, chunk = 0;       // Arnoldi blocks and elements per block
     int* reorth = nullptr;         // [R] second Gram-Schmidt pass needed (DGKS test)
-    double2* part = nullptr;   // [R][m+1][kRedBlocks]
+    double2* part = nullptr;   // [R][m+1][max(nblk, kRedBlocks)] block partials
+    double2* part2 = nullptr;  // [R][m+1][nblk] partials of the second Gram-Schmidt pass
     double* nrm = nullptr;     // [R]
     double* bnorm = nullptr;   // [R]
     double* res = nullptr;     // [R] estimated relative residual
@@ -71,6 +70,8 @@ struct Gm {
     int* jend = nullptr;       // [R]
     double* h_res = nullptr;   // pinned host mirror [R]
     int* h_act = nullptr;      // pinned host mirror [R]
+    int* h_ring = nullptr;     // pinned [2][R] convergence flags of the last two steps
+    cudaEvent_t ev[2] = {nullptr, nullptr};   // their copies done
     int64_t launches = 0;      // kernels launched by the solver itself
 };
 
@@ -201,64 +202,16 @@ __global__ void to_f32_kernel(float2* __restrict__ o, const double2* __restrict_
 }
 
 // ---------------------------------------------------------------- fused step
-// Block reduction of one complex value; result valid in thread 0.
-__device__ __forceinline__ double2 block_sum(double2 v, double2* red /* [blockDim/32] */) {
-    v = warp_sum(v);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) red[wid] = v;
-    __syncthreads();
-    double2 t = make_double2(0.0, 0.0);
-    if (wid == 0) {
-        t = lane < (int)(blockDim.x >> 5) ? red[lane] : make_double2(0.0, 0.0);
-        t = warp_sum(t);
-    }
-    return t;
-}
-
-// After every block wrote its partials: returns true in the last block to
-// arrive (classic threadfence reduction); that block resets the counter.
-__device__ __forceinline__ bool last_block(unsigned* counter, bool* flag) {
-    // every thread that wrote a partial makes it visible, then the whole
-    // block has finished writing before thread 0 announces it
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) *flag = atomicAdd(counter, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (*flag) {
-        __threadfence();
-        if (threadIdx.x == 0) *counter = 0;
-    }
-    return *flag;
-}
-
-// sum of part[r][i][0..nb) in block order -> out (one warp per i)
-__device__ __forceinline__ void finalize_sums(const double2* part, int nb, int nvec, int ldv, int r,
-                                              double2* out_hv, double2* Hcol, bool add) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int i = wid; i < nvec; i += nw) {
-        double2 acc = make_double2(0.0, 0.0);
-        for (int b = lane; b < nb; b += 32) {
-            const double2 v = part[((size_t)r * ldv + i) * nb + b];
-            acc.x += v.x;
-            acc.y += v.y;
-        }
-        acc = warp_sum(acc);
-        if (lane == 0) {
-            out_hv[(size_t)r * ldv + i] = acc;
-            if (Hcol) Hcol[i] = add ? make_double2(Hcol[i].x + acc.x, Hcol[i].y + acc.y) : acc;
-        }
-    }
-}
-
-// w -= sum_i c_i V_i on one element (c from shared memory), 8 loads in flight
+// w -= sum_i c_i V_i on one element (c from shared memory), 16 (FP32) or 8
+// (FP64) loads in flight
 template <typename VT>
 __device__ __forceinline__ VT update_one(const VT* __restrict__ V, int nvec, size_t vstride,
                                          size_t off, VT acc, const VT* __restrict__ cs) {
-    for (int i0 = 0; i0 < nvec; i0 += 8) {
-        VT v[8];
+    constexpr int G = sizeof(VT) == sizeof(float2) ? 16 : 8;   // loads in flight
+    for (int i0 = 0; i0 < nvec; i0 += G) {
+        VT v[G];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
+        for (int c = 0; c < G; ++c) {
             if (i0 + c < nvec) {
                 v[c] = V[(size_t)(i0 + c) * vstride + off];
             } else {
@@ -267,7 +220,7 @@ __device__ __forceinline__ VT update_one(const VT* __restrict__ V, int nvec, siz
             }
         }
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
+        for (int c = 0; c < G; ++c) {
             if (i0 + c < nvec) {
                 const VT q = cs[i0 + c];
                 acc.x -= q.x * v[c].x - q.y * v[c].y;
@@ -278,155 +231,242 @@ __device__ __forceinline__ VT update_one(const VT* __restrict__ V, int nvec, siz
     return acc;
 }
 
-// Projections h_i = V_i^H w (i < nvec) for every rhs.  Each block owns a
-// contiguous chunk of the vector: it stages that chunk of w in shared memory
-// (after applying w -= sum_i upd_i V_i when upd != nullptr, the previous
-// Gram-Schmidt pass), then one warp per Krylov vector forms the chunk's dot
-// product with a single warp reduction.  The last block sums the block
-// partials in block order into hv and sets (add = 0) or adds to column j of H.
-template <typename VT>
-__global__ void __launch_bounds__(kArnThreads)
-cgs_pass_kernel(const VT* __restrict__ V, int nvec, size_t vstride, VT* __restrict__ w,
-                size_t n, int chunk, const double2* __restrict__ upd, double2* __restrict__ part,
-                int ldv, unsigned* __restrict__ counter, double2* __restrict__ hv,
-                double2* __restrict__ H, int m, int j, int add, int* __restrict__ reorth) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    VT* ws = reinterpret_cast<VT*>(smem_raw);   // [chunk]
-    __shared__ VT cs[65];
-    __shared__ bool is_last;
-    const int r = blockIdx.y;
-    VT* wr = w + (size_t)r * n;
-    const size_t e0 = (size_t)blockIdx.x * chunk;
-    const int ne = (int)(e0 < n ? min((size_t)chunk, n - e0) : 0);
-    if (upd && !reorth[r]) {
-        // second pass not needed: apply the first pass's update only
-        for (int i = threadIdx.x; i < nvec; i += blockDim.x) cs[i] = from_d2<VT>(upd[(size_t)r * ldv + i]);
-        __syncthreads();
-        for (int q = threadIdx.x; q < ne; q += blockDim.x)
-            wr[e0 + q] = update_one(V, nvec, vstride, (size_t)r * n + e0 + q, wr[e0 + q], cs);
-        if (blockIdx.x == 0)
-            for (int i = threadIdx.x; i < nvec; i += blockDim.x) hv[(size_t)r * ldv + i] = make_double2(0.0, 0.0);
-        return;
-    }
-    if (upd) {
-        for (int i = threadIdx.x; i < nvec; i += blockDim.x) cs[i] = from_d2<VT>(upd[(size_t)r * ldv + i]);
-        __syncthreads();
-        for (int q = threadIdx.x; q < ne; q += blockDim.x) {
-            const VT v = update_one(V, nvec, vstride, (size_t)r * n + e0 + q, wr[e0 + q], cs);
-            wr[e0 + q] = v;
-            ws[q] = v;
-        }
-    } else {
-        for (int q = threadIdx.x; q < ne; q += blockDim.x) ws[q] = wr[e0 + q];
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    // the first pass also forms ||w||^2 (as "vector" nvec) for the
-    // reorthogonalisation test; lane sums in VT's precision, the warp sum in FP64
-    const int ndots = upd ? nvec : nvec + 1;
-    for (int i = wid; i < ndots; i += nw) {
-        const VT* a = (i < nvec ? V + (size_t)i * vstride + (size_t)r * n : wr) + e0;
-        VT accv;
-        accv.x = 0;
-        accv.y = 0;
-        for (int q = lane; q < ne; q += 32) {
-            const VT p = conj_mul(a[q], ws[q]);
-            accv.x += p.x;
-            accv.y += p.y;
-        }
-        const double2 acc = warp_sum(to_d2(accv));
-        if (lane == 0) part[((size_t)r * ldv + i) * gridDim.x + blockIdx.x] = acc;
-    }
-    if (last_block(counter + r, &is_last)) {
-        finalize_sums(part, gridDim.x, ndots, ldv, r, hv, nullptr, false);
-        __syncthreads();
-        double2* col = H + ((size_t)r * m + j) * (m + 1);
-        for (int i = threadIdx.x; i < nvec; i += blockDim.x)
-            col[i] = add ? make_double2(col[i].x + hv[(size_t)r * ldv + i].x, col[i].y + hv[(size_t)r * ldv + i].y)
-                         : hv[(size_t)r * ldv + i];
-        if (!upd && threadIdx.x == 0) {
-            // DGKS: after w' = w - V h, ||w'||^2 = ||w||^2 - ||h||^2; a second
-            // pass is needed when ||w'|| < ||w|| / sqrt(2)
-            double hh = 0.0;
-            for (int i = 0; i < nvec; ++i) {
-                const double2 v = hv[(size_t)r * ldv + i];
-                hh += v.x * v.x + v.y * v.y;
-            }
-            const double ww = hv[(size_t)r * ldv + nvec].x;
-            reorth[r] = (ww - hh < 0.5 * ww) ? 1 : 0;
-        }
-    }
-}
-
 __device__ void givens_update(int r, double2* __restrict__ col, double2* __restrict__ c,
                               double2* __restrict__ s, double2* __restrict__ gg,
                               const double* __restrict__ bnorm, double* __restrict__ res,
                               int* __restrict__ active, int* __restrict__ jend, int m, int j,
                               double rtol);
 
-// w -= sum_i upd_i V_i, ||w||, H[j+1][j] = ||w||, then (last block, one
-// thread per rhs) the Givens update of column j.
+// State of one Arnoldi step shared by its kernels.
+struct ArnStep {
+    double2* H;            // [R][m][m+1]
+    double2* cs;           // [R][m]
+    double2* sn;           // [R][m]
+    double2* g;            // [R][m+1]
+    const double* bnorm;   // [R]
+    double* res;           // [R]
+    int* active;           // [R]
+    int* jend;             // [R]
+    double* nrm;           // [R] H[j+1][j] of the step
+    int* reorth;           // [R] second Gram-Schmidt pass taken
+    double2* part1;        // [R][ldv][nch] chunk partials of the first pass
+    double2* part2;        // [R][ldv][nch] chunk partials of the second pass
+    int m, j, ldv, nch;
+    double rtol;
+};
+
+// H[j+1][j] = nu and the Givens update of column j (column, rotations and g
+// staged in shared memory; one thread rotates).  Whole block.
+__device__ void finish_column(const ArnStep& a, int r, double nu) {
+    __shared__ double2 scol[66], sc[65], ssn[65], sg[66];
+    const int j = a.j, m = a.m;
+    double2* col = a.H + ((size_t)r * m + j) * (m + 1);
+    __syncthreads();
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) scol[i] = col[i];
+    for (int i = threadIdx.x; i < j; i += blockDim.x) {
+        sc[i] = a.cs[(size_t)r * m + i];
+        ssn[i] = a.sn[(size_t)r * m + i];
+    }
+    for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) sg[i] = a.g[(size_t)r * (m + 1) + i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a.nrm[r] = nu;
+        scol[j + 1] = make_double2(nu, 0.0);
+        givens_update(r, scol, sc, ssn, sg, a.bnorm, a.res, a.active, a.jend, m, j, a.rtol);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) {
+        col[i] = scol[i];
+        a.g[(size_t)r * (m + 1) + i] = sg[i];
+    }
+    if (threadIdx.x == 0) {
+        a.cs[(size_t)r * m + j] = sc[j];
+        a.sn[(size_t)r * m + j] = ssn[j];
+    }
+}
+
+// Dot products of the staged chunk ws with V_0..V_{nvec-1} and with itself
+// (value nvec): one warp per vector, eight independent loads per lane in
+// flight, lane sums in VT's precision (fixed order), the warp sum in FP64,
+// chunk partials to part[r][i][c].
+template <typename VT>
+__device__ __forceinline__ void chunk_dots(const VT* __restrict__ V, int nvec, size_t vstride, const VT* ws,
+                                           int ne, size_t off, double2* part, int ldv, int nch, int r, int c) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = wid; i <= nvec; i += nw) {
+        const VT* a = i < nvec ? V + (size_t)i * vstride + off : ws;
+        VT accv;
+        accv.x = 0;
+        accv.y = 0;
+        for (int q0 = 0; q0 < ne; q0 += 256) {
+            VT av[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int q = q0 + 32 * u + lane;
+                if (q < ne) {
+                    av[u] = a[q];
+                } else {
+                    av[u].x = 0;
+                    av[u].y = 0;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int q = q0 + 32 * u + lane;
+                if (q < ne) {
+                    const VT p = conj_mul(av[u], ws[q]);
+                    accv.x += p.x;
+                    accv.y += p.y;
+                }
+            }
+        }
+        const double2 acc = warp_sum(to_d2(accv));
+        if (lane == 0) part[((size_t)r * ldv + i) * nch + c] = acc;
+    }
+}
+
+// sh[i] = sum over chunks of part[r][i][.] for i < nv (fixed order, so every
+// block that calls this gets bit-identical values), then sh[nv] holds nothing
+// new; returns sum_{i < nv - 1} |sh[i]|^2 in every thread.
+__device__ __forceinline__ double reduce_partials(const double2* __restrict__ part, int nv, int nch, int ldv,
+                                                  int r, double2* sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = wid; i < nv; i += nw) {
+        const double2* p = part + ((size_t)r * ldv + i) * nch;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int b0 = 0; b0 < nch; b0 += 256) {
+            double2 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int b = b0 + 32 * u + lane;
+                v[u] = b < nch ? __ldcg(p + b) : make_double2(0.0, 0.0);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                acc.x += v[u].x;
+                acc.y += v[u].y;
+            }
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) sh[i] = acc;
+    }
+    __syncthreads();
+    __shared__ double hh;
+    if (wid == 0) {
+        double t = 0.0;
+        for (int i = lane; i < nv - 1; i += 32) t += sh[i].x * sh[i].x + sh[i].y * sh[i].y;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) hh = t;
+    }
+    __syncthreads();
+    return hh;
+}
+
+// First classical Gram-Schmidt pass of Arnoldi step j (nvec = j + 1): each
+// block owns chunk c of the vector, stages it in shared memory and writes its
+// partials of h = V^H w and of ||w||^2.
 template <typename VT>
 __global__ void __launch_bounds__(kArnThreads)
-cgs_norm_givens_kernel(const VT* __restrict__ V, int nvec, size_t vstride,
-                       VT* __restrict__ w, size_t n, int chunk, const double2* __restrict__ upd,
-                       double2* __restrict__ part, int ldv, unsigned* __restrict__ counter,
-                       double* __restrict__ nrm, double2* __restrict__ H, double2* __restrict__ cs,
-                       double2* __restrict__ sn, double2* __restrict__ g,
-                       const double* __restrict__ bnorm, double* __restrict__ res,
-                       int* __restrict__ active, int* __restrict__ jend, int m, int j, double rtol,
-                       const int* __restrict__ reorth) {
-    using S = typename VScalar<VT>::T;
-    __shared__ double2 red[kArnThreads / 32];
-    __shared__ VT cs_[65];
-    __shared__ bool is_last;
-    const int r = blockIdx.y;
-    VT* wr = w + (size_t)r * n;
-    const size_t e0 = (size_t)blockIdx.x * chunk;
+arn_dots_kernel(const VT* __restrict__ V, size_t vstride, const VT* __restrict__ w, size_t n, int chunk,
+                ArnStep a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    VT* ws = reinterpret_cast<VT*>(smem_raw);   // [chunk]
+    const int r = blockIdx.y, c = blockIdx.x, nvec = a.j + 1;
+    const size_t e0 = (size_t)c * chunk;
     const int ne = (int)(e0 < n ? min((size_t)chunk, n - e0) : 0);
-    for (int i = threadIdx.x; i < nvec; i += blockDim.x) cs_[i] = from_d2<VT>(upd[(size_t)r * ldv + i]);
+    const VT* wr = w + (size_t)r * n + e0;
+    for (int q = threadIdx.x; q < ne; q += blockDim.x) ws[q] = wr[q];
     __syncthreads();
-    S ss = 0;
-    const bool second = reorth[r] != 0;
-    for (int q = threadIdx.x; q < ne; q += blockDim.x) {
-        const VT acc = second ? update_one(V, nvec, vstride, (size_t)r * n + e0 + q, wr[e0 + q], cs_)
-                              : wr[e0 + q];
-        if (second) wr[e0 + q] = acc;
-        ss += acc.x * acc.x + acc.y * acc.y;
+    chunk_dots(V, nvec, vstride, ws, ne, (size_t)r * n + e0, a.part1, a.ldv, a.nch, r, c);
+}
+
+// Second kernel of step j (grid nch + 1).  Every block sums the first pass's
+// partials (identically) and takes the DGKS decision: with ||w - V h||^2 =
+// ||w||^2 - ||h||^2 >= ||w||^2 / 2 no second pass is needed and that
+// difference is H[j+1][j] = nu, so chunk blocks write V_{j+1} = (w - V h) / nu.
+// Otherwise they store w' = w - V h and the partials of h2 = V^H w' and
+// ||w'||^2.  Block 0 writes column j of H (and, without a second pass,
+// H[j+1][j] and the Givens update).
+template <typename VT>
+__global__ void __launch_bounds__(kArnThreads)
+arn_update_kernel(const VT* __restrict__ V, size_t vstride, VT* __restrict__ w, VT* __restrict__ vnext,
+                  size_t n, int chunk, ArnStep a) {
+    using S = typename VScalar<VT>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    VT* ws = reinterpret_cast<VT*>(smem_raw);   // [chunk]
+    __shared__ double2 sh[66];
+    __shared__ VT cs[65];
+    const int r = blockIdx.y, nvec = a.j + 1;
+    const double hh = reduce_partials(a.part1, nvec + 1, a.nch, a.ldv, r, sh);
+    const double ww = sh[nvec].x;
+    const bool second = ww - hh < 0.5 * ww;
+    const double nu = sqrt(fmax(ww - hh, 0.0));
+    if (blockIdx.x == 0) {
+        double2* col = a.H + ((size_t)r * a.m + a.j) * (a.m + 1);
+        for (int i = threadIdx.x; i < nvec; i += blockDim.x) col[i] = sh[i];
+        if (threadIdx.x == 0) a.reorth[r] = second ? 1 : 0;
+        if (!second) finish_column(a, r, nu);
+        return;
     }
-    const double2 t = block_sum(make_double2((double)ss, 0.0), red);
-    if (threadIdx.x == 0) part[((size_t)r * ldv) * gridDim.x + blockIdx.x] = t;
-    if (last_block(counter + r, &is_last)) {
-        // stage column j, the rotations and g in shared memory (parallel loads)
-        __shared__ double2 scol[66], sc[65], ssn[65], sg[66];
-        double2* col = H + ((size_t)r * m + j) * (m + 1);
-        for (int i = threadIdx.x; i <= j; i += blockDim.x) scol[i] = col[i];
-        for (int i = threadIdx.x; i < j; i += blockDim.x) {
-            sc[i] = cs[(size_t)r * m + i];
-            ssn[i] = sn[(size_t)r * m + i];
+    const int c = blockIdx.x - 1;
+    const size_t e0 = (size_t)c * chunk;
+    const int ne = (int)(e0 < n ? min((size_t)chunk, n - e0) : 0);
+    const size_t off = (size_t)r * n + e0;
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) cs[i] = from_d2<VT>(sh[i]);
+    __syncthreads();
+    if (!second) {
+        const S sinv = (S)(nu > 0.0 ? 1.0 / nu : 0.0);
+        for (int q = threadIdx.x; q < ne; q += blockDim.x) {
+            VT v = update_one(V, nvec, vstride, off + q, w[off + q], cs);
+            v.x *= sinv;
+            v.y *= sinv;
+            vnext[off + q] = v;
         }
-        for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) sg[i] = g[(size_t)r * (m + 1) + i];
-        double acc = 0.0;
-        if (threadIdx.x < 32) {
-            for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) acc += part[((size_t)r * ldv) * gridDim.x + b].x;
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const double v = sqrt(fmax(acc, 0.0));
-            nrm[r] = v;
-            scol[j + 1] = make_double2(v, 0.0);
-            givens_update(r, scol, sc, ssn, sg, bnorm, res, active, jend, m, j, rtol);
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) {
-            col[i] = scol[i];
-            g[(size_t)r * (m + 1) + i] = sg[i];
-        }
-        if (threadIdx.x == 0) {
-            cs[(size_t)r * m + j] = sc[j];
-            sn[(size_t)r * m + j] = ssn[j];
-        }
+        return;
+    }
+    for (int q = threadIdx.x; q < ne; q += blockDim.x) {
+        const VT v = update_one(V, nvec, vstride, off + q, w[off + q], cs);
+        w[off + q] = v;
+        ws[q] = v;
+    }
+    __syncthreads();
+    chunk_dots(V, nvec, vstride, ws, ne, off, a.part2, a.ldv, a.nch, r, c);
+}
+
+// Third kernel of step j, only after a second pass (grid nch + 1): every
+// block sums the second pass's partials; H[j+1][j] = nu = sqrt(||w'||^2 -
+// ||h2||^2); chunk blocks write V_{j+1} = (w' - V h2) / nu; block 0 adds h2
+// to column j of H and does the Givens update.
+template <typename VT>
+__global__ void __launch_bounds__(kArnThreads)
+arn_reorth_kernel(const VT* __restrict__ V, size_t vstride, const VT* __restrict__ w, VT* __restrict__ vnext,
+                  size_t n, int chunk, ArnStep a) {
+    using S = typename VScalar<VT>::T;
+    const int r = blockIdx.y, nvec = a.j + 1;
+    if (!a.reorth[r]) return;
+    __shared__ double2 sh[66];
+    __shared__ VT cs[65];
+    const double hh = reduce_partials(a.part2, nvec + 1, a.nch, a.ldv, r, sh);
+    const double nu = sqrt(fmax(sh[nvec].x - hh, 0.0));
+    if (blockIdx.x == 0) {
+        double2* col = a.H + ((size_t)r * a.m + a.j) * (a.m + 1);
+        for (int i = threadIdx.x; i < nvec; i += blockDim.x) col[i] = make_double2(col[i].x + sh[i].x, col[i].y + sh[i].y);
+        finish_column(a, r, nu);
+        return;
+    }
+    const int c = blockIdx.x - 1;
+    const size_t e0 = (size_t)c * chunk;
+    const int ne = (int)(e0 < n ? min((size_t)chunk, n - e0) : 0);
+    const size_t off = (size_t)r * n + e0;
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) cs[i] = from_d2<VT>(sh[i]);
+    __syncthreads();
+    const S sinv = (S)(nu > 0.0 ? 1.0 / nu : 0.0);
+    for (int q = threadIdx.x; q < ne; q += blockDim.x) {
+        VT v = update_one(V, nvec, vstride, off + q, w[off + q], cs);
+        v.x *= sinv;
+        v.y *= sinv;
+        vnext[off + q] = v;
     }
 }
 
@@ -485,25 +525,38 @@ __device__ void givens_update(int r, double2* __restrict__ col, double2* __restr
     if (res[r] <= rtol || den == 0.0) active[r] = 0;
 }
 
-// y = H[0:jend,0:jend]^{-1} g[0:jend] by back substitution (one thread per rhs)
+// y = H[0:jend,0:jend]^{-1} g[0:jend] by back substitution: one block per
+// rhs stages its triangle and g in shared memory, then one thread solves
 __global__ void trisolve_kernel(const double2* __restrict__ H, const double2* __restrict__ g,
                                 double2* __restrict__ y, const int* __restrict__ jend, int m, int R) {
-    const int r = threadIdx.x;
+    __shared__ double2 sH[64 * 65 / 2];   // column k rows 0..k at k (k + 1) / 2
+    __shared__ double2 sg[65];
+    const int r = blockIdx.x;
     if (r >= R) return;
     const int n = jend[r];
+    const double2* Hr = H + (size_t)r * m * (m + 1);
+    for (int e = threadIdx.x; e < n * (m + 1); e += blockDim.x) {
+        const int k = e / (m + 1), i = e % (m + 1);
+        if (i <= k) sH[k * (k + 1) / 2 + i] = Hr[e];
+    }
+    for (int e = threadIdx.x; e < n; e += blockDim.x) sg[e] = g[(size_t)r * (m + 1) + e];
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double2* yr = y + (size_t)r * (m + 1);
     for (int i = n - 1; i >= 0; --i) {
-        double2 acc = g[(size_t)r * (m + 1) + i];
+        double2 acc = sg[i];
         for (int k = i + 1; k < n; ++k) {
-            const double2 hk = H[((size_t)r * m + k) * (m + 1) + i];
-            const double2 yk = y[(size_t)r * (m + 1) + k];
+            const double2 hk = sH[k * (k + 1) / 2 + i];
+            const double2 yk = sg[k];   // holds y[k] once solved
             acc.x -= hk.x * yk.x - hk.y * yk.y;
             acc.y -= hk.x * yk.y + hk.y * yk.x;
         }
-        const double2 d = H[((size_t)r * m + i) * (m + 1) + i];
+        const double2 d = sH[i * (i + 1) / 2 + i];
         const double dd = d.x * d.x + d.y * d.y;
-        y[(size_t)r * (m + 1) + i] = dd > 0.0 ? make_double2((acc.x * d.x + acc.y * d.y) / dd,
-                                                             (acc.y * d.x - acc.x * d.y) / dd)
-                                              : make_double2(0.0, 0.0);
+        const double2 yi = dd > 0.0 ? make_double2((acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd)
+                                    : make_double2(0.0, 0.0);
+        sg[i] = yi;
+        yr[i] = yi;
     }
 }
 
@@ -583,14 +636,12 @@ int gm_alloc(emsurf_handle* h, Gm*& gm, int m, int R) {
     EMS_TRY(dev_alloc(h, (void**)&g->g, sizeof(double2) * RR * (mm + 1)));
     EMS_TRY(dev_alloc(h, (void**)&g->hv, sizeof(double2) * RR * (mm + 1)));
     EMS_TRY(dev_alloc(h, (void**)&g->hv2, sizeof(double2) * RR * (mm + 1)));
-    EMS_TRY(dev_alloc(h, (void**)&g->counter, sizeof(unsigned) * RR));
     EMS_TRY(dev_alloc(h, (void**)&g->reorth, sizeof(int) * RR));
-    EMS_CUDA(cudaMemset(g->counter, 0, sizeof(unsigned) * RR));
-    EMS_CUDA(cudaDeviceSynchronize());   // the counters must be zero before any solve stream uses them
-    g->nblk = (int)std::max<size_t>(2 * 152, (g->n + kArnChunkMax - 1) / kArnChunkMax);
+    g->nblk = (int)std::max<size_t>(std::max(1, h->num_sms), (g->n + kArnChunkMax - 1) / kArnChunkMax);
     g->chunk = (int)((g->n + g->nblk - 1) / g->nblk);
     EMS_TRY(dev_alloc(h, (void**)&g->part,
                       sizeof(double2) * RR * (mm + 1) * std::max<size_t>(g->nblk, kRedBlocks)));
+    EMS_TRY(dev_alloc(h, (void**)&g->part2, sizeof(double2) * RR * (mm + 1) * g->nblk));
     EMS_TRY(dev_alloc(h, (void**)&g->nrm, sizeof(double) * RR));
     EMS_TRY(dev_alloc(h, (void**)&g->bnorm, sizeof(double) * RR));
     EMS_TRY(dev_alloc(h, (void**)&g->res, sizeof(double) * RR));
@@ -598,10 +649,14 @@ int gm_alloc(emsurf_handle* h, Gm*& gm, int m, int R) {
     EMS_TRY(dev_alloc(h, (void**)&g->jend, sizeof(int) * RR));
     EMS_CUDA(cudaMallocHost(&g->h_res, sizeof(double) * RR));
     EMS_CUDA(cudaMallocHost(&g->h_act, sizeof(int) * RR));
+    EMS_CUDA(cudaMallocHost(&g->h_ring, 2 * sizeof(int) * RR));
+    for (int i = 0; i < 2; ++i) EMS_CUDA(cudaEventCreateWithFlags(&g->ev[i], cudaEventDisableTiming));
     if (h->gm) {
         Gm* old = static_cast<Gm*>(h->gm);
         cudaFreeHost(old->h_res);
         cudaFreeHost(old->h_act);
+        cudaFreeHost(old->h_ring);
+        for (int i = 0; i < 2; ++i) cudaEventDestroy(old->ev[i]);
         delete old;   // device buffers stay in h->allocations until destroy
     }
     h->gm = g;
@@ -702,41 +757,44 @@ int gmres_core(emsurf_handle* h, Gm* g, Apply<VT>& A, const VT* b, VT* x, int R,
             } else {
                 EMS_TRY(A(Vj, K.w, R, st));
             }
-            // CGS with the DGKS second pass, norm and Givens: 3 fused kernels
-            const dim3 rg(g->nblk, R);
+            // classical Gram-Schmidt with the DGKS second pass, H[j+1][j] and
+            // the Givens update: 2 kernels, a third one after a second pass
             const size_t wsm = (size_t)g->chunk * sizeof(VT);
-            EMS_TRY(set_smem_once(cgs_pass_kernel<VT>, wsm));
+            EMS_TRY(set_smem_once(arn_dots_kernel<VT>, wsm));
+            EMS_TRY(set_smem_once(arn_update_kernel<VT>, wsm));
+            const ArnStep as{g->H, g->cs, g->sn, g->g, g->bnorm, g->res, g->active, g->jend, g->nrm,
+                             g->reorth, g->part, g->part2, m, j, m + 1, g->nblk, rtol};
+            VT* vnext = K.V + (size_t)(j + 1) * vstride;
             prof_mark(h, EMS_PH_ARNOLDI, true, st);
-            cgs_pass_kernel<VT><<<rg, kArnThreads, wsm, st>>>(K.V, j + 1, vstride, K.w, n, g->chunk, nullptr,
-                                                              g->part, m + 1, g->counter, g->hv, g->H, m, j, 0,
-                                                              g->reorth);
+            arn_dots_kernel<VT><<<dim3(g->nblk, R), kArnThreads, wsm, st>>>(K.V, vstride, K.w, n, g->chunk, as);
             EMS_CUDA(cudaGetLastError());
-            cgs_pass_kernel<VT><<<rg, kArnThreads, wsm, st>>>(K.V, j + 1, vstride, K.w, n, g->chunk, g->hv,
-                                                              g->part, m + 1, g->counter, g->hv2, g->H, m, j, 1,
-                                                              g->reorth);
+            arn_update_kernel<VT><<<dim3(g->nblk + 1, R), kArnThreads, wsm, st>>>(K.V, vstride, K.w, vnext, n,
+                                                                                 g->chunk, as);
             EMS_CUDA(cudaGetLastError());
-            cgs_norm_givens_kernel<VT><<<rg, kArnThreads, 0, st>>>(
-                K.V, j + 1, vstride, K.w, n, g->chunk, g->hv2, g->part, m + 1, g->counter, g->nrm, g->H,
-                g->cs, g->sn, g->g, g->bnorm, g->res, g->active, g->jend, m, j, rtol, g->reorth);
-            EMS_CUDA(cudaGetLastError());
-            normalize_kernel<VT><<<nb, 256, 0, st>>>(K.V + (size_t)(j + 1) * vstride, K.w, g->nrm, n,
-                                                     R, nullptr, m, j);
+            arn_reorth_kernel<VT><<<dim3(g->nblk + 1, R), kArnThreads, 0, st>>>(K.V, vstride, K.w, vnext, n,
+                                                                               g->chunk, as);
             EMS_CUDA(cudaGetLastError());
             prof_mark(h, EMS_PH_ARNOLDI, false, st);
-            g->launches += 4;
+            g->launches += 3;
             ++it;
-            // convergence is read back every kCheckEvery steps (the steps after
-            // a right-hand side converged leave its solution untouched)
+            // the convergence flags of step j are copied to pinned memory behind
+            // its kernels; the host reads those of step j - 1 while step j runs,
+            // so the GPU does not wait for the host and at most one step is
+            // computed after every rhs converged (such a step leaves the
+            // solution untouched: the update uses the steps before jend)
+            int* hr = g->h_ring + (size_t)(j & 1) * R;
+            EMS_CUDA(cudaMemcpyAsync(hr, g->active, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+            EMS_CUDA(cudaEventRecord(g->ev[j & 1], st));
             if (it >= max_iters) break;
-            if ((j + 1) % kCheckEvery == 0 && j + 1 < m) {
-                EMS_CUDA(cudaMemcpyAsync(g->h_act, g->active, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
-                EMS_CUDA(cudaStreamSynchronize(st));
+            if (j >= 1) {
+                EMS_CUDA(cudaEventSynchronize(g->ev[(j - 1) & 1]));
+                const int* hp = g->h_ring + (size_t)((j - 1) & 1) * R;
                 bool act = false;
-                for (int r = 0; r < R; ++r) act = act || g->h_act[r];
+                for (int r = 0; r < R; ++r) act = act || hp[r];
                 if (!act) break;
             }
         }
-        trisolve_kernel<<<1, 64, 0, st>>>(g->H, g->g, g->hv, g->jend, m, R);
+        trisolve_kernel<<<R, 256, 0, st>>>(g->H, g->g, g->hv, g->jend, m, R);
         EMS_CUDA(cudaGetLastError());
         ++g->launches;
         xupdate_kernel<VT><<<nb, 256, (size_t)R * (m + 1) * sizeof(VT), st>>>(
@@ -869,6 +927,9 @@ void gmres_release(emsurf_handle* h) {
     Gm* g = static_cast<Gm*>(h->gm);
     if (g->h_res) cudaFreeHost(g->h_res);
     if (g->h_act) cudaFreeHost(g->h_act);
+    if (g->h_ring) cudaFreeHost(g->h_ring);
+    for (int i = 0; i < 2; ++i)
+        if (g->ev[i]) cudaEventDestroy(g->ev[i]);
     delete g;   // device buffers are released with the handle's allocations
     h->gm = nullptr;
 }

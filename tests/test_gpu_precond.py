@@ -217,3 +217,39 @@ def test_precond_apply_tensor_cores(emsurf_lib, phys, R):
         assert np.all(np.isfinite(y[q]))
         assert np.linalg.norm(y[q] - ref) <= tol * np.linalg.norm(ref), (q, tol)
     h.close()
+
+
+def test_precond_apply_full_size_sampled(emsurf_lib):
+    """16 x 16 lattice, K = 576, one rhs: the single-rhs apply in the launch
+    configuration of the bench (95,496 owned rows over the SMs, subdomains of
+    up to ~850 unknowns).  The owned rows of a corner and an interior cell are
+    recomputed by the oracle from their subdomain blocks A[S_m, S_m]; bar as
+    above with kappa of those blocks."""
+    import torch
+    from paper_1911_04576_gb300 import binding as B
+    w = W.WORKLOADS["lattice16x16_k576"]
+    box = box_mesh(A, A, H, w.n)
+    idx, sgn, nu = lattice.overlap_map(box, w.nx, w.ny, A, A)
+    Lt, Kt = W.random_tables(w.nx, w.ny, w.E, 1700, decay=2.0)
+    Z = W.random_macromodels(w.n_types, w.K, 1701, diag=200.0)
+    tmap = W.type_map(w)
+    coef = (0.5j, 1.0, -1.0, 0.5j)
+    xy, owner = precond.unknown_positions(box, idx, w.nx, w.ny, A, A)
+    delta = 0.6 * A / w.n
+    h = B.emsurf_create(w.nx, w.ny, w.E, nu, tmap, Z, Lt, Kt, coef, idx, sgn, precision=B.MIXED,
+                        max_rhs=1, unknown_xy=xy, cell=(A, A), precond_overlap=delta)
+    r = W.random_vectors(1, nu, 1702)
+    rd = torch.from_numpy(r).cuda()
+    yd = torch.full_like(rd, float("nan"))
+    B.emsurf_precond_apply(h, rd, yd)
+    y = yd.cpu().numpy()[0]
+    assert np.all(np.isfinite(y))
+    subs = precond.subdomains(xy, owner, w.nx, w.ny, A, A, delta)
+    for m in (0, 8 * w.nx + 7):
+        S, own = subs[m]
+        As = precond.subdomain_matrix(S, Lt, Kt, coef, Z, tmap, idx, sgn, w.nx, w.ny)
+        ref = np.linalg.solve(As, r[0][S])[own]
+        tol = (3 * len(S) + 1) * U32 * np.linalg.cond(As) + 2.0 ** -11 * np.sqrt(len(S))
+        assert np.linalg.norm(y[S[own]] - ref) <= tol * np.linalg.norm(ref), (m, tol)
+    B.emsurf_check(h)
+    h.close()

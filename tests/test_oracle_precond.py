@@ -99,3 +99,23 @@ def test_block_diagonal_on_owners_is_exact(lat, delta):
     C = M + 0.05 * (rng.standard_normal((nu, nu)) + 1j * rng.standard_normal((nu, nu)))
     e = x - precond.ras_apply(C, subs, C @ x)
     assert 0 < np.linalg.norm(e) < 0.5 * np.linalg.norm(x)
+
+
+@pytest.mark.parametrize("delta", [0.0, 0.3 * A])
+def test_subdomain_matrix_is_the_dense_block(lat, delta):
+    """The restricted assembly of A[S, S] equals the same block of the dense
+    U_o^T [Z_eq + Z_o] U_o, for the cell subdomains and for an arbitrary
+    scattered set of unknowns (copies in several non-adjacent cells)."""
+    from paper_1911_04576_gb300 import workloads as W
+    box, nx, ny, idx, sgn, nu, xy, owner = lat
+    E = box.n_rwg
+    Lt, Kt = W.random_tables(nx, ny, E, 31)
+    Z = W.random_macromodels(2, 2 * E, 32)
+    tmap = np.array([0, 1, 1, 0, 1, 0], dtype=np.int32)
+    coef = (0.3j, 1.0, -1.0, 0.7j)
+    Ad = lattice.assemble_from_tables(Lt, Kt, coef, Z, tmap, idx, sgn, nu, nx, ny)
+    sets = [S for S, _ in precond.subdomains(xy, owner, nx, ny, A, B, delta)]
+    sets.append(np.sort(np.random.default_rng(33).choice(nu, 40, replace=False)))
+    for S in sets:
+        As = precond.subdomain_matrix(S, Lt, Kt, coef, Z, tmap, idx, sgn, nx, ny)
+        assert np.abs(As - Ad[np.ix_(S, S)]).max() <= 1e-12 * np.abs(Ad).max()
