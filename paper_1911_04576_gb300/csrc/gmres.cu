@@ -4,8 +4,12 @@
 // guess and orthogonalisation are not given.  Here: zero initial guess,
 // GMRES(m) with classical Gram-Schmidt and a second pass when the DGKS test
 // asks for it (||w'|| < ||w||/sqrt 2; Daniel, Gragg, Kaufman, Stewart 1976),
-// Givens rotations and the upper-triangular solve on the device, all FP64.  Right-hand sides are independent
-// systems that share every operator application.
+// Givens rotations and the upper-triangular solve on the device, all FP64.
+// H[j+1][j] comes from the same sums: ||w - V h||^2 = ||w||^2 - ||h||^2 for
+// orthonormal V, which the DGKS test bounds below by ||w||^2 / 2 when no
+// second pass is taken (after one, the identity is applied to w' and h2).
+// Right-hand sides are independent systems that share every operator
+// application.
 //
 // With the near-field preconditioner M (Sec. IV-A applies it on the right)
 // the Arnoldi process runs on A M^{-1} in its flexible form (Saad 1993):
