@@ -141,6 +141,8 @@ int create_impl(const emsurf_problem* p, emsurf_handle* h) {
     EMS_CUDA(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
     EMS_TRY(dev_alloc(h, (void**)&h->d_err, sizeof(int)));
     EMS_CUDA(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->setup_stream));
+    EMS_TRY(dev_alloc(h, (void**)&h->d_grid_bar, 2 * sizeof(unsigned)));
+    EMS_CUDA(cudaMemsetAsync(h->d_grid_bar, 0, 2 * sizeof(unsigned), h->setup_stream));
     EMS_TRY(fft_plan_create(h->plan_x, h->px));
     EMS_TRY(fft_plan_create(h->plan_y, h->py));
     const int M = h->M, K = h->K;
@@ -247,11 +249,13 @@ void prof_mark(emsurf_handle* h, int phase, bool begin, cudaStream_t st) {
 void gmres_release(emsurf_handle* h);
 
 // Clears the bounded-wait error flag and the state an aborted launch may
-// have left behind (the pair kernel's arrival counters).
+// have left behind (the pair kernel's arrival counters, the grid barrier of
+// the cooperative Arnoldi step).
 int clear_wait_error(emsurf_handle* h) {
     EMS_CUDA(cudaDeviceSynchronize());
     EMS_CUDA(cudaMemset(h->d_err, 0, sizeof(int)));
     if (h->d_pair_cnt) EMS_CUDA(cudaMemset(h->d_pair_cnt, 0, h->pair_cnt_bytes));
+    if (h->d_grid_bar) EMS_CUDA(cudaMemset(h->d_grid_bar, 0, 2 * sizeof(unsigned)));
     return EMSURF_OK;
 }
 

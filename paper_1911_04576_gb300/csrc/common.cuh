@@ -256,6 +256,8 @@ struct emsurf_handle {
     int32_t* pc_sub_ptr = nullptr;  // [M+1]
     int32_t* pc_sub_ids = nullptr;  // unique ids of each subdomain
     int* d_err = nullptr;             // device error flag of bounded waits (0 = ok)
+    unsigned* d_grid_bar = nullptr;   // [2] count and generation of the cooperative Arnoldi step's grid barrier
+    bool coop_ok = true;              // the cooperative Arnoldi step may be used (no overlapping solves)
     // GMRES workspace (FP64), allocated lazily by emsurf_solve
     void* gm = nullptr;
     // tracing: kernel launches issued by this handle, optional phase timers

@@ -77,6 +77,11 @@ struct Gm {
     int* h_ring = nullptr;     // pinned [2][R] convergence flags of the last two steps
     cudaEvent_t ev[2] = {nullptr, nullptr};   // their copies done
     int64_t launches = 0;      // kernels launched by the solver itself
+    // single-rhs cooperative Arnoldi step ([0] FP32, [1] FP64 vectors): blocks
+    // (chunks + the bookkeeping block, all resident) and elements per chunk;
+    // 0 blocks = not available (the three-kernel step is used)
+    int coop_blocks[2] = {0, 0};
+    int coop_chunk[2] = {0, 0};
 };
 
 template <typename VT> struct VScalar;
@@ -474,6 +479,125 @@ arn_reorth_kernel(const VT* __restrict__ V, size_t vstride, const VT* __restrict
     }
 }
 
+// ---------------------------------------------------------------- one-launch step
+// Grid barrier of a cooperative launch (all blocks co-resident): arrival
+// count bar[0], generation bar[1].  Thread 0 arrives; the last arrival resets
+// the count and advances the generation, the others poll it (bounded: on
+// expiry *err = 4 and false is returned, and the caller's block leaves).
+constexpr long long kBarLimit = 1LL << 22;
+
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* err) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = bar + 1;
+        const unsigned g0 = *gen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == nblocks - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+            ok = 1;
+        } else {
+            ok = 0;
+            for (long long it = 0; it < kBarLimit; ++it) {
+                if (*gen != g0) {
+                    ok = 1;
+                    break;
+                }
+                __nanosleep(64);
+            }
+            if (!ok) atomicExch(err, 4);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Arnoldi step j for one rhs as a single cooperative launch: blocks
+// 0 .. gridDim.x - 2 own chunks of the vector, the last block keeps H and the
+// Givens rotations.  Phases, separated by grid barriers: partials of h = V^H w
+// and ||w||^2; every block sums them (same order, same decision) and either
+// writes V_{j+1} = (w - V h) / sqrt(||w||^2 - ||h||^2) or, when the DGKS
+// test asks for a second pass, stores w' = w - V h with the partials of
+// h2 = V^H w' and ||w'||^2; after the second barrier V_{j+1} = (w' - V h2) /
+// sqrt(||w'||^2 - ||h2||^2).  The same arithmetic as arn_dots/update/reorth.
+template <typename VT>
+__global__ void __launch_bounds__(kArnThreads)
+arn_step_coop_kernel(const VT* __restrict__ V, size_t vstride, VT* __restrict__ w, VT* __restrict__ vnext,
+                     size_t n, int chunk, ArnStep a, unsigned* __restrict__ bar, int* __restrict__ err) {
+    using S = typename VScalar<VT>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    VT* ws = reinterpret_cast<VT*>(smem_raw);   // [chunk]
+    __shared__ double2 sh[66];
+    __shared__ VT cs[65];
+    const int nvec = a.j + 1, nch = gridDim.x - 1;
+    const bool book = (int)blockIdx.x == nch;
+    const int c = blockIdx.x;
+    const size_t e0 = (size_t)c * chunk;
+    const int ne = (!book && e0 < n) ? (int)min((size_t)chunk, n - e0) : 0;
+    if (!book) {
+        for (int q = threadIdx.x; q < ne; q += blockDim.x) ws[q] = w[e0 + q];
+        __syncthreads();
+        chunk_dots(V, nvec, vstride, ws, ne, e0, a.part1, a.ldv, nch, 0, c);
+    }
+    if (!grid_barrier(bar, gridDim.x, err)) return;
+    const double hh = reduce_partials(a.part1, nvec + 1, nch, a.ldv, 0, sh);
+    const double ww = sh[nvec].x;
+    const bool second = ww - hh < 0.5 * ww;
+    const double nu = sqrt(fmax(ww - hh, 0.0));
+    if (book) {
+        double2* col = a.H + (size_t)a.j * (a.m + 1);
+        for (int i = threadIdx.x; i < nvec; i += blockDim.x) col[i] = sh[i];
+        if (threadIdx.x == 0) a.reorth[0] = second ? 1 : 0;
+        if (!second) {
+            finish_column(a, 0, nu);
+            return;
+        }
+    } else {
+        for (int i = threadIdx.x; i < nvec; i += blockDim.x) cs[i] = from_d2<VT>(sh[i]);
+        __syncthreads();
+        if (!second) {
+            const S sinv = (S)(nu > 0.0 ? 1.0 / nu : 0.0);
+            for (int q = threadIdx.x; q < ne; q += blockDim.x) {
+                VT v = update_one(V, nvec, vstride, e0 + q, w[e0 + q], cs);
+                v.x *= sinv;
+                v.y *= sinv;
+                vnext[e0 + q] = v;
+            }
+            return;
+        }
+        for (int q = threadIdx.x; q < ne; q += blockDim.x) {
+            const VT v = update_one(V, nvec, vstride, e0 + q, w[e0 + q], cs);
+            w[e0 + q] = v;
+            ws[q] = v;
+        }
+        __syncthreads();
+        chunk_dots(V, nvec, vstride, ws, ne, e0, a.part2, a.ldv, nch, 0, c);
+    }
+    // a second pass (the decision is the same in every block)
+    if (!grid_barrier(bar, gridDim.x, err)) return;
+    const double hh2 = reduce_partials(a.part2, nvec + 1, nch, a.ldv, 0, sh);
+    const double nu2 = sqrt(fmax(sh[nvec].x - hh2, 0.0));
+    if (book) {
+        double2* col = a.H + (size_t)a.j * (a.m + 1);
+        for (int i = threadIdx.x; i < nvec; i += blockDim.x) col[i] = make_double2(col[i].x + sh[i].x, col[i].y + sh[i].y);
+        finish_column(a, 0, nu2);
+        return;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) cs[i] = from_d2<VT>(sh[i]);
+    __syncthreads();
+    const S sinv = (S)(nu2 > 0.0 ? 1.0 / nu2 : 0.0);
+    for (int q = threadIdx.x; q < ne; q += blockDim.x) {
+        VT v = update_one(V, nvec, vstride, e0 + q, w[e0 + q], cs);
+        v.x *= sinv;
+        v.y *= sinv;
+        vnext[e0 + q] = v;
+    }
+}
+
 // start of a cycle: g = [beta, 0...], res = beta/bnorm, active = res > rtol
 __global__ void cycle_start_kernel(const double* __restrict__ nrm, const double* __restrict__ bnorm,
                                    double2* __restrict__ g, double* __restrict__ res,
@@ -646,6 +770,32 @@ int gm_alloc(emsurf_handle* h, Gm*& gm, int m, int R) {
     EMS_TRY(dev_alloc(h, (void**)&g->part,
                       sizeof(double2) * RR * (mm + 1) * std::max<size_t>(g->nblk, kRedBlocks)));
     EMS_TRY(dev_alloc(h, (void**)&g->part2, sizeof(double2) * RR * (mm + 1) * g->nblk));
+    {
+        // one chunk block per SM but one, plus the bookkeeping block; used only
+        // when the device runs cooperative launches and all blocks fit at once
+        int coop = 0;
+        EMS_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device));
+        const int blocks = std::max(2, h->num_sms);
+        const size_t chunk = (g->n + blocks - 2) / (blocks - 1);
+        for (int t = 0; t < 2 && coop; ++t) {
+            const size_t wsm = chunk * (t ? sizeof(double2) : sizeof(float2));
+            if (wsm > 200 * 1024) continue;
+            int occ = 0;
+            if (t) {
+                EMS_TRY(set_smem_once(arn_step_coop_kernel<double2>, wsm));
+                EMS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, arn_step_coop_kernel<double2>,
+                                                                       kArnThreads, wsm));
+            } else {
+                EMS_TRY(set_smem_once(arn_step_coop_kernel<float2>, wsm));
+                EMS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, arn_step_coop_kernel<float2>,
+                                                                       kArnThreads, wsm));
+            }
+            if (occ * h->num_sms >= blocks) {
+                g->coop_blocks[t] = blocks;
+                g->coop_chunk[t] = (int)chunk;
+            }
+        }
+    }
     EMS_TRY(dev_alloc(h, (void**)&g->nrm, sizeof(double) * RR));
     EMS_TRY(dev_alloc(h, (void**)&g->bnorm, sizeof(double) * RR));
     EMS_TRY(dev_alloc(h, (void**)&g->res, sizeof(double) * RR));
@@ -762,24 +912,42 @@ int gmres_core(emsurf_handle* h, Gm* g, Apply<VT>& A, const VT* b, VT* x, int R,
                 EMS_TRY(A(Vj, K.w, R, st));
             }
             // classical Gram-Schmidt with the DGKS second pass, H[j+1][j] and
-            // the Givens update: 2 kernels, a third one after a second pass
-            const size_t wsm = (size_t)g->chunk * sizeof(VT);
-            EMS_TRY(set_smem_once(arn_dots_kernel<VT>, wsm));
-            EMS_TRY(set_smem_once(arn_update_kernel<VT>, wsm));
+            // the Givens update: one cooperative launch for a single rhs (all
+            // blocks resident), else 2 kernels and a third after a second pass
             const ArnStep as{g->H, g->cs, g->sn, g->g, g->bnorm, g->res, g->active, g->jend, g->nrm,
                              g->reorth, g->part, g->part2, m, j, m + 1, g->nblk, rtol};
             VT* vnext = K.V + (size_t)(j + 1) * vstride;
             prof_mark(h, EMS_PH_ARNOLDI, true, st);
-            arn_dots_kernel<VT><<<dim3(g->nblk, R), kArnThreads, wsm, st>>>(K.V, vstride, K.w, n, g->chunk, as);
-            EMS_CUDA(cudaGetLastError());
-            arn_update_kernel<VT><<<dim3(g->nblk + 1, R), kArnThreads, wsm, st>>>(K.V, vstride, K.w, vnext, n,
-                                                                                 g->chunk, as);
-            EMS_CUDA(cudaGetLastError());
-            arn_reorth_kernel<VT><<<dim3(g->nblk + 1, R), kArnThreads, 0, st>>>(K.V, vstride, K.w, vnext, n,
-                                                                               g->chunk, as);
-            EMS_CUDA(cudaGetLastError());
+            constexpr int ti = sizeof(VT) == sizeof(double2) ? 1 : 0;
+            if (R == 1 && h->coop_ok && g->coop_blocks[ti] > 0) {
+                ArnStep ac = as;
+                ac.nch = g->coop_blocks[ti] - 1;
+                const VT* Vc = K.V;
+                VT* wc = K.w;
+                size_t nn = n;
+                int ch = g->coop_chunk[ti];
+                unsigned* bar = h->d_grid_bar;
+                int* err = h->d_err;
+                void* args[] = {(void*)&Vc, (void*)&vstride, (void*)&wc, (void*)&vnext, (void*)&nn, (void*)&ch,
+                                (void*)&ac, (void*)&bar, (void*)&err};
+                EMS_CUDA(cudaLaunchCooperativeKernel((const void*)arn_step_coop_kernel<VT>, dim3(g->coop_blocks[ti], 1),
+                                                     dim3(kArnThreads), args, (size_t)ch * sizeof(VT), st));
+                g->launches += 1;
+            } else {
+                const size_t wsm = (size_t)g->chunk * sizeof(VT);
+                EMS_TRY(set_smem_once(arn_dots_kernel<VT>, wsm));
+                EMS_TRY(set_smem_once(arn_update_kernel<VT>, wsm));
+                arn_dots_kernel<VT><<<dim3(g->nblk, R), kArnThreads, wsm, st>>>(K.V, vstride, K.w, n, g->chunk, as);
+                EMS_CUDA(cudaGetLastError());
+                arn_update_kernel<VT><<<dim3(g->nblk + 1, R), kArnThreads, wsm, st>>>(K.V, vstride, K.w, vnext, n,
+                                                                                     g->chunk, as);
+                EMS_CUDA(cudaGetLastError());
+                arn_reorth_kernel<VT><<<dim3(g->nblk + 1, R), kArnThreads, 0, st>>>(K.V, vstride, K.w, vnext, n,
+                                                                                   g->chunk, as);
+                EMS_CUDA(cudaGetLastError());
+                g->launches += 3;
+            }
             prof_mark(h, EMS_PH_ARNOLDI, false, st);
-            g->launches += 3;
             ++it;
             // the convergence flags of step j are copied to pinned memory behind
             // its kernels; the host reads those of step j - 1 while step j runs,

@@ -155,6 +155,9 @@ int run_job(emsurf_server* sv, Job& jb, cudaStream_t st) {
             p.precond_overlap = q.precond_overlap;
         }
         if (!s) s = emsurf_create(&p, &hd);
+        // solves of several requests overlap on the device, so their Arnoldi
+        // steps must not rely on every block of a launch being resident
+        if (!s) hd->coop_ok = false;
     }
     cudaFree(L);
     cudaFree(Kt);
