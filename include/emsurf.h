@@ -209,11 +209,13 @@ EMSURF_API int emsurf_profile_read(emsurf_handle* h, int32_t phase, double* tota
  * before it returns.                                                      */
 EMSURF_API int emsurf_check(emsurf_handle* h);
 
-/* Self-test of the bounded-wait path (no counterpart in the paper): one
- * kernel waits on an mbarrier that nothing arrives on, at most `limit`
- * polls (1..2^22), then sets the handle's error flag exactly as the bin
- * multiply's waits do on expiry.  The next emsurf_check returns ETIMEDOUT
- * and clears the flag.  Nothing faults or hangs.                          */
+/* Self-test of the bounded-wait paths (no counterpart in the paper): one
+ * kernel waits on an mbarrier that nothing arrives on, another at a grid
+ * barrier for a block that is never launched, each at most `limit` polls
+ * (1..2^22); on expiry they set the handle's error flag exactly as the bin
+ * multiply's and the cooperative Arnoldi step's waits do.  The next
+ * emsurf_check returns ETIMEDOUT and clears the flag and the barrier
+ * state.  Nothing faults or hangs.                                        */
 EMSURF_API int emsurf_selftest_wait(emsurf_handle* h, int64_t limit, void* stream);
 
 /* Number of CUDA kernels this handle has launched since creation.        */

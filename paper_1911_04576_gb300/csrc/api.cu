@@ -445,7 +445,8 @@ EMSURF_API int emsurf_selftest_wait(emsurf_handle* h, int64_t limit, void* strea
         return EMSURF_EINVAL;
     }
     DeviceGuard dg(h->device);
-    return wait_selftest(h, (long long)limit, reinterpret_cast<cudaStream_t>(stream));
+    EMS_TRY(wait_selftest(h, (long long)limit, reinterpret_cast<cudaStream_t>(stream)));
+    return grid_barrier_selftest(h, (long long)limit, reinterpret_cast<cudaStream_t>(stream));
 }
 
 EMSURF_API int emsurf_launch_count(const emsurf_handle* h, int64_t* launches) {

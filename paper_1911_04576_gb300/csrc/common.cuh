@@ -289,6 +289,7 @@ template <typename T2>
 int build_operator(emsurf_handle* h, Operator<T2>& op, const emsurf_problem* pr);
 int derive_fp32_operator(emsurf_handle* h, const emsurf_problem* pr);
 int clear_wait_error(emsurf_handle* h);
+int grid_barrier_selftest(emsurf_handle* h, long long limit, cudaStream_t st);
 template <typename T2>
 int apply_operator(emsurf_handle* h, Operator<T2>& op, const double2* x, double2* y, int nrhs,
                    cudaStream_t st);

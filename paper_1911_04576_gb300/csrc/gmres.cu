@@ -486,7 +486,8 @@ arn_reorth_kernel(const VT* __restrict__ V, size_t vstride, const VT* __restrict
 // expiry *err = 4 and false is returned, and the caller's block leaves).
 constexpr long long kBarLimit = 1LL << 22;
 
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* err) {
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* err,
+                                             long long limit = kBarLimit) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -500,7 +501,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, in
             ok = 1;
         } else {
             ok = 0;
-            for (long long it = 0; it < kBarLimit; ++it) {
+            for (long long it = 0; it < limit; ++it) {
                 if (*gen != g0) {
                     ok = 1;
                     break;
@@ -596,6 +597,12 @@ arn_step_coop_kernel(const VT* __restrict__ V, size_t vstride, VT* __restrict__ 
         v.y *= sinv;
         vnext[e0 + q] = v;
     }
+}
+
+// Exercises the expiry path of grid_barrier: one block waits for a second
+// block that is never launched, at most `limit` polls.
+__global__ void grid_barrier_selftest_kernel(unsigned* bar, int* err, long long limit) {
+    grid_barrier(bar, 2u, err, limit);
 }
 
 // start of a cycle: g = [beta, 0...], res = beta/bnorm, active = res > rtol
@@ -997,6 +1004,13 @@ int true_residual(emsurf_handle* h, Gm* g, Apply<double2>& A, const double2* b, 
 }
 
 }  // namespace
+
+int grid_barrier_selftest(emsurf_handle* h, long long limit, cudaStream_t st) {
+    grid_barrier_selftest_kernel<<<1, 32, 0, st>>>(h->d_grid_bar, h->d_err, limit);
+    EMS_CUDA(cudaGetLastError());
+    h->launches += 1;
+    return EMSURF_OK;
+}
 
 int gmres_solve(emsurf_handle* h, const double2* b, double2* x, int R, const emsurf_solve_opts* o,
                 emsurf_solve_info* info, cudaStream_t st) {

@@ -143,9 +143,10 @@ def test_invalid_calls_rejected(emsurf_lib):
 
 
 def test_bounded_wait_expiry_is_reported(emsurf_lib):
-    """A device wait that nothing satisfies gives up after its limit, the
-    host reads ETIMEDOUT once, and the context stays usable (the product
-    afterwards is still exact)."""
+    """Device waits that nothing satisfies (an mbarrier wait and a grid
+    barrier) give up after their limit, the host reads ETIMEDOUT once, and
+    the context stays usable (the product afterwards is still exact, a solve
+    afterwards runs)."""
     from paper_1911_04576_gb300 import binding as B
     E, idx, sgn, nu, Lt, Kt, Z, tmap = random_case(2, 3, 2, 2, 77)
     h = B.emsurf_create(3, 2, E, nu, tmap, Z, Lt, Kt, COEF, idx, sgn, precision=B.MIXED)
@@ -161,6 +162,13 @@ def test_bounded_wait_expiry_is_reported(emsurf_lib):
     B.emsurf_check(h)
     with pytest.raises(B.EmsurfError):
         B.emsurf_selftest_wait(h, 0)        # limit outside [1, 2^22]
+    # the grid barrier of the cooperative Arnoldi step was reset with the
+    # flag: a solve afterwards runs its steps to the end without expiry
+    import torch
+    b = torch.from_numpy(W.random_vectors(1, nu, 79)).cuda()
+    st, info = B.emsurf_solve(h, b, torch.zeros_like(b), rtol=1e-10, restart=8, max_iters=16, max_refine=2)
+    assert st in (B.EMSURF_OK, B.EMSURF_ENOTCONV) and info[0]["iters"] > 0
+    B.emsurf_check(h)
     h.close()
 
 
