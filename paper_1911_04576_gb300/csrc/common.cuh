@@ -11,7 +11,7 @@
 
 namespace emsurf {
 
-constexpr int kMmGroup = 8;   // cells of one type per macromodel CTA
+constexpr int kMmGroup = 4;   // cells of one type per macromodel CTA
 
 // ---------------------------------------------------------------- errors
 void set_error(const char* fmt, ...);

@@ -736,9 +736,9 @@ __global__ void macromodel_kernel(const T2* __restrict__ Zt, const double2* __re
 // Single-rhs FP32 variant: each thread owns two adjacent output rows and
 // keeps eight 16-byte loads of Z in flight (the one-row kernel is bound by
 // load latency at one rhs); the staged x1 is read two columns at a time.
-constexpr int kMm2Unroll = 4;   // 16-byte loads per buffer (two blocks of 320 threads per SM)
+constexpr int kMm2Unroll = 4;   // 16-byte loads per buffer (three blocks of 320 threads per SM)
 template <int G>
-__global__ void __launch_bounds__(320, 2)
+__global__ void __launch_bounds__(320, 3)
 macromodel2_kernel(const float2* __restrict__ Zt, const double2* __restrict__ x,
                    const int32_t* __restrict__ idx, const int8_t* __restrict__ sgn,
                    const int32_t* __restrict__ type_cells, const MmBlock* __restrict__ blocks,
