@@ -414,16 +414,17 @@ pc_apply_kernel(const __half2* __restrict__ X, const float* __restrict__ rscale,
 // cell by cell: it gathers the cell's r segment straight from r into shared
 // memory (FP32, zero past n_m up to ld_m), then each warp takes two rows at a
 // time (16-byte loads of the FP16 rows, kApSegLoads per row and lane in
-// flight) and reduces both rows' sums with one reduce-scatter.
+// flight: all of a row of up to 1024 entries in one round) and reduces both
+// rows' sums with one reduce-scatter.
 constexpr int kApSegThreads = 256;
 constexpr int kApSegMaxLd = 1024;   // longest row (complex entries) of this kernel
-constexpr int kApSegLoads = 4;
+constexpr int kApSegLoads = 8;      // 16-byte row loads per row and lane in flight (a whole row of up to 1024)
 
 template <typename VT>
 __device__ __forceinline__ float2 to_f2(VT v) { return make_float2((float)v.x, (float)v.y); }
 
 template <int RQ, typename VT>
-__global__ void __launch_bounds__(kApSegThreads, RQ == 1 ? 4 : 3)
+__global__ void __launch_bounds__(kApSegThreads, RQ == 1 ? 3 : 2)
 pc_apply_seg_kernel(const __half2* __restrict__ X, const float* __restrict__ rscale,
                     const int64_t* __restrict__ xoff, const int32_t* __restrict__ ldx,
                     const int32_t* __restrict__ own_ptr, const int32_t* __restrict__ sub_ptr,
