@@ -47,7 +47,7 @@ PC_OVERLAP = 0.6               # preconditioner margin, in mesh cells (a / n)
 BINMUL_DRAM_BYTES_PER_BIN = (767108096 + 5353216) / 576
 # the same for binmul_tma_pair_kernel (half spectrum) per stored bin, from
 # profiles/binmul_tma_pair_lattice12x12_k576.md (290 stored bins)
-PAIR_DRAM_BYTES_PER_STORED_BIN = (389593600 + 5169408) / 290
+PAIR_DRAM_BYTES_PER_STORED_BIN = (387588096 + 3930624) / 290
 
 
 FALLBACK_BF16_TFLOPS = 1900.0
