@@ -10,7 +10,8 @@ step by step, in plain NumPy/SciPy, without blocking, fusion or FFTs:
 
 * ``quadrature``  -- triangle quadrature and closed-form potential integrals
                      used for singularity extraction (the paper is silent on
-                     quadrature; see the readings in the design doc).
+                     quadrature: 7-point Radon rule plus closed-form 1/R and
+                     grad 1/R parts over the source triangle).
 * ``mesh``        -- box surface S_eq and patch meshes, RWG bases (Sec. II-A,
                      Eqs. Hdiscretebox/Ediscretebox).
 * ``operators``   -- Galerkin L and K blocks (Eqs. SIE_LOperator1,

@@ -14,7 +14,7 @@ Follows the paper's steps for a cell whose interior is one homogeneous region
    solved with LU.
 
 Reading: the configurations' eps_r = 3 slab is not modelled; the patch sits
-in free space at the slab-top height (listed in the design doc).
+in free space at the slab-top height.
 
 Pins: empty box reproduces the incident-field currents (physics test);
 PEC patch obeys the optical theorem (lossless) and reciprocity

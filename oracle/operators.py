@@ -1,6 +1,6 @@
 """Galerkin L and K operators, plane-wave excitation and far field (oracle).
 
-Readings of the paper used here (listed in the design doc):
+Readings of the paper used here:
 
 * time convention e^{jwt}, Green's function G = e^{-jkR} / (4 pi R);
 * L[m,n] = int int [Lam_m . Lam_n - (div Lam_m)(div' Lam_n)/k^2] G dS' dS,
