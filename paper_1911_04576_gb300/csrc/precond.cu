@@ -560,7 +560,7 @@ int launch_apply_seg(emsurf_handle* h, const VT* r, VT* y, cudaStream_t st) {
 
 template <int RQ, typename VO>
 int launch_apply(emsurf_handle* h, VO* y, int r0, int nr, cudaStream_t st) {
-    // resident blocks per SM (the same for every device of this build)
+    // resident blocks per SM (computed once; the library is compiled for one architecture)
     static int occ[9][2] = {};
     int& o = occ[RQ][sizeof(VO) == sizeof(float2) ? 1 : 0];
     if (!o) {
