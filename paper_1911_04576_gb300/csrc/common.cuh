@@ -203,6 +203,10 @@ struct emsurf_handle {
     int nst = 0;
     int32_t* d_st_bin = nullptr;
     int32_t* d_st_part = nullptr;
+    // FP64-accuracy single-rhs bin multiply from FP32 hi/lo pairs: spectrum
+    // planes [bin][hi, lo][op][j][i] and the split X^ [bin][hi, lo][2E]
+    float2* ds_planes = nullptr;
+    float2* ds_x = nullptr;
     int pair_grid = 0;                // CTAs of the pair kernel (equal slab ranges)
     float2* d_pair_part = nullptr;    // partial row sums of straddling bins [cta][2][2E]
     int* d_pair_cnt = nullptr;        // arrival counters [stored bin][row warp]
@@ -289,6 +293,7 @@ template <typename T2>
 int build_operator(emsurf_handle* h, Operator<T2>& op, const emsurf_problem* pr);
 int derive_fp32_operator(emsurf_handle* h, const emsurf_problem* pr);
 int clear_wait_error(emsurf_handle* h);
+int build_ds_planes(emsurf_handle* h);
 int grid_barrier_selftest(emsurf_handle* h, long long limit, cudaStream_t st);
 template <typename T2>
 int apply_operator(emsurf_handle* h, Operator<T2>& op, const double2* x, double2* y, int nrhs,

@@ -338,6 +338,169 @@ size_t binmul_tma_smem(int E) {
            2ull * kBmStages * sizeof(uint64_t);
 }
 
+// ------------------------------------------------ K2, FP64 accuracy from FP32 arithmetic, one rhs
+// The FP64 bin multiply is bound by this part's FP64 rate (~1/60 of FP32).
+// Here every FP64 value v is held as a pair of floats, hi = rn(v) and
+// lo = rn(v - hi) (|v - hi - lo| <= 2^-48 |v|), and each complex product is
+// accumulated in double-single arithmetic: the rounding error of hi*hi is
+// recovered exactly with an FMA, the cross terms hi*lo + lo*hi are added to
+// it, and the partial sums are pairs (s, c) updated with Knuth's TwoSum, so
+// each product term carries a relative error of a few 2^-48 (the lo*lo term,
+// ~2^-48, is dropped).  The row sums are turned into FP64 at the end.  The
+// spectrum planes hold the same bytes as the FP64 spectrum; one thread per
+// test row as in binmul_tma_kernel, kDsJB-column slabs (hi and lo of L^ and
+// K^) in a kDsStages-deep ring fed by bulk copies.
+constexpr int kDsJB = 6;
+constexpr int kDsStages = 3;
+
+// (hi, lo) += (ah + al)(bh + bl); no operation is contracted or reassociated
+__device__ __forceinline__ void ds_mac(float& hi, float& lo, float ah, float al, float bh, float bl) {
+    const float p = __fmul_rn(ah, bh);
+    float e = __fmaf_rn(ah, bh, -p);           // ah bh - p, exactly
+    e = __fmaf_rn(ah, bl, e);
+    e = __fmaf_rn(al, bh, e);
+    const float s = __fadd_rn(hi, p);          // TwoSum(hi, p) = s + t exactly
+    const float bb = __fsub_rn(s, hi);
+    const float t = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    lo = __fadd_rn(lo, __fadd_rn(t, e));
+    hi = s;
+}
+
+struct DsC {   // complex double-single accumulator
+    float rh, rl, ih, il;
+};
+__device__ __forceinline__ void ds_cmac(DsC& a, float2 xh, float2 xl, float2 bh, float2 bl) {
+    ds_mac(a.rh, a.rl, xh.x, xl.x, bh.x, bl.x);
+    ds_mac(a.rh, a.rl, -xh.y, -xl.y, bh.y, bl.y);
+    ds_mac(a.ih, a.il, xh.x, xl.x, bh.y, bl.y);
+    ds_mac(a.ih, a.il, xh.y, xl.y, bh.x, bl.x);
+}
+__device__ __forceinline__ double2 ds_value(const DsC& a) {
+    return make_double2((double)a.rh + (double)a.rl, (double)a.ih + (double)a.il);
+}
+
+// out[b][0][r] = rn(in[b][r]), out[b][1][r] = rn(in[b][r] - out[b][0][r]) for
+// blocks b of `chunk` complex values
+__global__ void split_hilo_kernel(float2* __restrict__ out, const double2* __restrict__ in, size_t chunk,
+                                  size_t total) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t b = e / chunk, r = e - b * chunk;
+        const double2 v = in[e];
+        const float2 hi = make_float2((float)v.x, (float)v.y);
+        const float2 lo = make_float2((float)(v.x - (double)hi.x), (float)(v.y - (double)hi.y));
+        out[b * 2 * chunk + r] = hi;
+        out[b * 2 * chunk + chunk + r] = lo;
+    }
+}
+
+// planes: [bin][hi, lo][op][j][i] float2; xs: [bin][hi, lo][2E]; Yh: [bin][2E] FP64
+__global__ void binmul_ds_kernel(const float2* __restrict__ planes, const float2* __restrict__ xs,
+                                 double2* __restrict__ Yh, int E, int nbins, double2 ca, double2 cb,
+                                 double2 cg, double2 cd, int* __restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int stage_elems = 4 * kDsJB * E;      // [hi, lo][L, K][kDsJB][E]
+    float2* sbuf = reinterpret_cast<float2*>(smem_raw);
+    float2* xbuf = sbuf + (size_t)kDsStages * stage_elems;      // [2 buffers][hi, lo][2E]
+    uint64_t* full = reinterpret_cast<uint64_t*>(xbuf + 8 * E);
+    uint64_t* empty = full + kDsStages;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ncw = (E + 31) / 32;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kDsStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], ncw);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    const int nloc = (nbins - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int nj = (E + kDsJB - 1) / kDsJB;
+    const long long total = (long long)nloc * nj;
+    const size_t EE = (size_t)E * E;
+    if (warp == 0) {
+        if (lane != 0) return;
+        const uint64_t pol = l2_evict_first();
+        const uint32_t bytes_x = (uint32_t)(4 * E * sizeof(float2));
+        int s = 0, jb = 0, t = 0;
+        uint32_t ph = 0;
+        long long issued = 0;
+        bool ok = true;
+        for (long long q = 0; q < total; ++q) {
+            if (q >= kDsStages && !mbar_wait(&empty[s], ph ^ 1u)) {
+                ok = false;
+                break;
+            }
+            const int bin = (int)blockIdx.x + t * (int)gridDim.x;
+            const int j0 = jb * kDsJB, jn = min(kDsJB, E - j0);
+            const uint32_t bytes_op = (uint32_t)(jn * E * sizeof(float2));
+            mbar_expect_tx(&full[s], 4 * bytes_op + (jb == 0 ? bytes_x : 0u));
+            float2* dst = sbuf + (size_t)s * stage_elems;
+            for (int pl = 0; pl < 2; ++pl)
+                for (int o = 0; o < 2; ++o)
+                    bulk_g2s_hint(dst + (pl * 2 + o) * kDsJB * E,
+                                  planes + (((size_t)bin * 2 + pl) * 2 + o) * EE + (size_t)j0 * E, bytes_op,
+                                  &full[s], pol);
+            if (jb == 0) bulk_g2s(xbuf + (t & 1) * 4 * E, xs + (size_t)bin * 4 * E, bytes_x, &full[s]);
+            issued = q + 1;
+            if (++s == kDsStages) { s = 0; ph ^= 1u; }
+            if (++jb == nj) { jb = 0; ++t; }
+        }
+        if (!ok) {
+            atomicExch(err, 1);
+            for (long long u = (issued > kDsStages ? issued - kDsStages : 0); u < issued; ++u)
+                mbar_wait(&full[u % kDsStages], (uint32_t)((u / kDsStages) & 1));
+        }
+        return;
+    }
+    const int i = (warp - 1) * 32 + lane;
+    DsC lj{0.f, 0.f, 0.f, 0.f}, lm = lj, kj = lj, km = lj;
+    int s = 0, jb = 0, t = 0;
+    uint32_t ph = 0;
+    for (long long q = 0; q < total; ++q) {
+        if (!mbar_wait(&full[s], ph)) {
+            atomicExch(err, 1);
+            return;
+        }
+        const float2* S = sbuf + (size_t)s * stage_elems;
+        const float2* X = xbuf + (t & 1) * 4 * E;       // [hi, lo][2E]
+        const int j0 = jb * kDsJB, jn = min(kDsJB, E - j0);
+        if (i < E) {
+#pragma unroll
+            for (int jj = 0; jj < kDsJB; ++jj) {
+                if (jj < jn) {
+                    const float2 lh = S[(0 * kDsJB + jj) * E + i], kh = S[(1 * kDsJB + jj) * E + i];
+                    const float2 ll = S[(2 * kDsJB + jj) * E + i], kl = S[(3 * kDsJB + jj) * E + i];
+                    const float2 xjh = X[j0 + jj], xmh = X[E + j0 + jj];
+                    const float2 xjl = X[2 * E + j0 + jj], xml = X[3 * E + j0 + jj];
+                    ds_cmac(lj, xjh, xjl, lh, ll);
+                    ds_cmac(lm, xmh, xml, lh, ll);
+                    ds_cmac(kj, xjh, xjl, kh, kl);
+                    ds_cmac(km, xmh, xml, kh, kl);
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+        if (jb == nj - 1) {
+            if (i < E) {
+                const int bin = (int)blockIdx.x + t * (int)gridDim.x;
+                double2* Y = Yh + (size_t)bin * 2 * E;
+                Y[i] = cadd(cmul(ca, ds_value(lj)), cmul(cb, ds_value(km)));
+                Y[E + i] = cadd(cmul(cg, ds_value(kj)), cmul(cd, ds_value(lm)));
+            }
+            lj = lm = kj = km = DsC{0.f, 0.f, 0.f, 0.f};
+        }
+        if (++s == kDsStages) { s = 0; ph ^= 1u; }
+        if (++jb == nj) { jb = 0; ++t; }
+    }
+}
+
+size_t binmul_ds_smem(int E) {
+    return (size_t)kDsStages * 4 * kDsJB * E * sizeof(float2) + 8ull * E * sizeof(float2) +
+           2ull * kDsStages * sizeof(uint64_t);
+}
+
 // ------------------------------------------------ K2, FP32, one rhs, half spectrum
 // With reciprocal tables L^(-k) = L^(k)^T and K^(-k) = K^(k)^T, so only one
 // bin k of each pair (k, -k) is stored and its blocks serve both:
@@ -1026,6 +1189,24 @@ int derive_fp32_operator(emsurf_handle* h, const emsurf_problem* pr) {
     return EMSURF_OK;
 }
 
+// FP32 hi/lo planes of the FP64 spectrum for binmul_ds_kernel (single-rhs
+// handles; left out, and the FP64 kernel used, when the kernel's shape does
+// not fit or the device-memory budget has no room for them).
+int build_ds_planes(emsurf_handle* h) {
+    const int E = h->E;
+    const int ncw = (E + 31) / 32;
+    if (binmul_ds_smem(E) > 227 * 1024 || 32 * (1 + ncw) > 1024 || (E + kDsJB - 1) / kDsJB < kDsStages)
+        return EMSURF_OK;
+    const size_t nb = (size_t)h->nbins, EE = (size_t)E * E;
+    const size_t pbytes = nb * 2 * 2 * EE * sizeof(float2), xbytes = nb * 2 * 2 * E * sizeof(float2);
+    if (h->budget > 0 && h->device_bytes + (int64_t)(pbytes + xbytes) > h->budget) return EMSURF_OK;
+    EMS_TRY(dev_alloc(h, (void**)&h->ds_planes, pbytes));
+    EMS_TRY(dev_alloc(h, (void**)&h->ds_x, xbytes));
+    split_hilo_kernel<<<152 * 16, 256, 0, h->setup_stream>>>(h->ds_planes, h->op64.Bhat, 2 * EE, nb * 2 * EE);
+    EMS_CUDA(cudaGetLastError());
+    return EMSURF_OK;
+}
+
 // ---------------------------------------------------------------- apply
 template <typename T2>
 int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, const float2* xf,
@@ -1170,6 +1351,23 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
                 op.Bhat, op.Xg, op.Yg, E, nb, op.coef[0], op.coef[1], op.coef[2], op.coef[3], h->d_err);
             EMS_CUDA(cudaGetLastError());
             h->launches += 1;
+            bin_done = true;
+        }
+    }
+    if constexpr (std::is_same<T2, double2>::value) {
+        if (!bin_done && R == 1 && h->ds_planes) {
+            // FP64 accuracy from FP32 hi/lo arithmetic (the FP64 rate is ~1/60 of FP32)
+            const size_t lanes2 = (size_t)2 * E;
+            split_hilo_kernel<<<grid_for((size_t)nb * lanes2, 256), 256, 0, st>>>(h->ds_x, op.Xg, lanes2,
+                                                                                (size_t)nb * lanes2);
+            EMS_CUDA(cudaGetLastError());
+            const size_t smem = binmul_ds_smem(E);
+            EMS_TRY(set_smem_once(binmul_ds_kernel, smem));
+            const int grid = std::min(nb, std::max(1, h->num_sms));
+            binmul_ds_kernel<<<grid, 32 * (1 + (E + 31) / 32), smem, st>>>(
+                h->ds_planes, h->ds_x, op.Yg, E, nb, op.coef[0], op.coef[1], op.coef[2], op.coef[3], h->d_err);
+            EMS_CUDA(cudaGetLastError());
+            h->launches += 2;
             bin_done = true;
         }
     }
