@@ -214,3 +214,22 @@ def test_half_spectrum_parity(emsurf_lib, n, nx, ny, grid):
     B.emsurf_check(h)
     h.close()
     h2.close()
+
+
+@pytest.mark.parametrize("n,nx,ny", [(2, 3, 2), (3, 2, 3)])
+def test_fp64_single_rhs_double_single(emsurf_lib, n, nx, ny):
+    """Single-rhs handles take the FP64 bin multiply in double-single FP32
+    arithmetic (hi/lo planes, exact product errors, TwoSum sums): each product
+    term carries a few 2^-48 of relative error, so the FP64 product meets a
+    bar 100x below the FP64 path's 1e-10 (1e-12 rel-L2 against the oracle),
+    for one rhs and, on a two-rhs handle (the FP64 kernel), alike."""
+    from paper_1911_04576_gb300 import binding as B
+    seed = 900 + 10 * nx + ny
+    E, idx, sgn, nu, Lt, Kt, Z, tmap = random_case(n, nx, ny, 2, seed)
+    x = W.random_vectors(1, nu, seed + 3)
+    yref = lattice.matvec_direct(x, Lt, Kt, COEF, Z, tmap, idx, sgn, nu, nx, ny)
+    for R in (1, 2):
+        h = B.emsurf_create(nx, ny, E, nu, tmap, Z, Lt, Kt, COEF, idx, sgn, precision=B.MIXED, max_rhs=R)
+        assert relerr(run_matvec(B, h, x, B.FP64)[0], yref[0]) <= 1e-12
+        B.emsurf_check(h)
+        h.close()
