@@ -207,6 +207,7 @@ struct emsurf_handle {
     // planes [bin][hi, lo][op][j][i] and the split X^ [bin][hi, lo][2E]
     float2* ds_planes = nullptr;
     float2* ds_x = nullptr;
+    float2* ds_zt = nullptr;          // the macromodels as hi/lo planes [t][hi, lo][k'][k]
     int pair_grid = 0;                // CTAs of the pair kernel (equal slab ranges)
     float2* d_pair_part = nullptr;    // partial row sums of straddling bins [cta][2][2E]
     int* d_pair_cnt = nullptr;        // arrival counters [stored bin][row warp]

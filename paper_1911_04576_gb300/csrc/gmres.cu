@@ -663,12 +663,15 @@ __device__ void givens_update(int r, double2* __restrict__ col, double2* __restr
     if (res[r] <= rtol || den == 0.0) active[r] = 0;
 }
 
-// y = H[0:jend,0:jend]^{-1} g[0:jend] by back substitution: one block per
-// rhs stages its triangle and g in shared memory, then one thread solves
+// y = H[0:jend,0:jend]^{-1} g[0:jend] by back substitution, column by column:
+// one block per rhs stages its triangle in shared memory, then one warp runs
+// k = n-1 .. 0: the lane holding g_k forms y_k = g_k / H[k][k] and
+// broadcasts it, and every lane updates its g_i -= H[i][k] y_k (i < k; lanes
+// hold i and i + 32), so each step is one division, one shuffle and one
+// independent complex multiply-add per lane.
 __global__ void trisolve_kernel(const double2* __restrict__ H, const double2* __restrict__ g,
                                 double2* __restrict__ y, const int* __restrict__ jend, int m, int R) {
     __shared__ double2 sH[64 * 65 / 2];   // column k rows 0..k at k (k + 1) / 2
-    __shared__ double2 sg[65];
     const int r = blockIdx.x;
     if (r >= R) return;
     const int n = jend[r];
@@ -677,24 +680,35 @@ __global__ void trisolve_kernel(const double2* __restrict__ H, const double2* __
         const int k = e / (m + 1), i = e % (m + 1);
         if (i <= k) sH[k * (k + 1) / 2 + i] = Hr[e];
     }
-    for (int e = threadIdx.x; e < n; e += blockDim.x) sg[e] = g[(size_t)r * (m + 1) + e];
     __syncthreads();
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    double2 ga = lane < n ? g[(size_t)r * (m + 1) + lane] : make_double2(0.0, 0.0);
+    double2 gb = lane + 32 < n ? g[(size_t)r * (m + 1) + lane + 32] : make_double2(0.0, 0.0);
     double2* yr = y + (size_t)r * (m + 1);
-    for (int i = n - 1; i >= 0; --i) {
-        double2 acc = sg[i];
-        for (int k = i + 1; k < n; ++k) {
-            const double2 hk = sH[k * (k + 1) / 2 + i];
-            const double2 yk = sg[k];   // holds y[k] once solved
-            acc.x -= hk.x * yk.x - hk.y * yk.y;
-            acc.y -= hk.x * yk.y + hk.y * yk.x;
+    for (int k = n - 1; k >= 0; --k) {
+        const int owner = k & 31;
+        double2 yk = make_double2(0.0, 0.0);
+        if (lane == owner) {
+            const double2 gk = k < 32 ? ga : gb;
+            const double2 d = sH[k * (k + 1) / 2 + k];
+            const double dd = d.x * d.x + d.y * d.y;
+            if (dd > 0.0) yk = make_double2((gk.x * d.x + gk.y * d.y) / dd, (gk.y * d.x - gk.x * d.y) / dd);
+            yr[k] = yk;
         }
-        const double2 d = sH[i * (i + 1) / 2 + i];
-        const double dd = d.x * d.x + d.y * d.y;
-        const double2 yi = dd > 0.0 ? make_double2((acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd)
-                                    : make_double2(0.0, 0.0);
-        sg[i] = yi;
-        yr[i] = yi;
+        yk.x = __shfl_sync(0xffffffffu, yk.x, owner);
+        yk.y = __shfl_sync(0xffffffffu, yk.y, owner);
+        const double2* col = sH + k * (k + 1) / 2;
+        if (lane < k) {
+            const double2 h = col[lane];
+            ga.x -= h.x * yk.x - h.y * yk.y;
+            ga.y -= h.x * yk.y + h.y * yk.x;
+        }
+        if (lane + 32 < k) {
+            const double2 h = col[lane + 32];
+            gb.x -= h.x * yk.x - h.y * yk.y;
+            gb.y -= h.x * yk.y + h.y * yk.x;
+        }
     }
 }
 

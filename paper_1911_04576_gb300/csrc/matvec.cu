@@ -979,6 +979,75 @@ macromodel2_kernel(const float2* __restrict__ Zt, const double2* __restrict__ x,
     }
 }
 
+// Single-rhs FP64-accuracy variant in double-single FP32 arithmetic (see
+// binmul_ds_kernel): Z~ as FP32 hi/lo planes zp[t][hi, lo][k'][k], x1 split
+// into hi/lo while it is gathered, each thread two output rows for up to G
+// cells, products accumulated with ds_cmac, FP64 partial outputs.
+constexpr int kMmDsUnroll = 2;
+template <int G>
+__global__ void __launch_bounds__(320, 2)
+macromodel_ds_kernel(const float2* __restrict__ zp, const double2* __restrict__ x,
+                     const int32_t* __restrict__ idx, const int8_t* __restrict__ sgn,
+                     const int32_t* __restrict__ type_cells, const MmBlock* __restrict__ blocks,
+                     double2* __restrict__ Ymm, int K, int M, int chunk) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* xh = reinterpret_cast<float2*>(smem_raw);   // [G][chunk] hi
+    float2* xl = xh + (size_t)G * chunk;                // [G][chunk] lo
+    const MmBlock b = blocks[blockIdx.x];
+    const int s = blockIdx.y;
+    const int k0 = s * chunk, k1 = min(K, k0 + chunk), nk = k1 - k0;
+    for (int e = threadIdx.x; e < G * chunk; e += blockDim.x) {
+        const int g = e / chunk, kk = e % chunk;
+        double2 v = make_double2(0.0, 0.0);
+        if (g < b.count && kk < nk) {
+            const size_t loc = (size_t)type_cells[b.first + g] * K + k0 + kk;
+            const double2 xv = x[idx[loc]];
+            const double sg = (double)sgn[loc];
+            v = make_double2(sg * xv.x, sg * xv.y);
+        }
+        const float2 hi = make_float2((float)v.x, (float)v.y);
+        xh[e] = hi;
+        xl[e] = make_float2((float)(v.x - (double)hi.x), (float)(v.y - (double)hi.y));
+    }
+    __syncthreads();
+    const int K2 = K >> 1;
+    const size_t KK = (size_t)K * K;
+    const float4* Zh = reinterpret_cast<const float4*>(zp + (size_t)b.type * 2 * KK + (size_t)k0 * K);
+    const float4* Zl = reinterpret_cast<const float4*>(zp + ((size_t)b.type * 2 + 1) * KK + (size_t)k0 * K);
+    for (int k2 = threadIdx.x; k2 < K2; k2 += blockDim.x) {
+        DsC a0[G], a1[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) a0[g] = a1[g] = DsC{0.f, 0.f, 0.f, 0.f};
+        for (int kb = 0; kb < nk; kb += kMmDsUnroll) {
+            float4 zh[kMmDsUnroll], zl[kMmDsUnroll];
+#pragma unroll
+            for (int u = 0; u < kMmDsUnroll; ++u) {
+                const bool in = kb + u < nk;
+                zh[u] = in ? __ldg(Zh + (size_t)(kb + u) * K2 + k2) : make_float4(0.f, 0.f, 0.f, 0.f);
+                zl[u] = in ? __ldg(Zl + (size_t)(kb + u) * K2 + k2) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < kMmDsUnroll; ++u) {
+                if (kb + u < nk) {
+#pragma unroll
+                    for (int g = 0; g < G; ++g) {
+                        const float2 vh = xh[g * chunk + kb + u], vl = xl[g * chunk + kb + u];
+                        ds_cmac(a0[g], vh, vl, make_float2(zh[u].x, zh[u].y), make_float2(zl[u].x, zl[u].y));
+                        ds_cmac(a1[g], vh, vl, make_float2(zh[u].z, zh[u].w), make_float2(zl[u].z, zl[u].w));
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            if (g < b.count) {
+                double2* y = Ymm + ((size_t)s * M + type_cells[b.first + g]) * K + 2 * k2;
+                y[0] = ds_value(a0[g]);
+                y[1] = ds_value(a1[g]);
+            }
+    }
+}
+
 // ------------------------------------------------ K3 tail: U_o^T
 // y[r][u] = sum over local unknowns (m,k) of u: sign * y1[r][m][k]
 // (sums in the grid's precision; V2 is the output vector type)
@@ -1204,6 +1273,13 @@ int build_ds_planes(emsurf_handle* h) {
     EMS_TRY(dev_alloc(h, (void**)&h->ds_x, xbytes));
     split_hilo_kernel<<<152 * 16, 256, 0, h->setup_stream>>>(h->ds_planes, h->op64.Bhat, 2 * EE, nb * 2 * EE);
     EMS_CUDA(cudaGetLastError());
+    // the macromodels likewise (the transposed Z~ of each type)
+    const size_t KK = (size_t)h->K * h->K, zbytes = (size_t)h->T * 2 * KK * sizeof(float2);
+    if ((h->K & 1) == 0 && (h->budget <= 0 || h->device_bytes + (int64_t)zbytes <= h->budget)) {
+        EMS_TRY(dev_alloc(h, (void**)&h->ds_zt, zbytes));
+        split_hilo_kernel<<<152 * 16, 256, 0, h->setup_stream>>>(h->ds_zt, h->op64.Zt, KK, (size_t)h->T * KK);
+        EMS_CUDA(cudaGetLastError());
+    }
     return EMSURF_OK;
 }
 
@@ -1295,6 +1371,26 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
             macromodel2_kernel<kMmGroup><<<dim3(nblk, ns2), threads2, sm, st>>>(
                 op.Zt, x, h->d_uo_index, h->d_uo_sign, h->d_type_cells,
                 reinterpret_cast<const MmBlock*>(h->d_mm_blocks), op.Ymm, K, h->M, h->n_unique, chunk2, xf);
+            EMS_CUDA(cudaGetLastError());
+            nsplit = ns2;
+            mm_done = true;
+        }
+    }
+    if constexpr (std::is_same<T2, double2>::value) {
+        if (!mm_done && R == 1 && h->ds_zt) {
+            // one rhs, FP64 accuracy from double-single FP32 arithmetic
+            const int threads2 = std::min(320, ((K / 2 + 31) / 32) * 32);
+            const int nblk = h->n_mm_blocks;
+            int ns2 = std::max(1, std::min(kMmSplit, K / 64));
+            ns2 = std::max(1, std::min(ns2, h->num_sms * 2 / std::max(1, nblk)));
+            int chunk2 = (K + ns2 - 1) / ns2;
+            chunk2 = (chunk2 + kMmDsUnroll - 1) / kMmDsUnroll * kMmDsUnroll;
+            ns2 = (K + chunk2 - 1) / chunk2;
+            const size_t sm = (size_t)2 * kMmGroup * chunk2 * sizeof(float2);
+            EMS_TRY(set_smem_once(macromodel_ds_kernel<kMmGroup>, sm));
+            macromodel_ds_kernel<kMmGroup><<<dim3(nblk, ns2), threads2, sm, st>>>(
+                h->ds_zt, x, h->d_uo_index, h->d_uo_sign, h->d_type_cells,
+                reinterpret_cast<const MmBlock*>(h->d_mm_blocks), op.Ymm, K, h->M, chunk2);
             EMS_CUDA(cudaGetLastError());
             nsplit = ns2;
             mm_done = true;
