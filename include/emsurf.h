@@ -150,10 +150,15 @@ EMSURF_API int emsurf_matvec(emsurf_handle* h, const emsurf_c128* x, emsurf_c128
                              int32_t nrhs, int32_t precision, void* stream);
 
 /* Solve Eq. final for nrhs right-hand sides b with restarted GMRES on the
- * device (Sec. IV-A; zero initial guess, classical Gram-Schmidt applied
- * twice, Givens rotations, FP64 Krylov vectors).  x: device output.
+ * device (Sec. IV-A; zero initial guess, classical Gram-Schmidt with a
+ * second pass when ||w'|| < ||w|| / sqrt 10, Givens rotations; FP64 Krylov
+ * vectors, FP32 ones inside the MIXED refinement).  x: device output.
  * info: host array [nrhs] or NULL.  Returns ENOTCONV (x = best iterate) if
- * any right-hand side did not reach rtol within max_iters.              */
+ * any right-hand side did not reach rtol within max_iters.  With one rhs
+ * each Arnoldi step is one cooperative launch whose blocks wait for each
+ * other (bounded): solves of other handles running at the same time on the
+ * device can make those waits expire, which returns ETIMEDOUT instead of
+ * hanging; the server (emsurf_submit) runs its solves without it.        */
 EMSURF_API int emsurf_solve(emsurf_handle* h, const emsurf_c128* b, emsurf_c128* x,
                             int32_t nrhs, const emsurf_solve_opts* opts,
                             emsurf_solve_info* info, void* stream);
