@@ -65,10 +65,11 @@ typedef struct emsurf_handle emsurf_handle;
  *  uo_sign      [nx*ny*K] +1 / -1                                      (host)
  *  grid_px/py   FFT grid; 0 = smallest 2,3,5-smooth >= 2N-1; else >= 2N-1
  *               with no prime factor above 7 (EINVAL otherwise)
- *  max_rhs      largest nrhs later passed to matvec/solve (>= 1).  With 1,
- *               handles holding the FP64 operator also keep its spectrum as
- *               FP32 hi/lo planes (same bytes) for the double-single FP64-
- *               accuracy bin multiply, when device_mem_budget leaves room
+ *  max_rhs      largest nrhs later passed to matvec/solve (>= 1).  Handles
+ *               holding the FP64 operator also keep its spectrum and the
+ *               macromodels as FP32 hi/lo planes (same bytes) for the
+ *               double-single FP64-accuracy kernels, when device_mem_budget
+ *               leaves room
  *  tables_on_device  0: offset_L/K and macromodels are host pointers;
  *                    1: they are device pointers on `device`
  * The handle copies everything it needs; the caller may free the inputs

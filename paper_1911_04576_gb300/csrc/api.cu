@@ -204,7 +204,7 @@ int create_impl(const emsurf_problem* p, emsurf_handle* h) {
         EMS_TRY(derive_fp32_operator(h, p));
         h->have32 = true;
     }
-    if (h->have64 && h->max_rhs == 1) EMS_TRY(build_ds_planes(h));
+    if (h->have64) EMS_TRY(build_ds_planes(h));
     if (p->tensor_cores && h->have32 && h->E >= 64) EMS_TRY(tc_build(h));
     if (p->precond_overlap > 0.0 && p->unknown_xy) {
         if (!(p->cell_a > 0.0) || !(p->cell_b > 0.0)) {

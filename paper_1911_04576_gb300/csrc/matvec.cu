@@ -496,6 +496,64 @@ __global__ void binmul_ds_kernel(const float2* __restrict__ planes, const float2
     }
 }
 
+// Several rhs: RB of them per pass share each load of the hi/lo planes (the
+// register-blocked form of binmul_kernel); X^ is split into hi/lo while it is
+// staged in shared memory.  Compute-bound (about 60 FP32 operations per
+// complex multiply-add), so the planes are streamed once per RB rhs.
+template <int RB>
+__global__ void binmul_ds_multi_kernel(const float2* __restrict__ planes, const double2* __restrict__ Xh,
+                                       double2* __restrict__ Yh, int E, int nbins, int R, int r0,
+                                       double2 ca, double2 cb, double2 cg, double2 cd) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* xh = reinterpret_cast<float2*>(smem_raw);   // [RB][2E] hi
+    float2* xl = xh + (size_t)RB * 2 * E;               // [RB][2E] lo
+    const int K = 2 * E;
+    const size_t EE = (size_t)E * E;
+    for (int bin = blockIdx.x; bin < nbins; bin += gridDim.x) {
+        __syncthreads();
+        const double2* X = Xh + (size_t)bin * R * K;
+        for (int e = threadIdx.x; e < RB * K; e += blockDim.x) {
+            const int r = e / K, k = e - r * K;
+            const double2 v = (r0 + r < R) ? X[(size_t)(r0 + r) * K + k] : make_double2(0.0, 0.0);
+            const float2 hi = make_float2((float)v.x, (float)v.y);
+            xh[e] = hi;
+            xl[e] = make_float2((float)(v.x - (double)hi.x), (float)(v.y - (double)hi.y));
+        }
+        __syncthreads();
+        const float2* Lh = planes + (size_t)bin * 4 * EE;
+        const float2* Kh = Lh + EE;
+        const float2* Ll = Lh + 2 * EE;
+        const float2* Kl = Lh + 3 * EE;
+        for (int i = threadIdx.x; i < E; i += blockDim.x) {
+            DsC lj[RB], lm[RB], kj[RB], km[RB];
+#pragma unroll
+            for (int r = 0; r < RB; ++r) lj[r] = lm[r] = kj[r] = km[r] = DsC{0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
+            for (int j = 0; j < E; ++j) {
+                const size_t o = (size_t)j * E + i;
+                const float2 lh = __ldg(Lh + o), kh = __ldg(Kh + o), ll = __ldg(Ll + o), kl = __ldg(Kl + o);
+#pragma unroll
+                for (int r = 0; r < RB; ++r) {
+                    const float2 xjh = xh[r * K + j], xmh = xh[r * K + E + j];
+                    const float2 xjl = xl[r * K + j], xml = xl[r * K + E + j];
+                    ds_cmac(lj[r], xjh, xjl, lh, ll);
+                    ds_cmac(lm[r], xmh, xml, lh, ll);
+                    ds_cmac(kj[r], xjh, xjl, kh, kl);
+                    ds_cmac(km[r], xmh, xml, kh, kl);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < RB; ++r) {
+                if (r0 + r < R) {
+                    double2* Y = Yh + ((size_t)bin * R + r0 + r) * K;
+                    Y[i] = cadd(cmul(ca, ds_value(lj[r])), cmul(cb, ds_value(km[r])));
+                    Y[E + i] = cadd(cmul(cg, ds_value(kj[r])), cmul(cd, ds_value(lm[r])));
+                }
+            }
+        }
+    }
+}
+
 size_t binmul_ds_smem(int E) {
     return (size_t)kDsStages * 4 * kDsJB * E * sizeof(float2) + 8ull * E * sizeof(float2) +
            2ull * kDsStages * sizeof(uint64_t);
@@ -1258,9 +1316,10 @@ int derive_fp32_operator(emsurf_handle* h, const emsurf_problem* pr) {
     return EMSURF_OK;
 }
 
-// FP32 hi/lo planes of the FP64 spectrum for binmul_ds_kernel (single-rhs
-// handles; left out, and the FP64 kernel used, when the kernel's shape does
-// not fit or the device-memory budget has no room for them).
+// FP32 hi/lo planes of the FP64 spectrum and macromodels for the
+// double-single kernels (left out, and the FP64 kernels used, when the
+// single-rhs kernel's shape does not fit or the device-memory budget has no
+// room for them).
 int build_ds_planes(emsurf_handle* h) {
     const int E = h->E;
     const int ncw = (E + 31) / 32;
@@ -1464,6 +1523,22 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
                 h->ds_planes, h->ds_x, op.Yg, E, nb, op.coef[0], op.coef[1], op.coef[2], op.coef[3], h->d_err);
             EMS_CUDA(cudaGetLastError());
             h->launches += 2;
+            bin_done = true;
+        }
+        if (!bin_done && R > 1 && h->ds_planes) {
+            // several rhs: FP64 accuracy from double-single FP32 arithmetic,
+            // four rhs per pass over the planes
+            constexpr int RBd = 4;
+            const size_t smem = (size_t)2 * RBd * 2 * E * sizeof(float2);
+            EMS_TRY(set_smem_once(binmul_ds_multi_kernel<RBd>, smem));
+            const int grid = std::min(nb, 152 * 8);
+            for (int r0 = 0; r0 < R; r0 += RBd) {
+                binmul_ds_multi_kernel<RBd><<<grid, threads, smem, st>>>(h->ds_planes, op.Xg, op.Yg, E, nb, R, r0,
+                                                                      op.coef[0], op.coef[1], op.coef[2],
+                                                                      op.coef[3]);
+                EMS_CUDA(cudaGetLastError());
+                h->launches += 1;
+            }
             bin_done = true;
         }
     }

@@ -59,8 +59,8 @@ int64_t request_bytes(const emsurf_request& q) {
     if (q.precision == EMSURF_FP64) op = b64 + mm;
     else if (q.precision == EMSURF_FP32) op = b32 + b64 + mm;          // FP64 spectrum is a temporary
     else op = b64 + b32 + mm + mm / 2;
-    // FP32 hi/lo planes of the FP64 spectrum for single-rhs handles (= b64)
-    if (q.precision != EMSURF_FP32 && q.nrhs == 1) op += b64 + P * 4LL * E * 8 + mm;
+    // FP32 hi/lo planes of the FP64 spectrum and macromodels (= their FP64 bytes)
+    if (q.precision != EMSURF_FP32) op += b64 + P * 4LL * E * 8 + mm;
     // BF16x3 planes of the tensor-core path: spectrum (= b32) + X^ planes
     if (q.precision != EMSURF_FP64 && q.nrhs >= kTcMinRhs && E >= 64)
         op += b32 + P * 4LL * 32 * ((R + 31) / 32) * E * 4;

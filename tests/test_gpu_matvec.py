@@ -222,7 +222,7 @@ def test_fp64_single_rhs_double_single(emsurf_lib, n, nx, ny):
     arithmetic (hi/lo planes, exact product errors, TwoSum sums): each product
     term carries a few 2^-48 of relative error, so the FP64 product meets a
     bar 100x below the FP64 path's 1e-10 (1e-12 rel-L2 against the oracle),
-    for one rhs and, on a two-rhs handle (the FP64 kernel), alike."""
+    for one rhs and on a two-rhs handle (the register-blocked variant)."""
     from paper_1911_04576_gb300 import binding as B
     seed = 900 + 10 * nx + ny
     E, idx, sgn, nu, Lt, Kt, Z, tmap = random_case(n, nx, ny, 2, seed)
