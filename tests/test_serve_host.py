@@ -3,10 +3,21 @@ counts every resident array a request's handle creates, so it must grow
 with the lattice, the mesh and the rhs count, and a MIXED request (FP64
 operator, its FP32 hi/lo planes, the FP32 copy) must need more than an FP32
 one and at least the FP64 spectrum plus its planes."""
+import os
+
 import numpy as np
+import pytest
 
 from paper_1911_04576_gb300 import binding as B
 from paper_1911_04576_gb300 import workloads as W
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    from paper_1911_04576_gb300 import build
+    if not os.path.exists(B.LIB_PATH):
+        build.build()
+    return B.lib()
 
 
 def _bytes(n=3, nx=4, ny=4, rhs=1, precision=B.MIXED, overlap=0.0):
