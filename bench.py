@@ -176,6 +176,46 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def batched_section(B, W, torch):
+    """Many right-hand sides on a large lattice: 48 x 48 cells, K = 576
+    (839,432 unknowns), 32 plane waves, MIXED with tensor-core planes and the
+    near-field preconditioner.  One JSON line (a configuration of the paper's
+    batched use, not the benchmark line)."""
+    w = W.WORKLOADS["lattice48x48_k576_r32"]
+    t0 = time.time()
+    h, V, nu, setup = build_problem(B, W, torch, w, B.MIXED, max_rhs=w.n_rhs, tensor_cores=True)
+    setup["total_s"] = round(time.time() - t0, 2)
+    out = {"section": "batched", "workload": w.name, "unknowns": nu, "rhs": w.n_rhs, "setup": setup,
+           "fp32_matvec_ms": round(time_matvec(B, torch, h, nu, w.n_rhs, B.FP32, reps=5), 3),
+           "fp64_accuracy_matvec_ms": round(time_matvec(B, torch, h, nu, w.n_rhs, B.FP64, reps=2), 1)}
+    r = torch.randn_like(V)
+    y = torch.empty_like(V)
+    B.emsurf_precond_apply(h, r, y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(5):
+        B.emsurf_precond_apply(h, r, y)
+    e1.record()
+    torch.cuda.synchronize()
+    out["precond_apply_ms"] = round(e0.elapsed_time(e1) / 5, 3)
+    X = torch.zeros_like(V)
+    B.emsurf_profile(h, True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, info = B.emsurf_solve(h, V, X, rtol=RTOL, restart=RESTART, max_iters=20000, max_refine=20,
+                              solver=B.SOLVER_MIXED)
+    torch.cuda.synchronize()
+    out["solve_s"] = round(time.perf_counter() - t0, 3)
+    B.emsurf_profile(h, False)
+    out["solve"] = {"status": st, "iters": info[0]["iters"], "refinements": info[0]["refinements"],
+                    "max_rel_residual": max(i["rel_residual"] for i in info)}
+    out["phases_ms"] = {p: round(B.emsurf_profile_read(h, p)[0], 1) for p in B.PHASES}
+    B.emsurf_check(h)
+    h.close()
+    print(json.dumps(out))
+
+
 def max_over_ranks(dist, value, device):
     """The largest of every rank's value (a job takes as long as its slowest
     rank); value itself without a process group."""
@@ -370,6 +410,9 @@ def main():
                     help="profiler driver: right-hand sides of the --matvecs-only products")
     ap.add_argument("--tensor-cores", action="store_true",
                     help="profiler driver: build the tensor-core planes (--matvecs-only)")
+    ap.add_argument("--batched", action="store_true",
+                    help="measure the 48x48 / K = 576 / 32-plane-wave configuration (setup, products, "
+                         "preconditioner apply, MIXED solve of all rhs) and print it; not the bench line")
     ap.add_argument("--solve-iters", type=int, default=0,
                     help="profiler driver: with --matvecs-only, also run one mixed solve capped "
                          "at this many GMRES iterations")
@@ -388,6 +431,9 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     cpu = None
+    if args.batched:
+        batched_section(B, W, torch)
+        return
     if args.matvecs_only:
         prec = {"mixed": B.MIXED, "fp32": B.FP32, "fp64": B.FP64}[args.precision]
         R = args.rhs or w.n_rhs
