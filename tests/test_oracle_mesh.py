@@ -2,7 +2,7 @@
 import numpy as np
 import pytest
 
-from oracle.mesh import box_mesh, patch_mesh
+from oracle.mesh import box_mesh, patch_mesh, sphere_mesh
 from oracle.operators import _slot_coef
 from oracle.quadrature import tri_area
 
@@ -50,3 +50,24 @@ def test_patch_interior_edges_only():
     p = patch_mesh(0.009, 0.00076, 4)
     assert len(p.tris) == 32 and p.n_rwg == 3 * 16 - 2 * 4
     assert np.all(p.verts[:, 2] == 0.00076)
+
+
+@pytest.mark.parametrize("s", [0, 1, 2])
+def test_sphere_closed_surface(s):
+    r, c = 3e-3, np.array([0.0, 0.0, 3.75e-3])
+    m = sphere_mesh(r, c, s)
+    T = 20 * 4 ** s
+    assert len(m.tris) == T
+    assert m.n_rwg == 3 * T // 2                  # closed: every edge shared by two triangles
+    assert len(m.verts) - m.n_rwg + T == 2        # Euler characteristic of a sphere
+    assert np.allclose(np.linalg.norm(m.verts - c, axis=1), r)
+    # the facets approach the sphere's area from below as the mesh is refined
+    area = tri_area(m.tri_coords()).sum()
+    assert area < 4 * np.pi * r ** 2 and area > (0.76, 0.92, 0.98)[s] * 4 * np.pi * r ** 2
+    # RWG zero net charge: the +/- halves carry equal and opposite charge l
+    L = m.slot_len()
+    for e in range(0, m.n_rwg, 7):
+        tp, tm = m.tplus[e], m.tminus[e]
+        lp = L[tp][m.slot_rwg[tp] == e][0]
+        lm = L[tm][m.slot_rwg[tm] == e][0]
+        assert abs(lp - lm) <= 1e-15 * r
