@@ -177,3 +177,36 @@ def test_pec_sphere_matches_mie_series():
     e3 = _sphere_rcs_db_error(3, 2)
     assert e2.max() < 2.0 and e3.max() < 1.0
     assert e3.max() < 0.75 * e2.max() and e3.mean() < e2.mean()
+
+
+def test_bistatic_reciprocity():
+    """Reciprocity of the scattering amplitude: for a plane wave travelling
+    along k with polarisation e and the far field observed along r on
+    polarisation q, q . F(r; k, e) = e . F(-k; -r, q).  The Galerkin system
+    is symmetric up to the one-sided singular quadrature, so the identity
+    holds to a few percent, better on the finer box; a sign or conjugation
+    error in the excitation or the far field breaks it at O(1)."""
+    def sph(th, ph):
+        th, ph = np.radians(th), np.radians(ph)
+        return np.array([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)])
+
+    k1, r1 = -sph(30, 20), sph(50, 110)
+    e1 = np.cross(k1, [0, 0, 1])
+    e1 /= np.linalg.norm(e1)
+    q = np.cross(r1, [1, 0.3, 0])
+    q /= np.linalg.norm(q)
+    errs = []
+    for n in (2, 3):
+        box = box_mesh(A, B, H, n)
+        E = box.n_rwg
+        Z = macromodel.pec_patch(box, patch_mesh(0.3 * LAM, 0.76e-3, 3), K0) + macromodel.empty_box(box, K0)
+
+        def amp(khat, ehat, rhat, pol):
+            x = np.linalg.solve(Z, operators.excitation(box, (0, 0, 0), K0, khat, ehat))
+            F = operators.far_field(operators.radiation_vectors(box, (0, 0, 0), K0, rhat[None]), rhat[None],
+                                    K0, x[:E], x[E:])[0]
+            return pol @ F
+
+        a, b = amp(k1, e1, r1, q), amp(-r1, q, -k1, e1)
+        errs.append(abs(a - b) / abs(a))
+    assert errs[0] < 0.04 and errs[1] < 0.02 and errs[1] < 0.7 * errs[0]
