@@ -1,5 +1,6 @@
 // C ABI entry points: create / matvec / solve / query / destroy.
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstring>
 #include <map>
@@ -97,6 +98,24 @@ int validate(const emsurf_problem* p) {
     }
     const int64_t M = (int64_t)p->nx * p->ny, K = 2LL * p->n_edges;
     if (M * K > INT32_MAX) { set_error("too many local unknowns"); return EMSURF_EINVAL; }
+    for (int c = 0; c < 4; ++c)
+        if (!std::isfinite(p->coef[c].re) || !std::isfinite(p->coef[c].im)) {
+            set_error("coef[%d] is not finite", c);
+            return EMSURF_EINVAL;
+        }
+    if (!p->tables_on_device) {
+        // host inputs: a NaN or an infinity would spread through every product
+        const size_t nz = (size_t)p->n_types * (size_t)K * (size_t)K;
+        const size_t nt = (size_t)(2 * p->nx - 1) * (size_t)(2 * p->ny - 1) * (size_t)p->n_edges * p->n_edges;
+        const struct { const emsurf_c128* a; size_t n; const char* name; } arrays[3] = {
+            {p->macromodels, nz, "macromodels"}, {p->offset_L, nt, "offset_L"}, {p->offset_K, nt, "offset_K"}};
+        for (const auto& t : arrays)
+            for (size_t i = 0; i < t.n; ++i)
+                if (!std::isfinite(t.a[i].re) || !std::isfinite(t.a[i].im)) {
+                    set_error("%s[%zu] is not finite", t.name, i);
+                    return EMSURF_EINVAL;
+                }
+    }
     for (int64_t m = 0; m < M; ++m)
         if (p->type_map[m] < 0 || p->type_map[m] >= p->n_types) {
             set_error("type_map[%lld] = %d out of range", (long long)m, p->type_map[m]);

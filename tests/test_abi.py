@@ -52,7 +52,12 @@ def test_invalid_problem_rejected_without_device(lib):
         dict(nx=1, ny=1, precision=7),
         dict(nx=2, ny=2, grid=(2, 3), type_map=[0] * 4, uo_index=np.tile(idx, 4),
              uo_sign=np.ones(144)),                         # grid below 2N-1
+        dict(nx=1, ny=1, macromodels=_with(Z, (0, 3, 5), np.nan)),       # NaN in a macromodel
+        dict(nx=1, ny=1, offset_L=_with(L, (0, 0, 2, 2), np.inf)),       # infinity in a table
+        dict(nx=1, ny=1, offset_K=_with(L, (0, 0, 1, 7), 1j * np.nan)),
+        dict(nx=1, ny=1, coef=(1, np.nan, -1, 1)),                        # coefficient
     ]
+    finite_cases = cases[-4:]
     for c in cases:
         args = dict(nx=1, ny=1, n_edges=E, n_unique=nu, type_map=[0], macromodels=Z, offset_L=L,
                     offset_K=L, coef=(1, 1, -1, 1), uo_index=idx, uo_sign=sg)
@@ -61,6 +66,30 @@ def test_invalid_problem_rejected_without_device(lib):
             B.emsurf_create(**args)
         assert e.value.status == B.EMSURF_EINVAL, c
         assert B.emsurf_last_error()
+        if any(c is f for f in finite_cases):
+            assert "not finite" in str(e.value), str(e.value)
+
+
+def _with(a, at, v):
+    b = np.array(a, dtype=complex)
+    b[at] = v
+    return b
+
+
+def test_finite_valid_problem_passes_validation(lib):
+    """The same inputs without the planted values pass the host checks
+    (without a GPU the device selection that follows them refuses)."""
+    from paper_1911_04576_gb300 import binding as B
+    E, nu = 18, 36
+    Z = np.eye(36, dtype=complex)[None]
+    L = np.ones((1, 1, E, E), complex)
+    try:
+        h = B.emsurf_create(1, 1, E, nu, [0], Z, L, L, (1, 1, -1, 1), np.arange(36), np.ones(36))
+    except B.EmsurfError as e:
+        # no GPU here: the first device call refuses (device selection)
+        assert "not finite" not in str(e) and "device" in str(e), str(e)
+    else:
+        h.close()
 
 
 def test_null_handle_calls_rejected(lib):
