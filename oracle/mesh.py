@@ -160,3 +160,118 @@ def sphere_mesh(radius, center, subdivisions):
             split += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
         tris = split
     return Mesh(np.array(verts) * radius + np.asarray(center, dtype=np.float64), tris)
+
+
+def slab_zlevels(h, n, t):
+    """z of the box grid rows when a slab of thickness t fills the bottom of
+    the cell (reading of the configurations' cell: the side faces' first row
+    ends at the slab top so the interface meets S_eq on mesh edges, the
+    junction of Fig. composite; the other rows are uniform)."""
+    if n < 2 or not 0.0 < t < h:
+        raise ValueError("slab needs n >= 2 and 0 < t < h")
+    return np.concatenate([[0.0], t + (h - t) * np.arange(n) / (n - 1)])
+
+
+def _perimeter(m):
+    """Grid indices (i, j) of the boundary of an m x m quad grid, walked
+    counter-clockwise from (0, 0): m points per side, 4m in all."""
+    out = [(i, 0) for i in range(m)]
+    out += [(m, j) for j in range(m)]
+    out += [(m - i, m) for i in range(m)]
+    out += [(0, m - j) for j in range(m)]
+    return out
+
+
+def slab_top_mesh(a, b, z, n, side, patch_n, ring_layers=3):
+    """Dielectric interface at height z over the whole cell footprint
+    (the slab top, an interior surface of Sec. II-A), holding a centred
+    square PEC patch of the given side.
+
+    Vertices: the patch grid (patch_n + 1)^2 at index i*(patch_n+1)+j (as
+    patch_mesh); then ring_layers - 1 rings of 4 patch_n points (in the
+    order of _perimeter(patch_n)), ring k on the rectangle of half-widths
+    side/2 + (a/2 - side/2) (k/ring_layers)^2 (and likewise in y), graded
+    toward the patch edge where the interface fields are singular; then
+    the footprint boundary points in the order of _perimeter(n) -- they
+    coincide with the box vertices of grid row 1.
+    Triangles: the patch quads split as patch_mesh; each ring band in quads
+    (c00 = inner q, c10 = outer q, c11 = outer q+1, c01 = inner q+1) split
+    as (c00, c10, c11), (c00, c11, c01); then the last band joins the
+    outermost ring (patch_n segments per side) to the footprint boundary
+    (n segments per side) side by side, zipped from the corner: the next
+    triangle advances the outer polyline while its next parameter
+    (j+1)/n <= (i+1)/patch_n, else the inner one.
+
+    Returns (mesh, on_patch (T,) bool)."""
+    p, m = patch_n, ring_layers
+    if not 0.0 < side < min(a, b) or m < 1:
+        raise ValueError("patch must fit strictly inside the footprint; ring_layers >= 1")
+    xs = -0.5 * side + side * np.arange(p + 1) / p
+    verts = [[xs[i], xs[j], z] for i in range(p + 1) for j in range(p + 1)]
+    pidx = lambda i, j: i * (p + 1) + j
+    tris = []
+    for v in range(p):
+        for u in range(p):
+            c00, c10, c01, c11 = pidx(u, v), pidx(u + 1, v), pidx(u, v + 1), pidx(u + 1, v + 1)
+            tris.append((c00, c10, c11))
+            tris.append((c00, c11, c01))
+    npatch = len(tris)
+    per = _perimeter(p)
+    inner = [pidx(i, j) for i, j in per]
+    for k in range(1, m):
+        f = (k / m) ** 2
+        hx, hy = 0.5 * side + (0.5 * a - 0.5 * side) * f, 0.5 * side + (0.5 * b - 0.5 * side) * f
+        base = len(verts)
+        verts += [[-hx + 2 * hx * i / p, -hy + 2 * hy * j / p, z] for i, j in per]
+        ring = [base + q for q in range(4 * p)]
+        for q in range(4 * p):
+            c00, c01 = inner[q], inner[(q + 1) % (4 * p)]
+            c10, c11 = ring[q], ring[(q + 1) % (4 * p)]
+            tris.append((c00, c10, c11))
+            tris.append((c00, c11, c01))
+        inner = ring
+    nin = len(verts)
+    ox = -0.5 * a + a * np.arange(n + 1) / n
+    oy = -0.5 * b + b * np.arange(n + 1) / n
+    verts += [[ox[i], oy[j], z] for i, j in _perimeter(n)]
+    for s in range(4):
+        I = [inner[(s * p + i) % (4 * p)] for i in range(p + 1)]
+        O = [nin + (s * n + j) % (4 * n) for j in range(n + 1)]
+        i = j = 0
+        while i < p or j < n:
+            if j < n and (i == p or (j + 1) * p <= (i + 1) * n):
+                tris.append((I[i], O[j], O[j + 1]))
+                j += 1
+            else:
+                tris.append((I[i], O[j], I[i + 1]))
+                i += 1
+    on_patch = np.zeros(len(tris), dtype=bool)
+    on_patch[:npatch] = True
+    return Mesh(np.array(verts), tris), on_patch
+
+
+def slab_region_meshes(box, n, top):
+    """The closed surfaces S_v of the two interior regions of a slab cell
+    (Sec. II-A, V = 2): the air above the slab is bounded by the box
+    triangles above grid row 1 and the slab top, the slab by the box
+    triangles of row 0, the bottom face and the slab top.
+
+    box: box_mesh with slab_zlevels; top: slab_top_mesh.  The slab top's
+    footprint boundary vertices are identified with the box vertices of
+    grid row 1.  Returns [(mesh, keys)] for (air, slab), keys[t] = ('eq', tb)
+    or ('top', tt) naming where region triangle t comes from."""
+    pts = box_grid_points(n)
+    index = {q: m for m, q in enumerate(pts)}
+    row = np.array([max(pts[v][2] for v in tri) for tri in box.tris])   # highest grid row per triangle
+    nin = len(top.verts) - 4 * n
+    remap = np.arange(len(top.verts)) + len(box.verts)
+    for s, (i, j) in enumerate(_perimeter(n)):
+        remap[nin + s] = index[(i, j, 1)]
+    verts = np.concatenate([box.verts, top.verts])
+    out = []
+    for sel in (row >= 2, row <= 1):
+        tb = np.nonzero(sel)[0]
+        tris = np.concatenate([box.tris[tb], remap[top.tris]])
+        keys = [("eq", int(t)) for t in tb] + [("top", t) for t in range(len(top.tris))]
+        out.append((Mesh(verts, tris), keys))
+    return out

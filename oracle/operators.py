@@ -2,7 +2,9 @@
 
 Readings of the paper used here:
 
-* time convention e^{jwt}, Green's function G = e^{-jkR} / (4 pi R);
+* time convention e^{jwt}, Green's function G = e^{-jkR} / (4 pi R); in a
+  lossy region k = k0 sqrt(eps_r) is complex with Im k < 0 (Sec. II-B:
+  every operator of region v takes k_v = w sqrt(mu0 eps_v)), so G decays;
 * L[m,n] = int int [Lam_m . Lam_n - (div Lam_m)(div' Lam_n)/k^2] G dS' dS,
   the RWG-tested form of Eq. SIE_LOperator1;
 * K[m,n] = int int Lam_m(r) . [grad_r G(r,r') x Lam_n(r')] dS' dS, the
@@ -41,7 +43,7 @@ def _green_far(R, k):
 def _green_smooth(R, k):
     """Remainder after removing 1/(4 pi R): G_s and grad_r G_s = (r-r') * gfac."""
     kR = k * R
-    small = kR < 0.1
+    small = np.abs(k) * R < 0.1
     Rs = np.where(small, 1.0, R)
     e = np.exp(-1j * k * Rs)
     Gs_closed = (e - 1.0) / (FOUR_PI * Rs)

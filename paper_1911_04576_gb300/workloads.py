@@ -3,9 +3,10 @@
 Every number the method consumes is drawn here from numpy.random.default_rng
 with an explicit seed, with the shapes of the paper's reflectarray problems
 (Sec. V): f = 10 GHz (lambda = 30 mm), period lambda/2, boxes of height
-lambda/4 meshed n x n per face (K = 36 n^2 unknowns per box), one PEC
-square patch per cell at the slab-top height, sides drawn uniformly from a
-type library, a cell -> type map, plane-wave incidence angles.
+lambda/4 meshed n x n per face (K = 36 n^2 unknowns per box), a 0.76 mm
+eps_r = 3, tan delta = 0.001 slab filling the bottom of every cell, one PEC
+square patch per cell on the slab top, sides drawn uniformly from a type
+library, a cell -> type map, plane-wave incidence angles.
 
 Both the oracle-side tests and the product's bench/tests take their inputs
 from here; neither side's arithmetic is in this module.
@@ -19,6 +20,9 @@ K0 = 2.0 * np.pi / LAMBDA
 PERIOD = 0.5 * LAMBDA
 BOX_H = 0.25 * LAMBDA
 PATCH_Z = 0.76e-3
+SLAB_T = 0.76e-3                     # slab thickness: the patch sits on its top
+EPS_SLAB = 3.0 * (1.0 - 0.001j)      # eps_r (1 - j tan delta), tan delta = 0.001, e^{jwt}
+RING_LAYERS = 3                      # slab-top mesh: graded rings around the patch
 
 
 @dataclass
