@@ -2,9 +2,9 @@
 """Benchmark of the FFT-accelerated macromodel solve (Eq. final) on one GB300.
 
 Workload (default): 16 x 16 lattice of boxes meshed 4 x 4 per face
-(K = 576 unknowns per box), 32 PEC-patch cell types (sides uniform in
-[0.15, 0.45] lambda, seeded type map), one normal-incidence x-polarised
-plane wave at 10 GHz.  Every input is built on the product path: overlap
+(K = 576 unknowns per box), 32 cell types -- a PEC patch (side uniform in
+[0.15, 0.45] lambda) on a 0.76 mm eps_r = 3, tan delta = 0.001 slab,
+seeded type map -- one normal-incidence x-polarised plane wave at 10 GHz.  Every input is built on the product path: overlap
 map (C++ setup), offset tables and macromodels (GPU tabulation and Schur
 complement), excitation (GPU).
 
@@ -241,14 +241,17 @@ def build_problem(B, W, torch, w, precision, precond=True, max_rhs=None, tensor_
     coef = (1j * W.K0, 1.0, -1.0, 1j * W.K0)
     idx, sgn, nu = B.emsurf_setup_overlap(w.n, w.nx, w.ny)
     xy = B.emsurf_setup_unknown_xy(A, A, H, w.n, w.nx, w.ny, idx, nu) if precond else None
+    zl = B.emsurf_setup_slab_zlevels(H, w.n, W.SLAB_T)     # box rows end at the slab top
     L = torch.empty((2 * w.ny - 1, 2 * w.nx - 1, w.E, w.E), dtype=torch.complex128, device="cuda")
     K = torch.empty_like(L)
     t0 = time.time()
-    B.emsurf_tabulate_offsets(A, A, H, w.n, w.nx, w.ny, W.K0, L, K)
+    B.emsurf_tabulate_offsets(A, A, H, w.n, w.nx, w.ny, W.K0, L, K, zlevels=zl)
     t_tab = time.time() - t0
     Z = torch.empty((w.n_types, w.K, w.K), dtype=torch.complex128, device="cuda")
     t0 = time.time()
-    B.emsurf_macromodel_pec_patch(A, A, H, w.n, W.patch_sides(w), W.PATCH_Z, w.patch_n, W.K0, Z)
+    B.emsurf_macromodel_slab_patch(A, A, H, w.n, zl, W.patch_sides(w), w.patch_n, W.RING_LAYERS,
+                                   W.EPS_SLAB, W.K0, Z)
+    torch.cuda.synchronize()
     t_mm = time.time() - t0
     t0 = time.time()
     h = B.emsurf_create(w.nx, w.ny, w.E, nu, W.type_map(w), Z, L, K, coef, idx, sgn,
@@ -263,7 +266,7 @@ def build_problem(B, W, torch, w, precision, precond=True, max_rhs=None, tensor_
     waves = W.plane_waves(w)
     V = torch.empty((w.n_rhs, nu), dtype=torch.complex128, device="cuda")
     B.emsurf_excitation(h, A, A, H, w.n, W.K0, np.array([k for k, _ in waves]),
-                        np.array([e for _, e in waves]), V)
+                        np.array([e for _, e in waves]), V, zlevels=zl)
     return h, V, nu, {"tabulate_s": round(t_tab, 3), "macromodels_s": round(t_mm, 3),
                       "create_s": round(t_create, 3)}
 
@@ -327,7 +330,8 @@ def serve_stream(B, W, nreq, seed, precision, max_active, precond):
                          type_map=rng.integers(0, 32, N * N), khat=np.array([w_[0] for w_ in waves]),
                          ehat=np.array([w_[1] for w_ in waves]), precision=precision, rtol=RTOL,
                          restart=RESTART, max_iters=20000, max_refine=20,
-                         precond_overlap=PC_OVERLAP * W.PERIOD / n if precond else 0.0))
+                         precond_overlap=PC_OVERLAP * W.PERIOD / n if precond else 0.0,
+                         slab_t=W.SLAB_T, slab_eps=W.EPS_SLAB, ring_layers=W.RING_LAYERS))
     sv = B.emsurf_server_create(0, SERVE_BUDGET, max_active)
     tickets = []
     t0 = time.perf_counter()

@@ -18,7 +18,11 @@
  *   - calls are ordered on the given CUDA stream (NULL = legacy default);
  *     emsurf_solve synchronises that stream before it returns;
  *   - every call returns an emsurf_status; on EMSURF_EINVAL no output is
- *     written; emsurf_last_error() gives a thread-local message.
+ *     written; emsurf_last_error() gives a thread-local message;
+ *   - a handle keeps per-handle device workspaces (FFT grids, split
+ *     operands, Krylov basis, preconditioner buffers), so it serves one call
+ *     at a time: calls on one handle from different host threads or streams
+ *     must be serialised by the caller (different handles are independent).
  */
 #ifndef EMSURF_H
 #define EMSURF_H
@@ -262,6 +266,40 @@ EMSURF_API int emsurf_setup_patch_mesh(double side, double z, int32_t n, double*
                                        int32_t* tris, int32_t* edges, int32_t* tplus,
                                        int32_t* tminus, int32_t* slot_rwg, int8_t* slot_sgn);
 
+/* Row heights of a box whose bottom slab_t is a dielectric slab (the
+ * configurations' cell; Sec. II-A asks the interface to meet S_eq on mesh
+ * edges, the junction of Fig. composite): zlevels [n+1] = 0, slab_t, then
+ * uniform up to h.  n >= 2, 0 < slab_t < h.                               */
+EMSURF_API int emsurf_setup_slab_zlevels(double h, int32_t n, double slab_t, double* zlevels);
+
+/* The slab-top interface of that cell at height z (Sec. II-A: all surfaces
+ * inside S_eq meshed; the interface conforms to the box rows and the patch):
+ * vertices = the patch grid (patch_n+1)^2 at index i*(patch_n+1)+j, then
+ * ring_layers - 1 rings of 4 patch_n points on the rectangles of half-width
+ * side/2 + (a/2 - side/2) (k/ring_layers)^2 (likewise in y), then the 4n
+ * footprint boundary points (the box vertices of grid row 1), every ring
+ * walked counter-clockwise from its (-,-) corner.  Triangles: the patch
+ * quads (as emsurf_setup_patch_mesh), the ring bands, and a last band zipped
+ * from each corner onto the footprint boundary.  side <= 0: no patch, the
+ * n x n footprint grid (inner points i-major, then the boundary).  RWGs on
+ * interior edges; on_patch [T] = 1 for patch triangles.                    */
+EMSURF_API int emsurf_setup_slab_top_counts(double a, double b, int32_t n, double side,
+                                            int32_t patch_n, int32_t ring_layers,
+                                            int32_t* n_verts, int32_t* n_tris, int32_t* n_edges);
+EMSURF_API int emsurf_setup_slab_top_mesh(double a, double b, double z, int32_t n, double side,
+                                          int32_t patch_n, int32_t ring_layers, double* verts,
+                                          int32_t* tris, int32_t* edges, int32_t* tplus,
+                                          int32_t* tminus, int32_t* slot_rwg, int8_t* slot_sgn,
+                                          int8_t* on_patch);
+
+/* Sizes of that cell's interior system: unknowns eliminated by the Schur
+ * complement (n_interior) and RWGs of the air and slab region surfaces
+ * (region_edges[2]).                                                      */
+EMSURF_API int emsurf_setup_slab_cell_counts(double a, double b, double h, int32_t n,
+                                             const double* zlevels, double side, int32_t patch_n,
+                                             int32_t ring_layers, int32_t* n_interior,
+                                             int32_t* region_edges);
+
 /* Edge-midpoint (x, y) of every unique unknown of an nx x ny lattice
  * (box of cell (ix,iy) centred at (ix*a, iy*b)), from the canonical box
  * mesh and the overlap map: xy host [n_unique][2].                        */
@@ -325,16 +363,40 @@ EMSURF_API int emsurf_tabulate_noalloc(const double* test_verts, const int32_t* 
                                        void* stream);
 
 /* Offset tables of an nx x ny lattice of boxes (period a, b; height h; n x n
- * per face): L, K device [2ny-1][2nx-1][E][E] indexed [dy+ny-1][dx+nx-1],
+ * per face, rows at zlevels or uniform if NULL): L, K device [2ny-1][2nx-1][E][E] indexed [dy+ny-1][dx+nx-1],
  * d = test cell - source cell; closed-form singular parts for touching
  * boxes (|dx|, |dy| <= 1).  The tables are the reciprocal part of the
  * one-sided blocks of emsurf_tabulate, T(d) = (T1(d) + T1(-d)^T) / 2, so
  * L(-d) = L(d)^T and K(-d) = K(d)^T hold exactly (the one-sided closed-form
  * integration breaks them at touching offsets).  The layout emsurf_create
  * takes; with reciprocal tables it stores half of the FP32 spectrum.      */
-EMSURF_API int emsurf_tabulate_offsets(double a, double b, double h, int32_t n, int32_t nx,
-                                       int32_t ny, double k, emsurf_c128* L, emsurf_c128* K,
-                                       void* stream);
+EMSURF_API int emsurf_tabulate_offsets(double a, double b, double h, int32_t n,
+                                       const double* zlevels, int32_t nx, int32_t ny, double k,
+                                       emsurf_c128* L, emsurf_c128* K, void* stream);
+
+/* Macromodels Z~ of Eq. Zmacromodel of the patch-on-slab cell (Secs. II-A..D
+ * with two interior regions): a dielectric slab of relative permittivity
+ * eps_slab (lossy: Im < 0 under e^{jwt}) fills the bottom of the box up to
+ * the first row boundary zlevels[1] of the side faces, a flat PEC square
+ * patch of side sides[t] (patch_n x patch_n quads; sides[t] <= 0: slab
+ * only) lies centred on the slab top, air above.  Box rows at zlevels
+ * ([n+1], zlevels[0] = 0, zlevels[n] = h; see emsurf_setup_slab_zlevels).
+ * The slab top is meshed by emsurf_setup_slab_top_mesh (ring_layers graded
+ * rings around the patch).  Per region v the tested block
+ * [[jk0 L_v, K_v], [-K_v, jk0 eps_v L_v]] with k_v = k0 sqrt(eps_v)
+ * (Eq. ch5_macromodel_composite_SIE_Block); U (Eq. incidence1) joins them by
+ * the rules of Sec. II-C: interface (J, M shared, rule 1), PEC at the
+ * interface (one J per side, rule 2), PEC-dielectric junction (J shared,
+ * rule 3), and the junction of the interface with S_eq (label 2 of
+ * Fig. composite); Z~ is the Schur complement of U^T Z U (Eq. mmm_mult)
+ * on the interior unknowns.  Z: device [n_types][K][K] complex128.  EINVAL
+ * for n < 2, a patch that does not fit inside the footprint, Re eps <= 0 or
+ * Im eps > 0, or a singular interior block.  Synchronises `stream`.       */
+EMSURF_API int emsurf_macromodel_slab_patch(double a, double b, double h, int32_t n,
+                                            const double* zlevels, int32_t n_types,
+                                            const double* sides, int32_t patch_n,
+                                            int32_t ring_layers, emsurf_c128 eps_slab, double k0,
+                                            emsurf_c128* Z, void* stream);
 
 /* Macromodels Z~ of Eq. Zmacromodel for cells holding one flat PEC square
  * patch of side sides[t] (centred, height patch_z, patch_n x patch_n quads)
@@ -352,18 +414,21 @@ EMSURF_API int emsurf_macromodel_pec_patch(double a, double b, double h, int32_t
  * E_inc = ehat e^{-jk khat.r} (|E_inc| = 1 V/m): rows J test E_inc, rows M
  * test eta0 H_inc = (khat x ehat) e^{..} (Eq. out).  khat, ehat: host
  * [nrhs][3] unit vectors; V: device [nrhs][n_unique].  The box geometry
- * (a, b, h, n) must be the one the handle's tables were built for.        */
+ * (a, b, h, n, zlevels: row heights or NULL for uniform) must be the one
+ * the handle's tables were built for.                                     */
 EMSURF_API int emsurf_excitation(emsurf_handle* h, double a, double b, double hgt, int32_t n,
-                                 double k, int32_t nrhs, const double* khat, const double* ehat,
-                                 emsurf_c128* V, void* stream);
+                                 const double* zlevels, double k, int32_t nrhs, const double* khat,
+                                 const double* ehat, emsurf_c128* V, void* stream);
 
 /* Far field radiated by solved currents Y~ (device [nrhs][n_unique]) in
  * ndir directions rhat (host [ndir][3] unit vectors): F (device
  * [nrhs][ndir][3]) with E ~ F e^{-jkr}/r, and optionally the bistatic RCS
- * sigma = 4 pi |F|^2 (device [nrhs][ndir], m^2; NULL to skip).            */
+ * sigma = 4 pi |F|^2 (device [nrhs][ndir], m^2; NULL to skip).  Box
+ * geometry as for emsurf_excitation.                                      */
 EMSURF_API int emsurf_far_field(emsurf_handle* h, double a, double b, double hgt, int32_t n,
-                                double k, const emsurf_c128* Y, int32_t nrhs, int32_t ndir,
-                                const double* rhat, emsurf_c128* F, double* rcs, void* stream);
+                                const double* zlevels, double k, const emsurf_c128* Y,
+                                int32_t nrhs, int32_t ndir, const double* rhat, emsurf_c128* F,
+                                double* rcs, void* stream);
 
 /* ------------------------------------------------------------------------
  * Serving (no counterpart in the paper, which solves one array at a time):
@@ -403,6 +468,11 @@ typedef struct {
                                     valid until the result is collected       */
     double precond_overlap;      /* near-field preconditioner margin (m),
                                     <= 0: none                                */
+    double slab_t;               /* > 0: patch-on-slab cells (slab thickness,
+                                    m; the patch lies on the slab top and
+                                    patch_z is ignored); 0: free-space cells  */
+    emsurf_c128 slab_eps;        /* slab relative permittivity (Im <= 0)      */
+    int32_t ring_layers;         /* slab-top rings around the patch (0 = 3)   */
 } emsurf_request;
 
 typedef struct {

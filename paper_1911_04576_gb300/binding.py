@@ -96,10 +96,16 @@ def lib():
         L.emsurf_tabulate.argtypes = [vp, vp, vp, vp, i32, i32, vp, vp, vp, vp, i32, i32, vp, vp,
                                       i32, d, vp, vp, vp]
         L.emsurf_tabulate_noalloc.argtypes = L.emsurf_tabulate.argtypes
-        L.emsurf_tabulate_offsets.argtypes = [d, d, d, i32, i32, i32, d, vp, vp, vp]
+        L.emsurf_tabulate_offsets.argtypes = [d, d, d, i32, vp, i32, i32, d, vp, vp, vp]
         L.emsurf_macromodel_pec_patch.argtypes = [d, d, d, i32, i32, vp, d, i32, d, vp, vp]
-        L.emsurf_excitation.argtypes = [vp, d, d, d, i32, d, i32, vp, vp, vp, vp]
-        L.emsurf_far_field.argtypes = [vp, d, d, d, i32, d, vp, i32, i32, vp, vp, vp, vp]
+        L.emsurf_macromodel_slab_patch.argtypes = [d, d, d, i32, vp, i32, vp, i32, i32, C128, d,
+                                                   vp, vp]
+        L.emsurf_excitation.argtypes = [vp, d, d, d, i32, vp, d, i32, vp, vp, vp, vp]
+        L.emsurf_far_field.argtypes = [vp, d, d, d, i32, vp, d, vp, i32, i32, vp, vp, vp, vp]
+        L.emsurf_setup_slab_zlevels.argtypes = [d, i32, d, vp]
+        L.emsurf_setup_slab_cell_counts.argtypes = [d, d, d, i32, vp, d, i32, i32, ip, vp]
+        L.emsurf_setup_slab_top_counts.argtypes = [d, d, i32, d, i32, i32, ip, ip, ip]
+        L.emsurf_setup_slab_top_mesh.argtypes = [d, d, d, i32, d, i32, i32] + [vp] * 8
         _lib = L
     return _lib
 
@@ -321,9 +327,56 @@ def emsurf_tabulate_noalloc(test, src, shifts, singular, k, L, K, stream=None):
                                          _stream(stream)))
 
 
-def emsurf_tabulate_offsets(a, b, h, n, nx, ny, k, L, K, stream=None):
-    """emsurf_tabulate_offsets: L, K torch CUDA complex128 [2ny-1, 2nx-1, E, E]."""
-    _check(lib().emsurf_tabulate_offsets(a, b, h, n, nx, ny, k, _ptr(L), _ptr(K), _stream(stream)))
+def _z(zlevels):
+    return None if zlevels is None else np.ascontiguousarray(zlevels, dtype=np.float64)
+
+
+def emsurf_tabulate_offsets(a, b, h, n, nx, ny, k, L, K, stream=None, zlevels=None):
+    """emsurf_tabulate_offsets: L, K torch CUDA complex128 [2ny-1, 2nx-1, E, E];
+    zlevels: box row heights [n+1] (None: uniform)."""
+    z = _z(zlevels)
+    _check(lib().emsurf_tabulate_offsets(a, b, h, n, _ptr(z), nx, ny, k, _ptr(L), _ptr(K),
+                                         _stream(stream)))
+
+
+def emsurf_setup_slab_zlevels(h, n, slab_t):
+    """emsurf_setup_slab_zlevels: box row heights [n+1] of a slab cell."""
+    z = np.zeros(n + 1)
+    _check(lib().emsurf_setup_slab_zlevels(h, n, slab_t, _ptr(z)))
+    return z
+
+
+def emsurf_setup_slab_cell_counts(a, b, h, n, zlevels, side, patch_n, ring_layers=3):
+    """emsurf_setup_slab_cell_counts: (interior unknowns, (air RWGs, slab RWGs))."""
+    z = _z(zlevels)
+    ni = C.c_int32()
+    re = np.zeros(2, np.int32)
+    _check(lib().emsurf_setup_slab_cell_counts(a, b, h, n, _ptr(z), side, patch_n, ring_layers,
+                                               C.byref(ni), _ptr(re)))
+    return ni.value, (int(re[0]), int(re[1]))
+
+
+def emsurf_setup_slab_top_mesh(a, b, z, n, side, patch_n, ring_layers=3):
+    """emsurf_setup_slab_top_mesh: dict of the slab-top mesh arrays plus on_patch."""
+    V, T, E = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(lib().emsurf_setup_slab_top_counts(a, b, n, side, patch_n, ring_layers, C.byref(V),
+                                              C.byref(T), C.byref(E)))
+    out = _mesh_arrays(V.value, T.value, E.value)
+    out["on_patch"] = np.zeros(T.value, np.int8)
+    _check(lib().emsurf_setup_slab_top_mesh(a, b, z, n, side, patch_n, ring_layers,
+                                            *[_ptr(out[k]) for k in _MESH_KEYS + ("on_patch",)]))
+    return out
+
+
+def emsurf_macromodel_slab_patch(a, b, h, n, zlevels, sides, patch_n, ring_layers, eps_slab, k0, Z,
+                                 stream=None):
+    """emsurf_macromodel_slab_patch: Z torch CUDA complex128 [T, K, K]."""
+    sides = np.ascontiguousarray(sides, dtype=np.float64)
+    z = _z(zlevels)
+    e = complex(eps_slab)
+    _check(lib().emsurf_macromodel_slab_patch(a, b, h, n, _ptr(z), len(sides), _ptr(sides), patch_n,
+                                              ring_layers, C128(e.real, e.imag), k0, _ptr(Z),
+                                              _stream(stream)))
 
 
 def emsurf_macromodel_pec_patch(a, b, h, n, sides, patch_z, patch_n, k, Z, stream=None):
@@ -333,20 +386,22 @@ def emsurf_macromodel_pec_patch(a, b, h, n, sides, patch_z, patch_n, k, Z, strea
                                              k, _ptr(Z), _stream(stream)))
 
 
-def emsurf_excitation(hd, a, b, h, n, k, khat, ehat, V, stream=None):
+def emsurf_excitation(hd, a, b, h, n, k, khat, ehat, V, stream=None, zlevels=None):
     """emsurf_excitation: khat, ehat host [nrhs, 3]; V torch CUDA [nrhs, n_unique]."""
     khat = np.ascontiguousarray(np.atleast_2d(khat), dtype=np.float64)
     ehat = np.ascontiguousarray(np.atleast_2d(ehat), dtype=np.float64)
-    _check(lib().emsurf_excitation(hd.ptr, a, b, h, n, k, len(khat), _ptr(khat), _ptr(ehat), _ptr(V),
-                                   _stream(stream)))
+    z = _z(zlevels)
+    _check(lib().emsurf_excitation(hd.ptr, a, b, h, n, _ptr(z), k, len(khat), _ptr(khat), _ptr(ehat),
+                                   _ptr(V), _stream(stream)))
 
 
-def emsurf_far_field(hd, a, b, h, n, k, Y, rhat, F, rcs=None, stream=None):
+def emsurf_far_field(hd, a, b, h, n, k, Y, rhat, F, rcs=None, stream=None, zlevels=None):
     """emsurf_far_field: Y torch CUDA [nrhs, n_unique]; rhat host [ndir, 3];
     F torch CUDA complex128 [nrhs, ndir, 3]; rcs torch CUDA float64 [nrhs, ndir]."""
     rhat = np.ascontiguousarray(rhat, dtype=np.float64)
     nrhs = 1 if Y.dim() == 1 else Y.shape[0]
-    _check(lib().emsurf_far_field(hd.ptr, a, b, h, n, k, _ptr(Y), nrhs, len(rhat), _ptr(rhat),
+    z = _z(zlevels)
+    _check(lib().emsurf_far_field(hd.ptr, a, b, h, n, _ptr(z), k, _ptr(Y), nrhs, len(rhat), _ptr(rhat),
                                   _ptr(F), _ptr(rcs), _stream(stream)))
 
 
@@ -395,7 +450,8 @@ class Request(C.Structure):
                 ("patch_sides", C.c_void_p), ("patch_z", C.c_double), ("patch_n", C.c_int32),
                 ("type_map", C.c_void_p), ("nrhs", C.c_int32), ("khat", C.c_void_p),
                 ("ehat", C.c_void_p), ("precision", C.c_int32), ("opts", SolveOpts),
-                ("x_out", C.c_void_p), ("precond_overlap", C.c_double)]
+                ("x_out", C.c_void_p), ("precond_overlap", C.c_double), ("slab_t", C.c_double),
+                ("slab_eps", C128), ("ring_layers", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -448,8 +504,10 @@ def emsurf_server_create(device=0, device_mem_budget=0, max_active=2):
 
 def make_request(a, b, h, n, nx, ny, k0, patch_sides, patch_z, patch_n, type_map, khat, ehat,
                  precision=MIXED, rtol=1e-6, restart=30, max_iters=20000, max_refine=20,
-                 inner_rtol=0.0, solver=0, x_out=None, precond_overlap=0.0):
-    """Build an emsurf_request; returns (Request, arrays that must stay alive)."""
+                 inner_rtol=0.0, solver=0, x_out=None, precond_overlap=0.0, slab_t=0.0,
+                 slab_eps=1.0, ring_layers=0):
+    """Build an emsurf_request; returns (Request, arrays that must stay alive).
+    slab_t > 0: patch-on-slab cells (eps slab_eps, patch on the slab top)."""
     sides = np.ascontiguousarray(patch_sides, dtype=np.float64)
     tmap = np.ascontiguousarray(type_map, dtype=np.int32)
     kh = np.ascontiguousarray(np.atleast_2d(khat), dtype=np.float64)
@@ -457,7 +515,8 @@ def make_request(a, b, h, n, nx, ny, k0, patch_sides, patch_z, patch_n, type_map
     q = Request(a, b, h, n, nx, ny, k0, len(sides), _ptr(sides), patch_z, patch_n, _ptr(tmap),
                 len(kh), _ptr(kh), _ptr(eh), precision,
                 SolveOpts(rtol, restart, max_iters, max_refine, inner_rtol, solver, 0), _ptr(x_out),
-                precond_overlap)
+                precond_overlap, slab_t, C128(complex(slab_eps).real, complex(slab_eps).imag),
+                ring_layers)
     return q, (sides, tmap, kh, eh, x_out)
 
 

@@ -286,6 +286,33 @@ struct MeshView {
     const int8_t* slot_sgn;
     int T, E;
 };
+// the configurations' cell (slab + patch): the two region surfaces (air,
+// slab) and U of Eq. incidence1 as, per region, the region-local unknown
+// (J of RWG r: r, M: E_v + r) and sign of every X~ column (-1: absent);
+// X~ = [interior unknowns (n_int) | J_eq (E) | M_eq (E)]
+struct SlabRegionMesh {
+    std::vector<double> verts;
+    std::vector<int32_t> tris, slot_rwg;
+    std::vector<int8_t> slot_sgn;
+    int T = 0, E = 0;
+};
+struct SlabPlan {
+    SlabRegionMesh region[2];
+    int n_int = 0, N = 0, E = 0;
+    std::vector<int32_t> copy[2];
+    std::vector<int8_t> sgn[2];
+};
+int slab_cell_plan(double a, double b, double h, int n, const double* zlevels, double side,
+                   int patch_n, int ring_layers, SlabPlan& out);
+int slab_top(double a, double b, double z, int n, double side, int patch_n, int ring_layers,
+             std::vector<double>& verts, std::vector<int32_t>& tris, std::vector<int32_t>& edges,
+             std::vector<int32_t>& tplus, std::vector<int32_t>& tminus,
+             std::vector<int32_t>& slot_rwg, std::vector<int8_t>& slot_sgn,
+             std::vector<int8_t>& on_patch);
+// complex wavenumber k = kr + j ki (Im k < 0 in a lossy region, e^{jwt})
+int tabulate_blocks_cx(const MeshView& test, const MeshView& src, const double* shifts,
+                       const int8_t* singular, int nb, double kr, double ki, double2* L,
+                       double2* K, cudaStream_t st);
 // Galerkin L, K [nb][test E][src E] on the device for nb test-mesh shifts
 int tabulate_blocks(const MeshView& test, const MeshView& src, const double* shifts,
                     const int8_t* singular, int nb, double k, double2* L, double2* K,

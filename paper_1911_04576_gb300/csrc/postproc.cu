@@ -177,7 +177,8 @@ __global__ void far_field_kernel(const double2* __restrict__ S, const double2* _
     }
 }
 
-int box_quadrature(double a, double b, double h, int n, int E_expected, std::vector<RwgQuad>& out) {
+int box_quadrature(double a, double b, double h, int n, const double* zlevels, int E_expected,
+                   std::vector<RwgQuad>& out) {
     int32_t V, T, E;
     EMS_TRY(emsurf_setup_box_counts(n, &V, &T, &E));
     if (E != E_expected) {
@@ -187,7 +188,7 @@ int box_quadrature(double a, double b, double h, int n, int E_expected, std::vec
     std::vector<double> verts(3 * V);
     std::vector<int32_t> tris(3 * T), edges(2 * E), tp(E), tm(E), srw(3 * T);
     std::vector<int8_t> ssg(3 * T);
-    EMS_TRY(emsurf_setup_box_mesh(a, b, h, n, nullptr, verts.data(), tris.data(), edges.data(),
+    EMS_TRY(emsurf_setup_box_mesh(a, b, h, n, zlevels, verts.data(), tris.data(), edges.data(),
                                   tp.data(), tm.data(), srw.data(), ssg.data()));
     const double s15 = std::sqrt(15.0);
     const double a1 = (6.0 - s15) / 21.0, b1 = (9.0 + 2.0 * s15) / 21.0;
@@ -249,7 +250,7 @@ using namespace emsurf;
 extern "C" {
 
 EMSURF_API int emsurf_excitation(emsurf_handle* h, double a, double b, double hgt, int32_t n,
-                                 double k, int32_t nrhs, const double* khat, const double* ehat,
+                                 const double* zlevels, double k, int32_t nrhs, const double* khat, const double* ehat,
                                  emsurf_c128* V, void* stream) {
     if (!h || !khat || !ehat || !V || nrhs < 1 || !(k > 0.0)) {
         set_error("emsurf_excitation: bad arguments");
@@ -257,7 +258,7 @@ EMSURF_API int emsurf_excitation(emsurf_handle* h, double a, double b, double hg
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     std::vector<RwgQuad> q;
-    EMS_TRY(box_quadrature(a, b, hgt, n, h->E, q));
+    EMS_TRY(box_quadrature(a, b, hgt, n, zlevels, h->E, q));
     Scoped sc;
     RwgQuad* dq;
     double *dk, *de;
@@ -281,7 +282,8 @@ EMSURF_API int emsurf_excitation(emsurf_handle* h, double a, double b, double hg
     return EMSURF_OK;
 }
 
-EMSURF_API int emsurf_far_field(emsurf_handle* h, double a, double b, double hgt, int32_t n, double k,
+EMSURF_API int emsurf_far_field(emsurf_handle* h, double a, double b, double hgt, int32_t n,
+                                const double* zlevels, double k,
                                 const emsurf_c128* Y, int32_t nrhs, int32_t ndir, const double* rhat,
                                 emsurf_c128* F, double* rcs, void* stream) {
     if (!h || !Y || !rhat || !F || nrhs < 1 || ndir < 1 || !(k > 0.0)) {
@@ -290,7 +292,7 @@ EMSURF_API int emsurf_far_field(emsurf_handle* h, double a, double b, double hgt
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     std::vector<RwgQuad> q;
-    EMS_TRY(box_quadrature(a, b, hgt, n, h->E, q));
+    EMS_TRY(box_quadrature(a, b, hgt, n, zlevels, h->E, q));
     const int E = h->E, K = h->K;
     // directions in chunks so the per-chunk work arrays stay under ~512 MB
     const size_t per_dir = (size_t)E * 3 * sizeof(double2) + (size_t)nrhs * K * sizeof(double2);

@@ -72,7 +72,9 @@ int64_t request_bytes(const emsurf_request& q) {
         pc = M * nm * nm * 8 + 2 * M * nm * 4 + 50LL * E * E * 16;
         krylov += (int64_t)std::max(q.opts.restart, 1) * R * M * K * 16;   // Z_j of flexible GMRES
     }
-    return tables + mm + op + work + krylov + pc + (768LL << 20);       // + tabulation scratch, slack
+    int64_t cell = 0;                  // slab macromodels: elimination buffers (interior <= ~450)
+    if (q.slab_t > 0.0) cell = 2LL * q.n_types * (K + 450) * (K + 450) * 16 + q.n_types * 8LL * 400 * 400 * 16;
+    return tables + mm + op + work + krylov + pc + cell + (768LL << 20);   // + tabulation scratch, slack
 }
 
 }  // namespace
@@ -119,10 +121,22 @@ int run_job(emsurf_server* sv, Job& jb, cudaStream_t st) {
     alloc(&L, tab * sizeof(double2));
     alloc(&Kt, tab * sizeof(double2));
     alloc(&Z, (size_t)q.n_types * K * K * sizeof(double2));
-    if (!s) s = emsurf_tabulate_offsets(q.a, q.b, q.h, q.n, q.nx, q.ny, q.k0,
+    // slab cells: box rows end at the slab top (junction with S_eq)
+    std::vector<double> zl;
+    if (!s && q.slab_t > 0.0) {
+        zl.resize(q.n + 1);
+        s = emsurf_setup_slab_zlevels(q.h, q.n, q.slab_t, zl.data());
+    }
+    const double* zp = zl.empty() ? nullptr : zl.data();
+    if (!s) s = emsurf_tabulate_offsets(q.a, q.b, q.h, q.n, zp, q.nx, q.ny, q.k0,
                                         static_cast<emsurf_c128*>(L), static_cast<emsurf_c128*>(Kt), st);
-    if (!s) s = emsurf_macromodel_pec_patch(q.a, q.b, q.h, q.n, q.n_types, jb.sides.data(), q.patch_z,
-                                            q.patch_n, q.k0, static_cast<emsurf_c128*>(Z), st);
+    if (!s && zp)
+        s = emsurf_macromodel_slab_patch(q.a, q.b, q.h, q.n, zp, q.n_types, jb.sides.data(), q.patch_n,
+                                         q.ring_layers > 0 ? q.ring_layers : 3, q.slab_eps, q.k0,
+                                         static_cast<emsurf_c128*>(Z), st);
+    else if (!s)
+        s = emsurf_macromodel_pec_patch(q.a, q.b, q.h, q.n, q.n_types, jb.sides.data(), q.patch_z,
+                                        q.patch_n, q.k0, static_cast<emsurf_c128*>(Z), st);
     if (!s) {
         emsurf_problem p{};
         p.nx = q.nx;
@@ -166,7 +180,7 @@ int run_job(emsurf_server* sv, Job& jb, cudaStream_t st) {
     cudaFree(Z);
     alloc(&V, (size_t)q.nrhs * nu * sizeof(double2));
     alloc(&X, (size_t)q.nrhs * nu * sizeof(double2));
-    if (!s) s = emsurf_excitation(hd, q.a, q.b, q.h, q.n, q.k0, q.nrhs, jb.khat.data(), jb.ehat.data(),
+    if (!s) s = emsurf_excitation(hd, q.a, q.b, q.h, q.n, zp, q.k0, q.nrhs, jb.khat.data(), jb.ehat.data(),
                                   static_cast<emsurf_c128*>(V), st);
     jb.t_setup = Clock::now();
     if (!s) {

@@ -198,6 +198,262 @@ struct ParityDSU {
     }
 };
 
+// ---------------------------------------------------------------------------
+// The configurations' cell (Secs. II-A..C): a dielectric slab fills the
+// bottom of the box up to the first row boundary zlevels[1] of the side
+// faces; its top is an interface surface that meets S_eq on the box edges
+// of grid row 1 (the junction of Fig. composite) and carries a centred PEC
+// square patch.
+
+// boundary of an m x m quad grid, counter-clockwise from (0, 0), m points a side
+std::vector<std::pair<int, int>> grid_perimeter(int m) {
+    std::vector<std::pair<int, int>> out;
+    for (int i = 0; i < m; ++i) out.push_back({i, 0});
+    for (int j = 0; j < m; ++j) out.push_back({m, j});
+    for (int i = 0; i < m; ++i) out.push_back({m - i, m});
+    for (int j = 0; j < m; ++j) out.push_back({0, m - j});
+    return out;
+}
+
+void push_tri(MeshOut& m, int a, int b, int c) {
+    m.tris.push_back(a);
+    m.tris.push_back(b);
+    m.tris.push_back(c);
+}
+
+void push_vert(MeshOut& m, double x, double y, double z) {
+    m.verts.push_back(x);
+    m.verts.push_back(y);
+    m.verts.push_back(z);
+}
+
+// Slab top with a patch: patch grid, ring_layers - 1 graded rings of
+// 4 patch_n points, then the 4n footprint boundary points; patch quads,
+// ring bands, and a zipped last band to the footprint boundary.
+int build_slab_top(double a, double b, double z, int n, double side, int p, int layers,
+                   MeshOut& m, std::vector<int8_t>& pec) {
+    if (n < 2 || p < 1 || layers < 1 || !(side > 0.0) || !(side < std::min(a, b))) {
+        set_error("slab top needs n >= 2, patch_n >= 1, ring_layers >= 1 and 0 < side < min(a, b)");
+        return EMSURF_EINVAL;
+    }
+    for (int i = 0; i <= p; ++i)
+        for (int j = 0; j <= p; ++j)
+            push_vert(m, -0.5 * side + side * i / p, -0.5 * side + side * j / p, z);
+    auto pidx = [p](int i, int j) { return i * (p + 1) + j; };
+    for (int v = 0; v < p; ++v)
+        for (int u = 0; u < p; ++u) {
+            push_tri(m, pidx(u, v), pidx(u + 1, v), pidx(u + 1, v + 1));
+            push_tri(m, pidx(u, v), pidx(u + 1, v + 1), pidx(u, v + 1));
+        }
+    const int npatch = (int)m.tris.size() / 3;
+    const auto per = grid_perimeter(p);
+    std::vector<int> inner;
+    for (auto& q : per) inner.push_back(pidx(q.first, q.second));
+    for (int k = 1; k < layers; ++k) {
+        const double f = ((double)k / layers) * ((double)k / layers);
+        const double hx = 0.5 * side + (0.5 * a - 0.5 * side) * f;
+        const double hy = 0.5 * side + (0.5 * b - 0.5 * side) * f;
+        const int base = (int)m.verts.size() / 3;
+        for (auto& q : per) push_vert(m, -hx + 2.0 * hx * q.first / p, -hy + 2.0 * hy * q.second / p, z);
+        std::vector<int> ring(4 * p);
+        for (int q = 0; q < 4 * p; ++q) ring[q] = base + q;
+        for (int q = 0; q < 4 * p; ++q) {
+            const int c00 = inner[q], c01 = inner[(q + 1) % (4 * p)];
+            const int c10 = ring[q], c11 = ring[(q + 1) % (4 * p)];
+            push_tri(m, c00, c10, c11);
+            push_tri(m, c00, c11, c01);
+        }
+        inner = ring;
+    }
+    const int nin = (int)m.verts.size() / 3;
+    for (auto& q : grid_perimeter(n)) push_vert(m, -0.5 * a + a * q.first / n, -0.5 * b + b * q.second / n, z);
+    for (int s = 0; s < 4; ++s) {
+        int i = 0, j = 0;
+        auto I = [&](int x) { return inner[(s * p + x) % (4 * p)]; };
+        auto O = [&](int x) { return nin + (s * n + x) % (4 * n); };
+        while (i < p || j < n) {
+            if (j < n && (i == p || (j + 1) * p <= (i + 1) * n)) {
+                push_tri(m, I(i), O(j), O(j + 1));
+                ++j;
+            } else {
+                push_tri(m, I(i), O(j), I(i + 1));
+                ++i;
+            }
+        }
+    }
+    pec.assign(m.tris.size() / 3, 0);
+    std::fill(pec.begin(), pec.begin() + npatch, 1);
+    return finish_mesh(m, false);
+}
+
+// Slab top without a patch: the n x n footprint grid, inner points first
+// (i-major), then the boundary in grid_perimeter order; quads split as the
+// box faces.
+int build_bare_top(double a, double b, double z, int n, MeshOut& m, std::vector<int8_t>& pec) {
+    if (n < 2) { set_error("slab top needs n >= 2"); return EMSURF_EINVAL; }
+    std::vector<int> id((n + 1) * (n + 1), -1);
+    int c = 0;
+    for (int i = 1; i < n; ++i)
+        for (int j = 1; j < n; ++j) {
+            id[i * (n + 1) + j] = c++;
+            push_vert(m, -0.5 * a + a * i / n, -0.5 * b + b * j / n, z);
+        }
+    for (auto& q : grid_perimeter(n)) {
+        id[q.first * (n + 1) + q.second] = c++;
+        push_vert(m, -0.5 * a + a * q.first / n, -0.5 * b + b * q.second / n, z);
+    }
+    auto at = [&](int i, int j) { return id[i * (n + 1) + j]; };
+    for (int v = 0; v < n; ++v)
+        for (int u = 0; u < n; ++u) {
+            push_tri(m, at(u, v), at(u + 1, v), at(u + 1, v + 1));
+            push_tri(m, at(u, v), at(u + 1, v + 1), at(u, v + 1));
+        }
+    pec.assign(m.tris.size() / 3, 0);
+    return finish_mesh(m, false);
+}
+
+int slot_sign(const MeshOut& m, int rwg, int t) {
+    for (int i = 0; i < 3; ++i)
+        if (m.slot_rwg[3 * t + i] == rwg) return m.slot_sgn[3 * t + i];
+    return 0;
+}
+
+}  // namespace
+
+int slab_top(double a, double b, double z, int n, double side, int patch_n, int ring_layers,
+             std::vector<double>& verts, std::vector<int32_t>& tris, std::vector<int32_t>& edges,
+             std::vector<int32_t>& tplus, std::vector<int32_t>& tminus,
+             std::vector<int32_t>& slot_rwg, std::vector<int8_t>& slot_sgn,
+             std::vector<int8_t>& on_patch) {
+    MeshOut m;
+    if (side > 0.0) EMS_TRY(build_slab_top(a, b, z, n, side, patch_n, ring_layers, m, on_patch));
+    else EMS_TRY(build_bare_top(a, b, z, n, m, on_patch));
+    verts = m.verts;
+    tris = m.tris;
+    edges = m.edges;
+    tplus = m.tplus;
+    tminus = m.tminus;
+    slot_rwg = m.slot_rwg;
+    slot_sgn = m.slot_sgn;
+    return EMSURF_OK;
+}
+
+int slab_cell_plan(double a, double b, double h, int n, const double* zlevels, double side,
+                   int patch_n, int ring_layers, SlabPlan& out) {
+    if (!zlevels || n < 2) { set_error("slab cell needs n >= 2 and the box row heights"); return EMSURF_EINVAL; }
+    for (int k = 0; k < n; ++k)
+        if (!(zlevels[k + 1] > zlevels[k])) { set_error("zlevels must increase"); return EMSURF_EINVAL; }
+    if (zlevels[0] != 0.0 || zlevels[n] != h) { set_error("zlevels must run from 0 to h"); return EMSURF_EINVAL; }
+    MeshOut box, top;
+    std::vector<int32_t> gv;
+    EMS_TRY(build_box(a, b, h, n, zlevels, box, &gv));
+    std::vector<int8_t> pec;
+    const double zt = zlevels[1];
+    if (side > 0.0) EMS_TRY(build_slab_top(a, b, zt, n, side, patch_n, ring_layers, top, pec));
+    else EMS_TRY(build_bare_top(a, b, zt, n, top, pec));
+    const int Vb = (int)box.verts.size() / 3, Tb = (int)box.tris.size() / 3, E = (int)box.tplus.size();
+    const int Vt = (int)top.verts.size() / 3, Tt = (int)top.tris.size() / 3;
+    // top vertex -> region vertex: interior ones after the box's, boundary
+    // ones onto the box vertices of grid row 1
+    const std::vector<int32_t> bidx = box_index(n);
+    std::vector<int32_t> remap(Vt);
+    for (int v = 0; v < Vt; ++v) remap[v] = Vb + v;
+    const auto per = grid_perimeter(n);
+    for (int s = 0; s < 4 * n; ++s)
+        remap[Vt - 4 * n + s] = bidx[((size_t)per[s].first * (n + 1) + per[s].second) * (n + 1) + 1];
+    std::map<std::pair<int, int>, int> box_edge, top_rwg;
+    for (int e = 0; e < E; ++e) box_edge[{box.edges[2 * e], box.edges[2 * e + 1]}] = e;
+    for (int r = 0; r < (int)top.tplus.size(); ++r)
+        top_rwg[{std::min(top.tplus[r], top.tminus[r]), std::max(top.tplus[r], top.tminus[r])}] = r;
+    // region triangles: box triangles by their highest grid row, then the whole top
+    std::vector<std::vector<int>> key(2);      // >= 0: box triangle; < 0: -(top triangle) - 1
+    MeshOut reg[2];
+    for (int v = 0; v < 2; ++v) {
+        reg[v].verts = box.verts;
+        reg[v].verts.insert(reg[v].verts.end(), top.verts.begin(), top.verts.end());
+        for (int t = 0; t < Tb; ++t) {
+            int row = 0;
+            for (int c = 0; c < 3; ++c) row = std::max(row, gv[3 * box.tris[3 * t + c] + 2]);
+            if ((v == 0) != (row >= 2)) continue;
+            push_tri(reg[v], box.tris[3 * t], box.tris[3 * t + 1], box.tris[3 * t + 2]);
+            key[v].push_back(t);
+        }
+        for (int t = 0; t < Tt; ++t) {
+            push_tri(reg[v], remap[top.tris[3 * t]], remap[top.tris[3 * t + 1]], remap[top.tris[3 * t + 2]]);
+            key[v].push_back(-t - 1);
+        }
+        EMS_TRY(finish_mesh(reg[v], true));
+    }
+    // U (Eq. incidence1): region unknown -> X~ column, interior columns by
+    // first appearance, S_eq columns after them (coded -1 - k until then)
+    const int nrt = (int)top.tplus.size();
+    std::vector<int> shJ(nrt, -1), shM(nrt, -1);
+    int nint = 0;
+    struct Ent { int col, local, sgn; };
+    std::vector<Ent> ents[2];
+    for (int v = 0; v < 2; ++v) {
+        const MeshOut& m = reg[v];
+        const int Ev = (int)m.tplus.size();
+        const int side_v = v == 1 ? 1 : -1;
+        for (int r = 0; r < Ev; ++r) {
+            const int tp = m.tplus[r], tm = m.tminus[r];
+            const int kp = key[v][tp], km = key[v][tm];
+            if (kp >= 0 || km >= 0) {
+                const int te = kp >= 0 ? tp : tm, tb = kp >= 0 ? kp : km;
+                const int other = kp >= 0 ? km : kp;
+                if (other < 0 && pec[-other - 1]) { set_error("PEC touching S_eq is not modelled"); return EMSURF_EINVAL; }
+                const int p0 = m.edges[2 * r], p1 = m.edges[2 * r + 1];
+                auto it = box_edge.find({p0, p1});
+                if (p1 >= Vb || it == box_edge.end()) { set_error("slab cell: S_eq edge not found"); return EMSURF_EINVAL; }
+                const int e = it->second;
+                const int s = slot_sign(m, r, te) * slot_sign(box, e, tb);
+                ents[v].push_back({-1 - e, r, s});
+                ents[v].push_back({-1 - (E + e), Ev + r, s});
+                continue;
+            }
+            const int a0 = -kp - 1, b0 = -km - 1;
+            auto it = top_rwg.find({std::min(a0, b0), std::max(a0, b0)});
+            if (it == top_rwg.end()) { set_error("slab cell: interface RWG not found"); return EMSURF_EINVAL; }
+            const int sr = it->second;
+            const int s = slot_sign(m, r, tp) * slot_sign(top, sr, a0);
+            const int npec = pec[a0] + pec[b0];
+            if (npec == 2) {                                   // rule 2: one current per side
+                ents[v].push_back({nint++, r, s});
+            } else {                                           // rules 1 and 3: shared, opposite sides
+                if (shJ[sr] < 0) shJ[sr] = nint++;
+                ents[v].push_back({shJ[sr], r, side_v * s});
+                if (npec == 0) {                               // rule 1 also shares M
+                    if (shM[sr] < 0) shM[sr] = nint++;
+                    ents[v].push_back({shM[sr], Ev + r, side_v * s});
+                }
+            }
+        }
+    }
+    out.n_int = nint;
+    out.N = nint + 2 * E;
+    out.E = E;
+    for (int v = 0; v < 2; ++v) {
+        out.copy[v].assign(out.N, -1);
+        out.sgn[v].assign(out.N, 0);
+        for (const Ent& en : ents[v]) {
+            const int col = en.col >= 0 ? en.col : nint + (-en.col - 1);
+            if (out.copy[v][col] >= 0) { set_error("slab cell: two copies of one unknown in a region"); return EMSURF_EINVAL; }
+            if (en.sgn == 0) { set_error("slab cell: orientation lookup failed"); return EMSURF_EINVAL; }
+            out.copy[v][col] = en.local;
+            out.sgn[v][col] = (int8_t)en.sgn;
+        }
+        SlabRegionMesh& rm = out.region[v];
+        rm.verts = reg[v].verts;
+        rm.tris = reg[v].tris;
+        rm.slot_rwg = reg[v].slot_rwg;
+        rm.slot_sgn = reg[v].slot_sgn;
+        rm.T = (int)reg[v].tris.size() / 3;
+        rm.E = (int)reg[v].tplus.size();
+    }
+    return EMSURF_OK;
+}
+
+namespace {
 }  // namespace
 }  // namespace emsurf
 
@@ -346,6 +602,58 @@ EMSURF_API int emsurf_setup_overlap(int32_t n, int32_t nx, int32_t ny, int32_t* 
             uo_sign[c * K + k] = (int8_t)(p * it->second.second);
         }
     *n_unique = next;
+    return EMSURF_OK;
+}
+
+
+EMSURF_API int emsurf_setup_slab_zlevels(double h, int32_t n, double slab_t, double* zlevels) {
+    if (n < 2 || !(slab_t > 0.0) || !(slab_t < h) || !zlevels) {
+        set_error("emsurf_setup_slab_zlevels needs n >= 2 and 0 < slab_t < h");
+        return EMSURF_EINVAL;
+    }
+    zlevels[0] = 0.0;
+    for (int k = 1; k <= n; ++k) zlevels[k] = slab_t + (h - slab_t) * (k - 1) / (n - 1);
+    return EMSURF_OK;
+}
+
+EMSURF_API int emsurf_setup_slab_top_counts(double a, double b, int32_t n, double side,
+                                            int32_t patch_n, int32_t ring_layers,
+                                            int32_t* n_verts, int32_t* n_tris, int32_t* n_edges) {
+    std::vector<double> v;
+    std::vector<int32_t> t, e, tp, tm, sr;
+    std::vector<int8_t> ss, pc;
+    EMS_TRY(slab_top(a, b, 0.0, n, side, patch_n, ring_layers, v, t, e, tp, tm, sr, ss, pc));
+    if (n_verts) *n_verts = (int32_t)(v.size() / 3);
+    if (n_tris) *n_tris = (int32_t)(t.size() / 3);
+    if (n_edges) *n_edges = (int32_t)tp.size();
+    return EMSURF_OK;
+}
+
+EMSURF_API int emsurf_setup_slab_top_mesh(double a, double b, double z, int32_t n, double side,
+                                          int32_t patch_n, int32_t ring_layers, double* verts,
+                                          int32_t* tris, int32_t* edges, int32_t* tplus,
+                                          int32_t* tminus, int32_t* slot_rwg, int8_t* slot_sgn,
+                                          int8_t* on_patch) {
+    MeshOut m;
+    std::vector<int8_t> pc;
+    EMS_TRY(slab_top(a, b, z, n, side, patch_n, ring_layers, m.verts, m.tris, m.edges, m.tplus,
+                     m.tminus, m.slot_rwg, m.slot_sgn, pc));
+    copy_mesh(m, verts, tris, edges, tplus, tminus, slot_rwg, slot_sgn);
+    if (on_patch) std::copy(pc.begin(), pc.end(), on_patch);
+    return EMSURF_OK;
+}
+
+EMSURF_API int emsurf_setup_slab_cell_counts(double a, double b, double h, int32_t n,
+                                             const double* zlevels, double side, int32_t patch_n,
+                                             int32_t ring_layers, int32_t* n_interior,
+                                             int32_t* region_edges) {
+    SlabPlan pl;
+    EMS_TRY(slab_cell_plan(a, b, h, n, zlevels, side, patch_n, ring_layers, pl));
+    if (n_interior) *n_interior = pl.n_int;
+    if (region_edges) {
+        region_edges[0] = pl.region[0].E;
+        region_edges[1] = pl.region[1].E;
+    }
     return EMSURF_OK;
 }
 

@@ -108,6 +108,52 @@ __device__ __forceinline__ void green_smooth(double R, double k, double2& Gs, do
     gfac = make_double2(hh.x / (kFourPi * R), hh.y / (kFourPi * R));
 }
 
+// Lossy region (Sec. II-B, k_v = w sqrt(mu0 eps_v) with complex eps_v): the
+// same two functions for k = kr + j ki, e^{-jkR} = e^{ki R} e^{-j kr R}.
+__device__ __forceinline__ double2 exp_mjkR(double R, double kr, double ki) {
+    double s, c;
+    sincos(kr * R, &s, &c);
+    const double m = exp(ki * R);
+    return make_double2(m * c, -m * s);
+}
+
+__device__ __forceinline__ void green_far_cx(double R, double kr, double ki, double2& G, double2& gfac) {
+    const double2 e = exp_mjkR(R, kr, ki);
+    G = make_double2(e.x / (kFourPi * R), e.y / (kFourPi * R));
+    const double2 ae = cmul(make_double2(1.0 - ki * R, kr * R), e);     // (1 + jkR) e
+    const double d = -1.0 / (kFourPi * R * R * R);
+    gfac = make_double2(ae.x * d, ae.y * d);
+}
+
+__device__ __forceinline__ void green_smooth_cx(double R, double kr, double ki, double2& Gs, double2& gfac) {
+    if (hypot(kr, ki) * R < 0.1) {
+        double2 c = make_double2(1.0, 0.0);
+        double2 g = make_double2(0.0, 0.0), h = make_double2(0.0, 0.0);
+        double Rp_n1 = 1.0, Rp_n2 = 0.0;
+        for (int n = 1; n < 12; ++n) {
+            c = cmul(c, make_double2(ki / (double)n, -kr / (double)n));   // (-jk)^n / n!
+            g.x += c.x * Rp_n1;
+            g.y += c.y * Rp_n1;
+            if (n >= 2) {
+                h.x += c.x * (double)(n - 1) * Rp_n2;
+                h.y += c.y * (double)(n - 1) * Rp_n2;
+            }
+            Rp_n2 = Rp_n1;
+            Rp_n1 *= R;
+        }
+        Gs = make_double2(g.x / kFourPi, g.y / kFourPi);
+        if (R > 0.0) gfac = make_double2(h.x / (kFourPi * R), h.y / (kFourPi * R));
+        else gfac = make_double2(0.0, 0.0);
+        return;
+    }
+    const double2 e = exp_mjkR(R, kr, ki);
+    Gs = make_double2((e.x - 1.0) / (kFourPi * R), e.y / (kFourPi * R));
+    const double2 ae = cmul(make_double2(1.0 - ki * R, kr * R), e);
+    const double R2 = R * R;
+    const double2 hh = make_double2((1.0 - ae.x) / R2, -ae.y / R2);
+    gfac = make_double2(hh.x / (kFourPi * R), hh.y / (kFourPi * R));
+}
+
 __device__ __forceinline__ double edge_log(double lp, double lm, double Rp, double Rm, double R02) {
     if (lm >= 0.0) return log((Rp + lp) / (Rm + lm));
     if (lp <= 0.0) return log((Rm - lm) / (Rp - lp));
@@ -148,11 +194,13 @@ __device__ void potentials(Vec3 r, const TriGeo& T, double& I0, Vec3& I1, Vec3& 
     Ig = (-sg * bsum) * n - fu;
 }
 
-// out[((b*Tt + t)*Ts + s)*18 + {0..8: L(i,j), 9..17: K(i,j)}]
+// out[((b*Tt + t)*Ts + s)*18 + {0..8: L(i,j), 9..17: K(i,j)}]; CX: complex
+// wavenumber k + j ki (lossy region), else ki is ignored
+template <bool CX>
 __global__ void __launch_bounds__(128)
 tri_pairs_kernel(const TriGeo* __restrict__ tg, int Tt, const TriGeo* __restrict__ sg, int Ts,
                  const double* __restrict__ shifts, const int8_t* __restrict__ sing, int b0,
-                 double k, double2* __restrict__ out) {
+                 double k, double ki, double2* __restrict__ out) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const int t = blockIdx.y;
     const int bl = blockIdx.z;
@@ -162,7 +210,15 @@ tri_pairs_kernel(const TriGeo* __restrict__ tg, int Tt, const TriGeo* __restrict
     const TriGeo& S = sg[s];
     const Vec3 sh = v3(shifts + 3 * b);
     const bool singular = sing[b] != 0;
-    const double ik2 = 4.0 / (k * k);
+    double2 ik2c;                                   // 4 / k^2
+    if constexpr (CX) {
+        const double2 k2 = make_double2(k * k - ki * ki, 2.0 * k * ki);
+        const double d = 4.0 / (k2.x * k2.x + k2.y * k2.y);
+        ik2c = make_double2(k2.x * d, -k2.y * d);
+    } else {
+        ik2c = make_double2(4.0 / (k * k), 0.0);
+    }
+    const double ik2 = ik2c.x;
     double2 CL[9], CK[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) CL[q] = CK[q] = make_double2(0.0, 0.0);
@@ -182,8 +238,13 @@ tri_pairs_kernel(const TriGeo* __restrict__ tg, int Tt, const TriGeo* __restrict
             // coincident points (up to rounding) take the R -> 0 limit of the
             // remainder: -jk/(4 pi) and no gradient term
             if (singular && R <= 1e-9 * S.scale) R = 0.0;
-            if (singular) green_smooth(R, k, G, gf);
-            else green_far(R, k, G, gf);
+            if constexpr (CX) {
+                if (singular) green_smooth_cx(R, k, ki, G, gf);
+                else green_far_cx(R, k, ki, G, gf);
+            } else {
+                if (singular) green_smooth(R, k, G, gf);
+                else green_far(R, k, G, gf);
+            }
             const double2 WG = make_double2(W * G.x, W * G.y);
             sumWG.x += WG.x;
             sumWG.y += WG.y;
@@ -215,6 +276,7 @@ tri_pairs_kernel(const TriGeo* __restrict__ tg, int Tt, const TriGeo* __restrict
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
                     CL[3 * i + j].x += f * (dot(a[i], vecL) - ik2 * I0);
+                    if constexpr (CX) CL[3 * i + j].y -= f * ik2c.y * I0;
                     CK[3 * i + j].x += f * dot(a[i], cr);
                 }
             }
@@ -223,7 +285,12 @@ tri_pairs_kernel(const TriGeo* __restrict__ tg, int Tt, const TriGeo* __restrict
     double2* o = out + (((size_t)bl * Tt + t) * Ts + s) * 18;
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
-        o[q] = make_double2(CL[q].x - ik2 * sumWG.x, CL[q].y - ik2 * sumWG.y);
+        if constexpr (CX) {
+            const double2 t = cmul(ik2c, sumWG);
+            o[q] = make_double2(CL[q].x - t.x, CL[q].y - t.y);
+        } else {
+            o[q] = make_double2(CL[q].x - ik2 * sumWG.x, CL[q].y - ik2 * sumWG.y);
+        }
         o[9 + q] = CK[q];
     }
 }
@@ -323,11 +390,14 @@ int prepare_mesh(const double* verts, const int32_t* tris, const int32_t* slot_r
 }  // namespace
 
 
-// L, K: device [nb][Et][Es]
-int tabulate_blocks(const MeshView& test, const MeshView& src, const double* shifts,
-                    const int8_t* singular, int nb, double k, double2* L, double2* K,
-                    cudaStream_t st) {
-    if (!(k > 0.0) || nb < 1) { set_error("tabulate needs k > 0 and >= 1 block"); return EMSURF_EINVAL; }
+// L, K: device [nb][Et][Es]; wavenumber k + j ki (ki = 0: lossless)
+int tabulate_blocks_cx(const MeshView& test, const MeshView& src, const double* shifts,
+                       const int8_t* singular, int nb, double k, double ki, double2* L, double2* K,
+                       cudaStream_t st) {
+    if (!(k > 0.0) || !(ki <= 0.0) || nb < 1) {
+        set_error("tabulate needs Re k > 0, Im k <= 0 and >= 1 block");
+        return EMSURF_EINVAL;
+    }
     std::vector<TriGeo> tg, sgeo;
     std::vector<RwgSlots> tr, sr;
     EMS_TRY(prepare_mesh(test.verts, test.tris, test.slot_rwg, test.slot_sgn, test.T, test.E, tg, tr));
@@ -365,7 +435,10 @@ int tabulate_blocks(const MeshView& test, const MeshView& src, const double* shi
         for (int b0 = 0; b0 < nb && !status; b0 += chunk) {
             const int nc = std::min(chunk, nb - b0);
             dim3 g1((src.T + 127) / 128, test.T, nc);
-            tri_pairs_kernel<<<g1, 128, 0, st>>>(dtg, test.T, dsg, src.T, dsh, dsi, b0, k, scratch);
+            if (ki != 0.0)
+                tri_pairs_kernel<true><<<g1, 128, 0, st>>>(dtg, test.T, dsg, src.T, dsh, dsi, b0, k, ki, scratch);
+            else
+                tri_pairs_kernel<false><<<g1, 128, 0, st>>>(dtg, test.T, dsg, src.T, dsh, dsi, b0, k, 0.0, scratch);
             if ((e = cudaGetLastError()) != cudaSuccess) { fail(e, "tri_pairs_kernel"); break; }
             const size_t tot = (size_t)nc * test.E * src.E;
             const int g2 = (int)std::min<size_t>((tot + 255) / 256, 152 * 64);
@@ -385,6 +458,12 @@ int tabulate_blocks(const MeshView& test, const MeshView& src, const double* shi
     return status;
 }
 
+int tabulate_blocks(const MeshView& test, const MeshView& src, const double* shifts,
+                    const int8_t* singular, int nb, double k, double2* L, double2* K,
+                    cudaStream_t st) {
+    return tabulate_blocks_cx(test, src, shifts, singular, nb, k, 0.0, L, K, st);
+}
+
 // ---------------------------------------------------------------------------
 // Allocation-free tabulation.  Scratch lives in one file-scope device array
 // that every GPU loading this library holds until the process exits.  Host
@@ -398,7 +477,27 @@ static __device__ __align__(256) unsigned char g_tab_scratch[kNoAllocBytes];
 
 std::mutex g_tab_scratch_mu;
 constexpr int kMaxDevices = 64;
-void* g_tab_scratch_addr[kMaxDevices] = {nullptr};
+struct ScratchAddr {
+    void* ctx = nullptr;     // context the address was taken in
+    void* addr = nullptr;
+};
+ScratchAddr g_tab_scratch_addr[kMaxDevices];
+
+// cuCtxGetCurrent through the runtime's driver entry point (no link to the
+// driver library); a context created after a device reset gets a new handle,
+// so the cached address is taken again in it
+using CtxGetCurrentFn = int (*)(void**);
+CtxGetCurrentFn ctx_get_current() {
+    static CtxGetCurrentFn fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess || q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<CtxGetCurrentFn>(f);
+    }();
+    return fn;
+}
 
 int scratch_address(void** out) {
     int dev = -1;
@@ -407,18 +506,25 @@ int scratch_address(void** out) {
         set_error("device ordinal %d outside [0, %d)", dev, kMaxDevices);
         return EMSURF_EINVAL;
     }
+    const CtxGetCurrentFn fn = ctx_get_current();
+    void* ctx = nullptr;
+    if (fn) fn(&ctx);
     std::lock_guard<std::mutex> lock(g_tab_scratch_mu);
-    if (!g_tab_scratch_addr[dev]) {
+    ScratchAddr& c = g_tab_scratch_addr[dev];
+    if (!c.addr || !ctx || c.ctx != ctx) {
         void* p = nullptr;
+        // binds the device's primary context if none is current yet
         const cudaError_t e = cudaGetSymbolAddress(&p, g_tab_scratch);
         if (e != cudaSuccess || !p) {
             set_error("cudaGetSymbolAddress of the static scratch failed on device %d: %s", dev,
                       cudaGetErrorString(e));
             return EMSURF_ECUDA;
         }
-        g_tab_scratch_addr[dev] = p;
+        if (fn && !ctx) fn(&ctx);
+        c.ctx = ctx;
+        c.addr = p;
     }
-    *out = g_tab_scratch_addr[dev];
+    *out = c.addr;
     return EMSURF_OK;
 }
 
@@ -460,27 +566,37 @@ int tabulate_blocks_noalloc(const MeshView& test, const MeshView& src, const dou
     const int chunk = (int)std::min<size_t>(nb, (kNoAllocBytes - o_pairs) / per_block);
     double bary[7][3], w[7];
     radon7(bary, w);
-    EMS_CUDA(cudaMemcpyToSymbolAsync(c_w, w, sizeof(w), 0, cudaMemcpyHostToDevice, st));
-    EMS_CUDA(cudaMemcpyAsync(dtg, tg.data(), sizeof(TriGeo) * tg.size(), cudaMemcpyHostToDevice, st));
-    EMS_CUDA(cudaMemcpyAsync(dsg, sgeo.data(), sizeof(TriGeo) * sgeo.size(), cudaMemcpyHostToDevice, st));
-    EMS_CUDA(cudaMemcpyAsync(dtr, tr.data(), sizeof(RwgSlots) * tr.size(), cudaMemcpyHostToDevice, st));
-    EMS_CUDA(cudaMemcpyAsync(dsr, sr.data(), sizeof(RwgSlots) * sr.size(), cudaMemcpyHostToDevice, st));
-    EMS_CUDA(cudaMemcpyAsync(dsh, shifts, sizeof(double) * 3 * nb, cudaMemcpyHostToDevice, st));
-    EMS_CUDA(cudaMemcpyAsync(dsi, singular, nb, cudaMemcpyHostToDevice, st));
+    // from the first queued copy on, every return goes through the stream
+    // synchronisation below, so no queued work outlives the call
+    int status = EMSURF_OK;
+    auto step = [&](cudaError_t e, const char* what) {
+        if (status == EMSURF_OK && e != cudaSuccess) {
+            set_error("emsurf_tabulate_noalloc: %s: %s", what, cudaGetErrorString(e));
+            status = EMSURF_ECUDA;
+        }
+    };
+    step(cudaMemcpyToSymbolAsync(c_w, w, sizeof(w), 0, cudaMemcpyHostToDevice, st), "copy weights");
+    if (!status) step(cudaMemcpyAsync(dtg, tg.data(), sizeof(TriGeo) * tg.size(), cudaMemcpyHostToDevice, st), "copy");
+    if (!status) step(cudaMemcpyAsync(dsg, sgeo.data(), sizeof(TriGeo) * sgeo.size(), cudaMemcpyHostToDevice, st), "copy");
+    if (!status) step(cudaMemcpyAsync(dtr, tr.data(), sizeof(RwgSlots) * tr.size(), cudaMemcpyHostToDevice, st), "copy");
+    if (!status) step(cudaMemcpyAsync(dsr, sr.data(), sizeof(RwgSlots) * sr.size(), cudaMemcpyHostToDevice, st), "copy");
+    if (!status) step(cudaMemcpyAsync(dsh, shifts, sizeof(double) * 3 * nb, cudaMemcpyHostToDevice, st), "copy");
+    if (!status) step(cudaMemcpyAsync(dsi, singular, nb, cudaMemcpyHostToDevice, st), "copy");
     // every pair integral is written before it is read, so nothing needs clearing
-    for (int b0 = 0; b0 < nb; b0 += chunk) {
+    for (int b0 = 0; b0 < nb && !status; b0 += chunk) {
         const int nc = std::min(chunk, nb - b0);
         dim3 g1((src.T + 127) / 128, test.T, nc);
-        tri_pairs_kernel<<<g1, 128, 0, st>>>(dtg, test.T, dsg, src.T, dsh, dsi, b0, k, pairs);
-        EMS_CUDA(cudaGetLastError());
+        tri_pairs_kernel<false><<<g1, 128, 0, st>>>(dtg, test.T, dsg, src.T, dsh, dsi, b0, k, 0.0, pairs);
+        step(cudaGetLastError(), "tri_pairs_kernel");
+        if (status) break;
         const size_t tot = (size_t)nc * test.E * src.E;
         const int g2 = (int)std::min<size_t>((tot + 255) / 256, 152 * 64);
         rwg_gather_kernel<<<g2, 256, 0, st>>>(pairs, dtr, test.E, dsr, src.E, test.T, src.T, b0, nc,
                                               L, K);
-        EMS_CUDA(cudaGetLastError());
+        step(cudaGetLastError(), "rwg_gather_kernel");
     }
-    EMS_CUDA(cudaStreamSynchronize(st));
-    return EMSURF_OK;
+    step(cudaStreamSynchronize(st), "synchronize");
+    return status;
 }
 
 }  // namespace
@@ -558,9 +674,9 @@ __global__ void reciprocal_part_kernel(double2* __restrict__ L, double2* __restr
 
 extern "C" {
 
-EMSURF_API int emsurf_tabulate_offsets(double a, double b, double h, int32_t n, int32_t nx,
-                                       int32_t ny, double k, emsurf_c128* L, emsurf_c128* K,
-                                       void* stream) {
+EMSURF_API int emsurf_tabulate_offsets(double a, double b, double h, int32_t n,
+                                       const double* zlevels, int32_t nx, int32_t ny, double k,
+                                       emsurf_c128* L, emsurf_c128* K, void* stream) {
     if (n < 1 || nx < 1 || ny < 1 || !L || !K) {
         set_error("emsurf_tabulate_offsets: bad sizes or NULL output");
         return EMSURF_EINVAL;
@@ -570,7 +686,7 @@ EMSURF_API int emsurf_tabulate_offsets(double a, double b, double h, int32_t n, 
     std::vector<double> verts(3 * V);
     std::vector<int32_t> tris(3 * T), edges(2 * E), tp(E), tm(E), srw(3 * T);
     std::vector<int8_t> ssg(3 * T);
-    EMS_TRY(emsurf_setup_box_mesh(a, b, h, n, nullptr, verts.data(), tris.data(), edges.data(),
+    EMS_TRY(emsurf_setup_box_mesh(a, b, h, n, zlevels, verts.data(), tris.data(), edges.data(),
                                   tp.data(), tm.data(), srw.data(), ssg.data()));
     const int nox = 2 * nx - 1, noy = 2 * ny - 1;
     std::vector<double> shifts(3 * (size_t)nox * noy);

@@ -77,3 +77,45 @@ def test_unknown_positions_reject_bad_index(B):
     bad[5] = nu
     with pytest.raises(B.EmsurfError):
         B.emsurf_setup_unknown_xy(0.015, 0.015, 0.0075, 1, 2, 2, bad, nu)
+
+
+@pytest.mark.parametrize("n,side,pn,layers", [(2, 0.009, 3, 1), (3, 0.009, 4, 3), (4, 0.0135, 4, 3),
+                                              (4, 0.0045, 3, 2), (3, 0.0, 4, 3), (4, -1.0, 4, 3)])
+def test_slab_top_mesh_matches_oracle(B, n, side, pn, layers):
+    """The slab-top interface (patch grid, graded rings, zipped band onto the
+    footprint boundary; or the bare footprint grid) and its patch flags."""
+    from oracle.macromodel import _bare_top
+    from oracle.mesh import slab_top_mesh
+    a, b, z = 0.015, 0.015, 0.00076
+    p = B.emsurf_setup_slab_top_mesh(a, b, z, n, side, pn, layers)
+    o, pec = slab_top_mesh(a, b, z, n, side, pn, layers) if side > 0 else _bare_top(a, b, z, n)
+    _same_mesh(p, o)
+    assert np.array_equal(p["on_patch"].astype(bool), pec)
+
+
+def test_slab_zlevels_match_oracle(B):
+    from oracle.mesh import slab_zlevels
+    for n in (2, 3, 4, 6):
+        assert np.allclose(B.emsurf_setup_slab_zlevels(0.0075, n, 0.00076), slab_zlevels(0.0075, n, 0.00076),
+                           rtol=0, atol=1e-18)
+    for bad in ((0.0075, 1, 0.00076), (0.0075, 3, 0.0), (0.0075, 3, 0.008)):
+        with pytest.raises(B.EmsurfError):
+            B.emsurf_setup_slab_zlevels(*bad)
+
+
+@pytest.mark.parametrize("n,side,pn,layers", [(2, 0.009, 3, 2), (3, 0.0, 4, 3), (4, 0.0135, 4, 3)])
+def test_slab_cell_unknown_counts_match_oracle(B, n, side, pn, layers):
+    """The product's U plan eliminates as many interior unknowns as the
+    oracle's U of Eq. incidence1 (rules 1-3 count J and M per edge kind)."""
+    from oracle.macromodel import _bare_top
+    from oracle.mesh import slab_region_meshes, slab_top_mesh, slab_zlevels
+    a, h, t = 0.015, 0.0075, 0.00076
+    z = slab_zlevels(h, n, t)
+    box = box_mesh(a, a, h, n, z)
+    top, pec = slab_top_mesh(a, a, t, n, side, pn, layers) if side > 0 else _bare_top(a, a, t, n)
+    (air, _), (slab, _) = slab_region_meshes(box, n, top)
+    # interior unknowns by the rules: rule 1 edges J + M, rule 3 edges J, rule 2 edges J per side
+    npec = np.array([int(pec[top.tplus[e]]) + int(pec[top.tminus[e]]) for e in range(top.n_rwg)])
+    expect = 2 * np.sum(npec == 0) + np.sum(npec == 1) + 2 * np.sum(npec == 2)
+    ni, (ea, es) = B.emsurf_setup_slab_cell_counts(a, a, h, n, z, side, pn, layers)
+    assert ni == expect and ea == air.n_rwg and es == slab.n_rwg
