@@ -40,13 +40,13 @@ RESTART = 30
 REF_MATVECS_PER_SOLVE = 1907
 FALLBACK_HBM_GBS = 6800.0
 PC_OVERLAP = 0.6               # preconditioner margin, in mesh cells (a / n)
-# DRAM bytes (read + write) per bin of one binmul_tma_kernel launch, from the
-# ncu capture in profiles/binmul_tma_lattice12x12_k576.md (12x12 lattice,
-# 576 bins); the kernel streams each bin's blocks once, so traffic scales
-# with the bin count.
+# DRAM bytes (read + write) per bin of one binmul_tma_kernel launch, from an
+# ncu capture of the 12x12 lattice (576 bins, dram__bytes_read.sum +
+# dram__bytes_write.sum); the kernel streams each bin's blocks once, so
+# traffic scales with the bin count.
 BINMUL_DRAM_BYTES_PER_BIN = (767108096 + 5353216) / 576
 # the same for binmul_tma_pair_kernel (half spectrum) per stored bin, from
-# profiles/binmul_tma_pair_lattice12x12_k576.md (290 stored bins)
+# the capture of the 12x12 lattice (290 stored bins)
 PAIR_DRAM_BYTES_PER_STORED_BIN = (387588096 + 3930624) / 290
 
 
@@ -81,7 +81,7 @@ def multi_rhs_section(B, W, torch, w, hbm):
     out = {"R": MULTI_RHS}
     tflops_peak, tkind = bf16_peak()
     for tc in (True, False):
-        h, _, nu, _ = build_problem(B, W, torch, w, B.FP32, precond=False, max_rhs=MULTI_RHS,
+        h, _, nu, _, _ = build_problem(B, W, torch, w, B.FP32, precond=False, max_rhs=MULTI_RHS,
                                     tensor_cores=tc)
         px, py, _ = B.emsurf_query(h)
         P = px * py
@@ -176,44 +176,193 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def batched_section(B, W, torch):
-    """Many right-hand sides on a large lattice: 48 x 48 cells, K = 576
-    (839,432 unknowns), 32 plane waves, MIXED with tensor-core planes and the
-    near-field preconditioner.  One JSON line (a configuration of the paper's
-    batched use, not the benchmark line)."""
-    w = W.WORKLOADS["lattice48x48_k576_r32"]
-    t0 = time.time()
-    h, V, nu, setup = build_problem(B, W, torch, w, B.MIXED, max_rhs=w.n_rhs, tensor_cores=True)
-    setup["total_s"] = round(time.time() - t0, 2)
-    out = {"section": "batched", "workload": w.name, "unknowns": nu, "rhs": w.n_rhs, "setup": setup,
-           "fp32_matvec_ms": round(time_matvec(B, torch, h, nu, w.n_rhs, B.FP32, reps=5), 3),
-           "fp64_accuracy_matvec_ms": round(time_matvec(B, torch, h, nu, w.n_rhs, B.FP64, reps=2), 1)}
+def _rcs_grid(step_deg):
+    th = np.radians(np.arange(0.0, 180.0 + 1e-9, step_deg))
+    ph = np.radians(np.arange(0.0, 360.0, step_deg))
+    TH, PH = np.meshgrid(th, ph, indexing="ij")
+    return np.stack([np.sin(TH) * np.cos(PH), np.sin(TH) * np.sin(PH), np.cos(TH)], -1).reshape(-1, 3)
+
+
+def _rcs(B, torch, h, w, zl, X, rhat):
+    from paper_1911_04576_gb300 import workloads as W_
+    F = torch.empty((X.shape[0], len(rhat), 3), dtype=torch.complex128, device="cuda")
+    rcs = torch.empty((X.shape[0], len(rhat)), dtype=torch.float64, device="cuda")
+    B.emsurf_far_field(h, W_.PERIOD, W_.PERIOD, W_.BOX_H, w.n, W_.K0, X, rhat, F, rcs, zlevels=zl)
+    del F
+    return rcs
+
+
+def _db_diff(a, b, floor_db=40.0):
+    """max |10 log10(a/b)| over directions where b > max(b) - floor_db (per rhs)."""
+    a, b = np.asarray(a), np.asarray(b)
+    out = 0.0
+    for r in range(b.shape[0]):
+        bd = 10 * np.log10(np.maximum(b[r], 1e-300))
+        ad = 10 * np.log10(np.maximum(a[r], 1e-300))
+        keep = bd > bd.max() - floor_db
+        out = max(out, float(np.abs(ad[keep] - bd[keep]).max()))
+    return out
+
+
+def _timed(fn):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = fn()
+    torch.cuda.synchronize()
+    return r, (time.perf_counter() - t0) * 1e3
+
+
+def _binmul_live(B, torch, h, x, prec, reps):
+    """CUDA-event average of the bin multiply over `reps` products (the
+    phase timer records on the product's stream) and the products' average."""
+    y = torch.empty_like(x)
+    B.emsurf_matvec(h, x, y, prec)
+    B.emsurf_profile_phases(h, ["binmul32" if prec == B.FP32 else "binmul64"])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        B.emsurf_matvec(h, x, y, prec)
+    e1.record()
+    torch.cuda.synchronize()
+    B.emsurf_profile(h, False)
+    ms, n = B.emsurf_profile_read(h, "binmul32" if prec == B.FP32 else "binmul64")
+    return ms / max(n, 1), e0.elapsed_time(e1) / reps
+
+
+def many_rhs_section(B, W, torch, name, hbm, bf16, time_left_s, rcs_step):
+    """A many-right-hand-side configuration measured end to end on the
+    product path: setup, FP32 (tensor-core) and FP64-accuracy products with
+    all rhs, the preconditioner apply, the MIXED solve of all rhs to 1e-6,
+    and the bistatic RCS of every rhs on a rcs_step-degree grid; the
+    tensor-core bin multiply's live average against the HBM roofline."""
+    w = W.WORKLOADS[name]
+    t_start = time.time()
+    h, V, nu, setup, zl = build_problem(B, W, torch, w, B.MIXED, max_rhs=w.n_rhs, tensor_cores=True)
+    setup["total_s"] = round(time.time() - t_start, 2)
+    px, py, dev_bytes = B.emsurf_query(h)
+    P = px * py
+    out = {"workload": w.name, "lattice": [w.nx, w.ny], "K": w.K, "n_types": w.n_types,
+           "type_map": w.type_rule, "unknowns": nu, "rhs": w.n_rhs, "grid": [px, py],
+           "setup": setup, "device_bytes": dev_bytes}
+    x = torch.randn((w.n_rhs, nu), dtype=torch.complex128, device="cuda")
+    bm32, mv32 = _binmul_live(B, torch, h, x, B.FP32, 5)
+    spec = 2 * w.E * w.E * P * 8                       # bf16 hi + lo planes = complex64 bytes
+    useful = 32.0 * w.E * w.E * w.n_rhs * P            # complex MACs x 8 flops
+    out["fp32_matvec_ms"] = round(mv32, 3)
+    out["roofline"] = {"kernel": "binmul_tc_kernel (bin multiply, BF16x3 on tcgen05, %d rhs)" % w.n_rhs,
+                       "bound": "hbm", "achieved": round(spec / bm32 / 1e6, 1), "peak": hbm, "unit": "GB/s",
+                       "frac": round(spec / bm32 / 1e6 / hbm, 4), "avg_launch_ms": round(bm32, 4),
+                       "alg_bytes_per_launch": spec, "useful_tflops": round(useful / bm32 / 1e9, 1),
+                       "useful_frac_of_bf16_peak": round(useful / bm32 / 1e9 / bf16, 4)}
+    bm64, mv64 = _binmul_live(B, torch, h, x, B.FP64, 1)
+    out["fp64_accuracy_matvec_ms"] = round(mv64, 2)
+    out["fp64_accuracy_binmul_ms"] = round(bm64, 2)
     r = torch.randn_like(V)
     y = torch.empty_like(V)
     B.emsurf_precond_apply(h, r, y)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(5):
-        B.emsurf_precond_apply(h, r, y)
-    e1.record()
-    torch.cuda.synchronize()
-    out["precond_apply_ms"] = round(e0.elapsed_time(e1) / 5, 3)
+    _, t = _timed(lambda: [B.emsurf_precond_apply(h, r, y) for _ in range(5)])
+    out["precond_apply_ms"] = round(t / 5, 3)
+    del x, r, y
+    if time.time() - t_start > time_left_s:
+        out["skipped"] = "time limit before the solve"
+        h.close()
+        return out
     X = torch.zeros_like(V)
     B.emsurf_profile(h, True)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    st, info = B.emsurf_solve(h, V, X, rtol=RTOL, restart=RESTART, max_iters=20000, max_refine=20,
-                              solver=B.SOLVER_MIXED)
-    torch.cuda.synchronize()
-    out["solve_s"] = round(time.perf_counter() - t0, 3)
+    (st, info), t = _timed(lambda: B.emsurf_solve(h, V, X, rtol=RTOL, restart=RESTART, max_iters=20000,
+                                                  max_refine=20, solver=B.SOLVER_MIXED))
     B.emsurf_profile(h, False)
-    out["solve"] = {"status": st, "iters": info[0]["iters"], "refinements": info[0]["refinements"],
-                    "max_rel_residual": max(i["rel_residual"] for i in info)}
-    out["phases_ms"] = {p: round(B.emsurf_profile_read(h, p)[0], 1) for p in B.PHASES}
+    out["solve"] = {"rtol": RTOL, "ms": round(t, 1), "status": st, "iters": info[0]["iters"],
+                    "refinements": info[0]["refinements"], "n_matvec": info[0]["n_matvec"],
+                    "all_converged": all(i["converged"] for i in info),
+                    "max_rel_residual": max(i["rel_residual"] for i in info),
+                    "phases_ms": {p: round(B.emsurf_profile_read(h, p)[0], 1) for p in B.PHASES}}
+    if time.time() - t_start < time_left_s:
+        rhat = _rcs_grid(rcs_step)
+        rcs, t = _timed(lambda: _rcs(B, torch, h, w, zl, X, rhat))
+        s = rcs.cpu().numpy()
+        out["rcs"] = {"grid_deg": rcs_step, "directions": len(rhat), "rhs": w.n_rhs, "ms": round(t, 1),
+                      "max_dbsm": round(float(10 * np.log10(s.max())), 2)}
     B.emsurf_check(h)
     h.close()
-    print(json.dumps(out))
+    out["total_s"] = round(time.time() - t_start, 1)
+    return out
+
+
+def accuracy_section(B, torch, h, V, X_bench, w, zl):
+    """Result-level accuracy of the MIXED path against the FP64-operator
+    GMRES solved to 1e-11 (both preconditioned): currents (rel-L2) and
+    bistatic RCS (dB, where sigma > sigma_max - 40 dB) on a 2-degree grid,
+    for the bench's rtol and for the configuration's rtol 1e-8."""
+    X64 = torch.zeros_like(V)
+    (st, info64), t64 = _timed(lambda: B.emsurf_solve(h, V, X64, rtol=1e-11, restart=RESTART, max_iters=20000,
+                                                      solver=B.SOLVER_FP64))
+    X8 = torch.zeros_like(V)
+    (st8, info8), t8 = _timed(lambda: B.emsurf_solve(h, V, X8, rtol=1e-8, restart=RESTART, max_iters=20000,
+                                                     max_refine=20, solver=B.SOLVER_MIXED))
+    X8f = torch.zeros_like(V)
+    (st8f, info8f), t8f = _timed(lambda: B.emsurf_solve(h, V, X8f, rtol=1e-8, restart=RESTART, max_iters=20000,
+                                                        solver=B.SOLVER_FP64))
+    rhat = _rcs_grid(2.0)
+    s64 = _rcs(B, torch, h, w, zl, X64, rhat).cpu().numpy()
+    out = {"reference": "FP64-operator GMRES(30) + preconditioner to rtol 1e-11 (%d iters, %.1f ms)"
+                        % (info64[0]["iters"], t64),
+           "rcs_grid": "2 deg, %d directions; dB compared where sigma > sigma_max - 40 dB" % len(rhat)}
+    for key, X, t, info in (("mixed_rtol_1e-6", X_bench, None, None), ("mixed_rtol_1e-8", X8, t8, info8)):
+        xm = X.cpu().numpy()
+        x64 = X64.cpu().numpy()
+        sm = _rcs(B, torch, h, w, zl, X, rhat).cpu().numpy()
+        out[key] = {"currents_rel_l2": float(np.linalg.norm(xm - x64) / np.linalg.norm(x64)),
+                    "rcs_max_db": round(_db_diff(sm, s64), 5)}
+        if t is not None:
+            out[key]["solve_ms"] = round(t, 2)
+            out[key]["iters"] = info[0]["iters"]
+    out["fp64_rtol_1e-8"] = {"solve_ms": round(t8f, 2), "iters": info8f[0]["iters"],
+                             "converged": info8f[0]["converged"]}
+    return out
+
+
+def cpu_fft_section(W, w, nmv_plain, iters_pc):
+    """The timed CPU FFT baseline (complex128, scipy.fft with every host core
+    plus batched per-bin products): spectrum build, products, and GMRES
+    iterations with that product; the solve time is extrapolated by the
+    GPU FP64 GMRES(30)'s product count on the same operator."""
+    from oracle import cpu_fft, lattice, solve
+    from oracle.mesh import box_mesh
+    A = W.PERIOD
+    idx, sgn, nu = lattice.overlap_map(box_mesh(A, A, W.BOX_H, w.n), w.nx, w.ny, A, A)
+    Lt, Kt = W.random_tables(w.nx, w.ny, w.E, 1)
+    Z = W.random_macromodels(w.n_types, w.K, 2)
+    coef = (1j * W.K0, 1.0, -1.0, 1j * W.K0)
+    px, py = 2 * w.nx, 2 * w.ny
+    t0 = time.perf_counter()
+    Lh, Kh = cpu_fft.spectrum(Lt, Kt, px, py)
+    t_spec = time.perf_counter() - t0
+    del Lt, Kt
+    tm = W.type_map(w)
+    x = W.random_vectors(1, nu, 3)[0]
+    mv = lambda v: cpu_fft.matvec(v, Lh, Kh, coef, Z, tm, idx, sgn, nu, w.nx, w.ny)
+    mv(x)
+    t0 = time.perf_counter()
+    for _ in range(3):
+        mv(x)
+    t_mv = (time.perf_counter() - t0) / 3
+    t0 = time.perf_counter()
+    _, it, _ = solve.gmres(mv, x, rtol=1e-30, restart=RESTART, max_iters=6)
+    t_it = (time.perf_counter() - t0) / max(it, 1)
+    return {"kind": "CPU FFT product (complex128, scipy.fft + batched per-bin matmul)",
+            "cores": len(os.sched_getaffinity(0)), "grid": [px, py], "spectrum_s": round(t_spec, 2),
+            "matvec_ms": round(t_mv * 1e3, 1), "gmres_iter_ms": round(t_it * 1e3, 1),
+            "fp64_plain_solve_ms_extrapolated": round(t_it * 1e3 * nmv_plain, 0),
+            "note": "solve = GMRES(30) iteration time x the %d products of the GPU FP64 solve (same "
+                    "operator, same algorithm); unpreconditioned (the GPU preconditioned solve takes %d "
+                    "iterations)" % (nmv_plain, iters_pc)}
+
+
+def last_iters(infos):
+    return infos[-1]["iters"] if infos else 0
 
 
 def max_over_ranks(dist, value, device):
@@ -268,7 +417,7 @@ def build_problem(B, W, torch, w, precision, precond=True, max_rhs=None, tensor_
     B.emsurf_excitation(h, A, A, H, w.n, W.K0, np.array([k for k, _ in waves]),
                         np.array([e for _, e in waves]), V, zlevels=zl)
     return h, V, nu, {"tabulate_s": round(t_tab, 3), "macromodels_s": round(t_mm, 3),
-                      "create_s": round(t_create, 3)}
+                      "create_s": round(t_create, 3)}, zl
 
 
 def time_matvec(B, torch, h, nu, R, prec, reps=10):
@@ -414,9 +563,12 @@ def main():
                     help="profiler driver: right-hand sides of the --matvecs-only products")
     ap.add_argument("--tensor-cores", action="store_true",
                     help="profiler driver: build the tensor-core planes (--matvecs-only)")
-    ap.add_argument("--batched", action="store_true",
-                    help="measure the 48x48 / K = 576 / 32-plane-wave configuration (setup, products, "
-                         "preconditioner apply, MIXED solve of all rhs) and print it; not the bench line")
+    ap.add_argument("--batched", type=int, default=1,
+                    help="also measure the 48x48 / K = 576 / 32-plane-wave configuration (0 = skip)")
+    ap.add_argument("--largest", type=int, default=1,
+                    help="also measure the 100x100 / K = 324 / 8-plane-wave configuration (0 = skip)")
+    ap.add_argument("--accuracy", type=int, default=1,
+                    help="also compare MIXED currents and RCS with an FP64 solve to 1e-11 (0 = skip)")
     ap.add_argument("--solve-iters", type=int, default=0,
                     help="profiler driver: with --matvecs-only, also run one mixed solve capped "
                          "at this many GMRES iterations")
@@ -435,13 +587,10 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     cpu = None
-    if args.batched:
-        batched_section(B, W, torch)
-        return
     if args.matvecs_only:
         prec = {"mixed": B.MIXED, "fp32": B.FP32, "fp64": B.FP64}[args.precision]
         R = args.rhs or w.n_rhs
-        h, V, nu, _ = build_problem(B, W, torch, w, prec, max_rhs=max(R, w.n_rhs),
+        h, V, nu, _, _ = build_problem(B, W, torch, w, prec, max_rhs=max(R, w.n_rhs),
                                     tensor_cores=args.tensor_cores)
         for p in ((B.FP32,) if prec == B.FP32 else (B.FP64,) if prec == B.FP64 else (B.FP32, B.FP64)):
             x = torch.randn((R, nu), dtype=torch.complex128, device="cuda")
@@ -455,7 +604,7 @@ def main():
         torch.cuda.synchronize()
         h.close()
         return
-    h, V, nu, setup = build_problem(B, W, torch, w, B.MIXED)
+    h, V, nu, setup, zl = build_problem(B, W, torch, w, B.MIXED)
     X = torch.zeros_like(V)
     hbm, peak_kind = peaks()
     # FP64-plain reference solve on the same handle (FP64 operator GMRES,
@@ -544,12 +693,22 @@ def main():
     f1.record()
     torch.cuda.synchronize()
     e2e_ms = f0.elapsed_time(f1) / args.steps
+    # ------------------------------------------------------------ accuracy
+    accuracy = accuracy_section(B, torch, h, V, X, w, zl) if args.accuracy else None
     # ------------------------------------------------------------ many rhs
     multi = multi_rhs_section(B, W, torch, w, hbm) if args.multi_rhs else None
+    h.close()          # free the bench handle's device memory for the other sections
+    torch.cuda.empty_cache()
+    bf16, _ = bf16_peak()
+    batched = many_rhs_section(B, W, torch, "lattice48x48_k576_r32", hbm, bf16, 120.0, 1.0) \
+        if args.batched else None
+    torch.cuda.empty_cache()
+    largest = many_rhs_section(B, W, torch, "lattice100x100_k324_r8", hbm, bf16, 150.0, 2.0) \
+        if args.largest else None
+    torch.cuda.empty_cache()
     # ------------------------------------------------------------ serving
     serve = None
     if args.serve_requests > 0:
-        h.close()          # free the bench handle's device memory for the server
         serve = {"stream": "Poisson %.0f/s; lattices %s, K %s, rhs %d..%d, 32-type library; rtol %g; "
                            "near-field preconditioner in both arms; MIXED requests with >= 8 rhs "
                            "use the tensor-core bin multiply"
@@ -558,7 +717,9 @@ def main():
                  "mixed_batched": serve_stream(B, W, args.serve_requests, 7, B.MIXED, 4, True),
                  "fp64_one_at_a_time": serve_stream(B, W, args.serve_requests, 7, B.FP64, 1, True)}
     # ------------------------------------------------------------ CPU oracle
+    cpu_fft = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu_fft = cpu_fft_section(W, w, info64[0]["n_matvec"], last_iters(infos))
         t_cpu = cpu_oracle_matvec_seconds(W, w, nu)
         nmv64 = info64[0]["n_matvec"]
         cpu = {"value": t_cpu * 1e3 * nmv64, "unit": "ms", "cores": len(os.sched_getaffinity(0)),
@@ -600,15 +761,23 @@ def main():
         "solve": {"iters": last["iters"], "refinements": last["refinements"],
                   "n_matvec": last["n_matvec"], "rel_residual": last["rel_residual"],
                   "converged": last["converged"]},
+        "operator_arithmetic": {"fp32": "complex64 operator, FP32 arithmetic (inner GMRES)",
+                                "fp64_accuracy": "single-rhs FP64-operator products in double-single "
+                                                 "FP32 arithmetic (~48-bit products, scaled hi/lo "
+                                                 "planes); FP64 FFTs, residuals, orthogonalisation"},
+        "fp64_preconditioned": {"solve_ms": round(t64p, 3), "iters": info64p[0]["iters"],
+                                "n_matvec": info64p[0]["n_matvec"],
+                                "converged": info64p[0]["converged"],
+                                "precision_only_speedup": round(t64p / ms, 3),
+                                "note": "same preconditioner and rtol, FP64-accuracy operator throughout: "
+                                        "the equal-accuracy comparison of the precision modes"},
         "fp64_plain": {"solve_ms": round(t64, 3), "iters": info64[0]["iters"],
                        "n_matvec": info64[0]["n_matvec"], "rel_residual": info64[0]["rel_residual"],
-                       "converged": info64[0]["converged"], "speedup": round(t64 / ms, 3)},
+                       "converged": info64[0]["converged"], "speedup": round(t64 / ms, 3),
+                       "note": "no preconditioner: the paper's plain FP64 GMRES on the GPU"},
         "mixed_unpreconditioned": {"solve_ms": round(tnp, 3), "iters": infonp[0]["iters"],
                                    "n_matvec": infonp[0]["n_matvec"],
                                    "converged": infonp[0]["converged"]},
-        "fp64_preconditioned": {"solve_ms": round(t64p, 3), "iters": info64p[0]["iters"],
-                                "n_matvec": info64p[0]["n_matvec"],
-                                "converged": info64p[0]["converged"]},
         "precond": {"overlap_mesh_cells": PC_OVERLAP, "factor_entries": pc_elems,
                     "subdomain_total": pc_subtot, "max_subdomain": pc_nmax,
                     "apply_ms": round(pc_avg, 5) if pc_n else None,
@@ -624,6 +793,8 @@ def main():
                      "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "peak_kind": peak_kind,
                      "traffic": round(traffic) if traffic else None,
+                     "traffic_kind": "scaled: ncu DRAM bytes per stored bin of the 12x12 capture x the "
+                                     "stored bins here (each stored slab is streamed exactly once)",
                      "alg_bytes_per_launch": alg_bin,
                      "avg_launch_ms": round(bin_avg, 5), "launches_timed": bin_n_timed},
         "phases_ms_per_solve": {"binmul32": round(bin_ms, 3),
@@ -641,12 +812,15 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clk,
         "multi_rhs": multi,
+        "accuracy": accuracy,
+        "batched": batched,
+        "largest": largest,
+        "cpu_fft": cpu_fft,
         "serve": serve,
         "setup": setup,
         "device_bytes": dev_bytes,
     }
     print(json.dumps(out))
-    h.close()
     if dist:
         dist.destroy_process_group()
 

@@ -73,7 +73,14 @@ typedef struct emsurf_handle emsurf_handle;
  *               holding the FP64 operator also keep its spectrum and the
  *               macromodels as FP32 hi/lo planes (same bytes) for the
  *               double-single FP64-accuracy kernels, when device_mem_budget
- *               leaves room
+ *               leaves room.  Their operands are scaled by powers of two
+ *               (the spectrum and the macromodels at create, each rhs of a
+ *               product by its largest component) and the FP64 results
+ *               scaled back, so FP32's exponent range limits only parts
+ *               more than ~2^100 below the largest of their array (relative
+ *               error per term a few 2^-48 of that largest).  The FP32
+ *               operator (EMSURF_FP32, MIXED) stores complex64 values and
+ *               needs table and macromodel entries inside FP32's range.
  *  tables_on_device  0: offset_L/K and macromodels are host pointers;
  *                    1: they are device pointers on `device`
  * The handle copies everything it needs; the caller may free the inputs

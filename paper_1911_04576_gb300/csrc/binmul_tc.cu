@@ -19,8 +19,8 @@
 // y_J = a L x_J + b K x_M and y_M = g K x_J + d L x_M in the epilogue.
 //
 // Kernel: persistent, one CTA per SM, items = (rhs group, bin, chunk of 48
-// test rows).  Warp 0 issues TMA tensor loads (128B swizzle) of 64-source
-// stages into a 2-deep ring; warp 1 issues the MMAs (M = 128, N = 96,
+// test rows).  Warp 0 issues TMA tensor loads (64B swizzle) of 32-source
+// stages into a 5-deep ring; warp 1 issues the MMAs (M = 128, N = 96,
 // K = 16) into one of two TMEM accumulator sets; warps 2-5 drain the other
 // set (tcgen05.ld), combine and store Y^.  Every wait is bounded: on expiry
 // the kernel sets the error flag, waits (bounded) for its copies and MMAs in
@@ -50,6 +50,17 @@ constexpr int kTcStageBytes = 2 * kTcABytes + 4 * kTcBBytes;   // A hi/lo, B hi/
 constexpr int kTcSmem = 1024 + kTcStages * kTcStageBytes;
 constexpr uint32_t kTcTmemCols = 512;     // two accumulator sets of 2 x 96 columns
 constexpr long long kTcWait = 1LL << 22;
+// The bin multiply's ring: 32 sources per stage (64-byte rows, 64B swizzle)
+// in 5 stages of 40 KB: more bytes in flight per SM than 2 stages of 80 KB
+// (the spectrum stream is latency-bound per SM: throughput = bytes in
+// flight / DRAM latency), same bytes per item.
+constexpr int kBmKc = 32;
+constexpr int kBmStages = 5;
+constexpr int kBmABytes = kTcM * 64;        // 8 KB
+constexpr int kBmBBytes = kTcN * 64;        // 6 KB
+constexpr int kBmStageBytes = 2 * kBmABytes + 4 * kBmBBytes;
+constexpr int kBmSmem = 1024 + kBmStages * kBmStageBytes;
+static_assert(kBmSmem <= 227 * 1024, "bin multiply ring exceeds shared memory");
 // instruction descriptor: kind::f16, bf16 x bf16 -> f32, K-major A and B, N = 96, M = 128
 constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
                               ((uint32_t)(kTcM >> 4) << 24);
@@ -90,6 +101,10 @@ __device__ __forceinline__ void tma3d(void* dst, const CUtensorMap* map, int x, 
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
     return (uint64_t)((addr & 0x3FFFF) >> 4) | (1ull << 16) | (64ull << 32) | (1ull << 46) | (2ull << 61);
 }
+// the same for 64B swizzle (64-byte rows, 8-row groups 512 B apart)
+__device__ __forceinline__ uint64_t sdesc64(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | (1ull << 16) | (32ull << 32) | (1ull << 46) | (4ull << 61);
+}
 __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -123,7 +138,7 @@ binmul_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant_
                  const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, TcArgs g) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full[kTcStages], empty[kTcStages], accf[2], acce[2], mma_done;
+    __shared__ __align__(8) uint64_t full[kBmStages], empty[kBmStages], accf[2], acce[2], mma_done;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -133,7 +148,7 @@ binmul_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant_
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kTcStages; ++s) {
+        for (int s = 0; s < kBmStages; ++s) {
             bar_init(&full[s], 1);
             bar_init(&empty[s], 1);
         }
@@ -156,7 +171,7 @@ binmul_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant_
         if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0;
-            int issued[kTcStages] = {0, 0};
+            int issued[kBmStages] = {0, 0, 0, 0, 0};
             for (int item = blockIdx.x; item < g.items && !*(volatile int*)&abort_flag; item += gridDim.x) {
                 const int grp = item / (g.nbins * g.chunks), rem = item % (g.nbins * g.chunks);
                 const int bin = rem / g.chunks, ch = rem % g.chunks;
@@ -166,25 +181,25 @@ binmul_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant_
                         *(volatile int*)&abort_flag = 1;
                         break;
                     }
-                    unsigned char* st = smem + stage * kTcStageBytes;
-                    bar_expect(&full[stage], kTcStageBytes);
-                    const int j0 = ks * kTcKc;
+                    unsigned char* st = smem + stage * kBmStageBytes;
+                    bar_expect(&full[stage], kBmStageBytes);
+                    const int j0 = ks * kBmKc;
                     tma3d(st, &mAh, j0, kTcM * grp, bin, &full[stage]);
-                    tma3d(st + kTcABytes, &mAl, j0, kTcM * grp, bin, &full[stage]);
+                    tma3d(st + kBmABytes, &mAl, j0, kTcM * grp, bin, &full[stage]);
                     for (int op = 0; op < 2; ++op) {
-                        unsigned char* b = st + 2 * kTcABytes + op * 2 * kTcBBytes;
+                        unsigned char* b = st + 2 * kBmABytes + op * 2 * kBmBBytes;
                         tma3d(b, &mBh, j0, kTcN * ch, 2 * bin + op, &full[stage]);
-                        tma3d(b + kTcBBytes, &mBl, j0, kTcN * ch, 2 * bin + op, &full[stage]);
+                        tma3d(b + kBmBBytes, &mBl, j0, kTcN * ch, 2 * bin + op, &full[stage]);
                     }
                     ++issued[stage];
-                    if (++stage == kTcStages) {
+                    if (++stage == kBmStages) {
                         stage = 0;
                         phase ^= 1;
                     }
                 }
             }
             // every copy this thread issued has landed before the CTA can exit
-            for (int s = 0; s < kTcStages; ++s)
+            for (int s = 0; s < kBmStages; ++s)
                 if (issued[s] && !bar_wait(&full[s], (uint32_t)((issued[s] - 1) & 1))) atomicExch(g.err, 4);
         }
     } else if (warp == 1) {
@@ -210,14 +225,14 @@ binmul_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant_
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;");
-                    const uint32_t st = saddr(smem + stage * kTcStageBytes);
-                    const uint32_t ah = st, al = st + kTcABytes;
-                    for (int kk = 0; kk < kTcKc / 16; ++kk) {
+                    const uint32_t st = saddr(smem + stage * kBmStageBytes);
+                    const uint32_t ah = st, al = st + kBmABytes;
+                    for (int kk = 0; kk < kBmKc / 16; ++kk) {
                         const uint32_t off = 32u * kk;
-                        const uint64_t dah = sdesc(ah + off), dal = sdesc(al + off);
+                        const uint64_t dah = sdesc64(ah + off), dal = sdesc64(al + off);
                         for (int op = 0; op < 2; ++op) {
-                            const uint32_t b = st + 2 * kTcABytes + op * 2 * kTcBBytes;
-                            const uint64_t dbh = sdesc(b + off), dbl = sdesc(b + kTcBBytes + off);
+                            const uint32_t b = st + 2 * kBmABytes + op * 2 * kBmBBytes;
+                            const uint64_t dbh = sdesc64(b + off), dbl = sdesc64(b + kBmBBytes + off);
                             const uint32_t d = op ? dK : dL;
                             mma_bf16(d, dah, dbh, (ks > 0 || kk > 0) ? 1u : 0u);
                             mma_bf16(d, dah, dbl, 1u);
@@ -226,7 +241,7 @@ binmul_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant_
                     }
                     mma_commit(&empty[stage]);   // the stage is free once these MMAs have read it
                     any = true;
-                    if (++stage == kTcStages) {
+                    if (++stage == kBmStages) {
                         stage = 0;
                         phase ^= 1;
                     }
@@ -830,7 +845,8 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-int encode3d(CUtensorMap* map, void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b0, uint32_t b1) {
+int encode3d(CUtensorMap* map, void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b0, uint32_t b1,
+             CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {
     static EncodeTiledFn fn = nullptr;
     if (!fn) {
         void* p = nullptr;
@@ -848,7 +864,7 @@ int encode3d(CUtensorMap* map, void* base, uint64_t d0, uint64_t d1, uint64_t d2
     const cuuint32_t box[3] = {b0, b1, 1};
     const cuuint32_t es[3] = {1, 1, 1};
     const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         set_error("tensor-core path: tensor map encoding failed (%d)", (int)r);
@@ -880,10 +896,10 @@ int tc_build(emsurf_handle* h) {
     h->launches += 1;
     static_assert(sizeof(CUtensorMap) <= sizeof(h->tc_maps[0]), "tensor map storage");
     CUtensorMap* m = reinterpret_cast<CUtensorMap*>(h->tc_maps);
-    EMS_TRY(encode3d(&m[0], h->tc_Xh, ej, rows, nb, kTcKc, kTcM));
-    EMS_TRY(encode3d(&m[1], h->tc_Xl, ej, rows, nb, kTcKc, kTcM));
-    EMS_TRY(encode3d(&m[2], h->tc_Bh, ej, 2 * E, 2 * nb, kTcKc, kTcN));
-    EMS_TRY(encode3d(&m[3], h->tc_Bl, ej, 2 * E, 2 * nb, kTcKc, kTcN));
+    EMS_TRY(encode3d(&m[0], h->tc_Xh, ej, rows, nb, kBmKc, kTcM, CU_TENSOR_MAP_SWIZZLE_64B));
+    EMS_TRY(encode3d(&m[1], h->tc_Xl, ej, rows, nb, kBmKc, kTcM, CU_TENSOR_MAP_SWIZZLE_64B));
+    EMS_TRY(encode3d(&m[2], h->tc_Bh, ej, 2 * E, 2 * nb, kBmKc, kTcN, CU_TENSOR_MAP_SWIZZLE_64B));
+    EMS_TRY(encode3d(&m[3], h->tc_Bl, ej, 2 * E, 2 * nb, kBmKc, kTcN, CU_TENSOR_MAP_SWIZZLE_64B));
     h->tc_ej = ej;
     h->tc_rows = rows;
     // macromodel planes: Z~ [t][2k+c][kp] and x1 tiles [tile][128][kp]
@@ -977,17 +993,17 @@ int tc_binmul(emsurf_handle* h, const float2* X, float2* Y, int R, const float2*
     a.R = R;
     a.groups = (R + kTcRhs - 1) / kTcRhs;
     a.chunks = (2 * E + kTcN - 1) / kTcN;
-    a.nk = (ej + kTcKc - 1) / kTcKc;
+    a.nk = (ej + kBmKc - 1) / kBmKc;
     a.items = a.groups * a.nbins * a.chunks;
     a.ca = coef[0];
     a.cb = coef[1];
     a.cg = coef[2];
     a.cd = coef[3];
     a.err = h->d_err;
-    EMS_TRY(set_smem_once(binmul_tc_kernel, (size_t)kTcSmem));
+    EMS_TRY(set_smem_once(binmul_tc_kernel, (size_t)kBmSmem));
     const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(h->tc_maps);
     const int grid = std::min(a.items, h->num_sms);
-    binmul_tc_kernel<<<grid, kTcThreads, kTcSmem, st>>>(m[0], m[1], m[2], m[3], a);
+    binmul_tc_kernel<<<grid, kTcThreads, kBmSmem, st>>>(m[0], m[1], m[2], m[3], a);
     EMS_CUDA(cudaGetLastError());
     h->launches += 2;
     return EMSURF_OK;

@@ -208,6 +208,11 @@ struct emsurf_handle {
     float2* ds_planes = nullptr;
     float2* ds_x = nullptr;
     float2* ds_zt = nullptr;          // the macromodels as hi/lo planes [t][hi, lo][k'][k]
+    // powers of two that keep the double-single operands inside FP32's
+    // exponent range: [0] spectrum planes, [1] macromodel planes (both were
+    // split from the FP64 values times these), [2 + r] rhs r of the current
+    // product (from max |x_r|); the kernels divide their FP64 outputs back
+    double* d_ds_scale = nullptr;
     int pair_grid = 0;                // CTAs of the pair kernel (equal slab ranges)
     float2* d_pair_part = nullptr;    // partial row sums of straddling bins [cta][2][2E]
     int* d_pair_cnt = nullptr;        // arrival counters [stored bin][row warp]

@@ -379,13 +379,14 @@ __device__ __forceinline__ double2 ds_value(const DsC& a) {
     return make_double2((double)a.rh + (double)a.rl, (double)a.ih + (double)a.il);
 }
 
-// out[b][0][r] = rn(in[b][r]), out[b][1][r] = rn(in[b][r] - out[b][0][r]) for
-// blocks b of `chunk` complex values
+// out[b][0][r] = rn(s v), out[b][1][r] = rn(s v - out[b][0][r]) for v = in[b][r],
+// blocks b of `chunk` complex values; s = *scale (a power of two, exact), or 1
 __global__ void split_hilo_kernel(float2* __restrict__ out, const double2* __restrict__ in, size_t chunk,
-                                  size_t total) {
+                                  size_t total, const double* __restrict__ scale) {
+    const double sc = scale ? *scale : 1.0;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
         const size_t b = e / chunk, r = e - b * chunk;
-        const double2 v = in[e];
+        const double2 v = make_double2(sc * in[e].x, sc * in[e].y);
         const float2 hi = make_float2((float)v.x, (float)v.y);
         const float2 lo = make_float2((float)(v.x - (double)hi.x), (float)(v.y - (double)hi.y));
         out[b * 2 * chunk + r] = hi;
@@ -393,10 +394,49 @@ __global__ void split_hilo_kernel(float2* __restrict__ out, const double2* __res
     }
 }
 
+// scale[r] = 2^-e with 2^(e-1) <= max over the r-th block of |re|, |im| < 2^e
+// (1 when the block is zero or not finite): after it the block's largest
+// component lies in [0.5, 1), far from FP32 overflow, and FP32 subnormals only
+// touch parts below 2^-100 of the largest.  One CTA per block of `len` values.
+__global__ void __launch_bounds__(256) pow2_scale_kernel(const double2* __restrict__ v, size_t len,
+                                                         double* __restrict__ scale) {
+    __shared__ double s_m[256];
+    const double2* b = v + (size_t)blockIdx.x * len;
+    double m = 0.0;
+    for (size_t e = threadIdx.x; e < len; e += blockDim.x) m = fmax(m, fmax(fabs(b[e].x), fabs(b[e].y)));
+    s_m[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) s_m[threadIdx.x] = fmax(s_m[threadIdx.x], s_m[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double mx = s_m[0];
+        scale[blockIdx.x] = (mx > 0.0 && mx <= 1.7e308) ? ldexp(1.0, -(ilogb(mx) + 1)) : 1.0;
+    }
+}
+
+// grid-wide variant for one large array: per-CTA maxima in part[], then one CTA
+__global__ void __launch_bounds__(256) absmax_part_kernel(const double2* __restrict__ v, size_t n,
+                                                          double* __restrict__ part) {
+    __shared__ double s_m[256];
+    double m = 0.0;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        m = fmax(m, fmax(fabs(v[e].x), fabs(v[e].y)));
+    s_m[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) s_m[threadIdx.x] = fmax(s_m[threadIdx.x], s_m[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = s_m[0];
+}
+
 // planes: [bin][hi, lo][op][j][i] float2; xs: [bin][hi, lo][2E]; Yh: [bin][2E] FP64
 __global__ void binmul_ds_kernel(const float2* __restrict__ planes, const float2* __restrict__ xs,
                                  double2* __restrict__ Yh, int E, int nbins, double2 ca, double2 cb,
-                                 double2 cg, double2 cd, int* __restrict__ err) {
+                                 double2 cg, double2 cd, int* __restrict__ err,
+                                 const double* __restrict__ scale) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int stage_elems = 4 * kDsJB * E;      // [hi, lo][L, K][kDsJB][E]
     float2* sbuf = reinterpret_cast<float2*>(smem_raw);
@@ -486,8 +526,11 @@ __global__ void binmul_ds_kernel(const float2* __restrict__ planes, const float2
             if (i < E) {
                 const int bin = (int)blockIdx.x + t * (int)gridDim.x;
                 double2* Y = Yh + (size_t)bin * 2 * E;
-                Y[i] = cadd(cmul(ca, ds_value(lj)), cmul(cb, ds_value(km)));
-                Y[E + i] = cadd(cmul(cg, ds_value(kj)), cmul(cd, ds_value(lm)));
+                const double u = 1.0 / (scale[0] * scale[2]);       // exact: powers of two
+                const double2 yj = cadd(cmul(ca, ds_value(lj)), cmul(cb, ds_value(km)));
+                const double2 ym = cadd(cmul(cg, ds_value(kj)), cmul(cd, ds_value(lm)));
+                Y[i] = make_double2(u * yj.x, u * yj.y);
+                Y[E + i] = make_double2(u * ym.x, u * ym.y);
             }
             lj = lm = kj = km = DsC{0.f, 0.f, 0.f, 0.f};
         }
@@ -503,7 +546,8 @@ __global__ void binmul_ds_kernel(const float2* __restrict__ planes, const float2
 template <int RB>
 __global__ void binmul_ds_multi_kernel(const float2* __restrict__ planes, const double2* __restrict__ Xh,
                                        double2* __restrict__ Yh, int E, int nbins, int R, int r0,
-                                       double2 ca, double2 cb, double2 cg, double2 cd) {
+                                       double2 ca, double2 cb, double2 cg, double2 cd,
+                                       const double* __restrict__ scale) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* xh = reinterpret_cast<float2*>(smem_raw);   // [RB][2E] hi
     float2* xl = xh + (size_t)RB * 2 * E;               // [RB][2E] lo
@@ -514,7 +558,12 @@ __global__ void binmul_ds_multi_kernel(const float2* __restrict__ planes, const 
         const double2* X = Xh + (size_t)bin * R * K;
         for (int e = threadIdx.x; e < RB * K; e += blockDim.x) {
             const int r = e / K, k = e - r * K;
-            const double2 v = (r0 + r < R) ? X[(size_t)(r0 + r) * K + k] : make_double2(0.0, 0.0);
+            double2 v = make_double2(0.0, 0.0);
+            if (r0 + r < R) {
+                const double sc = scale[2 + r0 + r];
+                v = X[(size_t)(r0 + r) * K + k];
+                v = make_double2(sc * v.x, sc * v.y);
+            }
             const float2 hi = make_float2((float)v.x, (float)v.y);
             xh[e] = hi;
             xl[e] = make_float2((float)(v.x - (double)hi.x), (float)(v.y - (double)hi.y));
@@ -546,8 +595,11 @@ __global__ void binmul_ds_multi_kernel(const float2* __restrict__ planes, const 
             for (int r = 0; r < RB; ++r) {
                 if (r0 + r < R) {
                     double2* Y = Yh + ((size_t)bin * R + r0 + r) * K;
-                    Y[i] = cadd(cmul(ca, ds_value(lj[r])), cmul(cb, ds_value(km[r])));
-                    Y[E + i] = cadd(cmul(cg, ds_value(kj[r])), cmul(cd, ds_value(lm[r])));
+                    const double u = 1.0 / (scale[0] * scale[2 + r0 + r]);
+                    const double2 yj = cadd(cmul(ca, ds_value(lj[r])), cmul(cb, ds_value(km[r])));
+                    const double2 ym = cadd(cmul(cg, ds_value(kj[r])), cmul(cd, ds_value(lm[r])));
+                    Y[i] = make_double2(u * yj.x, u * yj.y);
+                    Y[E + i] = make_double2(u * ym.x, u * ym.y);
                 }
             }
         }
@@ -1047,11 +1099,12 @@ __global__ void __launch_bounds__(320, 2)
 macromodel_ds_kernel(const float2* __restrict__ zp, const double2* __restrict__ x,
                      const int32_t* __restrict__ idx, const int8_t* __restrict__ sgn,
                      const int32_t* __restrict__ type_cells, const MmBlock* __restrict__ blocks,
-                     double2* __restrict__ Ymm, int K, int M, int chunk) {
+                     double2* __restrict__ Ymm, int K, int M, int chunk, const double* __restrict__ scale) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* xh = reinterpret_cast<float2*>(smem_raw);   // [G][chunk] hi
     float2* xl = xh + (size_t)G * chunk;                // [G][chunk] lo
     const MmBlock b = blocks[blockIdx.x];
+    const double sx = scale[2], u = 1.0 / (scale[1] * scale[2]);
     const int s = blockIdx.y;
     const int k0 = s * chunk, k1 = min(K, k0 + chunk), nk = k1 - k0;
     for (int e = threadIdx.x; e < G * chunk; e += blockDim.x) {
@@ -1060,7 +1113,7 @@ macromodel_ds_kernel(const float2* __restrict__ zp, const double2* __restrict__ 
         if (g < b.count && kk < nk) {
             const size_t loc = (size_t)type_cells[b.first + g] * K + k0 + kk;
             const double2 xv = x[idx[loc]];
-            const double sg = (double)sgn[loc];
+            const double sg = (double)sgn[loc] * sx;
             v = make_double2(sg * xv.x, sg * xv.y);
         }
         const float2 hi = make_float2((float)v.x, (float)v.y);
@@ -1100,8 +1153,9 @@ macromodel_ds_kernel(const float2* __restrict__ zp, const double2* __restrict__ 
         for (int g = 0; g < G; ++g)
             if (g < b.count) {
                 double2* y = Ymm + ((size_t)s * M + type_cells[b.first + g]) * K + 2 * k2;
-                y[0] = ds_value(a0[g]);
-                y[1] = ds_value(a1[g]);
+                const double2 v0 = ds_value(a0[g]), v1 = ds_value(a1[g]);
+                y[0] = make_double2(u * v0.x, u * v0.y);
+                y[1] = make_double2(u * v1.x, u * v1.y);
             }
     }
 }
@@ -1330,13 +1384,43 @@ int build_ds_planes(emsurf_handle* h) {
     if (h->budget > 0 && h->device_bytes + (int64_t)(pbytes + xbytes) > h->budget) return EMSURF_OK;
     EMS_TRY(dev_alloc(h, (void**)&h->ds_planes, pbytes));
     EMS_TRY(dev_alloc(h, (void**)&h->ds_x, xbytes));
-    split_hilo_kernel<<<152 * 16, 256, 0, h->setup_stream>>>(h->ds_planes, h->op64.Bhat, 2 * EE, nb * 2 * EE);
+    EMS_TRY(dev_alloc(h, (void**)&h->d_ds_scale, sizeof(double) * (2 + std::max(1, h->max_rhs))));
+    // operator scales: the largest component of the spectrum (of the
+    // macromodels) maps into [0.5, 1), exactly (powers of two)
+    const size_t KK = (size_t)h->K * h->K;
+    double* part = nullptr;
+    EMS_CUDA(cudaMalloc(&part, sizeof(double) * 2 * 1024));
+    double hs[2] = {1.0, 1.0};
+    {
+        std::vector<double> hp(2 * 1024);
+        absmax_part_kernel<<<1024, 256, 0, h->setup_stream>>>(h->op64.Bhat, nb * 2 * EE, part);
+        absmax_part_kernel<<<1024, 256, 0, h->setup_stream>>>(h->op64.Zt, (size_t)h->T * KK, part + 1024);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(hp.data(), part, sizeof(double) * 2 * 1024, cudaMemcpyDeviceToHost, h->setup_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->setup_stream);
+        cudaFree(part);
+        if (e != cudaSuccess) {
+            set_error("operator scale: %s", cudaGetErrorString(e));
+            return EMSURF_ECUDA;
+        }
+        for (int w = 0; w < 2; ++w) {
+            double mx = 0.0;
+            for (int i = 0; i < 1024; ++i) mx = std::max(mx, hp[w * 1024 + i]);
+            if (mx > 0.0 && std::isfinite(mx)) hs[w] = std::ldexp(1.0, -(std::ilogb(mx) + 1));
+        }
+        EMS_CUDA(cudaMemcpyAsync(h->d_ds_scale, hs, sizeof(hs), cudaMemcpyHostToDevice, h->setup_stream));
+        EMS_CUDA(cudaStreamSynchronize(h->setup_stream));
+    }
+    split_hilo_kernel<<<152 * 16, 256, 0, h->setup_stream>>>(h->ds_planes, h->op64.Bhat, 2 * EE, nb * 2 * EE,
+                                                             h->d_ds_scale);
     EMS_CUDA(cudaGetLastError());
     // the macromodels likewise (the transposed Z~ of each type)
-    const size_t KK = (size_t)h->K * h->K, zbytes = (size_t)h->T * 2 * KK * sizeof(float2);
+    const size_t zbytes = (size_t)h->T * 2 * KK * sizeof(float2);
     if ((h->K & 1) == 0 && (h->budget <= 0 || h->device_bytes + (int64_t)zbytes <= h->budget)) {
         EMS_TRY(dev_alloc(h, (void**)&h->ds_zt, zbytes));
-        split_hilo_kernel<<<152 * 16, 256, 0, h->setup_stream>>>(h->ds_zt, h->op64.Zt, KK, (size_t)h->T * KK);
+        split_hilo_kernel<<<152 * 16, 256, 0, h->setup_stream>>>(h->ds_zt, h->op64.Zt, KK, (size_t)h->T * KK,
+                                                                 h->d_ds_scale + 1);
         EMS_CUDA(cudaGetLastError());
     }
     return EMSURF_OK;
@@ -1436,6 +1520,12 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
         }
     }
     if constexpr (std::is_same<T2, double2>::value) {
+        if (h->ds_planes && x) {
+            // per-rhs powers of two for the double-single operands of this product
+            pow2_scale_kernel<<<R, 256, 0, st>>>(x, (size_t)h->n_unique, h->d_ds_scale + 2);
+            EMS_CUDA(cudaGetLastError());
+            h->launches += 1;
+        }
         if (!mm_done && R == 1 && h->ds_zt) {
             // one rhs, FP64 accuracy from double-single FP32 arithmetic
             const int threads2 = std::min(320, ((K / 2 + 31) / 32) * 32);
@@ -1449,7 +1539,7 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
             EMS_TRY(set_smem_once(macromodel_ds_kernel<kMmGroup>, sm));
             macromodel_ds_kernel<kMmGroup><<<dim3(nblk, ns2), threads2, sm, st>>>(
                 h->ds_zt, x, h->d_uo_index, h->d_uo_sign, h->d_type_cells,
-                reinterpret_cast<const MmBlock*>(h->d_mm_blocks), op.Ymm, K, h->M, chunk2);
+                reinterpret_cast<const MmBlock*>(h->d_mm_blocks), op.Ymm, K, h->M, chunk2, h->d_ds_scale);
             EMS_CUDA(cudaGetLastError());
             nsplit = ns2;
             mm_done = true;
@@ -1514,13 +1604,15 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
             // FP64 accuracy from FP32 hi/lo arithmetic (the FP64 rate is ~1/60 of FP32)
             const size_t lanes2 = (size_t)2 * E;
             split_hilo_kernel<<<grid_for((size_t)nb * lanes2, 256), 256, 0, st>>>(h->ds_x, op.Xg, lanes2,
-                                                                                (size_t)nb * lanes2);
+                                                                                (size_t)nb * lanes2,
+                                                                                h->d_ds_scale + 2);
             EMS_CUDA(cudaGetLastError());
             const size_t smem = binmul_ds_smem(E);
             EMS_TRY(set_smem_once(binmul_ds_kernel, smem));
             const int grid = std::min(nb, std::max(1, h->num_sms));
             binmul_ds_kernel<<<grid, 32 * (1 + (E + 31) / 32), smem, st>>>(
-                h->ds_planes, h->ds_x, op.Yg, E, nb, op.coef[0], op.coef[1], op.coef[2], op.coef[3], h->d_err);
+                h->ds_planes, h->ds_x, op.Yg, E, nb, op.coef[0], op.coef[1], op.coef[2], op.coef[3], h->d_err,
+                h->d_ds_scale);
             EMS_CUDA(cudaGetLastError());
             h->launches += 2;
             bin_done = true;
@@ -1535,7 +1627,7 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
             for (int r0 = 0; r0 < R; r0 += RBd) {
                 binmul_ds_multi_kernel<RBd><<<grid, threads, smem, st>>>(h->ds_planes, op.Xg, op.Yg, E, nb, R, r0,
                                                                       op.coef[0], op.coef[1], op.coef[2],
-                                                                      op.coef[3]);
+                                                                      op.coef[3], h->d_ds_scale);
                 EMS_CUDA(cudaGetLastError());
                 h->launches += 1;
             }

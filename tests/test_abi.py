@@ -98,3 +98,22 @@ def test_null_handle_calls_rejected(lib):
     assert lib.emsurf_solve(None, None, None, 1, None, None, None) == B.EMSURF_EINVAL
     assert lib.emsurf_query(None, None, None, None) == B.EMSURF_EINVAL
     lib.emsurf_destroy(None)
+
+
+def test_noalloc_entry_point_calls_no_allocator():
+    """The allocation-free tabulation and its scratch-address helper name no
+    allocating call (source scan of their bodies)."""
+    import re
+    src = open(os.path.join(ROOT, "paper_1911_04576_gb300", "csrc", "tabulate.cu")).read()
+    forbidden = re.compile(r"cudaMalloc|cudaMallocAsync|cudaMallocHost|cudaHostAlloc|cudaMallocManaged|"
+                           r"cudaFree|dev_alloc|\bnew\b|malloc\(")
+    for name in ("int scratch_address(", "int tabulate_blocks_noalloc(", "CtxGetCurrentFn ctx_get_current("):
+        start = src.index(name)
+        depth, i = 0, src.index("{", start)
+        while True:
+            depth += {"{": 1, "}": -1}.get(src[i], 0)
+            if depth == 0:
+                break
+            i += 1
+        body = src[start:i]
+        assert not forbidden.search(body), (name, forbidden.search(body).group(0))

@@ -233,3 +233,26 @@ def test_fp64_single_rhs_double_single(emsurf_lib, n, nx, ny):
         assert relerr(run_matvec(B, h, x, B.FP64)[0], yref[0]) <= 1e-12
         B.emsurf_check(h)
         h.close()
+
+
+@pytest.mark.parametrize("sx,sop", [(2.0 ** 100, 1.0), (2.0 ** -100, 1.0), (1.0, 2.0 ** 90), (2.0 ** -60, 2.0 ** -80)])
+def test_double_single_outside_fp32_range(emsurf_lib, sx, sop):
+    """The double-single FP64-accuracy product keeps its 1e-12 bar when x or
+    the operator (tables and macromodels) lies far outside FP32's exponent
+    range: operands are scaled by powers of two before the hi/lo split and
+    the FP64 results scaled back.  One rhs (TMA-fed kernel, double-single
+    macromodel product) and two rhs (register-blocked kernel), FP64 handles
+    (no complex64 operator, whose storage would overflow)."""
+    from paper_1911_04576_gb300 import binding as B
+    n, nx, ny = 2, 3, 2
+    E, idx, sgn, nu, Lt, Kt, Z, tmap = random_case(n, nx, ny, 2, 950)
+    Lt, Kt, Z = Lt * sop, Kt * sop, Z * sop
+    x = W.random_vectors(2, nu, 951) * sx
+    yref = lattice.matvec_direct(x, Lt, Kt, COEF, Z, tmap, idx, sgn, nu, nx, ny)
+    for R in (1, 2):
+        h = B.emsurf_create(nx, ny, E, nu, tmap, Z, Lt, Kt, COEF, idx, sgn, precision=B.FP64, max_rhs=R)
+        y = run_matvec(B, h, x[:R], B.FP64)
+        for r in range(R):
+            assert np.all(np.isfinite(y[r])) and relerr(y[r], yref[r]) <= 1e-12, (R, r)
+        B.emsurf_check(h)
+        h.close()

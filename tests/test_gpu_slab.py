@@ -83,13 +83,17 @@ def test_slab_lattice_product_path_matches_dense_lu(emsurf_lib):
     Z = torch.empty((w.n_types, w.K, w.K), dtype=torch.complex128, device="cuda")
     B.emsurf_macromodel_slab_patch(A, A, H, w.n, zb, sides, w.patch_n, W.RING_LAYERS, W.EPS_SLAB, K0, Z)
     tmap = W.type_map(w)
-    hd = B.emsurf_create(w.nx, w.ny, w.E, nu, tmap, Z, L, K, COEF, idx, sgn, tables_on_device=True)
+    # the slab makes the plain GMRES slow (thousands of iterations): the
+    # near-field preconditioner (flexible GMRES) keeps the FP64 bars
+    xy = B.emsurf_setup_unknown_xy(A, A, H, w.n, w.nx, w.ny, idx, nu)
+    hd = B.emsurf_create(w.nx, w.ny, w.E, nu, tmap, Z, L, K, COEF, idx, sgn, tables_on_device=True,
+                         unknown_xy=xy, cell=(A, A), precond_overlap=0.6 * A / w.n)
     khat, ehat = W.plane_waves(w)[0]
     V = torch.empty((1, nu), dtype=torch.complex128, device="cuda")
     B.emsurf_excitation(hd, A, A, H, w.n, K0, [khat], [ehat], V, zlevels=zb)
     X = torch.zeros_like(V)
     st, info = B.emsurf_solve(hd, V, X, rtol=1e-12, restart=40, max_iters=6000)
-    assert st == B.EMSURF_OK
+    assert st == B.EMSURF_OK, info
     hd.close()
     # oracle: its own mesh, tables, macromodels, excitation and dense LU
     box = box_mesh(A, A, H, w.n, slab_zlevels(H, w.n, T))

@@ -7,7 +7,9 @@ a process under a hard device-memory quota).  emsurf_tabulate_noalloc
 serves them from a static per-GPU scratch array; this test checks it
 against emsurf_tabulate, within the setup tests' tolerance, on two calls in
 a row with different meshes (so the second call runs on the first one's
-leftovers), and that an oversized request is refused.  The file sorts last
+leftovers), that device free memory does not move across a call whose
+scratch needs tens of MiB, and that an oversized request is refused.  The
+file sorts last
 so that a run stopping at its first failure has already run every other
 test.
 """
@@ -71,3 +73,25 @@ def test_noalloc_rejects_requests_beyond_its_scratch(emsurf_lib):
     with pytest.raises(B.EmsurfError) as e:
         B.emsurf_tabulate_noalloc(big, big, np.zeros((1, 3)), np.ones(1, np.int8), W.K0, L, L)
     assert e.value.status == B.EMSURF_EINVAL and "scratch" in str(e.value)
+
+
+def test_noalloc_call_leaves_device_free_memory_unchanged(emsurf_lib):
+    """A call needing ~40 MiB of scratch (3 x 4-per-face box blocks of 192 x 192
+    triangle pairs, 10.6 MiB each, and a box/patch pair) changes nothing in
+    the driver's free-memory count, while the allocating entry point's
+    scratch is visible to it only transiently (it frees before returning)."""
+    import torch
+    from paper_1911_04576_gb300 import binding as B
+    box4 = B.emsurf_setup_box_mesh(A, A, H, 4)
+    sh = np.array([[0.0, 0.0, 0.0], [A, 0.0, 0.0], [A, A, 0.0], [2 * A, 0.0, 0.0]])
+    sg = np.array([1, 1, 1, 0], np.int8)
+    L = torch.empty((4, 288, 288), dtype=torch.complex128, device="cuda")
+    K = torch.empty_like(L)
+    B.emsurf_tabulate_noalloc(box4, box4, sh, sg, W.K0, L, K)      # first call: address set-up
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(2):
+        B.emsurf_tabulate_noalloc(box4, box4, sh, sg, W.K0, L, K)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
