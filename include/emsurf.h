@@ -154,6 +154,21 @@ typedef struct {
  * handle.  Errors: EINVAL (shape/index/sign out of range), ENOMEM, ECUDA.  */
 EMSURF_API int emsurf_create(const emsurf_problem* problem, emsurf_handle** out);
 
+/* emsurf_create for a lattice whose Fourier-domain blocks another handle
+ * already holds (no counterpart in the paper; used by the serving cache):
+ * the new handle reads `share`'s spectra (FP64 or its double-single planes,
+ * FP32, tensor-core planes) instead of building its own, and builds only
+ * what depends on the problem's macromodels and type map (macromodel
+ * copies, work space, preconditioner).  offset_L/offset_K are not read
+ * (may be NULL); nx, ny, n_edges, precision, device and the grid must match
+ * `share`; a share that keeps half of the FP32 spectrum (single rhs, no
+ * tensor cores) serves only such problems, and tensor cores need a share
+ * that has their planes.  `share` must outlive the new handle and must not
+ * be destroyed first; the two may run calls at the same time (the shared
+ * blocks are only read).  Errors: as emsurf_create, EINVAL on a mismatch. */
+EMSURF_API int emsurf_create_like(const emsurf_problem* problem, const emsurf_handle* share,
+                                  emsurf_handle** out);
+
 /* y = U_o^T [Z_eq + Z_o] U_o x  (Eq. MVP) for nrhs right-hand sides.
  * x, y: device [nrhs][n_unique] complex128; must not overlap.
  * precision: EMSURF_FP64 or EMSURF_FP32 (the operator must be resident).
@@ -441,8 +456,9 @@ EMSURF_API int emsurf_far_field(emsurf_handle* h, double a, double b, double hgt
  * Serving (no counterpart in the paper, which solves one array at a time):
  * continuous batching of whole lattice solves.  A request describes one
  * lattice; a server worker builds it on the device (U_o, offset tables,
- * macromodels, FFT-domain operator, excitation), solves Eq. final and copies
- * the currents to x_out.  Requests with nrhs >= 8 and an FP32 operator use
+ * macromodels, FFT-domain operator, excitation) -- or takes the resident
+ * blocks of an earlier request of the same lattice and cell library --
+ * solves Eq. final and copies the currents to x_out.  Requests with nrhs >= 8 and an FP32 operator use
  * the tensor-core bin multiply (see tensor_cores in emsurf_problem).  Up to
  * max_active requests run at once, each on its
  * own non-blocking stream; a queued request is admitted (first fit) when a
@@ -454,6 +470,13 @@ typedef struct {
     int32_t device;
     int64_t device_mem_budget;   /* bytes admitted at once; 0 = free memory   */
     int32_t max_active;          /* concurrent solves, 1..64                  */
+    int32_t no_cache;            /* 1: build every request from scratch; 0:
+                                    keep each lattice's Fourier-domain blocks
+                                    and each cell library's macromodels
+                                    resident (within the budget, least
+                                    recently used evicted first) and build
+                                    later requests of the same lattice with
+                                    emsurf_create_like                        */
 } emsurf_server_opts;
 
 typedef struct {
@@ -492,6 +515,7 @@ typedef struct {
     double latency_ms;           /* submit -> done                            */
     int64_t est_bytes;           /* admission estimate                        */
     int64_t handle_bytes;        /* device bytes the solve handle held        */
+    int32_t cache_hit;           /* 1: the lattice's blocks were resident     */
 } emsurf_result;
 
 EMSURF_API int emsurf_server_create(const emsurf_server_opts* opts, emsurf_server** out);
@@ -506,8 +530,13 @@ EMSURF_API int emsurf_poll(emsurf_server* s, uint64_t ticket, emsurf_result* out
 /* As poll, but blocks up to timeout_ms; ETIMEDOUT if not done by then.    */
 EMSURF_API int emsurf_wait(emsurf_server* s, uint64_t ticket, int64_t timeout_ms,
                            emsurf_result* out);
-/* Stops accepting requests, finishes the queued and running ones, frees. */
+/* Stops accepting requests, finishes the queued and running ones, frees
+ * them and the resident blocks.                                           */
 EMSURF_API void emsurf_server_destroy(emsurf_server* s);
+/* Resident cache: device bytes held, cached lattices (operators), cached
+ * cell libraries, entries evicted so far.                                 */
+EMSURF_API int emsurf_server_stats(emsurf_server* s, int64_t* cached_bytes, int32_t* operators,
+                                   int32_t* libraries, int64_t* evictions);
 
 /* Thread-local message of the last failing call on this thread.          */
 EMSURF_API const char* emsurf_last_error(void);

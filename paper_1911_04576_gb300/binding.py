@@ -68,6 +68,7 @@ def lib():
         L = C.CDLL(LIB_PATH)
         vp, i32 = C.c_void_p, C.c_int32
         L.emsurf_create.argtypes = [C.POINTER(Problem), C.POINTER(vp)]
+        L.emsurf_create_like.argtypes = [C.POINTER(Problem), vp, C.POINTER(vp)]
         L.emsurf_matvec.argtypes = [vp, vp, vp, i32, i32, vp]
         L.emsurf_solve.argtypes = [vp, vp, vp, i32, C.POINTER(SolveOpts), C.POINTER(SolveInfo), vp]
         L.emsurf_query.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_int64)]
@@ -162,18 +163,21 @@ class Handle:
 def emsurf_create(nx, ny, n_edges, n_unique, type_map, macromodels, offset_L, offset_K, coef,
                   uo_index, uo_sign, precision=FP64, max_rhs=1, grid=(0, 0),
                   tables_on_device=False, device_mem_budget=0, device=0, unknown_xy=None,
-                  cell=(0.0, 0.0), precond_overlap=0.0, tensor_cores=False):
+                  cell=(0.0, 0.0), precond_overlap=0.0, tensor_cores=False, share=None):
     """emsurf_create: host NumPy inputs (or torch CUDA tensors for the tables
     and macromodels when tables_on_device=True); returns a Handle.  With
     unknown_xy ([n_unique, 2] from emsurf_setup_unknown_xy), cell = (a, b) and
-    precond_overlap > 0 the near-field preconditioner is built."""
+    precond_overlap > 0 the near-field preconditioner is built.  With share
+    (a Handle of the same lattice) it calls emsurf_create_like: the tables are
+    not read (may be None) and the new handle reads share's spectra."""
     type_map = np.ascontiguousarray(type_map, dtype=np.int32)
     uo_index = np.ascontiguousarray(uo_index, dtype=np.int32)
     uo_sign = np.ascontiguousarray(uo_sign, dtype=np.int8)
     if not tables_on_device:
         macromodels = np.ascontiguousarray(macromodels, dtype=np.complex128)
-        offset_L = np.ascontiguousarray(offset_L, dtype=np.complex128)
-        offset_K = np.ascontiguousarray(offset_K, dtype=np.complex128)
+        if offset_L is not None:
+            offset_L = np.ascontiguousarray(offset_L, dtype=np.complex128)
+            offset_K = np.ascontiguousarray(offset_K, dtype=np.complex128)
     n_types = int(macromodels.shape[0])
     p = Problem()
     p.nx, p.ny, p.n_edges, p.n_types, p.n_unique, p.max_rhs = nx, ny, n_edges, n_types, n_unique, max_rhs
@@ -195,6 +199,9 @@ def emsurf_create(nx, ny, n_edges, n_unique, type_map, macromodels, offset_L, of
     p.precond_overlap = precond_overlap
     p.tensor_cores = 1 if tensor_cores else 0
     out = C.c_void_p()
+    if share is not None:
+        _check(lib().emsurf_create_like(C.byref(p), share.ptr, C.byref(out)))
+        return Handle(out.value, (type_map, uo_index, uo_sign, share))
     _check(lib().emsurf_create(C.byref(p), C.byref(out)))
     return Handle(out.value, (type_map, uo_index, uo_sign))
 
@@ -441,7 +448,8 @@ def emsurf_check(h):
 
 # ------------------------------------------------------------------ serving
 class ServerOpts(C.Structure):
-    _fields_ = [("device", C.c_int32), ("device_mem_budget", C.c_int64), ("max_active", C.c_int32)]
+    _fields_ = [("device", C.c_int32), ("device_mem_budget", C.c_int64), ("max_active", C.c_int32),
+                ("no_cache", C.c_int32)]
 
 
 class Request(C.Structure):
@@ -458,7 +466,7 @@ class Result(C.Structure):
     _fields_ = [("status", C.c_int32), ("n_unique", C.c_int32), ("nrhs", C.c_int32),
                 ("info", SolveInfo), ("queue_ms", C.c_double), ("setup_ms", C.c_double),
                 ("solve_ms", C.c_double), ("latency_ms", C.c_double), ("est_bytes", C.c_int64),
-                ("handle_bytes", C.c_int64)]
+                ("handle_bytes", C.c_int64), ("cache_hit", C.c_int32)]
 
 
 def _serve_lib():
@@ -472,6 +480,8 @@ def _serve_lib():
         L.emsurf_wait.argtypes = [vp, C.c_uint64, C.c_int64, C.POINTER(Result)]
         L.emsurf_server_destroy.argtypes = [vp]
         L.emsurf_server_destroy.restype = None
+        L.emsurf_server_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                          C.POINTER(C.c_int32), C.POINTER(C.c_int64)]
         L._serve_ready = True
     return L
 
@@ -495,8 +505,8 @@ class Server:
             pass
 
 
-def emsurf_server_create(device=0, device_mem_budget=0, max_active=2):
-    o = ServerOpts(device, device_mem_budget, max_active)
+def emsurf_server_create(device=0, device_mem_budget=0, max_active=2, cache=True):
+    o = ServerOpts(device, device_mem_budget, max_active, 0 if cache else 1)
     out = C.c_void_p()
     _check(_serve_lib().emsurf_server_create(C.byref(o), C.byref(out)))
     return Server(out.value)
@@ -556,3 +566,10 @@ def emsurf_wait(server, ticket, timeout_ms=600000):
     _check(_serve_lib().emsurf_wait(server.ptr, ticket, int(timeout_ms), C.byref(r)))
     server.keep.pop(ticket, None)
     return _result(r)
+
+
+def emsurf_server_stats(server):
+    """(cached bytes, cached operators, cached libraries, evictions)."""
+    b, o, l, e = C.c_int64(), C.c_int32(), C.c_int32(), C.c_int64()
+    _check(_serve_lib().emsurf_server_stats(server.ptr, C.byref(b), C.byref(o), C.byref(l), C.byref(e)))
+    return b.value, o.value, l.value, e.value

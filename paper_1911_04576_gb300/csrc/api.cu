@@ -57,6 +57,17 @@ int dev_alloc(emsurf_handle* h, void** p, size_t bytes) {
     return EMSURF_OK;
 }
 
+void dev_free(emsurf_handle* h, void* p, size_t bytes) {
+    if (!p) return;
+    for (size_t i = 0; i < h->allocations.size(); ++i)
+        if (h->allocations[i] == p) {
+            cudaFree(p);
+            h->allocations.erase(h->allocations.begin() + (long)i);
+            h->device_bytes -= (int64_t)std::max<size_t>(bytes, 16);
+            return;
+        }
+}
+
 namespace {
 
 class DeviceGuard {
@@ -141,7 +152,7 @@ int upload(emsurf_handle* h, T** d, const T* src, size_t n) {
     return EMSURF_OK;
 }
 
-int create_impl(const emsurf_problem* p, emsurf_handle* h) {
+int create_impl(const emsurf_problem* p, emsurf_handle* h, const emsurf_handle* share) {
     h->device = p->device;
     h->setup_stream = reinterpret_cast<cudaStream_t>(p->stream);
     h->nx = p->nx;
@@ -154,8 +165,8 @@ int create_impl(const emsurf_problem* p, emsurf_handle* h) {
     h->max_rhs = p->max_rhs;
     h->precision = p->precision;
     h->budget = p->device_mem_budget;
-    h->px = p->grid_px ? p->grid_px : smallest_smooth_at_least(2 * p->nx - 1);
-    h->py = p->grid_py ? p->grid_py : smallest_smooth_at_least(2 * p->ny - 1);
+    h->px = share ? share->px : p->grid_px ? p->grid_px : smallest_smooth_at_least(2 * p->nx - 1);
+    h->py = share ? share->py : p->grid_py ? p->grid_py : smallest_smooth_at_least(2 * p->ny - 1);
     h->nbins = h->px * h->py;
     EMS_CUDA(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
     EMS_TRY(dev_alloc(h, (void**)&h->d_err, sizeof(int)));
@@ -213,18 +224,24 @@ int create_impl(const emsurf_problem* p, emsurf_handle* h) {
     h->d_mm_blocks = dblk;
     // operators
     if (h->precision == EMSURF_FP64 || h->precision == EMSURF_MIXED) {
-        EMS_TRY(build_operator<double2>(h, h->op64, p));
+        EMS_TRY(build_operator<double2>(h, h->op64, p, share ? &share->op64 : nullptr));
         h->have64 = true;
     }
     if (h->precision == EMSURF_FP32) {
-        EMS_TRY(build_operator<float2>(h, h->op32, p));
+        EMS_TRY(build_operator<float2>(h, h->op32, p, share ? &share->op32 : nullptr));
         h->have32 = true;
     } else if (h->precision == EMSURF_MIXED) {
-        EMS_TRY(derive_fp32_operator(h, p));
+        EMS_TRY(derive_fp32_operator(h, p, share));
         h->have32 = true;
     }
-    if (h->have64) EMS_TRY(build_ds_planes(h));
-    if (p->tensor_cores && h->have32 && h->E >= 64) EMS_TRY(tc_build(h));
+    if (h->have64) EMS_TRY(build_ds_planes(h, share));
+    if (p->tensor_cores && h->have32 && h->E >= 64) EMS_TRY(tc_build(h, share));
+    if (share) {
+        h->near_L = share->near_L;
+        h->near_K = share->near_K;
+    } else {
+        EMS_TRY(stage_near_tables(h, p));
+    }
     if (p->precond_overlap > 0.0 && p->unknown_xy) {
         if (!(p->cell_a > 0.0) || !(p->cell_b > 0.0)) {
             set_error("the preconditioner needs cell_a, cell_b > 0");
@@ -233,6 +250,13 @@ int create_impl(const emsurf_problem* p, emsurf_handle* h) {
         EMS_TRY(pc_build(h, p));
     }
     EMS_CUDA(cudaStreamSynchronize(h->setup_stream));
+    // with the double-single planes every FP64-accuracy bin multiply reads
+    // them (one rhs and several), so the complex128 spectrum is not needed
+    // after create: its bytes (those of the planes) are given back
+    if (h->have64 && h->ds_planes && h->op64.Bhat) {
+        dev_free(h, h->op64.Bhat, (size_t)h->nbins * 2 * (size_t)h->E * h->E * sizeof(double2));
+        h->op64.Bhat = nullptr;
+    }
     return EMSURF_OK;
 }
 
@@ -295,7 +319,57 @@ EMSURF_API int emsurf_create(const emsurf_problem* problem, emsurf_handle** out)
     if (!dg.ok()) { set_error("cannot select device %d", problem->device); return EMSURF_EINVAL; }
     emsurf_handle* h = new (std::nothrow) emsurf_handle();
     if (!h) { set_error("host allocation failed"); return EMSURF_ENOMEM; }
-    const int s = create_impl(problem, h);
+    const int s = create_impl(problem, h, nullptr);
+    if (s != EMSURF_OK) {
+        cudaStreamSynchronize(h->setup_stream);
+        gmres_release(h);
+        free_handle(h);
+        return s;
+    }
+    *out = h;
+    return EMSURF_OK;
+}
+
+EMSURF_API int emsurf_create_like(const emsurf_problem* problem, const emsurf_handle* share,
+                                  emsurf_handle** out) {
+    if (!out || !share || !problem) { set_error("emsurf_create_like: NULL argument"); return EMSURF_EINVAL; }
+    *out = nullptr;
+    // the tables are not read: stand-ins pass the pointer checks
+    emsurf_problem p = *problem;
+    if (!p.offset_L) p.offset_L = p.macromodels;
+    if (!p.offset_K) p.offset_K = p.macromodels;
+    const int save_dev = p.tables_on_device;
+    p.tables_on_device = 1;                 // skip the host scan of tables that are not read
+    EMS_TRY(validate(&p));
+    p.tables_on_device = save_dev;
+    if (p.nx != share->nx || p.ny != share->ny || p.n_edges != share->E || p.precision != share->precision ||
+        p.device != share->device || (p.grid_px && p.grid_px != share->px) || (p.grid_py && p.grid_py != share->py)) {
+        set_error("emsurf_create_like: lattice, RWG count, grid, precision or device differ from the shared handle");
+        return EMSURF_EINVAL;
+    }
+    const bool tc_wanted = p.tensor_cores && p.precision != EMSURF_FP64 && p.n_edges >= 64;
+    if (share->half32 && (p.max_rhs != 1 || tc_wanted)) {
+        set_error("emsurf_create_like: the shared handle keeps half of the FP32 spectrum (one rhs, no tensor "
+                  "cores); this problem needs the full spectrum");
+        return EMSURF_EINVAL;
+    }
+    if (tc_wanted && !share->have_tc) {
+        set_error("emsurf_create_like: tensor cores asked for, the shared handle has no tensor-core planes");
+        return EMSURF_EINVAL;
+    }
+    if (!p.tables_on_device) {
+        const size_t nz = (size_t)p.n_types * (size_t)(2 * p.n_edges) * (size_t)(2 * p.n_edges);
+        for (size_t i = 0; i < nz; ++i)
+            if (!std::isfinite(p.macromodels[i].re) || !std::isfinite(p.macromodels[i].im)) {
+                set_error("macromodels[%zu] is not finite", i);
+                return EMSURF_EINVAL;
+            }
+    }
+    DeviceGuard dg(p.device);
+    if (!dg.ok()) { set_error("cannot select device %d", p.device); return EMSURF_EINVAL; }
+    emsurf_handle* h = new (std::nothrow) emsurf_handle();
+    if (!h) { set_error("host allocation failed"); return EMSURF_ENOMEM; }
+    const int s = create_impl(&p, h, share);
     if (s != EMSURF_OK) {
         cudaStreamSynchronize(h->setup_stream);
         gmres_release(h);

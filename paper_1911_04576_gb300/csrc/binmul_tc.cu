@@ -332,9 +332,9 @@ binmul_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant_
 // Split planes of the spectrum, test-major: out[bin][op][2i+c][j] = hi/lo of
 // (c ? Im : Re) Bhat[bin][op][j][i] (source-major FP32), rows padded to ej.
 __global__ void tc_split_spectrum_kernel(const float2* __restrict__ Bhat, __nv_bfloat16* __restrict__ hi,
-                                         __nv_bfloat16* __restrict__ lo, int E, int ej) {
+                                         __nv_bfloat16* __restrict__ lo, int E, int ej, int z0) {
     __shared__ float2 tile[32][33];
-    const int bo = blockIdx.z;                  // bin * 2 + op
+    const int bo = z0 + (int)blockIdx.z;        // bin * 2 + op (launches cover <= 65535 at a time)
     const int j0 = blockIdx.x * 32, i0 = blockIdx.y * 32;
     const float2* src = Bhat + (size_t)bo * E * E;
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
@@ -876,24 +876,35 @@ int encode3d(CUtensorMap* map, void* base, uint64_t d0, uint64_t d1, uint64_t d2
 }  // namespace
 
 // Create-time: split planes of the FP32 spectrum and the tensor maps.
-int tc_build(emsurf_handle* h) {
+int tc_build(emsurf_handle* h, const emsurf_handle* share) {
     const int E = h->E;
     const int ej = (E + 7) & ~7;     // rows of 16-byte multiples
     const int rows = 4 * kTcRhs * ((h->max_rhs + kTcRhs - 1) / kTcRhs);
     const size_t nb = (size_t)h->nbins;
     const size_t spec = nb * 2 * 2 * E * ej;
-    EMS_TRY(dev_alloc(h, (void**)&h->tc_Bh, spec * sizeof(__nv_bfloat16)));
-    EMS_TRY(dev_alloc(h, (void**)&h->tc_Bl, spec * sizeof(__nv_bfloat16)));
-    EMS_CUDA(cudaMemsetAsync(h->tc_Bh, 0, spec * sizeof(__nv_bfloat16), h->setup_stream));
-    EMS_CUDA(cudaMemsetAsync(h->tc_Bl, 0, spec * sizeof(__nv_bfloat16), h->setup_stream));
+    if (share) {
+        // the spectrum planes of a handle of the same lattice (not owned)
+        h->tc_Bh = share->tc_Bh;
+        h->tc_Bl = share->tc_Bl;
+    } else {
+        EMS_TRY(dev_alloc(h, (void**)&h->tc_Bh, spec * sizeof(__nv_bfloat16)));
+        EMS_TRY(dev_alloc(h, (void**)&h->tc_Bl, spec * sizeof(__nv_bfloat16)));
+        EMS_CUDA(cudaMemsetAsync(h->tc_Bh, 0, spec * sizeof(__nv_bfloat16), h->setup_stream));
+        EMS_CUDA(cudaMemsetAsync(h->tc_Bl, 0, spec * sizeof(__nv_bfloat16), h->setup_stream));
+    }
     const size_t xs = nb * rows * ej;
     EMS_TRY(dev_alloc(h, (void**)&h->tc_Xh, xs * sizeof(__nv_bfloat16)));
     EMS_TRY(dev_alloc(h, (void**)&h->tc_Xl, xs * sizeof(__nv_bfloat16)));
-    const dim3 grid((E + 31) / 32, (E + 31) / 32, (unsigned)(nb * 2));
-    tc_split_spectrum_kernel<<<grid, dim3(32, 8), 0, h->setup_stream>>>(
-        h->op32.Bhat, reinterpret_cast<__nv_bfloat16*>(h->tc_Bh), reinterpret_cast<__nv_bfloat16*>(h->tc_Bl), E, ej);
-    EMS_CUDA(cudaGetLastError());
-    h->launches += 1;
+    if (!share) {
+        for (size_t z0 = 0; z0 < nb * 2; z0 += 65535) {
+            const dim3 grid((E + 31) / 32, (E + 31) / 32, (unsigned)std::min<size_t>(65535, nb * 2 - z0));
+            tc_split_spectrum_kernel<<<grid, dim3(32, 8), 0, h->setup_stream>>>(
+                h->op32.Bhat, reinterpret_cast<__nv_bfloat16*>(h->tc_Bh), reinterpret_cast<__nv_bfloat16*>(h->tc_Bl),
+                E, ej, (int)z0);
+            EMS_CUDA(cudaGetLastError());
+            h->launches += 1;
+        }
+    }
     static_assert(sizeof(CUtensorMap) <= sizeof(h->tc_maps[0]), "tensor map storage");
     CUtensorMap* m = reinterpret_cast<CUtensorMap*>(h->tc_maps);
     EMS_TRY(encode3d(&m[0], h->tc_Xh, ej, rows, nb, kBmKc, kTcM, CU_TENSOR_MAP_SWIZZLE_64B));
@@ -911,7 +922,7 @@ int tc_build(emsurf_handle* h) {
     EMS_CUDA(cudaMemsetAsync(h->tc_Zl, 0, zs * sizeof(__nv_bfloat16), h->setup_stream));
     const dim3 zgrid((K + 31) / 32, (K + 31) / 32, (unsigned)h->T);
     tc_split_spectrum_kernel<<<zgrid, dim3(32, 8), 0, h->setup_stream>>>(
-        h->op32.Zt, reinterpret_cast<__nv_bfloat16*>(h->tc_Zh), reinterpret_cast<__nv_bfloat16*>(h->tc_Zl), K, kp);
+        h->op32.Zt, reinterpret_cast<__nv_bfloat16*>(h->tc_Zh), reinterpret_cast<__nv_bfloat16*>(h->tc_Zl), K, kp, 0);
     EMS_CUDA(cudaGetLastError());
     h->launches += 1;
     int maxtiles = 0;

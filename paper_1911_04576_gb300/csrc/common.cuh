@@ -213,6 +213,7 @@ struct emsurf_handle {
     // split from the FP64 values times these), [2 + r] rhs r of the current
     // product (from max |x_r|); the kernels divide their FP64 outputs back
     double* d_ds_scale = nullptr;
+    double h_ds_scale0 = 1.0;         // the spectrum planes' scale (host copy)
     int pair_grid = 0;                // CTAs of the pair kernel (equal slab ranges)
     float2* d_pair_part = nullptr;    // partial row sums of straddling bins [cta][2][2E]
     int* d_pair_cnt = nullptr;        // arrival counters [stored bin][row warp]
@@ -261,6 +262,8 @@ struct emsurf_handle {
     void* pc_tc_items = nullptr;    // (cell, first owned row) per item
     int pc_tc_nitems = 0, pc_tc_np = 0;
     alignas(64) unsigned char pc_tc_maps[4][128];
+    const double2* near_L = nullptr;  // near offset tables [5][5][E][E] (|dx|, |dy| <= 2)
+    const double2* near_K = nullptr;
     int32_t* pc_n = nullptr;        // [M] subdomain sizes
     int32_t* pc_own = nullptr;      // [M] owned unknowns (first in each subdomain)
     int32_t* pc_sub_ptr = nullptr;  // [M+1]
@@ -280,6 +283,8 @@ struct emsurf_handle {
 
 namespace emsurf {
 int dev_alloc(emsurf_handle* h, void** p, size_t bytes);
+// free one of the handle's allocations before destroy (bytes as allocated)
+void dev_free(emsurf_handle* h, void* p, size_t bytes);
 // record the start (begin = true) or end of a phase on stream st if profiling
 void prof_mark(emsurf_handle* h, int phase, bool begin, cudaStream_t st);
 
@@ -323,10 +328,12 @@ int tabulate_blocks(const MeshView& test, const MeshView& src, const double* shi
                     const int8_t* singular, int nb, double k, double2* L, double2* K,
                     cudaStream_t st);
 template <typename T2>
-int build_operator(emsurf_handle* h, Operator<T2>& op, const emsurf_problem* pr);
-int derive_fp32_operator(emsurf_handle* h, const emsurf_problem* pr);
+int build_operator(emsurf_handle* h, Operator<T2>& op, const emsurf_problem* pr,
+                   const Operator<T2>* share = nullptr);
+// share: a handle of the same lattice whose Fourier-domain blocks are reused
+int derive_fp32_operator(emsurf_handle* h, const emsurf_problem* pr, const emsurf_handle* share = nullptr);
 int clear_wait_error(emsurf_handle* h);
-int build_ds_planes(emsurf_handle* h);
+int build_ds_planes(emsurf_handle* h, const emsurf_handle* share = nullptr);
 int grid_barrier_selftest(emsurf_handle* h, long long limit, cudaStream_t st);
 template <typename T2>
 int apply_operator(emsurf_handle* h, Operator<T2>& op, const double2* x, double2* y, int nrhs,
@@ -334,10 +341,11 @@ int apply_operator(emsurf_handle* h, Operator<T2>& op, const double2* x, double2
 // FP32 operator on FP32 vectors [R][n_unique] (the inner solve of MIXED)
 int apply_operator_f32(emsurf_handle* h, const float2* x, float2* y, int R, cudaStream_t st);
 int pc_build(emsurf_handle* h, const emsurf_problem* p);
+int stage_near_tables(emsurf_handle* h, const emsurf_problem* p);
 int wait_selftest(emsurf_handle* h, long long limit, cudaStream_t st);
 // tensor-core bin multiply (BF16x3) for nrhs >= kTcMinRhs
 constexpr int kTcMinRhs = 8;
-int tc_build(emsurf_handle* h);
+int tc_build(emsurf_handle* h, const emsurf_handle* share = nullptr);
 int tc_binmul(emsurf_handle* h, const float2* X, float2* Y, int R, const float2* coef, cudaStream_t st);
 int tc_macromodel(emsurf_handle* h, const double2* x, const float2* xf, float2* Ymm, int R, cudaStream_t st);
 int pc_tc_build(emsurf_handle* h, const std::vector<int32_t>& own_ptr);

@@ -1200,8 +1200,53 @@ int grid_for(size_t n, int threads) {
 // first column (Eq. LJV3 read by columns, d = test - source) -- and
 // transforms the grid with the forward 2-D FFT: B^(k) = F[B](k).
 template <typename T2>
-int build_operator(emsurf_handle* h, Operator<T2>& op, const emsurf_problem* pr) {
+int build_spectrum(emsurf_handle* h, Operator<T2>& op, const emsurf_problem* pr);
+
+template <typename T2>
+int build_operator(emsurf_handle* h, Operator<T2>& op, const emsurf_problem* pr, const Operator<T2>* share) {
     const int E = h->E, K = h->K;
+    const size_t EE = (size_t)E * E;
+    const int nox = 2 * h->nx - 1, noy = 2 * h->ny - 1;
+    const size_t nbins = (size_t)h->nbins;
+    cudaStream_t st = h->setup_stream;
+    if (share) {
+        // the spectrum of a handle of the same lattice (not owned here)
+        op.Bhat = share->Bhat;
+    } else {
+        EMS_TRY(build_spectrum(h, op, pr));
+    }
+    // macromodels
+    const size_t zbytes = (size_t)h->T * K * K * sizeof(double2);
+    double2* zstage = nullptr;
+    if (pr->tables_on_device) {
+        zstage = const_cast<double2*>(reinterpret_cast<const double2*>(pr->macromodels));
+    } else {
+        EMS_CUDA(cudaMalloc(&zstage, zbytes));
+        EMS_CUDA(cudaMemcpyAsync(zstage, pr->macromodels, zbytes, cudaMemcpyHostToDevice, st));
+    }
+    EMS_TRY(dev_alloc(h, (void**)&op.Zt, (size_t)h->T * K * K * sizeof(T2)));
+    dim3 zg((K + 31) / 32, (K + 31) / 32, h->T);
+    transpose_mm_kernel<T2><<<zg, dim3(32, 8), 0, st>>>(op.Zt, zstage, K);
+    EMS_CUDA(cudaGetLastError());
+    EMS_CUDA(cudaStreamSynchronize(st));
+    if (!pr->tables_on_device) cudaFree(zstage);
+    // work buffers
+    const size_t grid_elems = nbins * (size_t)h->max_rhs * K;
+    EMS_TRY(dev_alloc(h, (void**)&op.Xg, grid_elems * sizeof(T2)));
+    EMS_TRY(dev_alloc(h, (void**)&op.Yg, grid_elems * sizeof(T2)));
+    EMS_TRY(dev_alloc(h, (void**)&op.Ymm, (size_t)kMmSplit * h->max_rhs * h->M * K * sizeof(T2)));
+    EMS_TRY(dev_alloc(h, (void**)&op.Y1, (size_t)h->max_rhs * h->M * K * sizeof(T2)));
+    for (int c = 0; c < 4; ++c) op.coef[c] = mk<T2>(pr->coef[c].re, pr->coef[c].im);
+    (void)nox;
+    (void)noy;
+    (void)EE;
+    return EMSURF_OK;
+}
+
+// The Fourier-domain blocks of Sec. IV-B from the offset tables.
+template <typename T2>
+int build_spectrum(emsurf_handle* h, Operator<T2>& op, const emsurf_problem* pr) {
+    const int E = h->E;
     const size_t EE = (size_t)E * E;
     const int nox = 2 * h->nx - 1, noy = 2 * h->ny - 1;
     const size_t nbins = (size_t)h->nbins;
@@ -1262,39 +1307,37 @@ int build_operator(emsurf_handle* h, Operator<T2>& op, const emsurf_problem* pr)
         EMS_CUDA(cudaStreamSynchronize(st));
         cudaFree(B64);
     }
-    // macromodels
-    const size_t zbytes = (size_t)h->T * K * K * sizeof(double2);
-    double2* zstage = nullptr;
-    if (pr->tables_on_device) {
-        zstage = const_cast<double2*>(reinterpret_cast<const double2*>(pr->macromodels));
-    } else {
-        EMS_CUDA(cudaMalloc(&zstage, zbytes));
-        EMS_CUDA(cudaMemcpyAsync(zstage, pr->macromodels, zbytes, cudaMemcpyHostToDevice, st));
-    }
-    EMS_TRY(dev_alloc(h, (void**)&op.Zt, (size_t)h->T * K * K * sizeof(T2)));
-    dim3 zg((K + 31) / 32, (K + 31) / 32, h->T);
-    transpose_mm_kernel<T2><<<zg, dim3(32, 8), 0, st>>>(op.Zt, zstage, K);
-    EMS_CUDA(cudaGetLastError());
-    EMS_CUDA(cudaStreamSynchronize(st));
-    if (!pr->tables_on_device) cudaFree(zstage);
-    // work buffers
-    const size_t grid_elems = nbins * (size_t)h->max_rhs * K;
-    EMS_TRY(dev_alloc(h, (void**)&op.Xg, grid_elems * sizeof(T2)));
-    EMS_TRY(dev_alloc(h, (void**)&op.Yg, grid_elems * sizeof(T2)));
-    EMS_TRY(dev_alloc(h, (void**)&op.Ymm, (size_t)kMmSplit * h->max_rhs * h->M * K * sizeof(T2)));
-    EMS_TRY(dev_alloc(h, (void**)&op.Y1, (size_t)h->max_rhs * h->M * K * sizeof(T2)));
-    for (int c = 0; c < 4; ++c) op.coef[c] = mk<T2>(pr->coef[c].re, pr->coef[c].im);
     return EMSURF_OK;
 }
 
+int derive_fp32_rest(emsurf_handle* h, const emsurf_problem* pr);
+
 // FP32 operator of a MIXED handle: round the resident FP64 spectrum and
 // macromodels instead of transforming the tables a second time.
-int derive_fp32_operator(emsurf_handle* h, const emsurf_problem* pr) {
+int derive_fp32_operator(emsurf_handle* h, const emsurf_problem* pr, const emsurf_handle* share) {
     const int K = h->K;
     const size_t EE = (size_t)h->E * h->E;
     const size_t nb = (size_t)h->nbins;
     cudaStream_t st = h->setup_stream;
     Operator<float2>& op = h->op32;
+    if (share) {
+        // the FP32 spectrum (and its stored-bin lists) of the shared handle;
+        // the pair kernel's partial sums and counters are per-handle work space
+        op.Bhat = share->op32.Bhat;
+        h->half32 = share->half32;
+        h->nst = share->nst;
+        h->d_st_bin = share->d_st_bin;
+        h->d_st_part = share->d_st_part;
+        if (h->half32) {
+            const int ncw = (h->E + 31) / 32;
+            h->pair_grid = share->pair_grid;
+            EMS_TRY(dev_alloc(h, (void**)&h->d_pair_part, (size_t)h->pair_grid * 2 * 2 * h->E * sizeof(float2)));
+            h->pair_cnt_bytes = (size_t)h->nst * ncw * sizeof(int);
+            EMS_TRY(dev_alloc(h, (void**)&h->d_pair_cnt, h->pair_cnt_bytes));
+            EMS_CUDA(cudaMemsetAsync(h->d_pair_cnt, 0, h->pair_cnt_bytes, st));
+        }
+        return derive_fp32_rest(h, pr);
+    }
     // With reciprocal tables L^(-k) = L^(k)^T and K^(-k) = K^(k)^T: single-rhs
     // handles without the tensor-core planes keep one bin of each pair
     // (k, -k) (checked here on the FP64 spectrum, to 1e-12 of its largest
@@ -1358,6 +1401,15 @@ int derive_fp32_operator(emsurf_handle* h, const emsurf_problem* pr) {
         round_kernel<<<152 * 8, 256, 0, st>>>(op.Bhat, h->op64.Bhat, nb * 2 * EE);
         EMS_CUDA(cudaGetLastError());
     }
+    return derive_fp32_rest(h, pr);
+}
+
+// the FP32 macromodels and work buffers of a MIXED handle
+int derive_fp32_rest(emsurf_handle* h, const emsurf_problem* pr) {
+    const int K = h->K;
+    const size_t nb = (size_t)h->nbins;
+    cudaStream_t st = h->setup_stream;
+    Operator<float2>& op = h->op32;
     EMS_TRY(dev_alloc(h, (void**)&op.Zt, (size_t)h->T * K * K * sizeof(float2)));
     round_kernel<<<152 * 8, 256, 0, st>>>(op.Zt, h->op64.Zt, (size_t)h->T * K * K);
     EMS_CUDA(cudaGetLastError());
@@ -1374,15 +1426,17 @@ int derive_fp32_operator(emsurf_handle* h, const emsurf_problem* pr) {
 // double-single kernels (left out, and the FP64 kernels used, when the
 // single-rhs kernel's shape does not fit or the device-memory budget has no
 // room for them).
-int build_ds_planes(emsurf_handle* h) {
+int build_ds_planes(emsurf_handle* h, const emsurf_handle* share) {
     const int E = h->E;
     const int ncw = (E + 31) / 32;
     if (binmul_ds_smem(E) > 227 * 1024 || 32 * (1 + ncw) > 1024 || (E + kDsJB - 1) / kDsJB < kDsStages)
         return EMSURF_OK;
     const size_t nb = (size_t)h->nbins, EE = (size_t)E * E;
     const size_t pbytes = nb * 2 * 2 * EE * sizeof(float2), xbytes = nb * 2 * 2 * E * sizeof(float2);
-    if (h->budget > 0 && h->device_bytes + (int64_t)(pbytes + xbytes) > h->budget) return EMSURF_OK;
-    EMS_TRY(dev_alloc(h, (void**)&h->ds_planes, pbytes));
+    if (share && !share->ds_planes) return EMSURF_OK;          // products use the shared FP64 spectrum
+    if (!share && h->budget > 0 && h->device_bytes + (int64_t)(pbytes + xbytes) > h->budget) return EMSURF_OK;
+    if (share) h->ds_planes = share->ds_planes;
+    else EMS_TRY(dev_alloc(h, (void**)&h->ds_planes, pbytes));
     EMS_TRY(dev_alloc(h, (void**)&h->ds_x, xbytes));
     EMS_TRY(dev_alloc(h, (void**)&h->d_ds_scale, sizeof(double) * (2 + std::max(1, h->max_rhs))));
     // operator scales: the largest component of the spectrum (of the
@@ -1393,7 +1447,7 @@ int build_ds_planes(emsurf_handle* h) {
     double hs[2] = {1.0, 1.0};
     {
         std::vector<double> hp(2 * 1024);
-        absmax_part_kernel<<<1024, 256, 0, h->setup_stream>>>(h->op64.Bhat, nb * 2 * EE, part);
+        if (!share) absmax_part_kernel<<<1024, 256, 0, h->setup_stream>>>(h->op64.Bhat, nb * 2 * EE, part);
         absmax_part_kernel<<<1024, 256, 0, h->setup_stream>>>(h->op64.Zt, (size_t)h->T * KK, part + 1024);
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess)
@@ -1404,17 +1458,21 @@ int build_ds_planes(emsurf_handle* h) {
             set_error("operator scale: %s", cudaGetErrorString(e));
             return EMSURF_ECUDA;
         }
-        for (int w = 0; w < 2; ++w) {
+        for (int w = share ? 1 : 0; w < 2; ++w) {
             double mx = 0.0;
             for (int i = 0; i < 1024; ++i) mx = std::max(mx, hp[w * 1024 + i]);
             if (mx > 0.0 && std::isfinite(mx)) hs[w] = std::ldexp(1.0, -(std::ilogb(mx) + 1));
         }
+        if (share) hs[0] = share->h_ds_scale0;
+        h->h_ds_scale0 = hs[0];
         EMS_CUDA(cudaMemcpyAsync(h->d_ds_scale, hs, sizeof(hs), cudaMemcpyHostToDevice, h->setup_stream));
         EMS_CUDA(cudaStreamSynchronize(h->setup_stream));
     }
-    split_hilo_kernel<<<152 * 16, 256, 0, h->setup_stream>>>(h->ds_planes, h->op64.Bhat, 2 * EE, nb * 2 * EE,
-                                                             h->d_ds_scale);
-    EMS_CUDA(cudaGetLastError());
+    if (!share) {
+        split_hilo_kernel<<<152 * 16, 256, 0, h->setup_stream>>>(h->ds_planes, h->op64.Bhat, 2 * EE, nb * 2 * EE,
+                                                                 h->d_ds_scale);
+        EMS_CUDA(cudaGetLastError());
+    }
     // the macromodels likewise (the transposed Z~ of each type)
     const size_t zbytes = (size_t)h->T * 2 * KK * sizeof(float2);
     if ((h->K & 1) == 0 && (h->budget <= 0 || h->device_bytes + (int64_t)zbytes <= h->budget)) {
@@ -1675,8 +1733,10 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
     return EMSURF_OK;
 }
 
-template int build_operator<double2>(emsurf_handle*, Operator<double2>&, const emsurf_problem*);
-template int build_operator<float2>(emsurf_handle*, Operator<float2>&, const emsurf_problem*);
+template int build_operator<double2>(emsurf_handle*, Operator<double2>&, const emsurf_problem*,
+                                     const Operator<double2>*);
+template int build_operator<float2>(emsurf_handle*, Operator<float2>&, const emsurf_problem*,
+                                    const Operator<float2>*);
 template <typename T2>
 int apply_operator(emsurf_handle* h, Operator<T2>& op, const double2* x, double2* y, int R,
                    cudaStream_t st) {

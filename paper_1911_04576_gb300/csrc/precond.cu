@@ -615,6 +615,31 @@ int pc_apply_f32(emsurf_handle* h, const float2* r, float2* y, int R, cudaStream
 }
 
 // Subdomains, near tables, assembly and factorisation (create time).
+// The near offset tables |dx|, |dy| <= 2 as [5][5][E][E] (zero outside the
+// lattice), kept by the handle for the preconditioner's subdomain blocks.
+int stage_near_tables(emsurf_handle* h, const emsurf_problem* p) {
+    const int E = h->E, nx = h->nx, ny = h->ny;
+    const size_t EE = (size_t)E * E;
+    cudaStream_t st = h->setup_stream;
+    double2 *nL = nullptr, *nK = nullptr;
+    EMS_TRY(dev_alloc(h, (void**)&nL, 25 * EE * sizeof(double2)));
+    EMS_TRY(dev_alloc(h, (void**)&nK, 25 * EE * sizeof(double2)));
+    EMS_CUDA(cudaMemsetAsync(nL, 0, 25 * EE * sizeof(double2), st));
+    EMS_CUDA(cudaMemsetAsync(nK, 0, 25 * EE * sizeof(double2), st));
+    const cudaMemcpyKind kind = p->tables_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    for (int dy = -2; dy <= 2; ++dy)
+        for (int dx = -2; dx <= 2; ++dx) {
+            if (std::abs(dx) > nx - 1 || std::abs(dy) > ny - 1) continue;
+            const size_t src = ((size_t)(dy + ny - 1) * (2 * nx - 1) + (dx + nx - 1)) * EE;
+            const size_t dst = (size_t)((dy + 2) * 5 + (dx + 2)) * EE;
+            EMS_CUDA(cudaMemcpyAsync(nL + dst, p->offset_L + src, EE * sizeof(double2), kind, st));
+            EMS_CUDA(cudaMemcpyAsync(nK + dst, p->offset_K + src, EE * sizeof(double2), kind, st));
+        }
+    h->near_L = nL;
+    h->near_K = nK;
+    return EMSURF_OK;
+}
+
 int pc_build(emsurf_handle* h, const emsurf_problem* p) {
     const int M = h->M, K = h->K, E = h->E, nx = h->nx, ny = h->ny;
     const double a = p->cell_a, b = p->cell_b, del = p->precond_overlap;
@@ -731,20 +756,10 @@ int pc_build(emsurf_handle* h, const emsurf_problem* p) {
     EMS_CUDA(cudaMalloc(&d_lu, (size_t)moff[M] * sizeof(float2)));
     // near offset tables |dx|, |dy| <= 2 -> [5][5][E][E] (zero outside the lattice)
     const size_t EE = (size_t)E * E;
-    double2 *nL = nullptr, *nK = nullptr;
-    EMS_CUDA(cudaMalloc(&nL, 25 * EE * sizeof(double2)));
-    EMS_CUDA(cudaMalloc(&nK, 25 * EE * sizeof(double2)));
-    EMS_CUDA(cudaMemsetAsync(nL, 0, 25 * EE * sizeof(double2), st));
-    EMS_CUDA(cudaMemsetAsync(nK, 0, 25 * EE * sizeof(double2), st));
-    const cudaMemcpyKind kind = p->tables_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    for (int dy = -2; dy <= 2; ++dy)
-        for (int dx = -2; dx <= 2; ++dx) {
-            if (std::abs(dx) > nx - 1 || std::abs(dy) > ny - 1) continue;
-            const size_t src = ((size_t)(dy + ny - 1) * (2 * nx - 1) + (dx + nx - 1)) * EE;
-            const size_t dst = (size_t)((dy + 2) * 5 + (dx + 2)) * EE;
-            EMS_CUDA(cudaMemcpyAsync(nL + dst, p->offset_L + src, EE * sizeof(double2), kind, st));
-            EMS_CUDA(cudaMemcpyAsync(nK + dst, p->offset_K + src, EE * sizeof(double2), kind, st));
-        }
+    // (kept by the handle: emsurf_create_like builds its preconditioner from them)
+    const double2* nL = h->near_L;
+    const double2* nK = h->near_K;
+    (void)EE;
     // macromodels (transposed, FP64) for the assembly
     double2* Zt = nullptr;
     bool own_zt = false;
@@ -790,8 +805,7 @@ int pc_build(emsurf_handle* h, const emsurf_problem* p) {
     cudaFree(d_lu);
     cudaFree(d_perm);
     cudaFree(d_luoff);
-    cudaFree(nL);
-    cudaFree(nK);
+
     if (own_zt) cudaFree(Zt);
     for (int m = 0; m < M; ++m)
         if (hs[m]) {

@@ -82,3 +82,46 @@ def test_admission_and_polling(emsurf_lib):
         B.emsurf_poll(sv, t1)                       # collected already
     assert e.value.status == B.EMSURF_EINVAL
     sv.close()
+
+
+def test_resident_blocks_are_reused(emsurf_lib):
+    """Requests of one lattice with other type maps and rhs counts read the
+    Fourier-domain blocks and the library macromodels the first one left
+    resident (cache hits), and give the result of a server that builds
+    everything per request; a request that needs another spectrum form (one
+    rhs: half of the FP32 spectrum) gets an entry of its own."""
+    from paper_1911_04576_gb300 import binding as B
+    rng = np.random.default_rng(7)
+    n, nx, ny, T = 2, 4, 3, 3
+    sides = rng.uniform(0.15, 0.45, T) * W.LAMBDA
+    _, _, nu = B.emsurf_setup_overlap(n, nx, ny)
+    reqs = []
+    for R in (2, 3, 2, 1):
+        waves = [W.plane_waves(W.Workload("w", 1, 1, 1, 1, 0, 0, angles=[(th, 0.0, "theta")]))[0]
+                 for th in rng.uniform(0, 50, R)]
+        reqs.append(dict(a=A, b=A, h=H, n=n, nx=nx, ny=ny, k0=W.K0, patch_sides=sides, patch_z=W.PATCH_Z,
+                         patch_n=3, type_map=rng.integers(0, T, nx * ny), khat=np.array([w_[0] for w_ in waves]),
+                         ehat=np.array([w_[1] for w_ in waves]), precision=B.MIXED, rtol=1e-9, restart=30,
+                         max_iters=6000, precond_overlap=0.6 * A / n, slab_t=W.SLAB_T, slab_eps=W.EPS_SLAB,
+                         ring_layers=2, nu=nu, R=R))
+
+    def serve(cache):
+        sv = B.emsurf_server_create(0, 0, 1, cache=cache)
+        xs, res = [], []
+        for r in reqs:                       # one at a time: the first builds, the rest read
+            x = np.zeros((r["R"], r["nu"]), np.complex128)
+            q, keep = B.make_request(x_out=x, **{k: v for k, v in r.items() if k not in ("nu", "R")})
+            res.append(B.emsurf_wait(sv, B.emsurf_submit(sv, q, keep), 600000))
+            xs.append(x)
+        stats = B.emsurf_server_stats(sv)
+        sv.close()
+        return xs, res, stats
+
+    xc, rc, stats = serve(True)
+    xn, rn, _ = serve(False)
+    assert [r["cache_hit"] for r in rc] == [0, 1, 1, 0]
+    assert [r["cache_hit"] for r in rn] == [0, 0, 0, 0]
+    assert stats[1] == 2 and stats[2] == 1 and stats[0] > 0       # two lattice forms, one library
+    for a, b, r in zip(xc, xn, rc):
+        assert r["status"] == B.EMSURF_OK and r["info"]["rel_residual"] <= 1e-9
+        assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(b)
