@@ -248,6 +248,9 @@ def many_rhs_section(B, W, torch, name, hbm, bf16, time_left_s, rcs_step):
            "setup": setup, "device_bytes": dev_bytes}
     x = torch.randn((w.n_rhs, nu), dtype=torch.complex128, device="cuda")
     bm32, mv32 = _binmul_live(B, torch, h, x, B.FP32, 5)
+    kc, ns, tms = B.emsurf_tc_tuning(h)
+    out["tc_autotune"] = {"picked": "%d sources x %d stages" % (kc, ns),
+                          "ms_32x5": round(tms[0], 4), "ms_64x2": round(tms[1], 4)}
     spec = 2 * w.E * w.E * P * 8                       # bf16 hi + lo planes = complex64 bytes
     useful = 32.0 * w.E * w.E * w.n_rhs * P            # complex MACs x 8 flops
     out["fp32_matvec_ms"] = round(mv32, 3)

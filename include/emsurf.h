@@ -213,6 +213,14 @@ EMSURF_API int emsurf_precond_info(const emsurf_handle* h, int64_t* factor_entri
  * and whether the tensor-core planes were built (1) or not (0).          */
 EMSURF_API int emsurf_operator_info(const emsurf_handle* h, int32_t* stored_bins, int32_t* tensor_cores);
 
+/* Ring shape of the tensor-core bin multiply chosen at create by timing
+ * both shapes on the handle's spectrum (the library's own autotuner; no
+ * counterpart in the paper): sources per pipeline stage (32 or 64), stages
+ * (5 or 2), and the two shapes' times in ms ([0]: 32 x 5, [1]: 64 x 2);
+ * all zero for a handle without tensor-core planes.                       */
+EMSURF_API int emsurf_tc_tuning(const emsurf_handle* h, int32_t* sources_per_stage, int32_t* stages,
+                                double* ms_shapes);
+
 /* Grid chosen by emsurf_create, unknown count and bytes of device memory
  * held by the handle.                                                     */
 EMSURF_API int emsurf_query(const emsurf_handle* h, int32_t* grid_px, int32_t* grid_py,

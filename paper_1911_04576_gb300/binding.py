@@ -84,6 +84,7 @@ def lib():
         L.emsurf_precond_apply.argtypes = [vp, vp, vp, i32, vp]
         L.emsurf_selftest_wait.argtypes = [vp, C.c_int64, vp]
         L.emsurf_operator_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
+        L.emsurf_tc_tuning.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), vp]
         L.emsurf_precond_info.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                           C.POINTER(i32)]
         L.emsurf_setup_unknown_xy.argtypes = [C.c_double, C.c_double, C.c_double, i32, i32, i32,
@@ -228,6 +229,15 @@ def emsurf_operator_info(h):
     nb, tc = C.c_int32(), C.c_int32()
     _check(lib().emsurf_operator_info(h.ptr, C.byref(nb), C.byref(tc)))
     return nb.value, bool(tc.value)
+
+
+def emsurf_tc_tuning(h):
+    """(sources per stage, stages, [ms of the 32 x 5 and 64 x 2 shapes]) of the
+    tensor-core bin multiply's autotuned ring."""
+    kc, ns = C.c_int32(), C.c_int32()
+    ms = np.zeros(2)
+    _check(lib().emsurf_tc_tuning(h.ptr, C.byref(kc), C.byref(ns), _ptr(ms)))
+    return kc.value, ns.value, ms.tolist()
 
 
 def emsurf_precond_info(h):

@@ -50,17 +50,22 @@ constexpr int kTcStageBytes = 2 * kTcABytes + 4 * kTcBBytes;   // A hi/lo, B hi/
 constexpr int kTcSmem = 1024 + kTcStages * kTcStageBytes;
 constexpr uint32_t kTcTmemCols = 512;     // two accumulator sets of 2 x 96 columns
 constexpr long long kTcWait = 1LL << 22;
-// The bin multiply's ring: 32 sources per stage (64-byte rows, 64B swizzle)
-// in 5 stages of 40 KB: more bytes in flight per SM than 2 stages of 80 KB
-// (the spectrum stream is latency-bound per SM: throughput = bytes in
-// flight / DRAM latency), same bytes per item.
-constexpr int kBmKc = 32;
-constexpr int kBmStages = 5;
-constexpr int kBmABytes = kTcM * 64;        // 8 KB
-constexpr int kBmBBytes = kTcN * 64;        // 6 KB
-constexpr int kBmStageBytes = 2 * kBmABytes + 4 * kBmBBytes;
-constexpr int kBmSmem = 1024 + kBmStages * kBmStageBytes;
-static_assert(kBmSmem <= 227 * 1024, "bin multiply ring exceeds shared memory");
+// The bin multiply's ring, two shapes chosen per handle by timing them at
+// create (the spectrum stream is latency-bound per SM, throughput = bytes in
+// flight / DRAM latency, so the deeper ring usually wins):
+//   KC = 32 sources per stage (64-byte rows, 64B swizzle), 5 stages of 40 KB;
+//   KC = 64 sources per stage (128-byte rows, 128B swizzle), 2 stages of 80 KB.
+template <int KC>
+struct BmShape {
+    static constexpr int ABytes = kTcM * KC * 2;
+    static constexpr int BBytes = kTcN * KC * 2;
+    static constexpr int StageBytes = 2 * ABytes + 4 * BBytes;
+};
+template <int KC, int STAGES>
+constexpr int bm_smem() {
+    return 1024 + STAGES * BmShape<KC>::StageBytes;
+}
+static_assert(bm_smem<32, 5>() <= 227 * 1024 && bm_smem<64, 2>() <= 227 * 1024, "bin multiply ring exceeds shared memory");
 // instruction descriptor: kind::f16, bf16 x bf16 -> f32, K-major A and B, N = 96, M = 128
 constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
                               ((uint32_t)(kTcM >> 4) << 24);
@@ -105,6 +110,11 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
 __device__ __forceinline__ uint64_t sdesc64(uint32_t addr) {
     return (uint64_t)((addr & 0x3FFFF) >> 4) | (1ull << 16) | (32ull << 32) | (1ull << 46) | (4ull << 61);
 }
+template <int KC>
+__device__ __forceinline__ uint64_t bm_desc(uint32_t addr) {
+    if constexpr (KC == 64) return sdesc(addr);
+    else return sdesc64(addr);
+}
 __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -133,12 +143,13 @@ struct TcArgs {
     int* err;
 };
 
+template <int KC, int STAGES>
 __global__ void __launch_bounds__(kTcThreads, 1)
 binmul_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
                  const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, TcArgs g) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full[kBmStages], empty[kBmStages], accf[2], acce[2], mma_done;
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], accf[2], acce[2], mma_done;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -148,7 +159,7 @@ binmul_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant_
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kBmStages; ++s) {
+        for (int s = 0; s < STAGES; ++s) {
             bar_init(&full[s], 1);
             bar_init(&empty[s], 1);
         }
@@ -171,7 +182,7 @@ binmul_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant_
         if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0;
-            int issued[kBmStages] = {0, 0, 0, 0, 0};
+            int issued[STAGES] = {};
             for (int item = blockIdx.x; item < g.items && !*(volatile int*)&abort_flag; item += gridDim.x) {
                 const int grp = item / (g.nbins * g.chunks), rem = item % (g.nbins * g.chunks);
                 const int bin = rem / g.chunks, ch = rem % g.chunks;
@@ -181,25 +192,25 @@ binmul_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant_
                         *(volatile int*)&abort_flag = 1;
                         break;
                     }
-                    unsigned char* st = smem + stage * kBmStageBytes;
-                    bar_expect(&full[stage], kBmStageBytes);
-                    const int j0 = ks * kBmKc;
+                    unsigned char* st = smem + stage * BmShape<KC>::StageBytes;
+                    bar_expect(&full[stage], BmShape<KC>::StageBytes);
+                    const int j0 = ks * KC;
                     tma3d(st, &mAh, j0, kTcM * grp, bin, &full[stage]);
-                    tma3d(st + kBmABytes, &mAl, j0, kTcM * grp, bin, &full[stage]);
+                    tma3d(st + BmShape<KC>::ABytes, &mAl, j0, kTcM * grp, bin, &full[stage]);
                     for (int op = 0; op < 2; ++op) {
-                        unsigned char* b = st + 2 * kBmABytes + op * 2 * kBmBBytes;
+                        unsigned char* b = st + 2 * BmShape<KC>::ABytes + op * 2 * BmShape<KC>::BBytes;
                         tma3d(b, &mBh, j0, kTcN * ch, 2 * bin + op, &full[stage]);
-                        tma3d(b + kBmBBytes, &mBl, j0, kTcN * ch, 2 * bin + op, &full[stage]);
+                        tma3d(b + BmShape<KC>::BBytes, &mBl, j0, kTcN * ch, 2 * bin + op, &full[stage]);
                     }
                     ++issued[stage];
-                    if (++stage == kBmStages) {
+                    if (++stage == STAGES) {
                         stage = 0;
                         phase ^= 1;
                     }
                 }
             }
             // every copy this thread issued has landed before the CTA can exit
-            for (int s = 0; s < kBmStages; ++s)
+            for (int s = 0; s < STAGES; ++s)
                 if (issued[s] && !bar_wait(&full[s], (uint32_t)((issued[s] - 1) & 1))) atomicExch(g.err, 4);
         }
     } else if (warp == 1) {
@@ -225,14 +236,14 @@ binmul_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant_
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;");
-                    const uint32_t st = saddr(smem + stage * kBmStageBytes);
-                    const uint32_t ah = st, al = st + kBmABytes;
-                    for (int kk = 0; kk < kBmKc / 16; ++kk) {
+                    const uint32_t st = saddr(smem + stage * BmShape<KC>::StageBytes);
+                    const uint32_t ah = st, al = st + BmShape<KC>::ABytes;
+                    for (int kk = 0; kk < KC / 16; ++kk) {
                         const uint32_t off = 32u * kk;
-                        const uint64_t dah = sdesc64(ah + off), dal = sdesc64(al + off);
+                        const uint64_t dah = bm_desc<KC>(ah + off), dal = bm_desc<KC>(al + off);
                         for (int op = 0; op < 2; ++op) {
-                            const uint32_t b = st + 2 * kBmABytes + op * 2 * kBmBBytes;
-                            const uint64_t dbh = sdesc64(b + off), dbl = sdesc64(b + kBmBBytes + off);
+                            const uint32_t b = st + 2 * BmShape<KC>::ABytes + op * 2 * BmShape<KC>::BBytes;
+                            const uint64_t dbh = bm_desc<KC>(b + off), dbl = bm_desc<KC>(b + BmShape<KC>::BBytes + off);
                             const uint32_t d = op ? dK : dL;
                             mma_bf16(d, dah, dbh, (ks > 0 || kk > 0) ? 1u : 0u);
                             mma_bf16(d, dah, dbl, 1u);
@@ -241,7 +252,7 @@ binmul_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant_
                     }
                     mma_commit(&empty[stage]);   // the stage is free once these MMAs have read it
                     any = true;
-                    if (++stage == kBmStages) {
+                    if (++stage == STAGES) {
                         stage = 0;
                         phase ^= 1;
                     }
@@ -875,6 +886,8 @@ int encode3d(CUtensorMap* map, void* base, uint64_t d0, uint64_t d1, uint64_t d2
 
 }  // namespace
 
+int tc_tune(emsurf_handle* h);
+
 // Create-time: split planes of the FP32 spectrum and the tensor maps.
 int tc_build(emsurf_handle* h, const emsurf_handle* share) {
     const int E = h->E;
@@ -907,10 +920,15 @@ int tc_build(emsurf_handle* h, const emsurf_handle* share) {
     }
     static_assert(sizeof(CUtensorMap) <= sizeof(h->tc_maps[0]), "tensor map storage");
     CUtensorMap* m = reinterpret_cast<CUtensorMap*>(h->tc_maps);
-    EMS_TRY(encode3d(&m[0], h->tc_Xh, ej, rows, nb, kBmKc, kTcM, CU_TENSOR_MAP_SWIZZLE_64B));
-    EMS_TRY(encode3d(&m[1], h->tc_Xl, ej, rows, nb, kBmKc, kTcM, CU_TENSOR_MAP_SWIZZLE_64B));
-    EMS_TRY(encode3d(&m[2], h->tc_Bh, ej, 2 * E, 2 * nb, kBmKc, kTcN, CU_TENSOR_MAP_SWIZZLE_64B));
-    EMS_TRY(encode3d(&m[3], h->tc_Bl, ej, 2 * E, 2 * nb, kBmKc, kTcN, CU_TENSOR_MAP_SWIZZLE_64B));
+    // maps of both ring shapes: [0..3] 32-source boxes (64B swizzle), [8..11] 64-source boxes (128B)
+    EMS_TRY(encode3d(&m[0], h->tc_Xh, ej, rows, nb, 32, kTcM, CU_TENSOR_MAP_SWIZZLE_64B));
+    EMS_TRY(encode3d(&m[1], h->tc_Xl, ej, rows, nb, 32, kTcM, CU_TENSOR_MAP_SWIZZLE_64B));
+    EMS_TRY(encode3d(&m[2], h->tc_Bh, ej, 2 * E, 2 * nb, 32, kTcN, CU_TENSOR_MAP_SWIZZLE_64B));
+    EMS_TRY(encode3d(&m[3], h->tc_Bl, ej, 2 * E, 2 * nb, 32, kTcN, CU_TENSOR_MAP_SWIZZLE_64B));
+    EMS_TRY(encode3d(&m[8], h->tc_Xh, ej, rows, nb, 64, kTcM));
+    EMS_TRY(encode3d(&m[9], h->tc_Xl, ej, rows, nb, 64, kTcM));
+    EMS_TRY(encode3d(&m[10], h->tc_Bh, ej, 2 * E, 2 * nb, 64, kTcN));
+    EMS_TRY(encode3d(&m[11], h->tc_Bl, ej, 2 * E, 2 * nb, 64, kTcN));
     h->tc_ej = ej;
     h->tc_rows = rows;
     // macromodel planes: Z~ [t][2k+c][kp] and x1 tiles [tile][128][kp]
@@ -940,6 +958,13 @@ int tc_build(emsurf_handle* h, const emsurf_handle* share) {
     h->tc_mm_tiles.assign(h->max_rhs + 1, nullptr);
     h->tc_mm_ntiles.assign(h->max_rhs + 1, 0);
     h->have_tc = true;
+    if (share) {
+        h->tc_variant = share->tc_variant;
+        h->tc_tune_ms[0] = share->tc_tune_ms[0];
+        h->tc_tune_ms[1] = share->tc_tune_ms[1];
+    } else {
+        EMS_TRY(tc_tune(h));
+    }
     return EMSURF_OK;
 }
 
@@ -989,6 +1014,41 @@ int tc_macromodel(emsurf_handle* h, const double2* x, const float2* xf, float2* 
     return EMSURF_OK;
 }
 
+// launch of the bin multiply's kernel in ring shape `variant` (0: 32 x 5, 1: 64 x 2)
+int tc_binmul_launch(emsurf_handle* h, float2* Y, int R, const float2* coef, int variant, cudaStream_t st) {
+    const int E = h->E, ej = h->tc_ej;
+    const size_t nb = (size_t)h->nbins;
+    TcArgs a;
+    a.Y = Y;
+    a.E = E;
+    a.nbins = (int)nb;
+    a.R = R;
+    a.groups = (R + kTcRhs - 1) / kTcRhs;
+    a.chunks = (2 * E + kTcN - 1) / kTcN;
+    const int kc = variant == 0 ? 32 : 64;
+    a.nk = (ej + kc - 1) / kc;
+    a.items = a.groups * a.nbins * a.chunks;
+    a.ca = coef[0];
+    a.cb = coef[1];
+    a.cg = coef[2];
+    a.cd = coef[3];
+    a.err = h->d_err;
+    const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(h->tc_maps);
+    const int grid = std::min(a.items, h->num_sms);
+    if (variant == 0) {
+        constexpr int sm = bm_smem<32, 5>();
+        EMS_TRY(set_smem_once(binmul_tc_kernel<32, 5>, (size_t)sm));
+        binmul_tc_kernel<32, 5><<<grid, kTcThreads, sm, st>>>(m[0], m[1], m[2], m[3], a);
+    } else {
+        constexpr int sm = bm_smem<64, 2>();
+        EMS_TRY(set_smem_once(binmul_tc_kernel<64, 2>, (size_t)sm));
+        binmul_tc_kernel<64, 2><<<grid, kTcThreads, sm, st>>>(m[8], m[9], m[10], m[11], a);
+    }
+    EMS_CUDA(cudaGetLastError());
+    h->launches += 1;
+    return EMSURF_OK;
+}
+
 // Y^ = B^ X^ for every bin on the tensor cores (R rhs, FP32 grids [bins][R][2E]).
 int tc_binmul(emsurf_handle* h, const float2* X, float2* Y, int R, const float2* coef, cudaStream_t st) {
     const int E = h->E, ej = h->tc_ej, rows = h->tc_rows;
@@ -997,27 +1057,44 @@ int tc_binmul(emsurf_handle* h, const float2* X, float2* Y, int R, const float2*
     tc_split_x_kernel<<<(int)std::min<size_t>((xs + 255) / 256, (size_t)h->num_sms * 16), 256, 0, st>>>(
         X, reinterpret_cast<__nv_bfloat16*>(h->tc_Xh), reinterpret_cast<__nv_bfloat16*>(h->tc_Xl), E, ej, R, rows, xs);
     EMS_CUDA(cudaGetLastError());
-    TcArgs a;
-    a.Y = Y;
-    a.E = E;
-    a.nbins = (int)nb;
-    a.R = R;
-    a.groups = (R + kTcRhs - 1) / kTcRhs;
-    a.chunks = (2 * E + kTcN - 1) / kTcN;
-    a.nk = (ej + kBmKc - 1) / kBmKc;
-    a.items = a.groups * a.nbins * a.chunks;
-    a.ca = coef[0];
-    a.cb = coef[1];
-    a.cg = coef[2];
-    a.cd = coef[3];
-    a.err = h->d_err;
-    EMS_TRY(set_smem_once(binmul_tc_kernel, (size_t)kBmSmem));
-    const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(h->tc_maps);
-    const int grid = std::min(a.items, h->num_sms);
-    binmul_tc_kernel<<<grid, kTcThreads, kBmSmem, st>>>(m[0], m[1], m[2], m[3], a);
-    EMS_CUDA(cudaGetLastError());
-    h->launches += 2;
-    return EMSURF_OK;
+    h->launches += 1;
+    return tc_binmul_launch(h, Y, R, coef, h->tc_variant, st);
+}
+
+// The project's autotuner for the bin multiply's ring shape: both shapes
+// run twice on this handle's spectrum (max_rhs rhs; the values in the X^
+// planes do not change the time), CUDA events on the setup stream, the
+// faster one kept.  Shared handles take their share's choice.
+int tc_tune(emsurf_handle* h) {
+    cudaStream_t st = h->setup_stream;
+    const float2 coef[4] = {make_float2(1.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(1.f, 0.f)};
+    float best = 1e30f;
+    cudaEvent_t e0, e1;
+    EMS_CUDA(cudaEventCreate(&e0));
+    EMS_CUDA(cudaEventCreate(&e1));
+    int status = EMSURF_OK;
+    for (int v = 0; v < 2 && !status; ++v) {
+        status = tc_binmul_launch(h, h->op32.Yg, h->max_rhs, coef, v, st);          // warm-up
+        if (status) break;
+        cudaEventRecord(e0, st);
+        status = tc_binmul_launch(h, h->op32.Yg, h->max_rhs, coef, v, st);
+        cudaEventRecord(e1, st);
+        if (status) break;
+        float ms = 0.f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            set_error("tensor-core autotune: event timing failed");
+            status = EMSURF_ECUDA;
+            break;
+        }
+        h->tc_tune_ms[v] = ms;
+        if (ms < best) {
+            best = ms;
+            h->tc_variant = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return status;
 }
 
 }  // namespace emsurf
@@ -1091,3 +1168,25 @@ template int pc_tc_apply<double2>(emsurf_handle*, const double2*, double2*, int,
 template int pc_tc_apply<float2>(emsurf_handle*, const float2*, float2*, int, cudaStream_t);
 
 }  // namespace emsurf
+
+extern "C" {
+
+EMSURF_API int emsurf_tc_tuning(const emsurf_handle* h, int32_t* sources_per_stage, int32_t* stages,
+                                double* ms_shapes) {
+    if (!h) { emsurf::set_error("emsurf_tc_tuning: NULL handle"); return EMSURF_EINVAL; }
+    if (!h->have_tc) {
+        if (sources_per_stage) *sources_per_stage = 0;
+        if (stages) *stages = 0;
+        if (ms_shapes) ms_shapes[0] = ms_shapes[1] = 0.0;
+        return EMSURF_OK;
+    }
+    if (sources_per_stage) *sources_per_stage = h->tc_variant == 0 ? 32 : 64;
+    if (stages) *stages = h->tc_variant == 0 ? 5 : 2;
+    if (ms_shapes) {
+        ms_shapes[0] = h->tc_tune_ms[0];
+        ms_shapes[1] = h->tc_tune_ms[1];
+    }
+    return EMSURF_OK;
+}
+
+}  // extern "C"

@@ -121,6 +121,14 @@ struct FftPlan {
 };
 
 int fft_plan_create(FftPlan& plan, int P);
+// fused 2-D transforms of square grids up to 64 x 64 (fft2d.cu)
+bool fft2d_fused_ok(int px, int py);
+template <typename T2>
+int fft2d_forward(T2* Xg, int P, long long lanes, int nx, int ny, int K, int n_unique, const double2* tw,
+                  const double2* x, const float2* xf, const int32_t* idx, const int8_t* sgn, cudaStream_t st);
+template <typename T2>
+int fft2d_inverse(const T2* Yg, int P, long long lanes, int nx, int ny, int K, int M, int R, int nsplit,
+                  double scale, const double2* tw, const T2* mm, T2* y1, cudaStream_t st);
 void fft_plan_destroy(FftPlan& plan);
 
 // In-place 1-D transform along p of data[outer][P][inner] (inner contiguous
@@ -232,7 +240,9 @@ struct emsurf_handle {
     std::vector<void*> tc_mm_tiles;   // per rhs count: device (type, first column) tile list
     std::vector<int> tc_mm_ntiles;
     // tensor maps: X hi, X lo, B hi, B lo (bin multiply); x1 hi, x1 lo, Z hi, Z lo (macromodels)
-    alignas(64) unsigned char tc_maps[8][128];
+    alignas(64) unsigned char tc_maps[12][128];
+    int tc_variant = 0;                    // bin multiply ring shape picked by the autotuner
+    float tc_tune_ms[2] = {0.f, 0.f};      // the two shapes' times at create
     int mm_occ[4] = {0, 0, 0, 0};          // resident macromodel CTAs per SM (FP32, FP64; x 1 / 4 rhs)
     int mm_threads[4] = {0, 0, 0, 0};      // macromodel block size per variant
     int mm2_occ = 0;                       // resident single-rhs FP32 macromodel CTAs per SM

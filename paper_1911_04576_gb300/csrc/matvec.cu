@@ -1498,9 +1498,16 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
     // K1: x-pass over the cell rows iy < ny reading x1 = U_o x directly
     // (points ix >= nx are the zero padding), then the y-pass with rows
     // iy >= ny taken as zero
-    EMS_TRY(fft_pass_gather<T2>(op.Xg, h->plan_x, lanes, h->ny, (long long)px * lanes, h->nx, x,
-                                h->d_uo_index, h->d_uo_sign, h->nx, K, h->n_unique, st, xf));
-    EMS_TRY(fft_pass<T2>(op.Xg, h->plan_y, (long long)px * lanes, 1, 0, -1, st, h->ny, py));
+    const bool fused = fft2d_fused_ok(px, py);
+    if (fused) {
+        // one launch: gather, both 1-D transforms, X^ stored
+        EMS_TRY(fft2d_forward<T2>(op.Xg, px, lanes, h->nx, h->ny, K, h->n_unique, h->plan_x.tw, x, xf,
+                                  h->d_uo_index, h->d_uo_sign, st));
+    } else {
+        EMS_TRY(fft_pass_gather<T2>(op.Xg, h->plan_x, lanes, h->ny, (long long)px * lanes, h->nx, x,
+                                    h->d_uo_index, h->d_uo_sign, h->nx, K, h->n_unique, st, xf));
+        EMS_TRY(fft_pass<T2>(op.Xg, h->plan_y, (long long)px * lanes, 1, 0, -1, st, h->ny, py));
+    }
     prof_mark(h, ph_fft, false, st);
     prof_mark(h, ph_mm, true, st);
     // K4
@@ -1716,9 +1723,14 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
     prof_mark(h, ph_bin, false, st);
     prof_mark(h, ph_fft, true, st);
     // K3: inverse y-pass on all columns, inverse x-pass on the rows kept
-    EMS_TRY(fft_pass<T2>(op.Yg, h->plan_y, (long long)px * lanes, 1, 0, +1, st, py, h->ny));
-    EMS_TRY(fft_pass_crop<T2>(op.Yg, h->plan_x, lanes, h->ny, (long long)px * lanes, h->nx, op.Ymm,
-                              nsplit, R, h->M, K, 1.0 / (double)h->nbins, op.Y1, st));
+    if (fused) {
+        EMS_TRY(fft2d_inverse<T2>(op.Yg, px, lanes, h->nx, h->ny, K, h->M, R, nsplit, 1.0 / (double)h->nbins,
+                                  h->plan_x.tw, op.Ymm, op.Y1, st));
+    } else {
+        EMS_TRY(fft_pass<T2>(op.Yg, h->plan_y, (long long)px * lanes, 1, 0, +1, st, py, h->ny));
+        EMS_TRY(fft_pass_crop<T2>(op.Yg, h->plan_x, lanes, h->ny, (long long)px * lanes, h->nx, op.Ymm,
+                                  nsplit, R, h->M, K, 1.0 / (double)h->nbins, op.Y1, st));
+    }
     prof_mark(h, ph_fft, false, st);
     prof_mark(h, EMS_PH_SCATTER, true, st);
     if (yf)
@@ -1729,7 +1741,7 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
             y, op.Y1, h->d_inv_ptr, h->d_inv_ent, h->d_inv_sgn, h->M * K, R, h->n_unique);
     EMS_CUDA(cudaGetLastError());
     prof_mark(h, EMS_PH_SCATTER, false, st);
-    h->launches += 6;   // 4 FFT passes, macromodel, crop/scatter
+    h->launches += fused ? 4 : 6;   // FFTs (2 fused or 4 passes), macromodel, scatter
     return EMSURF_OK;
 }
 

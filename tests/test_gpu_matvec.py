@@ -256,3 +256,31 @@ def test_double_single_outside_fp32_range(emsurf_lib, sx, sop):
             assert np.all(np.isfinite(y[r])) and relerr(y[r], yref[r]) <= 1e-12, (R, r)
         B.emsurf_check(h)
         h.close()
+
+
+@pytest.mark.parametrize("n,nx,ny,P,R", [(2, 4, 4, 8, 1), (2, 3, 3, 5, 3), (2, 8, 7, 16, 2), (1, 12, 12, 24, 2),
+                                         (2, 16, 16, 32, 1), (1, 20, 24, 48, 1)])
+def test_fused_2d_fft_matches_passes(emsurf_lib, n, nx, ny, P, R):
+    """Square grids up to 64 x 64 take the fused 2-D transforms (gather, both
+    passes and the crop/epilogue in one launch each); a taller grid takes the
+    pass-based ones.  Both embeddings are exact (any grid >= 2N - 1),
+    so FP64 products agree to rounding and both match the oracle."""
+    from paper_1911_04576_gb300 import binding as B
+    seed = 1300 + P + nx
+    E, idx, sgn, nu, Lt, Kt, Z, tmap = random_case(n, nx, ny, 2, seed)
+    x = W.random_vectors(R, nu, seed + 5)
+    Q = P + 1                      # a taller grid with no prime factor above 7
+    while any(Q % f == 0 for f in (11, 13, 17, 19, 23, 29, 31)):
+        Q += 1
+    ys = {}
+    for grid in ((P, P), (P, Q)):
+        h = B.emsurf_create(nx, ny, E, nu, tmap, Z, Lt, Kt, COEF, idx, sgn, precision=B.MIXED, max_rhs=R,
+                            grid=grid)
+        ys[grid] = (run_matvec(B, h, x, B.FP64), run_matvec(B, h, x, B.FP32))
+        B.emsurf_check(h)
+        h.close()
+    yref = lattice.matvec_direct(x, Lt, Kt, COEF, Z, tmap, idx, sgn, nu, nx, ny)
+    for r in range(R):
+        assert relerr(ys[(P, P)][0][r], ys[(P, Q)][0][r]) <= 1e-13
+        assert relerr(ys[(P, P)][0][r], yref[r]) <= TOL64
+        assert relerr(ys[(P, P)][1][r], yref[r]) <= TOL32
