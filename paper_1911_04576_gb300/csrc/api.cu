@@ -169,6 +169,9 @@ int create_impl(const emsurf_problem* p, emsurf_handle* h, const emsurf_handle* 
     h->py = share ? share->py : p->grid_py ? p->grid_py : smallest_smooth_at_least(2 * p->ny - 1);
     h->nbins = h->px * h->py;
     EMS_CUDA(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+    EMS_CUDA(cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking));
+    EMS_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    EMS_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
     EMS_TRY(dev_alloc(h, (void**)&h->d_err, sizeof(int)));
     EMS_CUDA(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->setup_stream));
     EMS_TRY(dev_alloc(h, (void**)&h->d_grid_bar, 2 * sizeof(unsigned)));
@@ -263,6 +266,12 @@ int create_impl(const emsurf_problem* p, emsurf_handle* h, const emsurf_handle* 
 void free_handle(emsurf_handle* h) {
     for (auto& pt : h->prof)
         for (cudaEvent_t e : pt.ev) cudaEventDestroy(e);
+    if (h->side_stream) {
+        cudaStreamSynchronize(h->side_stream);
+        cudaStreamDestroy(h->side_stream);
+    }
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     for (void* p : h->allocations) cudaFree(p);
     h->allocations.clear();
     fft_plan_destroy(h->plan_x);

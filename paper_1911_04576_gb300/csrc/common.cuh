@@ -247,6 +247,8 @@ struct emsurf_handle {
     int mm_threads[4] = {0, 0, 0, 0};      // macromodel block size per variant
     int mm2_occ = 0;                       // resident single-rhs FP32 macromodel CTAs per SM
     cudaStream_t setup_stream = nullptr;   // stream of the create-time work
+    cudaStream_t side_stream = nullptr;    // the macromodel product beside the bin multiply
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // near-field preconditioner (restricted additive Schwarz, FP32 LU blocks)
     bool have_pc = false;
     int pc_nmax = 0;

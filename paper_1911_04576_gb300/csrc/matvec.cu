@@ -1509,15 +1509,34 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
         EMS_TRY(fft_pass<T2>(op.Xg, h->plan_y, (long long)px * lanes, 1, 0, -1, st, h->ny, py));
     }
     prof_mark(h, ph_fft, false, st);
-    prof_mark(h, ph_mm, true, st);
-    // K4
+    if constexpr (std::is_same<T2, double2>::value) {
+        if (h->ds_planes && x) {
+            // per-rhs powers of two for the double-single operands of this product
+            pow2_scale_kernel<<<R, 256, 0, st>>>(x, (size_t)h->n_unique, h->d_ds_scale + 2);
+            EMS_CUDA(cudaGetLastError());
+            h->launches += 1;
+        }
+    }
+    // K4 runs on the handle's side stream, beside the forward transform and
+    // the bin multiply (it reads only x and writes only the partials Ymm the
+    // inverse transform adds): its L2- and FP32-bound work overlaps their
+    // HBM-bound streaming.  The tensor-core variant (>= 8 rhs) stays on the
+    // caller's stream.
+    const bool side = h->side_stream && !(h->have_tc && R >= kTcMinRhs);
+    cudaStream_t mst = st;
+    if (side) {
+        EMS_CUDA(cudaEventRecord(h->ev_fork, st));
+        EMS_CUDA(cudaStreamWaitEvent(h->side_stream, h->ev_fork, 0));
+        mst = h->side_stream;
+    }
+    prof_mark(h, ph_mm, true, mst);
     // K splits of the macromodel product: as many as fill one wave of
     // resident CTAs (a partial second wave would double its time), at most
     // kMmSplit and at least 32 columns each
     bool mm_done = false;
     if constexpr (std::is_same<T2, float2>::value) {
         if (h->have_tc && R >= kTcMinRhs) {
-            EMS_TRY(tc_macromodel(h, x, xf, op.Ymm, R, st));
+            EMS_TRY(tc_macromodel(h, x, xf, op.Ymm, R, mst));
             mm_done = true;
         }
     }
@@ -1576,7 +1595,7 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
             ns2 = (K + chunk2 - 1) / chunk2;
             const size_t sm = (size_t)kMmGroup * chunk2 * sizeof(float2);
             EMS_TRY(set_smem_once(macromodel2_kernel<kMmGroup>, sm));
-            macromodel2_kernel<kMmGroup><<<dim3(nblk, ns2), threads2, sm, st>>>(
+            macromodel2_kernel<kMmGroup><<<dim3(nblk, ns2), threads2, sm, mst>>>(
                 op.Zt, x, h->d_uo_index, h->d_uo_sign, h->d_type_cells,
                 reinterpret_cast<const MmBlock*>(h->d_mm_blocks), op.Ymm, K, h->M, h->n_unique, chunk2, xf);
             EMS_CUDA(cudaGetLastError());
@@ -1585,12 +1604,6 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
         }
     }
     if constexpr (std::is_same<T2, double2>::value) {
-        if (h->ds_planes && x) {
-            // per-rhs powers of two for the double-single operands of this product
-            pow2_scale_kernel<<<R, 256, 0, st>>>(x, (size_t)h->n_unique, h->d_ds_scale + 2);
-            EMS_CUDA(cudaGetLastError());
-            h->launches += 1;
-        }
         if (!mm_done && R == 1 && h->ds_zt) {
             // one rhs, FP64 accuracy from double-single FP32 arithmetic
             const int threads2 = std::min(320, ((K / 2 + 31) / 32) * 32);
@@ -1602,7 +1615,7 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
             ns2 = (K + chunk2 - 1) / chunk2;
             const size_t sm = (size_t)2 * kMmGroup * chunk2 * sizeof(float2);
             EMS_TRY(set_smem_once(macromodel_ds_kernel<kMmGroup>, sm));
-            macromodel_ds_kernel<kMmGroup><<<dim3(nblk, ns2), threads2, sm, st>>>(
+            macromodel_ds_kernel<kMmGroup><<<dim3(nblk, ns2), threads2, sm, mst>>>(
                 h->ds_zt, x, h->d_uo_index, h->d_uo_sign, h->d_type_cells,
                 reinterpret_cast<const MmBlock*>(h->d_mm_blocks), op.Ymm, K, h->M, chunk2, h->d_ds_scale);
             EMS_CUDA(cudaGetLastError());
@@ -1617,18 +1630,19 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
         if (blk4) {
             const size_t sm = (size_t)4 * kMmGroup * chunk * sizeof(T2);
             EMS_TRY(set_smem_once(macromodel_kernel<T2, kMmGroup, 4>, sm));
-            macromodel_kernel<T2, kMmGroup, 4><<<dim3(nblk, nsplit), mthreads, sm, st>>>(
+            macromodel_kernel<T2, kMmGroup, 4><<<dim3(nblk, nsplit), mthreads, sm, mst>>>(
                 op.Zt, x, h->d_uo_index, h->d_uo_sign, h->d_type_cells, blocks, op.Ymm, K, h->M, R,
                 h->n_unique, chunk, xf);
         } else {
             macromodel_kernel<T2, kMmGroup, 1><<<dim3(nblk, nsplit), mthreads,
-                                                 (size_t)kMmGroup * chunk * sizeof(T2), st>>>(
+                                                 (size_t)kMmGroup * chunk * sizeof(T2), mst>>>(
                 op.Zt, x, h->d_uo_index, h->d_uo_sign, h->d_type_cells, blocks, op.Ymm, K, h->M, R,
                 h->n_unique, chunk, xf);
         }
         EMS_CUDA(cudaGetLastError());
     }
-    prof_mark(h, ph_mm, false, st);
+    prof_mark(h, ph_mm, false, mst);
+    if (side) EMS_CUDA(cudaEventRecord(h->ev_join, mst));
     prof_mark(h, ph_bin, true, st);
     // K2
     const int threads = std::min(1024, ((E + 31) / 32) * 32);
@@ -1721,6 +1735,7 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
         }
     }
     prof_mark(h, ph_bin, false, st);
+    if (side) EMS_CUDA(cudaStreamWaitEvent(st, h->ev_join, 0));      // the partials are in Ymm
     prof_mark(h, ph_fft, true, st);
     // K3: inverse y-pass on all columns, inverse x-pass on the rows kept
     if (fused) {
