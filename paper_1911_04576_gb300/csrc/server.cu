@@ -410,8 +410,14 @@ int run_job(emsurf_server* sv, Job& jb, cudaStream_t st) {
     }
     cudaFree(V);
     cudaFree(X);
-    // a cached full handle stays; a light handle or an uncached one goes
-    const bool keep_hd = oe && build_op && hd == oe->h;
+    // a cached full handle stays (with the solve's work space: its bytes are
+    // counted again); a light handle or an uncached one goes
+    const bool keep_hd = oe && build_op && hd && hd == oe->h;
+    if (keep_hd) {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        jb.new_bytes += jb.peak_bytes - oe->bytes;
+        oe->bytes = jb.peak_bytes;
+    }
     if (hd && !keep_hd) emsurf_destroy(hd);
     if (!sv->cache_on && Z) cudaFree(Z);
     {
