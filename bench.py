@@ -42,7 +42,7 @@ RESTART = 30
 # because the oracle, at ~1.8 s per product, would need over two hours.
 REF_MATVECS_PER_SOLVE = 4389
 FALLBACK_HBM_GBS = 6800.0
-PC_OVERLAP = 0.6               # preconditioner margin, in mesh cells (a / n)
+PC_OVERLAP = 1.0               # preconditioner margin, in mesh cells (a / n)
 # DRAM bytes (read + write) per bin of one binmul_tma_kernel launch, from an
 # ncu capture of the 12x12 lattice (576 bins, dram__bytes_read.sum +
 # dram__bytes_write.sum); the kernel streams each bin's blocks once, so
@@ -244,6 +244,7 @@ def many_rhs_section(B, W, torch, name, hbm, bf16, time_left_s, rcs_step):
     t_start = time.time()
     h, V, nu, setup, zl = build_problem(B, W, torch, w, B.MIXED, max_rhs=w.n_rhs, tensor_cores=True)
     setup["total_s"] = round(time.time() - t_start, 2)
+    _log(name + " setup", setup)
     px, py, dev_bytes = B.emsurf_query(h)
     P = px * py
     out = {"workload": w.name, "lattice": [w.nx, w.ny], "K": w.K, "n_types": w.n_types,
@@ -367,6 +368,16 @@ def cpu_fft_section(W, w, nmv_plain, iters_pc):
                     "iterations)" % (nmv_plain, iters_pc)}
 
 
+_T0 = time.time()
+
+
+def _log(section, obj=None):
+    """Progress on stderr: seconds since start, the section, its result (so a
+    run cut short still shows where the time went and what was measured)."""
+    print("[bench %7.1fs] %s %s" % (time.time() - _T0, section, json.dumps(obj) if obj is not None else ""),
+          file=sys.stderr, flush=True)
+
+
 def last_iters(infos):
     return infos[-1]["iters"] if infos else 0
 
@@ -463,7 +474,7 @@ SERVE_MESH = (3, 4)            # boxes meshed n x n: K = 324 or 576
 SERVE_RHS = tuple(range(1, 17))   # rhs per request, uniform in 1..16
 SERVE_RATE = 20.0              # Poisson arrivals per second
 SERVE_BUDGET = 80 << 30        # device-memory budget of the server
-SERVE_FP64_SAMPLE = 16         # requests of the one-at-a-time FP64 arm
+SERVE_FP64_SAMPLE = 8         # requests of the one-at-a-time FP64 arm
 
 
 def serve_requests(B, W, nreq, seed, precision, precond):
@@ -591,7 +602,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--multi-rhs", type=int, default=1,
                     help="also time %d-rhs FP32 products, tensor cores vs FP32 kernels (0 = skip)" % 32)
-    ap.add_argument("--serve-requests", type=int, default=200,
+    ap.add_argument("--serve-requests", type=int, default=60,
                     help="requests of the serving stream (0 = skip the serving measurement)")
     ap.add_argument("--matvecs-only", type=int, default=0,
                     help="profiler driver: build the workload, run this many products, exit")
@@ -643,6 +654,7 @@ def main():
         h.close()
         return
     h, V, nu, setup, zl = build_problem(B, W, torch, w, B.MIXED)
+    _log("setup", setup)
     X = torch.zeros_like(V)
     hbm, peak_kind = peaks()
     # FP64-plain reference solve on the same handle (FP64 operator GMRES,
@@ -661,6 +673,7 @@ def main():
                                     solver=B.SOLVER_FP64)
     t64p = (time.perf_counter() - t0) * 1e3
     pc_elems, pc_subtot, pc_nmax = B.emsurf_precond_info(h)
+    _log("reference solves", {"fp64_plain_ms": t64, "mixed_unpreconditioned_ms": tnp, "fp64_precond_ms": t64p})
     # matvec rates
     R = w.n_rhs
     mv32 = time_matvec(B, torch, h, nu, R, B.FP32)
@@ -716,6 +729,7 @@ def main():
     fft64_ms, _ = B.emsurf_profile_read(h, "fft64")
     mm64_ms, _ = B.emsurf_profile_read(h, "mm64")
     ms = max_over_ranks(dist, ms_total / args.steps, "cuda")
+    _log("timed solves", {"ms_per_solve": ms, "iters": infos[-1]["iters"] if infos else None})
     # ------------------------------------------------------------ end to end
     Vh = V.cpu().pin_memory()
     Xh = torch.empty_like(Vh).pin_memory()
@@ -733,25 +747,31 @@ def main():
     e2e_ms = f0.elapsed_time(f1) / args.steps
     # ------------------------------------------------------------ accuracy
     accuracy = accuracy_section(B, torch, h, V, X, w, zl) if args.accuracy else None
+    _log("accuracy", accuracy)
     # ------------------------------------------------------------ many rhs
     multi = multi_rhs_section(B, W, torch, w, hbm) if args.multi_rhs else None
+    _log("multi_rhs", multi)
     h.close()          # free the bench handle's device memory for the other sections
     torch.cuda.empty_cache()
     bf16, _ = bf16_peak()
     batched = many_rhs_section(B, W, torch, "lattice48x48_k576_r32", hbm, bf16, 120.0, 1.0) \
         if args.batched else None
+    _log("batched", batched)
     torch.cuda.empty_cache()
     largest = many_rhs_section(B, W, torch, "lattice100x100_k324_r8", hbm, bf16, 150.0, 2.0) \
         if args.largest else None
+    _log("largest", largest)
     torch.cuda.empty_cache()
     # ------------------------------------------------------------ serving
     serve = None
     if args.serve_requests > 0:
         serve = serve_section(B, W, args.serve_requests)
+        _log("serve", serve)
     # ------------------------------------------------------------ CPU oracle
     cpu_fft = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu_fft = cpu_fft_section(W, w, info64[0]["n_matvec"], last_iters(infos))
+        _log("cpu_fft", cpu_fft)
         t_cpu = cpu_oracle_matvec_seconds(W, w, nu)
         nmv64 = info64[0]["n_matvec"]
         cpu = {"value": t_cpu * 1e3 * nmv64, "unit": "ms", "cores": len(os.sched_getaffinity(0)),
