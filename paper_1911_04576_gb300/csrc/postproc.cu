@@ -111,48 +111,132 @@ __global__ void radiation_kernel(const RwgQuad* __restrict__ q, int E, const dou
     }
 }
 
-// S[r][d][k] = sum_m e^{jk rhat_d . c_m} sign * Y[r][idx[m*K + k]]
-__global__ void lattice_sum_kernel(const double2* __restrict__ Y, const int32_t* __restrict__ idx,
-                                   const int8_t* __restrict__ sgn, int nx, int M, int K, int n_unique,
-                                   double a, double b, const double* __restrict__ rhat, int D,
-                                   int R, double k, double2* __restrict__ S) {
-    const size_t total = (size_t)R * D * K;
-    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < total;
-         x += (size_t)gridDim.x * blockDim.x) {
-        const int kk = (int)(x % K);
-        const int d = (int)((x / K) % D);
-        const int r = (int)(x / ((size_t)K * D));
-        const double* rh = rhat + 3 * d;
-        double2 acc = make_double2(0.0, 0.0);
-        for (int m = 0; m < M; ++m) {
-            const size_t loc = (size_t)m * K + kk;
-            const double2 y = Y[(size_t)r * n_unique + idx[loc]];
-            const double s = (double)sgn[loc];
-            const double2 ph = cexpj(k * (rh[0] * (m % nx) * a + rh[1] * (m / nx) * b));
-            acc.x += s * (ph.x * y.x - ph.y * y.y);
-            acc.y += s * (ph.x * y.y + ph.y * y.x);
-        }
-        S[x] = acc;
+// X1[m][r K + k] = sign * Y[r][idx[m K + k]]: every cell's box currents
+template <typename C>
+__global__ void gather_cells_kernel(const double2* __restrict__ Y, const int32_t* __restrict__ idx,
+                                    const int8_t* __restrict__ sgn, int M, int K, int R, int n_unique,
+                                    C* __restrict__ X1) {
+    const size_t N = (size_t)R * K, total = (size_t)M * N;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t m = e / N, rem = e - m * N;
+        const int r = (int)(rem / K), kk = (int)(rem - (size_t)r * K);
+        const size_t loc = m * K + kk;
+        const double s = (double)sgn[loc];
+        const double2 y = Y[(size_t)r * n_unique + idx[loc]];
+        C v;
+        v.x = s * y.x;
+        v.y = s * y.y;
+        X1[e] = v;
     }
 }
 
-__global__ void far_field_kernel(const double2* __restrict__ S, const double2* __restrict__ Rv,
+// The array factor of every column: S[d][n] = sum_m e^{jk rhat_d . c_m}
+// X1[m][n], c_m = (ix a, iy b, 0).  A block computes kLsD directions x kLsN
+// columns; the phase of cell m factors into per-direction tables
+// e^{jk rx a ix} e^{jk ry b iy} (one sincos per direction and row or column of
+// the lattice instead of one per term), X1 is staged kLsM cells at a time.
+// Each thread holds 2 directions x 4 columns (columns tn + 16 c, so a
+// warp's shared-memory reads are consecutive).  T: arithmetic type (double
+// for FP64 handles; float, with float accumulation over the cells, for
+// FP32 / MIXED handles).
+constexpr int kLsD = 32, kLsN = 64, kLsM = 16, kLsThreads = 256;
+
+template <typename T, typename C>
+__global__ void __launch_bounds__(kLsThreads)
+lattice_sum_tiled_kernel(const C* __restrict__ X1, int M, int N, int nx, int ny, double a, double b,
+                         const double* __restrict__ rhat, int nd, double k, C* __restrict__ S) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* px = reinterpret_cast<C*>(smem_raw);            // [kLsD][nx]
+    C* py = px + kLsD * nx;                            // [kLsD][ny]
+    C* xs = py + kLsD * ny;                            // [kLsM][kLsN]
+    const int d0 = blockIdx.y * kLsD, n0 = blockIdx.x * kLsN;
+    for (int e = threadIdx.x; e < kLsD * nx; e += blockDim.x) {
+        const int dd = e / nx, ix = e - dd * nx, d = d0 + dd;
+        double sn = 0.0, cs = 1.0;
+        if (d < nd) sincos(k * a * rhat[3 * d] * ix, &sn, &cs);
+        px[e].x = (T)cs;
+        px[e].y = (T)sn;
+    }
+    for (int e = threadIdx.x; e < kLsD * ny; e += blockDim.x) {
+        const int dd = e / ny, iy = e - dd * ny, d = d0 + dd;
+        double sn = 0.0, cs = 1.0;
+        if (d < nd) sincos(k * b * rhat[3 * d + 1] * iy, &sn, &cs);
+        py[e].x = (T)cs;
+        py[e].y = (T)sn;
+    }
+    const int tn = threadIdx.x & 15, td = threadIdx.x >> 4;     // 16 column groups x 16 direction pairs
+    C acc[2][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[i][c].x = acc[i][c].y = (T)0;
+    const C* pxa = px + (2 * td) * nx;
+    const C* pxb = pxa + nx;
+    const C* pya = py + (2 * td) * ny;
+    const C* pyb = pya + ny;
+    for (int m0 = 0; m0 < M; m0 += kLsM) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < kLsM * kLsN; e += blockDim.x) {
+            const int mm = e / kLsN, c = e - mm * kLsN;
+            C v;
+            v.x = v.y = (T)0;
+            if (m0 + mm < M && n0 + c < N) v = X1[(size_t)(m0 + mm) * N + n0 + c];
+            xs[e] = v;
+        }
+        __syncthreads();
+        const int mend = min(kLsM, M - m0);
+        for (int mm = 0; mm < mend; ++mm) {
+            const int m = m0 + mm, iy = m / nx, ix = m - iy * nx;
+            C pa, pb;
+            pa.x = pxa[ix].x * pya[iy].x - pxa[ix].y * pya[iy].y;
+            pa.y = pxa[ix].x * pya[iy].y + pxa[ix].y * pya[iy].x;
+            pb.x = pxb[ix].x * pyb[iy].x - pxb[ix].y * pyb[iy].y;
+            pb.y = pxb[ix].x * pyb[iy].y + pxb[ix].y * pyb[iy].x;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const C x = xs[mm * kLsN + tn + 16 * c];
+                acc[0][c].x += pa.x * x.x - pa.y * x.y;
+                acc[0][c].y += pa.x * x.y + pa.y * x.x;
+                acc[1][c].x += pb.x * x.x - pb.y * x.y;
+                acc[1][c].y += pb.x * x.y + pb.y * x.x;
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int d = d0 + 2 * td + i;
+        if (d >= nd) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int n = n0 + tn + 16 * c;
+            if (n < N) S[(size_t)d * N + n] = acc[i][c];
+        }
+    }
+}
+
+// F[r][d] = -(jk/4pi) [N_perp - rhat x L_M] of the column sums S[d][r K + e]
+template <typename C>
+__global__ void far_field_kernel(const C* __restrict__ S, const double2* __restrict__ Rv,
                                  const double* __restrict__ rhat, int D, int E, int R, double k,
-                                 double2* __restrict__ F, double* __restrict__ rcs) {
+                                 double2* __restrict__ F, double* __restrict__ rcs, int ndir_all) {
     const size_t total = (size_t)R * D;
+    const int K = 2 * E;
     for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < total;
          x += (size_t)gridDim.x * blockDim.x) {
-        const int d = (int)(x % D);
+        const int d = (int)(x % D), r = (int)(x / D);
         const double* rh = rhat + 3 * d;
-        const double2* s = S + x * 2 * E;
+        const C* s = S + (size_t)d * R * K + (size_t)r * K;
         const double2* rv = Rv + (size_t)d * E * 3;
         double2 N[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
         double2 L[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
-        for (int e = 0; e < E; ++e)
+        for (int e = 0; e < E; ++e) {
+            const double2 sj = make_double2((double)s[e].x, (double)s[e].y);
+            const double2 sm = make_double2((double)s[E + e].x, (double)s[E + e].y);
             for (int c = 0; c < 3; ++c) {
-                cfma(N[c], s[e], rv[3 * e + c]);
-                cfma(L[c], s[E + e], rv[3 * e + c]);
+                cfma(N[c], sj, rv[3 * e + c]);
+                cfma(L[c], sm, rv[3 * e + c]);
             }
+        }
         double2 rn = make_double2(0, 0);
         for (int c = 0; c < 3; ++c) {
             rn.x += rh[c] * N[c].x;
@@ -167,13 +251,14 @@ __global__ void far_field_kernel(const double2* __restrict__ S, const double2* _
             v[c] = make_double2(N[c].x - rn.x * rh[c] - rxl.x, N[c].y - rn.y * rh[c] - rxl.y);
         }
         double mag = 0.0;
+        double2* f = F + ((size_t)r * ndir_all + d) * 3;
         for (int c = 0; c < 3; ++c) {
             // -(jk / 4pi) v
-            const double2 f = make_double2(k * v[c].y / kFourPi, -k * v[c].x / kFourPi);
-            F[x * 3 + c] = f;
-            mag += f.x * f.x + f.y * f.y;
+            const double2 fc = make_double2(k * v[c].y / kFourPi, -k * v[c].x / kFourPi);
+            f[c] = fc;
+            mag += fc.x * fc.x + fc.y * fc.y;
         }
-        if (rcs) rcs[x] = kFourPi * mag;
+        if (rcs) rcs[(size_t)r * ndir_all + d] = kFourPi * mag;
     }
 }
 
@@ -242,6 +327,58 @@ struct Scoped {
     }
 };
 
+template <typename T, typename C>
+int far_field_run(emsurf_handle* h, const std::vector<RwgQuad>& q, double a, double b, double k,
+                  const emsurf_c128* Y, int nrhs, int ndir, const double* rhat, emsurf_c128* F, double* rcs,
+                  cudaStream_t st) {
+    const int E = h->E, K = h->K, M = h->M, N = nrhs * K;
+    // directions in chunks so the per-chunk arrays stay under ~512 MB
+    const size_t per_dir = (size_t)E * 3 * sizeof(double2) + (size_t)N * sizeof(C);
+    const int chunk = (int)std::max<size_t>(1, std::min<size_t>(ndir, (512ull << 20) / per_dir));
+    Scoped sc;
+    RwgQuad* dq;
+    double* dr;
+    double2* Rv;
+    C *S, *X1;
+    EMS_TRY(to_device(&dq, q.data(), q.size(), st));
+    sc.p.push_back(dq);
+    EMS_TRY(to_device(&dr, rhat, 3 * (size_t)ndir, st));
+    sc.p.push_back(dr);
+    EMS_CUDA(cudaMalloc(&Rv, sizeof(double2) * (size_t)chunk * E * 3));
+    sc.p.push_back(Rv);
+    EMS_CUDA(cudaMalloc(&S, sizeof(C) * (size_t)chunk * N));
+    sc.p.push_back(S);
+    EMS_CUDA(cudaMalloc(&X1, sizeof(C) * (size_t)M * N));
+    sc.p.push_back(X1);
+    gather_cells_kernel<C><<<(int)std::min<size_t>(((size_t)M * N + 255) / 256, 152 * 32), 256, 0, st>>>(
+        reinterpret_cast<const double2*>(Y), h->d_uo_index, h->d_uo_sign, M, K, nrhs, h->n_unique, X1);
+    EMS_CUDA(cudaGetLastError());
+    const size_t lsm = ((size_t)kLsD * (h->nx + h->ny) + (size_t)kLsM * kLsN) * sizeof(C);
+    if (lsm > 227 * 1024) {
+        set_error("emsurf_far_field: lattice %d x %d too large for the phase tables", h->nx, h->ny);
+        return EMSURF_EINVAL;
+    }
+    EMS_TRY(set_smem_once(lattice_sum_tiled_kernel<T, C>, lsm));
+    double2* Fo = reinterpret_cast<double2*>(F);
+    for (int d0 = 0; d0 < ndir; d0 += chunk) {
+        const int nd = std::min(chunk, ndir - d0);
+        const size_t t1 = (size_t)nd * E;
+        radiation_kernel<<<(int)std::min<size_t>((t1 + 127) / 128, 152 * 32), 128, 0, st>>>(
+            dq, E, dr + 3 * (size_t)d0, nd, k, Rv);
+        EMS_CUDA(cudaGetLastError());
+        const dim3 g2((unsigned)((N + kLsN - 1) / kLsN), (unsigned)((nd + kLsD - 1) / kLsD));
+        lattice_sum_tiled_kernel<T, C><<<g2, kLsThreads, lsm, st>>>(X1, M, N, h->nx, h->ny, a, b,
+                                                                     dr + 3 * (size_t)d0, nd, k, S);
+        EMS_CUDA(cudaGetLastError());
+        const size_t t3 = (size_t)nrhs * nd;
+        far_field_kernel<C><<<(int)std::min<size_t>((t3 + 127) / 128, 152 * 32), 128, 0, st>>>(
+            S, Rv, dr + 3 * (size_t)d0, nd, E, nrhs, k, Fo + (size_t)d0 * 3, rcs ? rcs + d0 : nullptr, ndir);
+        EMS_CUDA(cudaGetLastError());
+    }
+    EMS_CUDA(cudaStreamSynchronize(st));
+    return EMSURF_OK;
+}
+
 }  // namespace
 }  // namespace emsurf
 
@@ -293,46 +430,8 @@ EMSURF_API int emsurf_far_field(emsurf_handle* h, double a, double b, double hgt
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     std::vector<RwgQuad> q;
     EMS_TRY(box_quadrature(a, b, hgt, n, zlevels, h->E, q));
-    const int E = h->E, K = h->K;
-    // directions in chunks so the per-chunk work arrays stay under ~512 MB
-    const size_t per_dir = (size_t)E * 3 * sizeof(double2) + (size_t)nrhs * K * sizeof(double2);
-    const int chunk = (int)std::max<size_t>(1, std::min<size_t>(ndir, (512ull << 20) / per_dir));
-    Scoped sc;
-    RwgQuad* dq;
-    double* dr;
-    double2 *Rv, *S;
-    EMS_TRY(to_device(&dq, q.data(), q.size(), st));
-    sc.p.push_back(dq);
-    EMS_TRY(to_device(&dr, rhat, 3 * (size_t)ndir, st));
-    sc.p.push_back(dr);
-    EMS_CUDA(cudaMalloc(&Rv, sizeof(double2) * (size_t)chunk * E * 3));
-    sc.p.push_back(Rv);
-    EMS_CUDA(cudaMalloc(&S, sizeof(double2) * (size_t)chunk * nrhs * K));
-    sc.p.push_back(S);
-    double2* Fo = reinterpret_cast<double2*>(F);
-    std::vector<double2> hbuf;
-    for (int d0 = 0; d0 < ndir; d0 += chunk) {
-        const int nd = std::min(chunk, ndir - d0);
-        const size_t t1 = (size_t)nd * E;
-        radiation_kernel<<<(int)std::min<size_t>((t1 + 127) / 128, 152 * 32), 128, 0, st>>>(
-            dq, E, dr + 3 * (size_t)d0, nd, k, Rv);
-        EMS_CUDA(cudaGetLastError());
-        const size_t t2 = (size_t)nrhs * nd * K;
-        lattice_sum_kernel<<<(int)std::min<size_t>((t2 + 255) / 256, 152 * 32), 256, 0, st>>>(
-            reinterpret_cast<const double2*>(Y), h->d_uo_index, h->d_uo_sign, h->nx, h->M, K,
-            h->n_unique, a, b, dr + 3 * (size_t)d0, nd, nrhs, k, S);
-        EMS_CUDA(cudaGetLastError());
-        // F chunk is written per rhs into [nrhs][ndir][3]
-        for (int r = 0; r < nrhs; ++r) {
-            const size_t t3 = (size_t)nd;
-            far_field_kernel<<<(int)std::min<size_t>((t3 + 127) / 128, 152 * 32), 128, 0, st>>>(
-                S + (size_t)r * nd * K, Rv, dr + 3 * (size_t)d0, nd, E, 1, k,
-                Fo + ((size_t)r * ndir + d0) * 3, rcs ? rcs + (size_t)r * ndir + d0 : nullptr);
-            EMS_CUDA(cudaGetLastError());
-        }
-    }
-    EMS_CUDA(cudaStreamSynchronize(st));
-    return EMSURF_OK;
+    if (h->precision == EMSURF_FP64) return far_field_run<double, double2>(h, q, a, b, k, Y, nrhs, ndir, rhat, F, rcs, st);
+    return far_field_run<float, float2>(h, q, a, b, k, Y, nrhs, ndir, rhat, F, rcs, st);
 }
 
 }  // extern "C"
