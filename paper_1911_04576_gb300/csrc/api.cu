@@ -308,6 +308,8 @@ int clear_wait_error(emsurf_handle* h) {
     EMS_CUDA(cudaDeviceSynchronize());
     EMS_CUDA(cudaMemset(h->d_err, 0, sizeof(int)));
     if (h->d_pair_cnt) EMS_CUDA(cudaMemset(h->d_pair_cnt, 0, h->pair_cnt_bytes));
+    if (h->d_ds_max) EMS_CUDA(cudaMemset(h->d_ds_max, 0, sizeof(unsigned long long) * std::max(1, h->max_rhs)));
+    if (h->d_ds_cnt) EMS_CUDA(cudaMemset(h->d_ds_cnt, 0, sizeof(unsigned) * std::max(1, h->max_rhs)));
     if (h->d_grid_bar) EMS_CUDA(cudaMemset(h->d_grid_bar, 0, 2 * sizeof(unsigned)));
     return EMSURF_OK;
 }

@@ -222,6 +222,8 @@ struct emsurf_handle {
     // product (from max |x_r|); the kernels divide their FP64 outputs back
     double* d_ds_scale = nullptr;
     double h_ds_scale0 = 1.0;         // the spectrum planes' scale (host copy)
+    unsigned long long* d_ds_max = nullptr;   // per-rhs running maxima of the scale kernel (kept at 0)
+    unsigned* d_ds_cnt = nullptr;             // its per-rhs block arrival counters (kept at 0)
     int pair_grid = 0;                // CTAs of the pair kernel (equal slab ranges)
     float2* d_pair_part = nullptr;    // partial row sums of straddling bins [cta][2][2E]
     int* d_pair_cnt = nullptr;        // arrival counters [stored bin][row warp]

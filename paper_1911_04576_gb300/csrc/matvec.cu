@@ -394,16 +394,23 @@ __global__ void split_hilo_kernel(float2* __restrict__ out, const double2* __res
     }
 }
 
-// scale[r] = 2^-e with 2^(e-1) <= max over the r-th block of |re|, |im| < 2^e
-// (1 when the block is zero or not finite): after it the block's largest
+// scale[r] = 2^-e with 2^(e-1) <= max over the r-th vector of |re|, |im| < 2^e
+// (1 when the vector is zero or not finite): after it the vector's largest
 // component lies in [0.5, 1), far from FP32 overflow, and FP32 subnormals only
-// touch parts below 2^-100 of the largest.  One CTA per block of `len` values.
+// touch parts below 2^-100 of the largest.  Grid (blocks, R): every block
+// folds its maximum into maxbits[r] (the bit patterns of non-negative doubles
+// order like the values); the last block of rhs r to arrive (arrival counter)
+// writes the scale and resets maxbits[r] and count[r] for the next product.
 __global__ void __launch_bounds__(256) pow2_scale_kernel(const double2* __restrict__ v, size_t len,
-                                                         double* __restrict__ scale) {
+                                                         unsigned long long* __restrict__ maxbits,
+                                                         unsigned* __restrict__ count, double* __restrict__ scale) {
     __shared__ double s_m[256];
-    const double2* b = v + (size_t)blockIdx.x * len;
+    __shared__ bool s_last;
+    const int r = blockIdx.y;
+    const double2* b = v + (size_t)r * len;
     double m = 0.0;
-    for (size_t e = threadIdx.x; e < len; e += blockDim.x) m = fmax(m, fmax(fabs(b[e].x), fabs(b[e].y)));
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < len; e += (size_t)gridDim.x * blockDim.x)
+        m = fmax(m, fmax(fabs(b[e].x), fabs(b[e].y)));
     s_m[threadIdx.x] = m;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -411,8 +418,16 @@ __global__ void __launch_bounds__(256) pow2_scale_kernel(const double2* __restri
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const double mx = s_m[0];
-        scale[blockIdx.x] = (mx > 0.0 && mx <= 1.7e308) ? ldexp(1.0, -(ilogb(mx) + 1)) : 1.0;
+        atomicMax(&maxbits[r], (unsigned long long)__double_as_longlong(s_m[0]));
+        __threadfence();
+        s_last = atomicAdd(&count[r], 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        const double mx = __longlong_as_double((long long)atomicExch(&maxbits[r], 0ull));
+        count[r] = 0u;
+        scale[r] = (mx > 0.0 && mx <= 1.7e308) ? ldexp(1.0, -(ilogb(mx) + 1)) : 1.0;
     }
 }
 
@@ -1439,6 +1454,10 @@ int build_ds_planes(emsurf_handle* h, const emsurf_handle* share) {
     else EMS_TRY(dev_alloc(h, (void**)&h->ds_planes, pbytes));
     EMS_TRY(dev_alloc(h, (void**)&h->ds_x, xbytes));
     EMS_TRY(dev_alloc(h, (void**)&h->d_ds_scale, sizeof(double) * (2 + std::max(1, h->max_rhs))));
+    EMS_TRY(dev_alloc(h, (void**)&h->d_ds_max, sizeof(unsigned long long) * std::max(1, h->max_rhs)));
+    EMS_TRY(dev_alloc(h, (void**)&h->d_ds_cnt, sizeof(unsigned) * std::max(1, h->max_rhs)));
+    EMS_CUDA(cudaMemsetAsync(h->d_ds_max, 0, sizeof(unsigned long long) * std::max(1, h->max_rhs), h->setup_stream));
+    EMS_CUDA(cudaMemsetAsync(h->d_ds_cnt, 0, sizeof(unsigned) * std::max(1, h->max_rhs), h->setup_stream));
     // operator scales: the largest component of the spectrum (of the
     // macromodels) maps into [0.5, 1), exactly (powers of two)
     const size_t KK = (size_t)h->K * h->K;
@@ -1512,7 +1531,9 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
     if constexpr (std::is_same<T2, double2>::value) {
         if (h->ds_planes && x) {
             // per-rhs powers of two for the double-single operands of this product
-            pow2_scale_kernel<<<R, 256, 0, st>>>(x, (size_t)h->n_unique, h->d_ds_scale + 2);
+            const int nbl = (int)std::min<size_t>(((size_t)h->n_unique + 1023) / 1024, (size_t)h->num_sms);
+            pow2_scale_kernel<<<dim3(nbl, R), 256, 0, st>>>(x, (size_t)h->n_unique, h->d_ds_max, h->d_ds_cnt,
+                                                            h->d_ds_scale + 2);
             EMS_CUDA(cudaGetLastError());
             h->launches += 1;
         }
