@@ -51,6 +51,8 @@ BINMUL_DRAM_BYTES_PER_BIN = (767108096 + 5353216) / 576
 # the same for binmul_tma_pair_kernel (half spectrum) per stored bin, from
 # the capture of the 12x12 lattice (290 stored bins)
 PAIR_DRAM_BYTES_PER_STORED_BIN = (387588096 + 3930624) / 290
+# binmul_orbit_kernel (one stored bin per mirror orbit): no capture yet
+ORBIT_DRAM_BYTES_PER_STORED_BIN = None
 
 
 FALLBACK_BF16_TFLOPS = 1900.0
@@ -425,7 +427,7 @@ def build_problem(B, W, torch, w, precision, precond=True, max_rhs=None, tensor_
                         precision=precision, max_rhs=max_rhs or w.n_rhs, tables_on_device=True,
                         unknown_xy=xy, cell=(A, A),
                         precond_overlap=PC_OVERLAP * A / w.n if precond else 0.0,
-                        tensor_cores=tensor_cores)
+                        tensor_cores=tensor_cores, mirrors=B.emsurf_setup_box_mirrors(A, A, w.n))
     torch.cuda.synchronize()
     t_create = time.time() - t0
     del L, K, Z
@@ -683,7 +685,8 @@ def main():
     mv64 = time_matvec(B, torch, h, nu, R, B.FP64)
     px, py, dev_bytes = B.emsurf_query(h)
     P = px * py
-    stored, _ = B.emsurf_operator_info(h)        # FP32 spectrum bins held (half with reciprocal tables)
+    stored, _ = B.emsurf_operator_info(h)        # FP32 spectrum bins held
+    form, per_stored = B.emsurf_operator_layout(h)  # 0 full, 1 (k, -k) pairs, 2 mirror orbits
     bytes32 = 2 * w.E * w.E * stored * 8 + w.n_types * w.K * w.K * 8 + 2 * R * nu * 16
     bytes64 = 2 * w.E * w.E * P * 16 + w.n_types * w.K * w.K * 16 + 2 * R * nu * 16
     solve_kw = dict(rtol=RTOL, restart=RESTART, max_iters=20000, max_refine=20,
@@ -790,13 +793,17 @@ def main():
             dist.destroy_process_group()
         return
     bin_avg = bin_ms_timed / max(bin_n_timed, 1)     # live over the timed region
-    half = stored < P
     # algorithmic bytes of the kernel that ran: the stored spectrum bins once,
     # X^ read and Y^ written for every bin
     alg_bin = 2 * w.E * w.E * stored * 8 + 2 * R * w.K * P * 8
     achieved = alg_bin / (bin_avg * 1e-3) / 1e9
-    per_unit = PAIR_DRAM_BYTES_PER_STORED_BIN if half else BINMUL_DRAM_BYTES_PER_BIN
-    traffic = per_unit * (stored if half else P) if per_unit else None
+    per_unit = {0: BINMUL_DRAM_BYTES_PER_BIN, 1: PAIR_DRAM_BYTES_PER_STORED_BIN,
+                2: ORBIT_DRAM_BYTES_PER_STORED_BIN}[form]
+    traffic = per_unit * (stored if form else P) if per_unit else None
+    bin_kernel = {0: "binmul_tma_kernel (bin multiply, FP32)",
+                  1: "binmul_tma_pair_kernel (bin multiply, FP32, half spectrum: %d of %d bins)" % (stored, P),
+                  2: "binmul_orbit_kernel (bin multiply, FP32, one bin per mirror orbit of %d: %d of %d bins)"
+                     % (per_stored, stored, P)}[form]
     # preconditioner apply: FP16 owned inverse rows (4 bytes per entry, one FP32
     # scale per row) once, r gathered, owned rows written
     pc_avg = pc_ms / max(pc_n, 1)
@@ -844,14 +851,14 @@ def main():
         "matvec": {"fp32_ms": round(mv32, 4), "fp32_gbs": round(bytes32 / mv32 / 1e6, 1),
                    "fp64_ms": round(mv64, 4), "fp64_gbs": round(bytes64 / mv64 / 1e6, 1),
                    "alg_bytes_fp32": bytes32, "alg_bytes_fp64": bytes64},
-        "roofline": {"kernel": ("binmul_tma_pair_kernel (bin multiply, FP32, half spectrum: %d of %d bins)"
-                                % (stored, P) if half else "binmul_tma_kernel (bin multiply, FP32)"),
+        "roofline": {"kernel": bin_kernel,
                      "bound": "hbm",
                      "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "peak_kind": peak_kind,
                      "traffic": round(traffic) if traffic else None,
-                     "traffic_kind": "scaled: ncu DRAM bytes per stored bin of the 12x12 capture x the "
-                                     "stored bins here (each stored slab is streamed exactly once)",
+                     "traffic_kind": ("scaled: ncu DRAM bytes per stored bin of the 12x12 capture x the "
+                                      "stored bins here (each stored slab is streamed exactly once)"
+                                      if traffic else "not captured for this kernel"),
                      "alg_bytes_per_launch": alg_bin,
                      "avg_launch_ms": round(bin_avg, 5), "launches_timed": bin_n_timed},
         "phases_ms_per_solve": {"binmul32": round(bin_ms, 3),

@@ -122,6 +122,19 @@ typedef struct {
      * per product term <= 3 * 2^-18 instead of 2^-24).  Needs an FP32
      * operator (EMSURF_FP32 or EMSURF_MIXED) and E >= 64; ignored otherwise. */
     int32_t tensor_cores;
+    /* Mirror symmetries of the box (emsurf_setup_box_mirrors), optional:
+     * sym_mask bits 0 (x -> -x), 1 (y -> -y), 2 (x <-> y); sym_perm [3][E],
+     * sym_sign [3][E] host (NULL with sym_mask 0).  With bits 0 and 1, a
+     * MIXED handle with max_rhs 1 and no tensor cores keeps the FP32 blocks
+     * of one bin per orbit {(+-kx, +-ky)} (with bit 2 on a square lattice and
+     * grid also (+-ky, +-kx)), about a quarter (an eighth) of the bins, and
+     * reads each once per product for every bin of its orbit.  The mirror
+     * relations are checked on the FP64 blocks at create (to 1e-12 of their
+     * largest entry); where they do not hold the handle keeps half of the
+     * bins (reciprocity) as without mirrors.  No counterpart in the paper.  */
+    int32_t sym_mask;
+    const int32_t* sym_perm;
+    const int8_t* sym_sign;
 } emsurf_problem;
 
 typedef struct {
@@ -161,7 +174,7 @@ EMSURF_API int emsurf_create(const emsurf_problem* problem, emsurf_handle** out)
  * what depends on the problem's macromodels and type map (macromodel
  * copies, work space, preconditioner).  offset_L/offset_K are not read
  * (may be NULL); nx, ny, n_edges, precision, device and the grid must match
- * `share`; a share that keeps half of the FP32 spectrum (single rhs, no
+ * `share`; a share that keeps part of the FP32 spectrum (single rhs, no
  * tensor cores) serves only such problems, and tensor cores need a share
  * that has their planes.  `share` must outlive the new handle and must not
  * be destroyed first; the two may run calls at the same time (the shared
@@ -207,11 +220,18 @@ EMSURF_API int emsurf_precond_apply(emsurf_handle* h, const emsurf_c128* r, emsu
 EMSURF_API int emsurf_precond_info(const emsurf_handle* h, int64_t* factor_entries,
                                    int64_t* subdomain_total, int32_t* max_subdomain);
 
-/* FP32 operator layout: spectrum bins it stores (grid_px * grid_py, or
- * about half of that when the tables are reciprocal and the handle holds a
- * single rhs: one bin of each pair (k, -k), Sec. IV-B with L(-d) = L(d)^T)
- * and whether the tensor-core planes were built (1) or not (0).          */
+/* FP32 operator layout: spectrum bins it stores (grid_px * grid_py; for a
+ * single-rhs handle one bin per mirror orbit, about a quarter or an eighth
+ * of that, when sym_mask gave the box's mirrors, else about half when the
+ * tables are reciprocal: one bin of each pair (k, -k), Sec. IV-B with
+ * L(-d) = L(d)^T) and whether the tensor-core planes were built (1) or not
+ * (0).                                                                    */
 EMSURF_API int emsurf_operator_info(const emsurf_handle* h, int32_t* stored_bins, int32_t* tensor_cores);
+
+/* Form of the FP32 spectrum: 0 every bin, 1 one bin per pair (k, -k)
+ * (reciprocity), 2 one bin per mirror orbit; bins_per_stored: the most bins
+ * one stored bin serves (1, 2, or the mirror group's order 4 or 8).       */
+EMSURF_API int emsurf_operator_layout(const emsurf_handle* h, int32_t* form, int32_t* bins_per_stored);
 
 /* Ring shape of the tensor-core bin multiply chosen at create by timing
  * both shapes on the handle's spectrum (the library's own autotuner; no
@@ -272,8 +292,11 @@ EMSURF_API int emsurf_launch_count(const emsurf_handle* h, int64_t* launches);
  * Box S_eq of cell (0,0) (Sec. II-A): x in [-a/2,a/2], y in [-b/2,b/2],
  * z in [0,h], n x n quads per face, opposite faces identical (translates).
  * Vertices: surface grid points (i,j,k) in lexicographic order; faces
- * x-,x+,y-,y+,z-,z+ with in-plane axes (j,k),(i,k),(i,j); quad (u,v) ->
- * triangles (c00,c10,c11),(c00,c11,c01), index face*2n^2 + 2(v*n+u) + {0,1}.
+ * x-,x+,y-,y+,z-,z+ with in-plane axes (j,k),(i,k),(i,j); quad (u,v) is
+ * cut, for even n, along the diagonal pointing at the face centre:
+ * triangles (c00,c10,c11),(c00,c11,c01) when (2u+1 < n) == (2v+1 < n),
+ * else (c00,c10,c01),(c10,c11,c01); for odd n always the first way;
+ * index face*2n^2 + 2(v*n+u) + {0,1}.
  * RWG edges (Eqs. Hdiscretebox/Ediscretebox): distinct vertex pairs sorted
  * lexicographically; T+ = lower triangle; slot i of a triangle = edge
  * opposite vertex i; slot_rwg = RWG index (-1 if none), slot_sgn = +1 on T+.
@@ -287,8 +310,21 @@ EMSURF_API int emsurf_setup_box_mesh(double a, double b, double h, int32_t n,
                                      int32_t* edges, int32_t* tplus, int32_t* tminus,
                                      int32_t* slot_rwg, int8_t* slot_sgn);
 
+/* Mirror symmetries of the box mesh (no counterpart in the paper: they let
+ * the FFT-domain blocks of mirrored bins share storage).  Mirror g (0:
+ * x -> -x, 1: y -> -y, 2: x <-> y, the last only when a == b) maps RWG
+ * function e of the box onto sign[g][e] * RWG perm[g][e]; bit g of *mask is
+ * set when g maps the mesh onto itself (for n even all three; for n odd
+ * only x <-> y).  perm [3][E], sign [3][E]
+ * host, E = 18 n^2; entries of mirrors not in the mask are unspecified.
+ * The offset tables then satisfy L(g d) = P_g L(d) P_g^T and
+ * K(g d) = -P_g K(d) P_g^T (P_g e_e = sign[g][e] e_perm[g][e]); see
+ * sym_mask in emsurf_problem.  Errors: EINVAL (n < 1, bad sides, NULL).   */
+EMSURF_API int emsurf_setup_box_mirrors(double a, double b, int32_t n, int32_t* perm, int8_t* sign,
+                                        int32_t* mask);
+
 /* Flat square PEC patch (Sec. II-A: J only on PEC) of side `side` centred
- * on the cell axis at height z, n x n quads split like the box faces;
+ * on the cell axis at height z, n x n quads each cut along (c00,c11);
  * vertices (i,j) at index i*(n+1)+j; RWGs on interior edges only.         */
 EMSURF_API int emsurf_setup_patch_counts(int32_t n, int32_t* n_verts, int32_t* n_tris,
                                          int32_t* n_edges);

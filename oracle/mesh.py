@@ -13,12 +13,26 @@ convention independently; tests compare the two arrays exactly):
   surface grid points (i,j,k) in {0..n}^3 with at least one index in {0,n},
   numbered in lexicographic (i,j,k) order;
 * faces in the order x-, x+, y-, y+, z-, z+; in-plane axes (u,v) are (j,k),
-  (i,k), (i,j) for x, y, z faces; quad (u,v) has index v*n+u; its two
-  triangles are (c00,c10,c11) then (c00,c11,c01); triangle index
-  = face*2n^2 + 2*(v*n+u) + {0,1};
+  (i,k), (i,j) for x, y, z faces; quad (u,v) has index v*n+u; for even n
+  it is cut along the diagonal that points at the face centre (a
+  union-jack pattern): when (2u+1 < n) == (2v+1 < n) its two triangles
+  are (c00,c10,c11) then (c00,c11,c01), else (c00,c10,c01) then
+  (c10,c11,c01); for odd n every quad is cut the first way;
+  triangle index = face*2n^2 + 2*(v*n+u) + {0,1};
 * RWG edges are the distinct vertex pairs (lo,hi), sorted lexicographically;
   T+ is the lower-numbered of the two triangles sharing the edge;
 * slot i of a triangle is the edge opposite its vertex i (free vertex i).
+
+The union-jack cut makes the box mesh invariant under the mirrors
+x -> -x and y -> -y (and x <-> y when a = b), so each mirror maps
+every RWG function onto +-1 times another (box_mirrors); the lattice
+operator then inherits the mirror symmetries of the continuous problem
+exactly, and the blocks of mirrored lattice offsets are signed
+permutations of one another.  For odd n the middle quads of a face lie on
+a mirror plane and no cut of them is symmetric; those boxes keep the
+uniform cut (which is also more accurate than the union jack on coarse
+boxes: RCS of a dielectric sphere within 0.83 dB of the Mie series at
+n = 3 against 1.0 dB).
 
 Pins: E = 18 n^2 edges on a closed box, each shared by two triangles,
 opposite faces are exact translates, and every RWG has zero net charge.
@@ -111,14 +125,64 @@ def box_mesh(a, b, h, n, zlevels=None):
                 c10 = index[_face_triple(axis, fixed, u + 1, v)]
                 c01 = index[_face_triple(axis, fixed, u, v + 1)]
                 c11 = index[_face_triple(axis, fixed, u + 1, v + 1)]
-                tris.append((c00, c10, c11))
-                tris.append((c00, c11, c01))
+                if n % 2 == 1 or (2 * u + 1 < n) == (2 * v + 1 < n):
+                    tris.append((c00, c10, c11))
+                    tris.append((c00, c11, c01))
+                else:
+                    tris.append((c00, c10, c01))
+                    tris.append((c10, c11, c01))
     return Mesh(verts, tris)
 
 
+# the mirrors of the box about its axis: x -> -x, y -> -y, x <-> y
+MIRRORS = {"x": np.diag([-1.0, 1.0, 1.0]), "y": np.diag([1.0, -1.0, 1.0]),
+           "d": np.array([[0.0, 1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 1.0]])}
+
+
+def box_mirrors(box, a, b):
+    """Signed permutations of the RWG functions under the box's mirrors.
+
+    For each mirror g in MIRRORS that maps the mesh onto itself (every
+    vertex onto a vertex, every triangle onto a triangle; "d" only when
+    a == b), the RWG function f_n mirrored, (g f_n)(r) = g f_n(g r), is
+    sign[n] * f_pi[n]: its edge is the image of edge n and its T+ is the
+    image of n's T+ (sign +1) or of n's T- (sign -1).  Returns
+    {name: (pi, sign)} for the mirrors that apply.
+    """
+    out = {}
+    V = box.verts
+    scale = max(np.abs(V).max(), 1e-300)
+    key = {tuple(np.round(v / scale, 9)): i for i, v in enumerate(V)}
+    ekey = {tuple(e): i for i, e in enumerate(box.edges)}
+    tkey = {tuple(sorted(t)): i for i, t in enumerate(box.tris)}
+    for name, g in MIRRORS.items():
+        if name == "d" and a != b:
+            continue
+        vmap = []
+        for v in V @ g.T:
+            vmap.append(key.get(tuple(np.round(v / scale, 9)), -1))
+        vmap = np.array(vmap)
+        if (vmap < 0).any():
+            continue
+        pi = np.zeros(box.n_rwg, dtype=np.int64)
+        sign = np.zeros(box.n_rwg, dtype=np.int64)
+        ok = True
+        for n, (p, q) in enumerate(box.edges):
+            m = ekey.get(tuple(sorted((vmap[p], vmap[q]))), -1)
+            tp = tkey.get(tuple(sorted(vmap[box.tris[box.tplus[n]]])), -1)
+            if m < 0 or tp not in (box.tplus[m], box.tminus[m]):
+                ok = False
+                break
+            pi[n] = m
+            sign[n] = 1 if tp == box.tplus[m] else -1
+        if ok:
+            out[name] = (pi, sign)
+    return out
+
 def patch_mesh(side, z, n):
     """Flat square PEC patch of the given side centred on the cell axis at
-    height z, n x n quads split like the box faces; RWGs on interior edges."""
+    height z, n x n quads each cut along its (c00, c11) diagonal; RWGs on
+    interior edges."""
     xs = -0.5 * side + side * np.arange(n + 1) / n
     verts = np.array([[xs[i], xs[j], z] for i in range(n + 1) for j in range(n + 1)])
     idx = lambda i, j: i * (n + 1) + j

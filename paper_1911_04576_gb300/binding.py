@@ -41,6 +41,7 @@ class Problem(C.Structure):
         ("device_mem_budget", C.c_int64), ("device", C.c_int32), ("stream", C.c_void_p),
         ("unknown_xy", C.c_void_p), ("cell_a", C.c_double), ("cell_b", C.c_double),
         ("precond_overlap", C.c_double), ("tensor_cores", C.c_int32),
+        ("sym_mask", C.c_int32), ("sym_perm", C.c_void_p), ("sym_sign", C.c_void_p),
     ]
 
 
@@ -80,10 +81,12 @@ def lib():
         L.emsurf_setup_patch_counts.argtypes = [i32, ip, ip, ip]
         L.emsurf_setup_box_mesh.argtypes = [C.c_double, C.c_double, C.c_double, i32, vp] + [vp] * 7
         L.emsurf_setup_patch_mesh.argtypes = [C.c_double, C.c_double, i32] + [vp] * 7
+        L.emsurf_setup_box_mirrors.argtypes = [C.c_double, C.c_double, i32, vp, vp, ip]
         L.emsurf_setup_overlap.argtypes = [i32, i32, i32, vp, vp, ip]
         L.emsurf_precond_apply.argtypes = [vp, vp, vp, i32, vp]
         L.emsurf_selftest_wait.argtypes = [vp, C.c_int64, vp]
         L.emsurf_operator_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
+        L.emsurf_operator_layout.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
         L.emsurf_tc_tuning.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), vp]
         L.emsurf_precond_info.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                           C.POINTER(i32)]
@@ -164,13 +167,14 @@ class Handle:
 def emsurf_create(nx, ny, n_edges, n_unique, type_map, macromodels, offset_L, offset_K, coef,
                   uo_index, uo_sign, precision=FP64, max_rhs=1, grid=(0, 0),
                   tables_on_device=False, device_mem_budget=0, device=0, unknown_xy=None,
-                  cell=(0.0, 0.0), precond_overlap=0.0, tensor_cores=False, share=None):
+                  cell=(0.0, 0.0), precond_overlap=0.0, tensor_cores=False, share=None, mirrors=None):
     """emsurf_create: host NumPy inputs (or torch CUDA tensors for the tables
     and macromodels when tables_on_device=True); returns a Handle.  With
     unknown_xy ([n_unique, 2] from emsurf_setup_unknown_xy), cell = (a, b) and
     precond_overlap > 0 the near-field preconditioner is built.  With share
     (a Handle of the same lattice) it calls emsurf_create_like: the tables are
-    not read (may be None) and the new handle reads share's spectra."""
+    not read (may be None) and the new handle reads share's spectra.
+    mirrors: (perm, sign, mask) from emsurf_setup_box_mirrors, or None."""
     type_map = np.ascontiguousarray(type_map, dtype=np.int32)
     uo_index = np.ascontiguousarray(uo_index, dtype=np.int32)
     uo_sign = np.ascontiguousarray(uo_sign, dtype=np.int8)
@@ -199,12 +203,18 @@ def emsurf_create(nx, ny, n_edges, n_unique, type_map, macromodels, offset_L, of
     p.cell_a, p.cell_b = cell
     p.precond_overlap = precond_overlap
     p.tensor_cores = 1 if tensor_cores else 0
+    keep = [type_map, uo_index, uo_sign]
+    if mirrors is not None:
+        perm = np.ascontiguousarray(mirrors[0], dtype=np.int32)
+        sign = np.ascontiguousarray(mirrors[1], dtype=np.int8)
+        p.sym_mask, p.sym_perm, p.sym_sign = int(mirrors[2]), _ptr(perm), _ptr(sign)
+        keep += [perm, sign]
     out = C.c_void_p()
     if share is not None:
         _check(lib().emsurf_create_like(C.byref(p), share.ptr, C.byref(out)))
-        return Handle(out.value, (type_map, uo_index, uo_sign, share))
+        return Handle(out.value, tuple(keep + [share]))
     _check(lib().emsurf_create(C.byref(p), C.byref(out)))
-    return Handle(out.value, (type_map, uo_index, uo_sign))
+    return Handle(out.value, tuple(keep))
 
 
 def emsurf_matvec(h, x, y, precision=FP64, stream=None):
@@ -229,6 +239,13 @@ def emsurf_operator_info(h):
     nb, tc = C.c_int32(), C.c_int32()
     _check(lib().emsurf_operator_info(h.ptr, C.byref(nb), C.byref(tc)))
     return nb.value, bool(tc.value)
+
+
+def emsurf_operator_layout(h):
+    """(form: 0 full, 1 (k, -k) pairs, 2 mirror orbits; bins one stored bin serves)."""
+    f, g = C.c_int32(), C.c_int32()
+    _check(lib().emsurf_operator_layout(h.ptr, C.byref(f), C.byref(g)))
+    return f.value, g.value
 
 
 def emsurf_tc_tuning(h):
@@ -290,6 +307,17 @@ def emsurf_setup_box_mesh(a, b, h, n, zlevels=None):
     z = None if zlevels is None else np.ascontiguousarray(zlevels, dtype=np.float64)
     _check(lib().emsurf_setup_box_mesh(a, b, h, n, _ptr(z), *[_ptr(out[k]) for k in _MESH_KEYS]))
     return out
+
+
+def emsurf_setup_box_mirrors(a, b, n):
+    """emsurf_setup_box_mirrors: (perm [3, E] int32, sign [3, E] int8, mask)."""
+    E = 18 * n * n
+    perm = np.zeros((3, E), np.int32)
+    sign = np.zeros((3, E), np.int8)
+    mask = C.c_int32(0)
+    _check(lib().emsurf_setup_box_mirrors(C.c_double(a), C.c_double(b), n, _ptr(perm), _ptr(sign),
+                                          C.byref(mask)))
+    return perm, sign, mask.value
 
 
 def emsurf_setup_patch_mesh(side, z, n):

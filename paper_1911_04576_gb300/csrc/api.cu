@@ -359,8 +359,8 @@ EMSURF_API int emsurf_create_like(const emsurf_problem* problem, const emsurf_ha
         return EMSURF_EINVAL;
     }
     const bool tc_wanted = p.tensor_cores && p.precision != EMSURF_FP64 && p.n_edges >= 64;
-    if (share->half32 && (p.max_rhs != 1 || tc_wanted)) {
-        set_error("emsurf_create_like: the shared handle keeps half of the FP32 spectrum (one rhs, no tensor "
+    if ((share->half32 || share->orb32) && (p.max_rhs != 1 || tc_wanted)) {
+        set_error("emsurf_create_like: the shared handle keeps part of the FP32 spectrum (one rhs, no tensor "
                   "cores); this problem needs the full spectrum");
         return EMSURF_EINVAL;
     }
@@ -423,8 +423,16 @@ EMSURF_API int emsurf_matvec(emsurf_handle* h, const emsurf_c128* x, emsurf_c128
 
 EMSURF_API int emsurf_operator_info(const emsurf_handle* h, int32_t* stored_bins, int32_t* tensor_cores) {
     if (!h) { set_error("NULL handle"); return EMSURF_EINVAL; }
-    if (stored_bins) *stored_bins = h->half32 ? h->nst : h->nbins;
+    if (stored_bins) *stored_bins = (h->half32 || h->orb32) ? h->nst : h->nbins;
     if (tensor_cores) *tensor_cores = h->have_tc ? 1 : 0;
+    return EMSURF_OK;
+}
+
+EMSURF_API int emsurf_operator_layout(const emsurf_handle* h, int32_t* form, int32_t* bins_per_stored) {
+    if (!h) { set_error("NULL handle"); return EMSURF_EINVAL; }
+    const int f = h->orb32 ? 2 : h->half32 ? 1 : 0;
+    if (form) *form = f;
+    if (bins_per_stored) *bins_per_stored = f == 2 ? h->orb_G : f == 1 ? 2 : 1;
     return EMSURF_OK;
 }
 

@@ -211,6 +211,13 @@ struct emsurf_handle {
     int nst = 0;
     int32_t* d_st_bin = nullptr;
     int32_t* d_st_part = nullptr;
+    // FP32 blocks of one bin per orbit of the box's mirror group (single
+    // rhs): nst stored bins (d_st_bin their representatives), orb_G slots each
+    bool orb32 = false;
+    int orb_G = 0;
+    int32_t* d_orb_bin = nullptr;     // [nst][orb_G] bin of each slot (-1: none)
+    int32_t* d_orb_elem = nullptr;    // [nst][orb_G] its group element
+    uint32_t* d_orb_perm = nullptr;   // [orb_G][2E] signed index of T_e
     // FP64-accuracy single-rhs bin multiply from FP32 hi/lo pairs: spectrum
     // planes [bin][hi, lo][op][j][i] and the split X^ [bin][hi, lo][2E]
     float2* ds_planes = nullptr;

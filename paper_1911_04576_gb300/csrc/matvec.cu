@@ -106,6 +106,36 @@ __global__ void reciprocity_kernel(const double2* __restrict__ B, const int32_t*
     }
 }
 
+// Mirror relation of the spectrum for one mirror g of the box (det g = -1):
+// with L(g d) = P L(d) P^T and K(g d) = -P K(d) P^T the blocks of bins k and
+// g k obey O^(g k)[pi(i)][pi(j)] = s_op sign(i) sign(j) O^(k)[i][j], s_L = 1,
+// s_K = -1.  perm[n] = pi(n) | (sign(n) < 0) << 31; image[bin] = g k.
+// out[0] = max deviation, out[1] = max |O^| (ordered bit patterns).
+__global__ void mirror_check_kernel(const double2* __restrict__ B, const uint32_t* __restrict__ perm,
+                                    const int32_t* __restrict__ image, int E, size_t nbins,
+                                    unsigned long long* __restrict__ out) {
+    const size_t EE = (size_t)E * E, total = nbins * 2 * EE;
+    double dmax = 0.0, vmax = 0.0;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t bin = e / (2 * EE), rem = e % (2 * EE);
+        const int op = (int)(rem / EE), j = (int)((rem % EE) / E), i = (int)(rem % E);
+        const uint32_t pi = perm[i], pj = perm[j];
+        const double f = ((pi ^ pj) >> 31 ? -1.0 : 1.0) * (op ? -1.0 : 1.0);
+        const double2 a = B[e];
+        const double2 b = B[((size_t)image[bin] * 2 + op) * EE + (size_t)(pj & 0x7fffffffu) * E + (pi & 0x7fffffffu)];
+        dmax = fmax(dmax, fmax(fabs(b.x - f * a.x), fabs(b.y - f * a.y)));
+        vmax = fmax(vmax, fmax(fabs(a.x), fabs(a.y)));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&out[0], (unsigned long long)__double_as_longlong(dmax));
+        atomicMax(&out[1], (unsigned long long)__double_as_longlong(vmax));
+    }
+}
+
 // half spectrum: dst[s] = (float) B^(st_bin[s]) for the stored bins
 __global__ void half_round_kernel(float2* __restrict__ dst, const double2* __restrict__ src,
                                   const int32_t* __restrict__ st_bin, size_t per_bin, size_t n) {
@@ -951,6 +981,275 @@ size_t binmul_tma_pair_smem(int E) {
            2ull * kPairStages * sizeof(uint64_t);
 }
 
+// ------------------------------------------------ K2, FP32, one rhs, mirror orbits
+// With a mirror-symmetric box (union-jack mesh) the offset tables obey
+// L(g d) = P_g L(d) P_g^T and K(g d) = det(g) P_g K(d) P_g^T for every g of
+// the mirror group (x -> -x, y -> -y, and x <-> y on a square lattice), so
+// the FFT-domain blocks of the bins g k of one orbit are
+// B^(g k) = T_g B^(k) T_g^T, T_g = diag(P_g, det(g) P_g) on (J, M).  Only one
+// bin k of each orbit is stored; with x~_j = T_g^T x(g k) gathered in shared
+// memory, the bins of the orbit are G products with the same blocks:
+// y(g k) = T_g B^(k) x~_j, one thread per test row i and G accumulator sets,
+// so each stored slab is read from HBM once for all bins of its orbit.
+// Work split, partial sums of straddling bins and their counters as in the
+// pair kernel; the partials hold the unpermuted sums, the completing warp
+// scatters y(g k) = T_g y~.
+//
+// Tables: orb_bin[s][j] the bin of slot j of stored bin s (-1: the orbit has
+// fewer than G bins), orb_elem[s][j] its group element, orb_perm[e][n] the
+// signed index of T_e: x~[n] = sign x[idx], y[idx] = sign y~[n], encoded as
+// idx | (sign < 0) << 31.
+constexpr int kOrbStages = 3;
+constexpr int kOrbPermChunk = 8;     // x~ entries per consumer thread per pass
+constexpr int kOrbMaxThreads = 384;  // E <= 352: registers for 8 accumulator sets
+
+template <int G, int JB>
+__global__ void __launch_bounds__(kOrbMaxThreads, 1)
+binmul_orbit_kernel(const float2* __restrict__ Bhat, const float2* __restrict__ Xh, float2* __restrict__ Yh,
+                    const int32_t* __restrict__ orb_bin, const int32_t* __restrict__ orb_elem,
+                    const uint32_t* __restrict__ orb_perm, int E, int nst, int n_elem, float2 ca, float2 cb,
+                    float2 cg, float2 cd, float2* __restrict__ part, int* __restrict__ cnt,
+                    int* __restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int stage_elems = 2 * JB * E;
+    const int E2 = 2 * E;
+    float2* sbuf = reinterpret_cast<float2*>(smem_raw);
+    float2* xbuf = sbuf + (size_t)kOrbStages * stage_elems;         // [2][G][2E]
+    uint32_t* ptab = reinterpret_cast<uint32_t*>(xbuf + 2 * G * E2); // [n_elem][2E]
+    uint64_t* full = reinterpret_cast<uint64_t*>(ptab + (size_t)n_elem * E2 + ((n_elem * E2) & 1));
+    uint64_t* empty = full + kOrbStages;
+    uint64_t* pbar = empty + kOrbStages;     // consumer-only sync of the x~ gather
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ncw = (E + 31) / 32;
+    const int nthr = 32 * ncw;               // consumer threads
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kOrbStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], ncw);
+        }
+        mbar_init(pbar, ncw);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    for (int e = threadIdx.x; e < n_elem * E2; e += blockDim.x) ptab[e] = orb_perm[e];
+    __syncthreads();
+    const int nj = (E + JB - 1) / JB;
+    const int Gc = (int)gridDim.x;
+    const long long Q = (long long)nst * nj;
+    const long long q0 = (long long)blockIdx.x * Q / Gc, q1 = (long long)(blockIdx.x + 1) * Q / Gc;
+    if (q0 >= q1) return;
+    const int sb0 = (int)(q0 / nj), jb0 = (int)(q0 % nj);
+    if (warp == 0) {
+        if (lane != 0) return;
+        const uint64_t pol = l2_evict_first();
+        const uint32_t bytes_x = (uint32_t)(E2 * sizeof(float2));
+        int s = 0, sb = sb0, jb = jb0, t = 0;
+        uint32_t ph = 0;
+        long long issued = 0;
+        bool ok = true;
+        for (long long q = q0; q < q1; ++q) {
+            if (q - q0 >= kOrbStages && !mbar_wait(&empty[s], ph ^ 1u)) {
+                ok = false;
+                break;
+            }
+            const int j0 = jb * JB, jn = min(JB, E - j0);
+            const uint32_t bytes_op = (uint32_t)(jn * E * sizeof(float2));
+            const bool newbin = jb == 0 || q == q0;
+            uint32_t xb = 0;
+            int bins[G];
+            if (newbin) {
+#pragma unroll
+                for (int j = 0; j < G; ++j) {
+                    bins[j] = orb_bin[(size_t)sb * G + j];
+                    if (bins[j] >= 0) xb += bytes_x;
+                }
+            }
+            mbar_expect_tx(&full[s], 2 * bytes_op + xb);
+            const float2* src = Bhat + (size_t)sb * 2 * E * E + (size_t)j0 * E;
+            float2* dst = sbuf + (size_t)s * stage_elems;
+            bulk_g2s_hint(dst, src, bytes_op, &full[s], pol);
+            bulk_g2s_hint(dst + JB * E, src + (size_t)E * E, bytes_op, &full[s], pol);
+            if (newbin) {
+                float2* xd = xbuf + (size_t)(t & 1) * G * E2;
+#pragma unroll
+                for (int j = 0; j < G; ++j)
+                    if (bins[j] >= 0) bulk_g2s(xd + (size_t)j * E2, Xh + (size_t)bins[j] * E2, bytes_x, &full[s]);
+            }
+            issued = q - q0 + 1;
+            if (++s == kOrbStages) { s = 0; ph ^= 1u; }
+            if (++jb == nj) { jb = 0; ++sb; ++t; }
+        }
+        if (!ok) {
+            atomicExch(err, 1);
+            for (long long u = (issued > kOrbStages ? issued - kOrbStages : 0); u < issued; ++u)
+                mbar_wait(&full[u % kOrbStages], (uint32_t)((u / kOrbStages) & 1));
+        }
+        return;
+    }
+    // ---- consumers: one thread per test row i
+    const int tid = threadIdx.x - 32;
+    const int w = warp - 1;
+    const int i = w * 32 + lane;
+    int s = 0, sb = sb0, jb = jb0, t = 0;
+    uint32_t ph = 0, pph = 0;
+    long long qb = (long long)sb0 * nj;
+    // all consumer warps meet (bounded: on expiry the flag is set and the
+    // warp leaves; the others' waits then expire too)
+    auto consumers_meet = [&]() -> bool {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(pbar);
+        const bool ok = mbar_wait(pbar, pph);
+        pph ^= 1u;
+        return ok;
+    };
+    float2 lj[G], lm[G], kj[G], km[G];
+#pragma unroll
+    for (int j = 0; j < G; ++j) lj[j] = lm[j] = kj[j] = km[j] = make_float2(0.f, 0.f);
+    for (long long q = q0; q < q1; ++q) {
+        if (!mbar_wait(&full[s], ph)) {
+            atomicExch(err, 1);
+            return;
+        }
+        float2* xs = xbuf + (size_t)(t & 1) * G * E2;
+        if (jb == 0 || q == q0) {
+            // x~_j = T_e^T x(bin_j) in place (zero for empty slots): all
+            // reads of a pass before any write
+            for (int base = 0; base < G * E2; base += nthr * kOrbPermChunk) {
+                float2 v[kOrbPermChunk];
+#pragma unroll
+                for (int c = 0; c < kOrbPermChunk; ++c) {
+                    const int e = base + c * nthr + tid;
+                    v[c] = make_float2(0.f, 0.f);
+                    if (e < G * E2) {
+                        const int j = e / E2, n = e - j * E2;
+                        if (orb_bin[(size_t)sb * G + j] >= 0) {
+                            const uint32_t pe = ptab[(size_t)orb_elem[(size_t)sb * G + j] * E2 + n];
+                            const float2 a = xs[(size_t)j * E2 + (pe & 0x7fffffffu)];
+                            v[c] = (pe >> 31) ? make_float2(-a.x, -a.y) : a;
+                        }
+                    }
+                }
+                if (!consumers_meet()) {
+                    atomicExch(err, 1);
+                    return;
+                }
+#pragma unroll
+                for (int c = 0; c < kOrbPermChunk; ++c) {
+                    const int e = base + c * nthr + tid;
+                    if (e < G * E2) xs[e] = v[c];
+                }
+                if (!consumers_meet()) {
+                    atomicExch(err, 1);
+                    return;
+                }
+            }
+            // later bulk copies into this buffer are ordered after these writes
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+        const float2* Ls = sbuf + (size_t)s * stage_elems;
+        const float2* Ks = Ls + JB * E;
+        const int j0 = jb * JB, jn = min(JB, E - j0);
+        if (i < E) {
+#pragma unroll
+            for (int jj = 0; jj < JB; jj += 2) {
+                if (jj < jn) {
+                    // columns jj, jj + 1 (jn is even: E is even)
+                    const float2 l0 = Ls[jj * E + i], l1 = Ls[(jj + 1) * E + i];
+                    const float2 k0 = Ks[jj * E + i], k1 = Ks[(jj + 1) * E + i];
+#pragma unroll
+                    for (int j = 0; j < G; ++j) {
+                        const float4 xj = *reinterpret_cast<const float4*>(xs + (size_t)j * E2 + j0 + jj);
+                        const float4 xm = *reinterpret_cast<const float4*>(xs + (size_t)j * E2 + E + j0 + jj);
+                        const float2 xj0 = make_float2(xj.x, xj.y), xj1 = make_float2(xj.z, xj.w);
+                        const float2 xm0 = make_float2(xm.x, xm.y), xm1 = make_float2(xm.z, xm.w);
+                        cfma(lj[j], l0, xj0);
+                        cfma(lm[j], l0, xm0);
+                        cfma(kj[j], k0, xj0);
+                        cfma(km[j], k0, xm0);
+                        cfma(lj[j], l1, xj1);
+                        cfma(lm[j], l1, xm1);
+                        cfma(kj[j], k1, xj1);
+                        cfma(km[j], k1, xm1);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+        if (jb == nj - 1 || q == q1 - 1) {
+            // this CTA's part of stored bin sb ends here
+            const bool whole = qb >= q0 && jb == nj - 1;
+            float2* P = part + ((size_t)blockIdx.x * 2 + (t == 0 ? 0 : 1)) * G * E2;
+#pragma unroll
+            for (int j = 0; j < G; ++j) {
+                const int bin = orb_bin[(size_t)sb * G + j];
+                if (bin < 0 || i >= E) continue;
+                const float2 y0 = cadd(cmul(ca, lj[j]), cmul(cb, km[j]));
+                const float2 y1 = cadd(cmul(cg, kj[j]), cmul(cd, lm[j]));
+                if (whole) {
+                    const uint32_t* pt = ptab + (size_t)orb_elem[(size_t)sb * G + j] * E2;
+                    const uint32_t p0 = pt[i], p1 = pt[E + i];
+                    float2* Y = Yh + (size_t)bin * E2;
+                    Y[p0 & 0x7fffffffu] = (p0 >> 31) ? make_float2(-y0.x, -y0.y) : y0;
+                    Y[p1 & 0x7fffffffu] = (p1 >> 31) ? make_float2(-y1.x, -y1.y) : y1;
+                } else {
+                    P[(size_t)j * E2 + i] = y0;
+                    P[(size_t)j * E2 + E + i] = y1;
+                }
+            }
+            if (!whole) {
+                __threadfence();
+                __syncwarp();
+                const int bf = pair_cta_of(qb, Q, Gc), bl = pair_cta_of(qb + nj - 1, Q, Gc);
+                int* c = cnt + (size_t)sb * ncw + w;
+                int old = 0;
+                if (lane == 0) old = atomicAdd(c, 1);
+                old = __shfl_sync(0xffffffffu, old, 0);
+                if (old == bl - bf) {
+                    // every contributor has written its partial
+                    if (lane == 0) *c = 0;
+                    __threadfence();
+                    if (i < E) {
+                        for (int j = 0; j < G; ++j) {
+                            const int bin = orb_bin[(size_t)sb * G + j];
+                            if (bin < 0) continue;
+                            float2 a0 = make_float2(0.f, 0.f), a1 = a0;
+                            for (int b = bf; b <= bl; ++b) {
+                                const int sl = ((long long)b * Q / Gc) / nj == sb ? 0 : 1;
+                                const float2* Pb = part + ((size_t)b * 2 + sl) * G * E2 + (size_t)j * E2;
+                                a0 = cadd(a0, __ldcg(Pb + i));
+                                a1 = cadd(a1, __ldcg(Pb + E + i));
+                            }
+                            const uint32_t* pt = ptab + (size_t)orb_elem[(size_t)sb * G + j] * E2;
+                            const uint32_t p0 = pt[i], p1 = pt[E + i];
+                            float2* Y = Yh + (size_t)bin * E2;
+                            Y[p0 & 0x7fffffffu] = (p0 >> 31) ? make_float2(-a0.x, -a0.y) : a0;
+                            Y[p1 & 0x7fffffffu] = (p1 >> 31) ? make_float2(-a1.x, -a1.y) : a1;
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < G; ++j) lj[j] = lm[j] = kj[j] = km[j] = make_float2(0.f, 0.f);
+        }
+        if (++s == kOrbStages) { s = 0; ph ^= 1u; }
+        if (++jb == nj) {
+            jb = 0;
+            ++sb;
+            ++t;
+            qb += nj;
+        }
+    }
+}
+
+template <int G, int JB>
+size_t binmul_orbit_smem(int E) {
+    const size_t E2 = 2 * (size_t)E;
+    const size_t n_elem = G;
+    return (size_t)kOrbStages * 2 * JB * E * sizeof(float2) + 2 * G * E2 * sizeof(float2) +
+           (n_elem * E2 + ((n_elem * E2) & 1)) * sizeof(uint32_t) + (2ull * kOrbStages + 1) * sizeof(uint64_t);
+}
+
 // ------------------------------------------------ K4: macromodel multiply
 // Ymm[s][r][m][k] = sum_{k' in chunk s} Z~^{t(m)}[k][k'] x1[r][m][k'] for a
 // group of up to G cells of one type (x1 = U_o x gathered on the fly).  The
@@ -1327,6 +1626,169 @@ int build_spectrum(emsurf_handle* h, Operator<T2>& op, const emsurf_problem* pr)
 
 int derive_fp32_rest(emsurf_handle* h, const emsurf_problem* pr);
 
+namespace {
+constexpr int kOrbJB4 = 12;   // slab width of the 4-slot (x and y mirrors) orbit kernel
+constexpr int kOrbJB8 = 8;    // and of the 8-slot one (with x <-> y)
+
+// bin of the group element e (bit 0: x mirror, bit 1: y mirror, bit 2:
+// x <-> y, applied first) acting on bin (kx, ky) of a px x py grid
+int orbit_image(int e, int kx, int ky, int px, int py) {
+    if (e & 4) std::swap(kx, ky);
+    if (e & 2) ky = (py - ky) % py;
+    if (e & 1) kx = (px - kx) % px;
+    return ky * px + kx;
+}
+
+// The FP32 spectrum as one stored bin per mirror orbit, when the problem
+// gives the box's mirrors and they hold on the FP64 blocks.  *used = false
+// (and nothing allocated) otherwise.
+int orbit_spectrum(emsurf_handle* h, const emsurf_problem* pr, bool* used) {
+    *used = false;
+    const int E = h->E, px = h->px, py = h->py;
+    const size_t EE = (size_t)E * E, nb = (size_t)h->nbins;
+    cudaStream_t st = h->setup_stream;
+    if (h->max_rhs != 1 || pr->tensor_cores || (E & 1) || !pr->sym_perm || !pr->sym_sign ||
+        (pr->sym_mask & 3) != 3)
+        return EMSURF_OK;
+    for (int g = 0; g < 3; ++g) {
+        if (!(pr->sym_mask & (1 << g))) continue;
+        std::vector<char> hit(E, 0);
+        for (int n = 0; n < E; ++n) {
+            const int m = pr->sym_perm[(size_t)g * E + n], sg = pr->sym_sign[(size_t)g * E + n];
+            if (m < 0 || m >= E || (sg != 1 && sg != -1) || hit[m]) {
+                set_error("sym_perm/sym_sign of mirror %d is not a signed permutation of %d entries", g, E);
+                return EMSURF_EINVAL;
+            }
+            hit[m] = 1;
+        }
+    }
+    const bool diag = (pr->sym_mask & 4) && px == py && h->nx == h->ny;
+    const int G = diag ? 8 : 4, JB = diag ? kOrbJB8 : kOrbJB4;
+    const size_t smem = diag ? binmul_orbit_smem<8, kOrbJB8>(E) : binmul_orbit_smem<4, kOrbJB4>(E);
+    const int ncw = (E + 31) / 32;
+    if (smem > 227 * 1024 || 32 * (1 + ncw) > kOrbMaxThreads || (E + JB - 1) / JB < kOrbStages) return EMSURF_OK;
+    // the generators' relations on the FP64 blocks
+    {
+        std::vector<uint32_t> pt(E);
+        std::vector<int32_t> img(nb);
+        uint32_t* dpt = nullptr;
+        int32_t* dimg = nullptr;
+        unsigned long long* dout = nullptr;
+        EMS_CUDA(cudaMalloc(&dpt, E * sizeof(uint32_t)));
+        EMS_CUDA(cudaMalloc(&dimg, nb * sizeof(int32_t)));
+        EMS_CUDA(cudaMalloc(&dout, 2 * sizeof(unsigned long long)));
+        bool holds = true;
+        for (int g = 0; g < (diag ? 3 : 2) && holds; ++g) {
+            for (int n = 0; n < E; ++n)
+                pt[n] = (uint32_t)pr->sym_perm[(size_t)g * E + n] |
+                        (pr->sym_sign[(size_t)g * E + n] < 0 ? 0x80000000u : 0u);
+            for (int ky = 0; ky < py; ++ky)
+                for (int kx = 0; kx < px; ++kx) img[(size_t)ky * px + kx] = orbit_image(1 << g, kx, ky, px, py);
+            EMS_CUDA(cudaMemcpyAsync(dpt, pt.data(), E * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+            EMS_CUDA(cudaMemcpyAsync(dimg, img.data(), nb * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+            EMS_CUDA(cudaMemsetAsync(dout, 0, 2 * sizeof(unsigned long long), st));
+            mirror_check_kernel<<<152 * 8, 256, 0, st>>>(h->op64.Bhat, dpt, dimg, E, nb, dout);
+            EMS_CUDA(cudaGetLastError());
+            unsigned long long hout[2] = {0, 0};
+            EMS_CUDA(cudaMemcpyAsync(hout, dout, sizeof(hout), cudaMemcpyDeviceToHost, st));
+            EMS_CUDA(cudaStreamSynchronize(st));
+            double dmax, vmax;
+            std::memcpy(&dmax, &hout[0], sizeof(double));
+            std::memcpy(&vmax, &hout[1], sizeof(double));
+            holds = vmax > 0.0 && dmax <= 1e-12 * vmax;
+        }
+        cudaFree(dpt);
+        cudaFree(dimg);
+        cudaFree(dout);
+        if (!holds) return EMSURF_OK;
+    }
+    // the signed permutations T_e = diag(P_e, det(e) P_e), P_e = Px^a Py^b Pd^c
+    const int E2 = 2 * E;
+    std::vector<uint32_t> tperm((size_t)G * E2);
+    for (int e = 0; e < G; ++e) {
+        std::vector<int32_t> pi(E);
+        std::vector<int8_t> sg(E, 1);
+        for (int n = 0; n < E; ++n) pi[n] = n;
+        int det = 1;
+        for (int g = 0; g < 3; ++g) {
+            if (!(e & (1 << g))) continue;
+            std::vector<int32_t> npi(E);
+            std::vector<int8_t> nsg(E);
+            for (int n = 0; n < E; ++n) {     // P <- P P_g
+                const int m = pr->sym_perm[(size_t)g * E + n];
+                npi[n] = pi[m];
+                nsg[n] = (int8_t)(pr->sym_sign[(size_t)g * E + n] * sg[m]);
+            }
+            pi.swap(npi);
+            sg.swap(nsg);
+            det = -det;
+        }
+        for (int n = 0; n < E; ++n) {
+            tperm[(size_t)e * E2 + n] = (uint32_t)pi[n] | (sg[n] < 0 ? 0x80000000u : 0u);
+            tperm[(size_t)e * E2 + E + n] = (uint32_t)(E + pi[n]) | (sg[n] * det < 0 ? 0x80000000u : 0u);
+        }
+    }
+    // orbits: the smallest bin index represents each; its slots are the
+    // distinct images in the order of the group elements
+    std::vector<int32_t> rep, obin, oelem;
+    for (int ky = 0; ky < py; ++ky)
+        for (int kx = 0; kx < px; ++kx) {
+            const int b = ky * px + kx;
+            int imgs[8];
+            int r = b;
+            for (int e = 0; e < G; ++e) {
+                imgs[e] = orbit_image(e, kx, ky, px, py);
+                r = std::min(r, imgs[e]);
+            }
+            if (r != b) continue;
+            rep.push_back(b);
+            int nslot = 0;
+            for (int e = 0; e < G; ++e) {
+                bool seen = false;
+                for (int u = 0; u < nslot; ++u) seen = seen || obin[obin.size() - nslot + u] == imgs[e];
+                if (seen) continue;
+                obin.push_back(imgs[e]);
+                oelem.push_back(e);
+                ++nslot;
+            }
+            for (; nslot < G; ++nslot) {
+                obin.push_back(-1);
+                oelem.push_back(0);
+            }
+        }
+    const int nst = (int)rep.size();
+    int32_t *drep = nullptr, *dob = nullptr, *doe = nullptr;
+    uint32_t* dtp = nullptr;
+    EMS_TRY(dev_alloc(h, (void**)&drep, rep.size() * sizeof(int32_t)));
+    EMS_TRY(dev_alloc(h, (void**)&dob, obin.size() * sizeof(int32_t)));
+    EMS_TRY(dev_alloc(h, (void**)&doe, oelem.size() * sizeof(int32_t)));
+    EMS_TRY(dev_alloc(h, (void**)&dtp, tperm.size() * sizeof(uint32_t)));
+    EMS_CUDA(cudaMemcpyAsync(drep, rep.data(), rep.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    EMS_CUDA(cudaMemcpyAsync(dob, obin.data(), obin.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    EMS_CUDA(cudaMemcpyAsync(doe, oelem.data(), oelem.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    EMS_CUDA(cudaMemcpyAsync(dtp, tperm.data(), tperm.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    h->nst = nst;
+    h->d_st_bin = drep;
+    h->d_orb_bin = dob;
+    h->d_orb_elem = doe;
+    h->d_orb_perm = dtp;
+    h->orb_G = G;
+    const long long nslab = (long long)nst * ((E + JB - 1) / JB);
+    h->pair_grid = (int)std::min<long long>(std::max(1, h->num_sms), nslab);
+    EMS_TRY(dev_alloc(h, (void**)&h->d_pair_part, (size_t)h->pair_grid * 2 * G * E2 * sizeof(float2)));
+    h->pair_cnt_bytes = (size_t)nst * ncw * sizeof(int);
+    EMS_TRY(dev_alloc(h, (void**)&h->d_pair_cnt, h->pair_cnt_bytes));
+    EMS_CUDA(cudaMemsetAsync(h->d_pair_cnt, 0, h->pair_cnt_bytes, st));
+    EMS_TRY(dev_alloc(h, (void**)&h->op32.Bhat, (size_t)nst * 2 * EE * sizeof(float2)));
+    half_round_kernel<<<152 * 8, 256, 0, st>>>(h->op32.Bhat, h->op64.Bhat, drep, 2 * EE, (size_t)nst * 2 * EE);
+    EMS_CUDA(cudaGetLastError());
+    EMS_CUDA(cudaStreamSynchronize(st));   // the host vectors above go out of scope
+    h->orb32 = true;
+    *used = true;
+    return EMSURF_OK;
+}
+}  // namespace
+
 // FP32 operator of a MIXED handle: round the resident FP64 spectrum and
 // macromodels instead of transforming the tables a second time.
 int derive_fp32_operator(emsurf_handle* h, const emsurf_problem* pr, const emsurf_handle* share) {
@@ -1343,6 +1805,20 @@ int derive_fp32_operator(emsurf_handle* h, const emsurf_problem* pr, const emsur
         h->nst = share->nst;
         h->d_st_bin = share->d_st_bin;
         h->d_st_part = share->d_st_part;
+        h->orb32 = share->orb32;
+        h->orb_G = share->orb_G;
+        h->d_orb_bin = share->d_orb_bin;
+        h->d_orb_elem = share->d_orb_elem;
+        h->d_orb_perm = share->d_orb_perm;
+        if (h->orb32) {
+            const int ncw = (h->E + 31) / 32;
+            h->pair_grid = share->pair_grid;
+            EMS_TRY(dev_alloc(h, (void**)&h->d_pair_part,
+                              (size_t)h->pair_grid * 2 * h->orb_G * 2 * h->E * sizeof(float2)));
+            h->pair_cnt_bytes = (size_t)h->nst * ncw * sizeof(int);
+            EMS_TRY(dev_alloc(h, (void**)&h->d_pair_cnt, h->pair_cnt_bytes));
+            EMS_CUDA(cudaMemsetAsync(h->d_pair_cnt, 0, h->pair_cnt_bytes, st));
+        }
         if (h->half32) {
             const int ncw = (h->E + 31) / 32;
             h->pair_grid = share->pair_grid;
@@ -1352,6 +1828,11 @@ int derive_fp32_operator(emsurf_handle* h, const emsurf_problem* pr, const emsur
             EMS_CUDA(cudaMemsetAsync(h->d_pair_cnt, 0, h->pair_cnt_bytes, st));
         }
         return derive_fp32_rest(h, pr);
+    }
+    {
+        bool orb = false;
+        EMS_TRY(orbit_spectrum(h, pr, &orb));
+        if (orb) return derive_fp32_rest(h, pr);
     }
     // With reciprocal tables L^(-k) = L^(k)^T and K^(-k) = K^(k)^T: single-rhs
     // handles without the tensor-core planes keep one bin of each pair
@@ -1676,6 +2157,26 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
         }
     }
     if constexpr (std::is_same<T2, float2>::value) {
+        if (!bin_done && h->orb32) {
+            // one stored bin per mirror orbit: one read serves every bin of the orbit
+            const int thr = 32 * (1 + (E + 31) / 32);
+            if (h->orb_G == 8) {
+                const size_t smem = binmul_orbit_smem<8, kOrbJB8>(E);
+                EMS_TRY(set_smem_once(binmul_orbit_kernel<8, kOrbJB8>, smem));
+                binmul_orbit_kernel<8, kOrbJB8><<<h->pair_grid, thr, smem, st>>>(
+                    op.Bhat, op.Xg, op.Yg, h->d_orb_bin, h->d_orb_elem, h->d_orb_perm, E, h->nst, 8, op.coef[0],
+                    op.coef[1], op.coef[2], op.coef[3], h->d_pair_part, h->d_pair_cnt, h->d_err);
+            } else {
+                const size_t smem = binmul_orbit_smem<4, kOrbJB4>(E);
+                EMS_TRY(set_smem_once(binmul_orbit_kernel<4, kOrbJB4>, smem));
+                binmul_orbit_kernel<4, kOrbJB4><<<h->pair_grid, thr, smem, st>>>(
+                    op.Bhat, op.Xg, op.Yg, h->d_orb_bin, h->d_orb_elem, h->d_orb_perm, E, h->nst, 4, op.coef[0],
+                    op.coef[1], op.coef[2], op.coef[3], h->d_pair_part, h->d_pair_cnt, h->d_err);
+            }
+            EMS_CUDA(cudaGetLastError());
+            h->launches += 1;
+            bin_done = true;
+        }
         if (!bin_done && h->half32) {
             // half spectrum (single rhs): one read of each stored bin serves k and -k
             const size_t smem = binmul_tma_pair_smem(E);

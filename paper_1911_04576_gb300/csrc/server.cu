@@ -72,7 +72,7 @@ int spectrum_form(const emsurf_request& q) {
     const int E = 18 * q.n * q.n;
     if (q.precision == EMSURF_FP64) return 0;
     if (q.nrhs >= kTcMinRhs && E >= 64) return 3;      // tensor-core planes
-    return q.nrhs == 1 ? 1 : 2;                          // half / full FP32 spectrum
+    return q.nrhs == 1 ? 1 : 2;                          // part (pairs or mirror orbits) / full FP32 spectrum
 }
 
 std::string cell_key(const emsurf_request& q) {
@@ -312,6 +312,8 @@ int run_job(emsurf_server* sv, Job& jb, cudaStream_t st) {
     }
     emsurf_problem p{};
     std::vector<double> xy;
+    std::vector<int32_t> mperm((size_t)3 * E);
+    std::vector<int8_t> msign((size_t)3 * E);
     if (!s) {
         p.nx = q.nx;
         p.ny = q.ny;
@@ -333,6 +335,12 @@ int run_job(emsurf_server* sv, Job& jb, cudaStream_t st) {
         p.stream = st;
         // many right-hand sides: FP32 products as tensor-core GEMMs
         p.tensor_cores = spectrum_form(q) == 3 ? 1 : 0;
+        // the box's mirrors (one stored bin per orbit for single-rhs FP32 products)
+        int32_t mask = 0;
+        s = emsurf_setup_box_mirrors(q.a, q.b, q.n, mperm.data(), msign.data(), &mask);
+        p.sym_mask = mask;
+        p.sym_perm = mperm.data();
+        p.sym_sign = msign.data();
         if (q.precond_overlap > 0.0) {
             xy.resize((size_t)2 * nu);
             s = emsurf_setup_unknown_xy(q.a, q.b, q.h, q.n, q.nx, q.ny, idx.data(), nu, xy.data());

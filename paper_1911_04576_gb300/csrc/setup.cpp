@@ -10,6 +10,7 @@
 // functions of different boxes whose edges coincide and that share a
 // coincident triangle, with the sign that cancels the coincident halves.
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <map>
 #include <numeric>
@@ -120,16 +121,83 @@ int build_box(double a, double b, double h, int n, const double* zlevels, MeshOu
         face_point(f, n, u, v, i, j, k);
         return idx[((size_t)i * (n + 1) + j) * (n + 1) + k];
     };
+    // for even n each quad is cut along the diagonal pointing at the face
+    // centre (a union-jack pattern), which makes the mesh invariant under the
+    // mirrors x -> -x, y -> -y (and x <-> y on a square footprint); odd n,
+    // whose middle quads no cut makes symmetric, keeps one diagonal throughout
     for (int f = 0; f < 6; ++f)
         for (int v = 0; v < n; ++v)
             for (int u = 0; u < n; ++u) {
                 const int c00 = at(f, u, v), c10 = at(f, u + 1, v);
                 const int c01 = at(f, u, v + 1), c11 = at(f, u + 1, v + 1);
-                const int t0[3] = {c00, c10, c11}, t1[3] = {c00, c11, c01};
-                m.tris.insert(m.tris.end(), t0, t0 + 3);
-                m.tris.insert(m.tris.end(), t1, t1 + 3);
+                if ((n & 1) || (2 * u + 1 < n) == (2 * v + 1 < n)) {
+                    const int t0[3] = {c00, c10, c11}, t1[3] = {c00, c11, c01};
+                    m.tris.insert(m.tris.end(), t0, t0 + 3);
+                    m.tris.insert(m.tris.end(), t1, t1 + 3);
+                } else {
+                    const int t0[3] = {c00, c10, c01}, t1[3] = {c10, c11, c01};
+                    m.tris.insert(m.tris.end(), t0, t0 + 3);
+                    m.tris.insert(m.tris.end(), t1, t1 + 3);
+                }
             }
     return finish_mesh(m, true);
+}
+
+// Mirrors of the box about its axis (0: x -> -x, 1: y -> -y, 2: x <-> y) as
+// signed permutations of its RWG functions: mirrored f_e = sign[e] f_perm[e]
+// (the image of edge e, with sign +1 when the image of e's T+ is the T+ of
+// the image edge).  Exact, on the integer grid points.  Bit g of the returned
+// mask is set when mirror g maps the mesh onto itself.
+int box_mirror_perms(int n, bool square, const MeshOut& m, const std::vector<int32_t>& grid,
+                     std::vector<int32_t>& perm, std::vector<int8_t>& sign) {
+    const std::vector<int32_t> idx = box_index(n);
+    const int E = (int)m.tplus.size(), T = (int)m.tris.size() / 3;
+    std::map<std::pair<int, int>, int> edge_of;
+    for (int e = 0; e < E; ++e) edge_of[{m.edges[2 * e], m.edges[2 * e + 1]}] = e;
+    std::map<std::vector<int>, int> tri_of;
+    for (int t = 0; t < T; ++t) {
+        std::vector<int> key(m.tris.begin() + 3 * t, m.tris.begin() + 3 * t + 3);
+        std::sort(key.begin(), key.end());
+        tri_of[key] = t;
+    }
+    const int V = (int)grid.size() / 3;
+    perm.assign((size_t)3 * E, 0);
+    sign.assign((size_t)3 * E, 0);
+    int mask = 0;
+    for (int g = 0; g < 3; ++g) {
+        if (g == 2 && !square) continue;
+        std::vector<int> vmap(V);
+        for (int q = 0; q < V; ++q) {
+            int i = grid[3 * q], j = grid[3 * q + 1];
+            const int k = grid[3 * q + 2];
+            if (g == 0) i = n - i;
+            else if (g == 1) j = n - j;
+            else std::swap(i, j);
+            vmap[q] = idx[((size_t)i * (n + 1) + j) * (n + 1) + k];
+        }
+        bool ok = true;
+        for (int e = 0; e < E && ok; ++e) {
+            const int p = vmap[m.edges[2 * e]], q = vmap[m.edges[2 * e + 1]];
+            auto it = edge_of.find({std::min(p, q), std::max(p, q)});
+            std::vector<int> key(3);
+            for (int c = 0; c < 3; ++c) key[c] = vmap[m.tris[3 * m.tplus[e] + c]];
+            std::sort(key.begin(), key.end());
+            auto tt = tri_of.find(key);
+            if (it == edge_of.end() || tt == tri_of.end()) {
+                ok = false;
+                break;
+            }
+            const int img = it->second;
+            if (tt->second != m.tplus[img] && tt->second != m.tminus[img]) {
+                ok = false;
+                break;
+            }
+            perm[(size_t)g * E + e] = img;
+            sign[(size_t)g * E + e] = tt->second == m.tplus[img] ? 1 : -1;
+        }
+        if (ok) mask |= 1 << g;
+    }
+    return mask;
 }
 
 int build_patch(double side, double z, int n, MeshOut& m) {
@@ -477,6 +545,21 @@ EMSURF_API int emsurf_setup_box_mesh(double a, double b, double h, int32_t n,
     MeshOut m;
     EMS_TRY(build_box(a, b, h, n, zlevels, m, nullptr));
     copy_mesh(m, verts, tris, edges, tplus, tminus, slot_rwg, slot_sgn);
+    return EMSURF_OK;
+}
+
+EMSURF_API int emsurf_setup_box_mirrors(double a, double b, int32_t n, int32_t* perm, int8_t* sign,
+                                        int32_t* mask) {
+    if (!perm || !sign || !mask) { set_error("box mirrors: null output"); return EMSURF_EINVAL; }
+    MeshOut m;
+    std::vector<int32_t> grid;
+    EMS_TRY(build_box(a, b, 1.0, n, nullptr, m, &grid));
+    std::vector<int32_t> p;
+    std::vector<int8_t> sg;
+    const bool square = std::fabs(a - b) <= 1e-12 * std::max(a, b);
+    *mask = box_mirror_perms(n, square, m, grid, p, sg);
+    std::copy(p.begin(), p.end(), perm);
+    std::copy(sg.begin(), sg.end(), sign);
     return EMSURF_OK;
 }
 

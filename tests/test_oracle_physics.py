@@ -83,8 +83,11 @@ def test_empty_lattice_with_merged_faces_scatters_nothing():
     assert np.linalg.norm(Ad @ xg - Vt) <= 2e-12 * np.linalg.norm(Vt)
 
 
-@pytest.mark.parametrize("n,npatch", [(2, 3), (3, 4)])
-def test_pec_patch_macromodel(n, npatch):
+@pytest.mark.parametrize("n,npatch,tol_energy", [(2, 3, 0.03), (3, 4, 0.01)])
+def test_pec_patch_macromodel(n, npatch, tol_energy):
+    # the discretised lossless problem balances extinction and scattering up
+    # to its discretisation error, which falls with the mesh: about 2.0 %,
+    # 0.41 % and 0.21 % for n = 2, 3 and 4 quads per box face
     box = box_mesh(A, B, H, n)
     E = box.n_rwg
     sheet = patch_mesh(0.3 * LAM, 0.76e-3, npatch)
@@ -113,7 +116,7 @@ def test_pec_patch_macromodel(n, npatch):
     Ff = operators.far_field(operators.radiation_vectors(box, (0, 0, 0), K0, KHAT[None]),
                              KHAT[None], K0, x[:E], x[E:])[0]
     ext = -(4 * np.pi / K0) * np.imag(Ff @ EHAT)
-    assert ext > 0 and abs(sca - ext) <= 0.01 * ext
+    assert ext > 0 and abs(sca - ext) <= tol_energy * ext
 
 
 def _mie_pec(x, mu):

@@ -210,14 +210,15 @@ def test_lossy_dielectric_sphere_matches_mie_series():
     """Sphere of radius 3 mm (ka = 0.63), eps_r = 4 (1 - 0.2j) under e^{jwt}
     (m = sqrt(4 (1 + 0.2i)) in the e^{-iwt} convention of the series), at
     the centre of a box meshed n x n per face: the bistatic RCS in the E and
-    H planes at 7 angles within 1.5 dB (n = 2) and 1 dB (n = 3), on average
+    H planes at 7 angles within 1 dB (n = 3) and 0.75 dB (n = 4), on average
     closer on the finer box.  The E-plane angle of 90 degrees is the
-    dipole null and is left out."""
+    dipole null and is left out.  (The coarsest box, n = 2 with its
+    union-jack cut, misses by up to 2.8 dB: a discretisation error.)"""
     th = np.radians([0.0, 30.0, 60.0, 90.0, 120.0, 150.0, 180.0])
     eps = 4.0 * (1 - 0.2j)
     S1, S2 = _mie(K0 * 3.0e-3, np.sqrt(np.conj(eps)), np.cos(np.pi - th))
     res = []
-    for n in (2, 3):
+    for n in (3, 4):
         box, Zt = _sphere_cell(n, eps)
         x = _solve_cell(box, Zt)
         err = []
@@ -227,4 +228,4 @@ def test_lossy_dielectric_sphere_matches_mie_series():
             err.append(np.abs(10 * np.log10(sig / (4 * np.pi / K0 ** 2 * np.abs(S) ** 2))))
         e = np.concatenate([np.delete(err[0], 3), err[1]])
         res.append(e)
-    assert res[0].max() < 1.5 and res[1].max() < 1.0 and res[1].mean() < res[0].mean()
+    assert res[0].max() < 1.0 and res[1].max() < 0.75 and res[1].mean() < res[0].mean()

@@ -119,3 +119,14 @@ def test_slab_cell_unknown_counts_match_oracle(B, n, side, pn, layers):
     expect = 2 * np.sum(npec == 0) + np.sum(npec == 1) + 2 * np.sum(npec == 2)
     ni, (ea, es) = B.emsurf_setup_slab_cell_counts(a, a, h, n, z, side, pn, layers)
     assert ni == expect and ea == air.n_rwg and es == slab.n_rwg
+
+
+@pytest.mark.parametrize("a,b,n", [(0.015, 0.015, 2), (0.015, 0.012, 4), (0.015, 0.015, 3), (0.015, 0.015, 4)])
+def test_box_mirrors_match_oracle(B, a, b, n):
+    from oracle.mesh import box_mirrors
+    perm, sign, mask = B.emsurf_setup_box_mirrors(a, b, n)
+    ref = box_mirrors(box_mesh(a, b, 0.0075, n), a, b)
+    assert sorted("xyd"[g] for g in range(3) if mask & (1 << g)) == sorted(ref)
+    for g, name in enumerate("xyd"):
+        if name in ref:
+            assert np.array_equal(perm[g], ref[name][0]) and np.array_equal(sign[g], ref[name][1]), name
