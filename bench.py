@@ -475,18 +475,21 @@ def cpu_oracle_matvec_seconds(W, w, nu_expected):
 SERVE_SIZES = (8, 16, 24, 32, 64)   # lattice N x N of the serving stream
 SERVE_MESH = (3, 4)            # boxes meshed n x n: K = 324 or 576
 SERVE_RHS = tuple(range(1, 17))   # rhs per request, uniform in 1..16
-SERVE_RATE = 20.0              # Poisson arrivals per second
+SERVE_RATE = 1.0               # Poisson arrivals per second (default; --serve-rate)
+SERVE_MAX_MS = 20000.0         # wall-time limit of each request's solve
+SERVE_DRAIN_S = 30.0           # after the last arrival: queued requests are withdrawn
 SERVE_BUDGET = 80 << 30        # device-memory budget of the server
-SERVE_FP64_SAMPLE = 8         # requests of the one-at-a-time FP64 arm
+SERVE_FP64_SAMPLE = 6         # requests of the one-at-a-time FP64 arm
+SERVE_FP64_WINDOW_S = 45.0     # and its window (later requests are withdrawn)
 
 
-def serve_requests(B, W, nreq, seed, precision, precond):
+def serve_requests(B, W, nreq, seed, precision, precond, rate=SERVE_RATE):
     """The seeded stream: Poisson arrival times and the requests (lattice,
     mesh, rhs, type map, plane waves) drawn as the serving configuration
     says, cells from one 32-type patch-on-slab library."""
     rng = np.random.default_rng(seed)
     lib_sides = rng.uniform(0.15, 0.45, 32) * W.LAMBDA
-    arrivals = np.cumsum(rng.exponential(1.0 / SERVE_RATE, nreq))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, nreq))
     reqs = []
     for _ in range(nreq):
         N = int(rng.choice(SERVE_SIZES))
@@ -500,58 +503,89 @@ def serve_requests(B, W, nreq, seed, precision, precond):
                          patch_sides=lib_sides, patch_z=W.PATCH_Z, patch_n=4,
                          type_map=rng.integers(0, 32, N * N), khat=np.array([w_[0] for w_ in waves]),
                          ehat=np.array([w_[1] for w_ in waves]), precision=precision, rtol=RTOL,
-                         restart=RESTART, max_iters=20000, max_refine=20,
+                         restart=RESTART, max_iters=20000, max_refine=20, max_ms=SERVE_MAX_MS,
                          precond_overlap=PC_OVERLAP * W.PERIOD / n if precond else 0.0,
                          slab_t=W.SLAB_T, slab_eps=W.EPS_SLAB, ring_layers=W.RING_LAYERS))
     return arrivals, reqs
 
 
-def serve_stream(B, W, arrivals, reqs, max_active, cache):
-    """Submit the requests at their arrival times, wait for all; latency
-    percentiles over the admitted ones, throughput over the makespan."""
+def serve_stream(B, W, arrivals, reqs, max_active, cache, window_s):
+    """Submit the requests at their arrival times (those arriving within
+    window_s); when the window closes, withdraw the ones still queued and
+    collect the running ones (each solve is bounded by its max_ms).
+    Latency percentiles over the completed requests, throughput over the
+    makespan."""
     sv = B.emsurf_server_create(0, SERVE_BUDGET, max_active, cache=cache)
-    tickets, refused = [], 0
+    pending, res, refused, offered = [], [], 0, 0
+
+    def collect():
+        keep = []
+        for t in pending:
+            r = B.emsurf_poll(sv, t)
+            if r is None:
+                keep.append(t)
+            else:
+                res.append(r)
+        return keep
     t0 = time.perf_counter()
     for at, r in zip(arrivals, reqs):
+        if at > window_s:
+            break
         dt = t0 + at - time.perf_counter()
         if dt > 0:
             time.sleep(dt)
+        offered += 1
         q, keep = B.make_request(**r)
         try:
-            tickets.append(B.emsurf_submit(sv, q, keep))
+            pending.append(B.emsurf_submit(sv, q, keep))
         except B.EmsurfError as e:
             if e.status != B.EMSURF_EBUSY:
                 raise
             refused += 1
-    res = [B.emsurf_wait(sv, t, 3600 * 1000) for t in tickets]
+        pending = collect()
+    while pending and time.perf_counter() - t0 < window_s:
+        time.sleep(0.05)
+        pending = collect()
+    withdrawn = sum(1 for t in pending if B.emsurf_cancel(sv, t))
+    for t in pending:
+        r = B.emsurf_wait(sv, t, 3600 * 1000)
+        if r["status"] != B.EMSURF_ECANCELED:
+            res.append(r)
     makespan = time.perf_counter() - t0
     stats = B.emsurf_server_stats(sv)
     sv.close()
     lat = np.array([r["latency_ms"] for r in res]) if res else np.zeros(1)
     mean = lambda k: round(float(np.mean([r[k] for r in res])), 1) if res else None
-    return {"requests": len(reqs), "admitted": len(res), "refused_ebusy": refused,
-            "offered_rps": round(len(reqs) / max(float(arrivals[-1]), 1e-9), 2),
+    offered_span = float(arrivals[offered - 1]) if offered else 0.0
+    return {"offered": offered, "offered_rps": round(offered / max(offered_span, 1e-9), 2),
+            "completed": len(res), "refused_ebusy": refused, "withdrawn_at_window_end": withdrawn,
+            "converged": int(sum(r["status"] == B.EMSURF_OK for r in res)),
+            "stopped_at_max_ms": int(sum(r["status"] == B.EMSURF_ENOTCONV for r in res)),
             "throughput_rps": round(len(res) / makespan, 3), "makespan_s": round(makespan, 2),
+            "window_s": window_s,
             "p50_ms": round(float(np.percentile(lat, 50)), 1), "p99_ms": round(float(np.percentile(lat, 99)), 1),
             "mean_ms": round(float(lat.mean()), 1), "queue_ms_mean": mean("queue_ms"),
             "setup_ms_mean": mean("setup_ms"), "solve_ms_mean": mean("solve_ms"),
             "cache_hits": int(sum(r["cache_hit"] for r in res)),
             "cache": {"bytes": stats[0], "operators": stats[1], "libraries": stats[2], "evictions": stats[3]},
-            "all_converged": all(r["status"] == B.EMSURF_OK for r in res), "max_active": max_active}
+            "max_active": max_active}
 
 
-def serve_section(B, W, nreq):
-    arrivals, reqs = serve_requests(B, W, nreq, 7, B.MIXED, True)
-    out = {"stream": "Poisson %.0f/s; lattices %s, K %s, rhs %d..%d, 32-type patch-on-slab library; rtol %g; "
-                     "budget %d GB; near-field preconditioner; MIXED requests with >= 8 rhs use the "
-                     "tensor-core bin multiply" % (SERVE_RATE, list(SERVE_SIZES), [36 * m * m for m in SERVE_MESH],
-                                                  SERVE_RHS[0], SERVE_RHS[-1], RTOL, SERVE_BUDGET >> 30),
-           "mixed_batched_resident": serve_stream(B, W, arrivals, reqs, 4, True)}
+def serve_section(B, W, nreq, rate):
+    arrivals, reqs = serve_requests(B, W, nreq, 7, B.MIXED, True, rate)
+    window = float(arrivals[-1]) + SERVE_DRAIN_S
+    out = {"stream": "Poisson %.2f/s, %d requests; lattices %s, K %s, rhs %d..%d, 32-type patch-on-slab "
+                     "library; rtol %g; each solve limited to %.0f s; budget %d GB; near-field "
+                     "preconditioner; MIXED requests with >= 8 rhs use the tensor-core bin multiply; "
+                     "requests still queued %.0f s after the last arrival are withdrawn"
+                     % (rate, nreq, list(SERVE_SIZES), [36 * m * m for m in SERVE_MESH], SERVE_RHS[0],
+                        SERVE_RHS[-1], RTOL, SERVE_MAX_MS / 1e3, SERVE_BUDGET >> 30, SERVE_DRAIN_S),
+           "mixed_batched_resident": serve_stream(B, W, arrivals, reqs, 4, True, window)}
     # the FP64 reference arm, one request at a time and nothing kept between
     # requests, on the first requests of the same stream (a bounded sample)
     k = min(SERVE_FP64_SAMPLE, nreq)
-    a64, r64 = serve_requests(B, W, nreq, 7, B.FP64, True)
-    out["fp64_one_at_a_time"] = serve_stream(B, W, a64[:k], r64[:k], 1, False)
+    a64, r64 = serve_requests(B, W, nreq, 7, B.FP64, True, rate)
+    out["fp64_one_at_a_time"] = serve_stream(B, W, a64[:k], r64[:k], 1, False, SERVE_FP64_WINDOW_S)
     out["fp64_one_at_a_time"]["sample"] = "first %d requests of the stream" % k
     return out
 
@@ -605,8 +639,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--multi-rhs", type=int, default=1,
                     help="also time %d-rhs FP32 products, tensor cores vs FP32 kernels (0 = skip)" % 32)
-    ap.add_argument("--serve-requests", type=int, default=60,
+    ap.add_argument("--serve-requests", type=int, default=40,
                     help="requests of the serving stream (0 = skip the serving measurement)")
+    ap.add_argument("--serve-rate", type=float, default=SERVE_RATE,
+                    help="Poisson arrival rate of the serving stream (requests per second)")
     ap.add_argument("--matvecs-only", type=int, default=0,
                     help="profiler driver: build the workload, run this many products, exit")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32", "fp64"],
@@ -773,7 +809,7 @@ def main():
     # ------------------------------------------------------------ serving
     serve = None
     if args.serve_requests > 0:
-        serve = serve_section(B, W, args.serve_requests)
+        serve = serve_section(B, W, args.serve_requests, args.serve_rate)
         _log("serve", serve)
     # ------------------------------------------------------------ CPU oracle
     cpu_fft = None

@@ -45,7 +45,8 @@ typedef enum {
     EMSURF_ENOTCONV = 4,    /* solver hit max_iters; best iterate written     */
     EMSURF_EAGAIN = 5,      /* request still pending                          */
     EMSURF_ETIMEDOUT = 6,   /* a bounded wait ran out                         */
-    EMSURF_EBUSY = 7        /* request can never be admitted                  */
+    EMSURF_EBUSY = 7,       /* request can never be admitted                  */
+    EMSURF_ECANCELED = 8    /* request withdrawn before it ran                */
 } emsurf_status;
 
 /* Storage/arithmetic of the Fourier-domain blocks and macromodels.
@@ -150,6 +151,10 @@ typedef struct {
                              The operators it needs must be resident.         */
     int32_t precond;      /* 0: right-precondition with the handle's near-field
                              preconditioner if it was built; -1: do not      */
+    double max_ms;        /* wall-time limit (ms, 0 = none), checked at every
+                             GMRES restart and refinement: past it the solve
+                             stops as if max_iters were spent (ENOTCONV,
+                             x = best iterate)                                */
 } emsurf_solve_opts;
 
 typedef struct {
@@ -578,6 +583,10 @@ EMSURF_API int emsurf_poll(emsurf_server* s, uint64_t ticket, emsurf_result* out
 /* As poll, but blocks up to timeout_ms; ETIMEDOUT if not done by then.    */
 EMSURF_API int emsurf_wait(emsurf_server* s, uint64_t ticket, int64_t timeout_ms,
                            emsurf_result* out);
+/* Withdraws a request that is still queued (not yet admitted): OK, and its
+ * result (collected by poll/wait) has status ECANCELED; EBUSY once it runs
+ * (its opts.max_ms bounds it); EINVAL for an unknown ticket.             */
+EMSURF_API int emsurf_cancel(emsurf_server* s, uint64_t ticket);
 /* Stops accepting requests, finishes the queued and running ones, frees
  * them and the resident blocks.                                           */
 EMSURF_API void emsurf_server_destroy(emsurf_server* s);

@@ -14,7 +14,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libemsurf.so")
 
 EMSURF_OK, EMSURF_EINVAL, EMSURF_ENOMEM, EMSURF_ECUDA, EMSURF_ENOTCONV = 0, 1, 2, 3, 4
-EMSURF_EAGAIN, EMSURF_ETIMEDOUT, EMSURF_EBUSY = 5, 6, 7
+EMSURF_EAGAIN, EMSURF_ETIMEDOUT, EMSURF_EBUSY, EMSURF_ECANCELED = 5, 6, 7, 8
 FP64, FP32, MIXED = 0, 1, 2
 
 
@@ -48,7 +48,7 @@ class Problem(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("restart", C.c_int32), ("max_iters", C.c_int32),
                 ("max_refine", C.c_int32), ("inner_rtol", C.c_double), ("solver", C.c_int32),
-                ("precond", C.c_int32)]
+                ("precond", C.c_int32), ("max_ms", C.c_double)]
 
 
 class SolveInfo(C.Structure):
@@ -268,11 +268,12 @@ SOLVER_DEFAULT, SOLVER_FP64, SOLVER_FP32, SOLVER_MIXED = 0, 1, 2, 3
 
 
 def emsurf_solve(h, b, x, rtol=1e-8, restart=30, max_iters=5000, max_refine=10, inner_rtol=0.0,
-                 solver=SOLVER_DEFAULT, stream=None, precond=0):
+                 solver=SOLVER_DEFAULT, stream=None, precond=0, max_ms=0.0):
     """emsurf_solve: returns (status, [info dict per rhs]); ENOTCONV is not raised.
-    precond = -1 ignores the handle's near-field preconditioner."""
+    precond = -1 ignores the handle's near-field preconditioner; max_ms > 0
+    stops the solve at the first restart past that wall time."""
     nrhs = 1 if b.dim() == 1 else b.shape[0]
-    o = SolveOpts(rtol, restart, max_iters, max_refine, inner_rtol, solver, precond)
+    o = SolveOpts(rtol, restart, max_iters, max_refine, inner_rtol, solver, precond, max_ms)
     info = (SolveInfo * nrhs)()
     st = _check(lib().emsurf_solve(h.ptr, _ptr(b), _ptr(x), nrhs, C.byref(o), info, _stream(stream)),
                 ok=(EMSURF_OK, EMSURF_ENOTCONV))
@@ -516,6 +517,7 @@ def _serve_lib():
         L.emsurf_submit.argtypes = [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]
         L.emsurf_poll.argtypes = [vp, C.c_uint64, C.POINTER(Result)]
         L.emsurf_wait.argtypes = [vp, C.c_uint64, C.c_int64, C.POINTER(Result)]
+        L.emsurf_cancel.argtypes = [vp, C.c_uint64]
         L.emsurf_server_destroy.argtypes = [vp]
         L.emsurf_server_destroy.restype = None
         L.emsurf_server_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
@@ -553,16 +555,17 @@ def emsurf_server_create(device=0, device_mem_budget=0, max_active=2, cache=True
 def make_request(a, b, h, n, nx, ny, k0, patch_sides, patch_z, patch_n, type_map, khat, ehat,
                  precision=MIXED, rtol=1e-6, restart=30, max_iters=20000, max_refine=20,
                  inner_rtol=0.0, solver=0, x_out=None, precond_overlap=0.0, slab_t=0.0,
-                 slab_eps=1.0, ring_layers=0):
+                 slab_eps=1.0, ring_layers=0, max_ms=0.0):
     """Build an emsurf_request; returns (Request, arrays that must stay alive).
-    slab_t > 0: patch-on-slab cells (eps slab_eps, patch on the slab top)."""
+    slab_t > 0: patch-on-slab cells (eps slab_eps, patch on the slab top);
+    max_ms > 0: wall-time limit of the solve."""
     sides = np.ascontiguousarray(patch_sides, dtype=np.float64)
     tmap = np.ascontiguousarray(type_map, dtype=np.int32)
     kh = np.ascontiguousarray(np.atleast_2d(khat), dtype=np.float64)
     eh = np.ascontiguousarray(np.atleast_2d(ehat), dtype=np.float64)
     q = Request(a, b, h, n, nx, ny, k0, len(sides), _ptr(sides), patch_z, patch_n, _ptr(tmap),
                 len(kh), _ptr(kh), _ptr(eh), precision,
-                SolveOpts(rtol, restart, max_iters, max_refine, inner_rtol, solver, 0), _ptr(x_out),
+                SolveOpts(rtol, restart, max_iters, max_refine, inner_rtol, solver, 0, max_ms), _ptr(x_out),
                 precond_overlap, slab_t, C128(complex(slab_eps).real, complex(slab_eps).imag),
                 ring_layers)
     return q, (sides, tmap, kh, eh, x_out)
@@ -604,6 +607,13 @@ def emsurf_wait(server, ticket, timeout_ms=600000):
     _check(_serve_lib().emsurf_wait(server.ptr, ticket, int(timeout_ms), C.byref(r)))
     server.keep.pop(ticket, None)
     return _result(r)
+
+
+def emsurf_cancel(server, ticket):
+    """emsurf_cancel: True if the queued request was withdrawn, False if it
+    already runs or ran (its result is then collected as usual)."""
+    st = _check(_serve_lib().emsurf_cancel(server.ptr, ticket), ok=(EMSURF_OK, EMSURF_EBUSY))
+    return st == EMSURF_OK
 
 
 def emsurf_server_stats(server):

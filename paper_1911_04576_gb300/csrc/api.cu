@@ -232,6 +232,7 @@ int create_impl(const emsurf_problem* p, emsurf_handle* h, const emsurf_handle* 
     }
     if (h->precision == EMSURF_FP32) {
         EMS_TRY(build_operator<float2>(h, h->op32, p, share ? &share->op32 : nullptr));
+        if (share) EMS_TRY(adopt_fp32_form(h, share));
         h->have32 = true;
     } else if (h->precision == EMSURF_MIXED) {
         EMS_TRY(derive_fp32_operator(h, p, share));
@@ -469,7 +470,8 @@ EMSURF_API int emsurf_solve(emsurf_handle* h, const emsurf_c128* b, emsurf_c128*
         set_error("nrhs %d outside [1, %d]", nrhs, h->max_rhs);
         return EMSURF_EINVAL;
     }
-    if (!(opts->rtol > 0.0) || opts->restart < 1 || opts->restart > 64 || opts->max_iters < 1) {
+    if (!(opts->rtol > 0.0) || opts->restart < 1 || opts->restart > 64 || opts->max_iters < 1 ||
+        !(opts->max_ms >= 0.0)) {
         set_error("need rtol > 0, restart in [1, 64], max_iters >= 1");
         return EMSURF_EINVAL;
     }

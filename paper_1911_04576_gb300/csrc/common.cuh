@@ -353,6 +353,7 @@ int build_operator(emsurf_handle* h, Operator<T2>& op, const emsurf_problem* pr,
                    const Operator<T2>* share = nullptr);
 // share: a handle of the same lattice whose Fourier-domain blocks are reused
 int derive_fp32_operator(emsurf_handle* h, const emsurf_problem* pr, const emsurf_handle* share = nullptr);
+int adopt_fp32_form(emsurf_handle* h, const emsurf_handle* share);
 int clear_wait_error(emsurf_handle* h);
 int build_ds_planes(emsurf_handle* h, const emsurf_handle* share = nullptr);
 int grid_barrier_selftest(emsurf_handle* h, long long limit, cudaStream_t st);

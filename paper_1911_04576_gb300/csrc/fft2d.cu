@@ -19,7 +19,7 @@
 namespace emsurf {
 namespace {
 
-constexpr int kF2Threads = 256;
+constexpr int kF2Threads = 512;
 
 constexpr int f2_rad_count(int P) {
     int n = 0;

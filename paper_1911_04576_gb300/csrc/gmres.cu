@@ -45,6 +45,8 @@ constexpr int kArnThreads = 1024;   // 32 warps: one per Krylov vector in the do
 constexpr int kArnChunkMax = 4096;  // vector elements per block (64 KB of shared w)
 
 struct Gm {
+    std::chrono::steady_clock::time_point deadline{};   // wall-time limit of the current solve
+    bool has_deadline = false;
     int m = 0, R = 0;
     size_t n = 0;
     double2* V = nullptr;      // [(m+1)][R][n]
@@ -887,11 +889,26 @@ template <typename VT> Kv<VT> kv(Gm* g);
 template <> Kv<double2> kv<double2>(Gm* g) { return {g->V, g->Z, g->w, g->r0}; }
 template <> Kv<float2> kv<float2>(Gm* g) { return {g->V32, g->Z32, g->w32, g->r032}; }
 
+bool past_deadline(const Gm* g) {
+    return g->has_deadline && std::chrono::steady_clock::now() >= g->deadline;
+}
+
 // GMRES(m) from x (used as the initial guess), until every rhs reaches rtol
-// or the iteration budget runs out.  Returns the number of Arnoldi steps.
+// or the iteration budget (or the wall-time limit, checked per restart) runs
+// out.  Returns the number of Arnoldi steps.
+// stop_on_stall (the inner solves of the mixed refinement): also stop once
+// the worst relative residual of the active rhs has fallen by less than 1 %
+// over each of kStallCycles consecutive restarts.  A perturbed operator in
+// FP32 arithmetic cannot push the residual below about its own error times
+// the condition number; past that level more restarts gain nothing, and the
+// FP64 residual of the next refinement step is the way forward.
+constexpr int kStallCycles = 3;
+constexpr double kStallRatio = 0.99;
+
 template <typename VT>
 int gmres_core(emsurf_handle* h, Gm* g, Apply<VT>& A, const VT* b, VT* x, int R, int m,
-               double rtol, int max_iters, bool x_is_zero, bool pc, cudaStream_t st, int* iters_out) {
+               double rtol, int max_iters, bool x_is_zero, bool pc, cudaStream_t st, int* iters_out,
+               bool stop_on_stall = false) {
     const size_t n = g->n, nv = (size_t)R * n;
     const size_t vstride = nv;
     const int nb = blocks_for(nv);
@@ -901,6 +918,8 @@ int gmres_core(emsurf_handle* h, Gm* g, Apply<VT>& A, const VT* b, VT* x, int R,
     EMS_TRY(norms<VT>(g, b, R, st));
     EMS_CUDA(cudaMemcpyAsync(g->bnorm, g->nrm, sizeof(double) * R, cudaMemcpyDeviceToDevice, st));
     bool first = true;
+    double prev_worst = 0.0;
+    int stalls = 0;
     while (true) {
         if (first && x_is_zero) {
             EMS_CUDA(cudaMemcpyAsync(K.r0, b, nv * sizeof(VT), cudaMemcpyDeviceToDevice, st));
@@ -920,10 +939,19 @@ int gmres_core(emsurf_handle* h, Gm* g, Apply<VT>& A, const VT* b, VT* x, int R,
         EMS_CUDA(cudaGetLastError());
         ++g->launches;
         EMS_CUDA(cudaMemcpyAsync(g->h_act, g->active, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+        if (stop_on_stall) EMS_CUDA(cudaMemcpyAsync(g->h_res, g->res, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
         EMS_CUDA(cudaStreamSynchronize(st));
         bool any = false;
         for (int r = 0; r < R; ++r) any = any || g->h_act[r];
-        if (!any || it >= max_iters) break;
+        if (!any || it >= max_iters || past_deadline(g)) break;
+        if (stop_on_stall) {
+            double worst = 0.0;
+            for (int r = 0; r < R; ++r)
+                if (g->h_act[r]) worst = std::max(worst, g->h_res[r]);
+            stalls = (prev_worst > 0.0 && worst > kStallRatio * prev_worst) ? stalls + 1 : 0;
+            prev_worst = worst;
+            if (stalls >= kStallCycles) break;
+        }
         for (int j = 0; j < m; ++j) {
             VT* Vj = K.V + (size_t)j * vstride;
             if (pc) {
@@ -1035,6 +1063,10 @@ int gmres_solve(emsurf_handle* h, const double2* b, double2* x, int R, const ems
     const int m = o->restart;
     Gm* g = nullptr;
     EMS_TRY(gm_alloc(h, g, m, R));
+    g->has_deadline = o->max_ms > 0.0;
+    if (g->has_deadline)
+        g->deadline = t0 + std::chrono::duration_cast<std::chrono::steady_clock::duration>(
+                                std::chrono::duration<double, std::milli>(o->max_ms));
     const size_t nv = (size_t)R * g->n;
     EMS_CUDA(cudaMemsetAsync(x, 0, nv * sizeof(double2), st));
     const int64_t launches0 = g->launches;
@@ -1069,7 +1101,7 @@ int gmres_solve(emsurf_handle* h, const double2* b, double2* x, int R, const ems
             }
             double worst = 0.0;
             for (int r = 0; r < R; ++r) worst = std::max(worst, res[r]);
-            if (worst <= o->rtol || refines >= o->max_refine || iters >= o->max_iters) break;
+            if (worst <= o->rtol || refines >= o->max_refine || iters >= o->max_iters || past_deadline(g)) break;
             // inner solve A32 c = d with FP32-operator GMRES on FP32 vectors
             to_f32_kernel<<<blocks_for(nv), 256, 0, st>>>(g->d32, g->d, nv);
             EMS_CUDA(cudaGetLastError());
@@ -1078,7 +1110,7 @@ int gmres_solve(emsurf_handle* h, const double2* b, double2* x, int R, const ems
             const double tol = std::max(inner, 0.5 * o->rtol / std::max(worst, 1e-300));
             int it = 0;
             EMS_TRY(gmres_core<float2>(h, g, A32f, g->d32, g->c32, R, m, std::min(tol, 0.5),
-                                       o->max_iters - iters, true, pc, st, &it));
+                                       o->max_iters - iters, true, pc, st, &it, true));
             iters += it;
             axpy_kernel<float2><<<blocks_for(nv), 256, 0, st>>>(x, g->c32, nv);
             EMS_CUDA(cudaGetLastError());

@@ -1509,6 +1509,10 @@ int grid_for(size_t n, int threads) {
 
 }  // namespace
 
+namespace {
+int orbit_spectrum(emsurf_handle* h, const emsurf_problem* pr, const double2* B64, bool* used);
+}
+
 // ---------------------------------------------------------------- build
 // Places L(d), K(d) at grid point (dx mod px, dy mod py) -- the circulant's
 // first column (Eq. LJV3 read by columns, d = test - source) -- and
@@ -1614,6 +1618,20 @@ int build_spectrum(emsurf_handle* h, Operator<T2>& op, const emsurf_problem* pr)
     if (direct64) {
         op.Bhat = reinterpret_cast<T2*>(B64);
     } else {
+        // an FP32-only single-rhs handle of a mirror-symmetric box keeps one
+        // bin per orbit (the same form a MIXED handle derives)
+        bool orb = false;
+        if (h->precision == EMSURF_FP32) {
+            const int s = orbit_spectrum(h, pr, B64, &orb);
+            if (s != EMSURF_OK) {
+                cudaFree(B64);
+                return s;
+            }
+        }
+        if (orb) {
+            cudaFree(B64);
+            return EMSURF_OK;
+        }
         EMS_TRY(dev_alloc(h, (void**)&op.Bhat, nbins * 2 * EE * sizeof(T2)));
         round_kernel<<<152 * 8, 256, 0, st>>>(reinterpret_cast<float2*>(op.Bhat), B64,
                                              nbins * 2 * EE);
@@ -1642,7 +1660,7 @@ int orbit_image(int e, int kx, int ky, int px, int py) {
 // The FP32 spectrum as one stored bin per mirror orbit, when the problem
 // gives the box's mirrors and they hold on the FP64 blocks.  *used = false
 // (and nothing allocated) otherwise.
-int orbit_spectrum(emsurf_handle* h, const emsurf_problem* pr, bool* used) {
+int orbit_spectrum(emsurf_handle* h, const emsurf_problem* pr, const double2* B64, bool* used) {
     *used = false;
     const int E = h->E, px = h->px, py = h->py;
     const size_t EE = (size_t)E * E, nb = (size_t)h->nbins;
@@ -1687,7 +1705,7 @@ int orbit_spectrum(emsurf_handle* h, const emsurf_problem* pr, bool* used) {
             EMS_CUDA(cudaMemcpyAsync(dpt, pt.data(), E * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
             EMS_CUDA(cudaMemcpyAsync(dimg, img.data(), nb * sizeof(int32_t), cudaMemcpyHostToDevice, st));
             EMS_CUDA(cudaMemsetAsync(dout, 0, 2 * sizeof(unsigned long long), st));
-            mirror_check_kernel<<<152 * 8, 256, 0, st>>>(h->op64.Bhat, dpt, dimg, E, nb, dout);
+            mirror_check_kernel<<<152 * 8, 256, 0, st>>>(B64, dpt, dimg, E, nb, dout);
             EMS_CUDA(cudaGetLastError());
             unsigned long long hout[2] = {0, 0};
             EMS_CUDA(cudaMemcpyAsync(hout, dout, sizeof(hout), cudaMemcpyDeviceToHost, st));
@@ -1780,7 +1798,7 @@ int orbit_spectrum(emsurf_handle* h, const emsurf_problem* pr, bool* used) {
     EMS_TRY(dev_alloc(h, (void**)&h->d_pair_cnt, h->pair_cnt_bytes));
     EMS_CUDA(cudaMemsetAsync(h->d_pair_cnt, 0, h->pair_cnt_bytes, st));
     EMS_TRY(dev_alloc(h, (void**)&h->op32.Bhat, (size_t)nst * 2 * EE * sizeof(float2)));
-    half_round_kernel<<<152 * 8, 256, 0, st>>>(h->op32.Bhat, h->op64.Bhat, drep, 2 * EE, (size_t)nst * 2 * EE);
+    half_round_kernel<<<152 * 8, 256, 0, st>>>(h->op32.Bhat, B64, drep, 2 * EE, (size_t)nst * 2 * EE);
     EMS_CUDA(cudaGetLastError());
     EMS_CUDA(cudaStreamSynchronize(st));   // the host vectors above go out of scope
     h->orb32 = true;
@@ -1788,6 +1806,31 @@ int orbit_spectrum(emsurf_handle* h, const emsurf_problem* pr, bool* used) {
     return EMSURF_OK;
 }
 }  // namespace
+
+// The stored-bin lists of a shared handle's partial FP32 spectrum (pairs or
+// mirror orbits); the kernels' partial sums and counters are per-handle work
+// space.
+int adopt_fp32_form(emsurf_handle* h, const emsurf_handle* share) {
+    h->half32 = share->half32;
+    h->nst = share->nst;
+    h->d_st_bin = share->d_st_bin;
+    h->d_st_part = share->d_st_part;
+    h->orb32 = share->orb32;
+    h->orb_G = share->orb_G;
+    h->d_orb_bin = share->d_orb_bin;
+    h->d_orb_elem = share->d_orb_elem;
+    h->d_orb_perm = share->d_orb_perm;
+    if (h->half32 || h->orb32) {
+        const int ncw = (h->E + 31) / 32;
+        const int slots = h->orb32 ? h->orb_G : 2;
+        h->pair_grid = share->pair_grid;
+        EMS_TRY(dev_alloc(h, (void**)&h->d_pair_part, (size_t)h->pair_grid * 2 * slots * 2 * h->E * sizeof(float2)));
+        h->pair_cnt_bytes = (size_t)h->nst * ncw * sizeof(int);
+        EMS_TRY(dev_alloc(h, (void**)&h->d_pair_cnt, h->pair_cnt_bytes));
+        EMS_CUDA(cudaMemsetAsync(h->d_pair_cnt, 0, h->pair_cnt_bytes, h->setup_stream));
+    }
+    return EMSURF_OK;
+}
 
 // FP32 operator of a MIXED handle: round the resident FP64 spectrum and
 // macromodels instead of transforming the tables a second time.
@@ -1798,40 +1841,13 @@ int derive_fp32_operator(emsurf_handle* h, const emsurf_problem* pr, const emsur
     cudaStream_t st = h->setup_stream;
     Operator<float2>& op = h->op32;
     if (share) {
-        // the FP32 spectrum (and its stored-bin lists) of the shared handle;
-        // the pair kernel's partial sums and counters are per-handle work space
         op.Bhat = share->op32.Bhat;
-        h->half32 = share->half32;
-        h->nst = share->nst;
-        h->d_st_bin = share->d_st_bin;
-        h->d_st_part = share->d_st_part;
-        h->orb32 = share->orb32;
-        h->orb_G = share->orb_G;
-        h->d_orb_bin = share->d_orb_bin;
-        h->d_orb_elem = share->d_orb_elem;
-        h->d_orb_perm = share->d_orb_perm;
-        if (h->orb32) {
-            const int ncw = (h->E + 31) / 32;
-            h->pair_grid = share->pair_grid;
-            EMS_TRY(dev_alloc(h, (void**)&h->d_pair_part,
-                              (size_t)h->pair_grid * 2 * h->orb_G * 2 * h->E * sizeof(float2)));
-            h->pair_cnt_bytes = (size_t)h->nst * ncw * sizeof(int);
-            EMS_TRY(dev_alloc(h, (void**)&h->d_pair_cnt, h->pair_cnt_bytes));
-            EMS_CUDA(cudaMemsetAsync(h->d_pair_cnt, 0, h->pair_cnt_bytes, st));
-        }
-        if (h->half32) {
-            const int ncw = (h->E + 31) / 32;
-            h->pair_grid = share->pair_grid;
-            EMS_TRY(dev_alloc(h, (void**)&h->d_pair_part, (size_t)h->pair_grid * 2 * 2 * h->E * sizeof(float2)));
-            h->pair_cnt_bytes = (size_t)h->nst * ncw * sizeof(int);
-            EMS_TRY(dev_alloc(h, (void**)&h->d_pair_cnt, h->pair_cnt_bytes));
-            EMS_CUDA(cudaMemsetAsync(h->d_pair_cnt, 0, h->pair_cnt_bytes, st));
-        }
+        EMS_TRY(adopt_fp32_form(h, share));
         return derive_fp32_rest(h, pr);
     }
     {
         bool orb = false;
-        EMS_TRY(orbit_spectrum(h, pr, &orb));
+        EMS_TRY(orbit_spectrum(h, pr, h->op64.Bhat, &orb));
         if (orb) return derive_fp32_rest(h, pr);
     }
     // With reciprocal tables L^(-k) = L^(k)^T and K^(-k) = K^(k)^T: single-rhs

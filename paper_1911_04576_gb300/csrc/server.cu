@@ -597,7 +597,8 @@ EMSURF_API int emsurf_submit(emsurf_server* sv, const emsurf_request* req, uint6
     if (q.n < 1 || q.nx < 1 || q.ny < 1 || q.n_types < 1 || q.nrhs < 1 || q.nrhs > 64 || !q.patch_sides ||
         !q.type_map || !q.khat || !q.ehat || !(q.k0 > 0.0) ||
         (q.precision != EMSURF_FP64 && q.precision != EMSURF_FP32 && q.precision != EMSURF_MIXED) ||
-        !(q.opts.rtol > 0.0) || q.opts.restart < 1 || q.opts.restart > 64 || q.opts.max_iters < 1) {
+        !(q.opts.rtol > 0.0) || q.opts.restart < 1 || q.opts.restart > 64 || q.opts.max_iters < 1 ||
+        !(q.opts.max_ms >= 0.0)) {
         set_error("emsurf_submit: invalid request");
         return EMSURF_EINVAL;
     }
@@ -658,6 +659,30 @@ EMSURF_API int emsurf_wait(emsurf_server* sv, uint64_t ticket, int64_t timeout_m
     }
     fill_result(*jb, out);
     sv->jobs.erase(ticket);
+    return EMSURF_OK;
+}
+
+EMSURF_API int emsurf_cancel(emsurf_server* sv, uint64_t ticket) {
+    if (!sv) { set_error("emsurf_cancel: NULL server"); return EMSURF_EINVAL; }
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        auto it = sv->jobs.find(ticket);
+        if (it == sv->jobs.end()) {
+            set_error("emsurf_cancel: unknown ticket %llu", (unsigned long long)ticket);
+            return EMSURF_EINVAL;
+        }
+        auto q = std::find(sv->queue.begin(), sv->queue.end(), it->second);
+        if (q == sv->queue.end()) {
+            set_error("emsurf_cancel: ticket %llu is no longer queued", (unsigned long long)ticket);
+            return EMSURF_EBUSY;
+        }
+        Job& jb = *it->second;
+        sv->queue.erase(q);
+        jb.t_start = jb.t_setup = jb.t_end = Clock::now();
+        jb.status = EMSURF_ECANCELED;
+        jb.done = true;
+    }
+    sv->cv_done.notify_all();
     return EMSURF_OK;
 }
 

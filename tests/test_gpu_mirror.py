@@ -208,3 +208,29 @@ def test_orbit_full_size_sampled(emsurf_lib):
         assert np.array_equal(run_matvec(B, h, x, B.FP32)[0], y32)
         B.emsurf_check(h)
         h.close()
+
+
+def test_orbit_fp32_handle_and_shared_blocks(emsurf_lib):
+    """An FP32-only handle derives the same orbit form from its temporary FP64
+    blocks; a handle created like it (other macromodels and type map) reads
+    its orbit blocks and gives the product of its own problem."""
+    from paper_1911_04576_gb300 import binding as B
+    n, nx, ny = 2, 4, 4
+    E, idx, sgn, nu, Lt, Kt, Z, tmap, mir = symmetric_case(B, n, nx, ny, 7, 8100)
+    h = B.emsurf_create(nx, ny, E, nu, tmap, Z, Lt, Kt, COEF, idx, sgn, precision=B.FP32, mirrors=mir)
+    assert B.emsurf_operator_layout(h) == (2, 8)
+    px, py = B.emsurf_query(h)[:2]
+    assert B.emsurf_operator_info(h)[0] == n_orbits(px, py, 7)
+    x = W.random_vectors(1, nu, 8101)
+    yref = lattice.matvec_direct(x, Lt, Kt, COEF, Z, tmap, idx, sgn, nu, nx, ny)
+    assert relerr(run_matvec(B, h, x, B.FP32)[0], yref[0]) <= TOL32
+    Z2 = W.random_macromodels(2, 2 * E, 8102)
+    t2 = np.random.default_rng(8103).integers(0, 2, nx * ny).astype(np.int32)
+    like = B.emsurf_create(nx, ny, E, nu, t2, Z2, None, None, COEF, idx, sgn, precision=B.FP32, share=h,
+                           mirrors=mir)
+    assert B.emsurf_operator_layout(like) == (2, 8)
+    y2 = lattice.matvec_direct(x, Lt, Kt, COEF, Z2, t2, idx, sgn, nu, nx, ny)
+    assert relerr(run_matvec(B, like, x, B.FP32)[0], y2[0]) <= TOL32
+    B.emsurf_check(like)
+    like.close()
+    h.close()

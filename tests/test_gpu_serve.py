@@ -125,3 +125,59 @@ def test_resident_blocks_are_reused(emsurf_lib):
     for a, b, r in zip(xc, xn, rc):
         assert r["status"] == B.EMSURF_OK and r["info"]["rel_residual"] <= 1e-9
         assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(b)
+
+
+def test_cancel_withdraws_only_queued_requests(emsurf_lib):
+    """One worker: the first request runs, the later ones wait; withdrawing a
+    queued one gives ECANCELED, a request that already ran is not withdrawn."""
+    from paper_1911_04576_gb300 import binding as B
+    reqs = _requests(B)
+    sv = B.emsurf_server_create(0, 0, 1)
+    tickets, keeps = [], []
+    for r in reqs[:3]:
+        kw = {k: v for k, v in r.items() if k not in ("nu", "R")}
+        q, keep = B.make_request(**kw)
+        tickets.append(B.emsurf_submit(sv, q, keep))
+        keeps.append(keep)
+    withdrawn = B.emsurf_cancel(sv, tickets[2])
+    r0 = B.emsurf_wait(sv, tickets[0], 600000)
+    assert r0["status"] == B.EMSURF_OK
+    r2 = B.emsurf_wait(sv, tickets[2], 600000)
+    assert r2["status"] == (B.EMSURF_ECANCELED if withdrawn else B.EMSURF_OK)
+    r1 = B.emsurf_wait(sv, tickets[1], 600000)
+    assert r1["status"] == B.EMSURF_OK
+    with pytest.raises(B.EmsurfError):
+        B.emsurf_cancel(sv, 987654321)
+    sv.close()
+
+
+def test_solve_wall_time_limit(emsurf_lib):
+    """max_ms stops the solve at the first restart past it: ENOTCONV with the
+    best iterate, long before the iteration budget."""
+    import torch
+    from paper_1911_04576_gb300 import binding as B
+    w = W.WORKLOADS["lattice16x16_k576"]
+    idx, sgn, nu = B.emsurf_setup_overlap(w.n, w.nx, w.ny)
+    zl = B.emsurf_setup_slab_zlevels(H, w.n, W.SLAB_T)
+    L = torch.empty((2 * w.ny - 1, 2 * w.nx - 1, w.E, w.E), dtype=torch.complex128, device="cuda")
+    K = torch.empty_like(L)
+    B.emsurf_tabulate_offsets(A, A, H, w.n, w.nx, w.ny, W.K0, L, K, zlevels=zl)
+    Z = torch.empty((w.n_types, w.K, w.K), dtype=torch.complex128, device="cuda")
+    B.emsurf_macromodel_slab_patch(A, A, H, w.n, zl, W.patch_sides(w), w.patch_n, W.RING_LAYERS,
+                                   W.EPS_SLAB, W.K0, Z)
+    coef = (1j * W.K0, 1.0, -1.0, 1j * W.K0)
+    h = B.emsurf_create(w.nx, w.ny, w.E, nu, W.type_map(w), Z, L, K, coef, idx, sgn, precision=B.FP64,
+                        tables_on_device=True)
+    V = torch.empty((1, nu), dtype=torch.complex128, device="cuda")
+    waves = W.plane_waves(w)
+    B.emsurf_excitation(h, A, A, H, w.n, W.K0, [waves[0][0]], [waves[0][1]], V, zlevels=zl)
+    X = torch.zeros_like(V)
+    # unpreconditioned FP64 GMRES needs ~1800 iterations here
+    st, info = B.emsurf_solve(h, V, X, rtol=1e-6, restart=30, max_iters=20000, solver=B.SOLVER_FP64,
+                              max_ms=1.0)
+    assert st == B.EMSURF_ENOTCONV
+    assert info[0]["iters"] <= 60 and info[0]["rel_residual"] > 1e-6
+    assert np.isfinite(X.cpu().numpy()).all()
+    with pytest.raises(B.EmsurfError):
+        B.emsurf_solve(h, V, X, rtol=1e-6, max_ms=-1.0)
+    h.close()
