@@ -1000,7 +1000,6 @@ size_t binmul_tma_pair_smem(int E) {
 // signed index of T_e: x~[n] = sign x[idx], y[idx] = sign y~[n], encoded as
 // idx | (sign < 0) << 31.
 constexpr int kOrbStages = 3;
-constexpr int kOrbPermChunk = 8;     // x~ entries per consumer thread per pass
 constexpr int kOrbMaxThreads = 384;  // E <= 352: registers for 8 accumulator sets
 
 template <int G, int JB>
@@ -1112,36 +1111,36 @@ binmul_orbit_kernel(const float2* __restrict__ Bhat, const float2* __restrict__ 
         }
         float2* xs = xbuf + (size_t)(t & 1) * G * E2;
         if (jb == 0 || q == q0) {
-            // x~_j = T_e^T x(bin_j) in place (zero for empty slots): all
-            // reads of a pass before any write
-            for (int base = 0; base < G * E2; base += nthr * kOrbPermChunk) {
-                float2 v[kOrbPermChunk];
+            // x~_j = T_e^T x(bin_j) in place (zero for empty slots), in one
+            // pass: every read before any write.  The G x 2E entries fit in
+            // 2 G registers per thread because there are at least E
+            // consumer threads.
+            float2 v[2 * G];
 #pragma unroll
-                for (int c = 0; c < kOrbPermChunk; ++c) {
-                    const int e = base + c * nthr + tid;
-                    v[c] = make_float2(0.f, 0.f);
-                    if (e < G * E2) {
-                        const int j = e / E2, n = e - j * E2;
-                        if (orb_bin[(size_t)sb * G + j] >= 0) {
-                            const uint32_t pe = ptab[(size_t)orb_elem[(size_t)sb * G + j] * E2 + n];
-                            const float2 a = xs[(size_t)j * E2 + (pe & 0x7fffffffu)];
-                            v[c] = (pe >> 31) ? make_float2(-a.x, -a.y) : a;
-                        }
+            for (int c = 0; c < 2 * G; ++c) {
+                const int e = c * nthr + tid;
+                v[c] = make_float2(0.f, 0.f);
+                if (e < G * E2) {
+                    const int j = e / E2, n = e - j * E2;
+                    if (orb_bin[(size_t)sb * G + j] >= 0) {
+                        const uint32_t pe = ptab[(size_t)orb_elem[(size_t)sb * G + j] * E2 + n];
+                        const float2 a = xs[(size_t)j * E2 + (pe & 0x7fffffffu)];
+                        v[c] = (pe >> 31) ? make_float2(-a.x, -a.y) : a;
                     }
                 }
-                if (!consumers_meet()) {
-                    atomicExch(err, 1);
-                    return;
-                }
+            }
+            if (!consumers_meet()) {
+                atomicExch(err, 1);
+                return;
+            }
 #pragma unroll
-                for (int c = 0; c < kOrbPermChunk; ++c) {
-                    const int e = base + c * nthr + tid;
-                    if (e < G * E2) xs[e] = v[c];
-                }
-                if (!consumers_meet()) {
-                    atomicExch(err, 1);
-                    return;
-                }
+            for (int c = 0; c < 2 * G; ++c) {
+                const int e = c * nthr + tid;
+                if (e < G * E2) xs[e] = v[c];
+            }
+            if (!consumers_meet()) {
+                atomicExch(err, 1);
+                return;
             }
             // later bulk copies into this buffer are ordered after these writes
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
