@@ -547,6 +547,7 @@ def serve_stream(B, W, arrivals, reqs, max_active, cache, window_s):
         time.sleep(0.05)
         pending = collect()
     withdrawn = sum(1 for t in pending if B.emsurf_cancel(sv, t))
+    _log("serve window closed", {"completed": len(res), "withdrawn": withdrawn, "running": len(pending) - withdrawn})
     for t in pending:
         r = B.emsurf_wait(sv, t, 3600 * 1000)
         if r["status"] != B.EMSURF_ECANCELED:
@@ -581,6 +582,7 @@ def serve_section(B, W, nreq, rate):
                      % (rate, nreq, list(SERVE_SIZES), [36 * m * m for m in SERVE_MESH], SERVE_RHS[0],
                         SERVE_RHS[-1], RTOL, SERVE_MAX_MS / 1e3, SERVE_BUDGET >> 30, SERVE_DRAIN_S),
            "mixed_batched_resident": serve_stream(B, W, arrivals, reqs, 4, True, window)}
+    _log("serve mixed arm", out["mixed_batched_resident"])
     # the FP64 reference arm, one request at a time and nothing kept between
     # requests, on the first requests of the same stream (a bounded sample)
     k = min(SERVE_FP64_SAMPLE, nreq)
@@ -809,14 +811,17 @@ def main():
     # ------------------------------------------------------------ serving
     serve = None
     if args.serve_requests > 0:
+        _log("serve start")
         serve = serve_section(B, W, args.serve_requests, args.serve_rate)
         _log("serve", serve)
     # ------------------------------------------------------------ CPU oracle
     cpu_fft = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        _log("cpu baselines start")
         cpu_fft = cpu_fft_section(W, w, info64[0]["n_matvec"], last_iters(infos))
         _log("cpu_fft", cpu_fft)
         t_cpu = cpu_oracle_matvec_seconds(W, w, nu)
+        _log("cpu oracle product", {"s": round(t_cpu, 3)})
         nmv64 = info64[0]["n_matvec"]
         cpu = {"value": t_cpu * 1e3 * nmv64, "unit": "ms", "cores": len(os.sched_getaffinity(0)),
                "kind": "oracle",

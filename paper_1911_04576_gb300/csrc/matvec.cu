@@ -1000,10 +1000,13 @@ size_t binmul_tma_pair_smem(int E) {
 // signed index of T_e: x~[n] = sign x[idx], y[idx] = sign y~[n], encoded as
 // idx | (sign < 0) << 31.
 constexpr int kOrbStages = 3;
-constexpr int kOrbMaxThreads = 384;  // E <= 352: registers for 8 accumulator sets
+// NT consumer threads per test row, each with G / NT accumulator sets (4):
+// enough warps per SM to hide the shared-memory latency of the FMA stream
+template <int NT>
+constexpr int orb_max_threads() { return NT == 1 ? 384 : 640; }
 
-template <int G, int JB>
-__global__ void __launch_bounds__(kOrbMaxThreads, 1)
+template <int G, int JB, int NT>
+__global__ void __launch_bounds__(orb_max_threads<NT>(), 1)
 binmul_orbit_kernel(const float2* __restrict__ Bhat, const float2* __restrict__ Xh, float2* __restrict__ Yh,
                     const int32_t* __restrict__ orb_bin, const int32_t* __restrict__ orb_elem,
                     const uint32_t* __restrict__ orb_perm, int E, int nst, int n_elem, float2 ca, float2 cb,
@@ -1018,15 +1021,16 @@ binmul_orbit_kernel(const float2* __restrict__ Bhat, const float2* __restrict__ 
     uint64_t* full = reinterpret_cast<uint64_t*>(ptab + (size_t)n_elem * E2 + ((n_elem * E2) & 1));
     uint64_t* empty = full + kOrbStages;
     uint64_t* pbar = empty + kOrbStages;     // consumer-only sync of the x~ gather
+    constexpr int GS = G / NT;               // slots per consumer thread
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ncw = (E + 31) / 32;
-    const int nthr = 32 * ncw;               // consumer threads
+    const int ncw = (E + 31) / 32;           // row warps of one slot group
+    const int nthr = 32 * ncw * NT;          // consumer threads
     if (threadIdx.x == 0) {
         for (int s = 0; s < kOrbStages; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], ncw);
+            mbar_init(&empty[s], ncw * NT);
         }
-        mbar_init(pbar, ncw);
+        mbar_init(pbar, ncw * NT);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -1085,10 +1089,12 @@ binmul_orbit_kernel(const float2* __restrict__ Bhat, const float2* __restrict__ 
         }
         return;
     }
-    // ---- consumers: one thread per test row i
+    // ---- consumers: NT threads per test row i, slot group grp of GS slots
     const int tid = threadIdx.x - 32;
-    const int w = warp - 1;
-    const int i = w * 32 + lane;
+    const int w = warp - 1;                  // consumer warp (counter index)
+    const int grp = w / ncw;
+    const int i = (w - grp * ncw) * 32 + lane;
+    const int j_lo = grp * GS;
     int s = 0, sb = sb0, jb = jb0, t = 0;
     uint32_t ph = 0, pph = 0;
     long long qb = (long long)sb0 * nj;
@@ -1101,9 +1107,9 @@ binmul_orbit_kernel(const float2* __restrict__ Bhat, const float2* __restrict__ 
         pph ^= 1u;
         return ok;
     };
-    float2 lj[G], lm[G], kj[G], km[G];
+    float2 lj[GS], lm[GS], kj[GS], km[GS];
 #pragma unroll
-    for (int j = 0; j < G; ++j) lj[j] = lm[j] = kj[j] = km[j] = make_float2(0.f, 0.f);
+    for (int j = 0; j < GS; ++j) lj[j] = lm[j] = kj[j] = km[j] = make_float2(0.f, 0.f);
     for (long long q = q0; q < q1; ++q) {
         if (!mbar_wait(&full[s], ph)) {
             atomicExch(err, 1);
@@ -1113,11 +1119,11 @@ binmul_orbit_kernel(const float2* __restrict__ Bhat, const float2* __restrict__ 
         if (jb == 0 || q == q0) {
             // x~_j = T_e^T x(bin_j) in place (zero for empty slots), in one
             // pass: every read before any write.  The G x 2E entries fit in
-            // 2 G registers per thread because there are at least E
+            // 2 GS registers per thread because there are at least NT E
             // consumer threads.
-            float2 v[2 * G];
+            float2 v[2 * GS];
 #pragma unroll
-            for (int c = 0; c < 2 * G; ++c) {
+            for (int c = 0; c < 2 * GS; ++c) {
                 const int e = c * nthr + tid;
                 v[c] = make_float2(0.f, 0.f);
                 if (e < G * E2) {
@@ -1134,7 +1140,7 @@ binmul_orbit_kernel(const float2* __restrict__ Bhat, const float2* __restrict__ 
                 return;
             }
 #pragma unroll
-            for (int c = 0; c < 2 * G; ++c) {
+            for (int c = 0; c < 2 * GS; ++c) {
                 const int e = c * nthr + tid;
                 if (e < G * E2) xs[e] = v[c];
             }
@@ -1156,9 +1162,10 @@ binmul_orbit_kernel(const float2* __restrict__ Bhat, const float2* __restrict__ 
                     const float2 l0 = Ls[jj * E + i], l1 = Ls[(jj + 1) * E + i];
                     const float2 k0 = Ks[jj * E + i], k1 = Ks[(jj + 1) * E + i];
 #pragma unroll
-                    for (int j = 0; j < G; ++j) {
-                        const float4 xj = *reinterpret_cast<const float4*>(xs + (size_t)j * E2 + j0 + jj);
-                        const float4 xm = *reinterpret_cast<const float4*>(xs + (size_t)j * E2 + E + j0 + jj);
+                    for (int j = 0; j < GS; ++j) {
+                        const float2* xsj = xs + (size_t)(j_lo + j) * E2;
+                        const float4 xj = *reinterpret_cast<const float4*>(xsj + j0 + jj);
+                        const float4 xm = *reinterpret_cast<const float4*>(xsj + E + j0 + jj);
                         const float2 xj0 = make_float2(xj.x, xj.y), xj1 = make_float2(xj.z, xj.w);
                         const float2 xm0 = make_float2(xm.x, xm.y), xm1 = make_float2(xm.z, xm.w);
                         cfma(lj[j], l0, xj0);
@@ -1180,11 +1187,12 @@ binmul_orbit_kernel(const float2* __restrict__ Bhat, const float2* __restrict__ 
             const bool whole = qb >= q0 && jb == nj - 1;
             float2* P = part + ((size_t)blockIdx.x * 2 + (t == 0 ? 0 : 1)) * G * E2;
 #pragma unroll
-            for (int j = 0; j < G; ++j) {
+            for (int jl = 0; jl < GS; ++jl) {
+                const int j = j_lo + jl;
                 const int bin = orb_bin[(size_t)sb * G + j];
                 if (bin < 0 || i >= E) continue;
-                const float2 y0 = cadd(cmul(ca, lj[j]), cmul(cb, km[j]));
-                const float2 y1 = cadd(cmul(cg, kj[j]), cmul(cd, lm[j]));
+                const float2 y0 = cadd(cmul(ca, lj[jl]), cmul(cb, km[jl]));
+                const float2 y1 = cadd(cmul(cg, kj[jl]), cmul(cd, lm[jl]));
                 if (whole) {
                     const uint32_t* pt = ptab + (size_t)orb_elem[(size_t)sb * G + j] * E2;
                     const uint32_t p0 = pt[i], p1 = pt[E + i];
@@ -1200,7 +1208,7 @@ binmul_orbit_kernel(const float2* __restrict__ Bhat, const float2* __restrict__ 
                 __threadfence();
                 __syncwarp();
                 const int bf = pair_cta_of(qb, Q, Gc), bl = pair_cta_of(qb + nj - 1, Q, Gc);
-                int* c = cnt + (size_t)sb * ncw + w;
+                int* c = cnt + (size_t)sb * ncw * NT + w;
                 int old = 0;
                 if (lane == 0) old = atomicAdd(c, 1);
                 old = __shfl_sync(0xffffffffu, old, 0);
@@ -1209,7 +1217,7 @@ binmul_orbit_kernel(const float2* __restrict__ Bhat, const float2* __restrict__ 
                     if (lane == 0) *c = 0;
                     __threadfence();
                     if (i < E) {
-                        for (int j = 0; j < G; ++j) {
+                        for (int j = j_lo; j < j_lo + GS; ++j) {
                             const int bin = orb_bin[(size_t)sb * G + j];
                             if (bin < 0) continue;
                             float2 a0 = make_float2(0.f, 0.f), a1 = a0;
@@ -1229,7 +1237,7 @@ binmul_orbit_kernel(const float2* __restrict__ Bhat, const float2* __restrict__ 
                 }
             }
 #pragma unroll
-            for (int j = 0; j < G; ++j) lj[j] = lm[j] = kj[j] = km[j] = make_float2(0.f, 0.f);
+            for (int j = 0; j < GS; ++j) lj[j] = lm[j] = kj[j] = km[j] = make_float2(0.f, 0.f);
         }
         if (++s == kOrbStages) { s = 0; ph ^= 1u; }
         if (++jb == nj) {
@@ -1646,6 +1654,8 @@ int derive_fp32_rest(emsurf_handle* h, const emsurf_problem* pr);
 namespace {
 constexpr int kOrbJB4 = 12;   // slab width of the 4-slot (x and y mirrors) orbit kernel
 constexpr int kOrbJB8 = 8;    // and of the 8-slot one (with x <-> y)
+constexpr int kOrbNT4 = 1;    // consumer threads per test row (4 accumulator sets each)
+constexpr int kOrbNT8 = 2;
 
 // bin of the group element e (bit 0: x mirror, bit 1: y mirror, bit 2:
 // x <-> y, applied first) acting on bin (kx, ky) of a px x py grid
@@ -1680,10 +1690,11 @@ int orbit_spectrum(emsurf_handle* h, const emsurf_problem* pr, const double2* B6
         }
     }
     const bool diag = (pr->sym_mask & 4) && px == py && h->nx == h->ny;
-    const int G = diag ? 8 : 4, JB = diag ? kOrbJB8 : kOrbJB4;
+    const int G = diag ? 8 : 4, JB = diag ? kOrbJB8 : kOrbJB4, NT = diag ? kOrbNT8 : kOrbNT4;
     const size_t smem = diag ? binmul_orbit_smem<8, kOrbJB8>(E) : binmul_orbit_smem<4, kOrbJB4>(E);
     const int ncw = (E + 31) / 32;
-    if (smem > 227 * 1024 || 32 * (1 + ncw) > kOrbMaxThreads || (E + JB - 1) / JB < kOrbStages) return EMSURF_OK;
+    const int maxt = diag ? orb_max_threads<kOrbNT8>() : orb_max_threads<kOrbNT4>();
+    if (smem > 227 * 1024 || 32 * (1 + NT * ncw) > maxt || (E + JB - 1) / JB < kOrbStages) return EMSURF_OK;
     // the generators' relations on the FP64 blocks
     {
         std::vector<uint32_t> pt(E);
@@ -1793,7 +1804,7 @@ int orbit_spectrum(emsurf_handle* h, const emsurf_problem* pr, const double2* B6
     const long long nslab = (long long)nst * ((E + JB - 1) / JB);
     h->pair_grid = (int)std::min<long long>(std::max(1, h->num_sms), nslab);
     EMS_TRY(dev_alloc(h, (void**)&h->d_pair_part, (size_t)h->pair_grid * 2 * G * E2 * sizeof(float2)));
-    h->pair_cnt_bytes = (size_t)nst * ncw * sizeof(int);
+    h->pair_cnt_bytes = (size_t)nst * ncw * NT * sizeof(int);
     EMS_TRY(dev_alloc(h, (void**)&h->d_pair_cnt, h->pair_cnt_bytes));
     EMS_CUDA(cudaMemsetAsync(h->d_pair_cnt, 0, h->pair_cnt_bytes, st));
     EMS_TRY(dev_alloc(h, (void**)&h->op32.Bhat, (size_t)nst * 2 * EE * sizeof(float2)));
@@ -1824,7 +1835,7 @@ int adopt_fp32_form(emsurf_handle* h, const emsurf_handle* share) {
         const int slots = h->orb32 ? h->orb_G : 2;
         h->pair_grid = share->pair_grid;
         EMS_TRY(dev_alloc(h, (void**)&h->d_pair_part, (size_t)h->pair_grid * 2 * slots * 2 * h->E * sizeof(float2)));
-        h->pair_cnt_bytes = (size_t)h->nst * ncw * sizeof(int);
+        h->pair_cnt_bytes = share->pair_cnt_bytes;
         EMS_TRY(dev_alloc(h, (void**)&h->d_pair_cnt, h->pair_cnt_bytes));
         EMS_CUDA(cudaMemsetAsync(h->d_pair_cnt, 0, h->pair_cnt_bytes, h->setup_stream));
     }
@@ -2174,17 +2185,18 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
     if constexpr (std::is_same<T2, float2>::value) {
         if (!bin_done && h->orb32) {
             // one stored bin per mirror orbit: one read serves every bin of the orbit
-            const int thr = 32 * (1 + (E + 31) / 32);
             if (h->orb_G == 8) {
+                const int thr = 32 * (1 + kOrbNT8 * ((E + 31) / 32));
                 const size_t smem = binmul_orbit_smem<8, kOrbJB8>(E);
-                EMS_TRY(set_smem_once(binmul_orbit_kernel<8, kOrbJB8>, smem));
-                binmul_orbit_kernel<8, kOrbJB8><<<h->pair_grid, thr, smem, st>>>(
+                EMS_TRY(set_smem_once(binmul_orbit_kernel<8, kOrbJB8, kOrbNT8>, smem));
+                binmul_orbit_kernel<8, kOrbJB8, kOrbNT8><<<h->pair_grid, thr, smem, st>>>(
                     op.Bhat, op.Xg, op.Yg, h->d_orb_bin, h->d_orb_elem, h->d_orb_perm, E, h->nst, 8, op.coef[0],
                     op.coef[1], op.coef[2], op.coef[3], h->d_pair_part, h->d_pair_cnt, h->d_err);
             } else {
+                const int thr = 32 * (1 + kOrbNT4 * ((E + 31) / 32));
                 const size_t smem = binmul_orbit_smem<4, kOrbJB4>(E);
-                EMS_TRY(set_smem_once(binmul_orbit_kernel<4, kOrbJB4>, smem));
-                binmul_orbit_kernel<4, kOrbJB4><<<h->pair_grid, thr, smem, st>>>(
+                EMS_TRY(set_smem_once(binmul_orbit_kernel<4, kOrbJB4, kOrbNT4>, smem));
+                binmul_orbit_kernel<4, kOrbJB4, kOrbNT4><<<h->pair_grid, thr, smem, st>>>(
                     op.Bhat, op.Xg, op.Yg, h->d_orb_bin, h->d_orb_elem, h->d_orb_perm, E, h->nst, 4, op.coef[0],
                     op.coef[1], op.coef[2], op.coef[3], h->d_pair_part, h->d_pair_cnt, h->d_err);
             }
