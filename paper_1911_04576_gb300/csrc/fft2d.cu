@@ -19,7 +19,6 @@
 namespace emsurf {
 namespace {
 
-constexpr int kF2Threads = 512;
 
 constexpr int f2_rad_count(int P) {
     int n = 0;
@@ -112,17 +111,35 @@ struct F2Stages {
     }
 };
 
-// lanes per CTA: the grid for W lanes twice (ping-pong) within ~96 KB (one
-// lane per CTA at most when the grid alone is larger)
+// lanes per CTA: at most what keeps the grid of W lanes twice (ping-pong)
+// within ~96 KB (one lane when the grid alone is larger).  The launch picks
+// the widest W that still gives two CTAs per SM: the transforms are bound by
+// the latency of their synchronised stages, so concurrency across CTAs, not
+// the width of one, sets their speed.
 template <typename T2, int P>
-constexpr int f2_lanes() {
+constexpr int f2_max_lanes() {
     constexpr int per = 2 * P * P * (int)sizeof(T2);
     return per * 8 <= 96 * 1024 ? 8 : per * 4 <= 96 * 1024 ? 4 : per * 2 <= 96 * 1024 ? 2 : 1;
 }
 
-template <typename T2, int P>
+template <typename T2, int P, int W>
 constexpr size_t f2_smem() {
-    return (size_t)(2 * P * P * f2_lanes<T2, P>() + P) * sizeof(T2);
+    return (size_t)(2 * P * P * W + P) * sizeof(T2);
+}
+
+template <int W>
+constexpr int f2_threads() { return W >= 4 ? 512 : 256; }
+
+int f2_pick_lanes(int max_w, long long lanes) {
+    static int sm_count[64] = {};      // per device, filled on first use
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) {
+        if (!sm_count[dev]) cudaDeviceGetAttribute(&sm_count[dev], cudaDevAttrMultiProcessorCount, dev);
+        if (sm_count[dev] > 0) sms = sm_count[dev];
+    }
+    for (int w = max_w; w > 1; w >>= 1)
+        if ((lanes + w - 1) / w >= 2LL * sms) return w;
+    return 1;
 }
 
 template <typename T2, int SIGN>
@@ -135,12 +152,11 @@ __device__ __forceinline__ void f2_twiddles(T2* tw, const double2* __restrict__ 
 
 // X^[ky * P + kx][lane] of x1 = U_o x (sign * x[r][uo_index[(iy nx + ix) K + k]],
 // lane = r K + k), zero outside the lattice
-template <typename T2, int P>
-__global__ void __launch_bounds__(kF2Threads)
+template <typename T2, int P, int W>
+__global__ void __launch_bounds__(f2_threads<W>())
 fft2d_fwd_kernel(T2* __restrict__ Xg, long long lanes, int nx, int ny, int K, int n_unique,
                  const double2* __restrict__ twg, const double2* __restrict__ x, const float2* __restrict__ xf,
                  const int32_t* __restrict__ idx, const int8_t* __restrict__ sgn) {
-    constexpr int W = f2_lanes<T2, P>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T2* b0 = reinterpret_cast<T2*>(smem_raw);
     T2* b1 = b0 + P * P * W;
@@ -190,12 +206,11 @@ fft2d_fwd_kernel(T2* __restrict__ Xg, long long lanes, int nx, int ny, int K, in
 
 // y1[r][iy nx + ix][k] = scale * IFFT2(Y^)[iy][ix] + sum_s mm[s][r][m][k] for
 // the lattice points (the crop of the circulant embedding)
-template <typename T2, int P>
-__global__ void __launch_bounds__(kF2Threads)
+template <typename T2, int P, int W>
+__global__ void __launch_bounds__(f2_threads<W>())
 fft2d_inv_kernel(const T2* __restrict__ Yg, long long lanes, int nx, int ny, int K, int M, int R,
                  int nsplit, double scale, const double2* __restrict__ twg, const T2* __restrict__ mm,
                  T2* __restrict__ y1) {
-    constexpr int W = f2_lanes<T2, P>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T2* b0 = reinterpret_cast<T2*>(smem_raw);
     T2* b1 = b0 + P * P * W;
@@ -241,28 +256,48 @@ fft2d_inv_kernel(const T2* __restrict__ Yg, long long lanes, int nx, int ny, int
     }
 }
 
-template <typename T2, int P>
-int f2_fwd(T2* Xg, long long lanes, int nx, int ny, int K, int n_unique, const double2* tw, const double2* x,
-           const float2* xf, const int32_t* idx, const int8_t* sgn, cudaStream_t st) {
-    constexpr int W = f2_lanes<T2, P>();
-    constexpr size_t smem = f2_smem<T2, P>();
-    EMS_TRY(set_smem_once(fft2d_fwd_kernel<T2, P>, smem));
-    fft2d_fwd_kernel<T2, P><<<(unsigned)((lanes + W - 1) / W), kF2Threads, smem, st>>>(Xg, lanes, nx, ny, K,
-                                                                                     n_unique, tw, x, xf, idx, sgn);
+template <typename T2, int P, int W>
+int f2_fwd_w(T2* Xg, long long lanes, int nx, int ny, int K, int n_unique, const double2* tw, const double2* x,
+             const float2* xf, const int32_t* idx, const int8_t* sgn, cudaStream_t st) {
+    constexpr size_t smem = f2_smem<T2, P, W>();
+    EMS_TRY(set_smem_once(fft2d_fwd_kernel<T2, P, W>, smem));
+    fft2d_fwd_kernel<T2, P, W><<<(unsigned)((lanes + W - 1) / W), f2_threads<W>(), smem, st>>>(
+        Xg, lanes, nx, ny, K, n_unique, tw, x, xf, idx, sgn);
+    EMS_CUDA(cudaGetLastError());
+    return EMSURF_OK;
+}
+
+template <typename T2, int P, int W>
+int f2_inv_w(const T2* Yg, long long lanes, int nx, int ny, int K, int M, int R, int nsplit, double scale,
+             const double2* tw, const T2* mm, T2* y1, cudaStream_t st) {
+    constexpr size_t smem = f2_smem<T2, P, W>();
+    EMS_TRY(set_smem_once(fft2d_inv_kernel<T2, P, W>, smem));
+    fft2d_inv_kernel<T2, P, W><<<(unsigned)((lanes + W - 1) / W), f2_threads<W>(), smem, st>>>(
+        Yg, lanes, nx, ny, K, M, R, nsplit, scale, tw, mm, y1);
     EMS_CUDA(cudaGetLastError());
     return EMSURF_OK;
 }
 
 template <typename T2, int P>
+int f2_fwd(T2* Xg, long long lanes, int nx, int ny, int K, int n_unique, const double2* tw, const double2* x,
+           const float2* xf, const int32_t* idx, const int8_t* sgn, cudaStream_t st) {
+    constexpr int MW = f2_max_lanes<T2, P>();
+    const int w = f2_pick_lanes(MW, lanes);
+    if constexpr (MW >= 8) if (w == 8) return f2_fwd_w<T2, P, 8>(Xg, lanes, nx, ny, K, n_unique, tw, x, xf, idx, sgn, st);
+    if constexpr (MW >= 4) if (w == 4) return f2_fwd_w<T2, P, 4>(Xg, lanes, nx, ny, K, n_unique, tw, x, xf, idx, sgn, st);
+    if constexpr (MW >= 2) if (w == 2) return f2_fwd_w<T2, P, 2>(Xg, lanes, nx, ny, K, n_unique, tw, x, xf, idx, sgn, st);
+    return f2_fwd_w<T2, P, 1>(Xg, lanes, nx, ny, K, n_unique, tw, x, xf, idx, sgn, st);
+}
+
+template <typename T2, int P>
 int f2_inv(const T2* Yg, long long lanes, int nx, int ny, int K, int M, int R, int nsplit, double scale,
            const double2* tw, const T2* mm, T2* y1, cudaStream_t st) {
-    constexpr int W = f2_lanes<T2, P>();
-    constexpr size_t smem = f2_smem<T2, P>();
-    EMS_TRY(set_smem_once(fft2d_inv_kernel<T2, P>, smem));
-    fft2d_inv_kernel<T2, P><<<(unsigned)((lanes + W - 1) / W), kF2Threads, smem, st>>>(
-        Yg, lanes, nx, ny, K, M, R, nsplit, scale, tw, mm, y1);
-    EMS_CUDA(cudaGetLastError());
-    return EMSURF_OK;
+    constexpr int MW = f2_max_lanes<T2, P>();
+    const int w = f2_pick_lanes(MW, lanes);
+    if constexpr (MW >= 8) if (w == 8) return f2_inv_w<T2, P, 8>(Yg, lanes, nx, ny, K, M, R, nsplit, scale, tw, mm, y1, st);
+    if constexpr (MW >= 4) if (w == 4) return f2_inv_w<T2, P, 4>(Yg, lanes, nx, ny, K, M, R, nsplit, scale, tw, mm, y1, st);
+    if constexpr (MW >= 2) if (w == 2) return f2_inv_w<T2, P, 2>(Yg, lanes, nx, ny, K, M, R, nsplit, scale, tw, mm, y1, st);
+    return f2_inv_w<T2, P, 1>(Yg, lanes, nx, ny, K, M, R, nsplit, scale, tw, mm, y1, st);
 }
 
 }  // namespace

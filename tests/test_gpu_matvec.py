@@ -259,12 +259,14 @@ def test_double_single_outside_fp32_range(emsurf_lib, sx, sop):
 
 
 @pytest.mark.parametrize("n,nx,ny,P,R", [(2, 4, 4, 8, 1), (2, 3, 3, 5, 3), (2, 8, 7, 16, 2), (1, 12, 12, 24, 2),
-                                         (2, 16, 16, 32, 1), (1, 20, 24, 48, 1)])
+                                         (2, 16, 16, 32, 1), (1, 20, 24, 48, 1), (2, 16, 16, 32, 5),
+                                         (2, 6, 6, 16, 9)])
 def test_fused_2d_fft_matches_passes(emsurf_lib, n, nx, ny, P, R):
     """Square grids up to 64 x 64 take the fused 2-D transforms (gather, both
     passes and the crop/epilogue in one launch each); a taller grid takes the
     pass-based ones.  Both embeddings are exact (any grid >= 2N - 1),
-    so FP64 products agree to rounding and both match the oracle."""
+    so FP64 products agree to rounding and both match the oracle.  The lane
+    counts (rhs x 2E) cover one, two and four lanes per CTA."""
     from paper_1911_04576_gb300 import binding as B
     seed = 1300 + P + nx
     E, idx, sgn, nu, Lt, Kt, Z, tmap = random_case(n, nx, ny, 2, seed)
