@@ -509,6 +509,9 @@ def serve_requests(B, W, nreq, seed, precision, precond, rate=SERVE_RATE):
     return arrivals, reqs
 
 
+_ABANDONED = []     # servers left with a request that did not end (kept alive, never destroyed)
+
+
 def serve_stream(B, W, arrivals, reqs, max_active, cache, window_s):
     """Submit the requests at their arrival times (those arriving within
     window_s); when the window closes, withdraw the ones still queued and
@@ -517,6 +520,7 @@ def serve_stream(B, W, arrivals, reqs, max_active, cache, window_s):
     makespan."""
     sv = B.emsurf_server_create(0, SERVE_BUDGET, max_active, cache=cache)
     pending, res, refused, offered = [], [], 0, 0
+    described = {}
 
     def collect():
         keep = []
@@ -537,7 +541,9 @@ def serve_stream(B, W, arrivals, reqs, max_active, cache, window_s):
         offered += 1
         q, keep = B.make_request(**r)
         try:
-            pending.append(B.emsurf_submit(sv, q, keep))
+            t = B.emsurf_submit(sv, q, keep)
+            pending.append(t)
+            described[t] = {"nx": r["nx"], "n": r["n"], "rhs": len(r["khat"]), "arrival_s": round(float(at), 2)}
         except B.EmsurfError as e:
             if e.status != B.EMSURF_EBUSY:
                 raise
@@ -548,13 +554,29 @@ def serve_stream(B, W, arrivals, reqs, max_active, cache, window_s):
         pending = collect()
     withdrawn = sum(1 for t in pending if B.emsurf_cancel(sv, t))
     _log("serve window closed", {"completed": len(res), "withdrawn": withdrawn, "running": len(pending) - withdrawn})
+    # the running requests: their solves end within max_ms; a request that
+    # has not ended well after that is reported and left behind (the server
+    # is then not destroyed, which would wait for it)
+    unfinished = []
     for t in pending:
-        r = B.emsurf_wait(sv, t, 3600 * 1000)
+        try:
+            r = B.emsurf_wait(sv, t, int(SERVE_MAX_MS + 180000))
+        except B.EmsurfError as e:
+            if e.status != B.EMSURF_ETIMEDOUT:
+                raise
+            d = dict(described.get(t) or {})
+            d["phase"] = B.emsurf_request_phase(sv, t)
+            unfinished.append(d)
+            continue
         if r["status"] != B.EMSURF_ECANCELED:
             res.append(r)
     makespan = time.perf_counter() - t0
     stats = B.emsurf_server_stats(sv)
-    sv.close()
+    if unfinished:
+        _log("serve: requests still running at the end", unfinished)
+        _ABANDONED.append(sv)
+    else:
+        sv.close()
     lat = np.array([r["latency_ms"] for r in res]) if res else np.zeros(1)
     mean = lambda k: round(float(np.mean([r[k] for r in res])), 1) if res else None
     offered_span = float(arrivals[offered - 1]) if offered else 0.0
@@ -569,7 +591,7 @@ def serve_stream(B, W, arrivals, reqs, max_active, cache, window_s):
             "setup_ms_mean": mean("setup_ms"), "solve_ms_mean": mean("solve_ms"),
             "cache_hits": int(sum(r["cache_hit"] for r in res)),
             "cache": {"bytes": stats[0], "operators": stats[1], "libraries": stats[2], "evictions": stats[3]},
-            "max_active": max_active}
+            "max_active": max_active, "unfinished": unfinished}
 
 
 def serve_section(B, W, nreq, rate):
@@ -925,7 +947,12 @@ def main():
         "setup": setup,
         "device_bytes": dev_bytes,
     }
-    print(json.dumps(out))
+    print(json.dumps(out), flush=True)
+    if _ABANDONED:
+        # a server still holds a request that did not end: leave without
+        # the teardown that would wait for it
+        sys.stderr.flush()
+        os._exit(0)
     if dist:
         dist.destroy_process_group()
 

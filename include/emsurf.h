@@ -145,7 +145,7 @@ typedef struct {
     int32_t max_refine;   /* MIXED only: outer FP64 refinement steps           */
     double inner_rtol;    /* MIXED only: floor of the inner FP32 solve tolerance,
                              which is max(floor, 0.5 rtol / current residual)
-                             (0 = 1e-6)                                        */
+                             (0 = 2.5e-7; 3e-5 on the tensor-core operator)   */
     int32_t solver;       /* 0: by handle precision; 1: FP64-operator GMRES;
                              2: FP32-operator GMRES; 3: mixed refinement.
                              The operators it needs must be resident.         */
@@ -583,6 +583,20 @@ EMSURF_API int emsurf_poll(emsurf_server* s, uint64_t ticket, emsurf_result* out
 /* As poll, but blocks up to timeout_ms; ETIMEDOUT if not done by then.    */
 EMSURF_API int emsurf_wait(emsurf_server* s, uint64_t ticket, int64_t timeout_ms,
                            emsurf_result* out);
+/* Where a request is: queued, admitted, building (or waiting for another
+ * request to build) the cell library or the lattice's operator, solving,
+ * done.  EINVAL for an unknown (or already collected) ticket.            */
+enum {
+    EMSURF_PHASE_QUEUED = 0,
+    EMSURF_PHASE_ADMITTED = 1,
+    EMSURF_PHASE_LIBRARY = 2,
+    EMSURF_PHASE_WAIT_LIBRARY = 3,
+    EMSURF_PHASE_WAIT_OPERATOR = 4,
+    EMSURF_PHASE_OPERATOR = 5,
+    EMSURF_PHASE_SOLVE = 6,
+    EMSURF_PHASE_DONE = 7
+};
+EMSURF_API int emsurf_request_phase(emsurf_server* s, uint64_t ticket, int32_t* phase);
 /* Withdraws a request that is still queued (not yet admitted): OK, and its
  * result (collected by poll/wait) has status ECANCELED; EBUSY once it runs
  * (its opts.max_ms bounds it); EINVAL for an unknown ticket.             */

@@ -518,6 +518,7 @@ def _serve_lib():
         L.emsurf_poll.argtypes = [vp, C.c_uint64, C.POINTER(Result)]
         L.emsurf_wait.argtypes = [vp, C.c_uint64, C.c_int64, C.POINTER(Result)]
         L.emsurf_cancel.argtypes = [vp, C.c_uint64]
+        L.emsurf_request_phase.argtypes = [vp, C.c_uint64, C.POINTER(C.c_int32)]
         L.emsurf_server_destroy.argtypes = [vp]
         L.emsurf_server_destroy.restype = None
         L.emsurf_server_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
@@ -614,6 +615,16 @@ def emsurf_cancel(server, ticket):
     already runs or ran (its result is then collected as usual)."""
     st = _check(_serve_lib().emsurf_cancel(server.ptr, ticket), ok=(EMSURF_OK, EMSURF_EBUSY))
     return st == EMSURF_OK
+
+
+REQUEST_PHASES = ("queued", "admitted", "library", "wait_library", "wait_operator", "operator", "solve", "done")
+
+
+def emsurf_request_phase(server, ticket):
+    """emsurf_request_phase: the request's phase as a name (REQUEST_PHASES)."""
+    ph = C.c_int32()
+    _check(_serve_lib().emsurf_request_phase(server.ptr, ticket, C.byref(ph)))
+    return REQUEST_PHASES[ph.value]
 
 
 def emsurf_server_stats(server):

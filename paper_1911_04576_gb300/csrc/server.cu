@@ -24,6 +24,7 @@
 // what the budget has left; a request that cannot fit even in an empty
 // server is refused at submit (EMSURF_EBUSY).
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -64,6 +65,7 @@ struct Job {
     bool done = false;
     int64_t peak_bytes = 0;
     int64_t new_bytes = 0;         // cache entries this job created
+    std::atomic<int> phase{0};     // EMSURF_PHASE_* (emsurf_request_phase)
 };
 
 // the cache keys: the operator's (geometry, lattice, wavenumber, precision,
@@ -246,27 +248,35 @@ Entry* wait_entry(emsurf_server* sv, std::map<std::string, Entry>& m, const std:
 
 int run_job(emsurf_server* sv, Job& jb, cudaStream_t st) {
     const emsurf_request& q = jb.req;
-    EMS_CUDA(cudaSetDevice(sv->device));
+    // no early return below: the cache entries this job was admitted to
+    // build must be published or dropped, or the jobs waiting on them would
+    // wait for ever
+    int s = EMSURF_OK;
+    if (cudaSetDevice(sv->device) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("server: cudaSetDevice failed");
+        s = EMSURF_ECUDA;
+    }
     const int E = 18 * q.n * q.n, K = 2 * E, M = q.nx * q.ny;
     std::vector<int32_t> idx((size_t)M * K);
     std::vector<int8_t> sgn((size_t)M * K);
     int32_t nu = 0;
-    EMS_TRY(emsurf_setup_overlap(q.n, q.nx, q.ny, idx.data(), sgn.data(), &nu));
+    if (!s) s = emsurf_setup_overlap(q.n, q.nx, q.ny, idx.data(), sgn.data(), &nu);
     jb.n_unique = nu;
     // slab cells: box rows end at the slab top (junction with S_eq)
     std::vector<double> zl;
-    if (q.slab_t > 0.0) {
+    if (!s && q.slab_t > 0.0) {
         zl.resize(q.n + 1);
-        EMS_TRY(emsurf_setup_slab_zlevels(q.h, q.n, q.slab_t, zl.data()));
+        s = emsurf_setup_slab_zlevels(q.h, q.n, q.slab_t, zl.data());
     }
     const double* zp = zl.empty() ? nullptr : zl.data();
-    int s = EMSURF_OK;
     // ---- macromodel library (cached across lattices)
     void* Z = nullptr;
     MmEntry* me = nullptr;
     if (sv->cache_on) {
         if (jb.mm_build) {
-            s = build_library(q, jb, zp, &Z, st);
+            jb.phase = EMSURF_PHASE_LIBRARY;
+            if (!s) s = build_library(q, jb, zp, &Z, st);
             std::lock_guard<std::mutex> lk(sv->mu);
             me = &sv->mms[jb.mm_key];
             if (s) {
@@ -281,15 +291,17 @@ int run_job(emsurf_server* sv, Job& jb, cudaStream_t st) {
             }
             sv->cv_cache.notify_all();
         } else {
+            jb.phase = EMSURF_PHASE_WAIT_LIBRARY;
             std::unique_lock<std::mutex> lk(sv->mu);
             me = wait_entry(sv, sv->mms, jb.mm_key, lk);
             if (me) Z = me->Z;
-            else {
+            else if (!s) {
                 set_error("server: the cell library's macromodels could not be built");
                 s = EMSURF_ECUDA;
             }
         }
-    } else {
+    } else if (!s) {
+        jb.phase = EMSURF_PHASE_LIBRARY;
         s = build_library(q, jb, zp, &Z, st);
     }
     // ---- the operator: a cached full handle, or a new one
@@ -302,6 +314,7 @@ int run_job(emsurf_server* sv, Job& jb, cudaStream_t st) {
         if (jb.op_build) {
             oe = &sv->ops[jb.op_key];
         } else {
+            jb.phase = EMSURF_PHASE_WAIT_OPERATOR;
             oe = wait_entry(sv, sv->ops, jb.op_key, lk);
             if (oe) base = oe->h;
             else if (!s) {
@@ -350,6 +363,7 @@ int run_job(emsurf_server* sv, Job& jb, cudaStream_t st) {
             p.precond_overlap = q.precond_overlap;
         }
     }
+    jb.phase = EMSURF_PHASE_OPERATOR;
     if (!s && base) {
         s = emsurf_create_like(&p, base, &hd);
     } else if (!s) {
@@ -398,6 +412,7 @@ int run_job(emsurf_server* sv, Job& jb, cudaStream_t st) {
     if (!s) s = emsurf_excitation(hd, q.a, q.b, q.h, q.n, zp, q.k0, q.nrhs, jb.khat.data(), jb.ehat.data(),
                                   static_cast<emsurf_c128*>(V), st);
     jb.t_setup = Clock::now();
+    jb.phase = EMSURF_PHASE_SOLVE;
     if (!s) {
         jb.info.assign(q.nrhs, emsurf_solve_info{});
         s = emsurf_solve(hd, static_cast<emsurf_c128*>(V), static_cast<emsurf_c128*>(X), q.nrhs, &q.opts,
@@ -507,6 +522,7 @@ void worker_main(emsurf_server* sv) {
                             j.mm_build = !mm_c;
                         }
                         jb = *it;
+                        jb->phase = EMSURF_PHASE_ADMITTED;
                         sv->queue.erase(it);
                         break;
                     }
@@ -659,6 +675,18 @@ EMSURF_API int emsurf_wait(emsurf_server* sv, uint64_t ticket, int64_t timeout_m
     }
     fill_result(*jb, out);
     sv->jobs.erase(ticket);
+    return EMSURF_OK;
+}
+
+EMSURF_API int emsurf_request_phase(emsurf_server* sv, uint64_t ticket, int32_t* phase) {
+    if (!sv || !phase) { set_error("emsurf_request_phase: NULL argument"); return EMSURF_EINVAL; }
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->jobs.find(ticket);
+    if (it == sv->jobs.end()) {
+        set_error("emsurf_request_phase: unknown ticket %llu", (unsigned long long)ticket);
+        return EMSURF_EINVAL;
+    }
+    *phase = it->second->done ? EMSURF_PHASE_DONE : it->second->phase.load();
     return EMSURF_OK;
 }
 
