@@ -508,7 +508,17 @@ void worker_main(emsurf_server* sv) {
                     const bool op_c = sv->cache_on && sv->ops.count(j.op_key);
                     const bool mm_c = sv->cache_on && sv->mms.count(j.mm_key);
                     const int64_t need = op_c ? e.shared(mm_c) : e.full() - (mm_c ? e.library : 0);
-                    if (make_room(sv, need)) {
+                    // the entries this job would reuse stay pinned while room
+                    // is made: evicting one of them here would leave the job
+                    // waiting for an entry that nobody builds
+                    OpEntry* pin_op = op_c ? &sv->ops[j.op_key] : nullptr;
+                    MmEntry* pin_mm = mm_c ? &sv->mms[j.mm_key] : nullptr;
+                    if (pin_op) pin_op->refs += 1;
+                    if (pin_mm) pin_mm->refs += 1;
+                    const bool room = make_room(sv, need);
+                    if (pin_op) pin_op->refs -= 1;
+                    if (pin_mm) pin_mm->refs -= 1;
+                    if (room) {
                         j.est = need;
                         j.hit = op_c;
                         if (sv->cache_on) {

@@ -181,3 +181,32 @@ def test_solve_wall_time_limit(emsurf_lib):
     with pytest.raises(B.EmsurfError):
         B.emsurf_solve(h, V, X, rtol=1e-6, max_ms=-1.0)
     h.close()
+
+
+def test_admission_keeps_the_library_it_reuses(emsurf_lib):
+    """A second lattice of the same cell library under a budget that forces
+    eviction: room is made by evicting the first lattice's operator, never
+    the library the new request was admitted to reuse (evicting it would
+    leave the request waiting for an entry nobody builds)."""
+    from paper_1911_04576_gb300 import binding as B
+    rng = np.random.default_rng(11)
+    n, T = 2, 3
+    sides = rng.uniform(0.15, 0.45, T) * W.LAMBDA
+    reqs = []
+    for nx in (4, 5):
+        waves = [W.plane_waves(W.Workload("w", 1, 1, 1, 1, 0, 0, angles=[(20.0, 0.0, "theta")]))[0]]
+        reqs.append(dict(a=A, b=A, h=H, n=n, nx=nx, ny=nx, k0=W.K0, patch_sides=sides, patch_z=W.PATCH_Z,
+                         patch_n=3, type_map=rng.integers(0, T, nx * nx), khat=np.array([w_[0] for w_ in waves]),
+                         ehat=np.array([w_[1] for w_ in waves]), precision=B.MIXED, rtol=1e-8, restart=30,
+                         max_iters=6000, slab_t=W.SLAB_T, slab_eps=W.EPS_SLAB, ring_layers=2))
+    qs = [B.make_request(**r) for r in reqs]
+    need = max(B.emsurf_request_bytes(q) for q, _ in qs)
+    sv = B.emsurf_server_create(0, int(need * 1.1), 1, cache=True)
+    res = []
+    for q, keep in qs:
+        t = B.emsurf_submit(sv, q, keep)
+        res.append(B.emsurf_wait(sv, t, 300000))      # ETIMEDOUT (raised) if it waits for ever
+    stats = B.emsurf_server_stats(sv)
+    sv.close()
+    assert all(r["status"] == B.EMSURF_OK for r in res)
+    assert stats[2] == 1 and stats[3] >= 1           # one library kept, the first operator evicted
