@@ -201,7 +201,8 @@ def test_admission_keeps_the_library_it_reuses(emsurf_lib):
                          max_iters=6000, slab_t=W.SLAB_T, slab_eps=W.EPS_SLAB, ring_layers=2))
     qs = [B.make_request(**r) for r in reqs]
     need = max(B.emsurf_request_bytes(q) for q, _ in qs)
-    sv = B.emsurf_server_create(0, int(need * 1.1), 1, cache=True)
+    # room for one request's build: the second forces an eviction
+    sv = B.emsurf_server_create(0, need + (1 << 20), 1, cache=True)
     res = []
     for q, keep in qs:
         t = B.emsurf_submit(sv, q, keep)
