@@ -477,10 +477,10 @@ SERVE_MESH = (3, 4)            # boxes meshed n x n: K = 324 or 576
 SERVE_RHS = tuple(range(1, 17))   # rhs per request, uniform in 1..16
 SERVE_RATE = 1.0               # Poisson arrivals per second (default; --serve-rate)
 SERVE_MAX_MS = 20000.0         # wall-time limit of each request's solve
-SERVE_DRAIN_S = 30.0           # after the last arrival: queued requests are withdrawn
+SERVE_DRAIN_S = 20.0           # after the last arrival: queued requests are withdrawn
 SERVE_BUDGET = 80 << 30        # device-memory budget of the server
-SERVE_FP64_SAMPLE = 6         # requests of the one-at-a-time FP64 arm
-SERVE_FP64_WINDOW_S = 45.0     # and its window (later requests are withdrawn)
+SERVE_FP64_SAMPLE = 4         # requests of the one-at-a-time FP64 arm
+SERVE_FP64_WINDOW_S = 30.0     # and its window (later requests are withdrawn)
 
 
 def serve_requests(B, W, nreq, seed, precision, precond, rate=SERVE_RATE):
@@ -663,7 +663,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--multi-rhs", type=int, default=1,
                     help="also time %d-rhs FP32 products, tensor cores vs FP32 kernels (0 = skip)" % 32)
-    ap.add_argument("--serve-requests", type=int, default=40,
+    ap.add_argument("--serve-requests", type=int, default=24,
                     help="requests of the serving stream (0 = skip the serving measurement)")
     ap.add_argument("--serve-rate", type=float, default=SERVE_RATE,
                     help="Poisson arrival rate of the serving stream (requests per second)")

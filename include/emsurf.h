@@ -145,7 +145,7 @@ typedef struct {
     int32_t max_refine;   /* MIXED only: outer FP64 refinement steps           */
     double inner_rtol;    /* MIXED only: floor of the inner FP32 solve tolerance,
                              which is max(floor, 0.5 rtol / current residual)
-                             (0 = 2.5e-7; 3e-5 on the tensor-core operator)   */
+                             (0 = 1e-6; 3e-5 on the tensor-core operator)     */
     int32_t solver;       /* 0: by handle precision; 1: FP64-operator GMRES;
                              2: FP32-operator GMRES; 3: mixed refinement.
                              The operators it needs must be resident.         */

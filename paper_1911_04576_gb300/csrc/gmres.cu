@@ -1081,11 +1081,11 @@ int gmres_solve(emsurf_handle* h, const double2* b, double2* x, int R, const ems
     if (mode == 3) {
         // inner tolerance: the part of the remaining reduction that is still
         // needed (half of it), but not below what an FP32 operator can
-        // resolve (~1e-7 relative; the default floor 2.5e-7 keeps a margin),
+        // resolve (~1e-7 relative; the default floor 1e-6 keeps a margin),
         // so that one inner solve usually reaches rtol and the FP64 residual
         // only confirms it
         // (the BF16x3 tensor-core operator resolves ~3e-5, the FP32 one ~1e-7)
-        const double inner = o->inner_rtol > 0 ? o->inner_rtol : (h->have_tc && R >= kTcMinRhs ? 3e-5 : 2.5e-7);
+        const double inner = o->inner_rtol > 0 ? o->inner_rtol : (h->have_tc && R >= kTcMinRhs ? 3e-5 : 1e-6);
         bool zero = true;
         while (true) {
             // FP64 residual r = b - A64 x (x = 0 on the first pass)
