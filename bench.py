@@ -51,8 +51,9 @@ BINMUL_DRAM_BYTES_PER_BIN = (767108096 + 5353216) / 576
 # the same for binmul_tma_pair_kernel (half spectrum) per stored bin, from
 # the capture of the 12x12 lattice (290 stored bins)
 PAIR_DRAM_BYTES_PER_STORED_BIN = (387588096 + 3930624) / 290
-# binmul_orbit_kernel (one stored bin per mirror orbit): no capture yet
-ORBIT_DRAM_BYTES_PER_STORED_BIN = None
+# binmul_orbit_kernel (one stored bin per mirror orbit of 8), from the capture
+# of the 16x16 lattice itself (153 stored bins)
+ORBIT_DRAM_BYTES_PER_STORED_BIN = (207879936 + 4441344) / 153
 
 
 FALLBACK_BF16_TFLOPS = 1900.0
@@ -78,6 +79,36 @@ def bf16_peak():
 
 
 MULTI_RHS = 32
+
+
+def mirror_orbit_section(B, W, torch, w, steps):
+    """The same solve on a handle that stores one FP32 bin per mirror orbit
+    (153 of 1024 bins at 16x16) instead of one per (k, -k) pair: time per
+    solve, per bin multiply and per FP32 product."""
+    h, V, nu, _, _ = build_problem(B, W, torch, w, B.MIXED, mirrors=True)
+    X = torch.zeros_like(V)
+    kw = dict(rtol=RTOL, restart=RESTART, max_iters=20000, max_refine=20, solver=B.SOLVER_MIXED)
+    for _ in range(2):
+        B.emsurf_solve(h, V, X, **kw)
+    B.emsurf_profile_phases(h, ["binmul32"])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        st, info = B.emsurf_solve(h, V, X, **kw)
+    e1.record()
+    torch.cuda.synchronize()
+    B.emsurf_profile(h, False)
+    bin_ms, bin_n = B.emsurf_profile_read(h, "binmul32")
+    form, per = B.emsurf_operator_layout(h)
+    out = {"form": "one stored bin per mirror orbit of %d" % per if form == 2 else "form %d" % form,
+           "stored_bins": B.emsurf_operator_info(h)[0], "solve_ms": round(e0.elapsed_time(e1) / steps, 3),
+           "iters": info[0]["iters"], "refinements": info[0]["refinements"],
+           "binmul_ms_per_product": round(bin_ms / max(bin_n, 1), 5),
+           "fp32_matvec_ms": round(time_matvec(B, torch, h, nu, 1, B.FP32), 4)}
+    h.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def multi_rhs_section(B, W, torch, w, hbm):
@@ -403,7 +434,7 @@ def dist_init():
     return ws, rank, local
 
 
-def build_problem(B, W, torch, w, precision, precond=True, max_rhs=None, tensor_cores=False):
+def build_problem(B, W, torch, w, precision, precond=True, max_rhs=None, tensor_cores=False, mirrors=False):
     """Product-path setup (untimed): U_o, tables, macromodels, handle with
     the near-field preconditioner, V."""
     A, H = W.PERIOD, W.BOX_H
@@ -427,7 +458,8 @@ def build_problem(B, W, torch, w, precision, precond=True, max_rhs=None, tensor_
                         precision=precision, max_rhs=max_rhs or w.n_rhs, tables_on_device=True,
                         unknown_xy=xy, cell=(A, A),
                         precond_overlap=PC_OVERLAP * A / w.n if precond else 0.0,
-                        tensor_cores=tensor_cores, mirrors=B.emsurf_setup_box_mirrors(A, A, w.n))
+                        tensor_cores=tensor_cores,
+                        mirrors=B.emsurf_setup_box_mirrors(A, A, w.n) if mirrors else None)
     torch.cuda.synchronize()
     t_create = time.time() - t0
     del L, K, Z
@@ -665,6 +697,8 @@ def main():
                     help="also time %d-rhs FP32 products, tensor cores vs FP32 kernels (0 = skip)" % 32)
     ap.add_argument("--serve-requests", type=int, default=24,
                     help="requests of the serving stream (0 = skip the serving measurement)")
+    ap.add_argument("--mirror-orbits", type=int, default=1,
+                    help="also time the solve on a handle with one FP32 bin per mirror orbit (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=SERVE_RATE,
                     help="Poisson arrival rate of the serving stream (requests per second)")
     ap.add_argument("--matvecs-only", type=int, default=0,
@@ -814,6 +848,9 @@ def main():
     # ------------------------------------------------------------ accuracy
     accuracy = accuracy_section(B, torch, h, V, X, w, zl) if args.accuracy else None
     _log("accuracy", accuracy)
+    # ------------------------------------------------------------ mirror orbits
+    orbits = mirror_orbit_section(B, W, torch, w, min(args.steps, 10)) if args.mirror_orbits else None
+    _log("mirror_orbits", orbits)
     # ------------------------------------------------------------ many rhs
     multi = multi_rhs_section(B, W, torch, w, hbm) if args.multi_rhs else None
     _log("multi_rhs", multi)
@@ -938,6 +975,7 @@ def main():
                 "d2h_bytes_per_step": int(V.numel() * 16)},
         "gpu_launches": int(launches),
         "clocks": clk,
+        "mirror_orbits": orbits,
         "multi_rhs": multi,
         "accuracy": accuracy,
         "batched": batched,

@@ -112,10 +112,10 @@ struct F2Stages {
 };
 
 // lanes per CTA: at most what keeps the grid of W lanes twice (ping-pong)
-// within ~96 KB (one lane when the grid alone is larger).  The launch picks
-// the widest W that still gives two CTAs per SM: the transforms are bound by
-// the latency of their synchronised stages, so concurrency across CTAs, not
-// the width of one, sets their speed.
+// within ~96 KB (one lane when the grid alone is larger).  The launch takes
+// the widest W while that still gives at least one CTA per SM (measured at
+// 16x16, K = 576, one rhs: W = 4 with 512 threads 10.1 + 12.2 us per
+// forward + inverse pair, W = 1 with 256 threads 12.3 + 13.7 us).
 template <typename T2, int P>
 constexpr int f2_max_lanes() {
     constexpr int per = 2 * P * P * (int)sizeof(T2);
@@ -138,7 +138,7 @@ int f2_pick_lanes(int max_w, long long lanes) {
         if (sm_count[dev] > 0) sms = sm_count[dev];
     }
     for (int w = max_w; w > 1; w >>= 1)
-        if ((lanes + w - 1) / w >= 2LL * sms) return w;
+        if ((lanes + w - 1) / w >= (long long)sms * 9 / 10) return w;
     return 1;
 }
 
