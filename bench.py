@@ -40,7 +40,7 @@ RESTART = 30
 # GMRES is the same algorithm on the same operator, so it needs the same
 # count; it is counted by the GPU solve (the bench line's fp64_plain.n_matvec)
 # because the oracle, at ~1.8 s per product, would need over two hours.
-REF_MATVECS_PER_SOLVE = 4389
+REF_MATVECS_PER_SOLVE = 4129
 FALLBACK_HBM_GBS = 6800.0
 PC_OVERLAP = 1.0               # preconditioner margin, in mesh cells (a / n)
 # DRAM bytes (read + write) per bin of one binmul_tma_kernel launch, from an
@@ -707,6 +707,8 @@ def main():
                     help="operators kept resident (--matvecs-only)")
     ap.add_argument("--rhs", type=int, default=0,
                     help="profiler driver: right-hand sides of the --matvecs-only products")
+    ap.add_argument("--mirrors", type=int, default=0,
+                    help="profiler driver: give the handle the box's mirrors (--matvecs-only)")
     ap.add_argument("--tensor-cores", action="store_true",
                     help="profiler driver: build the tensor-core planes (--matvecs-only)")
     ap.add_argument("--batched", type=int, default=1,
@@ -739,7 +741,7 @@ def main():
         prec = {"mixed": B.MIXED, "fp32": B.FP32, "fp64": B.FP64}[args.precision]
         R = args.rhs or w.n_rhs
         h, V, nu, _, _ = build_problem(B, W, torch, w, prec, max_rhs=max(R, w.n_rhs),
-                                    tensor_cores=args.tensor_cores)
+                                    tensor_cores=args.tensor_cores, mirrors=bool(args.mirrors))
         for p in ((B.FP32,) if prec == B.FP32 else (B.FP64,) if prec == B.FP64 else (B.FP32, B.FP64)):
             x = torch.randn((R, nu), dtype=torch.complex128, device="cuda")
             y = torch.empty_like(x)

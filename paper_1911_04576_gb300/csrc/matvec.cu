@@ -2020,6 +2020,18 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
     const int ph_fft = f64 ? EMS_PH_FFT64 : EMS_PH_FFT32;
     const int ph_bin = f64 ? EMS_PH_BINMUL64 : EMS_PH_BINMUL32;
     const int ph_mm = f64 ? EMS_PH_MM64 : EMS_PH_MM32;
+    // K4 runs on the handle's side stream (it reads only x and writes only
+    // the partials Ymm that the inverse transform adds).  FP32 products fork
+    // before the forward transform, so the macromodel product starts while
+    // the transform runs; FP64-accuracy products fork after the per-rhs
+    // scales it reads.  The tensor-core variant (>= 8 rhs) stays on the
+    // caller's stream.
+    const bool side = h->side_stream && !(h->have_tc && R >= kTcMinRhs);
+    const bool early_fork = side && std::is_same<T2, float2>::value;
+    if (early_fork) {
+        EMS_CUDA(cudaEventRecord(h->ev_fork, st));
+        EMS_CUDA(cudaStreamWaitEvent(h->side_stream, h->ev_fork, 0));
+    }
     prof_mark(h, ph_fft, true, st);
     // K1: x-pass over the cell rows iy < ny reading x1 = U_o x directly
     // (points ix >= nx are the zero padding), then the y-pass with rows
@@ -2045,16 +2057,12 @@ int apply_operator_io(emsurf_handle* h, Operator<T2>& op, const double2* x, cons
             h->launches += 1;
         }
     }
-    // K4 runs on the handle's side stream, beside the forward transform and
-    // the bin multiply (it reads only x and writes only the partials Ymm the
-    // inverse transform adds): its L2- and FP32-bound work overlaps their
-    // HBM-bound streaming.  The tensor-core variant (>= 8 rhs) stays on the
-    // caller's stream.
-    const bool side = h->side_stream && !(h->have_tc && R >= kTcMinRhs);
     cudaStream_t mst = st;
     if (side) {
-        EMS_CUDA(cudaEventRecord(h->ev_fork, st));
-        EMS_CUDA(cudaStreamWaitEvent(h->side_stream, h->ev_fork, 0));
+        if (!early_fork) {
+            EMS_CUDA(cudaEventRecord(h->ev_fork, st));
+            EMS_CUDA(cudaStreamWaitEvent(h->side_stream, h->ev_fork, 0));
+        }
         mst = h->side_stream;
     }
     prof_mark(h, ph_mm, true, mst);
