@@ -78,7 +78,7 @@ def test_noalloc_rejects_requests_beyond_its_scratch(emsurf_lib):
 def test_noalloc_call_leaves_device_free_memory_unchanged(emsurf_lib):
     """A call needing ~40 MiB of scratch (3 x 4-per-face box blocks of 192 x 192
     triangle pairs, 10.6 MiB each, and a box/patch pair) changes nothing in
-    the driver's free-memory count, while the allocating entry point's
+    the CUDA driver's free-memory count, while the allocating entry point's
     scratch is visible to it only transiently (it frees before returning)."""
     import torch
     from paper_1911_04576_gb300 import binding as B
