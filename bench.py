@@ -81,16 +81,16 @@ def bf16_peak():
 MULTI_RHS = 32
 
 
-def mirror_orbit_section(B, W, torch, w, steps):
-    """The same solve on a handle that stores one FP32 bin per mirror orbit
-    (153 of 1024 bins at 16x16) instead of one per (k, -k) pair: time per
-    solve, per bin multiply and per FP32 product."""
-    h, V, nu, _, _ = build_problem(B, W, torch, w, B.MIXED, mirrors=True)
+def variant_section(B, W, torch, w, steps, **create_kw):
+    """The same solve on a handle built with other options (create_kw of
+    build_problem): time per solve, per bin multiply, per preconditioner
+    apply and per FP32 product."""
+    h, V, nu, _, _ = build_problem(B, W, torch, w, B.MIXED, **create_kw)
     X = torch.zeros_like(V)
     kw = dict(rtol=RTOL, restart=RESTART, max_iters=20000, max_refine=20, solver=B.SOLVER_MIXED)
     for _ in range(2):
         B.emsurf_solve(h, V, X, **kw)
-    B.emsurf_profile_phases(h, ["binmul32"])
+    B.emsurf_profile_phases(h, ["binmul32", "precond"])
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
@@ -100,11 +100,16 @@ def mirror_orbit_section(B, W, torch, w, steps):
     torch.cuda.synchronize()
     B.emsurf_profile(h, False)
     bin_ms, bin_n = B.emsurf_profile_read(h, "binmul32")
+    pc_ms, pc_n = B.emsurf_profile_read(h, "precond")
     form, per = B.emsurf_operator_layout(h)
-    out = {"form": "one stored bin per mirror orbit of %d" % per if form == 2 else "form %d" % form,
+    out = {"options": {k: bool(v) for k, v in create_kw.items()},
+           "spectrum": {0: "every bin", 1: "one bin per (k, -k) pair",
+                        2: "one bin per mirror orbit of %d" % per}[form],
            "stored_bins": B.emsurf_operator_info(h)[0], "solve_ms": round(e0.elapsed_time(e1) / steps, 3),
+           "converged": info[0]["converged"], "rel_residual": info[0]["rel_residual"],
            "iters": info[0]["iters"], "refinements": info[0]["refinements"],
            "binmul_ms_per_product": round(bin_ms / max(bin_n, 1), 5),
+           "precond_ms_per_apply": round(pc_ms / max(pc_n, 1), 5),
            "fp32_matvec_ms": round(time_matvec(B, torch, h, nu, 1, B.FP32), 4)}
     h.close()
     torch.cuda.empty_cache()
@@ -434,7 +439,8 @@ def dist_init():
     return ws, rank, local
 
 
-def build_problem(B, W, torch, w, precision, precond=True, max_rhs=None, tensor_cores=False, mirrors=False):
+def build_problem(B, W, torch, w, precision, precond=True, max_rhs=None, tensor_cores=False, mirrors=False,
+                  precond_int8=False):
     """Product-path setup (untimed): U_o, tables, macromodels, handle with
     the near-field preconditioner, V."""
     A, H = W.PERIOD, W.BOX_H
@@ -459,7 +465,8 @@ def build_problem(B, W, torch, w, precision, precond=True, max_rhs=None, tensor_
                         unknown_xy=xy, cell=(A, A),
                         precond_overlap=PC_OVERLAP * A / w.n if precond else 0.0,
                         tensor_cores=tensor_cores,
-                        mirrors=B.emsurf_setup_box_mirrors(A, A, w.n) if mirrors else None)
+                        mirrors=B.emsurf_setup_box_mirrors(A, A, w.n) if mirrors else None,
+                        precond_int8=precond_int8)
     torch.cuda.synchronize()
     t_create = time.time() - t0
     del L, K, Z
@@ -697,6 +704,8 @@ def main():
                     help="also time %d-rhs FP32 products, tensor cores vs FP32 kernels (0 = skip)" % 32)
     ap.add_argument("--serve-requests", type=int, default=24,
                     help="requests of the serving stream (0 = skip the serving measurement)")
+    ap.add_argument("--precond-int8", type=int, default=1,
+                    help="also time the solve with 8-bit preconditioner rows (0 = skip)")
     ap.add_argument("--mirror-orbits", type=int, default=1,
                     help="also time the solve on a handle with one FP32 bin per mirror orbit (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=SERVE_RATE,
@@ -851,8 +860,10 @@ def main():
     accuracy = accuracy_section(B, torch, h, V, X, w, zl) if args.accuracy else None
     _log("accuracy", accuracy)
     # ------------------------------------------------------------ mirror orbits
-    orbits = mirror_orbit_section(B, W, torch, w, min(args.steps, 10)) if args.mirror_orbits else None
+    orbits = variant_section(B, W, torch, w, min(args.steps, 10), mirrors=True) if args.mirror_orbits else None
     _log("mirror_orbits", orbits)
+    pc8 = variant_section(B, W, torch, w, min(args.steps, 10), precond_int8=True) if args.precond_int8 else None
+    _log("precond_int8", pc8)
     # ------------------------------------------------------------ many rhs
     multi = multi_rhs_section(B, W, torch, w, hbm) if args.multi_rhs else None
     _log("multi_rhs", multi)
@@ -978,6 +989,7 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clk,
         "mirror_orbits": orbits,
+        "precond_int8": pc8,
         "multi_rhs": multi,
         "accuracy": accuracy,
         "batched": batched,

@@ -136,6 +136,12 @@ typedef struct {
     int32_t sym_mask;
     const int32_t* sym_perm;
     const int8_t* sym_sign;
+    /* 1: store the preconditioner's owned inverse rows as 8-bit integers
+     * with one FP32 scale per row (absolute error <= 1/254 of the row's
+     * largest component per entry, half the bytes of the FP16 rows) for
+     * handles with max_rhs <= 2 and subdomains of up to 1024 unknowns;
+     * 0 (or otherwise): FP16 rows.  No counterpart in the paper.           */
+    int32_t precond_int8;
 } emsurf_problem;
 
 typedef struct {

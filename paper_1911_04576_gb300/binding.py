@@ -42,6 +42,7 @@ class Problem(C.Structure):
         ("unknown_xy", C.c_void_p), ("cell_a", C.c_double), ("cell_b", C.c_double),
         ("precond_overlap", C.c_double), ("tensor_cores", C.c_int32),
         ("sym_mask", C.c_int32), ("sym_perm", C.c_void_p), ("sym_sign", C.c_void_p),
+        ("precond_int8", C.c_int32),
     ]
 
 
@@ -167,14 +168,16 @@ class Handle:
 def emsurf_create(nx, ny, n_edges, n_unique, type_map, macromodels, offset_L, offset_K, coef,
                   uo_index, uo_sign, precision=FP64, max_rhs=1, grid=(0, 0),
                   tables_on_device=False, device_mem_budget=0, device=0, unknown_xy=None,
-                  cell=(0.0, 0.0), precond_overlap=0.0, tensor_cores=False, share=None, mirrors=None):
+                  cell=(0.0, 0.0), precond_overlap=0.0, tensor_cores=False, share=None, mirrors=None,
+                  precond_int8=False):
     """emsurf_create: host NumPy inputs (or torch CUDA tensors for the tables
     and macromodels when tables_on_device=True); returns a Handle.  With
     unknown_xy ([n_unique, 2] from emsurf_setup_unknown_xy), cell = (a, b) and
     precond_overlap > 0 the near-field preconditioner is built.  With share
     (a Handle of the same lattice) it calls emsurf_create_like: the tables are
     not read (may be None) and the new handle reads share's spectra.
-    mirrors: (perm, sign, mask) from emsurf_setup_box_mirrors, or None."""
+    mirrors: (perm, sign, mask) from emsurf_setup_box_mirrors, or None;
+    precond_int8: 8-bit preconditioner rows (one or two rhs)."""
     type_map = np.ascontiguousarray(type_map, dtype=np.int32)
     uo_index = np.ascontiguousarray(uo_index, dtype=np.int32)
     uo_sign = np.ascontiguousarray(uo_sign, dtype=np.int8)
@@ -203,6 +206,7 @@ def emsurf_create(nx, ny, n_edges, n_unique, type_map, macromodels, offset_L, of
     p.cell_a, p.cell_b = cell
     p.precond_overlap = precond_overlap
     p.tensor_cores = 1 if tensor_cores else 0
+    p.precond_int8 = 1 if precond_int8 else 0
     keep = [type_map, uo_index, uo_sign]
     if mirrors is not None:
         perm = np.ascontiguousarray(mirrors[0], dtype=np.int32)

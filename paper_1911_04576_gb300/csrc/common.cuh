@@ -265,7 +265,8 @@ struct emsurf_handle {
     int64_t pc_sub_total = 0;       // sum over cells of n_m
     int pc_own_max = 0;
     float2* pc_mat = nullptr;       // owned rows of A_m^{-1} in FP32 (create time only): own_m x ld_m per cell
-    void* pc_mat16 = nullptr;       // the same rows as FP16 (re, im) pairs, scaled per row
+    void* pc_mat16 = nullptr;       // the same rows as FP16 (re, im) pairs (or 8-bit, pc_int8), scaled per row
+    bool pc_int8 = false;           // rows stored as offset-binary 8-bit pairs (1-2 rhs handles that ask)
     float* pc_rscale = nullptr;     // [n_unique] scale of each owned row
     int64_t* pc_off = nullptr;      // [M] element offset of each cell's rows
     int32_t* pc_ld = nullptr;       // [M] row length (n_m rounded up to even)

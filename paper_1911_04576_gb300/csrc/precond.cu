@@ -305,6 +305,46 @@ __global__ void pc_to_half_kernel(const float2* __restrict__ X, const int64_t* _
     }
 }
 
+// 8-bit copy of the owned inverse rows (handles asking for it, 1-2 rhs): one
+// warp per owned row g, scale = (largest |component| of the row) / 127, each
+// component rounded to the nearest integer in [-127, 127] and stored offset
+// by 128 (so a byte b decodes to b - 128 exactly through its FP32 bit
+// pattern 2^23 + b); absolute error <= 2^-1 / 127 of the row's largest
+// component per entry.
+__global__ void pc_to_int8_kernel(const float2* __restrict__ X, const int64_t* __restrict__ xoff,
+                                  const int32_t* __restrict__ ldx, const int32_t* __restrict__ own_ptr, int M,
+                                  int n_rows, uchar2* __restrict__ Q, float* __restrict__ rscale) {
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < n_rows; g += warps) {
+        int lo = 0, hi = M;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (own_ptr[mid] <= g) lo = mid; else hi = mid;
+        }
+        const int m = lo, i = g - own_ptr[m], ld = ldx[m];
+        const float2* row = X + xoff[m] + (size_t)i * ld;
+        float mx = 0.f;
+        for (int c = lane; c < ld; c += 32) mx = fmaxf(mx, fmaxf(fabsf(row[c].x), fabsf(row[c].y)));
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const float sc = mx > 0.f ? mx / 127.f : 1.f;
+        const float inv = 1.f / sc;
+        uchar2* out = Q + xoff[m] + (size_t)i * ld;
+        for (int c = lane; c < ld; c += 32) {
+            const float qr = fminf(fmaxf(rintf(row[c].x * inv), -127.f), 127.f);
+            const float qi = fminf(fmaxf(rintf(row[c].y * inv), -127.f), 127.f);
+            out[c] = make_uchar2((unsigned char)((int)qr + 128), (unsigned char)((int)qi + 128));
+        }
+        if (lane == 0) rscale[g] = sc;
+    }
+}
+
+// b - 128 for byte k of w (offset-binary 8-bit entries): the float with bit
+// pattern 0x4B0000bb is 2^23 + b exactly
+__device__ __forceinline__ float pc_q8(uint32_t w, uint32_t k) {
+    return __int_as_float((int)__byte_perm(w, 0x4B000000u, 0x7540u | k)) - 8388736.0f;
+}
+
 // rs[q][j] = r[q][sub_ids[j]] in FP32 for every subdomain entry j (all cells
 // back to back, each cell's segment starting at an even index).
 template <typename VT>
@@ -423,9 +463,9 @@ constexpr int kApSegLoads = 8;      // 16-byte row loads per row and lane in fli
 template <typename VT>
 __device__ __forceinline__ float2 to_f2(VT v) { return make_float2((float)v.x, (float)v.y); }
 
-template <int RQ, typename VT>
+template <int RQ, typename VT, bool Q8>
 __global__ void __launch_bounds__(kApSegThreads, RQ == 1 ? 3 : 2)
-pc_apply_seg_kernel(const __half2* __restrict__ X, const float* __restrict__ rscale,
+pc_apply_seg_kernel(const void* __restrict__ X, const float* __restrict__ rscale,
                     const int64_t* __restrict__ xoff, const int32_t* __restrict__ ldx,
                     const int32_t* __restrict__ own_ptr, const int32_t* __restrict__ sub_ptr,
                     const int32_t* __restrict__ sub_ids, const VT* __restrict__ r, VT* __restrict__ y,
@@ -458,8 +498,13 @@ pc_apply_seg_kernel(const __half2* __restrict__ X, const float* __restrict__ rsc
                 rsm[q][c] = c < n ? to_f2(r[(size_t)q * n_unique + u]) : make_float2(0.f, 0.f);
         }
         __syncthreads();
-        const int quarter = ld >> 2;
-        const uint4* Xm = reinterpret_cast<const uint4*>(X + xoff[m]);
+        // 16-byte loads per row: 4 FP16 complex or 8 offset-binary 8-bit ones
+        constexpr int kPer = Q8 ? 8 : 4;
+        const int quarter = ld / kPer;
+        const uint4* Xm = reinterpret_cast<const uint4*>(reinterpret_cast<const unsigned char*>(X) +
+                                                         (size_t)xoff[m] * (Q8 ? 2 : 4));
+        // a load past the row reads as zeros (0x80 bytes in the 8-bit encoding)
+        const uint32_t zw = Q8 ? 0x80808080u : 0u;
         const int i0 = g - own_ptr[m], cnt = e - g;
         for (int p = 2 * warp; p < cnt; p += 2 * nw) {
             const int ia = i0 + p, ib = p + 1 < cnt ? ia + 1 : ia;
@@ -475,26 +520,43 @@ pc_apply_seg_kernel(const __half2* __restrict__ X, const float* __restrict__ rsc
 #pragma unroll
                 for (int u = 0; u < kApSegLoads; ++u) {
                     const bool in = c0 + 32 * u < quarter;
-                    xv[0][u] = in ? ldg_l2hint(ra + c0 + 32 * u, pol) : make_uint4(0u, 0u, 0u, 0u);
-                    xv[1][u] = in ? ldg_l2hint(rb + c0 + 32 * u, pol) : make_uint4(0u, 0u, 0u, 0u);
+                    xv[0][u] = in ? ldg_l2hint(ra + c0 + 32 * u, pol) : make_uint4(zw, zw, zw, zw);
+                    xv[1][u] = in ? ldg_l2hint(rb + c0 + 32 * u, pol) : make_uint4(zw, zw, zw, zw);
                 }
 #pragma unroll
                 for (int u = 0; u < kApSegLoads; ++u) {
                     const int c4 = min(c0 + 32 * u, quarter - 1);
 #pragma unroll
                     for (int q = 0; q < RQ; ++q) {
-                        const float4 r0 = reinterpret_cast<const float4*>(rsm[q])[2 * c4];
-                        const float4 r1 = reinterpret_cast<const float4*>(rsm[q])[2 * c4 + 1];
+                        if constexpr (Q8) {
+                            // 8 complex per load, two per 32-bit word (re, im, re, im)
 #pragma unroll
-                        for (int w = 0; w < 2; ++w) {
-                            const float2 f0 = __half22float2(*reinterpret_cast<const __half2*>(&xv[w][u].x));
-                            const float2 f1 = __half22float2(*reinterpret_cast<const __half2*>(&xv[w][u].y));
-                            const float2 f2 = __half22float2(*reinterpret_cast<const __half2*>(&xv[w][u].z));
-                            const float2 f3 = __half22float2(*reinterpret_cast<const __half2*>(&xv[w][u].w));
-                            acc[w][q].x += f0.x * r0.x - f0.y * r0.y + f1.x * r0.z - f1.y * r0.w +
-                                           f2.x * r1.x - f2.y * r1.y + f3.x * r1.z - f3.y * r1.w;
-                            acc[w][q].y += f0.x * r0.y + f0.y * r0.x + f1.x * r0.w + f1.y * r0.z +
-                                           f2.x * r1.y + f2.y * r1.x + f3.x * r1.w + f3.y * r1.z;
+                            for (int k = 0; k < 4; ++k) {
+                                const float4 rr = reinterpret_cast<const float4*>(rsm[q])[4 * c4 + k];
+#pragma unroll
+                                for (int w = 0; w < 2; ++w) {
+                                    const uint32_t wd = k == 0 ? xv[w][u].x : k == 1 ? xv[w][u].y
+                                                      : k == 2 ? xv[w][u].z : xv[w][u].w;
+                                    const float a0 = pc_q8(wd, 0), b0 = pc_q8(wd, 1);
+                                    const float a1 = pc_q8(wd, 2), b1 = pc_q8(wd, 3);
+                                    acc[w][q].x += a0 * rr.x - b0 * rr.y + a1 * rr.z - b1 * rr.w;
+                                    acc[w][q].y += a0 * rr.y + b0 * rr.x + a1 * rr.w + b1 * rr.z;
+                                }
+                            }
+                        } else {
+                            const float4 r0 = reinterpret_cast<const float4*>(rsm[q])[2 * c4];
+                            const float4 r1 = reinterpret_cast<const float4*>(rsm[q])[2 * c4 + 1];
+#pragma unroll
+                            for (int w = 0; w < 2; ++w) {
+                                const float2 f0 = __half22float2(*reinterpret_cast<const __half2*>(&xv[w][u].x));
+                                const float2 f1 = __half22float2(*reinterpret_cast<const __half2*>(&xv[w][u].y));
+                                const float2 f2 = __half22float2(*reinterpret_cast<const __half2*>(&xv[w][u].z));
+                                const float2 f3 = __half22float2(*reinterpret_cast<const __half2*>(&xv[w][u].w));
+                                acc[w][q].x += f0.x * r0.x - f0.y * r0.y + f1.x * r0.z - f1.y * r0.w +
+                                               f2.x * r1.x - f2.y * r1.y + f3.x * r1.z - f3.y * r1.w;
+                                acc[w][q].y += f0.x * r0.y + f0.y * r0.x + f1.x * r0.w + f1.y * r0.z +
+                                               f2.x * r1.y + f2.y * r1.x + f3.x * r1.w + f3.y * r1.z;
+                            }
                         }
                     }
                 }
@@ -540,18 +602,18 @@ pc_apply_seg_kernel(const __half2* __restrict__ X, const float* __restrict__ rsc
     }
 }
 
-template <int RQ, typename VT>
+template <int RQ, typename VT, bool Q8>
 int launch_apply_seg(emsurf_handle* h, const VT* r, VT* y, cudaStream_t st) {
-    static int occ[3][2] = {};
-    int& o = occ[RQ][sizeof(VT) == sizeof(float2) ? 1 : 0];
+    static int occ[3][2][2] = {};
+    int& o = occ[RQ][sizeof(VT) == sizeof(float2) ? 1 : 0][Q8 ? 1 : 0];
     if (!o) {
         int b = 0;
-        EMS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pc_apply_seg_kernel<RQ, VT>, kApSegThreads, 0));
+        EMS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pc_apply_seg_kernel<RQ, VT, Q8>, kApSegThreads, 0));
         o = std::max(b, 1);
     }
     const int blocks = std::max(1, std::min(h->num_sms * o, h->n_unique));
-    pc_apply_seg_kernel<RQ, VT><<<blocks, kApSegThreads, 0, st>>>(
-        reinterpret_cast<const __half2*>(h->pc_mat16), h->pc_rscale, h->pc_off, h->pc_ld, h->pc_own_ptr,
+    pc_apply_seg_kernel<RQ, VT, Q8><<<blocks, kApSegThreads, 0, st>>>(
+        h->pc_mat16, h->pc_rscale, h->pc_off, h->pc_ld, h->pc_own_ptr,
         h->pc_sub_ptr, h->pc_sub_ids, r, y, h->n_unique, h->M, h->n_unique);
     EMS_CUDA(cudaGetLastError());
     h->launches += 1;
@@ -588,8 +650,10 @@ int pc_apply_t(emsurf_handle* h, const VT* r, VT* y, int R, cudaStream_t st) {
         return EMSURF_EINVAL;
     }
     if (h->have_pc_tc && R >= kTcMinRhs) return pc_tc_apply<VT>(h, r, y, R, st);
+    if (h->pc_int8)      // 8-bit rows: handles of one or two rhs, rows of up to kApSegMaxLd
+        return R == 1 ? launch_apply_seg<1, VT, true>(h, r, y, st) : launch_apply_seg<2, VT, true>(h, r, y, st);
     if (R <= 2 && ((h->pc_nmax + 3) & ~3) <= kApSegMaxLd)
-        return R == 1 ? launch_apply_seg<1, VT>(h, r, y, st) : launch_apply_seg<2, VT>(h, r, y, st);
+        return R == 1 ? launch_apply_seg<1, VT, false>(h, r, y, st) : launch_apply_seg<2, VT, false>(h, r, y, st);
     const int total = (int)h->pc_sub_total;
     pc_gather_kernel<VT><<<std::min((total + 255) / 256, h->num_sms * 8), 256, 0, st>>>(
         r, h->pc_sub_ids, h->pc_sub_cell, h->pc_sub_ptr, h->pc_rs_off, h->pc_rs, total, h->n_unique,
@@ -704,9 +768,14 @@ int pc_build(emsurf_handle* h, const emsurf_problem* p) {
     // LU factors n_m x n_m (temporary); owned inverse rows own_m x ld_m (kept)
     std::vector<int64_t> moff(M + 1, 0), xoff(M + 1, 0);
     std::vector<int32_t> ldv(M);
+    int nmax_all = 0;
+    for (int m = 0; m < M; ++m) nmax_all = std::max(nmax_all, nsz[m]);
+    // 8-bit rows for the one- and two-rhs apply, when asked for and every row fits it
+    const bool q8 = p->precond_int8 && h->max_rhs <= 2 && ((nmax_all + 7) & ~7) <= kApSegMaxLd;
     for (int m = 0; m < M; ++m) {
         moff[m + 1] = moff[m] + (int64_t)nsz[m] * nsz[m];
-        ldv[m] = (nsz[m] + 3) & ~3;     // 4 complex per 16-byte load of the FP16 rows
+        // 16-byte loads: 4 complex of the FP16 rows, 8 of the 8-bit ones
+        ldv[m] = q8 ? (nsz[m] + 7) & ~7 : (nsz[m] + 3) & ~3;
         xoff[m + 1] = xoff[m] + (int64_t)own[m] * ldv[m];
         h->pc_own_max = std::max(h->pc_own_max, own[m]);
     }
@@ -816,12 +885,18 @@ int pc_build(emsurf_handle* h, const emsurf_problem* p) {
         }
     h->pc_elems = xoff[M];
     h->pc_sub_total = (int64_t)sids.size();
-    // FP16 rows with a per-row scale for the apply
-    EMS_TRY(dev_alloc(h, &h->pc_mat16, (size_t)xoff[M] * 4));
+    // FP16 (or 8-bit) rows with a per-row scale for the apply
+    EMS_TRY(dev_alloc(h, &h->pc_mat16, (size_t)xoff[M] * (q8 ? 2 : 4)));
     EMS_TRY(dev_alloc(h, (void**)&h->pc_rscale, (size_t)h->n_unique * sizeof(float)));
-    pc_to_half_kernel<<<h->num_sms * 16, 256, 0, st>>>(h->pc_mat, h->pc_off, h->pc_ld, h->pc_own_ptr, M,
-                                                       h->n_unique, reinterpret_cast<__half2*>(h->pc_mat16),
-                                                       h->pc_rscale);
+    if (q8)
+        pc_to_int8_kernel<<<h->num_sms * 16, 256, 0, st>>>(h->pc_mat, h->pc_off, h->pc_ld, h->pc_own_ptr, M,
+                                                           h->n_unique, reinterpret_cast<uchar2*>(h->pc_mat16),
+                                                           h->pc_rscale);
+    else
+        pc_to_half_kernel<<<h->num_sms * 16, 256, 0, st>>>(h->pc_mat, h->pc_off, h->pc_ld, h->pc_own_ptr, M,
+                                                           h->n_unique, reinterpret_cast<__half2*>(h->pc_mat16),
+                                                           h->pc_rscale);
+    h->pc_int8 = q8;
     EMS_CUDA(cudaGetLastError());
     h->launches += 1;
     h->have_pc = true;

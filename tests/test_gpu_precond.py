@@ -49,12 +49,12 @@ def phys():
                 xy=xy, delta=delta, subs=subs)
 
 
-def _handle(B, d, prec, delta=None, max_rhs=2, xy=None):
+def _handle(B, d, prec, delta=None, max_rhs=2, xy=None, int8=False):
     w = d["w"]
     return B.emsurf_create(w.nx, w.ny, w.E, d["nu"], d["tmap"], d["Z"], d["Lt"], d["Kt"], COEF,
                            d["idx"], d["sgn"], precision=prec, max_rhs=max_rhs,
                            unknown_xy=d["xy"] if xy is None else xy, cell=(A, A),
-                           precond_overlap=d["delta"] if delta is None else delta)
+                           precond_overlap=d["delta"] if delta is None else delta, precond_int8=int8)
 
 
 def _bound(Ad, subs):
@@ -253,3 +253,45 @@ def test_precond_apply_full_size_sampled(emsurf_lib):
         assert np.linalg.norm(y[S[own]] - ref) <= tol * np.linalg.norm(ref), (m, tol)
     B.emsurf_check(h)
     h.close()
+
+
+def test_precond_apply_int8_rows(emsurf_lib, phys):
+    """8-bit owned inverse rows (one FP32 scale per row): each entry within
+    1/254 of its row's largest component, so an output's error is at most
+    sqrt(n)/254 of the row's scale times |r| for random-phase r; the apply
+    stays within that of the oracle, and the preconditioned solves keep
+    their FP64 accuracy (flexible GMRES: the preconditioner only steers)."""
+    import torch
+    from paper_1911_04576_gb300 import binding as B
+    nmax = max(len(S) for S, _ in phys["subs"])
+    kap = max(np.linalg.cond(phys["Ad"][np.ix_(S, S)]) for S, _ in phys["subs"])
+    tol = (3 * nmax + 1) * U32 * kap + np.sqrt(nmax) / 254.0
+    for prec in ("MIXED", "FP64"):
+        h = _handle(B, phys, getattr(B, prec), int8=True)
+        r = W.random_vectors(2, phys["nu"], 43)
+        rd = torch.from_numpy(r).cuda()
+        yd = torch.full_like(rd, float("nan"))
+        B.emsurf_precond_apply(h, rd, yd)
+        y = yd.cpu().numpy()
+        h16 = _handle(B, phys, getattr(B, prec))
+        y16d = torch.full_like(rd, float("nan"))
+        B.emsurf_precond_apply(h16, rd, y16d)
+        y16 = y16d.cpu().numpy()
+        for q in range(2):
+            ref = precond.ras_apply(phys["Ad"], phys["subs"], r[q])
+            assert np.all(np.isfinite(y[q]))
+            e8 = np.linalg.norm(y[q] - ref) / np.linalg.norm(ref)
+            e16 = np.linalg.norm(y16[q] - ref) / np.linalg.norm(ref)
+            assert e8 <= tol, (prec, q, e8, tol)
+            assert e8 > e16          # the 8-bit rows are the coarser storage
+        h.close()
+        h16.close()
+    # solves with the 8-bit preconditioner reach the dense-LU solution
+    hs = _handle(B, phys, B.MIXED, max_rhs=1, int8=True)
+    b = torch.from_numpy(_rhs(phys, 1)).cuda()
+    x = torch.zeros_like(b)
+    st, info = B.emsurf_solve(hs, b, x, rtol=1e-10, restart=30, max_iters=4000, max_refine=20)
+    assert st == B.EMSURF_OK and info[0]["rel_residual"] <= 1e-10
+    xs = solve.dense_solve(phys["Ad"], phys["V"][0])
+    assert np.linalg.norm(x.cpu().numpy()[0] - xs) <= 1e-8 * np.linalg.norm(xs)
+    hs.close()
