@@ -334,6 +334,24 @@ EMSURF_API int emsurf_setup_box_mesh(double a, double b, double h, int32_t n,
 EMSURF_API int emsurf_setup_box_mirrors(double a, double b, int32_t n, int32_t* perm, int8_t* sign,
                                         int32_t* mask);
 
+/* The host logic of the mirror-orbit spectrum (exposed for tests and
+ * tools).  Group element e = bits (x mirror, y mirror, x <-> y applied
+ * first) acts on bin (kx, ky) of a px x py grid as k -> (+-kx, +-ky) mod
+ * the grid; n_elem is 4 (x and y mirrors) or 8 (with x <-> y; px == py).
+ * emsurf_setup_mirror_orbits: the orbits, each represented by its smallest
+ * bin index: *n_stored representatives rep[s] and n_elem slots each,
+ * slot_bin[s][j] (-1 past the orbit's size) and slot_elem[s][j] with
+ * slot_bin = e(rep); arrays of px*py (rep) and px*py*n_elem entries, or
+ * NULL to get *n_stored only.
+ * emsurf_setup_mirror_group: tperm[e][2E] = index | (sign < 0) << 31 of
+ * T_e = diag(P_e, det(e) P_e), P_e = Px^a Py^b Pd^c composed from the
+ * mirrors of emsurf_setup_box_mirrors (perm/sign [3][E]), det(e) =
+ * (-1)^(a+b+c); the FFT-domain blocks obey B^(e k) = T_e B^(k) T_e^T.    */
+EMSURF_API int emsurf_setup_mirror_orbits(int32_t px, int32_t py, int32_t n_elem, int32_t* n_stored,
+                                          int32_t* rep, int32_t* slot_bin, int32_t* slot_elem);
+EMSURF_API int emsurf_setup_mirror_group(int32_t n_edges, int32_t n_elem, const int32_t* perm, const int8_t* sign,
+                                         uint32_t* tperm);
+
 /* Flat square PEC patch (Sec. II-A: J only on PEC) of side `side` centred
  * on the cell axis at height z, n x n quads each cut along (c00,c11);
  * vertices (i,j) at index i*(n+1)+j; RWGs on interior edges only.         */

@@ -83,6 +83,8 @@ def lib():
         L.emsurf_setup_box_mesh.argtypes = [C.c_double, C.c_double, C.c_double, i32, vp] + [vp] * 7
         L.emsurf_setup_patch_mesh.argtypes = [C.c_double, C.c_double, i32] + [vp] * 7
         L.emsurf_setup_box_mirrors.argtypes = [C.c_double, C.c_double, i32, vp, vp, ip]
+        L.emsurf_setup_mirror_orbits.argtypes = [i32, i32, i32, ip, vp, vp, vp]
+        L.emsurf_setup_mirror_group.argtypes = [i32, i32, vp, vp, vp]
         L.emsurf_setup_overlap.argtypes = [i32, i32, i32, vp, vp, ip]
         L.emsurf_precond_apply.argtypes = [vp, vp, vp, i32, vp]
         L.emsurf_selftest_wait.argtypes = [vp, C.c_int64, vp]
@@ -323,6 +325,27 @@ def emsurf_setup_box_mirrors(a, b, n):
     _check(lib().emsurf_setup_box_mirrors(C.c_double(a), C.c_double(b), n, _ptr(perm), _ptr(sign),
                                           C.byref(mask)))
     return perm, sign, mask.value
+
+
+def emsurf_setup_mirror_orbits(px, py, n_elem):
+    """emsurf_setup_mirror_orbits: (rep [S], slot_bin [S, n_elem], slot_elem [S, n_elem])."""
+    ns = C.c_int32()
+    rep = np.zeros(px * py, np.int32)
+    sb = np.zeros(px * py * n_elem, np.int32)
+    se = np.zeros(px * py * n_elem, np.int32)
+    _check(lib().emsurf_setup_mirror_orbits(px, py, n_elem, C.byref(ns), _ptr(rep), _ptr(sb), _ptr(se)))
+    S = ns.value
+    return rep[:S], sb[:S * n_elem].reshape(S, n_elem), se[:S * n_elem].reshape(S, n_elem)
+
+
+def emsurf_setup_mirror_group(perm, sign, n_elem):
+    """emsurf_setup_mirror_group: (index [n_elem, 2E], sign [n_elem, 2E]) of T_e."""
+    perm = np.ascontiguousarray(perm, dtype=np.int32)
+    sign = np.ascontiguousarray(sign, dtype=np.int8)
+    E = perm.shape[1]
+    t = np.zeros((n_elem, 2 * E), np.uint32)
+    _check(lib().emsurf_setup_mirror_group(E, n_elem, _ptr(perm), _ptr(sign), _ptr(t)))
+    return (t & 0x7FFFFFFF).astype(np.int64), np.where(t >> 31, -1, 1)
 
 
 def emsurf_setup_patch_mesh(side, z, n):

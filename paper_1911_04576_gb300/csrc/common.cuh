@@ -354,6 +354,16 @@ int build_operator(emsurf_handle* h, Operator<T2>& op, const emsurf_problem* pr,
                    const Operator<T2>* share = nullptr);
 // share: a handle of the same lattice whose Fourier-domain blocks are reused
 int derive_fp32_operator(emsurf_handle* h, const emsurf_problem* pr, const emsurf_handle* share = nullptr);
+// mirror orbits of the spectrum's bins (setup.cpp): the bin of group element
+// e (bit 0: x mirror, bit 1: y mirror, bit 2: x <-> y, applied first) acting
+// on bin (kx, ky); the signed permutations T_e [G][2E] (index | sign << 31)
+// composed from the box's mirror permutations; the orbits, one
+// representative (the smallest bin) each, G slots (bin, element) per
+// representative, bin -1 past the orbit's size
+int orbit_image(int e, int kx, int ky, int px, int py);
+void mirror_group_perms(int E, int G, const int32_t* perm, const int8_t* sign, std::vector<uint32_t>& tperm);
+void mirror_orbits(int px, int py, int G, std::vector<int32_t>& rep, std::vector<int32_t>& obin,
+                   std::vector<int32_t>& oelem);
 int adopt_fp32_form(emsurf_handle* h, const emsurf_handle* share);
 int clear_wait_error(emsurf_handle* h);
 int build_ds_planes(emsurf_handle* h, const emsurf_handle* share = nullptr);

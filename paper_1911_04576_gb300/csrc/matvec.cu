@@ -1657,15 +1657,6 @@ constexpr int kOrbJB8 = 8;    // and of the 8-slot one (with x <-> y)
 constexpr int kOrbNT4 = 1;    // consumer threads per test row (4 accumulator sets each)
 constexpr int kOrbNT8 = 2;
 
-// bin of the group element e (bit 0: x mirror, bit 1: y mirror, bit 2:
-// x <-> y, applied first) acting on bin (kx, ky) of a px x py grid
-int orbit_image(int e, int kx, int ky, int px, int py) {
-    if (e & 4) std::swap(kx, ky);
-    if (e & 2) ky = (py - ky) % py;
-    if (e & 1) kx = (px - kx) % px;
-    return ky * px + kx;
-}
-
 // The FP32 spectrum as one stored bin per mirror orbit, when the problem
 // gives the box's mirrors and they hold on the FP64 blocks.  *used = false
 // (and nothing allocated) otherwise.
@@ -1730,60 +1721,13 @@ int orbit_spectrum(emsurf_handle* h, const emsurf_problem* pr, const double2* B6
         cudaFree(dout);
         if (!holds) return EMSURF_OK;
     }
-    // the signed permutations T_e = diag(P_e, det(e) P_e), P_e = Px^a Py^b Pd^c
+    // the signed permutations T_e of the group elements and the orbits
+    // (host logic in the setup library)
     const int E2 = 2 * E;
-    std::vector<uint32_t> tperm((size_t)G * E2);
-    for (int e = 0; e < G; ++e) {
-        std::vector<int32_t> pi(E);
-        std::vector<int8_t> sg(E, 1);
-        for (int n = 0; n < E; ++n) pi[n] = n;
-        int det = 1;
-        for (int g = 0; g < 3; ++g) {
-            if (!(e & (1 << g))) continue;
-            std::vector<int32_t> npi(E);
-            std::vector<int8_t> nsg(E);
-            for (int n = 0; n < E; ++n) {     // P <- P P_g
-                const int m = pr->sym_perm[(size_t)g * E + n];
-                npi[n] = pi[m];
-                nsg[n] = (int8_t)(pr->sym_sign[(size_t)g * E + n] * sg[m]);
-            }
-            pi.swap(npi);
-            sg.swap(nsg);
-            det = -det;
-        }
-        for (int n = 0; n < E; ++n) {
-            tperm[(size_t)e * E2 + n] = (uint32_t)pi[n] | (sg[n] < 0 ? 0x80000000u : 0u);
-            tperm[(size_t)e * E2 + E + n] = (uint32_t)(E + pi[n]) | (sg[n] * det < 0 ? 0x80000000u : 0u);
-        }
-    }
-    // orbits: the smallest bin index represents each; its slots are the
-    // distinct images in the order of the group elements
+    std::vector<uint32_t> tperm;
+    mirror_group_perms(E, G, pr->sym_perm, pr->sym_sign, tperm);
     std::vector<int32_t> rep, obin, oelem;
-    for (int ky = 0; ky < py; ++ky)
-        for (int kx = 0; kx < px; ++kx) {
-            const int b = ky * px + kx;
-            int imgs[8];
-            int r = b;
-            for (int e = 0; e < G; ++e) {
-                imgs[e] = orbit_image(e, kx, ky, px, py);
-                r = std::min(r, imgs[e]);
-            }
-            if (r != b) continue;
-            rep.push_back(b);
-            int nslot = 0;
-            for (int e = 0; e < G; ++e) {
-                bool seen = false;
-                for (int u = 0; u < nslot; ++u) seen = seen || obin[obin.size() - nslot + u] == imgs[e];
-                if (seen) continue;
-                obin.push_back(imgs[e]);
-                oelem.push_back(e);
-                ++nslot;
-            }
-            for (; nslot < G; ++nslot) {
-                obin.push_back(-1);
-                oelem.push_back(0);
-            }
-        }
+    mirror_orbits(px, py, G, rep, obin, oelem);
     const int nst = (int)rep.size();
     int32_t *drep = nullptr, *dob = nullptr, *doe = nullptr;
     uint32_t* dtp = nullptr;

@@ -521,6 +521,78 @@ int slab_cell_plan(double a, double b, double h, int n, const double* zlevels, d
     return EMSURF_OK;
 }
 
+int orbit_image(int e, int kx, int ky, int px, int py) {
+    if (e & 4) std::swap(kx, ky);
+    if (e & 2) ky = (py - ky) % py;
+    if (e & 1) kx = (px - kx) % px;
+    return ky * px + kx;
+}
+
+// T_e = diag(P_e, det(e) P_e) with P_e = Px^a Py^b Pd^c (bits a, b, c of e),
+// P e_n = sign_n e_perm[n]; products composed as (P_A P_B) e_n =
+// sign_B[n] sign_A[perm_B[n]] e_perm_A[perm_B[n]]
+void mirror_group_perms(int E, int G, const int32_t* perm, const int8_t* sign, std::vector<uint32_t>& tperm) {
+    const int E2 = 2 * E;
+    tperm.assign((size_t)G * E2, 0u);
+    for (int e = 0; e < G; ++e) {
+        std::vector<int32_t> pi(E);
+        std::vector<int8_t> sg(E, 1);
+        for (int n = 0; n < E; ++n) pi[n] = n;
+        int det = 1;
+        for (int g = 0; g < 3; ++g) {
+            if (!(e & (1 << g))) continue;
+            std::vector<int32_t> npi(E);
+            std::vector<int8_t> nsg(E);
+            for (int n = 0; n < E; ++n) {     // P <- P P_g
+                const int m = perm[(size_t)g * E + n];
+                npi[n] = pi[m];
+                nsg[n] = (int8_t)(sign[(size_t)g * E + n] * sg[m]);
+            }
+            pi.swap(npi);
+            sg.swap(nsg);
+            det = -det;
+        }
+        for (int n = 0; n < E; ++n) {
+            tperm[(size_t)e * E2 + n] = (uint32_t)pi[n] | (sg[n] < 0 ? 0x80000000u : 0u);
+            tperm[(size_t)e * E2 + E + n] = (uint32_t)(E + pi[n]) | (sg[n] * det < 0 ? 0x80000000u : 0u);
+        }
+    }
+}
+
+// the smallest bin index represents each orbit; its slots are the distinct
+// images in the order of the group elements
+void mirror_orbits(int px, int py, int G, std::vector<int32_t>& rep, std::vector<int32_t>& obin,
+                   std::vector<int32_t>& oelem) {
+    rep.clear();
+    obin.clear();
+    oelem.clear();
+    for (int ky = 0; ky < py; ++ky)
+        for (int kx = 0; kx < px; ++kx) {
+            const int b = ky * px + kx;
+            int imgs[8];
+            int r = b;
+            for (int e = 0; e < G; ++e) {
+                imgs[e] = orbit_image(e, kx, ky, px, py);
+                r = std::min(r, imgs[e]);
+            }
+            if (r != b) continue;
+            rep.push_back(b);
+            int nslot = 0;
+            for (int e = 0; e < G; ++e) {
+                bool seen = false;
+                for (int u = 0; u < nslot; ++u) seen = seen || obin[obin.size() - nslot + u] == imgs[e];
+                if (seen) continue;
+                obin.push_back(imgs[e]);
+                oelem.push_back(e);
+                ++nslot;
+            }
+            for (; nslot < G; ++nslot) {
+                obin.push_back(-1);
+                oelem.push_back(0);
+            }
+        }
+}
+
 namespace {
 }  // namespace
 }  // namespace emsurf
@@ -560,6 +632,33 @@ EMSURF_API int emsurf_setup_box_mirrors(double a, double b, int32_t n, int32_t* 
     *mask = box_mirror_perms(n, square, m, grid, p, sg);
     std::copy(p.begin(), p.end(), perm);
     std::copy(sg.begin(), sg.end(), sign);
+    return EMSURF_OK;
+}
+
+EMSURF_API int emsurf_setup_mirror_orbits(int32_t px, int32_t py, int32_t n_elem, int32_t* n_stored,
+                                          int32_t* rep, int32_t* slot_bin, int32_t* slot_elem) {
+    if (px < 1 || py < 1 || (n_elem != 4 && n_elem != 8) || (n_elem == 8 && px != py) || !n_stored) {
+        set_error("mirror orbits: grid >= 1, 4 or 8 group elements (8 on a square grid)");
+        return EMSURF_EINVAL;
+    }
+    std::vector<int32_t> r, ob, oe;
+    mirror_orbits(px, py, n_elem, r, ob, oe);
+    *n_stored = (int32_t)r.size();
+    if (rep) std::copy(r.begin(), r.end(), rep);
+    if (slot_bin) std::copy(ob.begin(), ob.end(), slot_bin);
+    if (slot_elem) std::copy(oe.begin(), oe.end(), slot_elem);
+    return EMSURF_OK;
+}
+
+EMSURF_API int emsurf_setup_mirror_group(int32_t n_edges, int32_t n_elem, const int32_t* perm, const int8_t* sign,
+                                         uint32_t* tperm) {
+    if (n_edges < 1 || (n_elem != 4 && n_elem != 8) || !perm || !sign || !tperm) {
+        set_error("mirror group: bad arguments");
+        return EMSURF_EINVAL;
+    }
+    std::vector<uint32_t> t;
+    mirror_group_perms(n_edges, n_elem, perm, sign, t);
+    std::copy(t.begin(), t.end(), tperm);
     return EMSURF_OK;
 }
 

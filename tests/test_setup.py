@@ -130,3 +130,69 @@ def test_box_mirrors_match_oracle(B, a, b, n):
     for g, name in enumerate("xyd"):
         if name in ref:
             assert np.array_equal(perm[g], ref[name][0]) and np.array_equal(sign[g], ref[name][1]), name
+
+
+def _image(e, kx, ky, px, py):
+    if e & 4:
+        kx, ky = ky, kx
+    if e & 2:
+        ky = (py - ky) % py
+    if e & 1:
+        kx = (px - kx) % px
+    return ky * px + kx
+
+
+@pytest.mark.parametrize("px,py,G", [(5, 5, 8), (8, 8, 8), (32, 32, 8), (7, 9, 4), (10, 4, 4), (32, 32, 4),
+                                     (1, 1, 8), (2, 3, 4)])
+def test_mirror_orbits_partition_the_bins(B, px, py, G):
+    rep, sb, se = B.emsurf_setup_mirror_orbits(px, py, G)
+    seen = np.zeros(px * py, int)
+    for s, r in enumerate(rep):
+        ky, kx = divmod(int(r), px)
+        orbit = {_image(e, kx, ky, px, py) for e in range(G)}
+        assert min(orbit) == r                                  # the smallest bin represents
+        got = [b for b in sb[s] if b >= 0]
+        assert sorted(got) == sorted(orbit) and len(got) == len(orbit)
+        for j, b in enumerate(sb[s]):
+            if b >= 0:
+                assert _image(int(se[s, j]), kx, ky, px, py) == b
+                seen[b] += 1
+    assert np.all(seen == 1)
+
+
+def test_mirror_group_relation_on_the_oracle_spectrum(B):
+    """The library's T_e of every group element, applied to the spectrum of
+    the oracle's own tables (union-jack box, 3 x 3 lattice, 5 x 5 grid),
+    gives the spectrum at the mirrored bin: B^(e k) = T_e B^(k) T_e^T."""
+    from oracle import lattice
+    a, h, n, nx = 0.015, 0.0075, 2, 3
+    k0 = 2 * np.pi / 0.03
+    box = box_mesh(a, a, h, n)
+    E = box.n_rwg
+    Lt, Kt = lattice.offset_tables(box, nx, nx, a, a, k0)
+    perm, sign, mask = B.emsurf_setup_box_mirrors(a, a, n)
+    assert mask == 7
+    P = 5
+    coef = (1j * k0, 1.0, -1.0, 1j * k0)
+
+    def spec(T):
+        S = np.zeros((P, P, E, E), complex)
+        for dy in range(-(nx - 1), nx):
+            for dx in range(-(nx - 1), nx):
+                S[dy % P, dx % P] += T[dy + nx - 1, dx + nx - 1]
+        return np.fft.fft2(S, axes=(0, 1))
+    Ls, Ks = spec(Lt), spec(Kt)
+
+    def full(ky, kx):
+        return np.block([[coef[0] * Ls[ky, kx], coef[1] * Ks[ky, kx]], [coef[2] * Ks[ky, kx], coef[3] * Ls[ky, kx]]])
+    idx, sg = B.emsurf_setup_mirror_group(perm, sign, 8)
+    scale = max(np.abs(Ls).max(), np.abs(Ks).max())
+    for e in range(8):
+        T = np.zeros((2 * E, 2 * E))
+        T[idx[e], np.arange(2 * E)] = sg[e]                    # T e_n = sign_n e_idx(n)
+        for ky in range(P):
+            for kx in range(P):
+                b = _image(e, kx, ky, P, P)
+                lhs = full(b // P, b % P)
+                rhs = T @ full(ky, kx) @ T.T
+                assert np.abs(lhs - rhs).max() <= 1e-12 * scale * max(abs(c) for c in coef), (e, kx, ky)
